@@ -1,0 +1,282 @@
+"""ctypes binding of the FP64 CPU oracle (``cov_oracle.c``).
+
+Test infrastructure only (see the package docstring).  All arrays are float64
+numpy arrays, C-contiguous, row-major, shapes as documented per function.
+
+Parity status per function:
+  gmm_score, svgd_field, sinkhorn_*, sinkhorn_field, sinkhorn_divergence,
+  linearize, rollout, lqr_track -- pinned (tests/test_oracle_*.py).
+  solve -- composition of pinned parts; pinned only by the one-iteration
+  composition check (single integrator, R -> 0: the trajectory moves by
+  eta * field) and by the decrease of the coverage divergence.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "cov_oracle.c")
+_HDR = os.path.join(_HERE, "cov_oracle.h")
+_LIB = os.path.join(_HERE, "libcov_oracle.so")
+
+SINGLE_INT, DOUBLE_INT, UNICYCLE = 0, 1, 2
+FIELD_SVGD, FIELD_SINKHORN = 0, 1
+MODEL_DIMS = {SINGLE_INT: (2, 2), DOUBLE_INT: (4, 2), UNICYCLE: (3, 2)}
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (plain IEEE FP64, no fast-math)."""
+    stale = (not os.path.exists(_LIB)) or any(
+        os.path.getmtime(p) > os.path.getmtime(_LIB) for p in (_SRC, _HDR))
+    if force or stale:
+        cmd = ["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11",
+               "-D_GNU_SOURCE", "-o", _LIB, _SRC, "-lm"]
+        subprocess.check_call(cmd)
+    return _LIB
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        _lib = ctypes.CDLL(_LIB)
+        _declare(_lib)
+    return _lib
+
+
+_D = ctypes.POINTER(ctypes.c_double)
+_I = ctypes.POINTER(ctypes.c_int)
+_i, _d = ctypes.c_int, ctypes.c_double
+
+
+def _declare(L):
+    sig = {
+        "orc_set_threads": (None, [_i]),
+        "orc_get_threads": (_i, []),
+        "orc_gmm_logpdf": (_d, [_D, _i, _i, _D, _D, _D]),
+        "orc_gmm_score": (None, [_D, _i, _i, _i, _D, _D, _D, _D]),
+        "orc_svgd_field": (None, [_D, _i, _i, _D, _d, _I, _i, _D]),
+        "orc_sinkhorn_g_update": (None, [_D, _i, _D, _i, _i, _d, _D, _I, _i, _D]),
+        "orc_sinkhorn_f_update": (None, [_D, _i, _D, _i, _D, _i, _d, _D, _I, _i, _D]),
+        "orc_sinkhorn_p_update": (None, [_D, _i, _i, _d, _D, _I, _i, _D]),
+        "orc_sinkhorn": (None, [_D, _i, _D, _i, _D, _i, _d, _i, _i, _D, _D, _D]),
+        "orc_sinkhorn_field": (None, [_D, _i, _D, _i, _D, _i, _d, _D, _D, _I, _i, _D]),
+        "orc_sinkhorn_converge": (_i, [_D, _i, _D, _i, _D, _i, _d, _d, _i, _D, _D, _D]),
+        "orc_sinkhorn_marginals": (None, [_D, _i, _D, _i, _D, _i, _d, _D, _D, _D, _D]),
+        "orc_sinkhorn_divergence": (_d, [_D, _i, _D, _i, _D, _i, _d, _d, _i]),
+        "orc_model_dims": (_i, [_i, _I, _I]),
+        "orc_step": (None, [_i, _D, _D, _d, _D]),
+        "orc_linearize": (None, [_i, _D, _D, _i, _d, _D, _D]),
+        "orc_rollout": (None, [_i, _D, _D, _i, _d, _D]),
+        "orc_lqr_track": (None, [_D, _D, _D, _D, _D, _i, _i, _i, _D, _D, _D]),
+        "orc_solve": (_i, [_i, _i, _d, _D, _i, _i, _D, _D, _i, _i, _D, _D, _D,
+                           _d, _i, _d, _D, _D, _d, _i, _D, _D]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(_D)
+
+
+def _rows(rows):
+    if rows is None:
+        return None, None, 0
+    r = np.ascontiguousarray(rows, dtype=np.int32)
+    return r, r.ctypes.data_as(_I), int(r.size)
+
+
+def set_threads(n: int) -> None:
+    lib().orc_set_threads(int(n))
+
+
+def get_threads() -> int:
+    return int(lib().orc_get_threads())
+
+
+# -- reference distribution ------------------------------------------------
+def gmm_logpdf(x, w, mu, sigma) -> float:
+    x, w, mu, sigma = _f64(x), _f64(w), _f64(mu), _f64(sigma)
+    return float(lib().orc_gmm_logpdf(_p(x), x.size, w.size, _p(w), _p(mu), _p(sigma)))
+
+
+def gmm_score(x, w, mu, sigma):
+    x, w, mu, sigma = _f64(x), _f64(w), _f64(mu), _f64(sigma)
+    T, d = x.shape
+    out = np.empty((T, d))
+    lib().orc_gmm_score(_p(x), T, d, w.size, _p(w), _p(mu), _p(sigma), _p(out))
+    return out
+
+
+# -- SVGD field (Eq. 4) ----------------------------------------------------
+def svgd_field(x, score, h, rows=None):
+    x, score = _f64(x), _f64(score)
+    T, d = x.shape
+    keep, rp, nr = _rows(rows)
+    out = np.empty((nr if rows is not None else T, d))
+    lib().orc_svgd_field(_p(x), T, d, _p(score), float(h), rp, nr, _p(out))
+    return out
+
+
+# -- Sinkhorn (Eq. 5-7) ----------------------------------------------------
+def sinkhorn_g_update(x, y, eps, f, rows=None):
+    x, y, f = _f64(x), _f64(y), _f64(f)
+    T, d = x.shape
+    M = y.shape[0]
+    keep, rp, nr = _rows(rows)
+    out = np.empty(nr if rows is not None else M)
+    lib().orc_sinkhorn_g_update(_p(x), T, _p(y), M, d, float(eps), _p(f), rp, nr, _p(out))
+    return out
+
+
+def sinkhorn_f_update(x, y, b, eps, g, rows=None):
+    x, y, g = _f64(x), _f64(y), _f64(g)
+    b = None if b is None else _f64(b)
+    T, d = x.shape
+    M = y.shape[0]
+    keep, rp, nr = _rows(rows)
+    out = np.empty(nr if rows is not None else T)
+    lib().orc_sinkhorn_f_update(_p(x), T, _p(y), M, _p(b), d, float(eps), _p(g), rp, nr, _p(out))
+    return out
+
+
+def sinkhorn_p_update(x, eps, p_old, rows=None):
+    x, p_old = _f64(x), _f64(p_old)
+    T, d = x.shape
+    keep, rp, nr = _rows(rows)
+    out = np.empty(nr if rows is not None else T)
+    lib().orc_sinkhorn_p_update(_p(x), T, d, float(eps), _p(p_old), rp, nr, _p(out))
+    return out
+
+
+def sinkhorn(x, y, b, eps, n_iter, f=None, g=None, p=None):
+    """Fixed-iteration log-domain Sinkhorn; cold start unless f, g, p given."""
+    x, y = _f64(x), _f64(y)
+    b = None if b is None else _f64(b)
+    T, d = x.shape
+    M = y.shape[0]
+    warm = f is not None
+    f = np.zeros(T) if f is None else _f64(f).copy()
+    g = np.zeros(M) if g is None else _f64(g).copy()
+    p = np.zeros(T) if p is None else _f64(p).copy()
+    lib().orc_sinkhorn(_p(x), T, _p(y), M, _p(b), d, float(eps), int(n_iter),
+                       int(warm), _p(f), _p(g), _p(p))
+    return f, g, p
+
+
+def sinkhorn_field(x, y, b, eps, g, p, rows=None):
+    x, y, g, p = _f64(x), _f64(y), _f64(g), _f64(p)
+    b = None if b is None else _f64(b)
+    T, d = x.shape
+    M = y.shape[0]
+    keep, rp, nr = _rows(rows)
+    out = np.empty((nr if rows is not None else T, d))
+    lib().orc_sinkhorn_field(_p(x), T, _p(y), M, _p(b), d, float(eps), _p(g), _p(p), rp, nr, _p(out))
+    return out
+
+
+def sinkhorn_converge(x, y, b, eps, tol=1e-12, max_iter=100000):
+    x, y = _f64(x), _f64(y)
+    b = None if b is None else _f64(b)
+    T, d = x.shape
+    M = y.shape[0]
+    f, g, p = np.zeros(T), np.zeros(M), np.zeros(T)
+    it = lib().orc_sinkhorn_converge(_p(x), T, _p(y), M, _p(b), d, float(eps), float(tol),
+                                     int(max_iter), _p(f), _p(g), _p(p))
+    return f, g, p, int(it)
+
+
+def sinkhorn_marginals(x, y, b, eps, f, g):
+    x, y, f, g = _f64(x), _f64(y), _f64(f), _f64(g)
+    b = None if b is None else _f64(b)
+    T, d = x.shape
+    M = y.shape[0]
+    rs, cs = np.empty(T), np.empty(M)
+    lib().orc_sinkhorn_marginals(_p(x), T, _p(y), M, _p(b), d, float(eps), _p(f), _p(g), _p(rs), _p(cs))
+    return rs, cs
+
+
+def sinkhorn_divergence(x, y, b, eps, tol=1e-10, max_iter=100000) -> float:
+    x, y = _f64(x), _f64(y)
+    b = None if b is None else _f64(b)
+    T, d = x.shape
+    M = y.shape[0]
+    return float(lib().orc_sinkhorn_divergence(_p(x), T, _p(y), M, _p(b), d, float(eps),
+                                               float(tol), int(max_iter)))
+
+
+# -- dynamics, linearisation, rollout (Eq. 3, 8) ---------------------------
+def step(model, s, u, dt):
+    s, u = _f64(s), _f64(u)
+    n, m = MODEL_DIMS[model]
+    out = np.empty(n)
+    lib().orc_step(int(model), _p(s), _p(u), float(dt), _p(out))
+    return out
+
+
+def linearize(model, s, u, dt):
+    s, u = _f64(s), _f64(u)
+    n, m = MODEL_DIMS[model]
+    T = u.shape[0]
+    A, B = np.empty((T, n, n)), np.empty((T, n, m))
+    lib().orc_linearize(int(model), _p(s), _p(u), T, float(dt), _p(A), _p(B))
+    return A, B
+
+
+def rollout(model, s0, u, dt):
+    s0, u = _f64(s0), _f64(u)
+    n, m = MODEL_DIMS[model]
+    T = u.shape[0]
+    s = np.empty((T + 1, n))
+    lib().orc_rollout(int(model), _p(s0), _p(u), T, float(dt), _p(s))
+    return s
+
+
+# -- LQR flow matching (Eq. 9-10) ------------------------------------------
+def lqr_track(A, B, Q, R, abar):
+    """abar[t-1] is the target at t = 1..T; returns v [T,m], z [T+1,n], P_1."""
+    A, B, Q, R, abar = _f64(A), _f64(B), _f64(Q), _f64(R), _f64(abar)
+    T, n, m = B.shape
+    v, z, P1 = np.empty((T, m)), np.empty((T + 1, n)), np.full((n, n), np.nan)
+    lib().orc_lqr_track(_p(A), _p(B), _p(Q), _p(R), _p(abar), T, n, m, _p(v), _p(z), _p(P1))
+    return v, z, P1
+
+
+# -- outer iteration -------------------------------------------------------
+def solve(model, dt, s0, u0, field, Q, R, eta, n_outer, *, d=2, y=None, b=None,
+          gmm=None, eps=0.0, n_iter=0, h=0.0):
+    """Returns (u, s) after n_outer iterations; u0 [T,m] is not modified."""
+    n, m = MODEL_DIMS[model]
+    u = _f64(u0).copy()
+    T = u.shape[0]
+    s = np.empty((T + 1, n))
+    s0 = _f64(s0)
+    Q, R = _f64(Q), _f64(R)
+    yv = None if y is None else _f64(y)
+    bv = None if b is None else _f64(b)
+    M = 0 if y is None else yv.shape[0]
+    if gmm is not None:
+        gw, gmu, gs = (_f64(v) for v in gmm)
+        K = gw.size
+    else:
+        gw = gmu = gs = None
+        K = 0
+    rc = lib().orc_solve(int(model), T, float(dt), _p(s0), int(field), int(d), _p(yv), _p(bv), M, K,
+                         _p(gw), _p(gmu), _p(gs), float(eps), int(n_iter), float(h), _p(Q), _p(R),
+                         float(eta), int(n_outer), _p(u), _p(s))
+    if rc != 0:
+        raise ValueError("orc_solve: bad arguments")
+    return u, s

@@ -1,0 +1,178 @@
+"""Pins of the oracle's log-domain Sinkhorn, Sinkhorn divergence (Eq. 5-6)
+and Sinkhorn-divergence field (Eq. 7).
+
+Independent references used here: the scaling-domain (matrix) form of the
+same Sinkhorn iterations written with scipy's distance matrix, the exact
+assignment optimum from scipy's linear_sum_assignment, the eps -> infinity
+limit, a hand-worked single pair, symmetry (y = x) and finite differences.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+from scipy.optimize import linear_sum_assignment
+from scipy.spatial.distance import cdist
+
+from paper_2511_11514_b300 import workloads as wl
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "worked_examples.json")
+
+
+def _scaling_sinkhorn(x, y, b, eps, n_iter):
+    """Kernel-matrix Sinkhorn (Cuturi 2013 form) with the same schedule as
+    the oracle's reading: g first, then f, then the averaged self update.
+    u = exp(f/eps), v = exp(g/eps), w = exp(p/eps)."""
+    T, M = len(x), len(y)
+    a = np.full(T, 1.0 / T)
+    b = b / b.sum()
+    K = np.exp(-cdist(x, y, "sqeuclidean") / eps)
+    Ks = np.exp(-cdist(x, x, "sqeuclidean") / eps)
+    u, w = np.ones(T), np.ones(T)
+    for _ in range(n_iter):
+        v = 1.0 / (K.T @ (a * u))
+        u = 1.0 / (K @ (b * v))
+        w = np.sqrt(w / (Ks @ (a * w)))
+    return eps * np.log(u), eps * np.log(v), eps * np.log(w)
+
+
+def test_fixed_iterations_match_scaling_form(orc):
+    x = wl.random_points(23, 2, seed=1)
+    y = wl.random_points(31, 2, seed=2)
+    b = wl.random_weights(31, seed=3)
+    eps = 0.08
+    for n_iter in (1, 2, 7):
+        f, g, p = orc.sinkhorn(x, y, b, eps, n_iter)
+        f2, g2, p2 = _scaling_sinkhorn(x, y, b, eps, n_iter)
+        np.testing.assert_allclose(f, f2, rtol=0, atol=1e-12)
+        np.testing.assert_allclose(g, g2, rtol=0, atol=1e-12)
+        np.testing.assert_allclose(p, p2, rtol=0, atol=1e-12)
+
+
+def test_converged_marginals(orc):
+    """Marginals of pi = a b exp((f+g-c)/eps), rebuilt with scipy's cost."""
+    x = wl.random_points(20, 2, seed=4)
+    y = wl.random_points(30, 2, seed=5)
+    b = wl.random_weights(30, seed=6)
+    eps = 0.05
+    f, g, p, it = orc.sinkhorn_converge(x, y, b, eps, tol=1e-12)
+    assert it > 0
+    a = np.full(20, 1 / 20)
+    b = b / b.sum()
+    pi = a[:, None] * b[None, :] * np.exp((f[:, None] + g[None, :] - cdist(x, y, "sqeuclidean")) / eps)
+    assert np.abs(pi.sum(1) - a).sum() <= 1e-10
+    assert np.abs(pi.sum(0) - b).sum() <= 1e-10
+    ps = a[:, None] * a[None, :] * np.exp((p[:, None] + p[None, :] - cdist(x, x, "sqeuclidean")) / eps)
+    assert np.abs(ps.sum(1) - a).sum() <= 1e-10
+    rs, cs = orc.sinkhorn_marginals(x, y, b, eps, f, g)
+    np.testing.assert_allclose(rs, pi.sum(1), rtol=1e-12)
+    np.testing.assert_allclose(cs, pi.sum(0), rtol=1e-12)
+
+
+def test_single_pair_hand_example(orc):
+    ex = json.load(open(GOLDEN))["sinkhorn_single_pair"]
+    x, y, eps = np.array(ex["x"]), np.array(ex["y"]), ex["eps"]
+    assert orc.sinkhorn_divergence(x, y, None, eps) == pytest.approx(ex["divergence"], rel=1e-12)
+    f, g, p = orc.sinkhorn(x, y, None, eps, 3)
+    np.testing.assert_allclose(orc.sinkhorn_field(x, y, None, eps, g, p), ex["field"], rtol=1e-12)
+
+
+def test_large_eps_limit(orc):
+    """eps -> infinity: pi -> a (x) b, so OT(x,y) -> E|x-y|^2 and the
+    debiased divergence -> |mean x - mean y|^2, and every field vector ->
+    2 (mean y - mean x)."""
+    x = wl.random_points(12, 2, seed=7)
+    y = wl.random_points(15, 2, seed=8) + 0.3
+    b = wl.random_weights(15, seed=9)
+    eps = 1e5
+    dmu = (b / b.sum()) @ y - x.mean(0)
+    assert orc.sinkhorn_divergence(x, y, b, eps) == pytest.approx(float(dmu @ dmu), rel=1e-5)
+    f, g, p = orc.sinkhorn(x, y, b, eps, 5)
+    fld = orc.sinkhorn_field(x, y, b, eps, g, p)
+    np.testing.assert_allclose(fld, np.tile(2 * dmu, (12, 1)), rtol=1e-4)
+
+
+def test_small_eps_reaches_assignment_optimum(orc):
+    """eps -> 0 with T = M and uniform weights: OT(x,y) -> the optimal
+    assignment cost, with 0 <= OT_eps - OT_0 <= eps log n (KL form)."""
+    n = 7
+    x = wl.random_points(n, 2, seed=10)
+    y = wl.random_points(n, 2, seed=11)
+    C = cdist(x, y, "sqeuclidean")
+    r, c = linear_sum_assignment(C)
+    ot0 = C[r, c].mean()
+    eps = 5e-3
+    f, g, p, it = orc.sinkhorn_converge(x, y, None, eps, tol=1e-11)
+    assert it > 0
+    ot = f.mean() + g.mean()
+    assert -1e-10 <= ot - ot0 <= eps * np.log(n) + 1e-10
+
+
+def test_field_vanishes_when_reference_equals_trajectory(orc):
+    """y = x with equal weights: cross and self problems coincide, so the
+    debiased field is zero (this fails if the self term is dropped)."""
+    x = wl.random_points(16, 2, seed=12)
+    eps = 0.03
+    f, g, p, it = orc.sinkhorn_converge(x, x, None, eps, tol=1e-13)
+    fld = orc.sinkhorn_field(x, x, None, eps, g, p)
+    assert np.abs(fld).max() < 1e-9
+    # without the debiasing term the field would not vanish
+    f2, g2, p2 = orc.sinkhorn(x, x, None, eps, 0)
+    assert np.abs(orc.sinkhorn_field(x, x, None, eps, g, np.full(16, -1e3))).max() > 1e-3
+
+
+def test_translation_equivariance(orc):
+    x = wl.random_points(9, 2, seed=13)
+    y = wl.random_points(11, 2, seed=14)
+    eps = 0.04
+    sh = np.array([0.25, -0.5])  # exact binary fractions keep costs identical
+    f, g, p = orc.sinkhorn(x, y, None, eps, 6)
+    f2, g2, p2 = orc.sinkhorn(x + sh, y + sh, None, eps, 6)
+    np.testing.assert_allclose(f2, f, atol=1e-12)
+    np.testing.assert_allclose(p2, p, atol=1e-12)
+    np.testing.assert_allclose(orc.sinkhorn_field(x + sh, y + sh, None, eps, g2, p2),
+                               orc.sinkhorn_field(x, y, None, eps, g, p), atol=1e-12)
+
+
+def test_field_is_scaled_descent_direction_of_divergence(orc):
+    """Envelope theorem at convergence: dD/dx_i = -(1/T) field_i, checked by
+    central finite differences (step 1e-6) of the divergence value."""
+    T, M = 6, 7
+    x = wl.random_points(T, 2, seed=15)
+    y = wl.random_points(M, 2, seed=16)
+    b = wl.random_weights(M, seed=17)
+    eps = 0.1
+    f, g, p, it = orc.sinkhorn_converge(x, y, b, eps, tol=1e-14)
+    fld = orc.sinkhorn_field(x, y, b, eps, g, p)
+    hstep = 1e-6
+    for i in range(T):
+        for c in range(2):
+            xp, xm = x.copy(), x.copy()
+            xp[i, c] += hstep
+            xm[i, c] -= hstep
+            fd = (orc.sinkhorn_divergence(xp, y, b, eps, tol=1e-14) -
+                  orc.sinkhorn_divergence(xm, y, b, eps, tol=1e-14)) / (2 * hstep)
+            assert fd == pytest.approx(-fld[i, c] / T, rel=1e-5, abs=1e-8)
+
+
+def test_row_updates_match_full_updates(orc):
+    x = wl.random_points(19, 2, seed=18)
+    y = wl.random_points(27, 2, seed=19)
+    b = wl.random_weights(27, seed=20)
+    eps = 0.02
+    f, g, p = orc.sinkhorn(x, y, b, eps, 3)
+    rows_y = np.array([0, 26, 3])
+    rows_x = np.array([18, 0, 4])
+    g_full = orc.sinkhorn_g_update(x, y, eps, f)
+    np.testing.assert_array_equal(orc.sinkhorn_g_update(x, y, eps, f, rows=rows_y), g_full[rows_y])
+    f_full = orc.sinkhorn_f_update(x, y, b, eps, g_full)
+    np.testing.assert_array_equal(orc.sinkhorn_f_update(x, y, b, eps, g_full, rows=rows_x), f_full[rows_x])
+    p_full = orc.sinkhorn_p_update(x, eps, p)
+    np.testing.assert_array_equal(orc.sinkhorn_p_update(x, eps, p, rows=rows_x), p_full[rows_x])
+    fld = orc.sinkhorn_field(x, y, b, eps, g, p)
+    np.testing.assert_array_equal(orc.sinkhorn_field(x, y, b, eps, g, p, rows=rows_x), fld[rows_x])
+    # one more iteration from the state = the fixed-iteration run of 4
+    f4, g4, p4 = orc.sinkhorn(x, y, b, eps, 4)
+    np.testing.assert_array_equal(g_full, g4)
+    np.testing.assert_array_equal(f_full, f4)
+    np.testing.assert_array_equal(p_full, p4)

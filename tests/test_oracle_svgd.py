@@ -1,0 +1,126 @@
+"""Pins of the oracle's reference score and Stein variational field (Eq. 4).
+
+Each check compares the oracle with something other than itself: a library
+log-density, a closed form, or a Gaussian-integral mean-field limit.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+from scipy.special import logsumexp
+from scipy.stats import multivariate_normal
+
+from paper_2511_11514_b300 import workloads as wl
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "worked_examples.json")
+
+
+def _scipy_logq(x, w, mu, sigma):
+    terms = [np.log(w[k]) + multivariate_normal(mu[k], sigma[k] ** 2 * np.eye(len(x))).logpdf(x)
+             for k in range(len(w))]
+    return logsumexp(terms)
+
+
+def test_gmm_logpdf_matches_scipy(orc):
+    w, mu, sigma = wl.gmm_params(4, seed=3)
+    for x in wl.random_points(5, 2, seed=4):
+        assert orc.gmm_logpdf(x, w, mu, sigma) == pytest.approx(_scipy_logq(x, w, mu, sigma), rel=1e-12)
+
+
+def test_gmm_score_is_gradient_of_library_logpdf(orc):
+    """Central finite difference (step 1e-6) of scipy's mixture log-density."""
+    w, mu, sigma = wl.gmm_params(5, seed=11)
+    x = wl.random_points(6, 2, seed=12)
+    score = orc.gmm_score(x, w, mu, sigma)
+    h = 1e-6
+    for i in range(len(x)):
+        for c in range(2):
+            e = np.zeros(2)
+            e[c] = h
+            fd = (_scipy_logq(x[i] + e, w, mu, sigma) - _scipy_logq(x[i] - e, w, mu, sigma)) / (2 * h)
+            assert score[i, c] == pytest.approx(fd, rel=1e-5, abs=1e-4)
+
+
+def test_gmm_score_single_gaussian_closed_form(orc):
+    mu = np.array([[0.4, 0.6]])
+    sigma = np.array([0.07])
+    x = wl.random_points(8, 2, seed=5)
+    score = orc.gmm_score(x, np.array([1.0]), mu, sigma)
+    np.testing.assert_allclose(score, -(x - mu) / sigma[0] ** 2, rtol=1e-13)
+
+
+def test_svgd_single_point_is_score(orc):
+    """T = 1: k(x,x) = 1 and its gradient vanishes, so g = score."""
+    ex = json.load(open(GOLDEN))["svgd_single_point"]
+    x = np.array([ex["x"]])
+    score = orc.gmm_score(x, np.array([1.0]), np.array([ex["mu"]]), np.array([ex["sigma"]]))
+    g = orc.svgd_field(x, score, h=ex["h"])
+    np.testing.assert_allclose(g[0], ex["field"], rtol=1e-13)
+
+
+def test_svgd_two_points_hand_example(orc):
+    """T = 2 with zero score at distance h: worked by hand in the fixture."""
+    ex = json.load(open(GOLDEN))["svgd_two_points_zero_score"]
+    x = np.array(ex["x"])
+    g = orc.svgd_field(x, np.zeros_like(x), h=ex["h"])
+    np.testing.assert_allclose(g, ex["field"], rtol=1e-12)
+
+
+def test_svgd_repulsion_cancels_in_sum(orc):
+    """With zero score the kernel-gradient terms are antisymmetric in (i,j),
+    so the field sums to zero."""
+    x = wl.random_points(17, 2, seed=8)
+    g = orc.svgd_field(x, np.zeros_like(x), h=0.2)
+    assert np.abs(g.sum(axis=0)).max() < 1e-13 * np.abs(g).max() * len(x)
+
+
+def _mean_field(xe, mu, sig, m, s, h):
+    """Gaussian-integral closed form of E_{x'~N(m, s^2 I)}[k(x', xe) score(x')
+    + grad_{x'} k(x', xe)] for q = N(mu, sig^2 I) and the RBF kernel with
+    length-scale h (d = 2)."""
+    d = len(xe)
+    v = h * h + s * s
+    Z = (h * h / v) ** (d / 2) * np.exp(-np.sum((xe - m) ** 2) / (2 * v))
+    mpost = (h * h * m + s * s * xe) / v            # E[x' k] / E[k]
+    return Z * (-(mpost - mu) / sig ** 2 + (xe - mpost) / h ** 2)
+
+
+def test_svgd_gaussian_mean_field_limit(orc):
+    """T = 2^16 particles from N(m, s^2 I), target N(mu, sig^2 I): the field
+    at sampled particles matches the Gaussian-integral closed form within
+    4 Monte-Carlo standard errors (estimated from 8 independent batches)."""
+    mu, sig = np.array([0.3, -0.2]), 0.8
+    m, s, h = np.array([0.0, 0.1]), 1.0, 0.7
+    T = 1 << 16
+    g = wl.rng(21)
+    x = m + s * g.standard_normal(size=(T, 2))
+    score = -(x - mu) / sig ** 2
+    rows = np.arange(8)
+    got = orc.svgd_field(x, score, h, rows=rows)
+    # batch means -> standard error of the full-T estimate
+    B = 8
+    bs = T // B
+    per_batch = []
+    for bi in range(B):
+        xb = x[bi * bs:(bi + 1) * bs]
+        xb = np.concatenate([x[rows], xb])
+        sb = -(xb - mu) / sig ** 2
+        per_batch.append(orc.svgd_field(xb, sb, h, rows=rows))
+    se = np.std(np.stack(per_batch), axis=0, ddof=1) / np.sqrt(B)
+    want = np.stack([_mean_field(x[i], mu, sig, m, s, h) for i in rows])
+    assert np.all(np.abs(got - want) <= 4 * se + 1e-12)
+    # the pin would catch a flipped repulsive term or a kernel without the 1/2
+    flipped = np.stack([_mean_field(x[i], mu, sig, m, s, h) -
+                        2 * ((x[i] - (h * h * m + s * s * x[i]) / (h * h + s * s)) / h ** 2) *
+                        (h * h / (h * h + s * s)) * np.exp(-np.sum((x[i] - m) ** 2) / (2 * (h * h + s * s)))
+                        for i in rows])
+    assert np.any(np.abs(got - flipped) > 4 * se)
+
+
+def test_svgd_row_subset_matches_full(orc):
+    x = wl.random_points(33, 2, seed=9)
+    sc = orc.gmm_score(x, *wl.gmm_params(3, seed=2))
+    full = orc.svgd_field(x, sc, 0.05)
+    rows = np.array([0, 5, 32, 7])
+    np.testing.assert_array_equal(orc.svgd_field(x, sc, 0.05, rows=rows), full[rows])
