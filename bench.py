@@ -1,0 +1,364 @@
+#!/usr/bin/env python
+"""Benchmark of the coverage hot path: one outer iteration (a "step") of the
+Sinkhorn coverage solve on the double-integrator workload -- T = 4096
+trajectory samples, M = 16384 reference samples from an 8-component
+Gaussian mixture, eps = 0.005, 50 log-domain Sinkhorn iterations per field,
+FP32 field + FP64 LQR/rollout -- through the C-ABI (cov_solve_continue).
+
+Prints ONE JSON line (rank 0).  `value` is pair evaluations per second over
+all ranks (one independent coverage problem per rank, weak scaling); one
+pair evaluation is one (row, column) term of a soft-c-transform, so a field
+costs n_iter (2TM + T^2) + (TM + T^2) of them.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+      [--workload NAME]
+
+`--impl reference` times the FP64 CPU oracle on the host cores (bounded
+row samples of the same workload); it is the reference arm.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_2511_11514_b300 import workloads as wl  # noqa: E402
+
+METRIC = "pair-evals/s & ms per coverage solve (field % of FP32/SFU roofline) vs FP64 oracle"
+UNIT = "pair-evals/s"
+DEFAULT_WORKLOAD = wl.SINKHORN_DOUBLE_T4096.name
+L2_FLUSH_BYTES = 256 << 20
+# Algorithmic FP32-pipe instructions per Sinkhorn pair evaluation (base-2,
+# prescaled, column term folded): 2 FMA for the d = 2 inner product, the max,
+# the max subtraction and the accumulation; one exponential (MUFU ex2).
+FP32_OPS_PER_PAIR = 5
+SM_COUNT_NOMINAL = 148
+SM_MAX_MHZ_NOMINAL = 2032.0
+FP32_LANES_PER_SM_CLK = 128
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(wl.WORKLOADS))
+    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
+
+
+# -- clocks sampled during the timed region ------------------------------------
+class Clocks:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, local_rank):
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+        self.index = vis.split(",")[local_rank] if vis else str(local_rank)
+        self.proc = None
+
+    def start(self):
+        self.out = tempfile.TemporaryFile(mode="w+")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", self.index, f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
+                                         stdout=self.out, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.out.seek(0)
+        sm, mx, pw, reasons = [], [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in self.out.read().splitlines():
+            f = [v.strip() for v in line.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+                pw.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "sm_mhz_min": min(sm),
+                "power_w_max": max(pw), "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# -- CPU oracle timing (reference arm and cpu_baseline) ---------------------------
+def oracle_sample(inst, rows, seed=0):
+    """One bounded sample of the workload on the oracle: `rows` rows of each
+    Sinkhorn update (g, f, p) from the initial trajectory.  Returns (pairs,
+    seconds)."""
+    import oracle as orc
+    w = inst.wl
+    s = orc.rollout(w.model, inst.s0, inst.u0, w.dt)
+    x = wl.f32_pair(s[1:, :2])[1]
+    y = inst.y
+    T, M = len(x), len(y)
+    r = wl.rng(seed)
+    ry = r.choice(M, size=min(rows, M), replace=False)
+    rx = r.choice(T, size=min(rows, T), replace=False)
+    f = np.zeros(T)
+    t0 = time.perf_counter()
+    g = orc.sinkhorn_g_update(x, y, w.eps, f, rows=ry)
+    gf = np.zeros(M)
+    gf[ry] = g
+    orc.sinkhorn_f_update(x, y, None, w.eps, gf, rows=rx)
+    orc.sinkhorn_p_update(x, w.eps, np.zeros(T), rows=rx)
+    dt = time.perf_counter() - t0
+    return len(ry) * T + len(rx) * M + len(rx) * T, dt
+
+
+def calibrate_rows(inst, seconds):
+    import oracle as orc
+    orc.set_threads(os.cpu_count() or 1)
+    pairs, dt = oracle_sample(inst, 64)
+    rate = pairs / max(dt, 1e-9)
+    per_row = pairs / 64
+    return max(64, int(seconds * rate / per_row))
+
+
+def cpu_baseline(inst, seconds):
+    import oracle as orc
+    orc.set_threads(os.cpu_count() or 1)
+    rows = calibrate_rows(inst, seconds)
+    pairs, dt = oracle_sample(inst, rows, seed=1)
+    T, M = inst.wl.T, inst.wl.M
+    return {"value": pairs / dt, "unit": UNIT, "cores": orc.get_threads(), "kind": "oracle",
+            "sample": f"FP64 oracle: {rows} rows of each Sinkhorn update (g over T={T}, f over M={M}, p over T) "
+                      f"of the workload, {pairs:.3e} pair evaluations in {dt:.1f} s, {orc.get_threads()} threads"}
+
+
+def workload_config(w, extra=None):
+    cfg = {"workload": w.name, "T": w.T, "M": w.M, "d": 2, "eps": w.eps, "n_iter": w.n_iter,
+           "model": {0: "single_integrator", 1: "double_integrator", 2: "unicycle"}[w.model],
+           "reference": "8-component Gaussian mixture" if w.reference == "gmm" else "512x512 density map",
+           "pairs_per_step": w.pairs_per_field, "outer_iterations_per_solve": w.n_outer,
+           "precision": "f32 field (MUFU ex2.approx), f64 LQR and rollout"}
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+def run_reference(args):
+    rank, local_rank, world = dist_env()
+    if rank != 0:
+        return 0
+    import oracle as orc
+    orc.build()
+    w = wl.WORKLOADS[args.workload]
+    inst = wl.make_instance(w)
+    orc.set_threads(os.cpu_count() or 1)
+    rows = calibrate_rows(inst, 3.0)
+    for k in range(args.warmup):
+        oracle_sample(inst, rows, seed=100 + k)
+    tot_pairs, tot_s = 0, 0.0
+    for k in range(args.steps):
+        p, dt = oracle_sample(inst, rows, seed=k)
+        tot_pairs += p
+        tot_s += dt
+    value = tot_pairs / tot_s
+    sample = (f"FP64 oracle, per step {rows} rows of each Sinkhorn update (g, f, p) of the workload, "
+              f"{orc.get_threads()} threads")
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000.0 * tot_s / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded Philox)",
+            "impl": "reference",
+            "config": workload_config(w, {"sample_rows_per_update": rows}),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": orc.get_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# -- our arm ------------------------------------------------------------------------
+def alu_peak(probe, num_sms):
+    """ALU roofline in pair evaluations/s at the maximum SM clock: min of the
+    MUFU ex2 rate (one exponential per pair) and the FP32 lane rate divided
+    by the algorithmic FP32 ops per pair.  The per-SM per-clock MUFU width is
+    read from the probe (rounded to a power of two)."""
+    clk = probe["sm_clock_mhz"] * 1e6
+    ex2_per_sm_clk = probe["ex2_lane_ops_s"] / (num_sms * clk)
+    width = 2 ** round(np.log2(max(ex2_per_sm_clk, 1.0)))
+    mufu = SM_COUNT_NOMINAL * width * SM_MAX_MHZ_NOMINAL * 1e6
+    fp32 = SM_COUNT_NOMINAL * FP32_LANES_PER_SM_CLK * SM_MAX_MHZ_NOMINAL * 1e6 / FP32_OPS_PER_PAIR
+    return min(mufu, fp32), {"mufu_ex2_per_sm_clk": width, "mufu_pairs_s": mufu, "fp32_pairs_s": fp32,
+                             "probe_ex2_per_sm_clk_measured": ex2_per_sm_clk}
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2511_11514_b300 import binding as cov
+
+    rank, local_rank, world = dist_env()
+    torch.cuda.set_device(local_rank)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    w = wl.WORKLOADS[args.workload]
+    if w.field != wl.FIELD_SINKHORN:
+        raise SystemExit("bench.py times the Sinkhorn workloads")
+    inst = wl.make_instance(w, seed=w.seed + rank)
+    ctx = cov.Context(local_rank)
+    dev = torch.device("cuda", local_rank)
+    y = torch.as_tensor(inst.y, dtype=torch.float32, device=dev).contiguous()
+    prob = cov.make_problem(w.model, w.T, w.dt, inst.s0, w.field, inst.Q, inst.R, w.eta, y=y, eps=w.eps,
+                            n_iter=w.n_iter)
+    u = torch.as_tensor(inst.u0, dtype=torch.float64, device=dev).contiguous()
+    s = cov.cov_solve(ctx, prob, 0, u)  # trajectory of the initial controls
+    stream = torch.cuda.current_stream()
+    for _ in range(max(3, args.warmup)):
+        cov.cov_solve_continue(ctx, prob, 1, u, s)
+    torch.cuda.synchronize()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clocks = Clocks(local_rank)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.2)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()  # L2 flush between steps (outside the step events)
+        ev0[k].record(stream)
+        cov.cov_solve_continue(ctx, prob, 1, u, s)
+        ev1[k].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
+    total_ms = torch.tensor([sum(step_ms)], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(total_ms, op=dist.ReduceOp.MAX)
+    total_ms = float(total_ms.item())
+    st, flags = ctx.device_status()
+    if st != cov.COV_OK:
+        raise SystemExit(f"device status {cov.status_string(st)} flags {flags}")
+    pairs_step = w.pairs_per_field
+    value = world * pairs_step * args.steps / (total_ms * 1e-3)
+    ms_per_step = total_ms / args.steps
+
+    # ---- roofline of the dominant kernel (the all-pairs soft-c-transform) -------
+    x = s[1:, :2].float().contiguous()
+    n_lo, n_hi = 4, 24
+
+    def field_ms(n_iter, reps=5):
+        ts = []
+        for _ in range(reps):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            cov.cov_field_sinkhorn(ctx, x, y, w.eps, n_iter, field=False)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return statistics.median(ts)
+
+    t_iter_ms = (field_ms(n_hi) - field_ms(n_lo)) / (n_hi - n_lo)
+    pairs_iter = 2 * w.T * w.M + w.T * w.T
+    achieved = pairs_iter / (t_iter_ms * 1e-3)
+    probe = cov.cov_probe_peaks(ctx, 4096)
+    peak, peak_info = alu_peak(probe, torch.cuda.get_device_properties(dev).multi_processor_count)
+
+    # ---- end to end through the C-ABI with host buffers ---------------------------
+    u_h = torch.as_tensor(inst.u0, dtype=torch.float64).pin_memory()
+    y_h = torch.as_tensor(inst.y, dtype=torch.float32).pin_memory()
+    u_out = torch.empty_like(u_h).pin_memory()
+    s_out = torch.empty((w.T + 1, s.shape[1]), dtype=torch.float64).pin_memory()
+    e_ms = []
+    for k in range(args.e2e_steps + 2):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        flush.zero_()
+        a.record(stream)
+        u.copy_(u_h, non_blocking=True)
+        y.copy_(y_h, non_blocking=True)
+        cov.cov_solve(ctx, prob, 1, u, s)
+        u_out.copy_(u, non_blocking=True)
+        s_out.copy_(s, non_blocking=True)
+        b.record(stream)
+        b.synchronize()
+        if k >= 2:
+            e_ms.append(a.elapsed_time(b))
+    e2e_ms = statistics.mean(e_ms)
+    h2d = u_h.numel() * 8 + y_h.numel() * 4
+    d2h = u_out.numel() * 8 + s_out.numel() * 8
+
+    launches_per_step = 3 * w.n_iter + 8
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded Philox Gaussian-mixture reference)",
+            "config": workload_config(w, {
+                "parallelism": f"{world} independent problems (one per GPU)" if world > 1 else "single GPU",
+                "l2": "flushed between steps (256 MiB write outside the per-step CUDA events)",
+                "ms_per_coverage_solve": ms_per_step * w.n_outer,
+                "wall_s_timed_region": wall}),
+            "roofline": {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Gpair/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "kernel": "pairs_kernel (Sinkhorn g/f/p soft-c-transform), per iteration of 3 launches",
+                         "peak_basis": "derived: 148 SMs x 2032 MHz x min(MUFU ex2 width, 128 FP32 lanes / "
+                                       f"{FP32_OPS_PER_PAIR} ops per pair)",
+                         "peak_detail": peak_info, "probe": probe},
+            "clocks": clk,
+            "e2e": {"value": pairs_step / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+            "gpu_launches": launches_per_step * args.steps,
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(inst, args.cpu_seconds)
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

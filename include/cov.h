@@ -1,0 +1,263 @@
+/*
+ * cov.h -- C-ABI of the B300 (sm_103a) coverage-field library, libcov.so.
+ *
+ * Coverage trajectory synthesis as statistical inference (Sun, Kwon,
+ * Murphey, arXiv 2511.11514).  A trajectory s_0..s_T is read as the sample
+ * set {s_1..s_T} with weights a_i = 1/T (Eq. 1).  Each outer iteration
+ *   1. evaluates a coverage flow field a_i = g(x_i) at all T samples at once
+ *      (Sec. II-B, "Parallelized flow evaluation"), either the Stein
+ *      variational field (Eq. 4) or the Sinkhorn-divergence field (Eq. 6-7);
+ *   2. tracks the field with the LQR problem of Eq. 9-10 on the linearised
+ *      dynamics of Eq. 8, giving a control direction v*;
+ *   3. updates u <- u + eta v* and rolls the dynamics out again (Sec. II-C).
+ *
+ * Conventions shared by every call below:
+ *   - Array arguments are caller-owned DEVICE pointers (e.g. the data_ptr()
+ *     of a contiguous torch tensor on the context's device), row-major, with
+ *     the shapes given in brackets.  Small descriptors (cov_gmm, Q, R,
+ *     cov_problem) are host memory and are read during the call.
+ *   - Calls are asynchronous on `stream` (a cudaStream_t; NULL is the legacy
+ *     default stream).  Inputs must stay alive until the stream reaches the
+ *     call.  Argument errors are returned synchronously and nothing is
+ *     launched.  Device-detected conditions (non-finite values, a wait that
+ *     ran out of its iteration limit, a non-SPD Riccati matrix) set bits in a
+ *     device status word read by cov_get_device_status().
+ *   - All device scratch memory is the context's workspace.  The workspace is
+ *     allocated only by cov_ctx_create / cov_ctx_reserve*; no other call
+ *     allocates.  A call whose sizes need more workspace than reserved
+ *     returns COV_ERR_WORKSPACE without launching.
+ *   - The library never aborts, prints or traps.  One context must not be
+ *     used from two host threads at the same time, and two calls on the same
+ *     context must not overlap on the GPU (they share the workspace): issue
+ *     them on one stream, or synchronise between streams.
+ *   - Precision: fields are computed in FP32 (exponentials through the
+ *     ex2.approx special-function unit), the LQR step and the rollout in
+ *     FP64.
+ */
+#ifndef COV_H
+#define COV_H
+
+#include <stddef.h>
+
+#if defined(__GNUC__)
+#define COV_API __attribute__((visibility("default")))
+#else
+#define COV_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* cov_stream_t; /* == cudaStream_t */
+typedef struct cov_ctx cov_ctx;
+
+typedef enum {
+    COV_OK = 0,
+    COV_ERR_INVALID_ARG = 1, /* bad size, pointer, or parameter value */
+    COV_ERR_WORKSPACE = 2,   /* workspace too small / allocation failed */
+    COV_ERR_CUDA = 3,        /* a CUDA runtime call failed */
+    COV_ERR_NONFINITE = 4,   /* device status: NaN/Inf or non-SPD matrix */
+    COV_ERR_TIMEOUT = 5,     /* device status: a bounded wait gave up */
+    COV_ERR_UNSUPPORTED = 6  /* size/dimension combination not built */
+} cov_status;
+
+/* Dynamics models: explicit Euler s_{t+1} = s_t + dt f(s_t, u_t).
+ *   COV_SINGLE_INT  s = (p0, p1),          u = (u0, u1)           n=2, m=2
+ *   COV_DOUBLE_INT  s = (p0, p1, v0, v1),  u = (acc0, acc1)       n=4, m=2
+ *   COV_UNICYCLE    s = (x, y, theta),     u = (speed, turn rate) n=3, m=2 */
+enum { COV_SINGLE_INT = 0, COV_DOUBLE_INT = 1, COV_UNICYCLE = 2 };
+enum { COV_FIELD_SVGD = 0, COV_FIELD_SINKHORN = 1 };
+/* cov_field_sinkhorn flags */
+enum { COV_WARM_START = 1 };
+/* device status bits (cov_get_device_status) */
+enum { COV_DEV_NONFINITE = 1, COV_DEV_TIMEOUT = 2, COV_DEV_NOT_SPD = 4 };
+
+#define COV_MAX_D 6        /* coverage dimensions of a field */
+#define COV_MAX_GMM 32     /* mixture components */
+#define COV_MAX_N 4        /* LQR state dimension */
+#define COV_MAX_M 3        /* LQR control dimension */
+
+/* Isotropic Gaussian mixture q(x) = sum_k w_k N(x; mu_k, sigma_k^2 I), the
+ * reference of the Stein field (Sec. II-A: q given as a density).  Host
+ * memory; the weights are normalised by the library. */
+typedef struct {
+    int K;              /* 1..COV_MAX_GMM */
+    int d;              /* dimension, equal to the field's d */
+    const float* w;     /* [K]   positive weights */
+    const float* mu;    /* [K][d] means */
+    const float* sigma; /* [K]   standard deviations, > 0 */
+} cov_gmm;
+
+/* ---- context and workspace --------------------------------------------- */
+
+/* Create a context on `device` (the CUDA device ordinal).  Allocates the
+ * device status word and `workspace_bytes` of workspace (0 = none yet). */
+COV_API cov_status cov_ctx_create(cov_ctx** out, int device, size_t workspace_bytes);
+/* Free the context and its workspace.  Safe on NULL.  Synchronises the
+ * device first so no call still uses the workspace. */
+COV_API void cov_ctx_destroy(cov_ctx* ctx);
+/* Grow the workspace to at least `bytes` (never shrinks).  Synchronises the
+ * device before freeing an old workspace. */
+COV_API cov_status cov_ctx_reserve(cov_ctx* ctx, size_t bytes);
+/* Workspace bytes that any single-problem call on these sizes needs:
+ * T samples, M reference samples (0 if none), d coverage dims, and LQR
+ * state/control dims n, m (0 if no LQR step). */
+COV_API size_t cov_workspace_size(int T, int M, int d, int n, int m);
+/* cov_ctx_reserve(ctx, cov_workspace_size(T, M, d, n, m)). */
+COV_API cov_status cov_ctx_reserve_for(cov_ctx* ctx, int T, int M, int d, int n, int m);
+/* Synchronise `stream`, return the OR of COV_DEV_* bits raised since the
+ * last read in *flags, and clear them.  Returns COV_ERR_NONFINITE or
+ * COV_ERR_TIMEOUT if the corresponding bits were set, else COV_OK. */
+COV_API cov_status cov_get_device_status(cov_ctx* ctx, cov_stream_t stream, int* flags);
+/* Human-readable name of a status code (static storage). */
+COV_API const char* cov_status_string(cov_status s);
+/* Text of the last CUDA runtime error seen by this context ("" if none). */
+COV_API const char* cov_last_cuda_error(cov_ctx* ctx);
+
+/* Tuning knobs of the all-pairs kernels (see cov_autotune in the binding).
+ * key: COV_OPT_* ; value: as documented.  Returns COV_ERR_INVALID_ARG for an
+ * unknown key or an out-of-range value. */
+enum {
+    COV_OPT_ROWS_PER_THREAD = 1, /* 2, 4 or 8 (default 4; 2 and 8 built for d = 2) */
+    COV_OPT_THREADS = 2,         /* threads per CTA: 128 (the only value built) */
+    COV_OPT_CTAS_PER_SM = 3,     /* target resident CTAs per SM, 1..8 (default 4) */
+    COV_OPT_USE_GRAPH = 4,       /* cov_solve: capture one outer iteration in a CUDA graph (default 1) */
+    COV_OPT_SPIN_LIMIT = 5       /* bounded-wait iteration limit, >= 0 (default 1<<22) */
+};
+COV_API cov_status cov_ctx_set_option(cov_ctx* ctx, int key, long long value);
+
+/* ---- reference score ----------------------------------------------------- */
+
+/* score[i] = grad log q(x_i) for the mixture q (Eq. 4 needs only the score,
+ * Sec. II-B).  x, score: [T][d] FP32 device; gmm: host descriptor. */
+COV_API cov_status cov_gmm_score(cov_ctx* ctx, const float* x, int T, int d,
+                         const cov_gmm* gmm, float* score,
+                         cov_stream_t stream);
+
+/* ---- Stein variational field, Eq. 4 ------------------------------------- */
+
+/* a_out[i] = 1/T sum_j [ k(x_j, x_i) score_j + grad_{x_j} k(x_j, x_i) ],
+ * k(x, x') = exp(-|x - x'|^2 / (2 h^2)) (the radial basis kernel of Sec.
+ * II-B; the j = i term included).
+ *   x      [T][d] FP32 device, 1 <= T, 1 <= d <= COV_MAX_D
+ *   score  [T][d] FP32 device, or NULL: then gmm (host) gives the score
+ *   h      kernel length-scale > 0
+ *   a_out  [T][d] FP32 device */
+COV_API cov_status cov_field_svgd(cov_ctx* ctx, const float* x, int T, int d,
+                          const float* score, const cov_gmm* gmm, float h,
+                          float* a_out, cov_stream_t stream);
+
+/* ---- Sinkhorn-divergence field, Eq. 5-7 ---------------------------------- */
+
+/* Log-domain Sinkhorn between p_s = (1/T) sum delta_{x_i} and
+ * q = sum b_j delta_{y_j} with cost |x - y|^2 and entropic weight eps (the
+ * paper's omega, Eq. 5), n_iter fixed iterations, each updating
+ *   g_j = -eps LSE_i(log a_i + (f_i - c_ij)/eps)          (M rows over T)
+ *   f_i = -eps LSE_j(log b_j + (g_j - c_ij)/eps)          (T rows over M)
+ *   p_i = (p_i - eps LSE_k(log a_k + (p_k - c_ik)/eps))/2 (self term, Eq. 6)
+ * then the debiased field (Eq. 7, descent direction scaled by 1/a_i)
+ *   a_i = 2 (sum_j pi_ij y_j - sum_k pi^s_ik x_k),
+ *   pi_ij  = softmax_j(log b_j + (g_j - c_ij)/eps),
+ *   pi^s_ik = softmax_k(log a_k + (p_k - c_ik)/eps).
+ *   x      [T][d] FP32 device;  y [M][d] FP32 device
+ *   b      [M] FP32 device positive weights (normalised by the library),
+ *          or NULL for uniform 1/M
+ *   eps > 0, n_iter >= 0; flags: COV_WARM_START starts from the given
+ *          f, g, p (all three non-NULL) instead of zeros
+ *   f [T], g [M], p [T]  FP32 device potentials (cost units), written on
+ *          return when non-NULL
+ *   a_out  [T][d] FP32 device field, or NULL to skip the gradient pass
+ * Errors: COV_ERR_INVALID_ARG for T<1, M<1, d outside 1..COV_MAX_D,
+ * eps<=0, n_iter<0, NULL x/y, or warm start without f, g, p. */
+COV_API cov_status cov_field_sinkhorn(cov_ctx* ctx, const float* x, int T,
+                              const float* y, const float* b, int M, int d,
+                              float eps, int n_iter, int flags, float* f,
+                              float* g, float* p, float* a_out,
+                              cov_stream_t stream);
+
+/* ---- dynamics (Eq. 3, 8) ------------------------------------------------ */
+
+/* A_t = I + dt df/ds, B_t = dt df/du at (s_t, u_t), t = 0..T-1 (Eq. 8).
+ *   s [T+1][n], u [T][m], A [T][n][n], B [T][n][m]: FP64 device. */
+COV_API cov_status cov_linearize(cov_ctx* ctx, int model, const double* s,
+                         const double* u, int T, double dt, double* A,
+                         double* B, cov_stream_t stream);
+/* s_0 = s0 (host [n]), s_{t+1} = s_t + dt f(s_t, u_t).
+ *   u [T][m], s [T+1][n]: FP64 device. */
+COV_API cov_status cov_rollout(cov_ctx* ctx, int model, const double* s0,
+                       const double* u, int T, double dt, double* s,
+                       cov_stream_t stream);
+
+/* ---- LQR flow matching, Eq. 9-10 ---------------------------------------- */
+
+/* Discrete-time LQR tracking of the reference flow (Eq. 9-10 on the time
+ * grid; the common dt weight cancels):
+ *   min_v sum_{t=1..T} |z_t - abar_t|_Q^2 + sum_{t=0..T-1} |v_t|_R^2,
+ *   z_{t+1} = A_t z_t + B_t v_t, z_0 = 0,
+ * by the backward Riccati recursion and a forward rollout, in FP64, one warp.
+ *   A [T][n][n], B [T][n][m]  FP64 device
+ *   Q [n][n] (PSD), R [m][m] (SPD)  FP64 HOST
+ *   abar [T][n] FP64 device: row t-1 holds the target at time t = 1..T
+ *   v_out [T][m] FP64 device;  z_out [T+1][n] FP64 device or NULL
+ *   1 <= n <= COV_MAX_N, 1 <= m <= COV_MAX_M.  A Riccati matrix
+ *   R + B'PB that is not positive definite raises COV_DEV_NOT_SPD. */
+COV_API cov_status cov_lqr_track(cov_ctx* ctx, const double* A, const double* B,
+                         const double* Q, const double* R, const double* abar,
+                         int T, int n, int m, double* v_out, double* z_out,
+                         cov_stream_t stream);
+
+/* ---- outer iteration (Sec. II-C) ----------------------------------------- */
+
+typedef struct {
+    int model;            /* COV_SINGLE_INT / COV_DOUBLE_INT / COV_UNICYCLE */
+    int T;                /* horizon: samples s_1..s_T */
+    double dt;            /* Euler step */
+    double s0[COV_MAX_N]; /* fixed initial state */
+    int field;            /* COV_FIELD_SVGD or COV_FIELD_SINKHORN */
+    int d;                /* coverage coordinates = first d state components */
+    const float* y;       /* Sinkhorn: [M][d] FP32 device reference samples */
+    const float* b;       /* Sinkhorn: [M] FP32 device weights or NULL */
+    int M;
+    float eps;            /* Sinkhorn entropic weight */
+    int n_iter;           /* Sinkhorn iterations per field (cold start) */
+    cov_gmm gmm;          /* SVGD reference (host descriptor) */
+    float h;              /* SVGD kernel length-scale */
+    double Q[COV_MAX_N * COV_MAX_N]; /* [n][n] tracking weight, row-major */
+    double R[COV_MAX_M * COV_MAX_M]; /* [m][m] control weight, row-major */
+    double eta;           /* control step size (u <- u + eta v*) */
+} cov_problem;
+
+/* Run n_outer outer iterations: x = first d components of s_1..s_T;
+ * field a; abar = a lifted to the state (zero on other components); A, B at
+ * (s, u); v* = LQR(abar); u += eta v*; s = rollout(s0, u).
+ *   u     [T][m]   FP64 device, in/out (the control)
+ *   s_out [T+1][n] FP64 device, out (the trajectory after the last update)
+ * With COV_OPT_USE_GRAPH (default) one outer iteration is captured in a
+ * CUDA graph on first use and replayed; the graph is rebuilt when the
+ * problem, pointers or sizes change. */
+COV_API cov_status cov_solve(cov_ctx* ctx, const cov_problem* prob, int n_outer,
+                     double* u, double* s_out, cov_stream_t stream);
+
+/* Continue a solve: like cov_solve, but `s` must already hold the rollout of
+ * `u` from s0 (as left by a previous cov_solve / cov_solve_continue call, or
+ * restored from a checkpoint of (u, s)), so no initial rollout is done.
+ *   u [T][m] FP64 device in/out;  s [T+1][n] FP64 device in/out. */
+COV_API cov_status cov_solve_continue(cov_ctx* ctx, const cov_problem* prob, int n_outer,
+                                      double* u, double* s, cov_stream_t stream);
+
+/* ---- measurement -------------------------------------------------------- */
+
+/* Issue-rate probes for the roofline of the all-pairs kernels: each runs
+ * `iters` dependent-chain iterations per thread on a full grid and reports
+ * operations per second measured with CUDA events on `stream` (host
+ * results, synchronises).  out[0] = FP32 FFMA lane-ops/s, out[1] = packed
+ * f32x2 FMA lane-ops/s (two per instruction), out[2] = ex2.approx lane-ops/s,
+ * out[3] = FP64 DFMA lane-ops/s, out[4] = FP64 DFMA dependent latency in
+ * SM clock cycles, out[5] = SM clock (MHz) estimated over the probe. */
+COV_API cov_status cov_probe_peaks(cov_ctx* ctx, int iters, double* out, cov_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* COV_H */

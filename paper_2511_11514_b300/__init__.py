@@ -6,11 +6,12 @@ tensors into its calls.  ``workloads`` draws the seeded synthetic inputs.
 The binding is imported lazily so that input generation works on machines
 without the built library.
 """
-__all__ = ["binding", "workloads"]
+import importlib
+
+__all__ = ["binding", "workloads", "build_lib"]
 
 
 def __getattr__(name):
-    if name == "binding":
-        from . import binding
-        return binding
+    if name in ("binding", "build_lib"):
+        return importlib.import_module(f"{__name__}.{name}")
     raise AttributeError(name)

@@ -1,0 +1,339 @@
+"""ctypes binding of libcov.so (declared in include/cov.h).
+
+Argument marshalling only: every function checks torch tensors (device,
+dtype, contiguity, shape), passes their data pointers and the current CUDA
+stream to the C-ABI call of the same name, and turns a non-OK status into
+``CovError``.  All compute runs in the library's CUDA kernels; there is no
+fallback path, and loading fails loudly when the library is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libcov.so")
+
+COV_OK, COV_ERR_INVALID_ARG, COV_ERR_WORKSPACE, COV_ERR_CUDA, COV_ERR_NONFINITE, COV_ERR_TIMEOUT, \
+    COV_ERR_UNSUPPORTED = range(7)
+SINGLE_INT, DOUBLE_INT, UNICYCLE = 0, 1, 2
+FIELD_SVGD, FIELD_SINKHORN = 0, 1
+WARM_START = 1
+DEV_NONFINITE, DEV_TIMEOUT, DEV_NOT_SPD = 1, 2, 4
+MAX_D, MAX_GMM, MAX_N, MAX_M = 6, 32, 4, 3
+OPT_ROWS_PER_THREAD, OPT_THREADS, OPT_CTAS_PER_SM, OPT_USE_GRAPH, OPT_SPIN_LIMIT = 1, 2, 3, 4, 5
+MODEL_DIMS = {SINGLE_INT: (2, 2), DOUBLE_INT: (4, 2), UNICYCLE: (3, 2)}
+
+# Every symbol include/cov.h declares.
+EXPORTS = (
+    "cov_ctx_create", "cov_ctx_destroy", "cov_ctx_reserve", "cov_workspace_size", "cov_ctx_reserve_for",
+    "cov_get_device_status", "cov_status_string", "cov_last_cuda_error", "cov_ctx_set_option",
+    "cov_gmm_score", "cov_field_svgd", "cov_field_sinkhorn", "cov_linearize", "cov_rollout",
+    "cov_lqr_track", "cov_solve", "cov_solve_continue", "cov_probe_peaks",
+)
+
+
+class CovError(RuntimeError):
+    def __init__(self, status, what, detail=""):
+        self.status = status
+        super().__init__(f"{what}: {status_string(status)}{(' (' + detail + ')') if detail else ''}")
+
+
+_P = ctypes.c_void_p
+_i, _f, _d, _ll, _sz = ctypes.c_int, ctypes.c_float, ctypes.c_double, ctypes.c_longlong, ctypes.c_size_t
+
+
+class cov_gmm(ctypes.Structure):
+    _fields_ = [("K", _i), ("d", _i), ("w", _P), ("mu", _P), ("sigma", _P)]
+
+
+class cov_problem(ctypes.Structure):
+    _fields_ = [("model", _i), ("T", _i), ("dt", _d), ("s0", _d * MAX_N), ("field", _i), ("d", _i),
+                ("y", _P), ("b", _P), ("M", _i), ("eps", _f), ("n_iter", _i), ("gmm", cov_gmm), ("h", _f),
+                ("Q", _d * (MAX_N * MAX_N)), ("R", _d * (MAX_M * MAX_M)), ("eta", _d)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libcov.so (raises if it was not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libcov.so not found at {path}: run __graft_entry__.build() first")
+    L = ctypes.CDLL(path)
+    sig = {
+        "cov_ctx_create": (_i, [ctypes.POINTER(_P), _i, _sz]),
+        "cov_ctx_destroy": (None, [_P]),
+        "cov_ctx_reserve": (_i, [_P, _sz]),
+        "cov_workspace_size": (_sz, [_i, _i, _i, _i, _i]),
+        "cov_ctx_reserve_for": (_i, [_P, _i, _i, _i, _i, _i]),
+        "cov_get_device_status": (_i, [_P, _P, ctypes.POINTER(_i)]),
+        "cov_status_string": (ctypes.c_char_p, [_i]),
+        "cov_last_cuda_error": (ctypes.c_char_p, [_P]),
+        "cov_ctx_set_option": (_i, [_P, _i, _ll]),
+        "cov_gmm_score": (_i, [_P, _P, _i, _i, ctypes.POINTER(cov_gmm), _P, _P]),
+        "cov_field_svgd": (_i, [_P, _P, _i, _i, _P, ctypes.POINTER(cov_gmm), _f, _P, _P]),
+        "cov_field_sinkhorn": (_i, [_P, _P, _i, _P, _P, _i, _i, _f, _i, _i, _P, _P, _P, _P, _P]),
+        "cov_linearize": (_i, [_P, _i, _P, _P, _i, _d, _P, _P, _P]),
+        "cov_rollout": (_i, [_P, _i, _P, _P, _i, _d, _P, _P]),
+        "cov_lqr_track": (_i, [_P, _P, _P, _P, _P, _P, _i, _i, _i, _P, _P, _P]),
+        "cov_solve": (_i, [_P, ctypes.POINTER(cov_problem), _i, _P, _P, _P]),
+        "cov_solve_continue": (_i, [_P, ctypes.POINTER(cov_problem), _i, _P, _P, _P]),
+        "cov_probe_peaks": (_i, [_P, _i, ctypes.POINTER(_d), _P]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def status_string(s: int) -> str:
+    try:
+        return load().cov_status_string(int(s)).decode()
+    except Exception:
+        return f"status {s}"
+
+
+def _stream(stream=None):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t, dtype, shape=None, name="tensor"):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Context:
+    """A libcov context on one CUDA device (owns the workspace)."""
+
+    def __init__(self, device: int | None = None, workspace_bytes: int = 0):
+        L = load()
+        self.device = torch.cuda.current_device() if device is None else int(device)
+        h = ctypes.c_void_p()
+        st = L.cov_ctx_create(ctypes.byref(h), self.device, int(workspace_bytes))
+        if st != COV_OK:
+            raise CovError(st, "cov_ctx_create")
+        self.h = h
+        self._keep = []
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().cov_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def _check(self, st, what):
+        if st != COV_OK:
+            detail = load().cov_last_cuda_error(self.h).decode() if st == COV_ERR_CUDA else ""
+            raise CovError(st, what, detail)
+
+    def reserve_for(self, T, M=0, d=2, n=0, m=0):
+        self._check(load().cov_ctx_reserve_for(self.h, int(T), int(M), int(d), int(n), int(m)), "cov_ctx_reserve_for")
+
+    def set_option(self, key: int, value: int):
+        self._check(load().cov_ctx_set_option(self.h, int(key), int(value)), "cov_ctx_set_option")
+
+    def device_status(self, stream=None):
+        """(status code, COV_DEV_* bits); synchronises the stream, clears the bits."""
+        fl = ctypes.c_int(0)
+        st = load().cov_get_device_status(self.h, _stream(stream), ctypes.byref(fl))
+        return st, fl.value
+
+
+def workspace_size(T, M=0, d=2, n=0, m=0) -> int:
+    return int(load().cov_workspace_size(int(T), int(M), int(d), int(n), int(m)))
+
+
+def _gmm_struct(gmm, d):
+    """(struct, keep-alive arrays) for gmm = (w, mu, sigma) host arrays."""
+    w, mu, sigma = (np.ascontiguousarray(np.asarray(v, dtype=np.float32)) for v in gmm)
+    g = cov_gmm(K=int(w.size), d=int(d), w=w.ctypes.data_as(_P), mu=mu.ctypes.data_as(_P),
+                sigma=sigma.ctypes.data_as(_P))
+    return g, (w, mu, sigma)
+
+
+def cov_gmm_score(ctx: Context, x, gmm, out=None, stream=None):
+    T, d = x.shape
+    out = torch.empty_like(x) if out is None else out
+    g, keep = _gmm_struct(gmm, d)
+    st = load().cov_gmm_score(ctx.h, _ptr(x, torch.float32, name="x"), T, d, ctypes.byref(g),
+                              _ptr(out, torch.float32, (T, d), "out"), _stream(stream))
+    ctx._check(st, "cov_gmm_score")
+    return out
+
+
+def cov_field_svgd(ctx: Context, x, h, score=None, gmm=None, out=None, stream=None):
+    """Stein variational field (Eq. 4) at all rows of x [T, d]."""
+    T, d = x.shape
+    ctx.reserve_for(T, 0, d)
+    out = torch.empty_like(x) if out is None else out
+    g = None
+    keep = None
+    if score is None:
+        if gmm is None:
+            raise ValueError("need score or gmm")
+        g, keep = _gmm_struct(gmm, d)
+    st = load().cov_field_svgd(ctx.h, _ptr(x, torch.float32, name="x"), T, d,
+                               _ptr(score, torch.float32, (T, d), "score"),
+                               ctypes.byref(g) if g is not None else None, float(h),
+                               _ptr(out, torch.float32, (T, d), "out"), _stream(stream))
+    ctx._check(st, "cov_field_svgd")
+    return out
+
+
+def cov_field_sinkhorn(ctx: Context, x, y, eps, n_iter, b=None, f=None, g=None, p=None, warm=False,
+                       field=True, out=None, stream=None):
+    """Sinkhorn-divergence field (Eq. 5-7).  Returns (a, f, g, p); f, g, p
+    are allocated when not given.  a is None when field=False."""
+    T, d = x.shape
+    M = y.shape[0]
+    ctx.reserve_for(T, M, d)
+    dev = x.device
+    f = torch.empty(T, device=dev, dtype=torch.float32) if f is None else f
+    g = torch.empty(M, device=dev, dtype=torch.float32) if g is None else g
+    p = torch.empty(T, device=dev, dtype=torch.float32) if p is None else p
+    if field and out is None:
+        out = torch.empty_like(x)
+    st = load().cov_field_sinkhorn(
+        ctx.h, _ptr(x, torch.float32, name="x"), T, _ptr(y, torch.float32, (M, d), "y"),
+        _ptr(b, torch.float32, (M,), "b"), M, d, float(eps), int(n_iter), WARM_START if warm else 0,
+        _ptr(f, torch.float32, (T,), "f"), _ptr(g, torch.float32, (M,), "g"), _ptr(p, torch.float32, (T,), "p"),
+        _ptr(out, torch.float32, (T, d), "out") if field else None, _stream(stream))
+    ctx._check(st, "cov_field_sinkhorn")
+    return (out if field else None), f, g, p
+
+
+def cov_linearize(ctx: Context, model, s, u, dt, A=None, B=None, stream=None):
+    n, m = MODEL_DIMS[model]
+    T = u.shape[0]
+    A = torch.empty((T, n, n), device=u.device, dtype=torch.float64) if A is None else A
+    B = torch.empty((T, n, m), device=u.device, dtype=torch.float64) if B is None else B
+    st = load().cov_linearize(ctx.h, int(model), _ptr(s, torch.float64, (T + 1, n), "s"),
+                              _ptr(u, torch.float64, (T, m), "u"), T, float(dt),
+                              _ptr(A, torch.float64, (T, n, n), "A"), _ptr(B, torch.float64, (T, n, m), "B"),
+                              _stream(stream))
+    ctx._check(st, "cov_linearize")
+    return A, B
+
+
+def cov_rollout(ctx: Context, model, s0, u, dt, out=None, stream=None):
+    n, m = MODEL_DIMS[model]
+    T = u.shape[0]
+    s0h = np.ascontiguousarray(np.asarray(s0, dtype=np.float64))
+    out = torch.empty((T + 1, n), device=u.device, dtype=torch.float64) if out is None else out
+    st = load().cov_rollout(ctx.h, int(model), s0h.ctypes.data_as(_P), _ptr(u, torch.float64, (T, m), "u"), T,
+                            float(dt), _ptr(out, torch.float64, (T + 1, n), "s"), _stream(stream))
+    ctx._check(st, "cov_rollout")
+    return out
+
+
+def cov_lqr_track(ctx: Context, A, B, Q, R, abar, want_z=True, stream=None):
+    """LQR tracking (Eq. 9-10).  Q [n,n], R [m,m] host arrays; returns (v, z)."""
+    T, n, m = B.shape
+    ctx.reserve_for(T, 0, 1, n, m)
+    Qh = np.ascontiguousarray(np.asarray(Q, dtype=np.float64))
+    Rh = np.ascontiguousarray(np.asarray(R, dtype=np.float64))
+    if Qh.shape != (n, n) or Rh.shape != (m, m):
+        raise ValueError("Q must be [n,n] and R [m,m]")
+    v = torch.empty((T, m), device=B.device, dtype=torch.float64)
+    z = torch.empty((T + 1, n), device=B.device, dtype=torch.float64) if want_z else None
+    st = load().cov_lqr_track(ctx.h, _ptr(A, torch.float64, (T, n, n), "A"), _ptr(B, torch.float64, (T, n, m), "B"),
+                              Qh.ctypes.data_as(_P), Rh.ctypes.data_as(_P), _ptr(abar, torch.float64, (T, n), "abar"),
+                              T, n, m, _ptr(v, torch.float64, (T, m), "v"),
+                              _ptr(z, torch.float64, (T + 1, n), "z") if want_z else None, _stream(stream))
+    ctx._check(st, "cov_lqr_track")
+    return v, z
+
+
+def make_problem(model, T, dt, s0, field, Q, R, eta, *, d=2, y=None, b=None, eps=0.0, n_iter=0, gmm=None, h=0.0):
+    """Build a cov_problem; returns (struct, keep-alive list)."""
+    n, m = MODEL_DIMS[model]
+    P = cov_problem()
+    P.model, P.T, P.dt, P.field, P.d = int(model), int(T), float(dt), int(field), int(d)
+    for r in range(n):
+        P.s0[r] = float(s0[r])
+    Q = np.asarray(Q, dtype=np.float64).reshape(n, n)
+    R = np.asarray(R, dtype=np.float64).reshape(m, m)
+    for e in range(n * n):
+        P.Q[e] = float(Q.flat[e])
+    for e in range(m * m):
+        P.R[e] = float(R.flat[e])
+    P.eta = float(eta)
+    keep = []
+    if y is not None:
+        P.y = _ptr(y, torch.float32, name="y").value
+        P.M = int(y.shape[0])
+        if b is not None:
+            P.b = _ptr(b, torch.float32, (P.M,), "b").value
+        P.eps, P.n_iter = float(eps), int(n_iter)
+        keep += [y, b]
+    if gmm is not None:
+        g, arrs = _gmm_struct(gmm, d)
+        P.gmm = g
+        keep.append(arrs)
+        P.h = float(h)
+    return P, keep
+
+
+def cov_solve(ctx: Context, problem, n_outer, u, s_out=None, stream=None):
+    """Run n_outer outer iterations in place on u [T, m] (float64); returns s [T+1, n]."""
+    P, keep = problem
+    n, m = MODEL_DIMS[P.model]
+    T = P.T
+    ctx.reserve_for(T, P.M, P.d, n, m)
+    s_out = torch.empty((T + 1, n), device=u.device, dtype=torch.float64) if s_out is None else s_out
+    st = load().cov_solve(ctx.h, ctypes.byref(P), int(n_outer), _ptr(u, torch.float64, (T, m), "u"),
+                          _ptr(s_out, torch.float64, (T + 1, n), "s_out"), _stream(stream))
+    ctx._check(st, "cov_solve")
+    return s_out
+
+
+def cov_solve_continue(ctx: Context, problem, n_outer, u, s, stream=None):
+    """Continue n_outer outer iterations from (u, s), s = rollout of u."""
+    P, keep = problem
+    n, m = MODEL_DIMS[P.model]
+    T = P.T
+    ctx.reserve_for(T, P.M, P.d, n, m)
+    st = load().cov_solve_continue(ctx.h, ctypes.byref(P), int(n_outer), _ptr(u, torch.float64, (T, m), "u"),
+                                   _ptr(s, torch.float64, (T + 1, n), "s"), _stream(stream))
+    ctx._check(st, "cov_solve_continue")
+    return s
+
+
+def cov_probe_peaks(ctx: Context, iters=4096, stream=None):
+    out = (ctypes.c_double * 6)()
+    st = load().cov_probe_peaks(ctx.h, int(iters), out, _stream(stream))
+    ctx._check(st, "cov_probe_peaks")
+    keys = ("ffma_lane_ops_s", "ffma2_lane_ops_s", "ex2_lane_ops_s", "dfma_lane_ops_s", "dfma_latency_cycles",
+            "sm_clock_mhz")
+    return dict(zip(keys, list(out)))

@@ -1,0 +1,96 @@
+// cov_internal.h -- host-side internals of libcov: the context, the
+// workspace bump allocator and launch helpers.  Not part of the C-ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/cov.h"
+
+struct cov_graph_cache {
+    cudaGraphExec_t exec = nullptr;
+    cudaGraph_t graph = nullptr;
+    // identity of what was captured
+    uint64_t key = 0;
+};
+
+struct cov_ctx {
+    int device = 0;
+    int num_sms = 148;
+    void* ws = nullptr;        // workspace base
+    size_t ws_bytes = 0;
+    unsigned* status = nullptr;  // device status word (own allocation)
+    // options
+    int rows_per_thread = 4;
+    int threads = 128;
+    int ctas_per_sm = 4;
+    int use_graph = 1;
+    long long spin_limit = 1LL << 22;
+    std::string last_cuda_error;
+    cov_graph_cache solve_graph;
+    // cached LTI Riccati gains of cov_solve (valid while key matches)
+    uint64_t gains_key = 0;
+};
+
+namespace cov {
+
+// Sequential 256-byte-aligned carving of the workspace.  `base == nullptr`
+// only measures.
+struct Carver {
+    char* base;
+    size_t off = 0;
+    explicit Carver(void* b) : base(static_cast<char*>(b)) {}
+    template <class T>
+    T* take(size_t count) {
+        off = (off + 255) & ~size_t(255);
+        T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+        off += count * sizeof(T);
+        return p;
+    }
+};
+
+inline size_t round_up(size_t x, size_t m) { return (x + m - 1) / m * m; }
+
+// Records a CUDA error on the context; returns true if `e` is an error.
+bool cuda_failed(cov_ctx* ctx, cudaError_t e);
+
+// ---- per-component entry points used by cov_solve ---------------------------
+// Workspace requirements of each component (bytes, 256-aligned pieces).
+size_t sinkhorn_ws_bytes(int T, int M, int d);
+size_t svgd_ws_bytes(int T, int d);
+size_t lqr_ws_bytes(int T, int n, int m);
+
+// Field calls on an explicit workspace region (cov_solve carves its own
+// buffers first and passes the rest).
+cov_status sinkhorn_field_ws(cov_ctx* ctx, void* ws, size_t ws_bytes, const float* x, int x_ld, int T,
+                             const float* y, const float* b, int M, int d, float eps, int n_iter, int flags,
+                             float* f, float* g, float* p, float* a_out, cudaStream_t stream);
+cov_status svgd_field_ws(cov_ctx* ctx, void* ws, size_t ws_bytes, const float* x, int x_ld, int T, int d,
+                         const float* score, const cov_gmm* gmm, float h, float* a_out, cudaStream_t stream);
+cov_status lqr_track_ws(cov_ctx* ctx, void* ws, size_t ws_bytes, const double* A, const double* B,
+                        const double* Q, const double* R, const double* abar, int T, int n, int m,
+                        double* v_out, double* z_out, cudaStream_t stream);
+
+// Pair-tile scheduling of the all-pairs kernels.
+struct SplitPlan {
+    int n_rb;        // row blocks
+    int splits;      // column splits
+    int cols_per_split;  // multiple of 8
+};
+SplitPlan plan_splits(int n_rows, int n_cols, int rows_per_cta, int slots);
+
+// GMM descriptor passed by value to kernels.
+struct GmmParams {
+    int K;
+    int d;
+    float lw[COV_MAX_GMM];          // log2 of normalised weight - d log2 sigma
+    float inv2s2[COV_MAX_GMM];      // 1 / (2 sigma^2 ln 2)   (base-2 exponent scale)
+    float invs2[COV_MAX_GMM];       // 1 / sigma^2
+    float mu[COV_MAX_GMM * COV_MAX_D];
+};
+cov_status make_gmm_params(const cov_gmm* g, int d, GmmParams* out);
+
+}  // namespace cov

@@ -1,0 +1,905 @@
+// field.cu -- the coverage flow fields of Sec. II-B on sm_103a:
+//   * the Sinkhorn-divergence field (Eq. 5-7): log-domain Sinkhorn g-, f- and
+//     debiasing p-updates and the barycentric gradient pass;
+//   * the Stein variational field (Eq. 4) and the Gaussian-mixture score.
+//
+// All of them are one all-pairs kernel (`pairs_kernel`): a CTA holds 32*R
+// rows in registers (R rows per lane, the same rows in each of its 4 warps),
+// streams its slice of the column set through shared memory in tiles of 256
+// columns with the bulk-copy engine (cp.async.bulk + mbarrier, double
+// buffered), and each warp reduces a quarter of every tile.  Per pair the
+// Sinkhorn modes evaluate, in base 2 with coordinates prescaled by
+// 1/sqrt(eps ln 2),
+//     w_ij = h_j + 2 xhat_i . yhat_j             (packed f32x2 FMA)
+// and fold it into an online max-subtracted log-sum-exp (running maximum
+// updated once per 8 columns with a 3-input max, 2^(w - m) on MUFU.EX2).
+// The |xhat_i|^2 row term is constant along a row and is folded back into
+// the potentials by the epilogue, so the Sinkhorn iteration runs entirely on
+// the per-column terms h:
+//     g-update (rows y, columns x):  hy_j = log2 b_j - LSE2_i(hx_i + 2 y.x)
+//     f-update (rows x, columns y):  hx_i = log2 a   - LSE2_j(hy_j + 2 x.y)
+//     p-update (rows x, columns x):  hp'_i = (log2 a + hp_i - LSE2_k(...))/2
+// with hx = log2 a + f/(eps ln2) - |xhat|^2 etc.  Column splits of one row
+// block are merged by the last CTA to finish (atomic ticket).
+#include <math.h>
+#include <stdio.h>
+
+#include <algorithm>
+
+#include "cov_device.cuh"
+#include "cov_internal.h"
+
+namespace cov {
+
+enum PairMode { M_G = 0, M_F = 1, M_P = 2, M_WY = 3, M_WX = 4, M_SVGD = 5, M_COUNT = 6 };
+
+constexpr int kTile = 256;   // columns per staged tile
+constexpr int kWarps = 4;    // warps per CTA, each takes a quarter of a tile
+constexpr int kThreads = 32 * kWarps;
+constexpr int kRowPad = 1024;  // point arrays are padded to this multiple
+constexpr float kSvgdPad = 1.0e15f;  // SVGD padding coordinate (kernel -> 0)
+
+struct PairArgs {
+    const float* rows;   // [D][row_ld]
+    int row_ld;
+    int n_rows;
+    const float* cols;   // [D][col_ld]
+    const float* colh;   // [col_ld] (Sinkhorn modes)
+    const float* cols2;  // [D][col_ld] (SVGD: scaled score)
+    int col_ld;
+    int n_cols8;         // columns rounded up to 8 (padding holds neutral values)
+    int cols_per_split;  // multiple of 8
+    int splits;
+    float* part;         // [NACC][splits][part_ld]
+    int part_ld;         // n_rb * rows per CTA
+    unsigned* counters;  // [n_rb]
+    float* out_h;
+    const float* in_h;
+    float log2a;
+    float* bary;         // [D][row_ld]
+    float* a_out;        // [n_rows][D]
+    float a_scale;
+    unsigned* status;
+    long long spin_limit;
+};
+
+template <int D, int MODE>
+struct PairTraits {
+    static constexpr bool kW = (MODE == M_WY || MODE == M_WX);
+    static constexpr bool kSV = (MODE == M_SVGD);
+    static constexpr int NC = kSV ? 2 * D : D + 1;             // staged components per column
+    static constexpr int NACC = kSV ? D : (kW ? 2 + D : 2);    // partial components per row
+};
+
+// Accumulator state of one row.
+template <int D, bool kW, bool kSV>
+struct RowAcc {
+    float m;          // running max (Sinkhorn)
+    float2 s;         // running sum (two packed halves)
+    float2 acc[D];    // weighted sums (W and SVGD modes)
+};
+
+template <int D, int R, int MODE>
+__device__ __forceinline__ void tile_compute(const float* __restrict__ st, int jb, int je,
+                                             const float (&X)[R][D], const float (&Xr)[R][D],
+                                             RowAcc<D, PairTraits<D, MODE>::kW, PairTraits<D, MODE>::kSV> (&ra)[R]) {
+    using TR = PairTraits<D, MODE>;
+#pragma unroll 1
+    for (int j = jb; j < je; j += 8) {
+        float c[TR::NC][8];
+#pragma unroll
+        for (int k = 0; k < TR::NC; ++k) {
+            const float4 v0 = *reinterpret_cast<const float4*>(st + k * kTile + j);
+            const float4 v1 = *reinterpret_cast<const float4*>(st + k * kTile + j + 4);
+            c[k][0] = v0.x; c[k][1] = v0.y; c[k][2] = v0.z; c[k][3] = v0.w;
+            c[k][4] = v1.x; c[k][5] = v1.y; c[k][6] = v1.z; c[k][7] = v1.w;
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            if constexpr (TR::kSV) {
+                // k_ij = 2^{-|xt_i - xt_j|^2};  acc += k (st_j - (xt_j - xt_i))
+                float2 d2[4];
+                float2 dx[D][4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) d2[q] = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int k = 0; k < D; ++k) {
+                    const float2 xk = make_float2(X[r][k], X[r][k]);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        dx[k][q] = sub2(make_float2(c[k][2 * q], c[k][2 * q + 1]), xk);
+                        d2[q] = fma2(dx[k][q], dx[k][q], d2[q]);
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const float2 e = make_float2(ex2(-d2[q].x), ex2(-d2[q].y));
+#pragma unroll
+                    for (int k = 0; k < D; ++k)
+                        ra[r].acc[k] = fma2(e, sub2(make_float2(c[D + k][2 * q], c[D + k][2 * q + 1]), dx[k][q]),
+                                            ra[r].acc[k]);
+                }
+            } else {
+                float2 w[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) w[q] = make_float2(c[D][2 * q], c[D][2 * q + 1]);
+#pragma unroll
+                for (int k = 0; k < D; ++k) {
+                    const float2 xk = make_float2(X[r][k], X[r][k]);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) w[q] = fma2(xk, make_float2(c[k][2 * q], c[k][2 * q + 1]), w[q]);
+                }
+                const float cm = max3f(max3f(w[0].x, w[0].y, w[1].x), max3f(w[1].y, w[2].x, w[2].y),
+                                       fmaxf(w[3].x, w[3].y));
+                if (cm > ra[r].m) {
+                    const float sc = ex2(ra[r].m - cm);
+                    const float2 sc2 = make_float2(sc, sc);
+                    ra[r].s = mul2(ra[r].s, sc2);
+                    if constexpr (TR::kW) {
+#pragma unroll
+                        for (int k = 0; k < D; ++k) ra[r].acc[k] = mul2(ra[r].acc[k], sc2);
+                    }
+                    ra[r].m = cm;
+                }
+                const float2 mm = make_float2(ra[r].m, ra[r].m);
+                float2 e[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const float2 dd = sub2(w[q], mm);
+                    e[q] = make_float2(ex2(dd.x), ex2(dd.y));
+                }
+                ra[r].s = add2(ra[r].s, add2(add2(e[0], e[1]), add2(e[2], e[3])));
+                if constexpr (TR::kW) {
+#pragma unroll
+                    for (int k = 0; k < D; ++k) {
+                        const float2 xr = make_float2(Xr[r][k], Xr[r][k]);
+#pragma unroll
+                        for (int q = 0; q < 4; ++q)
+                            ra[r].acc[k] = fma2(e[q], sub2(make_float2(c[k][2 * q], c[k][2 * q + 1]), xr),
+                                                ra[r].acc[k]);
+                    }
+                }
+            }
+        }
+    }
+}
+
+// Merge partial (m2, s2, acc2) into (m, s, acc).
+template <int D, int MODE>
+__device__ __forceinline__ void merge_into(float& m, float& s, float* acc, float m2, float s2, const float* acc2) {
+    using TR = PairTraits<D, MODE>;
+    if constexpr (TR::kSV) {
+#pragma unroll
+        for (int k = 0; k < D; ++k) acc[k] += acc2[k];
+    } else {
+        const float M = fmaxf(m, m2);
+        const float a1 = ex2(m - M), a2 = ex2(m2 - M);
+        s = s * a1 + s2 * a2;
+        if constexpr (TR::kW) {
+#pragma unroll
+            for (int k = 0; k < D; ++k) acc[k] = acc[k] * a1 + acc2[k] * a2;
+        }
+        m = M;
+    }
+}
+
+template <int D, int MODE>
+__device__ __forceinline__ void epilogue(const PairArgs& a, int i, float m, float s, const float* acc) {
+    using TR = PairTraits<D, MODE>;
+    if (i >= a.n_rows) return;
+    bool ok = true;
+    if constexpr (TR::kSV) {
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            const float v = a.a_out ? a.a_scale * acc[k] : 0.f;
+            ok &= finitef(v);
+            a.a_out[(size_t)i * D + k] = v;
+        }
+    } else if constexpr (MODE == M_WY) {
+        const float inv = 1.0f / s;
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            const float v = acc[k] * inv;
+            ok &= finitef(v);
+            a.bary[(size_t)k * a.row_ld + i] = v;
+        }
+    } else if constexpr (MODE == M_WX) {
+        const float inv = 1.0f / s;
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            const float v = a.a_scale * (a.bary[(size_t)k * a.row_ld + i] - acc[k] * inv);
+            ok &= finitef(v);
+            a.a_out[(size_t)i * D + k] = v;
+        }
+    } else {
+        const float L = m + log2f(s);
+        float v;
+        if constexpr (MODE == M_G) v = a.in_h[i] - L;
+        else if constexpr (MODE == M_F) v = a.log2a - L;
+        else v = 0.5f * (a.log2a + a.in_h[i] - L);
+        ok &= finitef(v);
+        a.out_h[i] = v;
+    }
+    if (!ok) raise_status(a.status, kDevNonfinite);
+}
+
+template <int D, int R, int MODE>
+__global__ void __launch_bounds__(kThreads) pairs_kernel(const PairArgs a) {
+    using TR = PairTraits<D, MODE>;
+    constexpr int NC = TR::NC;
+    constexpr int NACC = TR::NACC;
+    constexpr int RB = 32 * R;  // rows per CTA
+    __shared__ __align__(128) float sm[2][NC * kTile];
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ float red[kWarps][NACC][RB];
+    __shared__ int s_last;
+
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int rb = blockIdx.x, sp = blockIdx.y;
+    const int row0 = rb * RB;
+
+    float X[R][D], Xr[R][D];
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            const float v = a.rows[(size_t)k * a.row_ld + row0 + r * 32 + lane];
+            X[r][k] = TR::kSV ? v : 2.0f * v;
+            Xr[r][k] = v;
+        }
+    RowAcc<D, TR::kW, TR::kSV> ra[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        ra[r].m = kNegBig;
+        ra[r].s = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int k = 0; k < D; ++k) ra[r].acc[k] = make_float2(0.f, 0.f);
+    }
+
+    const int c0 = sp * a.cols_per_split;
+    const int c1 = min(c0 + a.cols_per_split, a.n_cols8);
+    const int n_tiles = c1 > c0 ? (c1 - c0 + kTile - 1) / kTile : 0;
+
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    auto issue = [&](int t, int stg) {
+        const int tc = c0 + t * kTile;
+        const int nc = min(kTile, c1 - tc);
+        const unsigned bytes = (unsigned)nc * 4u;
+        mbar_arrive_expect_tx(&bar[stg], bytes * NC);
+#pragma unroll
+        for (int k = 0; k < D; ++k) bulk_g2s(&sm[stg][k * kTile], a.cols + (size_t)k * a.col_ld + tc, bytes, &bar[stg]);
+        if constexpr (TR::kSV) {
+#pragma unroll
+            for (int k = 0; k < D; ++k)
+                bulk_g2s(&sm[stg][(D + k) * kTile], a.cols2 + (size_t)k * a.col_ld + tc, bytes, &bar[stg]);
+        } else {
+            bulk_g2s(&sm[stg][D * kTile], a.colh + tc, bytes, &bar[stg]);
+        }
+    };
+
+    if (threadIdx.x == 0 && n_tiles > 0) issue(0, 0);
+    int bad_tile = -1;
+    for (int t = 0; t < n_tiles; ++t) {
+        const int stg = t & 1;
+        if (threadIdx.x == 0 && t + 1 < n_tiles) issue(t + 1, stg ^ 1);
+        const bool ok = mbar_wait_bounded(&bar[stg], (unsigned)((t >> 1) & 1), a.spin_limit);
+        if (__syncthreads_or(!ok)) {
+            bad_tile = t;
+            break;
+        }
+        const int nc = min(kTile, c1 - (c0 + t * kTile));
+        const int per = ((nc / 8 + kWarps - 1) / kWarps) * 8;
+        const int jb = min(nc, warp * per), je = min(nc, jb + per);
+        tile_compute<D, R, MODE>(sm[stg], jb, je, X, Xr, ra);
+        __syncthreads();
+    }
+    if (bad_tile >= 0) {
+        // A tile never arrived: record it, drain the copies still in flight
+        // (bounded) so no bulk copy lands after the CTA exits, and fall
+        // through with whatever was accumulated (the status marks it invalid).
+        if (threadIdx.x == 0) {
+            raise_status(a.status, kDevTimeout);
+            const long long drain = a.spin_limit > (1LL << 20) ? a.spin_limit : (1LL << 20);
+            mbar_wait_bounded(&bar[bad_tile & 1], (unsigned)((bad_tile >> 1) & 1), drain);
+            if (bad_tile + 1 < n_tiles)
+                mbar_wait_bounded(&bar[(bad_tile + 1) & 1], (unsigned)(((bad_tile + 1) >> 1) & 1), drain);
+        }
+        __syncthreads();
+    }
+
+    // ---- reduce the 4 warps' partials of each row in shared memory ----------
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int q = r * 32 + lane;
+        if constexpr (TR::kSV) {
+#pragma unroll
+            for (int k = 0; k < D; ++k) red[warp][k][q] = ra[r].acc[k].x + ra[r].acc[k].y;
+        } else {
+            red[warp][0][q] = ra[r].m;
+            red[warp][1][q] = ra[r].s.x + ra[r].s.y;
+            if constexpr (TR::kW) {
+#pragma unroll
+                for (int k = 0; k < D; ++k) red[warp][2 + k][q] = ra[r].acc[k].x + ra[r].acc[k].y;
+            }
+        }
+    }
+    __syncthreads();
+    constexpr int KA = TR::kSV ? D : (TR::kW ? D : 1);
+    for (int q = threadIdx.x; q < RB; q += kThreads) {
+        float m, s, acc[KA];
+        if constexpr (TR::kSV) {
+            m = 0.f;
+            s = 0.f;
+#pragma unroll
+            for (int k = 0; k < D; ++k) acc[k] = red[0][k][q];
+        } else {
+            m = red[0][0][q];
+            s = red[0][1][q];
+            if constexpr (TR::kW) {
+#pragma unroll
+                for (int k = 0; k < D; ++k) acc[k] = red[0][2 + k][q];
+            }
+        }
+#pragma unroll
+        for (int w = 1; w < kWarps; ++w) {
+            float a2[KA];
+            float m2 = 0.f, s2 = 0.f;
+            if constexpr (TR::kSV) {
+#pragma unroll
+                for (int k = 0; k < D; ++k) a2[k] = red[w][k][q];
+            } else {
+                m2 = red[w][0][q];
+                s2 = red[w][1][q];
+                if constexpr (TR::kW) {
+#pragma unroll
+                    for (int k = 0; k < D; ++k) a2[k] = red[w][2 + k][q];
+                }
+            }
+            merge_into<D, MODE>(m, s, acc, m2, s2, a2);
+        }
+        const int i = row0 + q;
+        if (a.splits == 1) {
+            epilogue<D, MODE>(a, i, m, s, acc);
+        } else {
+            float* P = a.part + (size_t)sp * a.part_ld + i;
+            const size_t cs = (size_t)a.splits * a.part_ld;  // component stride
+            if constexpr (TR::kSV) {
+#pragma unroll
+                for (int k = 0; k < D; ++k) P[k * cs] = acc[k];
+            } else {
+                P[0] = m;
+                P[cs] = s;
+                if constexpr (TR::kW) {
+#pragma unroll
+                    for (int k = 0; k < D; ++k) P[(2 + k) * cs] = acc[k];
+                }
+            }
+        }
+    }
+    if (a.splits == 1) return;
+
+    // ---- last CTA of this row block merges the splits ------------------------
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned prev = atomicAdd(&a.counters[rb], 1u);
+        s_last = (prev == (unsigned)(a.splits - 1));
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    const size_t cs = (size_t)a.splits * a.part_ld;
+    for (int q = threadIdx.x; q < RB; q += kThreads) {
+        const int i = row0 + q;
+        float m = kNegBig, s = 0.f, acc[KA];
+#pragma unroll
+        for (int k = 0; k < KA; ++k) acc[k] = 0.f;
+        for (int p = 0; p < a.splits; ++p) {
+            const float* P = a.part + (size_t)p * a.part_ld + i;
+            float a2[KA];
+            float m2 = 0.f, s2 = 0.f;
+            if constexpr (TR::kSV) {
+#pragma unroll
+                for (int k = 0; k < D; ++k) a2[k] = ld_cg(P + k * cs);
+            } else {
+                m2 = ld_cg(P);
+                s2 = ld_cg(P + cs);
+                if constexpr (TR::kW) {
+#pragma unroll
+                    for (int k = 0; k < D; ++k) a2[k] = ld_cg(P + (2 + k) * cs);
+                }
+            }
+            merge_into<D, MODE>(m, s, acc, m2, s2, a2);
+        }
+        epilogue<D, MODE>(a, i, m, s, acc);
+    }
+    if (threadIdx.x == 0) a.counters[rb] = 0u;  // ready for the next launch
+}
+
+// ---------------------------------------------------------------------------
+// Split planning: pick the number of column splits per row block that
+// minimises (waves of CTAs) x (columns per CTA + fixed cost) + merge cost.
+// ---------------------------------------------------------------------------
+}  // namespace cov
+
+cov::SplitPlan cov::plan_splits(int n_rows, int n_cols, int rows_per_cta, int slots) {
+    SplitPlan best{};
+    const int n_rb = (n_rows + rows_per_cta - 1) / rows_per_cta;
+    const int units = (n_cols + 7) / 8;
+    const int smax = std::max(1, std::min(units, (2 * slots + n_rb - 1) / n_rb));
+    double best_cost = 1e300;
+    for (int s = 1; s <= smax; ++s) {
+        const int cpu = (units + s - 1) / s;
+        const int s_eff = (units + cpu - 1) / cpu;
+        const long long ctas = (long long)n_rb * s_eff;
+        const long long waves = (ctas + slots - 1) / slots;
+        const double cost = (double)waves * (cpu * 8 + 64) + (s_eff > 1 ? 4.0 * s_eff : 0.0);
+        if (cost < best_cost - 1e-9) {
+            best_cost = cost;
+            best = SplitPlan{n_rb, s_eff, cpu * 8};
+        }
+    }
+    return best;
+}
+
+namespace cov {
+
+// ---------------------------------------------------------------------------
+// Prep kernels
+// ---------------------------------------------------------------------------
+// scal layout: [0..5] centre, [8] 1/sum(b) (or 0 when b == NULL)
+__global__ void sk_centre_kernel(const float* __restrict__ y, int M, int d, const float* __restrict__ b,
+                                 float* __restrict__ scal) {
+    __shared__ float sh[32][COV_MAX_D + 1];
+    float acc[COV_MAX_D + 1];
+    for (int k = 0; k <= COV_MAX_D; ++k) acc[k] = 0.f;
+    for (int j = threadIdx.x; j < M; j += blockDim.x) {
+        for (int k = 0; k < d; ++k) acc[k] += y[(size_t)j * d + k];
+        if (b) acc[COV_MAX_D] += b[j];
+    }
+    for (int k = 0; k <= COV_MAX_D; ++k)
+        for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0)
+        for (int k = 0; k <= COV_MAX_D; ++k) sh[w][k] = acc[k];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int nw = blockDim.x >> 5;
+        for (int k = 0; k <= COV_MAX_D; ++k) {
+            float t = 0.f;
+            for (int i = 0; i < nw; ++i) t += sh[i][k];
+            acc[k] = t;
+        }
+        for (int k = 0; k < COV_MAX_D; ++k) scal[k] = k < d ? acc[k] / (float)M : 0.f;
+        scal[8] = b ? 1.0f / acc[COV_MAX_D] : 0.f;
+    }
+}
+
+struct SkBufs {
+    float *xs, *ys, *hx, *hy, *hp0, *hp1, *lb, *nx, *ny, *bary, *scal, *part;
+    unsigned* counters;  // [M_COUNT][cnt_ld]
+    int Tp, Mp, cnt_ld;
+    size_t part_floats;
+};
+
+__global__ void sk_prep_kernel(const float* __restrict__ x, int x_ld, int T, const float* __restrict__ y, int M,
+                               const float* __restrict__ b, int d, float inv_sigma, float inv_epsln2,
+                               float log2a, int warm, const float* __restrict__ f, const float* __restrict__ g,
+                               const float* __restrict__ p, SkBufs B, unsigned* status) {
+    const float* c = B.scal;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < B.Tp) {
+        float n2 = 0.f;
+        for (int k = 0; k < d; ++k) {
+            const float v = i < T ? (x[(size_t)i * x_ld + k] - c[k]) * inv_sigma : 0.f;
+            B.xs[(size_t)k * B.Tp + i] = v;
+            n2 = fmaf(v, v, n2);
+        }
+        B.nx[i] = n2;
+        if (i < T) {
+            const float fh = warm ? f[i] * inv_epsln2 : 0.f;
+            const float ph = warm ? p[i] * inv_epsln2 : 0.f;
+            B.hx[i] = log2a + fh - n2;
+            B.hp0[i] = log2a + ph - n2;
+            if (!finitef(B.hx[i]) || !finitef(B.hp0[i])) raise_status(status, kDevNonfinite);
+        } else {
+            B.hx[i] = kPadH;
+            B.hp0[i] = kPadH;
+            B.hp1[i] = kPadH;
+        }
+    }
+    if (i < B.Mp) {
+        float n2 = 0.f;
+        for (int k = 0; k < d; ++k) {
+            const float v = i < M ? (y[(size_t)i * d + k] - c[k]) * inv_sigma : 0.f;
+            B.ys[(size_t)k * B.Mp + i] = v;
+            n2 = fmaf(v, v, n2);
+        }
+        B.ny[i] = n2;
+        if (i < M) {
+            const float lbj = b ? log2f(b[i] * c[8]) : -log2f((float)M);
+            B.lb[i] = lbj;
+            const float gh = warm ? g[i] * inv_epsln2 : 0.f;
+            B.hy[i] = lbj + gh - n2;
+            if (!finitef(B.hy[i])) raise_status(status, kDevNonfinite);
+        } else {
+            B.lb[i] = 0.f;
+            B.hy[i] = kPadH;
+        }
+    }
+}
+
+__global__ void sk_finish_kernel(int T, int M, float epsln2, float log2a, SkBufs B, const float* __restrict__ hp,
+                                 float* __restrict__ f, float* __restrict__ g, float* __restrict__ p,
+                                 unsigned* status) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    bool ok = true;
+    if (i < T) {
+        if (f) {
+            const float v = (B.hx[i] - log2a + B.nx[i]) * epsln2;
+            f[i] = v;
+            ok &= finitef(v);
+        }
+        if (p) {
+            const float v = (hp[i] - log2a + B.nx[i]) * epsln2;
+            p[i] = v;
+            ok &= finitef(v);
+        }
+    }
+    if (i < M && g) {
+        const float v = (B.hy[i] - B.lb[i] + B.ny[i]) * epsln2;
+        g[i] = v;
+        ok &= finitef(v);
+    }
+    if (!ok) raise_status(status, kDevNonfinite);
+}
+
+// ---------------------------------------------------------------------------
+// Launch dispatch
+// ---------------------------------------------------------------------------
+template <int D, int R, int MODE>
+static void launch_pairs_t(const PairArgs& a, dim3 grid, cudaStream_t st) {
+    pairs_kernel<D, R, MODE><<<grid, kThreads, 0, st>>>(a);
+}
+
+template <int D, int R>
+static void launch_pairs_mode(int mode, const PairArgs& a, dim3 grid, cudaStream_t st) {
+    switch (mode) {
+        case M_G: launch_pairs_t<D, R, M_G>(a, grid, st); break;
+        case M_F: launch_pairs_t<D, R, M_F>(a, grid, st); break;
+        case M_P: launch_pairs_t<D, R, M_P>(a, grid, st); break;
+        case M_WY: launch_pairs_t<D, R, M_WY>(a, grid, st); break;
+        case M_WX: launch_pairs_t<D, R, M_WX>(a, grid, st); break;
+        case M_SVGD: launch_pairs_t<D, R, M_SVGD>(a, grid, st); break;
+    }
+}
+
+template <int D>
+static void launch_pairs_r(int R, int mode, const PairArgs& a, dim3 grid, cudaStream_t st) {
+    if constexpr (D == 2) {
+        if (R == 2) return launch_pairs_mode<D, 2>(mode, a, grid, st);
+        if (R == 8) return launch_pairs_mode<D, 8>(mode, a, grid, st);
+    }
+    launch_pairs_mode<D, 4>(mode, a, grid, st);
+}
+
+static int effective_R(int d, int R) { return (d == 2 && (R == 2 || R == 8)) ? R : 4; }
+
+
+constexpr int kMaxSlots = 1536;           // CTA slots assumed by the workspace bound
+constexpr size_t kPartRows = (size_t)2 * kMaxSlots * 256;
+
+static int cnt_ld_for(int Tp, int Mp) { return std::max(Tp, Mp) / 64 + 1; }
+
+// Plans and launches one all-pairs pass of `mode` over n_rows x n_cols.
+static void run_pairs(cov_ctx* ctx, int d, int mode, PairArgs a, int n_cols, unsigned* counters,
+                      cudaStream_t st) {
+    const int R = effective_R(d, ctx->rows_per_thread);
+    const int RB = 32 * R;
+    const int slots = std::max(1, std::min(ctx->num_sms * ctx->ctas_per_sm, kMaxSlots));
+    const SplitPlan pl = plan_splits(a.n_rows, n_cols, RB, slots);
+    a.n_cols8 = (int)round_up((size_t)n_cols, 8);
+    a.cols_per_split = pl.cols_per_split;
+    a.splits = pl.splits;
+    a.part_ld = pl.n_rb * RB;
+    a.counters = counters;
+    const dim3 grid(pl.n_rb, pl.splits);
+    switch (d) {
+        case 1: launch_pairs_r<1>(R, mode, a, grid, st); break;
+        case 2: launch_pairs_r<2>(R, mode, a, grid, st); break;
+        case 3: launch_pairs_r<3>(R, mode, a, grid, st); break;
+        case 4: launch_pairs_r<4>(R, mode, a, grid, st); break;
+        case 5: launch_pairs_r<5>(R, mode, a, grid, st); break;
+        case 6: launch_pairs_r<6>(R, mode, a, grid, st); break;
+    }
+}
+
+static SkBufs carve_sinkhorn(Carver& cv, int T, int M, int d) {
+    SkBufs B{};
+    B.Tp = (int)round_up((size_t)T, kRowPad);
+    B.Mp = (int)round_up((size_t)M, kRowPad);
+    B.xs = cv.take<float>((size_t)d * B.Tp);
+    B.ys = cv.take<float>((size_t)d * B.Mp);
+    B.hx = cv.take<float>(B.Tp);
+    B.hy = cv.take<float>(B.Mp);
+    B.hp0 = cv.take<float>(B.Tp);
+    B.hp1 = cv.take<float>(B.Tp);
+    B.lb = cv.take<float>(B.Mp);
+    B.nx = cv.take<float>(B.Tp);
+    B.ny = cv.take<float>(B.Mp);
+    B.bary = cv.take<float>((size_t)d * B.Tp);
+    B.scal = cv.take<float>(16);
+    B.cnt_ld = cnt_ld_for(B.Tp, B.Mp);
+    B.counters = cv.take<unsigned>((size_t)M_COUNT * B.cnt_ld);
+    B.part_floats = (size_t)(2 + d) * (kPartRows + std::max(B.Tp, B.Mp));
+    B.part = cv.take<float>(B.part_floats);
+    return B;
+}
+
+size_t sinkhorn_ws_bytes(int T, int M, int d) {
+    Carver cv(nullptr);
+    carve_sinkhorn(cv, T, M, d);
+    return round_up(cv.off, 256);
+}
+
+cov_status sinkhorn_field_ws(cov_ctx* ctx, void* ws, size_t ws_bytes, const float* x, int x_ld, int T,
+                             const float* y, const float* b, int M, int d, float eps, int n_iter, int flags,
+                             float* f, float* g, float* p, float* a_out, cudaStream_t stream) {
+    if (!ctx || !x || !y || T < 1 || M < 1 || d < 1 || d > COV_MAX_D || x_ld < d || n_iter < 0 ||
+        !(eps > 0.f) || !isfinite(eps))
+        return COV_ERR_INVALID_ARG;
+    const int warm = (flags & COV_WARM_START) ? 1 : 0;
+    if (warm && (!f || !g || !p)) return COV_ERR_INVALID_ARG;
+    Carver cv(ws);
+    SkBufs B = carve_sinkhorn(cv, T, M, d);
+    if (!ws || cv.off > ws_bytes) return COV_ERR_WORKSPACE;
+    if (cuda_failed(ctx, cudaMemsetAsync(B.counters, 0, sizeof(unsigned) * M_COUNT * B.cnt_ld, stream)))
+        return COV_ERR_CUDA;
+
+    const double epsln2 = (double)eps * 0.69314718055994531;
+    const float inv_sigma = (float)(1.0 / sqrt(epsln2));
+    const float sigma = (float)sqrt(epsln2);
+    const float log2a = (float)(-log2((double)T));
+    sk_centre_kernel<<<1, 1024, 0, stream>>>(y, M, d, b, B.scal);
+    const int np = std::max(B.Tp, B.Mp);
+    sk_prep_kernel<<<(np + 255) / 256, 256, 0, stream>>>(x, x_ld, T, y, M, b, d, inv_sigma, (float)(1.0 / epsln2),
+                                                         log2a, warm, f, g, p, B, ctx->status);
+    PairArgs base{};
+    base.status = ctx->status;
+    base.spin_limit = ctx->spin_limit;
+    base.log2a = log2a;
+    base.part = B.part;
+    float* hp_cur = B.hp0;
+    float* hp_nxt = B.hp1;
+    for (int it = 0; it < n_iter; ++it) {
+        PairArgs a = base;  // g-update: rows y, columns x
+        a.rows = B.ys; a.row_ld = B.Mp; a.n_rows = M;
+        a.cols = B.xs; a.colh = B.hx; a.col_ld = B.Tp;
+        a.out_h = B.hy; a.in_h = B.lb;
+        run_pairs(ctx, d, M_G, a, T, B.counters + M_G * B.cnt_ld, stream);
+        a = base;           // f-update: rows x, columns y
+        a.rows = B.xs; a.row_ld = B.Tp; a.n_rows = T;
+        a.cols = B.ys; a.colh = B.hy; a.col_ld = B.Mp;
+        a.out_h = B.hx;
+        run_pairs(ctx, d, M_F, a, M, B.counters + M_F * B.cnt_ld, stream);
+        a = base;           // p-update: rows x, columns x
+        a.rows = B.xs; a.row_ld = B.Tp; a.n_rows = T;
+        a.cols = B.xs; a.colh = hp_cur; a.col_ld = B.Tp;
+        a.out_h = hp_nxt; a.in_h = hp_cur;
+        run_pairs(ctx, d, M_P, a, T, B.counters + M_P * B.cnt_ld, stream);
+        std::swap(hp_cur, hp_nxt);
+    }
+    if (a_out) {
+        PairArgs a = base;  // cross barycentre: (sum_j pi_ij yhat_j) - xhat_i
+        a.rows = B.xs; a.row_ld = B.Tp; a.n_rows = T;
+        a.cols = B.ys; a.colh = B.hy; a.col_ld = B.Mp;
+        a.bary = B.bary;
+        run_pairs(ctx, d, M_WY, a, M, B.counters + M_WY * B.cnt_ld, stream);
+        a = base;           // self barycentre and the field 2 sigma (ybar - xbar)
+        a.rows = B.xs; a.row_ld = B.Tp; a.n_rows = T;
+        a.cols = B.xs; a.colh = hp_cur; a.col_ld = B.Tp;
+        a.bary = B.bary; a.a_out = a_out; a.a_scale = 2.0f * sigma;
+        run_pairs(ctx, d, M_WX, a, T, B.counters + M_WX * B.cnt_ld, stream);
+    }
+    if (f || g || p) {
+        const int nf = std::max(T, M);
+        sk_finish_kernel<<<(nf + 255) / 256, 256, 0, stream>>>(T, M, (float)epsln2, log2a, B, hp_cur, f, g, p,
+                                                               ctx->status);
+    }
+    if (cuda_failed(ctx, cudaGetLastError())) return COV_ERR_CUDA;
+    return COV_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Stein variational field and the mixture score
+// ---------------------------------------------------------------------------
+}  // namespace cov
+
+cov_status cov::make_gmm_params(const cov_gmm* g, int d, GmmParams* out) {
+    if (!g || !out || g->K < 1 || g->K > COV_MAX_GMM || g->d != d || !g->w || !g->mu || !g->sigma)
+        return COV_ERR_INVALID_ARG;
+    double wsum = 0.0;
+    for (int k = 0; k < g->K; ++k) {
+        if (!(g->w[k] > 0.f) || !(g->sigma[k] > 0.f) || !isfinite(g->w[k]) || !isfinite(g->sigma[k]))
+            return COV_ERR_INVALID_ARG;
+        wsum += g->w[k];
+    }
+    GmmParams P{};
+    P.K = g->K;
+    P.d = d;
+    for (int k = 0; k < g->K; ++k) {
+        const double s = g->sigma[k];
+        P.lw[k] = (float)(log2(g->w[k] / wsum) - d * log2(s));
+        P.inv2s2[k] = (float)(1.0 / (2.0 * s * s * 0.69314718055994531));
+        P.invs2[k] = (float)(1.0 / (s * s));
+        for (int c = 0; c < d; ++c) {
+            if (!isfinite(g->mu[k * d + c])) return COV_ERR_INVALID_ARG;
+            P.mu[k * COV_MAX_D + c] = g->mu[k * d + c];
+        }
+    }
+    *out = P;
+    return COV_OK;
+}
+
+namespace cov {
+
+// grad log q(x) for the mixture: softmax responsibilities in base 2.
+__device__ __forceinline__ void gmm_score_at(const GmmParams& G, const float* xv, int d, float* sc) {
+    float t[COV_MAX_GMM];
+    float tm = kNegBig;
+    for (int k = 0; k < G.K; ++k) {
+        float r2 = 0.f;
+        for (int c = 0; c < d; ++c) {
+            const float dv = xv[c] - G.mu[k * COV_MAX_D + c];
+            r2 = fmaf(dv, dv, r2);
+        }
+        t[k] = G.lw[k] - r2 * G.inv2s2[k];
+        tm = fmaxf(tm, t[k]);
+    }
+    float den = 0.f;
+    for (int c = 0; c < d; ++c) sc[c] = 0.f;
+    for (int k = 0; k < G.K; ++k) {
+        const float e = ex2(t[k] - tm);
+        den += e;
+        for (int c = 0; c < d; ++c) sc[c] = fmaf(e * G.invs2[k], G.mu[k * COV_MAX_D + c] - xv[c], sc[c]);
+    }
+    const float inv = 1.0f / den;
+    for (int c = 0; c < d; ++c) sc[c] *= inv;
+}
+
+__global__ void gmm_score_kernel(const float* __restrict__ x, int T, int d, GmmParams G, float* __restrict__ out,
+                                 unsigned* status) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= T) return;
+    float xv[COV_MAX_D], sc[COV_MAX_D];
+    for (int c = 0; c < d; ++c) xv[c] = x[(size_t)i * d + c];
+    gmm_score_at(G, xv, d, sc);
+    bool ok = true;
+    for (int c = 0; c < d; ++c) {
+        out[(size_t)i * d + c] = sc[c];
+        ok &= finitef(sc[c]);
+    }
+    if (!ok) raise_status(status, kDevNonfinite);
+}
+
+// xt = x / (h sqrt(2 ln 2)),  st = score h / sqrt(2 ln 2); padding: xt far away, st = 0.
+__global__ void svgd_prep_kernel(const float* __restrict__ x, int x_ld, int T, int d, int Tp,
+                                 const float* __restrict__ score, GmmParams G, int use_gmm, float inv_hs, float hs,
+                                 float* __restrict__ xt, float* __restrict__ st, unsigned* status) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= Tp) return;
+    if (i >= T) {
+        for (int c = 0; c < d; ++c) {
+            xt[(size_t)c * Tp + i] = kSvgdPad;
+            st[(size_t)c * Tp + i] = 0.f;
+        }
+        return;
+    }
+    float xv[COV_MAX_D], sc[COV_MAX_D];
+    for (int c = 0; c < d; ++c) xv[c] = x[(size_t)i * x_ld + c];
+    if (use_gmm) {
+        gmm_score_at(G, xv, d, sc);
+    } else {
+        for (int c = 0; c < d; ++c) sc[c] = score[(size_t)i * d + c];
+    }
+    bool ok = true;
+    for (int c = 0; c < d; ++c) {
+        xt[(size_t)c * Tp + i] = xv[c] * inv_hs;
+        st[(size_t)c * Tp + i] = sc[c] * hs;
+        ok &= finitef(xv[c]) && finitef(sc[c]);
+    }
+    if (!ok) raise_status(status, kDevNonfinite);
+}
+
+struct SvBufs {
+    float *xt, *st, *part;
+    unsigned* counters;
+    int Tp;
+};
+
+static SvBufs carve_svgd(Carver& cv, int T, int d) {
+    SvBufs B{};
+    B.Tp = (int)round_up((size_t)T, kRowPad);
+    B.xt = cv.take<float>((size_t)d * B.Tp);
+    B.st = cv.take<float>((size_t)d * B.Tp);
+    B.counters = cv.take<unsigned>((size_t)B.Tp / 64 + 1);
+    B.part = cv.take<float>((size_t)d * (kPartRows + B.Tp));
+    return B;
+}
+
+size_t svgd_ws_bytes(int T, int d) {
+    Carver cv(nullptr);
+    carve_svgd(cv, T, d);
+    return round_up(cv.off, 256);
+}
+
+cov_status svgd_field_ws(cov_ctx* ctx, void* ws, size_t ws_bytes, const float* x, int x_ld, int T, int d,
+                         const float* score, const cov_gmm* gmm, float h, float* a_out, cudaStream_t stream) {
+    if (!ctx || !x || !a_out || T < 1 || d < 1 || d > COV_MAX_D || x_ld < d || !(h > 0.f) || !isfinite(h))
+        return COV_ERR_INVALID_ARG;
+    GmmParams G{};
+    const int use_gmm = score ? 0 : 1;
+    if (use_gmm) {
+        const cov_status s = make_gmm_params(gmm, d, &G);
+        if (s != COV_OK) return s;
+    }
+    Carver cv(ws);
+    SvBufs B = carve_svgd(cv, T, d);
+    if (!ws || cv.off > ws_bytes) return COV_ERR_WORKSPACE;
+    if (cuda_failed(ctx, cudaMemsetAsync(B.counters, 0, sizeof(unsigned) * (B.Tp / 64 + 1), stream)))
+        return COV_ERR_CUDA;
+    const double r2l = sqrt(2.0 * 0.69314718055994531);
+    svgd_prep_kernel<<<(B.Tp + 255) / 256, 256, 0, stream>>>(x, x_ld, T, d, B.Tp, score, G, use_gmm,
+                                                             (float)(1.0 / (h * r2l)), (float)(h / r2l), B.xt,
+                                                             B.st, ctx->status);
+    PairArgs a{};
+    a.status = ctx->status;
+    a.spin_limit = ctx->spin_limit;
+    a.part = B.part;
+    a.rows = B.xt; a.row_ld = B.Tp; a.n_rows = T;
+    a.cols = B.xt; a.cols2 = B.st; a.col_ld = B.Tp;
+    a.a_out = a_out;
+    a.a_scale = (float)(r2l / ((double)h * T));
+    run_pairs(ctx, d, M_SVGD, a, T, B.counters, stream);
+    if (cuda_failed(ctx, cudaGetLastError())) return COV_ERR_CUDA;
+    return COV_OK;
+}
+
+}  // namespace cov
+
+// ---------------------------------------------------------------------------
+// C-ABI entry points
+// ---------------------------------------------------------------------------
+extern "C" cov_status cov_field_sinkhorn(cov_ctx* ctx, const float* x, int T, const float* y, const float* b, int M,
+                                         int d, float eps, int n_iter, int flags, float* f, float* g, float* p,
+                                         float* a_out, cov_stream_t stream) {
+    if (!ctx) return COV_ERR_INVALID_ARG;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return COV_ERR_CUDA;
+    return cov::sinkhorn_field_ws(ctx, ctx->ws, ctx->ws_bytes, x, d, T, y, b, M, d, eps, n_iter, flags, f, g, p,
+                                  a_out, (cudaStream_t)stream);
+}
+
+extern "C" cov_status cov_field_svgd(cov_ctx* ctx, const float* x, int T, int d, const float* score,
+                                     const cov_gmm* gmm, float h, float* a_out, cov_stream_t stream) {
+    if (!ctx) return COV_ERR_INVALID_ARG;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return COV_ERR_CUDA;
+    return cov::svgd_field_ws(ctx, ctx->ws, ctx->ws_bytes, x, d, T, d, score, gmm, h, a_out, (cudaStream_t)stream);
+}
+
+extern "C" cov_status cov_gmm_score(cov_ctx* ctx, const float* x, int T, int d, const cov_gmm* gmm, float* score,
+                                    cov_stream_t stream) {
+    if (!ctx || !x || !score || T < 1 || d < 1 || d > COV_MAX_D) return COV_ERR_INVALID_ARG;
+    cov::GmmParams G{};
+    const cov_status s = cov::make_gmm_params(gmm, d, &G);
+    if (s != COV_OK) return s;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return COV_ERR_CUDA;
+    cov::gmm_score_kernel<<<(T + 255) / 256, 256, 0, (cudaStream_t)stream>>>(x, T, d, G, score, ctx->status);
+    if (cov::cuda_failed(ctx, cudaGetLastError())) return COV_ERR_CUDA;
+    return COV_OK;
+}

@@ -1,0 +1,195 @@
+// solve.cu -- the outer iteration of Sec. II-C (cov_solve): coverage field on
+// all samples, lift to the state space, linearise, LQR tracking, control
+// update and rollout, repeated n_outer times on one stream.  One outer
+// iteration is captured in a CUDA graph and replayed.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+
+#include "cov_device.cuh"
+#include "cov_internal.h"
+
+namespace cov {
+
+int model_dims(int model, int* n, int* m);
+cov_status lqr_update_rollout(cov_ctx* ctx, void* ws, size_t ws_bytes, int model, const double* A, const double* B,
+                              const double* Q, const double* R, const double* abar, int T, double dt, double eta,
+                              const double* s0, double* u, double* s, double* v, cudaStream_t stream);
+cov_status linearize_launch(cov_ctx* ctx, int model, const double* s, const double* u, int T, double dt, double* A,
+                            double* B, cudaStream_t stream);
+
+struct SolveBufs {
+    float *x, *a;
+    double *abar, *A, *B, *v;
+};
+
+static SolveBufs carve_solve(Carver& cv, int T, int d, int n, int m) {
+    SolveBufs b{};
+    b.x = cv.take<float>((size_t)T * d);
+    b.a = cv.take<float>((size_t)T * d);
+    b.abar = cv.take<double>((size_t)T * n);
+    b.A = cv.take<double>((size_t)T * n * n);
+    b.B = cv.take<double>((size_t)T * n * m);
+    b.v = cv.take<double>((size_t)T * m);
+    return b;
+}
+
+size_t solve_buffers_bytes(int T, int d, int n, int m) {
+    Carver cv(nullptr);
+    carve_solve(cv, T, d, n, m);
+    return round_up(cv.off, 256);
+}
+
+void drop_solve_graph(cov_ctx* ctx) {
+    if (ctx->solve_graph.exec) cudaGraphExecDestroy(ctx->solve_graph.exec);
+    if (ctx->solve_graph.graph) cudaGraphDestroy(ctx->solve_graph.graph);
+    ctx->solve_graph = cov_graph_cache{};
+}
+
+// x_i = first d components of s_{i+1} (FP32 coverage coordinates).
+__global__ void extract_kernel(const double* __restrict__ s, int T, int n, int d, float* __restrict__ x) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= T) return;
+    for (int k = 0; k < d; ++k) x[(size_t)i * d + k] = (float)s[(size_t)(i + 1) * n + k];
+}
+
+// abar_t = P' a_t: the field on the coverage coordinates, zero elsewhere.
+__global__ void lift_kernel(const float* __restrict__ a, int T, int n, int d, double* __restrict__ abar) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= T) return;
+    for (int r = 0; r < n; ++r) abar[(size_t)i * n + r] = r < d ? (double)a[(size_t)i * d + r] : 0.0;
+}
+
+static uint64_t fnv(const void* p, size_t n, uint64_t h) {
+    const unsigned char* c = static_cast<const unsigned char*>(p);
+    for (size_t i = 0; i < n; ++i) h = (h ^ c[i]) * 1099511628211ull;
+    return h;
+}
+
+static cov_status validate(const cov_problem* P, int* n, int* m) {
+    if (!P || model_dims(P->model, n, m) != 0) return COV_ERR_INVALID_ARG;
+    if (P->T < 1 || !isfinite(P->dt) || !isfinite(P->eta) || P->d < 1 || P->d > std::min(*n, COV_MAX_D))
+        return COV_ERR_INVALID_ARG;
+    for (int r = 0; r < *n; ++r)
+        if (!isfinite(P->s0[r])) return COV_ERR_INVALID_ARG;
+    if (P->field == COV_FIELD_SINKHORN) {
+        if (!P->y || P->M < 1 || !(P->eps > 0.f) || P->n_iter < 0) return COV_ERR_INVALID_ARG;
+    } else if (P->field == COV_FIELD_SVGD) {
+        GmmParams G;
+        if (!(P->h > 0.f) || make_gmm_params(&P->gmm, P->d, &G) != COV_OK) return COV_ERR_INVALID_ARG;
+    } else {
+        return COV_ERR_INVALID_ARG;
+    }
+    return COV_OK;
+}
+
+// Enqueue one outer iteration on `st`.
+static cov_status enqueue_iteration(cov_ctx* ctx, const cov_problem* P, int n, int m, const SolveBufs& b, void* rest,
+                                    size_t rest_bytes, double* u, double* s, cudaStream_t st) {
+    const int T = P->T, d = P->d;
+    const int nb = (T + 255) / 256;
+    extract_kernel<<<nb, 256, 0, st>>>(s, T, n, d, b.x);
+    cov_status r;
+    if (P->field == COV_FIELD_SINKHORN)
+        r = sinkhorn_field_ws(ctx, rest, rest_bytes, b.x, d, T, P->y, P->b, P->M, d, P->eps, P->n_iter, 0, nullptr,
+                              nullptr, nullptr, b.a, st);
+    else
+        r = svgd_field_ws(ctx, rest, rest_bytes, b.x, d, T, d, nullptr, &P->gmm, P->h, b.a, st);
+    if (r != COV_OK) return r;
+    lift_kernel<<<nb, 256, 0, st>>>(b.a, T, n, d, b.abar);
+    r = linearize_launch(ctx, P->model, s, u, T, P->dt, b.A, b.B, st);
+    if (r != COV_OK) return r;
+    r = lqr_update_rollout(ctx, rest, rest_bytes, P->model, b.A, b.B, P->Q, P->R, b.abar, T, P->dt, P->eta, P->s0,
+                           u, s, b.v, st);
+    if (r != COV_OK) return r;
+    if (cuda_failed(ctx, cudaGetLastError())) return COV_ERR_CUDA;
+    return COV_OK;
+}
+
+}  // namespace cov
+
+namespace cov {
+static cov_status solve_impl(cov_ctx* ctx, const cov_problem* prob, int n_outer, double* u, double* s_out,
+                             cudaStream_t stream, bool initial_rollout);
+}
+
+extern "C" cov_status cov_solve(cov_ctx* ctx, const cov_problem* prob, int n_outer, double* u, double* s_out,
+                                cov_stream_t stream) {
+    return cov::solve_impl(ctx, prob, n_outer, u, s_out, (cudaStream_t)stream, true);
+}
+
+extern "C" cov_status cov_solve_continue(cov_ctx* ctx, const cov_problem* prob, int n_outer, double* u, double* s,
+                                         cov_stream_t stream) {
+    return cov::solve_impl(ctx, prob, n_outer, u, s, (cudaStream_t)stream, false);
+}
+
+static cov_status cov::solve_impl(cov_ctx* ctx, const cov_problem* prob, int n_outer, double* u, double* s_out,
+                                  cudaStream_t stream, bool initial_rollout) {
+    using namespace cov;
+    int n, m;
+    if (!ctx || !u || !s_out || n_outer < 0) return COV_ERR_INVALID_ARG;
+    cov_status r = validate(prob, &n, &m);
+    if (r != COV_OK) return r;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return COV_ERR_CUDA;
+    cudaStream_t st = stream;
+    Carver cv(ctx->ws);
+    SolveBufs b = carve_solve(cv, prob->T, prob->d, n, m);
+    const size_t used = round_up(cv.off, 256);
+    if (!ctx->ws || used > ctx->ws_bytes) return COV_ERR_WORKSPACE;
+    void* rest = static_cast<char*>(ctx->ws) + used;
+    const size_t rest_bytes = ctx->ws_bytes - used;
+
+    // initial trajectory from s0 and the given controls
+    if (initial_rollout) {
+        r = cov_rollout(ctx, prob->model, prob->s0, u, prob->T, prob->dt, s_out, (cov_stream_t)stream);
+        if (r != COV_OK) return r;
+    }
+    if (n_outer == 0) return COV_OK;
+
+    if (!ctx->use_graph) {
+        for (int k = 0; k < n_outer; ++k) {
+            r = enqueue_iteration(ctx, prob, n, m, b, rest, rest_bytes, u, s_out, st);
+            if (r != COV_OK) return r;
+        }
+        return COV_OK;
+    }
+    uint64_t key = 1469598103934665603ull;
+    key = fnv(prob, sizeof(cov_problem), key);
+    if (prob->field == COV_FIELD_SVGD) {
+        key = fnv(prob->gmm.w, sizeof(float) * prob->gmm.K, key);
+        key = fnv(prob->gmm.mu, sizeof(float) * prob->gmm.K * prob->d, key);
+        key = fnv(prob->gmm.sigma, sizeof(float) * prob->gmm.K, key);
+    }
+    const void* ptrs[3] = {u, s_out, ctx->ws};
+    key = fnv(ptrs, sizeof(ptrs), key);
+    if (!ctx->solve_graph.exec || ctx->solve_graph.key != key) {
+        drop_solve_graph(ctx);
+        cudaStream_t cap;
+        if (cuda_failed(ctx, cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking))) return COV_ERR_CUDA;
+        cudaGraph_t g = nullptr;
+        if (cuda_failed(ctx, cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal))) {
+            cudaStreamDestroy(cap);
+            return COV_ERR_CUDA;
+        }
+        const cov_status er = enqueue_iteration(ctx, prob, n, m, b, rest, rest_bytes, u, s_out, cap);
+        const cudaError_t ce = cudaStreamEndCapture(cap, &g);
+        cudaStreamDestroy(cap);
+        if (er != COV_OK) {
+            if (g) cudaGraphDestroy(g);
+            return er;
+        }
+        if (cuda_failed(ctx, ce)) return COV_ERR_CUDA;
+        cudaGraphExec_t ex = nullptr;
+        if (cuda_failed(ctx, cudaGraphInstantiate(&ex, g, 0))) {
+            cudaGraphDestroy(g);
+            return COV_ERR_CUDA;
+        }
+        ctx->solve_graph.graph = g;
+        ctx->solve_graph.exec = ex;
+        ctx->solve_graph.key = key;
+    }
+    for (int k = 0; k < n_outer; ++k)
+        if (cuda_failed(ctx, cudaGraphLaunch(ctx->solve_graph.exec, st))) return COV_ERR_CUDA;
+    return COV_OK;
+}

@@ -1,0 +1,83 @@
+"""Argument checking, workspace errors and device status of the C-ABI."""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+from conftest import dev32, dev64, host
+from paper_2511_11514_b300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+def test_invalid_arguments_are_rejected_without_launching(cov, ctx):
+    x = dev32(wl.random_points(10, 2, 1))
+    y = dev32(wl.random_points(12, 2, 2))
+    with pytest.raises(cov.CovError) as e:
+        cov.cov_field_sinkhorn(ctx, x, y, 0.0, 3)
+    assert e.value.status == cov.COV_ERR_INVALID_ARG
+    with pytest.raises(cov.CovError):
+        cov.cov_field_sinkhorn(ctx, x, y, 0.1, -1)
+    with pytest.raises(cov.CovError):
+        cov.cov_field_svgd(ctx, x, -1.0, score=x)
+    x7 = dev32(wl.random_points(10, 7, 1))
+    with pytest.raises(cov.CovError):
+        cov.cov_field_svgd(ctx, x7, 0.1, score=x7)
+    L = cov.load()
+    st = L.cov_field_sinkhorn(ctx.h, ctypes.c_void_p(x.data_ptr()), 10, ctypes.c_void_p(y.data_ptr()), None, 12, 2,
+                              ctypes.c_float(0.1), 1, cov.WARM_START, None, None, None, None, None)
+    assert st == cov.COV_ERR_INVALID_ARG
+    assert ctx.device_status() == (cov.COV_OK, 0)
+
+
+def test_workspace_too_small(cov):
+    c = cov.Context(0, workspace_bytes=1024)
+    try:
+        x = dev32(wl.random_points(100, 2, 1))
+        out = torch.empty_like(x)
+        L = cov.load()
+        st = L.cov_field_svgd(c.h, ctypes.c_void_p(x.data_ptr()), 100, 2, ctypes.c_void_p(x.data_ptr()), None,
+                              ctypes.c_float(0.1), ctypes.c_void_p(out.data_ptr()), None)
+        assert st == cov.COV_ERR_WORKSPACE
+    finally:
+        c.close()
+
+
+def test_nonfinite_input_sets_status(cov, ctx):
+    x = wl.random_points(50, 2, 1)
+    x[3, 0] = np.nan
+    cov.cov_field_sinkhorn(ctx, dev32(x), dev32(wl.random_points(60, 2, 2)), 0.05, 2)
+    st, fl = ctx.device_status()
+    assert fl & cov.DEV_NONFINITE and st == cov.COV_ERR_NONFINITE
+    assert ctx.device_status() == (cov.COV_OK, 0)   # read clears
+
+
+def test_bounded_wait_gives_up_and_reports_timeout(cov, ctx, orc):
+    """A wait limit of zero polls makes every tile wait give up at once; the
+    kernel drains its copies, raises the timeout bit and returns, and the
+    context stays usable."""
+    x = wl.random_points(300, 2, 1)
+    y = wl.random_points(400, 2, 2)
+    ctx.set_option(cov.OPT_SPIN_LIMIT, 0)
+    try:
+        cov.cov_field_sinkhorn(ctx, dev32(x), dev32(y), 0.05, 1)
+        st, fl = ctx.device_status()
+    finally:
+        ctx.set_option(cov.OPT_SPIN_LIMIT, 1 << 22)
+    assert fl & cov.DEV_TIMEOUT and st == cov.COV_ERR_TIMEOUT
+    a, f, g, p = cov.cov_field_sinkhorn(ctx, dev32(x), dev32(y), 0.05, 1)
+    fo, go, po = orc.sinkhorn(x, y, None, 0.05, 1)
+    assert np.abs(host(f) - fo).max() / 0.05 <= 1e-4
+    assert ctx.device_status() == (cov.COV_OK, 0)
+
+
+def test_ragged_and_degenerate_sizes(cov, ctx, orc):
+    # identical points: field zero by symmetry of the debiased divergence
+    x = wl.random_points(33, 2, 4)
+    a, f, g, p = cov.cov_field_sinkhorn(ctx, dev32(x), dev32(x), 0.05, 200)
+    assert np.abs(host(a)).max() < 1e-3
+    # every trajectory point at the same place, one reference point
+    xs = np.tile([[0.25, 0.75]], (17, 1))
+    a, f, g, p = cov.cov_field_sinkhorn(ctx, dev32(xs), dev32(np.array([[0.5, 0.25]])), 0.01, 3)
+    np.testing.assert_allclose(host(a), np.tile(2 * (np.array([0.5, 0.25]) - [0.25, 0.75]), (17, 1)), rtol=1e-5)

@@ -1,0 +1,85 @@
+"""GPU parity of the Stein field (Eq. 4), the mixture score, linearisation
+(Eq. 8), rollout and the FP64 LQR step (Eq. 9-10) with the FP64 oracle."""
+import numpy as np
+import pytest
+import torch
+
+from conftest import dev32, dev64, host, rel_norm
+from paper_2511_11514_b300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("T,d,K", [(1, 2, 1), (2, 2, 3), (37, 1, 2), (256, 2, 3), (1000, 3, 4), (4099, 2, 16),
+                                   (300, 6, 5)])
+def test_svgd_field_with_mixture_score(cov, ctx, orc, T, d, K):
+    w, mu, sigma = wl.gmm_params(K, seed=T + K, d=d)
+    w, mu, sigma = (wl.f32_pair(v)[1] for v in (w, mu, sigma))
+    x = wl.random_points(T, d, seed=T)
+    h = 0.05 if d <= 2 else 0.2
+    a = cov.cov_field_svgd(ctx, dev32(x), h, gmm=(w, mu, sigma))
+    ao = orc.svgd_field(x, orc.gmm_score(x, w, mu, sigma), h)
+    assert rel_norm(host(a), ao) <= 1e-4
+    assert ctx.device_status()[1] == 0
+
+
+@pytest.mark.parametrize("T,d", [(5, 2), (777, 2), (2500, 3)])
+def test_svgd_field_with_given_score(cov, ctx, orc, T, d):
+    x = wl.random_points(T, d, seed=1)
+    sc = wl.f32_pair(wl.rng(2).standard_normal((T, d)) * 10)[1]
+    a = cov.cov_field_svgd(ctx, dev32(x), 0.1, score=dev32(sc))
+    assert rel_norm(host(a), orc.svgd_field(x, sc, 0.1)) <= 1e-4
+
+
+def test_gmm_score(cov, ctx, orc):
+    w, mu, sigma = (wl.f32_pair(v)[1] for v in wl.gmm_params(7, seed=3))
+    x = wl.random_points(3000, 2, seed=4)
+    sc = cov.cov_gmm_score(ctx, dev32(x), (w, mu, sigma))
+    assert rel_norm(host(sc), orc.gmm_score(x, w, mu, sigma)) <= 1e-5
+
+
+def _random_lqr(T, n, m, seed):
+    g = wl.rng(seed)
+    A = np.eye(n) + 0.1 * g.standard_normal((T, n, n))
+    B = 0.3 * g.standard_normal((T, n, m))
+    L = g.standard_normal((n, n))
+    Q = L @ L.T / n + 0.1 * np.eye(n)
+    Rm = g.standard_normal((m, m))
+    R = 0.05 * (Rm @ Rm.T + np.eye(m))
+    abar = g.standard_normal((T, n))
+    return A, B, Q, R, abar
+
+
+@pytest.mark.parametrize("T,n,m", [(1, 2, 2), (2, 1, 1), (33, 4, 2), (100, 3, 2), (1000, 4, 3), (4096, 4, 2),
+                                   (65, 2, 1), (70, 3, 3)])
+def test_lqr_track_matches_oracle(cov, ctx, orc, T, n, m):
+    A, B, Q, R, abar = _random_lqr(T, n, m, seed=T + 10 * n + m)
+    v, z = cov.cov_lqr_track(ctx, dev64(A), dev64(B), Q, R, dev64(abar))
+    vo, zo, _ = orc.lqr_track(A, B, Q, R, abar)
+    np.testing.assert_allclose(host(v), vo, rtol=1e-9, atol=1e-10 * np.abs(vo).max())
+    np.testing.assert_allclose(host(z), zo, rtol=1e-9, atol=1e-10 * np.abs(zo).max())
+    assert ctx.device_status()[1] == 0
+
+
+def test_lqr_reports_non_spd_riccati(cov, ctx):
+    T, n, m = 8, 2, 2
+    A, B, Q, R, abar = _random_lqr(T, n, m, seed=1)
+    cov.cov_lqr_track(ctx, dev64(A), dev64(B), Q, -np.eye(2), dev64(abar))
+    st, fl = ctx.device_status()
+    assert fl & cov.DEV_NOT_SPD and st == cov.COV_ERR_NONFINITE
+
+
+@pytest.mark.parametrize("model", [wl.SINGLE_INT, wl.DOUBLE_INT, wl.UNICYCLE])
+def test_linearize_and_rollout_match_oracle(cov, ctx, orc, model):
+    n, m = wl.MODEL_DIMS[model]
+    T, dt = 513, 0.03
+    g = wl.rng(model)
+    s0 = g.standard_normal(n)
+    u = g.standard_normal((T, m))
+    s = cov.cov_rollout(ctx, model, s0, dev64(u), dt)
+    so = orc.rollout(model, s0, u, dt)
+    np.testing.assert_allclose(host(s), so, rtol=1e-12, atol=1e-12)
+    A, B = cov.cov_linearize(ctx, model, dev64(so), dev64(u), dt)
+    Ao, Bo = orc.linearize(model, so, u, dt)
+    np.testing.assert_allclose(host(A), Ao, rtol=1e-13, atol=1e-15)
+    np.testing.assert_allclose(host(B), Bo, rtol=1e-13, atol=1e-15)
