@@ -30,10 +30,17 @@ def cov():
 
 
 @pytest.fixture(scope="session")
-def ctx(cov):
+def _session_ctx(cov):
     c = cov.Context(0)
     yield c
     c.close()
+
+
+@pytest.fixture
+def ctx(_session_ctx):
+    """The shared context, with its device status cleared before each test."""
+    _session_ctx.device_status()
+    return _session_ctx
 
 
 def dev32(a):

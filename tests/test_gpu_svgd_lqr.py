@@ -39,8 +39,9 @@ def test_gmm_score(cov, ctx, orc):
 
 
 def _random_lqr(T, n, m, seed):
+    """Time-varying, well-conditioned: A_t = 0.97 x (random orthogonal)."""
     g = wl.rng(seed)
-    A = np.eye(n) + 0.1 * g.standard_normal((T, n, n))
+    A = np.stack([0.97 * np.linalg.qr(g.standard_normal((n, n)))[0] for _ in range(T)])
     B = 0.3 * g.standard_normal((T, n, m))
     L = g.standard_normal((n, n))
     Q = L @ L.T / n + 0.1 * np.eye(n)
@@ -58,6 +59,22 @@ def test_lqr_track_matches_oracle(cov, ctx, orc, T, n, m):
     vo, zo, _ = orc.lqr_track(A, B, Q, R, abar)
     np.testing.assert_allclose(host(v), vo, rtol=1e-9, atol=1e-10 * np.abs(vo).max())
     np.testing.assert_allclose(host(z), zo, rtol=1e-9, atol=1e-10 * np.abs(zo).max())
+    assert ctx.device_status()[1] == 0
+
+
+def test_lqr_double_integrator_long_horizon(cov, ctx, orc):
+    """The benchmark's LQR: double integrator, coverage weight on position
+    only (Q PSD), R = 0.01 I, T = 4096."""
+    T, dt = 4096, 0.05
+    s = np.zeros((T + 1, 4))
+    A, B = orc.linearize(wl.DOUBLE_INT, s, np.zeros((T, 2)), dt)
+    abar = np.zeros((T, 4))
+    abar[:, :2] = wl.rng(5).standard_normal((T, 2)) * 0.1
+    Q, R = wl.coverage_Q(wl.DOUBLE_INT), 0.01 * np.eye(2)
+    v, z = cov.cov_lqr_track(ctx, dev64(A), dev64(B), Q, R, dev64(abar))
+    vo, zo, _ = orc.lqr_track(A, B, Q, R, abar)
+    np.testing.assert_allclose(host(v), vo, rtol=1e-9, atol=1e-11 * np.abs(vo).max())
+    np.testing.assert_allclose(host(z), zo, rtol=1e-9, atol=1e-11 * np.abs(zo).max())
     assert ctx.device_status()[1] == 0
 
 
