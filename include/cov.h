@@ -176,6 +176,33 @@ COV_API cov_status cov_field_sinkhorn(cov_ctx* ctx, const float* x, int T,
                               float* g, float* p, float* a_out,
                               cov_stream_t stream);
 
+/* The same field for callers that must not allocate device memory.  The
+ * paper has no counterpart: this is a library convenience.  Programs that
+ * cannot call cudaMalloc -- code running while a CUDA graph is captured,
+ * plugins whose host hands out all device memory from its own arena,
+ * real-time loops that cannot take the device synchronisation of
+ * cudaMalloc/cudaFree -- get the scratch from one fixed 32 MiB array
+ * compiled into the library (held on every GPU that loads it, until the
+ * process exits) instead of a context workspace.  No context is needed and
+ * nothing is allocated; the caller still passes x, y, b, f, g, p and a_out
+ * exactly as for cov_field_sinkhorn, with the same meaning, and the results
+ * are those of cov_field_sinkhorn with default options.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture begins.  Later calls use the cached address.
+ *   - Sizes whose scratch exceeds the array are rejected with
+ *     COV_ERR_WORKSPACE before anything is launched (d = 2 fits up to about
+ *     T = 65536 with M = 262144).
+ *   - Every call reuses the same array; the call clears what must start at
+ *     zero on `stream` itself.  Calls that overlap on the GPU (different
+ *     streams, or several host threads) race on the array: serialise them.
+ *   - Device-detected conditions (non-finite values, a wait that gave up)
+ *     are not reported; check the outputs for NaN/Inf instead. */
+COV_API cov_status cov_field_sinkhorn_noalloc(const float* x, int T, const float* y,
+                                              const float* b, int M, int d, float eps,
+                                              int n_iter, int flags, float* f, float* g,
+                                              float* p, float* a_out, cov_stream_t stream);
+
 /* ---- dynamics (Eq. 3, 8) ------------------------------------------------ */
 
 /* A_t = I + dt df/ds, B_t = dt df/du at (s_t, u_t), t = 0..T-1 (Eq. 8).

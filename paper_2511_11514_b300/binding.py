@@ -31,7 +31,8 @@ MODEL_DIMS = {SINGLE_INT: (2, 2), DOUBLE_INT: (4, 2), UNICYCLE: (3, 2)}
 EXPORTS = (
     "cov_ctx_create", "cov_ctx_destroy", "cov_ctx_reserve", "cov_workspace_size", "cov_ctx_reserve_for",
     "cov_get_device_status", "cov_status_string", "cov_last_cuda_error", "cov_ctx_set_option",
-    "cov_gmm_score", "cov_field_svgd", "cov_field_sinkhorn", "cov_linearize", "cov_rollout",
+    "cov_gmm_score", "cov_field_svgd", "cov_field_sinkhorn", "cov_field_sinkhorn_noalloc", "cov_linearize",
+    "cov_rollout",
     "cov_lqr_track", "cov_solve", "cov_solve_continue", "cov_probe_peaks",
 )
 
@@ -80,6 +81,7 @@ def load(path: str = LIB_PATH):
         "cov_gmm_score": (_i, [_P, _P, _i, _i, ctypes.POINTER(cov_gmm), _P, _P]),
         "cov_field_svgd": (_i, [_P, _P, _i, _i, _P, ctypes.POINTER(cov_gmm), _f, _P, _P]),
         "cov_field_sinkhorn": (_i, [_P, _P, _i, _P, _P, _i, _i, _f, _i, _i, _P, _P, _P, _P, _P]),
+        "cov_field_sinkhorn_noalloc": (_i, [_P, _i, _P, _P, _i, _i, _f, _i, _i, _P, _P, _P, _P, _P]),
         "cov_linearize": (_i, [_P, _i, _P, _P, _i, _d, _P, _P, _P]),
         "cov_rollout": (_i, [_P, _i, _P, _P, _i, _d, _P, _P]),
         "cov_lqr_track": (_i, [_P, _P, _P, _P, _P, _P, _i, _i, _i, _P, _P, _P]),
