@@ -17,6 +17,7 @@ bool cov::cuda_failed(cov_ctx* ctx, cudaError_t e) {
 namespace cov {
 size_t solve_buffers_bytes(int T, int d, int n, int m);
 void drop_solve_graph(cov_ctx* ctx);
+void lqr_set_attributes();
 }  // namespace cov
 
 extern "C" const char* cov_status_string(cov_status s) {
@@ -42,6 +43,7 @@ extern "C" cov_status cov_ctx_create(cov_ctx** out, int device, size_t workspace
     if (!ctx) return COV_ERR_WORKSPACE;
     ctx->device = device;
     cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
+    cov::lqr_set_attributes();
     if (cudaMalloc(&ctx->status, 256) != cudaSuccess) {
         delete ctx;
         return COV_ERR_WORKSPACE;

@@ -3,18 +3,29 @@
 //   * the LQR flow-matching problem of Eq. 9-10 on the time grid,
 //       min sum_{t=1..T} |z_t - abar_t|_Q^2 + sum_{t=0..T-1} |v_t|_R^2,
 //       z_{t+1} = A_t z_t + B_t v_t, z_0 = 0,
-//     solved by one warp: a backward Riccati recursion over t = T-1..0
-//       S = R + B'P'B, G = B'P'A, h = B'p', K = S^-1 G, k = S^-1 h,
-//       P = Q_t + A'P'A - G'K,  p = -Q_t abar_t + A'p' - K'h
-//     (P_T = Q, p_T = -Q abar_T, Q_0 = 0) and a forward pass
-//       v_t = -K_t z_t - k_t, z_{t+1} = A_t z_t + B_t v_t;
-//   * optionally, fused into the forward pass, the control update
-//     u_t <- u_t + eta v_t and the rollout s_{t+1} = s_t + dt f(s_t, u_t).
+//     with value function z'P_t z + 2 p_t'z:
+//       Riccati (backward, nonlinear in P; one warp, serial):
+//         S = R + B'P'B, G = B'P'A, K = S^-1 G, P = Q_t + A'P'A - G'K
+//         (P and S kept exactly symmetric: upper triangle computed, mirrored),
+//         and the closed loop M_t = A_t - B_t K_t, N_t = S^-1 B_t'
+//       affine part (backward, linear in p):
+//         p_t = M_t' p_{t+1} + c_t,  c_t = -Q_t abar_t,  p_T = -Q abar_T,
+//         k_t = N_t p_{t+1}
+//       forward pass (linear in z):
+//         z_{t+1} = M_t z_t + e_t,  e_t = -B_t k_t,  v_t = -K_t z_t - k_t
+//     (Q_0 = 0; this is the usual recursion written with K'SK = G'K);
+//   * the control update u <- u + eta v and the Euler rollout.
 //
-// The recursion is a chain of T dependent steps, so it runs on one warp with
-// the lanes spread over matrix entries (each lane owns one entry of a
-// product per phase, four phases per backward step, two per forward step)
-// and the per-step matrices streamed into shared memory one chunk ahead.
+// FP64 on B300 has a ~65-cycle dependent-FMA latency and ~1.6 FMA/clk per
+// SM, so the serial chains are what cost time.  The design keeps only the
+// Riccati recursion serial (and caches it for time-invariant models), and
+// runs the two affine recursions as chunked parallel-in-time scans: each
+// chunk of C steps composes its affine map (one warp per chunk, spread over
+// the SMs), one warp chains the chunk maps, and each chunk then fills in its
+// steps from its boundary value.  The rollout of every model is a sum of
+// Euler increments, done as block-wide prefix sums.  Inside a warp every
+// lane runs the same dot product on different operands, so no phase
+// diverges.
 #include <math.h>
 
 #include <algorithm>
@@ -29,38 +40,9 @@ struct LqrConst {
     double R[COV_MAX_M * COV_MAX_M];
 };
 
-struct RolloutArgs {
-    int model;     // < 0: no update/rollout
-    double dt;
-    double eta;
-    double s0[COV_MAX_N];
-    double* u;     // [T][MC] in/out
-    double* s;     // [T+1][N] out
-};
-
-__device__ __forceinline__ void dyn_f(int model, const double* s, const double* u, double* f) {
-    switch (model) {
-        case COV_SINGLE_INT:
-            f[0] = u[0];
-            f[1] = u[1];
-            break;
-        case COV_DOUBLE_INT:
-            f[0] = s[2];
-            f[1] = s[3];
-            f[2] = u[0];
-            f[3] = u[1];
-            break;
-        default: {  // unicycle
-            double sn, cs;
-            sincos(s[2], &sn, &cs);
-            f[0] = u[0] * cs;
-            f[1] = u[0] * sn;
-            f[2] = u[1];
-        }
-    }
-}
-
-constexpr int kCh = 32;  // steps per streamed chunk
+constexpr int kSB = 32;          // steps per streamed sub-block
+constexpr int kMaxChunk = 512;   // steps per scan chunk
+constexpr int kMaxChunks = 1024; // scan chunks
 
 // Inverse of a small SPD matrix (MC <= 3) by the adjugate; returns false if
 // a leading principal minor is not positive.
@@ -95,7 +77,7 @@ __device__ __forceinline__ bool spd_inverse(const double* S, double* Si) {
     }
 }
 
-// Asynchronous 8-byte global->shared copies (cp.async), so the next chunk
+// Asynchronous 8-byte global->shared copies (cp.async): the next sub-block
 // of per-step matrices streams in while the current one is processed.
 __device__ __forceinline__ void cp_async8(void* dst, const void* src) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
@@ -104,251 +86,443 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait_all_but_one() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
-template <int N, int MC>
-struct LqrSmem {
-    double A[2][kCh][N * N];
-    double B[2][kCh][N * MC];
-    double ab[2][kCh][N];      // backward: targets; forward: unused
-    double K[2][kCh][MC * N];  // forward: gains
-    double k[2][kCh][MC];
-    double u[2][kCh][MC];      // forward: controls (rollout)
-    double P[N * N], p[N];
-    double PA[N * N], PB[N * MC], h[MC], Atp[N], qa[N];
-    double S[MC * MC], G[MC * N], AtPA[N * N];
-    double Kc[MC * N], kc[MC];
-    double z[N], v[MC], s[N];
-};
-
-// Copy `cnt` consecutive rows of `e` doubles starting at row t0 into dst.
+// Copy rows t0 .. t0+cnt-1 (each `e` doubles) of src into dst.
 __device__ __forceinline__ void stream_rows(double* dst, const double* __restrict__ src, int t0, int cnt, int e,
                                             int lane) {
     for (int i = lane; i < cnt * e; i += 32) cp_async8(dst + i, src + (size_t)t0 * e + i);
 }
 
+// Sub-blocks of a step range [lo, hi] (inclusive), visited backward or
+// forward: sub-block b covers steps first(b) .. first(b)+count(b)-1.
+struct SubBlocks {
+    int lo, hi, n;
+    bool bwd;
+    __device__ SubBlocks(int lo_, int hi_, bool b) : lo(lo_), hi(hi_), bwd(b) { n = (hi - lo + kSB) / kSB; }
+    __device__ int first(int b) const { return bwd ? max(lo, hi + 1 - (b + 1) * kSB) : lo + b * kSB; }
+    __device__ int count(int b) const {
+        return bwd ? (hi + 1 - b * kSB) - first(b) : min(kSB, hi + 1 - first(b));
+    }
+};
+
+// ---------------------------------------------------------------------------
+// Riccati recursion (one warp).  Outputs per step: K_t [MC][N], M_t [N][N],
+// N_t [MC][N].
+// ---------------------------------------------------------------------------
 template <int N, int MC>
-__global__ void __launch_bounds__(32, 1) lqr_kernel(const double* __restrict__ A, const double* __restrict__ B,
-                                                    LqrConst C, const double* __restrict__ abar, int T,
-                                                    double* __restrict__ Kg, double* __restrict__ kg,
-                                                    double* __restrict__ v_out, double* __restrict__ z_out,
-                                                    RolloutArgs ro, unsigned* status) {
-    __shared__ __align__(16) LqrSmem<N, MC> sm;
+struct RicSmem {
+    double A[2][kSB][N * N];
+    double B[2][kSB][N * MC];
+    double P[N * N], PA[N * N], PB[N * MC], S[MC * MC], G[MC * N], AtPA[N * N], K[MC * N];
+};
+
+template <int N, int MC>
+__global__ void __launch_bounds__(32, 1) riccati_kernel(const double* __restrict__ A, const double* __restrict__ B,
+                                                        LqrConst C, int T, double* __restrict__ Kg,
+                                                        double* __restrict__ Mg, double* __restrict__ Ng,
+                                                        unsigned* status) {
+    __shared__ __align__(16) RicSmem<N, MC> sm;
     const int lane = threadIdx.x;
     bool spd_ok = true;
-
-    // P_T = Q, p_T = -Q abar_T
     for (int e = lane; e < N * N; e += 32) sm.P[e] = C.Q[e];
-    if (lane < N) {
-        double acc = 0.0;
-        for (int c = 0; c < N; ++c) acc += C.Q[lane * N + c] * abar[(size_t)(T - 1) * N + c];
-        sm.p[lane] = -acc;
-    }
-    // ---- backward pass: chunk c covers t = lo(c) .. T-1-c*kCh ------------------
-    const int n_chunks = (T + kCh - 1) / kCh;
-    auto chunk_lo = [&](int c) { return max(0, T - (c + 1) * kCh); };
-    auto chunk_cnt = [&](int c) { return T - c * kCh - chunk_lo(c); };
-    // abar row for step t is t-1; step t = 0 has no target (zero row)
-    auto issue_bwd = [&](int c, int b) {
-        const int lo = chunk_lo(c), cnt = chunk_cnt(c);
-        stream_rows(&sm.A[b][0][0], A, lo, cnt, N * N, lane);
-        stream_rows(&sm.B[b][0][0], B, lo, cnt, N * MC, lane);
-        if (lo == 0) {
-            if (lane < N) sm.ab[b][0][lane] = 0.0;
-            if (cnt > 1) stream_rows(&sm.ab[b][1][0], abar, 0, cnt - 1, N, lane);
-        } else {
-            stream_rows(&sm.ab[b][0][0], abar, lo - 1, cnt, N, lane);
-        }
+
+    // phase-1 role of this lane: PA = P'A (N*N entries) or PB = P'B (N*MC)
+    const bool p1v = lane < N * N + N * MC;
+    const bool p1A = lane < N * N;
+    const int p1f = p1A ? lane : lane - N * N;
+    const int p1w = p1A ? N : MC;
+    const int p1r = p1v ? p1f / p1w : 0, p1c = p1v ? p1f % p1w : 0;
+    double* p1dst = p1A ? &sm.PA[p1f] : &sm.PB[p1v ? p1f : 0];
+    constexpr int NP2 = MC * MC + MC * N + N * N;
+
+    const SubBlocks sb(0, T - 1, true);
+    auto issue = [&](int b, int buf) {
+        stream_rows(&sm.A[buf][0][0], A, sb.first(b), sb.count(b), N * N, lane);
+        stream_rows(&sm.B[buf][0][0], B, sb.first(b), sb.count(b), N * MC, lane);
         cp_async_commit();
     };
-    issue_bwd(0, 0);
-    for (int c = 0; c < n_chunks; ++c) {
-        const int buf = c & 1;
-        if (c + 1 < n_chunks) {
-            issue_bwd(c + 1, buf ^ 1);
+    issue(0, 0);
+    for (int b = 0; b < sb.n; ++b) {
+        const int buf = b & 1;
+        if (b + 1 < sb.n) {
+            issue(b + 1, buf ^ 1);
             cp_async_wait_all_but_one();
         } else {
             cp_async_wait_all();
         }
         __syncwarp();
-        const int lo = chunk_lo(c), cnt = chunk_cnt(c);
-        for (int j = cnt - 1; j >= 0; --j) {
-            const int t = lo + j;
+        const int t0 = sb.first(b);
+        for (int j = sb.count(b) - 1; j >= 0; --j) {
+            const int t = t0 + j;
             const double* At = sm.A[buf][j];
             const double* Bt = sm.B[buf][j];
-            const double* at = sm.ab[buf][j];
-            // phase 1: PA = P'A, PB = P'B, h = B'p'
-            for (int e = lane; e < N * N + N * MC + MC; e += 32) {
-                if (e < N * N) {
-                    const int r = e / N, cc = e % N;
-                    double acc = 0.0;
+            // phase 1: PA = P'A, PB = P'B
+            if (p1v) {
+                const double* X = p1A ? At : Bt;
+                double acc = 0.0;
 #pragma unroll
-                    for (int q = 0; q < N; ++q) acc = fma(sm.P[r * N + q], At[q * N + cc], acc);
-                    sm.PA[e] = acc;
-                } else if (e < N * N + N * MC) {
-                    const int f = e - N * N, r = f / MC, cc = f % MC;
-                    double acc = 0.0;
-#pragma unroll
-                    for (int q = 0; q < N; ++q) acc = fma(sm.P[r * N + q], Bt[q * MC + cc], acc);
-                    sm.PB[f] = acc;
-                } else {
-                    const int r = e - N * N - N * MC;
-                    double acc = 0.0;
-#pragma unroll
-                    for (int q = 0; q < N; ++q) acc = fma(Bt[q * MC + r], sm.p[q], acc);
-                    sm.h[r] = acc;
-                }
+                for (int q = 0; q < N; ++q) acc = fma(sm.P[p1r * N + q], X[q * p1w + p1c], acc);
+                *p1dst = acc;
             }
             __syncwarp();
-            // phase 2: S = R + B'PB, G = B'PA, AtPA = A'PA, Atp = A'p', qa = Q_t abar_t
-            for (int e = lane; e < MC * MC + MC * N + N * N + 2 * N; e += 32) {
-                if (e < MC * MC) {
-                    const int r = e / MC, cc = e % MC;
-                    double acc = C.R[e];
+            // phase 2: S = R + B'PB, G = B'PA, AtPA = A'PA
+            for (int e = lane; e < NP2; e += 32) {
+                const int role = e < MC * MC ? 0 : (e < MC * MC + MC * N ? 1 : 2);
+                const int f = e - (role == 0 ? 0 : (role == 1 ? MC * MC : MC * MC + MC * N));
+                const int w = role == 0 ? MC : N;
+                const int r = f / w, c = f % w;
+                const double* Y = role == 2 ? At : Bt;
+                const int ys = role == 2 ? N : MC;
+                const double* Z = role == 0 ? sm.PB : sm.PA;
+                const int zs = role == 0 ? MC : N;
+                double acc = role == 0 ? C.R[f] : 0.0;
 #pragma unroll
-                    for (int q = 0; q < N; ++q) acc = fma(Bt[q * MC + r], sm.PB[q * MC + cc], acc);
-                    sm.S[e] = acc;
-                } else if (e < MC * MC + MC * N) {
-                    const int f = e - MC * MC, r = f / N, cc = f % N;
-                    double acc = 0.0;
-#pragma unroll
-                    for (int q = 0; q < N; ++q) acc = fma(Bt[q * MC + r], sm.PA[q * N + cc], acc);
-                    sm.G[f] = acc;
-                } else if (e < MC * MC + MC * N + N * N) {
-                    const int f = e - MC * MC - MC * N, r = f / N, cc = f % N;
-                    double acc = 0.0;
-#pragma unroll
-                    for (int q = 0; q < N; ++q) acc = fma(At[q * N + r], sm.PA[q * N + cc], acc);
-                    sm.AtPA[f] = acc;
-                } else if (e < MC * MC + MC * N + N * N + N) {
-                    const int r = e - MC * MC - MC * N - N * N;
-                    double acc = 0.0;
-#pragma unroll
-                    for (int q = 0; q < N; ++q) acc = fma(At[q * N + r], sm.p[q], acc);
-                    sm.Atp[r] = acc;
-                } else {
-                    const int r = e - MC * MC - MC * N - N * N - N;
-                    double acc = 0.0;
-                    if (t >= 1) {
-#pragma unroll
-                        for (int q = 0; q < N; ++q) acc = fma(C.Q[r * N + q], at[q], acc);
-                    }
-                    sm.qa[r] = acc;
-                }
+                for (int q = 0; q < N; ++q) acc = fma(Y[q * ys + r], Z[q * zs + c], acc);
+                // S is written from its upper triangle only and mirrored, so it
+                // stays exactly symmetric
+                double* dst = role == 0 ? &sm.S[f] : (role == 1 ? &sm.G[f] : &sm.AtPA[f]);
+                if (role != 0 || r <= c) *dst = acc;
+                if (role == 0 && r < c) sm.S[c * MC + r] = acc;
             }
             __syncwarp();
-            // phase 3: K = S^-1 G, k = S^-1 h
-            if (lane < MC * N + MC) {
+            // phase 3: K = S^-1 G, N_t = S^-1 B'
+            {
                 double Si[MC * MC];
                 spd_ok &= spd_inverse<MC>(sm.S, Si);
-                if (lane < MC * N) {
-                    const int r = lane / N, cc = lane % N;
+                if (lane < 2 * MC * N) {
+                    const bool isK = lane < MC * N;
+                    const int f = isK ? lane : lane - MC * N;
+                    const int r = f / N, c = f % N;
+                    const double* W = isK ? sm.G : Bt;
+                    const int ws = isK ? N : 1, wo = isK ? c : c * MC;
                     double acc = 0.0;
 #pragma unroll
-                    for (int q = 0; q < MC; ++q) acc = fma(Si[r * MC + q], sm.G[q * N + cc], acc);
-                    sm.Kc[lane] = acc;
-                    Kg[(size_t)t * MC * N + lane] = acc;
-                } else {
-                    const int r = lane - MC * N;
-                    double acc = 0.0;
-#pragma unroll
-                    for (int q = 0; q < MC; ++q) acc = fma(Si[r * MC + q], sm.h[q], acc);
-                    sm.kc[r] = acc;
-                    kg[(size_t)t * MC + r] = acc;
+                    for (int q = 0; q < MC; ++q) acc = fma(Si[r * MC + q], W[q * ws + wo], acc);
+                    double* g = isK ? Kg : Ng;
+                    g[(size_t)t * MC * N + f] = acc;
+                    if (isK) sm.K[f] = acc;
                 }
             }
             __syncwarp();
-            // phase 4: P = Q_t + A'PA - G'K, p = -Q_t abar_t + A'p' - K'h
-            if (lane < N * N) {
-                const int r = lane / N, cc = lane % N;
-                double acc = sm.AtPA[lane] + (t >= 1 ? C.Q[lane] : 0.0);
+            // phase 4: P = Q_t + A'PA - G'K, M_t = A - B K
+            {
+                const bool has_q = t >= 1;
+                const bool isP = lane < N * N;
+                const int f = isP ? lane : lane - N * N;
+                if (lane < 2 * N * N) {
+                    const int r = f / N, c = f % N;
+                    double acc = isP ? (has_q ? C.Q[f] : 0.0) + sm.AtPA[f] : At[f];
+                    const double* U = isP ? sm.G : Bt;
+                    const int us = isP ? N : 1, uo = isP ? r : r * MC;
 #pragma unroll
-                for (int q = 0; q < MC; ++q) acc = fma(-sm.G[q * N + r], sm.Kc[q * N + cc], acc);
-                sm.P[lane] = acc;
-            } else if (lane < N * N + N) {
-                const int r = lane - N * N;
-                double acc = sm.Atp[r] - sm.qa[r];
-#pragma unroll
-                for (int q = 0; q < MC; ++q) acc = fma(-sm.Kc[q * N + r], sm.h[q], acc);
-                sm.p[r] = acc;
+                    for (int q = 0; q < MC; ++q) acc = fma(-U[q * us + uo], sm.K[q * N + c], acc);
+                    // P from its upper triangle, mirrored: rounding never gives it an
+                    // antisymmetric part, which this recursion would amplify
+                    if (isP) {
+                        if (r <= c) {
+                            sm.P[r * N + c] = acc;
+                            sm.P[c * N + r] = acc;
+                        }
+                    } else {
+                        Mg[(size_t)t * N * N + f] = acc;
+                    }
+                }
             }
             __syncwarp();
         }
         __syncwarp();
     }
     if (!spd_ok) raise_status(status, kDevNotSpd);
-    __threadfence_block();
-    __syncwarp();
+}
 
-    // ---- forward pass (+ optional control update and rollout) ----------------
-    const bool do_roll = ro.model >= 0;
-    if (lane < N) {
-        sm.z[lane] = 0.0;
-        if (z_out) z_out[lane] = 0.0;
-        if (do_roll) {
-            sm.s[lane] = ro.s0[lane];
-            ro.s[lane] = ro.s0[lane];
+// ---------------------------------------------------------------------------
+// Affine recursions as chunked scans.  Backward (BWD): p_t = M_t' p_{t+1} +
+// c_t for t = T-1..0.  Forward: z_{t+1} = M_t z_t + e_t for t = 0..T-1.
+// Chunk c covers steps [c*C, min((c+1)*C, T) - 1].
+// ---------------------------------------------------------------------------
+
+// Compose the chunk's affine map (Phi | phi) and write its forcing terms:
+//   BWD: c_t = -Q_t abar_t (abar row t-1, t >= 1; c_0 = 0); map p_lo = Phi p_{hi+1} + phi
+//   FWD: e_t = -B_t k_t;                                    map z_{hi+1} = Phi z_lo + phi
+template <int N, int MC, bool BWD>
+__global__ void __launch_bounds__(32) compose_kernel(const double* __restrict__ Mg, LqrConst Cq,
+                                                     const double* __restrict__ abar, const double* __restrict__ Bg,
+                                                     const double* __restrict__ kg, int T, int C,
+                                                     double* __restrict__ force, double* __restrict__ maps) {
+    extern __shared__ __align__(16) double dyn[];
+    __shared__ __align__(16) double Ms[2][kSB][N * N];
+    __shared__ double X[N * (N + 1)];
+    const int lane = threadIdx.x;
+    const int lo = blockIdx.x * C, hi = min(lo + C, T) - 1, cnt = hi - lo + 1;
+    double* fs = dyn;  // [cnt][N]
+    for (int i = lane; i < cnt * N; i += 32) {
+        const int t = lo + i / N, r = i % N;
+        double acc = 0.0;
+        if constexpr (BWD) {
+            if (t >= 1) {
+#pragma unroll
+                for (int q = 0; q < N; ++q) acc = fma(-Cq.Q[r * N + q], abar[(size_t)(t - 1) * N + q], acc);
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < MC; ++q) acc = fma(-Bg[((size_t)t * N + r) * MC + q], kg[(size_t)t * MC + q], acc);
         }
+        fs[i] = acc;
+        force[(size_t)t * N + r] = acc;
     }
-    auto issue_fwd = [&](int c, int b) {
-        const int t0 = c * kCh, cnt = min(kCh, T - t0);
-        stream_rows(&sm.A[b][0][0], A, t0, cnt, N * N, lane);
-        stream_rows(&sm.B[b][0][0], B, t0, cnt, N * MC, lane);
-        stream_rows(&sm.K[b][0][0], Kg, t0, cnt, MC * N, lane);
-        stream_rows(&sm.k[b][0][0], kg, t0, cnt, MC, lane);
-        if (do_roll) stream_rows(&sm.u[b][0][0], ro.u, t0, cnt, MC, lane);
+    constexpr int NX = N * (N + 1);
+    const int xr = lane / (N + 1), xc = lane % (N + 1);
+    if (lane < NX) X[lane] = (xc == xr) ? 1.0 : 0.0;
+    const SubBlocks sb(lo, hi, BWD);
+    auto issue = [&](int b, int buf) {
+        stream_rows(&Ms[buf][0][0], Mg, sb.first(b), sb.count(b), N * N, lane);
         cp_async_commit();
     };
-    issue_fwd(0, 0);
-    for (int c = 0; c < n_chunks; ++c) {
-        const int buf = c & 1;
-        if (c + 1 < n_chunks) {
-            issue_fwd(c + 1, buf ^ 1);
+    issue(0, 0);
+    for (int b = 0; b < sb.n; ++b) {
+        const int buf = b & 1;
+        if (b + 1 < sb.n) {
+            issue(b + 1, buf ^ 1);
             cp_async_wait_all_but_one();
         } else {
             cp_async_wait_all();
         }
         __syncwarp();
-        const int t0 = c * kCh, cnt = min(kCh, T - t0);
-        for (int j = 0; j < cnt; ++j) {
+        const int t0 = sb.first(b), cntb = sb.count(b);
+        for (int jj = 0; jj < cntb; ++jj) {
+            const int j = BWD ? cntb - 1 - jj : jj;
+            const double* Mt = Ms[buf][j];
+            double acc = 0.0;
+            if (lane < NX) {
+                acc = (xc == N) ? fs[(t0 + j - lo) * N + xr] : 0.0;
+#pragma unroll
+                for (int q = 0; q < N; ++q) {
+                    const double mq = BWD ? Mt[q * N + xr] : Mt[xr * N + q];
+                    acc = fma(mq, X[q * (N + 1) + xc], acc);
+                }
+            }
+            __syncwarp();
+            if (lane < NX) X[lane] = acc;
+            __syncwarp();
+        }
+        __syncwarp();
+    }
+    if (lane < NX) maps[(size_t)blockIdx.x * NX + lane] = X[lane];
+}
+
+// Chain the chunk maps (one warp): bnd[c] = the value entering chunk c
+// (BWD: p_{hi+1}; FWD: z_lo).
+template <int N, bool BWD>
+__global__ void __launch_bounds__(32, 1) boundaries_kernel(const double* __restrict__ maps, int n_chunks, LqrConst Cq,
+                                                           const double* __restrict__ abar, int T,
+                                                           double* __restrict__ bnd) {
+    extern __shared__ __align__(16) double mp[];  // [n_chunks][N][N+1]
+    __shared__ double w[N];
+    const int lane = threadIdx.x;
+    constexpr int NX = N * (N + 1);
+    for (int i = lane; i < n_chunks * NX; i += 32) cp_async8(mp + i, maps + i);
+    cp_async_commit();
+    if (lane < N) {
+        double acc = 0.0;
+        if constexpr (BWD) {
+#pragma unroll
+            for (int q = 0; q < N; ++q) acc = fma(-Cq.Q[lane * N + q], abar[(size_t)(T - 1) * N + q], acc);
+        }
+        w[lane] = acc;
+    }
+    cp_async_wait_all();
+    __syncwarp();
+    for (int k = 0; k < n_chunks; ++k) {
+        const int c = BWD ? n_chunks - 1 - k : k;
+        const double* m = mp + (size_t)c * NX;
+        double acc = 0.0;
+        if (lane < N) {
+            bnd[(size_t)c * N + lane] = w[lane];
+            acc = m[lane * (N + 1) + N];
+#pragma unroll
+            for (int q = 0; q < N; ++q) acc = fma(m[lane * (N + 1) + q], w[q], acc);
+        }
+        __syncwarp();
+        if (lane < N) w[lane] = acc;
+        __syncwarp();
+    }
+}
+
+// Fill the steps of one chunk from its boundary value.
+//   BWD: p_t = M_t' p_{t+1} + c_t and k_t = N_t p_{t+1}      -> k [T][MC]
+//   FWD: z_{t+1} = M_t z_t + e_t and v_t = -K_t z_t - k_t   -> v [T][MC], z [T+1][N]
+template <int N, int MC, bool BWD>
+__global__ void __launch_bounds__(32) fill_kernel(const double* __restrict__ Mg, const double* __restrict__ Wg,
+                                                  const double* __restrict__ force, const double* __restrict__ kin,
+                                                  const double* __restrict__ bnd, int T, int C,
+                                                  double* __restrict__ out_m, double* __restrict__ z_out) {
+    __shared__ __align__(16) double Ms[2][kSB][N * N];
+    __shared__ __align__(16) double Ws[2][kSB][MC * N];  // BWD: N_t, FWD: K_t
+    __shared__ __align__(16) double Fs[2][kSB][N];
+    __shared__ __align__(16) double Ks[2][kSB][MC];      // FWD: k_t
+    __shared__ double w[N], wn[N];
+    const int lane = threadIdx.x;
+    const int lo = blockIdx.x * C, hi = min(lo + C, T) - 1;
+    if (lane < N) {
+        w[lane] = bnd[(size_t)blockIdx.x * N + lane];
+        wn[lane] = -w[lane];
+        if (!BWD && z_out && blockIdx.x == 0) z_out[lane] = w[lane];
+    }
+    const bool isS = lane < N;                 // state lanes
+    const bool isO = lane >= N && lane < N + MC;  // output lanes (k or v)
+    const int ro = isO ? lane - N : 0;
+    const SubBlocks sb(lo, hi, BWD);
+    auto issue = [&](int b, int buf) {
+        stream_rows(&Ms[buf][0][0], Mg, sb.first(b), sb.count(b), N * N, lane);
+        stream_rows(&Ws[buf][0][0], Wg, sb.first(b), sb.count(b), MC * N, lane);
+        stream_rows(&Fs[buf][0][0], force, sb.first(b), sb.count(b), N, lane);
+        if (!BWD) stream_rows(&Ks[buf][0][0], kin, sb.first(b), sb.count(b), MC, lane);
+        cp_async_commit();
+    };
+    issue(0, 0);
+    __syncwarp();
+    for (int b = 0; b < sb.n; ++b) {
+        const int buf = b & 1;
+        if (b + 1 < sb.n) {
+            issue(b + 1, buf ^ 1);
+            cp_async_wait_all_but_one();
+        } else {
+            cp_async_wait_all();
+        }
+        __syncwarp();
+        const int t0 = sb.first(b), cntb = sb.count(b);
+        for (int jj = 0; jj < cntb; ++jj) {
+            const int j = BWD ? cntb - 1 - jj : jj;
             const int t = t0 + j;
-            // phase F1: v_t = -K_t z_t - k_t
-            if (lane < MC) {
-                double acc = -sm.k[buf][j][lane];
+            const double* Mt = Ms[buf][j];
+            const double* Wt = Ws[buf][j];
+            double acc = 0.0;
+            if (isS || isO) {
+                // uniform dot: state lanes use M (transposed when BWD) on w;
+                // output lanes use W (N_t or K_t) on w (BWD) or -w (FWD)
+                const double* X = isS ? Mt : Wt;
+                int xs, xo;
+                if (isS) {
+                    xs = BWD ? N : 1;
+                    xo = BWD ? lane : lane * N;
+                } else {
+                    xs = 1;
+                    xo = ro * N;
+                }
+                const double* wv = (isO && !BWD) ? wn : w;
+                acc = isS ? Fs[buf][j][lane] : (BWD ? 0.0 : -Ks[buf][j][ro]);
 #pragma unroll
-                for (int q = 0; q < N; ++q) acc = fma(-sm.K[buf][j][lane * N + q], sm.z[q], acc);
-                sm.v[lane] = acc;
-                v_out[(size_t)t * MC + lane] = acc;
+                for (int q = 0; q < N; ++q) acc = fma(X[q * xs + xo], wv[q], acc);
             }
             __syncwarp();
-            // phase F2: z_{t+1} = A z + B v (lanes 0..N-1); rollout with the
-            // updated control (lanes 8..8+N-1); control write-back (16..16+MC-1)
-            double out = 0.0;
-            if (lane < N) {
-                double acc = 0.0;
-#pragma unroll
-                for (int q = 0; q < N; ++q) acc = fma(sm.A[buf][j][lane * N + q], sm.z[q], acc);
-#pragma unroll
-                for (int q = 0; q < MC; ++q) acc = fma(sm.B[buf][j][lane * MC + q], sm.v[q], acc);
-                out = acc;
-            } else if (do_roll && lane >= 8 && lane < 8 + N) {
-                double un[MC], f[COV_MAX_N];
-#pragma unroll
-                for (int q = 0; q < MC; ++q) un[q] = fma(ro.eta, sm.v[q], sm.u[buf][j][q]);
-                dyn_f(ro.model, sm.s, un, f);
-                out = fma(ro.dt, f[lane - 8], sm.s[lane - 8]);
-            } else if (do_roll && lane >= 16 && lane < 16 + MC) {
-                ro.u[(size_t)t * MC + (lane - 16)] = fma(ro.eta, sm.v[lane - 16], sm.u[buf][j][lane - 16]);
-            }
-            __syncwarp();
-            if (lane < N) {
-                sm.z[lane] = out;
-                if (z_out) z_out[(size_t)(t + 1) * N + lane] = out;
-            } else if (do_roll && lane >= 8 && lane < 8 + N) {
-                sm.s[lane - 8] = out;
-                ro.s[(size_t)(t + 1) * N + (lane - 8)] = out;
+            if (isS) {
+                w[lane] = acc;
+                wn[lane] = -acc;
+                if (!BWD && z_out) z_out[(size_t)(t + 1) * N + lane] = acc;
+            } else if (isO) {
+                out_m[(size_t)t * MC + ro] = acc;
             }
             __syncwarp();
         }
         __syncwarp();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Control update and rollout (one CTA): u_t += eta v_t, then the Euler
+// rollout as prefix sums of the increments dt f(s_t, u_t):
+//   single integrator: p += dt u
+//   double integrator: vel += dt u, then p += dt vel
+//   unicycle: theta += dt omega, then x += dt v cos(theta), y += dt v sin(theta)
+// ---------------------------------------------------------------------------
+struct RolloutArgs {
+    int model;
+    double dt;
+    double eta;
+    double s0[COV_MAX_N];
+};
+
+// Inclusive prefix sum of a[0], a[st], ..., a[(L-1) st] in place (one CTA).
+__device__ void cta_inclusive_scan(double* a, int st, int L, double* sh) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+    const int S = (L + nt - 1) / nt;
+    const int b = min(tid * S, L), e = min(b + S, L);
+    double run = 0.0;
+    for (int i = b; i < e; ++i) {
+        run += a[(size_t)i * st];
+        a[(size_t)i * st] = run;
+    }
+    double x = run;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const double y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) sh[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        double v = lane < nw ? sh[lane] : 0.0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const double y = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += y;
+        }
+        sh[lane] = v;
+    }
+    __syncthreads();
+    const double off = (x - run) + (warp > 0 ? sh[warp - 1] : 0.0);
+    for (int i = b; i < e; ++i) a[(size_t)i * st] += off;
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(1024) update_rollout_kernel(RolloutArgs ro, double* __restrict__ u,
+                                                               const double* __restrict__ v, int T, int n, int m,
+                                                               double* __restrict__ s) {
+    __shared__ double sh[32];
+    const int tid = threadIdx.x, nt = blockDim.x;
+    if (v)
+        for (int i = tid; i < T * m; i += nt) u[i] = fma(ro.eta, v[i], u[i]);
+    for (int r = tid; r < n; r += nt) s[r] = ro.s0[r];
+    __syncthreads();
+    const double dt = ro.dt;
+    switch (ro.model) {
+        case COV_SINGLE_INT:
+            for (int i = tid; i < T * 2; i += nt) s[(size_t)(i / 2 + 1) * n + i % 2] = dt * u[i];
+            __syncthreads();
+            for (int r = 0; r < 2; ++r) cta_inclusive_scan(s + n + r, n, T, sh);
+            for (int i = tid; i < T * 2; i += nt) s[(size_t)(i / 2 + 1) * n + i % 2] += ro.s0[i % 2];
+            break;
+        case COV_DOUBLE_INT:
+            for (int i = tid; i < T * 2; i += nt) s[(size_t)(i / 2 + 1) * n + 2 + i % 2] = dt * u[i];
+            __syncthreads();
+            for (int r = 0; r < 2; ++r) cta_inclusive_scan(s + n + 2 + r, n, T, sh);
+            for (int i = tid; i < T * 2; i += nt) s[(size_t)(i / 2 + 1) * n + 2 + i % 2] += ro.s0[2 + i % 2];
+            __syncthreads();
+            // positions: increments dt vel_t (vel_t = state at time t)
+            for (int i = tid; i < T * 2; i += nt) {
+                const int t = i / 2, r = i % 2;
+                s[(size_t)(t + 1) * n + r] = dt * s[(size_t)t * n + 2 + r];
+            }
+            __syncthreads();
+            for (int r = 0; r < 2; ++r) cta_inclusive_scan(s + n + r, n, T, sh);
+            for (int i = tid; i < T * 2; i += nt) s[(size_t)(i / 2 + 1) * n + i % 2] += ro.s0[i % 2];
+            break;
+        default:  // unicycle
+            for (int t = tid; t < T; t += nt) s[(size_t)(t + 1) * n + 2] = dt * u[(size_t)t * m + 1];
+            __syncthreads();
+            cta_inclusive_scan(s + n + 2, n, T, sh);
+            for (int t = tid; t < T; t += nt) s[(size_t)(t + 1) * n + 2] += ro.s0[2];
+            __syncthreads();
+            for (int t = tid; t < T; t += nt) {
+                double sn, cs;
+                sincos(s[(size_t)t * n + 2], &sn, &cs);
+                const double sp = dt * u[(size_t)t * m];
+                s[(size_t)(t + 1) * n + 0] = sp * cs;
+                s[(size_t)(t + 1) * n + 1] = sp * sn;
+            }
+            __syncthreads();
+            for (int r = 0; r < 2; ++r) cta_inclusive_scan(s + n + r, n, T, sh);
+            for (int i = tid; i < T * 2; i += nt) s[(size_t)(i / 2 + 1) * n + i % 2] += ro.s0[i % 2];
     }
 }
 
@@ -385,22 +559,6 @@ __global__ void linearize_kernel(int model, const double* __restrict__ s, const 
     }
 }
 
-__global__ void rollout_kernel(int model, RolloutArgs ro, const double* __restrict__ u, int T, int n, int m) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    double s[COV_MAX_N], f[COV_MAX_N];
-    for (int r = 0; r < n; ++r) {
-        s[r] = ro.s0[r];
-        ro.s[r] = s[r];
-    }
-    for (int t = 0; t < T; ++t) {
-        dyn_f(model, s, u + (size_t)t * m, f);
-        for (int r = 0; r < n; ++r) {
-            s[r] = fma(ro.dt, f[r], s[r]);
-            ro.s[(size_t)(t + 1) * n + r] = s[r];
-        }
-    }
-}
-
 int model_dims(int model, int* n, int* m) {
     switch (model) {
         case COV_SINGLE_INT: *n = 2; *m = 2; return 0;
@@ -410,32 +568,47 @@ int model_dims(int model, int* n, int* m) {
     return -1;
 }
 
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+struct ScanPlan {
+    int C, n_chunks;
+};
+
+static bool scan_plan(int T, ScanPlan* p) {
+    int C = (int)ceil(sqrt(T / 2.0));
+    C = std::max(1, std::min(C, kMaxChunk));
+    int nc = (T + C - 1) / C;
+    if (nc > kMaxChunks) {
+        C = (T + kMaxChunks - 1) / kMaxChunks;
+        nc = (T + C - 1) / C;
+    }
+    if (C > kMaxChunk) return false;
+    *p = ScanPlan{C, nc};
+    return true;
+}
+
+size_t lqr_gain_doubles(int T, int n, int m) { return (size_t)T * (2 * (size_t)m * n + (size_t)n * n); }
+
+struct AffineBufs {
+    double *fc, *fe, *k, *maps, *bnd;
+};
+
+static AffineBufs carve_affine(Carver& cv, int T, int n, int m) {
+    AffineBufs b{};
+    b.fc = cv.take<double>((size_t)T * n);
+    b.fe = cv.take<double>((size_t)T * n);
+    b.k = cv.take<double>((size_t)T * m);
+    b.maps = cv.take<double>((size_t)kMaxChunks * n * (n + 1));
+    b.bnd = cv.take<double>((size_t)kMaxChunks * n);
+    return b;
+}
+
 size_t lqr_ws_bytes(int T, int n, int m) {
     Carver cv(nullptr);
-    cv.take<double>((size_t)T * m * n);
-    cv.take<double>((size_t)T * m);
+    cv.take<double>(lqr_gain_doubles(T, n, m));
+    carve_affine(cv, T, n, m);
     return round_up(cv.off, 256);
-}
-
-template <int N, int MC>
-static void launch_lqr_t(const double* A, const double* B, const LqrConst& C, const double* abar, int T, double* Kg,
-                         double* kg, double* v, double* z, const RolloutArgs& ro, unsigned* st, cudaStream_t s) {
-    lqr_kernel<N, MC><<<1, 32, 0, s>>>(A, B, C, abar, T, Kg, kg, v, z, ro, st);
-}
-
-static cov_status launch_lqr(int n, int m, const double* A, const double* B, const LqrConst& C, const double* abar,
-                             int T, double* Kg, double* kg, double* v, double* z, const RolloutArgs& ro,
-                             unsigned* st, cudaStream_t s) {
-#define COV_LQR_CASE(NN, MM)                                               \
-    if (n == NN && m == MM) {                                              \
-        launch_lqr_t<NN, MM>(A, B, C, abar, T, Kg, kg, v, z, ro, st, s);  \
-        return COV_OK;                                                     \
-    }
-    COV_LQR_CASE(1, 1) COV_LQR_CASE(2, 1) COV_LQR_CASE(3, 1) COV_LQR_CASE(4, 1)
-    COV_LQR_CASE(1, 2) COV_LQR_CASE(2, 2) COV_LQR_CASE(3, 2) COV_LQR_CASE(4, 2)
-    COV_LQR_CASE(1, 3) COV_LQR_CASE(2, 3) COV_LQR_CASE(3, 3) COV_LQR_CASE(4, 3)
-#undef COV_LQR_CASE
-    return COV_ERR_UNSUPPORTED;
 }
 
 static bool make_lqr_const(const double* Q, const double* R, int n, int m, LqrConst* C) {
@@ -452,6 +625,84 @@ static bool make_lqr_const(const double* Q, const double* R, int n, int m, LqrCo
     return true;
 }
 
+template <int N, int MC>
+static void launch_riccati_t(const double* A, const double* B, const LqrConst& C, int T, double* gains, unsigned* st,
+                             cudaStream_t s) {
+    double* K = gains;
+    double* M = gains + (size_t)T * MC * N;
+    double* Nt = M + (size_t)T * N * N;
+    riccati_kernel<N, MC><<<1, 32, 0, s>>>(A, B, C, T, K, M, Nt, st);
+}
+
+template <int N, int MC>
+static void launch_affine_t(const double* B, const double* gains, const LqrConst& C, const double* abar, int T,
+                            const ScanPlan& pl, const AffineBufs& ab, double* v, double* z, cudaStream_t s) {
+    const double* K = gains;
+    const double* M = gains + (size_t)T * MC * N;
+    const double* Nt = M + (size_t)T * N * N;
+    const size_t fsb = sizeof(double) * pl.C * N;
+    const size_t mpb = sizeof(double) * pl.n_chunks * N * (N + 1);
+    compose_kernel<N, MC, true><<<pl.n_chunks, 32, fsb, s>>>(M, C, abar, nullptr, nullptr, T, pl.C, ab.fc, ab.maps);
+    boundaries_kernel<N, true><<<1, 32, mpb, s>>>(ab.maps, pl.n_chunks, C, abar, T, ab.bnd);
+    fill_kernel<N, MC, true><<<pl.n_chunks, 32, 0, s>>>(M, Nt, ab.fc, nullptr, ab.bnd, T, pl.C, ab.k, nullptr);
+    compose_kernel<N, MC, false><<<pl.n_chunks, 32, fsb, s>>>(M, C, nullptr, B, ab.k, T, pl.C, ab.fe, ab.maps);
+    boundaries_kernel<N, false><<<1, 32, mpb, s>>>(ab.maps, pl.n_chunks, C, nullptr, T, ab.bnd);
+    fill_kernel<N, MC, false><<<pl.n_chunks, 32, 0, s>>>(M, K, ab.fe, ab.k, ab.bnd, T, pl.C, v, z);
+}
+
+template <int N, int MC>
+static void set_attrs_t() {
+    const int big = (int)(sizeof(double) * kMaxChunks * N * (N + 1));
+    cudaFuncSetAttribute(boundaries_kernel<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    cudaFuncSetAttribute(boundaries_kernel<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+}
+
+#define COV_LQR_DISPATCH(MACRO) \
+    MACRO(1, 1) MACRO(2, 1) MACRO(3, 1) MACRO(4, 1) MACRO(1, 2) MACRO(2, 2) MACRO(3, 2) MACRO(4, 2) \
+    MACRO(1, 3) MACRO(2, 3) MACRO(3, 3) MACRO(4, 3)
+
+void lqr_set_attributes() {
+#define COV_ATTR_CASE(NN, MM) set_attrs_t<NN, MM>();
+    COV_LQR_DISPATCH(COV_ATTR_CASE)
+#undef COV_ATTR_CASE
+    cudaGetLastError();
+}
+
+cov_status lqr_riccati(cov_ctx* ctx, int n, int m, const double* A, const double* B, const double* Q,
+                       const double* R, int T, double* gains, cudaStream_t stream) {
+    LqrConst C;
+    if (!make_lqr_const(Q, R, n, m, &C)) return COV_ERR_INVALID_ARG;
+#define COV_RIC_CASE(NN, MM)                                                  \
+    if (n == NN && m == MM) {                                                 \
+        launch_riccati_t<NN, MM>(A, B, C, T, gains, ctx->status, stream);     \
+        return cuda_failed(ctx, cudaGetLastError()) ? COV_ERR_CUDA : COV_OK; \
+    }
+    COV_LQR_DISPATCH(COV_RIC_CASE)
+#undef COV_RIC_CASE
+    return COV_ERR_UNSUPPORTED;
+}
+
+cov_status lqr_affine(cov_ctx* ctx, void* ws, size_t ws_bytes, int n, int m, const double* B, const double* gains,
+                      const double* Q, const double* abar, int T, double* v_out, double* z_out,
+                      cudaStream_t stream) {
+    LqrConst C;
+    const double R1[COV_MAX_M * COV_MAX_M] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+    if (!make_lqr_const(Q, R1, n, m, &C)) return COV_ERR_INVALID_ARG;
+    ScanPlan pl;
+    if (!scan_plan(T, &pl)) return COV_ERR_UNSUPPORTED;
+    Carver cv(ws);
+    const AffineBufs ab = carve_affine(cv, T, n, m);
+    if (!ws || cv.off > ws_bytes) return COV_ERR_WORKSPACE;
+#define COV_AFF_CASE(NN, MM)                                                          \
+    if (n == NN && m == MM) {                                                         \
+        launch_affine_t<NN, MM>(B, gains, C, abar, T, pl, ab, v_out, z_out, stream);  \
+        return cuda_failed(ctx, cudaGetLastError()) ? COV_ERR_CUDA : COV_OK;         \
+    }
+    COV_LQR_DISPATCH(COV_AFF_CASE)
+#undef COV_AFF_CASE
+    return COV_ERR_UNSUPPORTED;
+}
+
 cov_status lqr_track_ws(cov_ctx* ctx, void* ws, size_t ws_bytes, const double* A, const double* B, const double* Q,
                         const double* R, const double* abar, int T, int n, int m, double* v_out, double* z_out,
                         cudaStream_t stream) {
@@ -459,41 +710,29 @@ cov_status lqr_track_ws(cov_ctx* ctx, void* ws, size_t ws_bytes, const double* A
         return COV_ERR_INVALID_ARG;
     LqrConst C;
     if (!make_lqr_const(Q, R, n, m, &C)) return COV_ERR_INVALID_ARG;
+    ScanPlan pl;
+    if (!scan_plan(T, &pl)) return COV_ERR_UNSUPPORTED;
     Carver cv(ws);
-    double* Kg = cv.take<double>((size_t)T * m * n);
-    double* kg = cv.take<double>((size_t)T * m);
-    if (!ws || cv.off > ws_bytes) return COV_ERR_WORKSPACE;
-    RolloutArgs ro{};
-    ro.model = -1;
-    const cov_status s = launch_lqr(n, m, A, B, C, abar, T, Kg, kg, v_out, z_out, ro, ctx->status, stream);
+    double* gains = cv.take<double>(lqr_gain_doubles(T, n, m));
+    const size_t used = round_up(cv.off, 256);
+    if (!ws || used > ws_bytes) return COV_ERR_WORKSPACE;
+    cov_status s = lqr_riccati(ctx, n, m, A, B, Q, R, T, gains, stream);
     if (s != COV_OK) return s;
-    if (cuda_failed(ctx, cudaGetLastError())) return COV_ERR_CUDA;
-    return COV_OK;
+    return lqr_affine(ctx, static_cast<char*>(ws) + used, ws_bytes - used, n, m, B, gains, Q, abar, T, v_out, z_out,
+                      stream);
 }
 
-// Fused LQR + control update + rollout used by cov_solve.
-cov_status lqr_update_rollout(cov_ctx* ctx, void* ws, size_t ws_bytes, int model, const double* A, const double* B,
-                              const double* Q, const double* R, const double* abar, int T, double dt, double eta,
-                              const double* s0, double* u, double* s, double* v, cudaStream_t stream) {
+cov_status update_rollout(cov_ctx* ctx, int model, const double* s0, double* u, const double* v, double eta, int T,
+                          double dt, double* s, cudaStream_t stream) {
     int n, m;
     if (model_dims(model, &n, &m) != 0) return COV_ERR_INVALID_ARG;
-    LqrConst C;
-    if (!make_lqr_const(Q, R, n, m, &C)) return COV_ERR_INVALID_ARG;
-    Carver cv(ws);
-    double* Kg = cv.take<double>((size_t)T * m * n);
-    double* kg = cv.take<double>((size_t)T * m);
-    if (!ws || cv.off > ws_bytes) return COV_ERR_WORKSPACE;
     RolloutArgs ro{};
     ro.model = model;
     ro.dt = dt;
     ro.eta = eta;
     for (int r = 0; r < n; ++r) ro.s0[r] = s0[r];
-    ro.u = u;
-    ro.s = s;
-    const cov_status st = launch_lqr(n, m, A, B, C, abar, T, Kg, kg, v, nullptr, ro, ctx->status, stream);
-    if (st != COV_OK) return st;
-    if (cuda_failed(ctx, cudaGetLastError())) return COV_ERR_CUDA;
-    return COV_OK;
+    update_rollout_kernel<<<1, 1024, 0, stream>>>(ro, u, v, T, n, m, s);
+    return cuda_failed(ctx, cudaGetLastError()) ? COV_ERR_CUDA : COV_OK;
 }
 
 cov_status linearize_launch(cov_ctx* ctx, int model, const double* s, const double* u, int T, double dt, double* A,
@@ -521,15 +760,10 @@ extern "C" cov_status cov_rollout(cov_ctx* ctx, int model, const double* s0, con
     int n, m;
     if (!ctx || !s0 || !u || !s || T < 1 || !isfinite(dt) || cov::model_dims(model, &n, &m) != 0)
         return COV_ERR_INVALID_ARG;
+    for (int r = 0; r < n; ++r)
+        if (!isfinite(s0[r])) return COV_ERR_INVALID_ARG;
     if (cudaSetDevice(ctx->device) != cudaSuccess) return COV_ERR_CUDA;
-    cov::RolloutArgs ro{};
-    ro.model = model;
-    ro.dt = dt;
-    for (int r = 0; r < n; ++r) ro.s0[r] = s0[r];
-    ro.s = s;
-    cov::rollout_kernel<<<1, 32, 0, (cudaStream_t)stream>>>(model, ro, u, T, n, m);
-    if (cov::cuda_failed(ctx, cudaGetLastError())) return COV_ERR_CUDA;
-    return COV_OK;
+    return cov::update_rollout(ctx, model, s0, const_cast<double*>(u), nullptr, 0.0, T, dt, s, (cudaStream_t)stream);
 }
 
 extern "C" cov_status cov_lqr_track(cov_ctx* ctx, const double* A, const double* B, const double* Q,

@@ -13,15 +13,23 @@
 namespace cov {
 
 int model_dims(int model, int* n, int* m);
-cov_status lqr_update_rollout(cov_ctx* ctx, void* ws, size_t ws_bytes, int model, const double* A, const double* B,
-                              const double* Q, const double* R, const double* abar, int T, double dt, double eta,
-                              const double* s0, double* u, double* s, double* v, cudaStream_t stream);
+size_t lqr_gain_doubles(int T, int n, int m);
+cov_status lqr_riccati(cov_ctx* ctx, int n, int m, const double* A, const double* B, const double* Q,
+                       const double* R, int T, double* gains, cudaStream_t stream);
+cov_status lqr_affine(cov_ctx* ctx, void* ws, size_t ws_bytes, int n, int m, const double* B, const double* gains,
+                      const double* Q, const double* abar, int T, double* v_out, double* z_out, cudaStream_t stream);
+cov_status update_rollout(cov_ctx* ctx, int model, const double* s0, double* u, const double* v, double eta, int T,
+                          double dt, double* s, cudaStream_t stream);
 cov_status linearize_launch(cov_ctx* ctx, int model, const double* s, const double* u, int T, double dt, double* A,
                             double* B, cudaStream_t stream);
 
+// Time-invariant models: A_t, B_t do not depend on the trajectory, so the
+// Riccati gains are the same in every outer iteration.
+static bool model_is_lti(int model) { return model == COV_SINGLE_INT || model == COV_DOUBLE_INT; }
+
 struct SolveBufs {
     float *x, *a;
-    double *abar, *A, *B, *v;
+    double *abar, *A, *B, *v, *gains;
 };
 
 static SolveBufs carve_solve(Carver& cv, int T, int d, int n, int m) {
@@ -32,6 +40,7 @@ static SolveBufs carve_solve(Carver& cv, int T, int d, int n, int m) {
     b.A = cv.take<double>((size_t)T * n * n);
     b.B = cv.take<double>((size_t)T * n * m);
     b.v = cv.take<double>((size_t)T * m);
+    b.gains = cv.take<double>(lqr_gain_doubles(T, n, m));
     return b;
 }
 
@@ -45,6 +54,7 @@ void drop_solve_graph(cov_ctx* ctx) {
     if (ctx->solve_graph.exec) cudaGraphExecDestroy(ctx->solve_graph.exec);
     if (ctx->solve_graph.graph) cudaGraphDestroy(ctx->solve_graph.graph);
     ctx->solve_graph = cov_graph_cache{};
+    ctx->gains_key = 0;
 }
 
 // x_i = first d components of s_{i+1} (FP32 coverage coordinates).
@@ -98,10 +108,15 @@ static cov_status enqueue_iteration(cov_ctx* ctx, const cov_problem* P, int n, i
         r = svgd_field_ws(ctx, rest, rest_bytes, b.x, d, T, d, nullptr, &P->gmm, P->h, b.a, st);
     if (r != COV_OK) return r;
     lift_kernel<<<nb, 256, 0, st>>>(b.a, T, n, d, b.abar);
-    r = linearize_launch(ctx, P->model, s, u, T, P->dt, b.A, b.B, st);
+    if (!model_is_lti(P->model)) {
+        r = linearize_launch(ctx, P->model, s, u, T, P->dt, b.A, b.B, st);
+        if (r != COV_OK) return r;
+        r = lqr_riccati(ctx, n, m, b.A, b.B, P->Q, P->R, T, b.gains, st);
+        if (r != COV_OK) return r;
+    }
+    r = lqr_affine(ctx, rest, rest_bytes, n, m, b.B, b.gains, P->Q, b.abar, T, b.v, nullptr, st);
     if (r != COV_OK) return r;
-    r = lqr_update_rollout(ctx, rest, rest_bytes, P->model, b.A, b.B, P->Q, P->R, b.abar, T, P->dt, P->eta, P->s0,
-                           u, s, b.v, st);
+    r = update_rollout(ctx, P->model, P->s0, u, b.v, P->eta, T, P->dt, s, st);
     if (r != COV_OK) return r;
     if (cuda_failed(ctx, cudaGetLastError())) return COV_ERR_CUDA;
     return COV_OK;
@@ -146,6 +161,27 @@ static cov_status cov::solve_impl(cov_ctx* ctx, const cov_problem* prob, int n_o
         if (r != COV_OK) return r;
     }
     if (n_outer == 0) return COV_OK;
+
+    if (model_is_lti(prob->model)) {
+        // gains of a time-invariant model: computed once per (model, T, dt,
+        // Q, R, workspace) and reused by every later outer iteration
+        uint64_t gk = 88172645463325252ull;
+        gk = fnv(&prob->model, sizeof(int), gk);
+        gk = fnv(&prob->T, sizeof(int), gk);
+        gk = fnv(&prob->dt, sizeof(double), gk);
+        gk = fnv(prob->Q, sizeof(prob->Q), gk);
+        gk = fnv(prob->R, sizeof(prob->R), gk);
+        const void* wsp = ctx->ws;
+        gk = fnv(&wsp, sizeof(wsp), gk);
+        if (gk == 0) gk = 1;
+        if (ctx->gains_key != gk) {
+            r = linearize_launch(ctx, prob->model, s_out, u, prob->T, prob->dt, b.A, b.B, st);
+            if (r != COV_OK) return r;
+            r = lqr_riccati(ctx, n, m, b.A, b.B, prob->Q, prob->R, prob->T, b.gains, st);
+            if (r != COV_OK) return r;
+            ctx->gains_key = gk;
+        }
+    }
 
     if (!ctx->use_graph) {
         for (int k = 0; k < n_outer; ++k) {

@@ -35,10 +35,16 @@ def _dense_kkt(A, B, Q, R, abar):
     return v.reshape(T, m), z
 
 
-@pytest.mark.parametrize("T,n,m", [(1, 2, 2), (7, 3, 2), (40, 4, 2), (25, 4, 3)])
-def test_lqr_matches_dense_kkt(orc, T, n, m):
+@pytest.mark.parametrize("T,n,m,stable", [(1, 2, 2, False), (7, 3, 2, False), (40, 4, 2, False),
+                                          (25, 4, 3, False), (600, 4, 2, True)])
+def test_lqr_matches_dense_kkt(orc, T, n, m, stable):
+    """Also at a long horizon (T = 600, A_t = 0.97 x random orthogonal), where
+    a Riccati recursion that lets P lose symmetry drifts away."""
     g = wl.rng(100 + T)
-    A = np.eye(n) + 0.1 * g.standard_normal((T, n, n))
+    if stable:
+        A = np.stack([0.97 * np.linalg.qr(g.standard_normal((n, n)))[0] for _ in range(T)])
+    else:
+        A = np.eye(n) + 0.1 * g.standard_normal((T, n, n))
     B = 0.3 * g.standard_normal((T, n, m))
     L = g.standard_normal((n, n))
     Q = L @ L.T / n + 0.1 * np.eye(n)
