@@ -12,7 +12,9 @@
 // 1/sqrt(eps ln 2),
 //     w_ij = h_j + 2 xhat_i . yhat_j             (packed f32x2 FMA)
 // and fold it into an online max-subtracted log-sum-exp (running maximum
-// updated once per 8 columns with a 3-input max, 2^(w - m) on MUFU.EX2).
+// updated once per 8 columns with 3-input max instructions, the running sum
+// rescaled by 2^(m_old - m_new) under a warp-uniform vote, 2^(w - m) on
+// MUFU.EX2).
 // The |xhat_i|^2 row term is constant along a row and is folded back into
 // the potentials by the epilogue, so the Sinkhorn iteration runs entirely on
 // the per-column terms h:
@@ -53,6 +55,9 @@ struct PairArgs {
     float* part;         // [NACC][splits][part_ld]
     int part_ld;         // n_rb * rows per CTA
     unsigned* counters;  // [n_rb]
+    int n_rb;            // row blocks of this segment
+    int emode;           // log-sum-exp epilogue: M_G, M_F or M_P
+    int pre_ok;          // rows and column coordinates were written before the previous launch
     float* out_h;
     const float* in_h;
     float log2a;
@@ -95,7 +100,7 @@ __device__ __forceinline__ void tile_compute(const float* __restrict__ st, int j
             c[k][4] = v1.x; c[k][5] = v1.y; c[k][6] = v1.z; c[k][7] = v1.w;
         }
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
+        for (int r = 0; r < (TR::kSV ? R : 0); ++r) {
             if constexpr (TR::kSV) {
                 // k_ij = 2^{-|xt_i - xt_j|^2};  acc += k (st_j - (xt_j - xt_i))
                 float2 d2[4];
@@ -119,33 +124,50 @@ __device__ __forceinline__ void tile_compute(const float* __restrict__ st, int j
                         ra[r].acc[k] = fma2(e, sub2(make_float2(c[D + k][2 * q], c[D + k][2 * q + 1]), dx[k][q]),
                                             ra[r].acc[k]);
                 }
-            } else {
-                float2 w[4];
+            }
+        }
+        if constexpr (!TR::kSV) {
+            // exponents of this chunk for all R rows, and each row's new running max
+            float2 w[R][4];
+            float mn[R];
+            bool grew = false;
 #pragma unroll
-                for (int q = 0; q < 4; ++q) w[q] = make_float2(c[D][2 * q], c[D][2 * q + 1]);
+            for (int r = 0; r < R; ++r) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) w[r][q] = make_float2(c[D][2 * q], c[D][2 * q + 1]);
 #pragma unroll
                 for (int k = 0; k < D; ++k) {
                     const float2 xk = make_float2(X[r][k], X[r][k]);
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) w[q] = fma2(xk, make_float2(c[k][2 * q], c[k][2 * q + 1]), w[q]);
+                    for (int q = 0; q < 4; ++q) w[r][q] = fma2(xk, make_float2(c[k][2 * q], c[k][2 * q + 1]), w[r][q]);
                 }
-                const float cm = max3f(max3f(w[0].x, w[0].y, w[1].x), max3f(w[1].y, w[2].x, w[2].y),
-                                       fmaxf(w[3].x, w[3].y));
-                if (cm > ra[r].m) {
-                    const float sc = ex2(ra[r].m - cm);
+                mn[r] = max3f(max3f(ra[r].m, w[r][0].x, w[r][0].y), max3f(w[r][1].x, w[r][1].y, w[r][2].x),
+                              max3f(w[r][2].y, w[r][3].x, w[r][3].y));
+                grew |= mn[r] > ra[r].m;
+            }
+            // rescale what was accumulated by 2^(m_old - m_new) only when some
+            // row of the warp raised its maximum (rare after the first tiles);
+            // the vote keeps the branch uniform across the warp
+            if (__any_sync(0xffffffffu, grew)) {
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const float sc = ex2(ra[r].m - mn[r]);
                     const float2 sc2 = make_float2(sc, sc);
                     ra[r].s = mul2(ra[r].s, sc2);
                     if constexpr (TR::kW) {
 #pragma unroll
                         for (int k = 0; k < D; ++k) ra[r].acc[k] = mul2(ra[r].acc[k], sc2);
                     }
-                    ra[r].m = cm;
+                    ra[r].m = mn[r];
                 }
+            }
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
                 const float2 mm = make_float2(ra[r].m, ra[r].m);
                 float2 e[4];
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    const float2 dd = sub2(w[q], mm);
+                    const float2 dd = sub2(w[r][q], mm);
                     e[q] = make_float2(ex2(dd.x), ex2(dd.y));
                 }
                 ra[r].s = add2(ra[r].s, add2(add2(e[0], e[1]), add2(e[2], e[3])));
@@ -214,8 +236,8 @@ __device__ __forceinline__ void epilogue(const PairArgs& a, int i, float m, floa
     } else {
         const float L = m + log2f(s);
         float v;
-        if constexpr (MODE == M_G) v = a.in_h[i] - L;
-        else if constexpr (MODE == M_F) v = a.log2a - L;
+        if (a.emode == M_G) v = a.in_h[i] - L;
+        else if (a.emode == M_F) v = a.log2a - L;
         else v = 0.5f * (a.log2a + a.in_h[i] - L);
         ok &= finitef(v);
         a.out_h[i] = v;
@@ -223,8 +245,21 @@ __device__ __forceinline__ void epilogue(const PairArgs& a, int i, float m, floa
     if (!ok) raise_status(a.status, kDevNonfinite);
 }
 
+// One launch covers up to two independent passes ("segments", e.g. the
+// g-update and the self p-update of the same Sinkhorn iteration): CTAs
+// [0, ctas0) belong to seg[0], the rest to seg[1].
+struct PairLaunch {
+    PairArgs seg[2];
+    int ctas0;
+};
+
+// Programmatic dependent launch: wait for the previous grid's results, and
+// let the next grid start its prologue while this one runs.
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_dep_launch() { asm volatile("griddepcontrol.launch_dependents;" :::); }
+
 template <int D, int R, int MODE>
-__global__ void __launch_bounds__(kThreads) pairs_kernel(const PairArgs a) {
+__global__ void __launch_bounds__(kThreads) pairs_kernel(const __grid_constant__ PairLaunch L) {
     using TR = PairTraits<D, MODE>;
     constexpr int NC = TR::NC;
     constexpr int NACC = TR::NACC;
@@ -235,8 +270,18 @@ __global__ void __launch_bounds__(kThreads) pairs_kernel(const PairArgs a) {
     __shared__ int s_last;
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int rb = blockIdx.x, sp = blockIdx.y;
+    const int segi = ((int)blockIdx.x >= L.ctas0) ? 1 : 0;
+    const PairArgs a = segi ? L.seg[1] : L.seg[0];
+    const int lb = (int)blockIdx.x - (segi ? L.ctas0 : 0);
+    const int rb = lb / a.splits, sp = lb % a.splits;
     const int row0 = rb * RB;
+
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (!a.pre_ok) grid_dep_wait();
 
     float X[R][D], Xr[R][D];
 #pragma unroll
@@ -259,21 +304,22 @@ __global__ void __launch_bounds__(kThreads) pairs_kernel(const PairArgs a) {
     const int c0 = sp * a.cols_per_split;
     const int c1 = min(c0 + a.cols_per_split, a.n_cols8);
     const int n_tiles = c1 > c0 ? (c1 - c0 + kTile - 1) / kTile : 0;
-
-    if (threadIdx.x == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
     __syncthreads();
 
-    auto issue = [&](int t, int stg) {
+    // A tile is the column coordinates (constant over the Sinkhorn loop) and
+    // the per-column term h (written by the previous launch).
+    auto issue_coords = [&](int t, int stg) {
         const int tc = c0 + t * kTile;
         const int nc = min(kTile, c1 - tc);
         const unsigned bytes = (unsigned)nc * 4u;
         mbar_arrive_expect_tx(&bar[stg], bytes * NC);
 #pragma unroll
         for (int k = 0; k < D; ++k) bulk_g2s(&sm[stg][k * kTile], a.cols + (size_t)k * a.col_ld + tc, bytes, &bar[stg]);
+    };
+    auto issue_h = [&](int t, int stg) {
+        const int tc = c0 + t * kTile;
+        const int nc = min(kTile, c1 - tc);
+        const unsigned bytes = (unsigned)nc * 4u;
         if constexpr (TR::kSV) {
 #pragma unroll
             for (int k = 0; k < D; ++k)
@@ -282,8 +328,15 @@ __global__ void __launch_bounds__(kThreads) pairs_kernel(const PairArgs a) {
             bulk_g2s(&sm[stg][D * kTile], a.colh + tc, bytes, &bar[stg]);
         }
     };
+    auto issue = [&](int t, int stg) {
+        issue_coords(t, stg);
+        issue_h(t, stg);
+    };
 
-    if (threadIdx.x == 0 && n_tiles > 0) issue(0, 0);
+    if (threadIdx.x == 0 && n_tiles > 0) issue_coords(0, 0);
+    if (a.pre_ok) grid_dep_wait();
+    grid_dep_launch();
+    if (threadIdx.x == 0 && n_tiles > 0) issue_h(0, 0);
     int bad_tile = -1;
     for (int t = 0; t < n_tiles; ++t) {
         const int stg = t & 1;
@@ -561,63 +614,103 @@ __global__ void sk_finish_kernel(int T, int M, float epsln2, float log2a, SkBufs
 }
 
 // ---------------------------------------------------------------------------
-// Launch dispatch
+// Launch dispatch.  Kernel families: M_G (log-sum-exp updates; the epilogue
+// g/f/p is chosen per segment at run time), M_WY, M_WX, M_SVGD.  Launches use
+// programmatic stream serialisation (PDL), so a launch's prologue overlaps
+// the tail of the previous one; every kernel waits (griddepcontrol.wait)
+// before it reads the previous launch's results or writes scratch.
 // ---------------------------------------------------------------------------
 template <int D, int R, int MODE>
-static void launch_pairs_t(const PairArgs& a, dim3 grid, cudaStream_t st) {
-    pairs_kernel<D, R, MODE><<<grid, kThreads, 0, st>>>(a);
+static cudaError_t launch_pairs_t(const PairLaunch& L, int n_ctas, cudaStream_t st) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)n_ctas);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, pairs_kernel<D, R, MODE>, L);
 }
 
 template <int D, int R>
-static void launch_pairs_mode(int mode, const PairArgs& a, dim3 grid, cudaStream_t st) {
-    switch (mode) {
-        case M_G: launch_pairs_t<D, R, M_G>(a, grid, st); break;
-        case M_F: launch_pairs_t<D, R, M_F>(a, grid, st); break;
-        case M_P: launch_pairs_t<D, R, M_P>(a, grid, st); break;
-        case M_WY: launch_pairs_t<D, R, M_WY>(a, grid, st); break;
-        case M_WX: launch_pairs_t<D, R, M_WX>(a, grid, st); break;
-        case M_SVGD: launch_pairs_t<D, R, M_SVGD>(a, grid, st); break;
+static cudaError_t launch_pairs_mode(int family, const PairLaunch& L, int n, cudaStream_t st) {
+    switch (family) {
+        case M_G: return launch_pairs_t<D, R, M_G>(L, n, st);
+        case M_WY: return launch_pairs_t<D, R, M_WY>(L, n, st);
+        case M_WX: return launch_pairs_t<D, R, M_WX>(L, n, st);
+        case M_SVGD: return launch_pairs_t<D, R, M_SVGD>(L, n, st);
     }
+    return cudaErrorInvalidValue;
 }
 
 template <int D>
-static void launch_pairs_r(int R, int mode, const PairArgs& a, dim3 grid, cudaStream_t st) {
+static cudaError_t launch_pairs_r(int R, int family, const PairLaunch& L, int n, cudaStream_t st) {
     if constexpr (D == 2) {
-        if (R == 2) return launch_pairs_mode<D, 2>(mode, a, grid, st);
-        if (R == 8) return launch_pairs_mode<D, 8>(mode, a, grid, st);
+        if (R == 2) return launch_pairs_mode<D, 2>(family, L, n, st);
+        if (R == 8) return launch_pairs_mode<D, 8>(family, L, n, st);
     }
-    launch_pairs_mode<D, 4>(mode, a, grid, st);
+    return launch_pairs_mode<D, 4>(family, L, n, st);
 }
 
 static int effective_R(int d, int R) { return (d == 2 && (R == 2 || R == 8)) ? R : 4; }
 
-
 constexpr int kMaxSlots = 1536;           // CTA slots assumed by the workspace bound
-constexpr size_t kPartRows = (size_t)2 * kMaxSlots * 256;
+constexpr size_t kPartRows = (size_t)2 * kMaxSlots * 256 + 256;
 
 static int cnt_ld_for(int Tp, int Mp) { return std::max(Tp, Mp) / 64 + 1; }
 
-// Plans and launches one all-pairs pass of `mode` over n_rows x n_cols.
-static void run_pairs(cov_ctx* ctx, int d, int mode, PairArgs a, int n_cols, unsigned* counters,
-                      cudaStream_t st) {
-    const int R = effective_R(d, ctx->rows_per_thread);
-    const int RB = 32 * R;
-    const int slots = std::max(1, std::min(ctx->num_sms * ctx->ctas_per_sm, kMaxSlots));
+static void plan_segment(PairArgs& a, int n_cols, int RB, int slots, unsigned* counters) {
     const SplitPlan pl = plan_splits(a.n_rows, n_cols, RB, slots);
     a.n_cols8 = (int)round_up((size_t)n_cols, 8);
     a.cols_per_split = pl.cols_per_split;
     a.splits = pl.splits;
+    a.n_rb = pl.n_rb;
     a.part_ld = pl.n_rb * RB;
     a.counters = counters;
-    const dim3 grid(pl.n_rb, pl.splits);
-    switch (d) {
-        case 1: launch_pairs_r<1>(R, mode, a, grid, st); break;
-        case 2: launch_pairs_r<2>(R, mode, a, grid, st); break;
-        case 3: launch_pairs_r<3>(R, mode, a, grid, st); break;
-        case 4: launch_pairs_r<4>(R, mode, a, grid, st); break;
-        case 5: launch_pairs_r<5>(R, mode, a, grid, st); break;
-        case 6: launch_pairs_r<6>(R, mode, a, grid, st); break;
+}
+
+// Plans and launches one or two all-pairs passes of one kernel family in a
+// single grid.  seg[k] covers seg[k].n_rows rows x n_cols[k] columns; with
+// two segments the CTA slots are shared in proportion to their pair counts
+// and seg[1]'s partials follow seg[0]'s in the partial buffer.
+static cov_status run_pairs(cov_ctx* ctx, int d, int family, PairArgs* seg, const int* n_cols, int nseg,
+                            const int* cnt_off, unsigned* counters, cudaStream_t st) {
+    const int R = effective_R(d, ctx->rows_per_thread);
+    const int RB = 32 * R;
+    const int slots = std::max(1, std::min(ctx->num_sms * ctx->ctas_per_sm, kMaxSlots));
+    const int nacc = family == M_SVGD ? d : ((family == M_WY || family == M_WX) ? 2 + d : 2);
+    PairLaunch L{};
+    if (nseg == 1) {
+        plan_segment(seg[0], n_cols[0], RB, slots, counters + cnt_off[0]);
+        L.seg[0] = seg[0];
+        L.seg[1] = seg[0];
+        L.ctas0 = seg[0].n_rb * seg[0].splits;
+    } else {
+        const double w0 = (double)seg[0].n_rows * n_cols[0], w1 = (double)seg[1].n_rows * n_cols[1];
+        int s0 = (int)llround(slots * w0 / (w0 + w1));
+        s0 = std::max(1, std::min(s0, slots - 1));
+        const int s1 = std::max(1, slots - s0);
+        plan_segment(seg[0], n_cols[0], RB, s0, counters + cnt_off[0]);
+        plan_segment(seg[1], n_cols[1], RB, s1, counters + cnt_off[1]);
+        seg[1].part = seg[0].part + (size_t)nacc * seg[0].splits * seg[0].part_ld;
+        L.seg[0] = seg[0];
+        L.seg[1] = seg[1];
+        L.ctas0 = seg[0].n_rb * seg[0].splits;
     }
+    const int total = L.ctas0 + (nseg == 2 ? seg[1].n_rb * seg[1].splits : 0);
+    cudaError_t e = cudaErrorInvalidValue;
+    switch (d) {
+        case 1: e = launch_pairs_r<1>(R, family, L, total, st); break;
+        case 2: e = launch_pairs_r<2>(R, family, L, total, st); break;
+        case 3: e = launch_pairs_r<3>(R, family, L, total, st); break;
+        case 4: e = launch_pairs_r<4>(R, family, L, total, st); break;
+        case 5: e = launch_pairs_r<5>(R, family, L, total, st); break;
+        case 6: e = launch_pairs_r<6>(R, family, L, total, st); break;
+    }
+    return cuda_failed(ctx, e) ? COV_ERR_CUDA : COV_OK;
 }
 
 static SkBufs carve_sinkhorn(Carver& cv, int T, int M, int d) {
@@ -637,7 +730,7 @@ static SkBufs carve_sinkhorn(Carver& cv, int T, int M, int d) {
     B.scal = cv.take<float>(16);
     B.cnt_ld = cnt_ld_for(B.Tp, B.Mp);
     B.counters = cv.take<unsigned>((size_t)M_COUNT * B.cnt_ld);
-    B.part_floats = (size_t)(2 + d) * (kPartRows + std::max(B.Tp, B.Mp));
+    B.part_floats = (size_t)(2 + d) * (kPartRows + B.Tp + B.Mp);
     B.part = cv.take<float>(B.part_floats);
     return B;
 }
@@ -675,37 +768,53 @@ cov_status sinkhorn_field_ws(cov_ctx* ctx, void* ws, size_t ws_bytes, const floa
     base.spin_limit = ctx->spin_limit;
     base.log2a = log2a;
     base.part = B.part;
+    base.pre_ok = 1;
     float* hp_cur = B.hp0;
     float* hp_nxt = B.hp1;
-    for (int it = 0; it < n_iter; ++it) {
-        PairArgs a = base;  // g-update: rows y, columns x
-        a.rows = B.ys; a.row_ld = B.Mp; a.n_rows = M;
-        a.cols = B.xs; a.colh = B.hx; a.col_ld = B.Tp;
-        a.out_h = B.hy; a.in_h = B.lb;
-        run_pairs(ctx, d, M_G, a, T, B.counters + M_G * B.cnt_ld, stream);
-        a = base;           // f-update: rows x, columns y
+    bool first = true;  // the first pass reads what the prep kernel just wrote
+    cov_status r = COV_OK;
+    for (int it = 0; it < n_iter && r == COV_OK; ++it) {
+        // launch A: g-update (rows y, columns x) and self p-update (rows x,
+        // columns x) -- independent, same column set
+        PairArgs sg[2] = {base, base};
+        sg[0].rows = B.ys; sg[0].row_ld = B.Mp; sg[0].n_rows = M;
+        sg[0].cols = B.xs; sg[0].colh = B.hx; sg[0].col_ld = B.Tp;
+        sg[0].out_h = B.hy; sg[0].in_h = B.lb; sg[0].emode = M_G;
+        sg[1].rows = B.xs; sg[1].row_ld = B.Tp; sg[1].n_rows = T;
+        sg[1].cols = B.xs; sg[1].colh = hp_cur; sg[1].col_ld = B.Tp;
+        sg[1].out_h = hp_nxt; sg[1].in_h = hp_cur; sg[1].emode = M_P;
+        if (first) sg[0].pre_ok = sg[1].pre_ok = 0;
+        first = false;
+        const int ncA[2] = {T, T}, coA[2] = {M_G * B.cnt_ld, M_P * B.cnt_ld};
+        r = run_pairs(ctx, d, M_G, sg, ncA, 2, coA, B.counters, stream);
+        if (r != COV_OK) break;
+        // launch B: f-update (rows x, columns y)
+        PairArgs a = base;
         a.rows = B.xs; a.row_ld = B.Tp; a.n_rows = T;
         a.cols = B.ys; a.colh = B.hy; a.col_ld = B.Mp;
-        a.out_h = B.hx;
-        run_pairs(ctx, d, M_F, a, M, B.counters + M_F * B.cnt_ld, stream);
-        a = base;           // p-update: rows x, columns x
-        a.rows = B.xs; a.row_ld = B.Tp; a.n_rows = T;
-        a.cols = B.xs; a.colh = hp_cur; a.col_ld = B.Tp;
-        a.out_h = hp_nxt; a.in_h = hp_cur;
-        run_pairs(ctx, d, M_P, a, T, B.counters + M_P * B.cnt_ld, stream);
+        a.out_h = B.hx; a.emode = M_F;
+        const int ncB[1] = {M}, coB[1] = {M_F * B.cnt_ld};
+        r = run_pairs(ctx, d, M_G, &a, ncB, 1, coB, B.counters, stream);
         std::swap(hp_cur, hp_nxt);
     }
+    if (r != COV_OK) return r;
     if (a_out) {
         PairArgs a = base;  // cross barycentre: (sum_j pi_ij yhat_j) - xhat_i
         a.rows = B.xs; a.row_ld = B.Tp; a.n_rows = T;
         a.cols = B.ys; a.colh = B.hy; a.col_ld = B.Mp;
         a.bary = B.bary;
-        run_pairs(ctx, d, M_WY, a, M, B.counters + M_WY * B.cnt_ld, stream);
+        if (first) a.pre_ok = 0;
+        first = false;
+        const int nc1[1] = {M}, co1[1] = {M_WY * B.cnt_ld};
+        r = run_pairs(ctx, d, M_WY, &a, nc1, 1, co1, B.counters, stream);
+        if (r != COV_OK) return r;
         a = base;           // self barycentre and the field 2 sigma (ybar - xbar)
         a.rows = B.xs; a.row_ld = B.Tp; a.n_rows = T;
         a.cols = B.xs; a.colh = hp_cur; a.col_ld = B.Tp;
         a.bary = B.bary; a.a_out = a_out; a.a_scale = 2.0f * sigma;
-        run_pairs(ctx, d, M_WX, a, T, B.counters + M_WX * B.cnt_ld, stream);
+        const int nc2[1] = {T}, co2[1] = {M_WX * B.cnt_ld};
+        r = run_pairs(ctx, d, M_WX, &a, nc2, 1, co2, B.counters, stream);
+        if (r != COV_OK) return r;
     }
     if (f || g || p) {
         const int nf = std::max(T, M);
@@ -866,7 +975,10 @@ cov_status svgd_field_ws(cov_ctx* ctx, void* ws, size_t ws_bytes, const float* x
     a.cols = B.xt; a.cols2 = B.st; a.col_ld = B.Tp;
     a.a_out = a_out;
     a.a_scale = (float)(r2l / ((double)h * T));
-    run_pairs(ctx, d, M_SVGD, a, T, B.counters, stream);
+    a.pre_ok = 0;
+    const int nc[1] = {T}, co[1] = {0};
+    const cov_status r = run_pairs(ctx, d, M_SVGD, &a, nc, 1, co, B.counters, stream);
+    if (r != COV_OK) return r;
     if (cuda_failed(ctx, cudaGetLastError())) return COV_ERR_CUDA;
     return COV_OK;
 }
