@@ -121,7 +121,7 @@ COV_API const char* cov_last_cuda_error(cov_ctx* ctx);
 enum {
     COV_OPT_ROWS_PER_THREAD = 1, /* 2, 4 or 8 (default 4; 2 and 8 built for d = 2) */
     COV_OPT_THREADS = 2,         /* threads per CTA: 128 (the only value built) */
-    COV_OPT_CTAS_PER_SM = 3,     /* target resident CTAs per SM, 1..8 (default 4) */
+    COV_OPT_CTAS_PER_SM = 3,     /* cap on resident CTAs per SM planned for, 1..8 (default 8; the register budget may allow fewer) */
     COV_OPT_USE_GRAPH = 4,       /* cov_solve: capture one outer iteration in a CUDA graph (default 1) */
     COV_OPT_SPIN_LIMIT = 5       /* bounded-wait iteration limit, >= 0 (default 1<<22) */
 };

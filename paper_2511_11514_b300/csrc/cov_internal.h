@@ -26,7 +26,7 @@ struct cov_ctx {
     // options
     int rows_per_thread = 4;
     int threads = 128;
-    int ctas_per_sm = 4;
+    int ctas_per_sm = 8;
     int use_graph = 1;
     long long spin_limit = 1LL << 22;
     std::string last_cuda_error;

@@ -620,8 +620,29 @@ __global__ void sk_finish_kernel(int T, int M, float epsln2, float log2a, SkBufs
 // the tail of the previous one; every kernel waits (griddepcontrol.wait)
 // before it reads the previous launch's results or writes scratch.
 // ---------------------------------------------------------------------------
+// Resident CTAs per SM of one kernel instantiation (queried once).
 template <int D, int R, int MODE>
-static cudaError_t launch_pairs_t(const PairLaunch& L, int n_ctas, cudaStream_t st) {
+static int occupancy_t() {
+    static int occ = 0;
+    if (occ == 0) {
+        int v = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, pairs_kernel<D, R, MODE>, kThreads, 0) != cudaSuccess ||
+            v < 1) {
+            cudaGetLastError();
+            v = 1;
+        }
+        occ = v;
+    }
+    return occ;
+}
+
+// n_ctas > 0: launch; n_ctas == 0: return the resident CTAs per SM in *occ.
+template <int D, int R, int MODE>
+static cudaError_t launch_pairs_t(const PairLaunch& L, int n_ctas, cudaStream_t st, int* occ = nullptr) {
+    if (occ) {
+        *occ = occupancy_t<D, R, MODE>();
+        return cudaSuccess;
+    }
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3((unsigned)n_ctas);
     cfg.blockDim = dim3(kThreads);
@@ -636,23 +657,35 @@ static cudaError_t launch_pairs_t(const PairLaunch& L, int n_ctas, cudaStream_t 
 }
 
 template <int D, int R>
-static cudaError_t launch_pairs_mode(int family, const PairLaunch& L, int n, cudaStream_t st) {
+static cudaError_t launch_pairs_mode(int family, const PairLaunch& L, int n, cudaStream_t st, int* occ) {
     switch (family) {
-        case M_G: return launch_pairs_t<D, R, M_G>(L, n, st);
-        case M_WY: return launch_pairs_t<D, R, M_WY>(L, n, st);
-        case M_WX: return launch_pairs_t<D, R, M_WX>(L, n, st);
-        case M_SVGD: return launch_pairs_t<D, R, M_SVGD>(L, n, st);
+        case M_G: return launch_pairs_t<D, R, M_G>(L, n, st, occ);
+        case M_WY: return launch_pairs_t<D, R, M_WY>(L, n, st, occ);
+        case M_WX: return launch_pairs_t<D, R, M_WX>(L, n, st, occ);
+        case M_SVGD: return launch_pairs_t<D, R, M_SVGD>(L, n, st, occ);
     }
     return cudaErrorInvalidValue;
 }
 
 template <int D>
-static cudaError_t launch_pairs_r(int R, int family, const PairLaunch& L, int n, cudaStream_t st) {
+static cudaError_t launch_pairs_r(int R, int family, const PairLaunch& L, int n, cudaStream_t st, int* occ) {
     if constexpr (D == 2) {
-        if (R == 2) return launch_pairs_mode<D, 2>(family, L, n, st);
-        if (R == 8) return launch_pairs_mode<D, 8>(family, L, n, st);
+        if (R == 2) return launch_pairs_mode<D, 2>(family, L, n, st, occ);
+        if (R == 8) return launch_pairs_mode<D, 8>(family, L, n, st, occ);
     }
-    return launch_pairs_mode<D, 4>(family, L, n, st);
+    return launch_pairs_mode<D, 4>(family, L, n, st, occ);
+}
+
+static cudaError_t launch_pairs_d(int d, int R, int family, const PairLaunch& L, int n, cudaStream_t st, int* occ) {
+    switch (d) {
+        case 1: return launch_pairs_r<1>(R, family, L, n, st, occ);
+        case 2: return launch_pairs_r<2>(R, family, L, n, st, occ);
+        case 3: return launch_pairs_r<3>(R, family, L, n, st, occ);
+        case 4: return launch_pairs_r<4>(R, family, L, n, st, occ);
+        case 5: return launch_pairs_r<5>(R, family, L, n, st, occ);
+        case 6: return launch_pairs_r<6>(R, family, L, n, st, occ);
+    }
+    return cudaErrorInvalidValue;
 }
 
 static int effective_R(int d, int R) { return (d == 2 && (R == 2 || R == 8)) ? R : 4; }
@@ -680,7 +713,11 @@ static cov_status run_pairs(cov_ctx* ctx, int d, int family, PairArgs* seg, cons
                             const int* cnt_off, unsigned* counters, cudaStream_t st) {
     const int R = effective_R(d, ctx->rows_per_thread);
     const int RB = 32 * R;
-    const int slots = std::max(1, std::min(ctx->num_sms * ctx->ctas_per_sm, kMaxSlots));
+    // one wave: as many CTAs as can be resident (the register budget decides
+    // how many per SM), capped by the tuning option
+    int occ = 1;
+    launch_pairs_d(d, R, family, PairLaunch{}, 0, st, &occ);
+    const int slots = std::max(1, std::min(ctx->num_sms * std::min(occ, ctx->ctas_per_sm), kMaxSlots));
     const int nacc = family == M_SVGD ? d : ((family == M_WY || family == M_WX) ? 2 + d : 2);
     PairLaunch L{};
     if (nseg == 1) {
@@ -701,15 +738,7 @@ static cov_status run_pairs(cov_ctx* ctx, int d, int family, PairArgs* seg, cons
         L.ctas0 = seg[0].n_rb * seg[0].splits;
     }
     const int total = L.ctas0 + (nseg == 2 ? seg[1].n_rb * seg[1].splits : 0);
-    cudaError_t e = cudaErrorInvalidValue;
-    switch (d) {
-        case 1: e = launch_pairs_r<1>(R, family, L, total, st); break;
-        case 2: e = launch_pairs_r<2>(R, family, L, total, st); break;
-        case 3: e = launch_pairs_r<3>(R, family, L, total, st); break;
-        case 4: e = launch_pairs_r<4>(R, family, L, total, st); break;
-        case 5: e = launch_pairs_r<5>(R, family, L, total, st); break;
-        case 6: e = launch_pairs_r<6>(R, family, L, total, st); break;
-    }
+    const cudaError_t e = launch_pairs_d(d, R, family, L, total, st, nullptr);
     return cuda_failed(ctx, e) ? COV_ERR_CUDA : COV_OK;
 }
 
