@@ -58,6 +58,7 @@ def parse_args():
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-tune", action="store_true", help="skip the tile-shape autotuner")
     return ap.parse_args()
 
 
@@ -239,6 +240,11 @@ def run_ours(args):
                             n_iter=w.n_iter)
     u = torch.as_tensor(inst.u0, dtype=torch.float64, device=dev).contiguous()
     s = cov.cov_solve(ctx, prob, 0, u)  # trajectory of the initial controls
+    tiling = {"R": 4, "ctas_per_sm": 8, "source": "default"}
+    if not args.no_tune:
+        from paper_2511_11514_b300 import autotune
+        ch = autotune.tune_sinkhorn(ctx, s[1:, :2].float().contiguous(), y, w.eps)
+        tiling = {"R": ch["R"], "ctas_per_sm": ch["ctas_per_sm"], "source": "autotune (before the timed region)"}
     stream = torch.cuda.current_stream()
     for _ in range(max(3, args.warmup)):
         cov.cov_solve_continue(ctx, prob, 1, u, s)
@@ -332,6 +338,7 @@ def run_ours(args):
                 "parallelism": f"{world} independent problems (one per GPU)" if world > 1 else "single GPU",
                 "l2": "flushed between steps (256 MiB write outside the per-step CUDA events)",
                 "ms_per_coverage_solve": ms_per_step * w.n_outer,
+                "tiling": tiling,
                 "wall_s_timed_region": wall}),
             "roofline": {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Gpair/s",
                          "frac": achieved / peak, "traffic": None,

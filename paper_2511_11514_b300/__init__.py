@@ -8,10 +8,10 @@ without the built library.
 """
 import importlib
 
-__all__ = ["binding", "workloads", "build_lib"]
+__all__ = ["binding", "workloads", "build_lib", "autotune"]
 
 
 def __getattr__(name):
-    if name in ("binding", "build_lib"):
+    if name in ("binding", "build_lib", "autotune"):
         return importlib.import_module(f"{__name__}.{name}")
     raise AttributeError(name)

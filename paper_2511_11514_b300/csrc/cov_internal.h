@@ -65,9 +65,15 @@ size_t lqr_ws_bytes(int T, int n, int m);
 
 // Field calls on an explicit workspace region (cov_solve carves its own
 // buffers first and passes the rest).
+// scal_given: device [16] floats from sinkhorn_reference_stats (centre of y,
+// 1/sum b), or nullptr to compute them in this call.
 cov_status sinkhorn_field_ws(cov_ctx* ctx, void* ws, size_t ws_bytes, const float* x, int x_ld, int T,
                              const float* y, const float* b, int M, int d, float eps, int n_iter, int flags,
-                             float* f, float* g, float* p, float* a_out, cudaStream_t stream);
+                             float* f, float* g, float* p, float* a_out, cudaStream_t stream,
+                             const float* scal_given = nullptr);
+// Statistics of a reference set that every field evaluation on it needs:
+// scal[0..d) = mean of y, scal[8] = 1 / sum b (0 when b == NULL).
+void sinkhorn_reference_stats(const float* y, int M, int d, const float* b, float* scal, cudaStream_t stream);
 cov_status svgd_field_ws(cov_ctx* ctx, void* ws, size_t ws_bytes, const float* x, int x_ld, int T, int d,
                          const float* score, const cov_gmm* gmm, float h, float* a_out, cudaStream_t stream);
 cov_status lqr_track_ws(cov_ctx* ctx, void* ws, size_t ws_bytes, const double* A, const double* B,

@@ -764,6 +764,10 @@ static SkBufs carve_sinkhorn(Carver& cv, int T, int M, int d) {
     return B;
 }
 
+void sinkhorn_reference_stats(const float* y, int M, int d, const float* b, float* scal, cudaStream_t stream) {
+    sk_centre_kernel<<<1, 1024, 0, stream>>>(y, M, d, b, scal);
+}
+
 size_t sinkhorn_ws_bytes(int T, int M, int d) {
     Carver cv(nullptr);
     carve_sinkhorn(cv, T, M, d);
@@ -772,7 +776,8 @@ size_t sinkhorn_ws_bytes(int T, int M, int d) {
 
 cov_status sinkhorn_field_ws(cov_ctx* ctx, void* ws, size_t ws_bytes, const float* x, int x_ld, int T,
                              const float* y, const float* b, int M, int d, float eps, int n_iter, int flags,
-                             float* f, float* g, float* p, float* a_out, cudaStream_t stream) {
+                             float* f, float* g, float* p, float* a_out, cudaStream_t stream,
+                             const float* scal_given) {
     if (!ctx || !x || !y || T < 1 || M < 1 || d < 1 || d > COV_MAX_D || x_ld < d || n_iter < 0 ||
         !(eps > 0.f) || !isfinite(eps))
         return COV_ERR_INVALID_ARG;
@@ -788,7 +793,10 @@ cov_status sinkhorn_field_ws(cov_ctx* ctx, void* ws, size_t ws_bytes, const floa
     const float inv_sigma = (float)(1.0 / sqrt(epsln2));
     const float sigma = (float)sqrt(epsln2);
     const float log2a = (float)(-log2((double)T));
-    sk_centre_kernel<<<1, 1024, 0, stream>>>(y, M, d, b, B.scal);
+    if (scal_given)
+        B.scal = const_cast<float*>(scal_given);
+    else
+        sk_centre_kernel<<<1, 1024, 0, stream>>>(y, M, d, b, B.scal);
     const int np = std::max(B.Tp, B.Mp);
     sk_prep_kernel<<<(np + 255) / 256, 256, 0, stream>>>(x, x_ld, T, y, M, b, d, inv_sigma, (float)(1.0 / epsln2),
                                                          log2a, warm, f, g, p, B, ctx->status);

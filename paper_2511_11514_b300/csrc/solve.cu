@@ -28,7 +28,7 @@ cov_status linearize_launch(cov_ctx* ctx, int model, const double* s, const doub
 static bool model_is_lti(int model) { return model == COV_SINGLE_INT || model == COV_DOUBLE_INT; }
 
 struct SolveBufs {
-    float *x, *a;
+    float *x, *a, *scal;
     double *abar, *A, *B, *v, *gains;
 };
 
@@ -41,6 +41,7 @@ static SolveBufs carve_solve(Carver& cv, int T, int d, int n, int m) {
     b.B = cv.take<double>((size_t)T * n * m);
     b.v = cv.take<double>((size_t)T * m);
     b.gains = cv.take<double>(lqr_gain_doubles(T, n, m));
+    b.scal = cv.take<float>(16);
     return b;
 }
 
@@ -103,7 +104,7 @@ static cov_status enqueue_iteration(cov_ctx* ctx, const cov_problem* P, int n, i
     cov_status r;
     if (P->field == COV_FIELD_SINKHORN)
         r = sinkhorn_field_ws(ctx, rest, rest_bytes, b.x, d, T, P->y, P->b, P->M, d, P->eps, P->n_iter, 0, nullptr,
-                              nullptr, nullptr, b.a, st);
+                              nullptr, nullptr, b.a, st, b.scal);
     else
         r = svgd_field_ws(ctx, rest, rest_bytes, b.x, d, T, d, nullptr, &P->gmm, P->h, b.a, st);
     if (r != COV_OK) return r;
@@ -161,6 +162,9 @@ static cov_status cov::solve_impl(cov_ctx* ctx, const cov_problem* prob, int n_o
         if (r != COV_OK) return r;
     }
     if (n_outer == 0) return COV_OK;
+    // the reference set is fixed during a solve: its centre and weight sum
+    // are computed once per call
+    if (prob->field == COV_FIELD_SINKHORN) sinkhorn_reference_stats(prob->y, prob->M, prob->d, prob->b, b.scal, st);
 
     if (model_is_lti(prob->model)) {
         // gains of a time-invariant model: computed once per (model, T, dt,
