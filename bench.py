@@ -59,6 +59,10 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-tune", action="store_true", help="skip the tile-shape autotuner")
+    ap.add_argument("--batched", type=int, default=0,
+                    help="time cov_solve_batched on this many uneven problems (and the same problems one by one)")
+    ap.add_argument("--no-large-roofline", action="store_true",
+                    help="skip the all-pairs roofline at T = 65536, M = 262144")
     return ap.parse_args()
 
 
@@ -304,6 +308,37 @@ def run_ours(args):
     probe = cov.cov_probe_peaks(ctx, 4096)
     peak, peak_info = alu_peak(probe, torch.cuda.get_device_properties(dev).multi_processor_count)
 
+    # the same kernel at the large workload (T = 65536, M = 262144), where the
+    # per-launch fixed costs are amortised: (t(3 iterations) - t(1)) / 2
+    big = None
+    if rank == 0 and not args.no_large_roofline:
+        wb = wl.SINKHORN_UNICYCLE_T65536
+        ib = wl.make_instance(wb)
+        ub = torch.as_tensor(ib.u0, dtype=torch.float64, device=dev)
+        xb = cov.cov_rollout(ctx, wb.model, ib.s0, ub, wb.dt)[1:, :2].float().contiguous()
+        yb = torch.as_tensor(ib.y, dtype=torch.float32, device=dev).contiguous()
+        if not args.no_tune:
+            from paper_2511_11514_b300 import autotune
+            chb = autotune.tune_sinkhorn(ctx, xb, yb, wb.eps)
+        cov.cov_field_sinkhorn(ctx, xb, yb, wb.eps, 1, field=False)
+
+        def big_ms(n):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            cov.cov_field_sinkhorn(ctx, xb, yb, wb.eps, n, field=False)
+            b.record(stream)
+            torch.cuda.synchronize()
+            return a.elapsed_time(b)
+
+        tb = (big_ms(3) - big_ms(1)) / 2
+        ach_b = (2 * wb.T * wb.M + wb.T * wb.T) / (tb * 1e-3)
+        big = {"bound": "alu", "achieved": ach_b / 1e9, "peak": peak / 1e9, "unit": "Gpair/s", "frac": ach_b / peak,
+               "traffic": None, "workload": wb.name, "ms_per_sinkhorn_iteration": tb}
+        if not args.no_tune:
+            apply_choice = {"R": tiling["R"], "ctas_per_sm": tiling["ctas_per_sm"]}
+            autotune.apply(ctx, apply_choice)
+
     # ---- end to end through the C-ABI with host buffers ---------------------------
     u_h = torch.as_tensor(inst.u0, dtype=torch.float64).pin_memory()
     y_h = torch.as_tensor(inst.y, dtype=torch.float32).pin_memory()
@@ -346,6 +381,7 @@ def run_ours(args):
                          "peak_basis": "derived: 148 SMs x 2032 MHz x min(MUFU ex2 width, 128 FP32 lanes / "
                                        f"{FP32_OPS_PER_PAIR} ops per pair)",
                          "peak_detail": peak_info, "probe": probe},
+            "roofline_large": big,
             "clocks": clk,
             "e2e": {"value": pairs_step / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
@@ -360,10 +396,81 @@ def run_ours(args):
     return 0
 
 
+def run_batched(args):
+    """Batched form: N independent double-integrator problems, T ~ U{128..4096},
+    M ~ U{512..16384}, half Stein / half Sinkhorn (50 iterations), advanced by
+    one CUDA-graph launch per outer iteration, against the same problems solved
+    one by one with cov_solve on the same GPU."""
+    import torch
+
+    from paper_2511_11514_b300 import binding as cov
+
+    torch.cuda.set_device(0)
+    insts = wl.make_batch(args.batched, seed=0)
+    ctx = cov.Context(0)
+    dev = torch.device("cuda", 0)
+    ys = [torch.as_tensor(i.y, dtype=torch.float32, device=dev) if i.y is not None else None for i in insts]
+    probs = []
+    for i, y in zip(insts, ys):
+        w = i.wl
+        if w.field == wl.FIELD_SVGD:
+            probs.append(cov.make_problem(w.model, w.T, w.dt, i.s0, w.field, i.Q, i.R, w.eta, gmm=i.gmm, h=w.h))
+        else:
+            probs.append(cov.make_problem(w.model, w.T, w.dt, i.s0, w.field, i.Q, i.R, w.eta, y=y, eps=w.eps,
+                                          n_iter=w.n_iter))
+    pairs = sum(i.wl.pairs_per_field for i in insts)
+    us = [torch.as_tensor(i.u0, dtype=torch.float64, device=dev) for i in insts]
+    t0 = time.perf_counter()
+    ss = cov.cov_solve_batched(ctx, probs, max(1, args.warmup), us)  # includes graph capture
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    clocks = Clocks(0)
+    clocks.start()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record()
+    cov.cov_solve_batched(ctx, probs, args.steps, us, ss)
+    b.record()
+    torch.cuda.synchronize()
+    batched_ms = a.elapsed_time(b)
+    clk = clocks.stop()
+    st, flags = ctx.device_status()
+    if st != cov.COV_OK:
+        raise SystemExit(f"device status {cov.status_string(st)} flags {flags}")
+    # one by one: cov_solve per problem (its graph captured in an untimed call)
+    one_ms = 0.0
+    for pr, i in zip(probs, insts):
+        u1 = torch.as_tensor(i.u0, dtype=torch.float64, device=dev)
+        cov.cov_solve(ctx, pr, 1, u1)
+        a.record()
+        cov.cov_solve(ctx, pr, args.steps, u1)
+        b.record()
+        torch.cuda.synchronize()
+        one_ms += a.elapsed_time(b)
+    value = pairs * args.steps / (batched_ms * 1e-3)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": batched_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded Philox mixtures, uneven sizes)",
+            "config": {"workload": f"batched_double_integrator_{args.batched}_problems",
+                       "problems": args.batched, "T": "U{128..4096}", "M": "U{512..16384}",
+                       "fields": "half Stein (h = 0.05), half Sinkhorn (eps = 0.005, 50 iterations)",
+                       "pairs_per_step": pairs, "graph_capture_and_setup_s": setup_s,
+                       "l2": "not flushed (the batch working set, ~GBs, exceeds L2)"},
+            "one_by_one": {"value": pairs * args.steps / (one_ms * 1e-3), "unit": UNIT,
+                           "ms_per_step": one_ms / args.steps,
+                           "how": "cov_solve on each problem in turn, same GPU, same context, graphs pre-captured"},
+            "batched_speedup": one_ms / batched_ms, "clocks": clk}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.batched:
+        return run_batched(args)
     return run_ours(args)
 
 

@@ -273,6 +273,23 @@ COV_API cov_status cov_solve(cov_ctx* ctx, const cov_problem* prob, int n_outer,
 COV_API cov_status cov_solve_continue(cov_ctx* ctx, const cov_problem* prob, int n_outer,
                                       double* u, double* s, cov_stream_t stream);
 
+/* Batched outer iterations of n_probs independent problems (each as in
+ * cov_solve: its own model, horizon, field kind, reference, weights).  One
+ * outer iteration of every problem is captured once into a single CUDA graph
+ * (one independent branch per problem) and the graph is launched n_outer
+ * times, so one launch advances all problems and the GPU interleaves their
+ * kernels.  Problem p uses its own region of the workspace (reserve
+ * cov_workspace_size_batched bytes).  Results equal those of cov_solve on
+ * each problem alone.
+ *   probs [n_probs] host;  u[p] [T_p][m_p], s_out[p] [T_p+1][n_p] FP64 device
+ *   (u and s_out are host arrays of device pointers). */
+COV_API cov_status cov_solve_batched(cov_ctx* ctx, const cov_problem* probs, int n_probs,
+                                     int n_outer, double* const* u, double* const* s_out,
+                                     cov_stream_t stream);
+/* Workspace bytes cov_solve_batched needs for these problems (0 if one of
+ * them is invalid). */
+COV_API size_t cov_workspace_size_batched(const cov_problem* probs, int n_probs);
+
 /* ---- measurement -------------------------------------------------------- */
 
 /* Issue-rate probes for the roofline of the all-pairs kernels: each runs

@@ -33,7 +33,8 @@ EXPORTS = (
     "cov_get_device_status", "cov_status_string", "cov_last_cuda_error", "cov_ctx_set_option",
     "cov_gmm_score", "cov_field_svgd", "cov_field_sinkhorn", "cov_field_sinkhorn_noalloc", "cov_linearize",
     "cov_rollout",
-    "cov_lqr_track", "cov_solve", "cov_solve_continue", "cov_probe_peaks",
+    "cov_lqr_track", "cov_solve", "cov_solve_continue", "cov_solve_batched", "cov_workspace_size_batched",
+    "cov_probe_peaks",
 )
 
 
@@ -87,6 +88,9 @@ def load(path: str = LIB_PATH):
         "cov_lqr_track": (_i, [_P, _P, _P, _P, _P, _P, _i, _i, _i, _P, _P, _P]),
         "cov_solve": (_i, [_P, ctypes.POINTER(cov_problem), _i, _P, _P, _P]),
         "cov_solve_continue": (_i, [_P, ctypes.POINTER(cov_problem), _i, _P, _P, _P]),
+        "cov_solve_batched": (_i, [_P, ctypes.POINTER(cov_problem), _i, _i, ctypes.POINTER(_P),
+                                   ctypes.POINTER(_P), _P]),
+        "cov_workspace_size_batched": (_sz, [ctypes.POINTER(cov_problem), _i]),
         "cov_probe_peaks": (_i, [_P, _i, ctypes.POINTER(_d), _P]),
     }
     for name, (res, args) in sig.items():
@@ -330,6 +334,28 @@ def cov_solve_continue(ctx: Context, problem, n_outer, u, s, stream=None):
                                    _ptr(s, torch.float64, (T + 1, n), "s"), _stream(stream))
     ctx._check(st, "cov_solve_continue")
     return s
+
+
+def cov_solve_batched(ctx: Context, problems, n_outer, us, ss=None, stream=None):
+    """n_outer outer iterations of independent problems [(struct, keep), ...]
+    in one CUDA graph per iteration; us[p] (float64 [T_p, m_p]) are updated in
+    place; returns the trajectories ss[p] ([T_p+1, n_p])."""
+    n = len(problems)
+    arr = (cov_problem * n)(*[pr[0] for pr in problems])
+    if ss is None:
+        ss = [torch.empty((pr[0].T + 1, MODEL_DIMS[pr[0].model][0]), device=u.device, dtype=torch.float64)
+              for pr, u in zip(problems, us)]
+    up = (_P * n)(*[_ptr(u, torch.float64, (pr[0].T, MODEL_DIMS[pr[0].model][1]), "u").value
+                    for pr, u in zip(problems, us)])
+    sp = (_P * n)(*[_ptr(s, torch.float64, (pr[0].T + 1, MODEL_DIMS[pr[0].model][0]), "s").value
+                    for pr, s in zip(problems, ss)])
+    need = int(load().cov_workspace_size_batched(arr, n))
+    if need == 0:
+        raise CovError(COV_ERR_INVALID_ARG, "cov_workspace_size_batched")
+    ctx._check(load().cov_ctx_reserve(ctx.h, need), "cov_ctx_reserve")
+    st = load().cov_solve_batched(ctx.h, arr, n, int(n_outer), up, sp, _stream(stream))
+    ctx._check(st, "cov_solve_batched")
+    return ss
 
 
 def cov_probe_peaks(ctx: Context, iters=4096, stream=None):

@@ -17,6 +17,8 @@ struct cov_graph_cache {
     uint64_t key = 0;
 };
 
+#include <vector>
+
 struct cov_ctx {
     int device = 0;
     int num_sms = 148;
@@ -31,6 +33,8 @@ struct cov_ctx {
     long long spin_limit = 1LL << 22;
     std::string last_cuda_error;
     cov_graph_cache solve_graph;
+    cov_graph_cache batch_graph;       // cov_solve_batched: one outer iteration of all problems
+    std::vector<cudaStream_t> pool;    // streams the batched graph's branches are captured on
     // cached LTI Riccati gains of cov_solve (valid while key matches)
     uint64_t gains_key = 0;
 };

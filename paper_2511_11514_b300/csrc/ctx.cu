@@ -17,6 +17,7 @@ bool cov::cuda_failed(cov_ctx* ctx, cudaError_t e) {
 namespace cov {
 size_t solve_buffers_bytes(int T, int d, int n, int m);
 void drop_solve_graph(cov_ctx* ctx);
+void destroy_stream_pool(cov_ctx* ctx);
 void lqr_set_attributes();
 }  // namespace cov
 
@@ -71,6 +72,7 @@ extern "C" void cov_ctx_destroy(cov_ctx* ctx) {
     cudaSetDevice(ctx->device);
     cudaDeviceSynchronize();
     cov::drop_solve_graph(ctx);
+    cov::destroy_stream_pool(ctx);
     if (ctx->ws) cudaFree(ctx->ws);
     if (ctx->status) cudaFree(ctx->status);
     delete ctx;

@@ -56,6 +56,14 @@ void drop_solve_graph(cov_ctx* ctx) {
     if (ctx->solve_graph.graph) cudaGraphDestroy(ctx->solve_graph.graph);
     ctx->solve_graph = cov_graph_cache{};
     ctx->gains_key = 0;
+    if (ctx->batch_graph.exec) cudaGraphExecDestroy(ctx->batch_graph.exec);
+    if (ctx->batch_graph.graph) cudaGraphDestroy(ctx->batch_graph.graph);
+    ctx->batch_graph = cov_graph_cache{};
+}
+
+void destroy_stream_pool(cov_ctx* ctx) {
+    for (cudaStream_t s : ctx->pool) cudaStreamDestroy(s);
+    ctx->pool.clear();
 }
 
 // x_i = first d components of s_{i+1} (FP32 coverage coordinates).
@@ -231,5 +239,184 @@ static cov_status cov::solve_impl(cov_ctx* ctx, const cov_problem* prob, int n_o
     }
     for (int k = 0; k < n_outer; ++k)
         if (cuda_failed(ctx, cudaGraphLaunch(ctx->solve_graph.exec, st))) return COV_ERR_CUDA;
+    return COV_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Batched solve: many independent problems, one CUDA graph per outer
+// iteration.  Each problem owns a contiguous region of the workspace (its
+// solve buffers, then the field / LQR scratch).  One outer iteration of every
+// problem is captured as an independent branch of a single graph (branches
+// forked over a pool of streams during capture), so one graph launch
+// advances all problems and the GPU interleaves their kernels.
+// ---------------------------------------------------------------------------
+namespace cov {
+
+static constexpr int kPoolStreams = 32;
+
+static size_t problem_ws_bytes(const cov_problem* P, int n, int m) {
+    const size_t solve = solve_buffers_bytes(P->T, P->d, n, m);
+    const size_t field =
+        P->field == COV_FIELD_SINKHORN ? sinkhorn_ws_bytes(P->T, P->M, P->d) : svgd_ws_bytes(P->T, P->d);
+    const size_t lqr = lqr_ws_bytes(P->T, n, m);
+    return round_up(solve + std::max(field, lqr) + 4096, 256);
+}
+
+static cov_status ensure_pool(cov_ctx* ctx, int k) {
+    while ((int)ctx->pool.size() < k) {
+        cudaStream_t s;
+        if (cuda_failed(ctx, cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking))) return COV_ERR_CUDA;
+        ctx->pool.push_back(s);
+    }
+    return COV_OK;
+}
+
+// Make each of streams[0..k) wait for the work so far on `from`.
+static cov_status fork_streams(cov_ctx* ctx, cudaStream_t from, const std::vector<cudaStream_t>& to, int k) {
+    cudaEvent_t e;
+    if (cuda_failed(ctx, cudaEventCreateWithFlags(&e, cudaEventDisableTiming))) return COV_ERR_CUDA;
+    cov_status r = COV_OK;
+    if (cuda_failed(ctx, cudaEventRecord(e, from))) r = COV_ERR_CUDA;
+    for (int i = 0; i < k && r == COV_OK; ++i)
+        if (cuda_failed(ctx, cudaStreamWaitEvent(to[i], e, 0))) r = COV_ERR_CUDA;
+    cudaEventDestroy(e);
+    return r;
+}
+
+// Make `into` wait for the work so far on streams[0..k).
+static cov_status join_streams(cov_ctx* ctx, const std::vector<cudaStream_t>& from, int k, cudaStream_t into) {
+    for (int i = 0; i < k; ++i) {
+        cudaEvent_t e;
+        if (cuda_failed(ctx, cudaEventCreateWithFlags(&e, cudaEventDisableTiming))) return COV_ERR_CUDA;
+        const bool bad = cuda_failed(ctx, cudaEventRecord(e, from[i])) || cuda_failed(ctx, cudaStreamWaitEvent(into, e, 0));
+        cudaEventDestroy(e);
+        if (bad) return COV_ERR_CUDA;
+    }
+    return COV_OK;
+}
+
+}  // namespace cov
+
+extern "C" size_t cov_workspace_size_batched(const cov_problem* probs, int n_probs) {
+    if (!probs || n_probs < 1) return 0;
+    size_t total = 0;
+    for (int p = 0; p < n_probs; ++p) {
+        int n, m;
+        if (cov::validate(&probs[p], &n, &m) != COV_OK) return 0;
+        total += cov::problem_ws_bytes(&probs[p], n, m);
+    }
+    return total + 4096;
+}
+
+extern "C" cov_status cov_solve_batched(cov_ctx* ctx, const cov_problem* probs, int n_probs, int n_outer,
+                                        double* const* u, double* const* s_out, cov_stream_t stream) {
+    using namespace cov;
+    if (!ctx || !probs || n_probs < 1 || n_outer < 0 || !u || !s_out) return COV_ERR_INVALID_ARG;
+    std::vector<int> nn(n_probs), mm(n_probs);
+    std::vector<size_t> off(n_probs);
+    size_t total = 0;
+    for (int p = 0; p < n_probs; ++p) {
+        if (!u[p] || !s_out[p]) return COV_ERR_INVALID_ARG;
+        const cov_status r = validate(&probs[p], &nn[p], &mm[p]);
+        if (r != COV_OK) return r;
+        off[p] = total;
+        total += problem_ws_bytes(&probs[p], nn[p], mm[p]);
+    }
+    if (!ctx->ws || total > ctx->ws_bytes) return COV_ERR_WORKSPACE;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return COV_ERR_CUDA;
+    ctx->gains_key = 0;  // the problem regions overlap what cov_solve cached
+    cudaStream_t st = (cudaStream_t)stream;
+    const int K = std::min(n_probs, kPoolStreams);
+    if (ensure_pool(ctx, K) != COV_OK) return COV_ERR_CUDA;
+
+    std::vector<SolveBufs> bufs(n_probs);
+    std::vector<void*> rest(n_probs);
+    std::vector<size_t> rest_bytes(n_probs);
+    for (int p = 0; p < n_probs; ++p) {
+        char* base = static_cast<char*>(ctx->ws) + off[p];
+        Carver cv(base);
+        bufs[p] = carve_solve(cv, probs[p].T, probs[p].d, nn[p], mm[p]);
+        const size_t used = round_up(cv.off, 256);
+        rest[p] = base + used;
+        rest_bytes[p] = problem_ws_bytes(&probs[p], nn[p], mm[p]) - used;
+    }
+
+    // set-up of every problem, spread over the pool: initial rollout, the
+    // reference statistics, and the Riccati gains of time-invariant models
+    cov_status r = fork_streams(ctx, st, ctx->pool, K);
+    if (r != COV_OK) return r;
+    for (int p = 0; p < n_probs && r == COV_OK; ++p) {
+        const cov_problem* P = &probs[p];
+        cudaStream_t sp = ctx->pool[p % K];
+        r = cov_rollout(ctx, P->model, P->s0, u[p], P->T, P->dt, s_out[p], (cov_stream_t)sp);
+        if (r != COV_OK || n_outer == 0) continue;
+        if (P->field == COV_FIELD_SINKHORN) sinkhorn_reference_stats(P->y, P->M, P->d, P->b, bufs[p].scal, sp);
+        if (model_is_lti(P->model)) {
+            r = linearize_launch(ctx, P->model, s_out[p], u[p], P->T, P->dt, bufs[p].A, bufs[p].B, sp);
+            if (r == COV_OK) r = lqr_riccati(ctx, nn[p], mm[p], bufs[p].A, bufs[p].B, P->Q, P->R, P->T,
+                                             bufs[p].gains, sp);
+        }
+    }
+    if (r != COV_OK) return r;
+    r = join_streams(ctx, ctx->pool, K, st);
+    if (r != COV_OK || n_outer == 0) return r;
+
+    if (!ctx->use_graph) {
+        for (int k = 0; k < n_outer && r == COV_OK; ++k) {
+            r = fork_streams(ctx, st, ctx->pool, K);
+            for (int p = 0; p < n_probs && r == COV_OK; ++p)
+                r = enqueue_iteration(ctx, &probs[p], nn[p], mm[p], bufs[p], rest[p], rest_bytes[p], u[p], s_out[p],
+                                      ctx->pool[p % K]);
+            if (r == COV_OK) r = join_streams(ctx, ctx->pool, K, st);
+        }
+        return r;
+    }
+
+    uint64_t key = 1469598103934665603ull;
+    for (int p = 0; p < n_probs; ++p) {
+        key = fnv(&probs[p], sizeof(cov_problem), key);
+        if (probs[p].field == COV_FIELD_SVGD) {
+            key = fnv(probs[p].gmm.w, sizeof(float) * probs[p].gmm.K, key);
+            key = fnv(probs[p].gmm.mu, sizeof(float) * probs[p].gmm.K * probs[p].d, key);
+            key = fnv(probs[p].gmm.sigma, sizeof(float) * probs[p].gmm.K, key);
+        }
+        const void* ptrs[2] = {u[p], s_out[p]};
+        key = fnv(ptrs, sizeof(ptrs), key);
+    }
+    const void* wsp = ctx->ws;
+    key = fnv(&wsp, sizeof(wsp), key);
+    if (!ctx->batch_graph.exec || ctx->batch_graph.key != key) {
+        if (ctx->batch_graph.exec) cudaGraphExecDestroy(ctx->batch_graph.exec);
+        if (ctx->batch_graph.graph) cudaGraphDestroy(ctx->batch_graph.graph);
+        ctx->batch_graph = cov_graph_cache{};
+        cudaStream_t cap;
+        if (cuda_failed(ctx, cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking))) return COV_ERR_CUDA;
+        if (cuda_failed(ctx, cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal))) {
+            cudaStreamDestroy(cap);
+            return COV_ERR_CUDA;
+        }
+        r = fork_streams(ctx, cap, ctx->pool, K);
+        for (int p = 0; p < n_probs && r == COV_OK; ++p)
+            r = enqueue_iteration(ctx, &probs[p], nn[p], mm[p], bufs[p], rest[p], rest_bytes[p], u[p], s_out[p],
+                                  ctx->pool[p % K]);
+        if (r == COV_OK) r = join_streams(ctx, ctx->pool, K, cap);
+        cudaGraph_t g = nullptr;
+        const cudaError_t ce = cudaStreamEndCapture(cap, &g);
+        cudaStreamDestroy(cap);
+        if (r != COV_OK || cuda_failed(ctx, ce)) {
+            if (g) cudaGraphDestroy(g);
+            return r != COV_OK ? r : COV_ERR_CUDA;
+        }
+        cudaGraphExec_t ex = nullptr;
+        if (cuda_failed(ctx, cudaGraphInstantiate(&ex, g, 0))) {
+            cudaGraphDestroy(g);
+            return COV_ERR_CUDA;
+        }
+        ctx->batch_graph.graph = g;
+        ctx->batch_graph.exec = ex;
+        ctx->batch_graph.key = key;
+    }
+    for (int k = 0; k < n_outer; ++k)
+        if (cuda_failed(ctx, cudaGraphLaunch(ctx->batch_graph.exec, st))) return COV_ERR_CUDA;
     return COV_OK;
 }

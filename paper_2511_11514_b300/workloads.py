@@ -217,3 +217,29 @@ def random_weights(n: int, seed: int):
     w = rng(seed).uniform(0.5, 1.5, size=n)
     w32 = (w / w.sum()).astype(np.float32)
     return w32.astype(np.float64)
+
+
+# -- batched workload: many independent problems of uneven size ---------------
+def make_batch(n: int, seed: int = 0, T_range=(128, 4096), M_range=(512, 16384), K_range=(2, 16)):
+    """n double-integrator coverage problems; T ~ U{T_range}, M ~ U{M_range},
+    each with its own 2-16 component mixture (seed = problem index); even
+    indices use the Stein field, odd ones the Sinkhorn field (eps = 0.005,
+    50 iterations).  Returns a list of Instance."""
+    g = rng(seed)
+    out = []
+    for p in range(n):
+        T = int(g.integers(T_range[0], T_range[1] + 1))
+        M = int(g.integers(M_range[0], M_range[1] + 1))
+        K = int(g.integers(K_range[0], K_range[1] + 1))
+        svgd = p % 2 == 0
+        w = Workload(name=f"batch_{p}", model=DOUBLE_INT, field=FIELD_SVGD if svgd else FIELD_SINKHORN, T=T,
+                     dt=0.05, n_outer=100, eta=1e-3 if svgd else 0.5, M=0 if svgd else M, eps=0.0 if svgd else 0.005,
+                     n_iter=0 if svgd else 50, h=0.05 if svgd else 0.0, gmm_K=K, seed=p)
+        s0, u0 = double_int_init(T, w.dt)
+        wts, mu, sigma = gmm_params(K, seed=p, dirichlet=True)
+        inst = Instance(wl=w, s0=s0, u0=u0, Q=coverage_Q(DOUBLE_INT), R=w.R_scale * np.eye(2),
+                        gmm=tuple(f32_pair(v)[1] for v in (wts, mu, sigma)))
+        if not svgd:
+            inst.y = f32_pair(gmm_samples(wts, mu, sigma, M, seed=p + 100000))[1]
+        out.append(inst)
+    return out
