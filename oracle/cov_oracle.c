@@ -632,3 +632,366 @@ int orc_solve(int model, int T, double dt, const double* s0, int field,
     free(v); free(z); free(f); free(p); free(g);
     return 0;
 }
+
+/* ------------------------------------------------------------------------
+ * Adjoints.  Reverse mode of the definitions above, written out by hand:
+ * for every softmax-type update the derivative of -eps LSE_k(z_k) is
+ * -eps pi_k dz_k with pi = softmax(z), and dc(x, y)/dx = 2 (x - y).
+ * ---------------------------------------------------------------------- */
+static void softmax_inplace(double* z, int n) {
+    double L = lse(z, n);
+    for (int k = 0; k < n; ++k) z[k] = exp(z[k] - L);
+}
+
+void orc_sinkhorn_field_vjp(const double* x, int T, const double* y, int M,
+                            const double* b, int d, double eps, int n_iter,
+                            const double* abar, double* xbar, double* ybar,
+                            double* bbar) {
+    const int n = n_iter;
+    const double bs = wsum(b, M);
+    double* F = (double*)calloc((size_t)(n + 1) * T, sizeof(double));
+    double* G = (double*)calloc((size_t)(n + 1) * M, sizeof(double));
+    double* Pp = (double*)calloc((size_t)(n + 1) * T, sizeof(double));
+    /* forward with the potentials of every iteration (cold start) */
+    for (int t = 1; t <= n; ++t) {
+        orc_sinkhorn_g_update(x, T, y, M, d, eps, F + (size_t)(t - 1) * T, NULL, 0, G + (size_t)t * M);
+        orc_sinkhorn_f_update(x, T, y, M, b, d, eps, G + (size_t)t * M, NULL, 0, F + (size_t)t * T);
+        orc_sinkhorn_p_update(x, T, d, eps, Pp + (size_t)(t - 1) * T, NULL, 0, Pp + (size_t)t * T);
+    }
+    double* gbar = (double*)calloc(M, sizeof(double));
+    double* fbar = (double*)calloc(T, sizeof(double));
+    double* pbar = (double*)calloc(T, sizeof(double));
+    double* pprev = (double*)calloc(T, sizeof(double));
+    double* lbbar = (double*)calloc(M, sizeof(double));
+    double* z = (double*)malloc(sizeof(double) * (M > T ? M : T));
+    const double* g = G + (size_t)n * M;
+    const double* p = Pp + (size_t)n * T;
+
+    /* field_i = 2 (sum_j pi_ij y_j - sum_k pi^s_ik x_k), objective <abar, field> */
+    for (int i = 0; i < T; ++i) {
+        const double* xi = x + (size_t)i * d;
+        double A[16], yb[16], Ay = 0.0;
+        for (int j = 0; j < M; ++j)
+            z[j] = log(wt(b, M, j, bs)) + (g[j] - sqdist(xi, y + (size_t)j * d, d)) / eps;
+        softmax_inplace(z, M);
+        for (int c = 0; c < d; ++c) {
+            A[c] = 2.0 * abar[(size_t)i * d + c];
+            yb[c] = 0.0;
+            for (int j = 0; j < M; ++j) yb[c] += z[j] * y[(size_t)j * d + c];
+            Ay += A[c] * yb[c];
+        }
+        for (int j = 0; j < M; ++j) {
+            const double* yj = y + (size_t)j * d;
+            double Ayj = 0.0;
+            for (int c = 0; c < d; ++c) {
+                ybar[(size_t)j * d + c] += A[c] * z[j];
+                Ayj += A[c] * yj[c];
+            }
+            const double sb = z[j] * (Ayj - Ay);
+            gbar[j] += sb / eps;
+            lbbar[j] += sb;
+            const double cb = -sb / eps;
+            for (int c = 0; c < d; ++c) {
+                xbar[(size_t)i * d + c] += cb * 2.0 * (xi[c] - yj[c]);
+                ybar[(size_t)j * d + c] += cb * 2.0 * (yj[c] - xi[c]);
+            }
+        }
+    }
+    for (int i = 0; i < T; ++i) {
+        const double* xi = x + (size_t)i * d;
+        double Bv[16], xb[16], Bx = 0.0;
+        for (int k = 0; k < T; ++k)
+            z[k] = log(1.0 / T) + (p[k] - sqdist(xi, x + (size_t)k * d, d)) / eps;
+        softmax_inplace(z, T);
+        for (int c = 0; c < d; ++c) {
+            Bv[c] = -2.0 * abar[(size_t)i * d + c];
+            xb[c] = 0.0;
+            for (int k = 0; k < T; ++k) xb[c] += z[k] * x[(size_t)k * d + c];
+            Bx += Bv[c] * xb[c];
+        }
+        for (int k = 0; k < T; ++k) {
+            const double* xk = x + (size_t)k * d;
+            double Bxk = 0.0;
+            for (int c = 0; c < d; ++c) {
+                xbar[(size_t)k * d + c] += Bv[c] * z[k];
+                Bxk += Bv[c] * xk[c];
+            }
+            const double sb = z[k] * (Bxk - Bx);
+            pbar[k] += sb / eps;
+            const double cb = -sb / eps;
+            for (int c = 0; c < d; ++c) {
+                xbar[(size_t)i * d + c] += cb * 2.0 * (xi[c] - xk[c]);
+                xbar[(size_t)k * d + c] += cb * 2.0 * (xk[c] - xi[c]);
+            }
+        }
+    }
+    /* back through the iterations, last first */
+    for (int t = n; t >= 1; --t) {
+        const double* pold = Pp + (size_t)(t - 1) * T;
+        const double* gt = G + (size_t)t * M;
+        const double* fold = F + (size_t)(t - 1) * T;
+        /* p^t = (p^{t-1} - eps LSE_k(log a_k + (p^{t-1}_k - c_ik)/eps)) / 2 */
+        for (int i = 0; i < T; ++i) pprev[i] = 0.5 * pbar[i];
+        for (int i = 0; i < T; ++i) {
+            const double* xi = x + (size_t)i * d;
+            for (int k = 0; k < T; ++k)
+                z[k] = log(1.0 / T) + (pold[k] - sqdist(xi, x + (size_t)k * d, d)) / eps;
+            softmax_inplace(z, T);
+            for (int k = 0; k < T; ++k) {
+                const double w = 0.5 * pbar[i] * z[k];
+                const double* xk = x + (size_t)k * d;
+                pprev[k] -= w;
+                for (int c = 0; c < d; ++c) {
+                    xbar[(size_t)i * d + c] += w * 2.0 * (xi[c] - xk[c]);
+                    xbar[(size_t)k * d + c] += w * 2.0 * (xk[c] - xi[c]);
+                }
+            }
+        }
+        memcpy(pbar, pprev, sizeof(double) * T);
+        /* f^t = -eps LSE_j(log b_j + (g^t_j - c_ij)/eps) */
+        for (int i = 0; i < T; ++i) {
+            const double* xi = x + (size_t)i * d;
+            for (int j = 0; j < M; ++j)
+                z[j] = log(wt(b, M, j, bs)) + (gt[j] - sqdist(xi, y + (size_t)j * d, d)) / eps;
+            softmax_inplace(z, M);
+            for (int j = 0; j < M; ++j) {
+                const double w = fbar[i] * z[j];
+                const double* yj = y + (size_t)j * d;
+                gbar[j] -= w;
+                lbbar[j] -= eps * w;
+                for (int c = 0; c < d; ++c) {
+                    xbar[(size_t)i * d + c] += w * 2.0 * (xi[c] - yj[c]);
+                    ybar[(size_t)j * d + c] += w * 2.0 * (yj[c] - xi[c]);
+                }
+            }
+        }
+        for (int i = 0; i < T; ++i) fbar[i] = 0.0;
+        /* g^t = -eps LSE_i(log a_i + (f^{t-1}_i - c_ij)/eps) */
+        for (int j = 0; j < M; ++j) {
+            const double* yj = y + (size_t)j * d;
+            for (int i = 0; i < T; ++i)
+                z[i] = log(1.0 / T) + (fold[i] - sqdist(x + (size_t)i * d, yj, d)) / eps;
+            softmax_inplace(z, T);
+            for (int i = 0; i < T; ++i) {
+                const double w = gbar[j] * z[i];
+                const double* xi = x + (size_t)i * d;
+                fbar[i] -= w;
+                for (int c = 0; c < d; ++c) {
+                    xbar[(size_t)i * d + c] += w * 2.0 * (xi[c] - yj[c]);
+                    ybar[(size_t)j * d + c] += w * 2.0 * (yj[c] - xi[c]);
+                }
+            }
+        }
+        for (int j = 0; j < M; ++j) gbar[j] = 0.0;
+    }
+    /* log of the normalised weights -> raw weights */
+    if (b && bbar) {
+        double S = 0.0;
+        for (int j = 0; j < M; ++j) S += lbbar[j];
+        for (int j = 0; j < M; ++j) bbar[j] += lbbar[j] / b[j] - S / bs;
+    }
+    free(F); free(G); free(Pp); free(gbar); free(fbar); free(pbar); free(pprev); free(lbbar); free(z);
+}
+
+/* Adjoint of abar -> v.  v solves (G'QG + R) v = G'Q abar with z = G v, so
+ * abar_bar = Q G w with (G'QG + R) w = vbar: w minimises
+ * sum_t z'_t Q z'_t + w_t'R w_t - 2 vbar_t'w_t, z' = G w, an LQR problem
+ * with a linear control cost r_t = -vbar_t and no state target:
+ *   k_t = S^-1 (B'p' + r_t),  p_t = A'p' - K'(B'p' + r_t),  p_T = 0. */
+void orc_lqr_vjp(const double* A, const double* B, const double* Q,
+                 const double* R, const double* vbar, int T, int n, int m,
+                 double* abar_bar) {
+    double* K = (double*)malloc(sizeof(double) * (size_t)T * m * n);
+    double* k = (double*)malloc(sizeof(double) * (size_t)T * m);
+    double P[64], p[8], Pn[64], pn[8];
+    for (int r = 0; r < n * n; ++r) P[r] = Q[r];
+    for (int r = 0; r < n; ++r) p[r] = 0.0;
+    for (int t = T - 1; t >= 0; --t) {
+        const double* At = A + (size_t)t * n * n;
+        const double* Bt = B + (size_t)t * n * m;
+        double PA[64], PB[64], S[64], G[64], hh[8];
+        for (int r = 0; r < n; ++r)
+            for (int c = 0; c < n; ++c) {
+                PA[r * n + c] = 0.0;
+                for (int q = 0; q < n; ++q) PA[r * n + c] += P[r * n + q] * At[q * n + c];
+            }
+        for (int r = 0; r < n; ++r)
+            for (int c = 0; c < m; ++c) {
+                PB[r * m + c] = 0.0;
+                for (int q = 0; q < n; ++q) PB[r * m + c] += P[r * n + q] * Bt[q * m + c];
+            }
+        for (int r = 0; r < m; ++r) {
+            for (int c = 0; c < m; ++c) {
+                S[r * m + c] = R[r * m + c];
+                for (int q = 0; q < n; ++q) S[r * m + c] += Bt[q * m + r] * PB[q * m + c];
+            }
+            for (int c = 0; c < n; ++c) {
+                G[r * n + c] = 0.0;
+                for (int q = 0; q < n; ++q) G[r * n + c] += Bt[q * m + r] * PA[q * n + c];
+            }
+            hh[r] = -vbar[(size_t)t * m + r];
+            for (int q = 0; q < n; ++q) hh[r] += Bt[q * m + r] * p[q];
+        }
+        double* Kt = K + (size_t)t * m * n;
+        double* kt = k + (size_t)t * m;
+        chol_solve(S, m, G, n, Kt);
+        chol_solve(S, m, hh, 1, kt);
+        for (int r = 0; r < n; ++r) {
+            for (int c = 0; c < n; ++c) {
+                double s = (t >= 1) ? Q[r * n + c] : 0.0;
+                for (int q = 0; q < n; ++q) s += At[q * n + r] * PA[q * n + c];
+                for (int q = 0; q < m; ++q) s -= G[q * n + r] * Kt[q * n + c];
+                Pn[r * n + c] = s;
+            }
+            double s = 0.0;
+            for (int q = 0; q < n; ++q) s += At[q * n + r] * p[q];
+            for (int q = 0; q < m; ++q) s -= Kt[q * n + r] * hh[q];
+            pn[r] = s;
+        }
+        memcpy(P, Pn, sizeof(double) * n * n);
+        memcpy(p, pn, sizeof(double) * n);
+    }
+    double zc[8], zn[8], w[8];
+    for (int r = 0; r < n; ++r) zc[r] = 0.0;
+    for (int t = 0; t < T; ++t) {
+        const double* At = A + (size_t)t * n * n;
+        const double* Bt = B + (size_t)t * n * m;
+        const double* Kt = K + (size_t)t * m * n;
+        const double* kt = k + (size_t)t * m;
+        for (int r = 0; r < m; ++r) {
+            w[r] = -kt[r];
+            for (int c = 0; c < n; ++c) w[r] -= Kt[r * n + c] * zc[c];
+        }
+        for (int r = 0; r < n; ++r) {
+            double s = 0.0;
+            for (int c = 0; c < n; ++c) s += At[r * n + c] * zc[c];
+            for (int c = 0; c < m; ++c) s += Bt[r * m + c] * w[c];
+            zn[r] = s;
+        }
+        for (int r = 0; r < n; ++r) {
+            double s = 0.0;
+            for (int c = 0; c < n; ++c) s += Q[r * n + c] * zn[c];
+            abar_bar[(size_t)t * n + r] = s;
+        }
+        memcpy(zc, zn, sizeof(double) * n);
+    }
+    free(K);
+    free(k);
+}
+
+/* s_{t+1} = F(s_t, u_t): lambda_T = sbar_T, u_bar_t = B_t' lambda_{t+1},
+ * lambda_t = sbar_t + A_t' lambda_{t+1}; d/ds0 = lambda_0. */
+void orc_rollout_vjp(int model, const double* s, const double* u, int T,
+                     double dt, const double* sbar, double* ubar,
+                     double* s0bar) {
+    int n, m;
+    orc_model_dims(model, &n, &m);
+    double* A = (double*)malloc(sizeof(double) * (size_t)T * n * n);
+    double* B = (double*)malloc(sizeof(double) * (size_t)T * n * m);
+    orc_linearize(model, s, u, T, dt, A, B);
+    double lam[8], ln[8];
+    for (int r = 0; r < n; ++r) lam[r] = sbar[(size_t)T * n + r];
+    for (int t = T - 1; t >= 0; --t) {
+        const double* At = A + (size_t)t * n * n;
+        const double* Bt = B + (size_t)t * n * m;
+        for (int c = 0; c < m; ++c) {
+            double acc = 0.0;
+            for (int r = 0; r < n; ++r) acc += Bt[r * m + c] * lam[r];
+            ubar[(size_t)t * m + c] = acc;
+        }
+        for (int c = 0; c < n; ++c) {
+            double acc = sbar[(size_t)t * n + c];
+            for (int r = 0; r < n; ++r) acc += At[r * n + c] * lam[r];
+            ln[c] = acc;
+        }
+        memcpy(lam, ln, sizeof(double) * n);
+    }
+    for (int r = 0; r < n; ++r) s0bar[r] += lam[r];
+    free(A);
+    free(B);
+}
+
+/* Gradient of the coverage loss through n_outer outer iterations (Sec. II-C)
+ * by reverse mode with the controls u^k and trajectories s^k of every outer
+ * iteration kept (the checkpoints), for time-invariant dynamics (A, B do
+ * not depend on the trajectory).  The loss gradient with respect to the
+ * final positions is -(1/T) times the field at converged potentials (the
+ * envelope theorem, exact at convergence). */
+double orc_solve_sinkhorn_grad(int model, int T, double dt, const double* s0,
+                               int d, const double* y, const double* b, int M,
+                               double eps, int n_iter, const double* Q,
+                               const double* R, double eta, int n_outer,
+                               const double* u0, const double* y_loss,
+                               const double* b_loss, int M_loss,
+                               double eps_loss, double* ybar, double* bbar,
+                               double* s0bar) {
+    int n, m;
+    if (orc_model_dims(model, &n, &m) != 0 || model == ORC_UNICYCLE || d > n) return NAN;
+    const int K = n_outer;
+    const size_t us = (size_t)T * m, ss = (size_t)(T + 1) * n;
+    double* U = (double*)malloc(sizeof(double) * (K + 1) * us);
+    double* S = (double*)malloc(sizeof(double) * (K + 1) * ss);
+    double* x = (double*)malloc(sizeof(double) * (size_t)T * d);
+    double* a = (double*)malloc(sizeof(double) * (size_t)T * d);
+    double* abar = (double*)malloc(sizeof(double) * (size_t)T * n);
+    double* A = (double*)malloc(sizeof(double) * (size_t)T * n * n);
+    double* Bm = (double*)malloc(sizeof(double) * (size_t)T * n * m);
+    double* v = (double*)malloc(sizeof(double) * us);
+    double* z = (double*)malloc(sizeof(double) * ss);
+    double* f = (double*)malloc(sizeof(double) * (size_t)(T > M_loss ? T : M_loss));
+    double* g = (double*)malloc(sizeof(double) * (size_t)(M > M_loss ? M : M_loss));
+    double* p = (double*)malloc(sizeof(double) * (size_t)T);
+    memcpy(U, u0, sizeof(double) * us);
+    orc_rollout(model, s0, U, T, dt, S);
+    for (int k = 1; k <= K; ++k) {
+        const double* Sp = S + (size_t)(k - 1) * ss;
+        for (int i = 0; i < T; ++i)
+            for (int c = 0; c < d; ++c) x[(size_t)i * d + c] = Sp[(size_t)(i + 1) * n + c];
+        orc_sinkhorn(x, T, y, M, b, d, eps, n_iter, 0, f, g, p);
+        orc_sinkhorn_field(x, T, y, M, b, d, eps, g, p, NULL, 0, a);
+        for (int i = 0; i < T; ++i)
+            for (int r = 0; r < n; ++r) abar[(size_t)i * n + r] = r < d ? a[(size_t)i * d + r] : 0.0;
+        orc_linearize(model, Sp, U + (size_t)(k - 1) * us, T, dt, A, Bm);
+        orc_lqr_track(A, Bm, Q, R, abar, T, n, m, v, z, NULL);
+        for (size_t r = 0; r < us; ++r) U[(size_t)k * us + r] = U[(size_t)(k - 1) * us + r] + eta * v[r];
+        orc_rollout(model, s0, U + (size_t)k * us, T, dt, S + (size_t)k * ss);
+    }
+    /* loss and its gradient with respect to the final positions */
+    const double* SK = S + (size_t)K * ss;
+    for (int i = 0; i < T; ++i)
+        for (int c = 0; c < d; ++c) x[(size_t)i * d + c] = SK[(size_t)(i + 1) * n + c];
+    const double L = orc_sinkhorn_divergence(x, T, y_loss, M_loss, b_loss, d, eps_loss, 1e-12, 100000);
+    orc_sinkhorn_converge(x, T, y_loss, M_loss, b_loss, d, eps_loss, 1e-12, 100000, f, g, p);
+    orc_sinkhorn_field(x, T, y_loss, M_loss, b_loss, d, eps_loss, g, p, NULL, 0, a);
+    double* sbar = (double*)calloc(ss, sizeof(double));
+    double* ubar = (double*)calloc(us, sizeof(double));
+    double* ub2 = (double*)calloc(us, sizeof(double));
+    double* xbar = (double*)calloc((size_t)T * d, sizeof(double));
+    double* fa = (double*)calloc((size_t)T * d, sizeof(double));
+    double* abb = (double*)calloc((size_t)T * n, sizeof(double));
+    for (int i = 0; i < T; ++i)
+        for (int c = 0; c < d; ++c) sbar[(size_t)(i + 1) * n + c] = -a[(size_t)i * d + c] / T;
+    orc_rollout_vjp(model, SK, U + (size_t)K * us, T, dt, sbar, ubar, s0bar);
+    for (int k = K; k >= 1; --k) {
+        const double* Sp = S + (size_t)(k - 1) * ss;
+        const double* Up = U + (size_t)(k - 1) * us;
+        for (size_t r = 0; r < us; ++r) v[r] = eta * ubar[r];
+        orc_linearize(model, Sp, Up, T, dt, A, Bm);
+        orc_lqr_vjp(A, Bm, Q, R, v, T, n, m, abb);
+        for (int i = 0; i < T; ++i)
+            for (int c = 0; c < d; ++c) {
+                fa[(size_t)i * d + c] = abb[(size_t)i * n + c];
+                x[(size_t)i * d + c] = Sp[(size_t)(i + 1) * n + c];
+                xbar[(size_t)i * d + c] = 0.0;
+            }
+        orc_sinkhorn_field_vjp(x, T, y, M, b, d, eps, n_iter, fa, xbar, ybar, bbar);
+        for (size_t r = 0; r < ss; ++r) sbar[r] = 0.0;
+        for (int i = 0; i < T; ++i)
+            for (int c = 0; c < d; ++c) sbar[(size_t)(i + 1) * n + c] = xbar[(size_t)i * d + c];
+        orc_rollout_vjp(model, Sp, Up, T, dt, sbar, ub2, s0bar);
+        for (size_t r = 0; r < us; ++r) ubar[r] += ub2[r];
+    }
+    free(U); free(S); free(x); free(a); free(abar); free(A); free(Bm); free(v); free(z);
+    free(f); free(g); free(p); free(sbar); free(ubar); free(ub2); free(xbar); free(fa); free(abb);
+    return L;
+}

@@ -95,6 +95,40 @@ int orc_solve(int model, int T, double dt, const double* s0, int field,
               const double* R, double eta, int n_outer, double* u,
               double* s);
 
+/* ---- adjoints (reverse mode of the definitions above) ------------------- */
+/* Vector-Jacobian product of the Sinkhorn-divergence field (orc_sinkhorn with
+ * n_iter cold-start iterations followed by orc_sinkhorn_field) with respect
+ * to x, y and the raw weights b (normalised inside): given abar [T][d],
+ * xbar += d<abar, field>/dx, ybar += .../dy, bbar += .../db (bbar may be NULL;
+ * ignored when b == NULL). */
+void orc_sinkhorn_field_vjp(const double* x, int T, const double* y, int M,
+                            const double* b, int d, double eps, int n_iter,
+                            const double* abar, double* xbar, double* ybar,
+                            double* bbar);
+/* Adjoint of the linear map abar -> v of orc_lqr_track: given vbar [T][m],
+ * returns abar_bar [T][n] (row t-1 for target t = 1..T). */
+void orc_lqr_vjp(const double* A, const double* B, const double* Q,
+                 const double* R, const double* vbar, int T, int n, int m,
+                 double* abar_bar);
+/* Adjoint of orc_rollout: given sbar [T+1][n], returns ubar [T][m] and adds
+ * d/ds0 to s0bar [n] (A_t, B_t at the rollout's own (s_t, u_t)). */
+void orc_rollout_vjp(int model, const double* s, const double* u, int T,
+                     double dt, const double* sbar, double* ubar,
+                     double* s0bar);
+/* Gradient of the coverage loss L = converged Sinkhorn divergence (weight
+ * eps_loss) between the positions of the final trajectory and (y_loss, b_loss)
+ * after n_outer Sinkhorn-field outer iterations, with respect to the field's
+ * reference samples y [M][d], raw weights b [M] (may be NULL) and s0 [n].
+ * Time-invariant models only (single / double integrator).  Returns L. */
+double orc_solve_sinkhorn_grad(int model, int T, double dt, const double* s0,
+                               int d, const double* y, const double* b, int M,
+                               double eps, int n_iter, const double* Q,
+                               const double* R, double eta, int n_outer,
+                               const double* u0, const double* y_loss,
+                               const double* b_loss, int M_loss,
+                               double eps_loss, double* ybar, double* bbar,
+                               double* s0bar);
+
 #ifdef __cplusplus
 }
 #endif

@@ -6,6 +6,9 @@ numpy arrays, C-contiguous, row-major, shapes as documented per function.
 Parity status per function:
   gmm_score, svgd_field, sinkhorn_*, sinkhorn_field, sinkhorn_divergence,
   linearize, rollout, lqr_track -- pinned (tests/test_oracle_*.py).
+  sinkhorn_field_vjp, lqr_vjp, rollout_vjp, solve_sinkhorn_grad -- pinned by
+  central finite differences of the forward functions and, for lqr_vjp, by
+  the transpose identity against the dense KKT solve (tests/test_oracle_adjoint.py).
   solve -- composition of pinned parts; pinned only by the one-iteration
   composition check (single integrator, R -> 0: the trajectory moves by
   eta * field) and by the decrease of the coverage divergence.
@@ -77,6 +80,11 @@ def _declare(L):
         "orc_lqr_track": (None, [_D, _D, _D, _D, _D, _i, _i, _i, _D, _D, _D]),
         "orc_solve": (_i, [_i, _i, _d, _D, _i, _i, _D, _D, _i, _i, _D, _D, _D,
                            _d, _i, _d, _D, _D, _d, _i, _D, _D]),
+        "orc_sinkhorn_field_vjp": (None, [_D, _i, _D, _i, _D, _i, _d, _i, _D, _D, _D, _D]),
+        "orc_lqr_vjp": (None, [_D, _D, _D, _D, _D, _i, _i, _i, _D]),
+        "orc_rollout_vjp": (None, [_i, _D, _D, _i, _d, _D, _D, _D]),
+        "orc_solve_sinkhorn_grad": (_d, [_i, _i, _d, _D, _i, _D, _D, _i, _d, _i, _D, _D, _d, _i,
+                                         _D, _D, _D, _i, _d, _D, _D, _D]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -280,3 +288,59 @@ def solve(model, dt, s0, u0, field, Q, R, eta, n_outer, *, d=2, y=None, b=None,
     if rc != 0:
         raise ValueError("orc_solve: bad arguments")
     return u, s
+
+
+# -- adjoints (reverse mode of the functions above) -------------------------
+def sinkhorn_field_vjp(x, y, b, eps, n_iter, abar):
+    """Gradient of <abar, field(x, y, b)> after n_iter cold-start iterations.
+
+    Returns (xbar [T,d], ybar [M,d], bbar [M] or None)."""
+    x, y, abar = _f64(x), _f64(y), _f64(abar)
+    b = None if b is None else _f64(b)
+    T, d = x.shape
+    M = y.shape[0]
+    xbar, ybar = np.zeros((T, d)), np.zeros((M, d))
+    bbar = None if b is None else np.zeros(M)
+    lib().orc_sinkhorn_field_vjp(_p(x), T, _p(y), M, _p(b), d, float(eps), int(n_iter), _p(abar),
+                                 _p(xbar), _p(ybar), _p(bbar))
+    return xbar, ybar, bbar
+
+
+def lqr_vjp(A, B, Q, R, vbar):
+    """Gradient of <vbar, v(abar)> with respect to abar (v is linear in abar)."""
+    A, B, Q, R, vbar = _f64(A), _f64(B), _f64(Q), _f64(R), _f64(vbar)
+    T, n, m = B.shape
+    out = np.empty((T, n))
+    lib().orc_lqr_vjp(_p(A), _p(B), _p(Q), _p(R), _p(vbar), T, n, m, _p(out))
+    return out
+
+
+def rollout_vjp(model, s, u, dt, sbar):
+    """Gradient of <sbar, rollout(s0, u)> at the trajectory s: (ubar, s0bar)."""
+    s, u, sbar = _f64(s), _f64(u), _f64(sbar)
+    n, m = MODEL_DIMS[model]
+    T = u.shape[0]
+    ubar, s0bar = np.empty((T, m)), np.zeros(n)
+    lib().orc_rollout_vjp(int(model), _p(s), _p(u), T, float(dt), _p(sbar), _p(ubar), _p(s0bar))
+    return ubar, s0bar
+
+
+def solve_sinkhorn_grad(model, dt, s0, u0, d, y, b, eps, n_iter, Q, R, eta, n_outer,
+                        y_loss, b_loss, eps_loss):
+    """Loss S_eps_loss(trajectory after n_outer iterations, (y_loss, b_loss)) and
+    its gradient with respect to (y, b, s0).  Time-invariant models only."""
+    n, m = MODEL_DIMS[model]
+    s0, u0, y, Q, R, yl = _f64(s0), _f64(u0), _f64(y), _f64(Q), _f64(R), _f64(y_loss)
+    b = None if b is None else _f64(b)
+    bl = None if b_loss is None else _f64(b_loss)
+    T = u0.shape[0]
+    M, ML = y.shape[0], yl.shape[0]
+    ybar, s0bar = np.zeros((M, d)), np.zeros(n)
+    bbar = None if b is None else np.zeros(M)
+    L = lib().orc_solve_sinkhorn_grad(int(model), T, float(dt), _p(s0), int(d), _p(y), _p(b), M,
+                                      float(eps), int(n_iter), _p(Q), _p(R), float(eta),
+                                      int(n_outer), _p(u0), _p(yl), _p(bl), ML, float(eps_loss),
+                                      _p(ybar), _p(bbar), _p(s0bar))
+    if not np.isfinite(L):
+        raise ValueError("orc_solve_sinkhorn_grad: bad arguments")
+    return float(L), ybar, bbar, s0bar

@@ -1,0 +1,187 @@
+"""Pins of the oracle's reverse-mode adjoints (gradients through the outer
+iteration of Sec. II-C).
+
+Independent references: central finite differences of the forward oracle
+functions along random directions (every input perturbed separately, so a
+wrong term in one input's gradient cannot be hidden by another), and, for the
+LQR adjoint, the transpose of a dense KKT solve built with numpy plus the
+dot-product identity <vbar, v(abar)> = <abar, vjp(vbar)> of a linear map.
+"""
+import numpy as np
+import pytest
+
+from paper_2511_11514_b300 import workloads as wl
+
+from test_oracle_lqr import _dense_kkt
+
+H = 1e-6
+
+
+def _field_obj(orc, x, y, b, eps, n_iter, abar):
+    f, g, p = orc.sinkhorn(x, y, b, eps, n_iter)
+    return float(np.sum(abar * orc.sinkhorn_field(x, y, b, eps, g, p)))
+
+
+def _fd(fun, base, direction, h=H):
+    return (fun(base + h * direction) - fun(base - h * direction)) / (2 * h)
+
+
+@pytest.mark.parametrize("T,M,d,eps,n_iter,weighted", [
+    (9, 13, 2, 0.05, 0, True),      # zero potentials: the field of the plain softmax barycentres
+    (9, 13, 2, 0.05, 1, False),
+    (11, 17, 2, 0.02, 6, True),
+    (7, 10, 3, 0.1, 4, True),
+])
+def test_field_vjp_matches_central_differences(orc, T, M, d, eps, n_iter, weighted):
+    x = wl.random_points(T, d, seed=31)
+    y = wl.random_points(M, d, seed=32)
+    b = wl.random_weights(M, seed=33) if weighted else None
+    r = wl.rng(34)
+    abar = r.standard_normal((T, d))
+    xbar, ybar, bbar = orc.sinkhorn_field_vjp(x, y, b, eps, n_iter, abar)
+    scale = max(np.abs(xbar).max(), np.abs(ybar).max(), 1.0)
+
+    dx = r.standard_normal((T, d))
+    fd = _fd(lambda xx: _field_obj(orc, xx, y, b, eps, n_iter, abar), x, dx)
+    assert np.sum(xbar * dx) == pytest.approx(fd, rel=1e-6, abs=1e-7 * scale)
+
+    dy = r.standard_normal((M, d))
+    fd = _fd(lambda yy: _field_obj(orc, x, yy, b, eps, n_iter, abar), y, dy)
+    assert np.sum(ybar * dy) == pytest.approx(fd, rel=1e-6, abs=1e-7 * scale)
+
+    if weighted:
+        db = r.standard_normal(M) * b          # relative perturbation keeps b > 0
+        fd = _fd(lambda bb: _field_obj(orc, x, y, bb, eps, n_iter, abar), b, db)
+        assert np.sum(bbar * db) == pytest.approx(fd, rel=1e-6, abs=1e-7 * scale)
+        # scaling all weights leaves the normalised measure, hence the field, unchanged
+        assert np.sum(bbar * b) == pytest.approx(0.0, abs=1e-9 * np.abs(bbar * b).sum())
+
+
+def test_field_vjp_single_coordinates(orc):
+    """Every coordinate of x and y separately on a tiny case (catches a
+    transposed index that a random direction could average away)."""
+    T, M, d, eps, n_iter = 4, 5, 2, 0.08, 3
+    x = wl.random_points(T, d, seed=41)
+    y = wl.random_points(M, d, seed=42)
+    abar = wl.rng(43).standard_normal((T, d))
+    xbar, ybar, _ = orc.sinkhorn_field_vjp(x, y, None, eps, n_iter, abar)
+    for arr, grad, which in ((x, xbar, 0), (y, ybar, 1)):
+        for i in range(arr.shape[0]):
+            for c in range(d):
+                e = np.zeros_like(arr)
+                e[i, c] = 1.0
+                if which == 0:
+                    fd = _fd(lambda xx: _field_obj(orc, xx, y, None, eps, n_iter, abar), x, e)
+                else:
+                    fd = _fd(lambda yy: _field_obj(orc, x, yy, None, eps, n_iter, abar), y, e)
+                assert grad[i, c] == pytest.approx(fd, rel=1e-6, abs=1e-7)
+
+
+def _lqr_case(T, n, m, seed, time_varying):
+    r = wl.rng(seed)
+    if time_varying:
+        A = np.stack([0.97 * np.linalg.qr(r.standard_normal((n, n)))[0] for _ in range(T)])
+    else:
+        A = np.broadcast_to(np.eye(n) + 0.05 * r.standard_normal((n, n)), (T, n, n)).copy()
+    B = r.standard_normal((T, n, m)) * 0.3
+    L = r.standard_normal((n, n))
+    Q = L @ L.T + 0.5 * np.eye(n)
+    Rm = 0.1 * np.eye(m) + 0.01 * np.diag(r.random(m))
+    return A, B, Q, Rm
+
+
+@pytest.mark.parametrize("T,n,m,tv", [(1, 2, 2, False), (6, 3, 2, True), (30, 4, 2, False),
+                                      (25, 4, 3, True)])
+def test_lqr_vjp_is_transpose_of_dense_kkt(orc, T, n, m, tv):
+    A, B, Q, Rm = _lqr_case(T, n, m, 50 + T, tv)
+    r = wl.rng(60 + T)
+    vbar = r.standard_normal((T, m))
+    got = orc.lqr_vjp(A, B, Q, Rm, vbar)
+    # dense: v = H^-1 G'Qb abar  =>  abar_bar = Qb G H^-1 vbar
+    Gm = np.zeros((T * n, T * m))
+    for s in range(T):
+        blk = B[s]
+        for t in range(s + 1, T + 1):
+            Gm[(t - 1) * n:t * n, s * m:(s + 1) * m] = blk
+            if t < T:
+                blk = A[t] @ blk
+    Qb = np.kron(np.eye(T), Q)
+    Hm = Gm.T @ Qb @ Gm + np.kron(np.eye(T), Rm)
+    want = (Qb @ Gm @ np.linalg.solve(Hm, vbar.reshape(-1))).reshape(T, n)
+    np.testing.assert_allclose(got, want, rtol=1e-9, atol=1e-10 * np.abs(want).max())
+    # the same through the forward oracle: <vbar, v(abar)> = <abar, vjp(vbar)>
+    abar = r.standard_normal((T, n))
+    v, _, _ = orc.lqr_track(A, B, Q, Rm, abar)
+    vd, _ = _dense_kkt(A, B, Q, Rm, abar)
+    np.testing.assert_allclose(v, vd, rtol=1e-9, atol=1e-11)
+    assert np.sum(vbar * v) == pytest.approx(np.sum(abar * got), rel=1e-10)
+
+
+@pytest.mark.parametrize("model", [wl.SINGLE_INT, wl.DOUBLE_INT, wl.UNICYCLE])
+def test_rollout_vjp_matches_central_differences(orc, model):
+    n, m = wl.MODEL_DIMS[model]
+    T, dt = 15, 0.05
+    r = wl.rng(70 + model)
+    s0 = np.concatenate([[0.2, 0.3], 0.3 * r.standard_normal(n - 2)])
+    u = r.standard_normal((T, m))
+    s = orc.rollout(model, s0, u, dt)
+    sbar = r.standard_normal((T + 1, n))
+    ubar, s0bar = orc.rollout_vjp(model, s, u, dt, sbar)
+    obj_u = lambda uu: float(np.sum(sbar * orc.rollout(model, s0, uu, dt)))
+    obj_s = lambda ss: float(np.sum(sbar * orc.rollout(model, ss, u, dt)))
+    du = r.standard_normal(u.shape)
+    assert np.sum(ubar * du) == pytest.approx(_fd(obj_u, u, du), rel=1e-7, abs=1e-9)
+    for c in range(n):
+        e = np.zeros(n)
+        e[c] = 1.0
+        assert s0bar[c] == pytest.approx(_fd(obj_s, s0, e), rel=1e-7, abs=1e-9)
+
+
+def _small_solve_case(model):
+    n, m = wl.MODEL_DIMS[model]
+    T, M, ML, dt = 20, 24, 30, 0.05
+    if model == wl.DOUBLE_INT:
+        s0, u0 = wl.double_int_init(T, dt)
+    else:
+        s0 = np.array([0.15, 0.2])
+        u0 = np.tile([[0.6, 0.5]], (T, 1))
+    y = wl.random_points(M, 2, seed=81, lo=0.2, hi=0.8)
+    b = wl.random_weights(M, seed=82)
+    yl = wl.random_points(ML, 2, seed=83, lo=0.1, hi=0.9)
+    Q = wl.coverage_Q(model)
+    Rm = 0.05 * np.eye(m)
+    return dict(model=model, dt=dt, s0=s0, u0=u0, d=2, y=y, b=b, eps=0.05, n_iter=6, Q=Q, R=Rm,
+                eta=0.5, n_outer=3, y_loss=yl, b_loss=None, eps_loss=0.05)
+
+
+@pytest.mark.parametrize("model", [wl.SINGLE_INT, wl.DOUBLE_INT])
+def test_solve_gradient_matches_central_differences(orc, model):
+    """Loss after three outer iterations, differentiated with respect to the
+    reference samples y, their weights b and the initial state s0."""
+    kw = _small_solve_case(model)
+    L, ybar, bbar, s0bar = orc.solve_sinkhorn_grad(**kw)
+    assert L > 0.0
+    r = wl.rng(90 + model)
+
+    def loss(**over):
+        k = dict(kw, **over)
+        return orc.solve_sinkhorn_grad(**k)[0]
+
+    dy = r.standard_normal(kw["y"].shape)
+    fd = _fd(lambda yy: loss(y=yy), kw["y"], dy, h=1e-5)
+    assert np.sum(ybar * dy) == pytest.approx(fd, rel=1e-5, abs=1e-9)
+    db = r.standard_normal(kw["b"].shape) * kw["b"]
+    fd = _fd(lambda bb: loss(b=bb), kw["b"], db, h=1e-5)
+    assert np.sum(bbar * db) == pytest.approx(fd, rel=1e-5, abs=1e-9)
+    for c in range(len(kw["s0"])):
+        e = np.zeros(len(kw["s0"]))
+        e[c] = 1.0
+        fd = _fd(lambda ss: loss(s0=ss), kw["s0"], e, h=1e-5)
+        assert s0bar[c] == pytest.approx(fd, rel=1e-5, abs=1e-9)
+
+
+def test_solve_gradient_rejects_trajectory_dependent_linearisation(orc):
+    kw = _small_solve_case(wl.DOUBLE_INT)
+    kw.update(model=wl.UNICYCLE, s0=np.array([0.1, 0.1, 0.3]), Q=wl.coverage_Q(wl.UNICYCLE))
+    with pytest.raises(ValueError):
+        orc.solve_sinkhorn_grad(**kw)
