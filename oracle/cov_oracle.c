@@ -911,72 +911,45 @@ void orc_rollout_vjp(int model, const double* s, const double* u, int T,
     free(B);
 }
 
-/* Gradient of the coverage loss through n_outer outer iterations (Sec. II-C)
- * by reverse mode with the controls u^k and trajectories s^k of every outer
- * iteration kept (the checkpoints), for time-invariant dynamics (A, B do
- * not depend on the trajectory).  The loss gradient with respect to the
- * final positions is -(1/T) times the field at converged potentials (the
- * envelope theorem, exact at convergence). */
-double orc_solve_sinkhorn_grad(int model, int T, double dt, const double* s0,
-                               int d, const double* y, const double* b, int M,
-                               double eps, int n_iter, const double* Q,
-                               const double* R, double eta, int n_outer,
-                               const double* u0, const double* y_loss,
-                               const double* b_loss, int M_loss,
-                               double eps_loss, double* ybar, double* bbar,
-                               double* s0bar) {
+/* Reverse sweep of the outer iteration (Sec. II-C) for time-invariant
+ * dynamics, given the trajectories of every outer iteration (the
+ * checkpoints s_hist[k] = s^k, k = 0..K-1, each [T+1][n]) and the loss
+ * gradient sbar_K with respect to the final trajectory s^K.  With A, B
+ * independent of the trajectory, v^k depends on s^{k-1} only through the
+ * field, so
+ *   ubar^K = rollout_vjp(sbar_K),
+ *   for k = K..1:  abar_bar = lqr_vjp(eta ubar^k);
+ *                  (xbar, ybar, bbar) += field_vjp(x^{k-1}; abar_bar);
+ *                  ubar^{k-1} = ubar^k + rollout_vjp(lift(xbar)).
+ * Outputs are accumulated into ybar [M][d], bbar [M] (may be NULL), s0bar [n]
+ * and written to u0bar [T][m] (may be NULL).  Returns 0, or -1 for a
+ * trajectory-dependent linearisation. */
+int orc_solve_backward(int model, int T, double dt, int d, const double* y,
+                       const double* b, int M, double eps, int n_iter,
+                       const double* Q, const double* R, double eta,
+                       int n_outer, const double* s_hist, const double* sbar_K,
+                       double* ybar, double* bbar, double* s0bar,
+                       double* u0bar) {
     int n, m;
-    if (orc_model_dims(model, &n, &m) != 0 || model == ORC_UNICYCLE || d > n) return NAN;
-    const int K = n_outer;
+    if (orc_model_dims(model, &n, &m) != 0 || model == ORC_UNICYCLE || d > n) return -1;
     const size_t us = (size_t)T * m, ss = (size_t)(T + 1) * n;
-    double* U = (double*)malloc(sizeof(double) * (K + 1) * us);
-    double* S = (double*)malloc(sizeof(double) * (K + 1) * ss);
-    double* x = (double*)malloc(sizeof(double) * (size_t)T * d);
-    double* a = (double*)malloc(sizeof(double) * (size_t)T * d);
-    double* abar = (double*)malloc(sizeof(double) * (size_t)T * n);
     double* A = (double*)malloc(sizeof(double) * (size_t)T * n * n);
     double* Bm = (double*)malloc(sizeof(double) * (size_t)T * n * m);
-    double* v = (double*)malloc(sizeof(double) * us);
-    double* z = (double*)malloc(sizeof(double) * ss);
-    double* f = (double*)malloc(sizeof(double) * (size_t)(T > M_loss ? T : M_loss));
-    double* g = (double*)malloc(sizeof(double) * (size_t)(M > M_loss ? M : M_loss));
-    double* p = (double*)malloc(sizeof(double) * (size_t)T);
-    memcpy(U, u0, sizeof(double) * us);
-    orc_rollout(model, s0, U, T, dt, S);
-    for (int k = 1; k <= K; ++k) {
-        const double* Sp = S + (size_t)(k - 1) * ss;
-        for (int i = 0; i < T; ++i)
-            for (int c = 0; c < d; ++c) x[(size_t)i * d + c] = Sp[(size_t)(i + 1) * n + c];
-        orc_sinkhorn(x, T, y, M, b, d, eps, n_iter, 0, f, g, p);
-        orc_sinkhorn_field(x, T, y, M, b, d, eps, g, p, NULL, 0, a);
-        for (int i = 0; i < T; ++i)
-            for (int r = 0; r < n; ++r) abar[(size_t)i * n + r] = r < d ? a[(size_t)i * d + r] : 0.0;
-        orc_linearize(model, Sp, U + (size_t)(k - 1) * us, T, dt, A, Bm);
-        orc_lqr_track(A, Bm, Q, R, abar, T, n, m, v, z, NULL);
-        for (size_t r = 0; r < us; ++r) U[(size_t)k * us + r] = U[(size_t)(k - 1) * us + r] + eta * v[r];
-        orc_rollout(model, s0, U + (size_t)k * us, T, dt, S + (size_t)k * ss);
-    }
-    /* loss and its gradient with respect to the final positions */
-    const double* SK = S + (size_t)K * ss;
-    for (int i = 0; i < T; ++i)
-        for (int c = 0; c < d; ++c) x[(size_t)i * d + c] = SK[(size_t)(i + 1) * n + c];
-    const double L = orc_sinkhorn_divergence(x, T, y_loss, M_loss, b_loss, d, eps_loss, 1e-12, 100000);
-    orc_sinkhorn_converge(x, T, y_loss, M_loss, b_loss, d, eps_loss, 1e-12, 100000, f, g, p);
-    orc_sinkhorn_field(x, T, y_loss, M_loss, b_loss, d, eps_loss, g, p, NULL, 0, a);
-    double* sbar = (double*)calloc(ss, sizeof(double));
     double* ubar = (double*)calloc(us, sizeof(double));
     double* ub2 = (double*)calloc(us, sizeof(double));
+    double* v = (double*)calloc(us, sizeof(double));
+    double* u0 = (double*)calloc(us, sizeof(double));
+    double* sbar = (double*)calloc(ss, sizeof(double));
+    double* x = (double*)malloc(sizeof(double) * (size_t)T * d);
     double* xbar = (double*)calloc((size_t)T * d, sizeof(double));
     double* fa = (double*)calloc((size_t)T * d, sizeof(double));
     double* abb = (double*)calloc((size_t)T * n, sizeof(double));
-    for (int i = 0; i < T; ++i)
-        for (int c = 0; c < d; ++c) sbar[(size_t)(i + 1) * n + c] = -a[(size_t)i * d + c] / T;
-    orc_rollout_vjp(model, SK, U + (size_t)K * us, T, dt, sbar, ubar, s0bar);
-    for (int k = K; k >= 1; --k) {
-        const double* Sp = S + (size_t)(k - 1) * ss;
-        const double* Up = U + (size_t)(k - 1) * us;
+    /* A, B do not depend on (s, u) for these models: take them anywhere */
+    orc_linearize(model, s_hist, u0, T, dt, A, Bm);
+    orc_rollout_vjp(model, s_hist, u0, T, dt, sbar_K, ubar, s0bar);
+    for (int k = n_outer; k >= 1; --k) {
+        const double* Sp = s_hist + (size_t)(k - 1) * ss;
         for (size_t r = 0; r < us; ++r) v[r] = eta * ubar[r];
-        orc_linearize(model, Sp, Up, T, dt, A, Bm);
         orc_lqr_vjp(A, Bm, Q, R, v, T, n, m, abb);
         for (int i = 0; i < T; ++i)
             for (int c = 0; c < d; ++c) {
@@ -988,10 +961,57 @@ double orc_solve_sinkhorn_grad(int model, int T, double dt, const double* s0,
         for (size_t r = 0; r < ss; ++r) sbar[r] = 0.0;
         for (int i = 0; i < T; ++i)
             for (int c = 0; c < d; ++c) sbar[(size_t)(i + 1) * n + c] = xbar[(size_t)i * d + c];
-        orc_rollout_vjp(model, Sp, Up, T, dt, sbar, ub2, s0bar);
+        orc_rollout_vjp(model, Sp, u0, T, dt, sbar, ub2, s0bar);
         for (size_t r = 0; r < us; ++r) ubar[r] += ub2[r];
     }
-    free(U); free(S); free(x); free(a); free(abar); free(A); free(Bm); free(v); free(z);
-    free(f); free(g); free(p); free(sbar); free(ubar); free(ub2); free(xbar); free(fa); free(abb);
+    if (u0bar) memcpy(u0bar, ubar, sizeof(double) * us);
+    free(A); free(Bm); free(ubar); free(ub2); free(v); free(u0); free(sbar);
+    free(x); free(xbar); free(fa); free(abb);
+    return 0;
+}
+
+/* Gradient of the coverage loss through n_outer outer iterations (Sec. II-C)
+ * by reverse mode with the trajectory of every outer iteration kept (the
+ * checkpoints), for time-invariant dynamics.  The loss is the Sinkhorn
+ * divergence of the final positions to (y_loss, b_loss); its gradient with
+ * respect to the final positions is -(1/T) times the field at converged
+ * potentials (the envelope theorem, exact at convergence). */
+double orc_solve_sinkhorn_grad(int model, int T, double dt, const double* s0,
+                               int d, const double* y, const double* b, int M,
+                               double eps, int n_iter, const double* Q,
+                               const double* R, double eta, int n_outer,
+                               const double* u0, const double* y_loss,
+                               const double* b_loss, int M_loss,
+                               double eps_loss, double* ybar, double* bbar,
+                               double* s0bar) {
+    int n, m;
+    if (orc_model_dims(model, &n, &m) != 0 || model == ORC_UNICYCLE || d > n) return NAN;
+    const size_t us = (size_t)T * m, ss = (size_t)(T + 1) * n;
+    double* S = (double*)malloc(sizeof(double) * (size_t)(n_outer + 1) * ss);
+    double* u = (double*)malloc(sizeof(double) * us);
+    double* x = (double*)malloc(sizeof(double) * (size_t)T * d);
+    double* a = (double*)malloc(sizeof(double) * (size_t)T * d);
+    double* f = (double*)malloc(sizeof(double) * (size_t)T);
+    double* g = (double*)malloc(sizeof(double) * (size_t)M_loss);
+    double* p = (double*)malloc(sizeof(double) * (size_t)T);
+    double* sbar = (double*)calloc(ss, sizeof(double));
+    memcpy(u, u0, sizeof(double) * us);
+    orc_rollout(model, s0, u, T, dt, S);
+    for (int k = 1; k <= n_outer; ++k) {
+        memcpy(S + (size_t)k * ss, S + (size_t)(k - 1) * ss, sizeof(double) * ss);
+        orc_solve(model, T, dt, s0, ORC_FIELD_SINKHORN, d, y, b, M, 0, NULL, NULL, NULL, eps, n_iter,
+                  0.0, Q, R, eta, 1, u, S + (size_t)k * ss);
+    }
+    const double* SK = S + (size_t)n_outer * ss;
+    for (int i = 0; i < T; ++i)
+        for (int c = 0; c < d; ++c) x[(size_t)i * d + c] = SK[(size_t)(i + 1) * n + c];
+    const double L = orc_sinkhorn_divergence(x, T, y_loss, M_loss, b_loss, d, eps_loss, 1e-12, 100000);
+    orc_sinkhorn_converge(x, T, y_loss, M_loss, b_loss, d, eps_loss, 1e-12, 100000, f, g, p);
+    orc_sinkhorn_field(x, T, y_loss, M_loss, b_loss, d, eps_loss, g, p, NULL, 0, a);
+    for (int i = 0; i < T; ++i)
+        for (int c = 0; c < d; ++c) sbar[(size_t)(i + 1) * n + c] = -a[(size_t)i * d + c] / T;
+    orc_solve_backward(model, T, dt, d, y, b, M, eps, n_iter, Q, R, eta, n_outer, S, sbar, ybar, bbar,
+                       s0bar, NULL);
+    free(S); free(u); free(x); free(a); free(f); free(g); free(p); free(sbar);
     return L;
 }

@@ -120,6 +120,7 @@ void orc_rollout_vjp(int model, const double* s, const double* u, int T,
  * after n_outer Sinkhorn-field outer iterations, with respect to the field's
  * reference samples y [M][d], raw weights b [M] (may be NULL) and s0 [n].
  * Time-invariant models only (single / double integrator).  Returns L. */
+int orc_solve_backward(int model, int T, double dt, int d, const double* y, const double* b, int M, double eps, int n_iter, const double* Q, const double* R, double eta, int n_outer, const double* s_hist, const double* sbar_K, double* ybar, double* bbar, double* s0bar, double* u0bar);
 double orc_solve_sinkhorn_grad(int model, int T, double dt, const double* s0,
                                int d, const double* y, const double* b, int M,
                                double eps, int n_iter, const double* Q,

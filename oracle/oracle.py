@@ -6,7 +6,7 @@ numpy arrays, C-contiguous, row-major, shapes as documented per function.
 Parity status per function:
   gmm_score, svgd_field, sinkhorn_*, sinkhorn_field, sinkhorn_divergence,
   linearize, rollout, lqr_track -- pinned (tests/test_oracle_*.py).
-  sinkhorn_field_vjp, lqr_vjp, rollout_vjp, solve_sinkhorn_grad -- pinned by
+  sinkhorn_field_vjp, lqr_vjp, rollout_vjp, solve_backward, solve_sinkhorn_grad -- pinned by
   central finite differences of the forward functions and, for lqr_vjp, by
   the transpose identity against the dense KKT solve (tests/test_oracle_adjoint.py).
   solve -- composition of pinned parts; pinned only by the one-iteration
@@ -83,6 +83,8 @@ def _declare(L):
         "orc_sinkhorn_field_vjp": (None, [_D, _i, _D, _i, _D, _i, _d, _i, _D, _D, _D, _D]),
         "orc_lqr_vjp": (None, [_D, _D, _D, _D, _D, _i, _i, _i, _D]),
         "orc_rollout_vjp": (None, [_i, _D, _D, _i, _d, _D, _D, _D]),
+        "orc_solve_backward": (_i, [_i, _i, _d, _i, _D, _D, _i, _d, _i, _D, _D, _d, _i, _D, _D,
+                                    _D, _D, _D, _D]),
         "orc_solve_sinkhorn_grad": (_d, [_i, _i, _d, _D, _i, _D, _D, _i, _d, _i, _D, _D, _d, _i,
                                          _D, _D, _D, _i, _d, _D, _D, _D]),
     }
@@ -344,3 +346,33 @@ def solve_sinkhorn_grad(model, dt, s0, u0, d, y, b, eps, n_iter, Q, R, eta, n_ou
     if not np.isfinite(L):
         raise ValueError("orc_solve_sinkhorn_grad: bad arguments")
     return float(L), ybar, bbar, s0bar
+
+
+def solve_history(model, dt, s0, u0, Q, R, eta, n_outer, *, d, y, b, eps, n_iter):
+    """Trajectories s^0..s^K of a Sinkhorn solve: [K+1][T+1][n] (s^k after k updates)."""
+    u = _f64(u0).copy()
+    hist = [rollout(model, s0, u, dt)]
+    for _ in range(n_outer):
+        u, s = solve(model, dt, s0, u, FIELD_SINKHORN, Q, R, eta, 1, d=d, y=y, b=b, eps=eps,
+                     n_iter=n_iter)
+        hist.append(s)
+    return np.stack(hist)
+
+
+def solve_backward(model, dt, d, y, b, eps, n_iter, Q, R, eta, s_hist, sbar_K):
+    """Reverse sweep through K = len(s_hist) outer iterations given the
+    checkpoints s_hist [K][T+1][n] (s^0..s^{K-1}) and dL/ds^K: returns (ybar [M][d], bbar [M] or None, s0bar [n], u0bar [T][m])."""
+    n, m = MODEL_DIMS[model]
+    y, Q, R, sh, sb = _f64(y), _f64(Q), _f64(R), _f64(s_hist), _f64(sbar_K)
+    b = None if b is None else _f64(b)
+    n_outer = sh.shape[0]
+    T = sh.shape[1] - 1
+    M = y.shape[0]
+    ybar, s0bar, u0bar = np.zeros((M, d)), np.zeros(n), np.zeros((T, m))
+    bbar = None if b is None else np.zeros(M)
+    rc = lib().orc_solve_backward(int(model), T, float(dt), int(d), _p(y), _p(b), M, float(eps),
+                                  int(n_iter), _p(Q), _p(R), float(eta), int(n_outer), _p(sh), _p(sb),
+                                  _p(ybar), _p(bbar), _p(s0bar), _p(u0bar))
+    if rc != 0:
+        raise ValueError("orc_solve_backward: bad arguments")
+    return ybar, bbar, s0bar, u0bar

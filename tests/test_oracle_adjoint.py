@@ -185,3 +185,31 @@ def test_solve_gradient_rejects_trajectory_dependent_linearisation(orc):
     kw.update(model=wl.UNICYCLE, s0=np.array([0.1, 0.1, 0.3]), Q=wl.coverage_Q(wl.UNICYCLE))
     with pytest.raises(ValueError):
         orc.solve_sinkhorn_grad(**kw)
+
+
+def test_backward_with_checkpoints_matches_central_differences_in_u0(orc):
+    """The reverse sweep from explicit checkpoints: its u0 gradient of a
+    linear functional of the final trajectory against central differences
+    (two outer iterations, the functional <sbar, s^K>)."""
+    kw = _small_solve_case(wl.DOUBLE_INT)
+    K = 2
+    r = wl.rng(99)
+    sbar = r.standard_normal((kw["u0"].shape[0] + 1, 4))
+    common = dict(d=2, y=kw["y"], b=kw["b"], eps=kw["eps"], n_iter=kw["n_iter"])
+    hist = orc.solve_history(kw["model"], kw["dt"], kw["s0"], kw["u0"], kw["Q"], kw["R"], kw["eta"], K,
+                             **common)
+    ybar, bbar, s0bar, u0bar = orc.solve_backward(kw["model"], kw["dt"], 2, kw["y"], kw["b"], kw["eps"],
+                                                  kw["n_iter"], kw["Q"], kw["R"], kw["eta"], hist[:K], sbar)
+
+    def fun(u0=kw["u0"], y=kw["y"], s0=kw["s0"]):
+        c = dict(common, y=y)
+        h = orc.solve_history(kw["model"], kw["dt"], s0, u0, kw["Q"], kw["R"], kw["eta"], K, **c)
+        return float(np.sum(sbar * h[-1]))
+
+    du = r.standard_normal(kw["u0"].shape)
+    assert np.sum(u0bar * du) == pytest.approx(_fd(lambda uu: fun(u0=uu), kw["u0"], du, h=1e-5), rel=1e-6)
+    dy = r.standard_normal(kw["y"].shape)
+    assert np.sum(ybar * dy) == pytest.approx(_fd(lambda yy: fun(y=yy), kw["y"], dy, h=1e-5), rel=1e-5)
+    e = np.zeros(4)
+    e[1] = 1.0
+    assert s0bar[1] == pytest.approx(_fd(lambda ss: fun(s0=ss), kw["s0"], e, h=1e-5), rel=1e-6)
