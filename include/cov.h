@@ -290,6 +290,88 @@ COV_API cov_status cov_solve_batched(cov_ctx* ctx, const cov_problem* probs, int
  * them is invalid). */
 COV_API size_t cov_workspace_size_batched(const cov_problem* probs, int n_probs);
 
+/* ---- adjoints: gradients through the outer iteration --------------------- */
+
+/* Vector-Jacobian product of the Sinkhorn-divergence field (the map
+ * (x, y, b) -> a of cov_field_sinkhorn, cold start, n_iter iterations) with
+ * abar: the exact reverse mode of the unrolled log-domain iterations
+ * (differentiability of the Sinkhorn iterations, Sec. II-B).  Every forward
+ * softmax is rebuilt from a recorded forward run (the potentials of every
+ * iteration are kept), so each reverse step is one all-pairs pass:
+ *   xbar = d<abar, a>/dx,  ybar = d<abar, a>/dy,  bbar = d<abar, a>/db
+ * with b the raw (unnormalised) weights.
+ *   x [T][d], y [M][d], abar [T][d] FP32 device;  b [M] FP32 device or NULL
+ *   xbar [T][d], ybar [M][d] FP32 device, written
+ *   bbar [M] FP32 device, written (ignored when b is NULL)
+ *   1 <= d <= 3 (COV_ERR_UNSUPPORTED above), n_iter >= 0.
+ * Workspace: cov_workspace_size_vjp(T, M, d, n_iter) bytes (the record of
+ * n_iter iterations: about 4 (2 + d)(n_iter + 2)(T + M) bytes plus the
+ * forward's own scratch). */
+COV_API size_t cov_workspace_size_vjp(int T, int M, int d, int n_iter);
+COV_API cov_status cov_field_sinkhorn_vjp(cov_ctx* ctx, const float* x, int T,
+                                          const float* y, const float* b, int M,
+                                          int d, float eps, int n_iter,
+                                          const float* abar, float* xbar,
+                                          float* ybar, float* bbar,
+                                          cov_stream_t stream);
+
+/* Vector-Jacobian product of cov_lqr_track's v(abar) (Eq. 9-10; v is linear
+ * in abar): abar_bar = Q G (G'QG + R)^-1 vbar with z = G v, computed as the
+ * same LQR with a linear control cost -2 vbar'w and no state target
+ * (Riccati gains, then the two affine scans).
+ *   A [T][n][n], B [T][n][m], vbar [T][m] FP64 device; Q, R FP64 HOST
+ *   abar_bar [T][n] FP64 device, written (row t-1 pairs with abar row t-1)
+ * Workspace: cov_workspace_size_lqr_vjp(T, n, m). */
+COV_API size_t cov_workspace_size_lqr_vjp(int T, int n, int m);
+COV_API cov_status cov_lqr_vjp(cov_ctx* ctx, const double* A, const double* B,
+                               const double* Q, const double* R,
+                               const double* vbar, int T, int n, int m,
+                               double* abar_bar, cov_stream_t stream);
+
+/* Vector-Jacobian product of cov_rollout at the trajectory s (Eq. 3, 8):
+ *   lambda_T = sbar_T, lambda_t = A_t' lambda_{t+1} + sbar_t,
+ *   ubar_t = B_t' lambda_{t+1}, s0bar = lambda_0,
+ * with A_t, B_t the linearisation at (s_t, u_t), as a chunked scan.
+ *   s [T+1][n], u [T][m], sbar [T+1][n] FP64 device
+ *   ubar [T][m], s0bar [n] FP64 device, written
+ * Workspace: cov_workspace_size_lqr_vjp(T, n, m). */
+COV_API cov_status cov_rollout_vjp(cov_ctx* ctx, int model, const double* s,
+                                   const double* u, int T, double dt,
+                                   const double* sbar, double* ubar,
+                                   double* s0bar, cov_stream_t stream);
+
+/* cov_solve that also keeps the checkpoints of a later cov_solve_backward:
+ * s_hist[k] = the trajectory entering outer iteration k, k = 0..n_outer-1.
+ *   s_hist [n_outer][T+1][n] FP64 device (NULL only when n_outer = 0). */
+COV_API cov_status cov_solve_checkpointed(cov_ctx* ctx, const cov_problem* prob,
+                                          int n_outer, double* u, double* s_out,
+                                          double* s_hist, cov_stream_t stream);
+
+/* Gradient of a scalar loss L(s^K) through n_outer = K outer iterations of
+ * cov_solve started from the control u0 (Sec. II-C), for a Sinkhorn field
+ * on a time-invariant model (COV_SINGLE_INT, COV_DOUBLE_INT; d <= 3;
+ * COV_ERR_UNSUPPORTED otherwise: the unicycle's A_t, B_t depend on the
+ * trajectory and would need second derivatives of the dynamics).  Reverse
+ * sweep over k = K..1: rollout adjoint, LQR adjoint (cov_lqr_vjp), field
+ * adjoint (cov_field_sinkhorn_vjp, recomputing the inner Sinkhorn
+ * iterations from the checkpoint s^{k-1}).
+ *   u0     [T][m] FP64 device: the control the forward started from
+ *   s_hist [K][T+1][n] FP64 device checkpoints from cov_solve_checkpointed,
+ *          or NULL: they are rebuilt by replaying the forward (K-1 extra
+ *          outer iterations)
+ *   sbar_K [T+1][n] FP64 device: dL/ds^K
+ *   ybar [M][d] FP32 device, bbar [M] FP32 device (NULL allowed only when
+ *          prob->b is NULL), written: dL/dy, dL/db
+ *   s0bar [n] FP64 device, written: dL/ds_0;  u0bar [T][m] FP64 device or
+ *          NULL, written: dL/du0
+ * Workspace: cov_workspace_size_backward(prob, K, s_hist == NULL). */
+COV_API size_t cov_workspace_size_backward(const cov_problem* prob, int n_outer, int replay);
+COV_API cov_status cov_solve_backward(cov_ctx* ctx, const cov_problem* prob,
+                                      int n_outer, const double* u0,
+                                      const double* s_hist, const double* sbar_K,
+                                      float* ybar, float* bbar, double* s0bar,
+                                      double* u0bar, cov_stream_t stream);
+
 /* ---- measurement -------------------------------------------------------- */
 
 /* Issue-rate probes for the roofline of the all-pairs kernels: each runs

@@ -34,7 +34,9 @@ EXPORTS = (
     "cov_gmm_score", "cov_field_svgd", "cov_field_sinkhorn", "cov_field_sinkhorn_noalloc", "cov_linearize",
     "cov_rollout",
     "cov_lqr_track", "cov_solve", "cov_solve_continue", "cov_solve_batched", "cov_workspace_size_batched",
-    "cov_probe_peaks",
+    "cov_probe_peaks", "cov_workspace_size_vjp", "cov_field_sinkhorn_vjp", "cov_workspace_size_lqr_vjp",
+    "cov_lqr_vjp", "cov_rollout_vjp", "cov_solve_checkpointed", "cov_workspace_size_backward",
+    "cov_solve_backward",
 )
 
 
@@ -92,6 +94,14 @@ def load(path: str = LIB_PATH):
                                    ctypes.POINTER(_P), _P]),
         "cov_workspace_size_batched": (_sz, [ctypes.POINTER(cov_problem), _i]),
         "cov_probe_peaks": (_i, [_P, _i, ctypes.POINTER(_d), _P]),
+        "cov_workspace_size_vjp": (_sz, [_i, _i, _i, _i]),
+        "cov_field_sinkhorn_vjp": (_i, [_P, _P, _i, _P, _P, _i, _i, _f, _i, _P, _P, _P, _P, _P]),
+        "cov_workspace_size_lqr_vjp": (_sz, [_i, _i, _i]),
+        "cov_lqr_vjp": (_i, [_P, _P, _P, _P, _P, _P, _i, _i, _i, _P, _P]),
+        "cov_rollout_vjp": (_i, [_P, _i, _P, _P, _i, _d, _P, _P, _P, _P]),
+        "cov_solve_checkpointed": (_i, [_P, ctypes.POINTER(cov_problem), _i, _P, _P, _P, _P]),
+        "cov_workspace_size_backward": (_sz, [ctypes.POINTER(cov_problem), _i, _i]),
+        "cov_solve_backward": (_i, [_P, ctypes.POINTER(cov_problem), _i, _P, _P, _P, _P, _P, _P, _P, _P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -165,6 +175,11 @@ class Context:
 
     def reserve_for(self, T, M=0, d=2, n=0, m=0):
         self._check(load().cov_ctx_reserve_for(self.h, int(T), int(M), int(d), int(n), int(m)), "cov_ctx_reserve_for")
+
+    def reserve(self, nbytes: int):
+        if int(nbytes) <= 0:
+            raise CovError(COV_ERR_INVALID_ARG, "workspace size")
+        self._check(load().cov_ctx_reserve(self.h, int(nbytes)), "cov_ctx_reserve")
 
     def set_option(self, key: int, value: int):
         self._check(load().cov_ctx_set_option(self.h, int(key), int(value)), "cov_ctx_set_option")
@@ -365,3 +380,97 @@ def cov_probe_peaks(ctx: Context, iters=4096, stream=None):
     keys = ("ffma_lane_ops_s", "ffma2_lane_ops_s", "ex2_lane_ops_s", "dfma_lane_ops_s", "dfma_latency_cycles",
             "sm_clock_mhz")
     return dict(zip(keys, list(out)))
+
+
+# -- adjoints -------------------------------------------------------------------
+def cov_field_sinkhorn_vjp(ctx: Context, x, y, eps, n_iter, abar, b=None, stream=None):
+    """(xbar, ybar, bbar) = gradients of <abar, field(x, y, b)> (bbar None for uniform weights)."""
+    T, d = x.shape
+    M = y.shape[0]
+    ctx.reserve(load().cov_workspace_size_vjp(T, M, d, int(n_iter)))
+    xbar = torch.empty_like(x)
+    ybar = torch.empty_like(y)
+    bbar = torch.empty_like(b) if b is not None else None
+    st = load().cov_field_sinkhorn_vjp(
+        ctx.h, _ptr(x, torch.float32, name="x"), T, _ptr(y, torch.float32, (M, d), "y"),
+        _ptr(b, torch.float32, (M,), "b"), M, d, float(eps), int(n_iter), _ptr(abar, torch.float32, (T, d), "abar"),
+        _ptr(xbar, torch.float32, (T, d), "xbar"), _ptr(ybar, torch.float32, (M, d), "ybar"),
+        _ptr(bbar, torch.float32, (M,), "bbar"), _stream(stream))
+    ctx._check(st, "cov_field_sinkhorn_vjp")
+    return xbar, ybar, bbar
+
+
+def cov_lqr_vjp(ctx: Context, A, B, Q, R, vbar, stream=None):
+    """abar_bar [T, n]: gradient of <vbar, v(abar)> of cov_lqr_track."""
+    T, n, m = B.shape
+    ctx.reserve(load().cov_workspace_size_lqr_vjp(T, n, m))
+    Qh = np.ascontiguousarray(np.asarray(Q, dtype=np.float64))
+    Rh = np.ascontiguousarray(np.asarray(R, dtype=np.float64))
+    if Qh.shape != (n, n) or Rh.shape != (m, m):
+        raise ValueError("Q must be [n,n] and R [m,m]")
+    out = torch.empty((T, n), device=B.device, dtype=torch.float64)
+    st = load().cov_lqr_vjp(ctx.h, _ptr(A, torch.float64, (T, n, n), "A"), _ptr(B, torch.float64, (T, n, m), "B"),
+                            Qh.ctypes.data_as(_P), Rh.ctypes.data_as(_P), _ptr(vbar, torch.float64, (T, m), "vbar"),
+                            T, n, m, _ptr(out, torch.float64, (T, n), "abar_bar"), _stream(stream))
+    ctx._check(st, "cov_lqr_vjp")
+    return out
+
+
+def cov_rollout_vjp(ctx: Context, model, s, u, dt, sbar, stream=None):
+    """(ubar [T, m], s0bar [n]): gradient of <sbar, rollout(s0, u)> at the trajectory s."""
+    n, m = MODEL_DIMS[model]
+    T = u.shape[0]
+    ctx.reserve(load().cov_workspace_size_lqr_vjp(T, n, m))
+    ubar = torch.empty((T, m), device=u.device, dtype=torch.float64)
+    s0bar = torch.empty(n, device=u.device, dtype=torch.float64)
+    st = load().cov_rollout_vjp(ctx.h, int(model), _ptr(s, torch.float64, (T + 1, n), "s"),
+                                _ptr(u, torch.float64, (T, m), "u"), T, float(dt),
+                                _ptr(sbar, torch.float64, (T + 1, n), "sbar"), _ptr(ubar, torch.float64, (T, m), "ubar"),
+                                _ptr(s0bar, torch.float64, (n,), "s0bar"), _stream(stream))
+    ctx._check(st, "cov_rollout_vjp")
+    return ubar, s0bar
+
+
+def cov_solve_checkpointed(ctx: Context, problem, n_outer, u, s_out=None, s_hist=None, stream=None):
+    """cov_solve that also returns the checkpoints s_hist [n_outer, T+1, n]."""
+    P, keep = problem
+    n, m = MODEL_DIMS[P.model]
+    T = P.T
+    ctx.reserve_for(T, P.M, P.d, n, m)
+    s_out = torch.empty((T + 1, n), device=u.device, dtype=torch.float64) if s_out is None else s_out
+    if s_hist is None:
+        s_hist = torch.empty((max(int(n_outer), 1), T + 1, n), device=u.device, dtype=torch.float64)
+    st = load().cov_solve_checkpointed(ctx.h, ctypes.byref(P), int(n_outer), _ptr(u, torch.float64, (T, m), "u"),
+                                       _ptr(s_out, torch.float64, (T + 1, n), "s_out"),
+                                       _ptr(s_hist, torch.float64, name="s_hist"), _stream(stream))
+    ctx._check(st, "cov_solve_checkpointed")
+    return s_out, s_hist
+
+
+def cov_solve_backward(ctx: Context, problem, n_outer, u0, sbar_K, s_hist=None, stream=None):
+    """(ybar [M, d], bbar [M] or None, s0bar [n], u0bar [T, m]) = dL/d(y, b, s0, u0)
+    given dL/ds^K = sbar_K and the checkpoints (replayed from u0 when None)."""
+    P, keep = problem
+    n, m = MODEL_DIMS[P.model]
+    T = P.T
+    need = int(load().cov_workspace_size_backward(ctypes.byref(P), int(n_outer), int(s_hist is None)))
+    if need == 0:
+        raise CovError(COV_ERR_UNSUPPORTED, "cov_solve_backward (Sinkhorn field, time-invariant model, d <= 3)")
+    ctx.reserve(need)
+    dev = u0.device
+    ybar = torch.empty((P.M, P.d), device=dev, dtype=torch.float32)
+    bbar = torch.empty(P.M, device=dev, dtype=torch.float32) if P.b else None
+    s0bar = torch.empty(n, device=dev, dtype=torch.float64)
+    u0bar = torch.empty((T, m), device=dev, dtype=torch.float64)
+    hist_p = None
+    if s_hist is not None:
+        hist_p = _ptr(s_hist, torch.float64, name="s_hist")
+        if s_hist.shape[0] < int(n_outer) or tuple(s_hist.shape[1:]) != (T + 1, n):
+            raise ValueError("s_hist must be [n_outer, T+1, n]")
+    st = load().cov_solve_backward(ctx.h, ctypes.byref(P), int(n_outer), _ptr(u0, torch.float64, (T, m), "u0"),
+                                   hist_p, _ptr(sbar_K, torch.float64, (T + 1, n), "sbar_K"),
+                                   _ptr(ybar, torch.float32, (P.M, P.d), "ybar"),
+                                   _ptr(bbar, torch.float32, (P.M,), "bbar"), _ptr(s0bar, torch.float64, (n,), "s0bar"),
+                                   _ptr(u0bar, torch.float64, (T, m), "u0bar"), _stream(stream))
+    ctx._check(st, "cov_solve_backward")
+    return ybar, bbar, s0bar, u0bar

@@ -75,6 +75,41 @@ cov_status sinkhorn_field_ws(cov_ctx* ctx, void* ws, size_t ws_bytes, const floa
                              const float* y, const float* b, int M, int d, float eps, int n_iter, int flags,
                              float* f, float* g, float* p, float* a_out, cudaStream_t stream,
                              const float* scal_given = nullptr);
+// Forward record of a fixed-iteration, cold-start Sinkhorn run (device
+// arrays inside the workspace), everything the adjoint needs.  Column terms
+// are in the base-2 prescaled form of the forward kernels:
+//   xhat = (x - centre) / sigma, sigma = sqrt(eps ln 2),
+//   hx^t = log2 a + f^t/(eps ln 2) - |xhat|^2, hy^t = log2 b + g^t/(eps ln 2) - |yhat|^2,
+//   hp^t = log2 a + p^t/(eps ln 2) - |xhat|^2;  padding entries hold -1e30.
+struct SkTape {
+    int n_iter, T, M, d, Tp, Mp;
+    float eps, sigma, log2a;
+    const float* xs;  // [d][Tp] xhat (padding 0)
+    const float* ys;  // [d][Mp] yhat
+    const float* lb;  // [Mp] log2 of the normalised weights
+    const float* scal;  // [16]: centre of y, 1/sum b (0 for uniform weights)
+    float* hx;        // [n+1][Tp]: slot t = hx^t (slot 0 the cold start; n = 0: the field's normaliser)
+    float* hy;        // [n+1][Mp]: slot t = hy^t (slot 0 the cold start)
+    float* hp;        // [n+2][Tp]: slot t = hp^t; slot n+1 = one more update (self-field normaliser)
+    float* Df;        // [n+1][d][Tp]: slot t = sum_j pi^f_ij (yhat_j - xhat_i) of the f-update t
+    float* Dg;        // [n+1][d][Mp]: slot t = sum_i pi^g_ji (xhat_i - yhat_j) of the g-update t
+    float* Dp;        // [n+1][d][Tp]: slot t = sum_k pi^p_ik (xhat_k - xhat_i) of the p-update t
+};
+size_t sinkhorn_tape_bytes(int T, int M, int d, int n_iter);
+// Runs the recorded forward; *used = the workspace bytes it occupies (the
+// tape must stay untouched while the adjoint reads it).
+cov_status sinkhorn_tape_ws(cov_ctx* ctx, void* ws, size_t ws_bytes, const float* x, int x_ld, int T,
+                            const float* y, const float* b, int M, int d, float eps, int n_iter,
+                            const float* scal_given, SkTape* tape, size_t* used, cudaStream_t stream);
+// Reverse mode of the field (adjoint.cu).  abar [T][abar_ld] FP32 device (the
+// first d entries of each row are used), xbar [T][xbar_ld] written;
+// ybar [M][d] and bbar [M] (NULL for uniform weights) written, or added to
+// when accumulate != 0.
+size_t sinkhorn_vjp_bytes(int T, int M, int d, int n_iter);
+cov_status sinkhorn_vjp_ws(cov_ctx* ctx, void* ws, size_t ws_bytes, const float* x, int x_ld, int T,
+                           const float* y, const float* b, int M, int d, float eps, int n_iter,
+                           const float* scal_given, const float* abar, int abar_ld, float* xbar, int xbar_ld,
+                           float* ybar, float* bbar, int accumulate, cudaStream_t stream);
 // Statistics of a reference set that every field evaluation on it needs:
 // scal[0..d) = mean of y, scal[8] = 1 / sum b (0 when b == NULL).
 void sinkhorn_reference_stats(const float* y, int M, int d, const float* b, float* scal, cudaStream_t stream);

@@ -33,7 +33,10 @@
 
 namespace cov {
 
-enum PairMode { M_G = 0, M_F = 1, M_P = 2, M_WY = 3, M_WX = 4, M_SVGD = 5, M_COUNT = 6 };
+// M_GW: a log-sum-exp update (epilogue as M_G) that also writes the
+// barycentric offset sum_j pi_ij (c_j - r_i) of its own softmax (the forward
+// record the adjoint needs).
+enum PairMode { M_G = 0, M_F = 1, M_P = 2, M_WY = 3, M_WX = 4, M_SVGD = 5, M_GW = 6, M_COUNT = 7 };
 
 constexpr int kTile = 256;   // columns per staged tile
 constexpr int kWarps = 4;    // warps per CTA, each takes a quarter of a tile
@@ -70,7 +73,7 @@ struct PairArgs {
 
 template <int D, int MODE>
 struct PairTraits {
-    static constexpr bool kW = (MODE == M_WY || MODE == M_WX);
+    static constexpr bool kW = (MODE == M_WY || MODE == M_WX || MODE == M_GW);
     static constexpr bool kSV = (MODE == M_SVGD);
     static constexpr int NC = kSV ? 2 * D : D + 1;             // staged components per column
     static constexpr int NACC = kSV ? D : (kW ? 2 + D : 2);    // partial components per row
@@ -241,6 +244,13 @@ __device__ __forceinline__ void epilogue(const PairArgs& a, int i, float m, floa
         else v = 0.5f * (a.log2a + a.in_h[i] - L);
         ok &= finitef(v);
         a.out_h[i] = v;
+        if constexpr (MODE == M_GW) {
+            if (a.bary) {
+                const float inv = 1.0f / s;
+#pragma unroll
+                for (int k = 0; k < D; ++k) a.bary[(size_t)k * a.row_ld + i] = acc[k] * inv;
+            }
+        }
     }
     if (!ok) raise_status(a.status, kDevNonfinite);
 }
@@ -663,6 +673,7 @@ static cudaError_t launch_pairs_mode(int family, const PairLaunch& L, int n, cud
         case M_WY: return launch_pairs_t<D, R, M_WY>(L, n, st, occ);
         case M_WX: return launch_pairs_t<D, R, M_WX>(L, n, st, occ);
         case M_SVGD: return launch_pairs_t<D, R, M_SVGD>(L, n, st, occ);
+        case M_GW: return launch_pairs_t<D, R, M_GW>(L, n, st, occ);
     }
     return cudaErrorInvalidValue;
 }
@@ -718,7 +729,7 @@ static cov_status run_pairs(cov_ctx* ctx, int d, int family, PairArgs* seg, cons
     int occ = 1;
     launch_pairs_d(d, R, family, PairLaunch{}, 0, st, &occ);
     const int slots = std::max(1, std::min(ctx->num_sms * std::min(occ, ctx->ctas_per_sm), kMaxSlots));
-    const int nacc = family == M_SVGD ? d : ((family == M_WY || family == M_WX) ? 2 + d : 2);
+    const int nacc = family == M_SVGD ? d : ((family == M_WY || family == M_WX || family == M_GW) ? 2 + d : 2);
     PairLaunch L{};
     if (nseg == 1) {
         plan_segment(seg[0], n_cols[0], RB, slots, counters + cnt_off[0]);
@@ -858,6 +869,150 @@ cov_status sinkhorn_field_ws(cov_ctx* ctx, void* ws, size_t ws_bytes, const floa
         sk_finish_kernel<<<(nf + 255) / 256, 256, 0, stream>>>(T, M, (float)epsln2, log2a, B, hp_cur, f, g, p,
                                                                ctx->status);
     }
+    if (cuda_failed(ctx, cudaGetLastError())) return COV_ERR_CUDA;
+    return COV_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Recorded forward for the adjoint: the same iterations as sinkhorn_field_ws
+// (cold start), every iteration's per-column terms kept in their own slot,
+// plus the barycentric offsets of each update's softmax and one further
+// self update whose log-sum-exp normalises the self term of the field.
+// ---------------------------------------------------------------------------
+__global__ void tape_pad_kernel(SkTape tp) {
+    // padding entries of every history slot: hx (n+1 slots) and hp (n+2
+    // slots) over [T, Tp), hy (n+1 slots) over [M, Mp)
+    const int n = tp.n_iter;
+    const int padx = tp.Tp - tp.T, pady = tp.Mp - tp.M;
+    const long long nx = padx > 0 ? (long long)(2 * n + 3) * padx : 0;
+    const long long ny = pady > 0 ? (long long)(n + 1) * pady : 0;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nx + ny;
+         e += (long long)gridDim.x * blockDim.x) {
+        if (e < nx) {
+            const long long slot = e / padx, i = tp.T + e % padx;
+            if (slot <= n) tp.hx[slot * tp.Tp + i] = kPadH;
+            else tp.hp[(slot - n - 1) * tp.Tp + i] = kPadH;
+        } else {
+            const long long f = e - nx, slot = f / pady, j = tp.M + f % pady;
+            tp.hy[slot * tp.Mp + j] = kPadH;
+        }
+    }
+}
+
+static void carve_tape(Carver& cv, int n_iter, int d, int Tp, int Mp, SkTape* tp) {
+    tp->hx = cv.take<float>((size_t)(n_iter + 1) * Tp);
+    tp->hy = cv.take<float>((size_t)(n_iter + 1) * Mp);
+    tp->hp = cv.take<float>((size_t)(n_iter + 2) * Tp);
+    tp->Df = cv.take<float>((size_t)(n_iter + 1) * d * Tp);
+    tp->Dg = cv.take<float>((size_t)(n_iter + 1) * d * Mp);
+    tp->Dp = cv.take<float>((size_t)(n_iter + 1) * d * Tp);
+}
+
+size_t sinkhorn_tape_bytes(int T, int M, int d, int n_iter) {
+    Carver cv(nullptr);
+    SkBufs B = carve_sinkhorn(cv, T, M, d);
+    SkTape tp{};
+    carve_tape(cv, n_iter, d, B.Tp, B.Mp, &tp);
+    return round_up(cv.off, 256);
+}
+
+cov_status sinkhorn_tape_ws(cov_ctx* ctx, void* ws, size_t ws_bytes, const float* x, int x_ld, int T,
+                            const float* y, const float* b, int M, int d, float eps, int n_iter,
+                            const float* scal_given, SkTape* tape, size_t* used, cudaStream_t stream) {
+    if (!ctx || !x || !y || !tape || T < 1 || M < 1 || d < 1 || d > COV_MAX_D || x_ld < d || n_iter < 0 ||
+        !(eps > 0.f) || !isfinite(eps))
+        return COV_ERR_INVALID_ARG;
+    Carver cv(ws);
+    SkBufs B = carve_sinkhorn(cv, T, M, d);
+    SkTape tp{};
+    carve_tape(cv, n_iter, d, B.Tp, B.Mp, &tp);
+    if (!ws || cv.off > ws_bytes) return COV_ERR_WORKSPACE;
+    if (used) *used = round_up(cv.off, 256);
+    const int n = n_iter;
+    const double epsln2 = (double)eps * 0.69314718055994531;
+    tp.n_iter = n;
+    tp.T = T; tp.M = M; tp.d = d; tp.Tp = B.Tp; tp.Mp = B.Mp;
+    tp.eps = eps;
+    tp.sigma = (float)sqrt(epsln2);
+    tp.log2a = (float)(-log2((double)T));
+    tp.xs = B.xs; tp.ys = B.ys; tp.lb = B.lb;
+    // slot 0 of each history is the cold start written by the prep kernel
+    B.hx = tp.hx;
+    B.hy = tp.hy;
+    B.hp0 = tp.hp;
+    if (cuda_failed(ctx, cudaMemsetAsync(B.counters, 0, sizeof(unsigned) * M_COUNT * B.cnt_ld, stream)))
+        return COV_ERR_CUDA;
+    if (scal_given)
+        B.scal = const_cast<float*>(scal_given);
+    else
+        sk_centre_kernel<<<1, 1024, 0, stream>>>(y, M, d, b, B.scal);
+    const int np = std::max(B.Tp, B.Mp);
+    sk_prep_kernel<<<(np + 255) / 256, 256, 0, stream>>>(x, x_ld, T, y, M, b, d, (float)(1.0 / tp.sigma),
+                                                         (float)(1.0 / epsln2), tp.log2a, 0, nullptr, nullptr,
+                                                         nullptr, B, ctx->status);
+    tape_pad_kernel<<<std::min(1024, (int)((2LL * n + 2) * B.Tp / 256 + 1)), 256, 0, stream>>>(tp);
+    if (cuda_failed(ctx, cudaGetLastError())) return COV_ERR_CUDA;
+    PairArgs base{};
+    base.status = ctx->status;
+    base.spin_limit = ctx->spin_limit;
+    base.log2a = tp.log2a;
+    base.part = B.part;
+    base.pre_ok = 1;
+    bool first = true;
+    cov_status r = COV_OK;
+    for (int t = 1; t <= n && r == COV_OK; ++t) {
+        float* hx_prev = tp.hx + (size_t)(t - 1) * B.Tp;
+        float* hx_t = tp.hx + (size_t)t * B.Tp;
+        float* hy_t = tp.hy + (size_t)t * B.Mp;
+        float* hp_prev = tp.hp + (size_t)(t - 1) * B.Tp;
+        float* hp_t = tp.hp + (size_t)t * B.Tp;
+        PairArgs sg[2] = {base, base};
+        sg[0].rows = B.ys; sg[0].row_ld = B.Mp; sg[0].n_rows = M;
+        sg[0].cols = B.xs; sg[0].colh = hx_prev; sg[0].col_ld = B.Tp;
+        sg[0].out_h = hy_t; sg[0].in_h = B.lb; sg[0].emode = M_G;
+        sg[0].bary = tp.Dg + (size_t)t * d * B.Mp;
+        sg[1].rows = B.xs; sg[1].row_ld = B.Tp; sg[1].n_rows = T;
+        sg[1].cols = B.xs; sg[1].colh = hp_prev; sg[1].col_ld = B.Tp;
+        sg[1].out_h = hp_t; sg[1].in_h = hp_prev; sg[1].emode = M_P;
+        sg[1].bary = tp.Dp + (size_t)t * d * B.Tp;
+        if (first) sg[0].pre_ok = sg[1].pre_ok = 0;
+        first = false;
+        const int ncA[2] = {T, T}, coA[2] = {M_G * B.cnt_ld, M_P * B.cnt_ld};
+        r = run_pairs(ctx, d, M_GW, sg, ncA, 2, coA, B.counters, stream);
+        if (r != COV_OK) break;
+        PairArgs a = base;
+        a.rows = B.xs; a.row_ld = B.Tp; a.n_rows = T;
+        a.cols = B.ys; a.colh = hy_t; a.col_ld = B.Mp;
+        a.out_h = hx_t; a.emode = M_F;
+        a.bary = tp.Df + (size_t)t * d * B.Tp;
+        const int ncB[1] = {M}, coB[1] = {M_F * B.cnt_ld};
+        r = run_pairs(ctx, d, M_GW, &a, ncB, 1, coB, B.counters, stream);
+    }
+    if (r != COV_OK) return r;
+    // the cross normaliser of the field: f-update on the last g (only needed
+    // when no iteration ran; otherwise it is hx^n itself)
+    if (n == 0) {
+        PairArgs a = base;
+        a.rows = B.xs; a.row_ld = B.Tp; a.n_rows = T;
+        a.cols = B.ys; a.colh = tp.hy; a.col_ld = B.Mp;
+        a.out_h = tp.hx; a.emode = M_F;
+        if (first) a.pre_ok = 0;
+        first = false;
+        const int nc[1] = {M}, co[1] = {M_F * B.cnt_ld};
+        r = run_pairs(ctx, d, M_G, &a, nc, 1, co, B.counters, stream);
+        if (r != COV_OK) return r;
+    }
+    {   // one more self update: hp^{n+1}, the normaliser of the self softmax
+        PairArgs a = base;
+        a.rows = B.xs; a.row_ld = B.Tp; a.n_rows = T;
+        a.cols = B.xs; a.colh = tp.hp + (size_t)n * B.Tp; a.col_ld = B.Tp;
+        a.out_h = tp.hp + (size_t)(n + 1) * B.Tp; a.in_h = a.colh; a.emode = M_P;
+        const int nc[1] = {T}, co[1] = {M_P * B.cnt_ld};
+        r = run_pairs(ctx, d, M_G, &a, nc, 1, co, B.counters, stream);
+        if (r != COV_OK) return r;
+    }
+    tp.scal = B.scal;
+    *tape = tp;
     if (cuda_failed(ctx, cudaGetLastError())) return COV_ERR_CUDA;
     return COV_OK;
 }

@@ -106,7 +106,7 @@ struct SubBlocks {
 
 // ---------------------------------------------------------------------------
 // Riccati recursion (one warp).  Outputs per step: K_t [MC][N], M_t [N][N],
-// N_t [MC][N].
+// N_t [MC][N], S_t^-1 [MC][MC] (the last for the adjoint).
 // ---------------------------------------------------------------------------
 template <int N, int MC>
 struct RicSmem {
@@ -119,7 +119,7 @@ template <int N, int MC>
 __global__ void __launch_bounds__(32, 1) riccati_kernel(const double* __restrict__ A, const double* __restrict__ B,
                                                         LqrConst C, int T, double* __restrict__ Kg,
                                                         double* __restrict__ Mg, double* __restrict__ Ng,
-                                                        unsigned* status) {
+                                                        double* __restrict__ Sg, unsigned* status) {
     __shared__ __align__(16) RicSmem<N, MC> sm;
     const int lane = threadIdx.x;
     bool spd_ok = true;
@@ -188,6 +188,7 @@ __global__ void __launch_bounds__(32, 1) riccati_kernel(const double* __restrict
             {
                 double Si[MC * MC];
                 spd_ok &= spd_inverse<MC>(sm.S, Si);
+                if (lane < MC * MC) Sg[(size_t)t * MC * MC + lane] = Si[lane];
                 if (lane < 2 * MC * N) {
                     const bool isK = lane < MC * N;
                     const int f = isK ? lane : lane - MC * N;
@@ -241,13 +242,15 @@ __global__ void __launch_bounds__(32, 1) riccati_kernel(const double* __restrict
 // ---------------------------------------------------------------------------
 
 // Compose the chunk's affine map (Phi | phi) and write its forcing terms:
-//   BWD: c_t = -Q_t abar_t (abar row t-1, t >= 1; c_0 = 0); map p_lo = Phi p_{hi+1} + phi
+//   BWD: c_t = -Q_t abar_t (abar row t-1, t >= 1; c_0 = 0), or c_t = cin[t]
+//        when cin is given;                                 map p_lo = Phi p_{hi+1} + phi
 //   FWD: e_t = -B_t k_t;                                    map z_{hi+1} = Phi z_lo + phi
 template <int N, int MC, bool BWD>
 __global__ void __launch_bounds__(32) compose_kernel(const double* __restrict__ Mg, LqrConst Cq,
                                                      const double* __restrict__ abar, const double* __restrict__ Bg,
-                                                     const double* __restrict__ kg, int T, int C,
-                                                     double* __restrict__ force, double* __restrict__ maps) {
+                                                     const double* __restrict__ kg, const double* __restrict__ cin,
+                                                     int T, int C, double* __restrict__ force,
+                                                     double* __restrict__ maps) {
     extern __shared__ __align__(16) double dyn[];
     __shared__ __align__(16) double Ms[2][kSB][N * N];
     __shared__ double X[N * (N + 1)];
@@ -258,7 +261,9 @@ __global__ void __launch_bounds__(32) compose_kernel(const double* __restrict__ 
         const int t = lo + i / N, r = i % N;
         double acc = 0.0;
         if constexpr (BWD) {
-            if (t >= 1) {
+            if (cin) {
+                acc = cin[(size_t)t * N + r];
+            } else if (t >= 1) {
 #pragma unroll
                 for (int q = 0; q < N; ++q) acc = fma(-Cq.Q[r * N + q], abar[(size_t)(t - 1) * N + q], acc);
             }
@@ -310,10 +315,12 @@ __global__ void __launch_bounds__(32) compose_kernel(const double* __restrict__ 
 }
 
 // Chain the chunk maps (one warp): bnd[c] = the value entering chunk c
-// (BWD: p_{hi+1}; FWD: z_lo).
+// (BWD: p_{hi+1}, starting from p_T = -Q abar_T or the given w0; FWD: z_lo,
+// starting from 0).
 template <int N, bool BWD>
 __global__ void __launch_bounds__(32, 1) boundaries_kernel(const double* __restrict__ maps, int n_chunks, LqrConst Cq,
-                                                           const double* __restrict__ abar, int T,
+                                                           const double* __restrict__ abar,
+                                                           const double* __restrict__ w0, int T,
                                                            double* __restrict__ bnd) {
     extern __shared__ __align__(16) double mp[];  // [n_chunks][N][N+1]
     __shared__ double w[N];
@@ -324,8 +331,12 @@ __global__ void __launch_bounds__(32, 1) boundaries_kernel(const double* __restr
     if (lane < N) {
         double acc = 0.0;
         if constexpr (BWD) {
+            if (w0) {
+                acc = w0[lane];
+            } else {
 #pragma unroll
-            for (int q = 0; q < N; ++q) acc = fma(-Cq.Q[lane * N + q], abar[(size_t)(T - 1) * N + q], acc);
+                for (int q = 0; q < N; ++q) acc = fma(-Cq.Q[lane * N + q], abar[(size_t)(T - 1) * N + q], acc);
+            }
         }
         w[lane] = acc;
     }
@@ -348,13 +359,15 @@ __global__ void __launch_bounds__(32, 1) boundaries_kernel(const double* __restr
 }
 
 // Fill the steps of one chunk from its boundary value.
-//   BWD: p_t = M_t' p_{t+1} + c_t and k_t = N_t p_{t+1}      -> k [T][MC]
+//   BWD: p_t = M_t' p_{t+1} + c_t and k_t = N_t p_{t+1} (+ kx_t when given)
+//        -> k [T][MC]; p_0 -> p0_out when given
 //   FWD: z_{t+1} = M_t z_t + e_t and v_t = -K_t z_t - k_t   -> v [T][MC], z [T+1][N]
 template <int N, int MC, bool BWD>
 __global__ void __launch_bounds__(32) fill_kernel(const double* __restrict__ Mg, const double* __restrict__ Wg,
                                                   const double* __restrict__ force, const double* __restrict__ kin,
-                                                  const double* __restrict__ bnd, int T, int C,
-                                                  double* __restrict__ out_m, double* __restrict__ z_out) {
+                                                  const double* __restrict__ bnd, const double* __restrict__ kx,
+                                                  int T, int C, double* __restrict__ out_m,
+                                                  double* __restrict__ z_out, double* __restrict__ p0_out) {
     __shared__ __align__(16) double Ms[2][kSB][N * N];
     __shared__ __align__(16) double Ws[2][kSB][MC * N];  // BWD: N_t, FWD: K_t
     __shared__ __align__(16) double Fs[2][kSB][N];
@@ -409,7 +422,7 @@ __global__ void __launch_bounds__(32) fill_kernel(const double* __restrict__ Mg,
                     xo = ro * N;
                 }
                 const double* wv = (isO && !BWD) ? wn : w;
-                acc = isS ? Fs[buf][j][lane] : (BWD ? 0.0 : -Ks[buf][j][ro]);
+                acc = isS ? Fs[buf][j][lane] : (BWD ? (kx ? kx[(size_t)t * MC + ro] : 0.0) : -Ks[buf][j][ro]);
 #pragma unroll
                 for (int q = 0; q < N; ++q) acc = fma(X[q * xs + xo], wv[q], acc);
             }
@@ -425,6 +438,57 @@ __global__ void __launch_bounds__(32) fill_kernel(const double* __restrict__ Mg,
         }
         __syncwarp();
     }
+    if (BWD && p0_out && blockIdx.x == 0 && lane < N) p0_out[lane] = w[lane];
+}
+
+// ---------------------------------------------------------------------------
+// Adjoints.  The LQR solution v(abar) is linear in abar: v = H^-1 G'Q abar
+// with z = G v and H = G'QG + R (z_0 = 0), so its VJP abar_bar = Q G H^-1 vbar
+// is the same LQR with the linear control cost -2 vbar_t'w_t and no state
+// target.  With the gains of the same Riccati recursion:
+//   p_T = 0,  p_t = M_t' p_{t+1} + K_t' vbar_t,
+//   k_t = N_t p_{t+1} - S_t^-1 vbar_t,
+//   z_0 = 0,  z_{t+1} = M_t z_t - B_t k_t,   abar_bar_t = Q z_{t+1}.
+// The rollout's VJP is the backward affine recursion
+//   lambda_T = sbar_T,  lambda_t = A_t' lambda_{t+1} + sbar_t,  ubar_t = B_t' lambda_{t+1},
+// i.e. the same scan with M_t := A_t, N_t := B_t', c_t = sbar_t; s0bar = lambda_0.
+// ---------------------------------------------------------------------------
+__global__ void lqr_vjp_prep_kernel(const double* __restrict__ K, const double* __restrict__ Si,
+                                    const double* __restrict__ vbar, int T, int n, int m, double* __restrict__ c,
+                                    double* __restrict__ kx) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= T) return;
+    const double* Kt = K + (size_t)t * m * n;
+    const double* St = Si + (size_t)t * m * m;
+    const double* vt = vbar + (size_t)t * m;
+    for (int r = 0; r < n; ++r) {
+        double acc = 0.0;
+        for (int q = 0; q < m; ++q) acc = fma(Kt[q * n + r], vt[q], acc);
+        c[(size_t)t * n + r] = acc;
+    }
+    for (int r = 0; r < m; ++r) {
+        double acc = 0.0;
+        for (int q = 0; q < m; ++q) acc = fma(-St[r * m + q], vt[q], acc);
+        kx[(size_t)t * m + r] = acc;
+    }
+}
+
+__global__ void lqr_vjp_out_kernel(LqrConst C, const double* __restrict__ z, int T, int n, double* __restrict__ out) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= T) return;
+    const double* zt = z + (size_t)(t + 1) * n;
+    for (int r = 0; r < n; ++r) {
+        double acc = 0.0;
+        for (int q = 0; q < n; ++q) acc = fma(C.Q[r * n + q], zt[q], acc);
+        out[(size_t)t * n + r] = acc;
+    }
+}
+
+__global__ void transpose_steps_kernel(const double* __restrict__ B, int T, int n, int m, double* __restrict__ Bt) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= T * n * m) return;
+    const int t = e / (n * m), f = e % (n * m), r = f / m, q = f % m;  // B_t[r][q] -> Bt_t[q][r]
+    Bt[(size_t)t * n * m + q * n + r] = B[e];
 }
 
 // ---------------------------------------------------------------------------
@@ -588,7 +652,10 @@ static bool scan_plan(int T, ScanPlan* p) {
     return true;
 }
 
-size_t lqr_gain_doubles(int T, int n, int m) { return (size_t)T * (2 * (size_t)m * n + (size_t)n * n); }
+// Gains per step: K [m][n], M [n][n], N [m][n], S^-1 [m][m].
+size_t lqr_gain_doubles(int T, int n, int m) {
+    return (size_t)T * (2 * (size_t)m * n + (size_t)n * n + (size_t)m * m);
+}
 
 struct AffineBufs {
     double *fc, *fe, *k, *maps, *bnd;
@@ -631,7 +698,8 @@ static void launch_riccati_t(const double* A, const double* B, const LqrConst& C
     double* K = gains;
     double* M = gains + (size_t)T * MC * N;
     double* Nt = M + (size_t)T * N * N;
-    riccati_kernel<N, MC><<<1, 32, 0, s>>>(A, B, C, T, K, M, Nt, st);
+    double* Si = Nt + (size_t)T * MC * N;
+    riccati_kernel<N, MC><<<1, 32, 0, s>>>(A, B, C, T, K, M, Nt, Si, st);
 }
 
 template <int N, int MC>
@@ -642,12 +710,15 @@ static void launch_affine_t(const double* B, const double* gains, const LqrConst
     const double* Nt = M + (size_t)T * N * N;
     const size_t fsb = sizeof(double) * pl.C * N;
     const size_t mpb = sizeof(double) * pl.n_chunks * N * (N + 1);
-    compose_kernel<N, MC, true><<<pl.n_chunks, 32, fsb, s>>>(M, C, abar, nullptr, nullptr, T, pl.C, ab.fc, ab.maps);
-    boundaries_kernel<N, true><<<1, 32, mpb, s>>>(ab.maps, pl.n_chunks, C, abar, T, ab.bnd);
-    fill_kernel<N, MC, true><<<pl.n_chunks, 32, 0, s>>>(M, Nt, ab.fc, nullptr, ab.bnd, T, pl.C, ab.k, nullptr);
-    compose_kernel<N, MC, false><<<pl.n_chunks, 32, fsb, s>>>(M, C, nullptr, B, ab.k, T, pl.C, ab.fe, ab.maps);
-    boundaries_kernel<N, false><<<1, 32, mpb, s>>>(ab.maps, pl.n_chunks, C, nullptr, T, ab.bnd);
-    fill_kernel<N, MC, false><<<pl.n_chunks, 32, 0, s>>>(M, K, ab.fe, ab.k, ab.bnd, T, pl.C, v, z);
+    compose_kernel<N, MC, true><<<pl.n_chunks, 32, fsb, s>>>(M, C, abar, nullptr, nullptr, nullptr, T, pl.C, ab.fc,
+                                                             ab.maps);
+    boundaries_kernel<N, true><<<1, 32, mpb, s>>>(ab.maps, pl.n_chunks, C, abar, nullptr, T, ab.bnd);
+    fill_kernel<N, MC, true><<<pl.n_chunks, 32, 0, s>>>(M, Nt, ab.fc, nullptr, ab.bnd, nullptr, T, pl.C, ab.k, nullptr,
+                                                        nullptr);
+    compose_kernel<N, MC, false><<<pl.n_chunks, 32, fsb, s>>>(M, C, nullptr, B, ab.k, nullptr, T, pl.C, ab.fe,
+                                                              ab.maps);
+    boundaries_kernel<N, false><<<1, 32, mpb, s>>>(ab.maps, pl.n_chunks, C, nullptr, nullptr, T, ab.bnd);
+    fill_kernel<N, MC, false><<<pl.n_chunks, 32, 0, s>>>(M, K, ab.fe, ab.k, ab.bnd, nullptr, T, pl.C, v, z, nullptr);
 }
 
 template <int N, int MC>
@@ -722,6 +793,106 @@ cov_status lqr_track_ws(cov_ctx* ctx, void* ws, size_t ws_bytes, const double* A
                       stream);
 }
 
+struct AdjScanBufs {
+    AffineBufs ab;
+    double *c, *kx, *vtmp, *z, *zero, *Bt;
+};
+
+static AdjScanBufs carve_adj_scan(Carver& cv, int T, int n, int m) {
+    AdjScanBufs b{};
+    b.ab = carve_affine(cv, T, n, m);
+    b.c = cv.take<double>((size_t)T * n);
+    b.kx = cv.take<double>((size_t)T * m);
+    b.vtmp = cv.take<double>((size_t)T * m);
+    b.z = cv.take<double>((size_t)(T + 1) * n);
+    b.zero = cv.take<double>(COV_MAX_N);
+    b.Bt = cv.take<double>((size_t)T * n * m);
+    return b;
+}
+
+size_t lqr_adj_ws_bytes(int T, int n, int m) {
+    Carver cv(nullptr);
+    carve_adj_scan(cv, T, n, m);
+    return round_up(cv.off, 256);
+}
+
+template <int N, int MC>
+static void launch_lqr_vjp_t(const double* B, const double* gains, const LqrConst& C, const double* vbar, int T,
+                             const ScanPlan& pl, const AdjScanBufs& b, double* out, cudaStream_t s) {
+    const double* K = gains;
+    const double* M = gains + (size_t)T * MC * N;
+    const double* Nt = M + (size_t)T * N * N;
+    const double* Si = Nt + (size_t)T * MC * N;
+    const size_t fsb = sizeof(double) * pl.C * N;
+    const size_t mpb = sizeof(double) * pl.n_chunks * N * (N + 1);
+    const AffineBufs& ab = b.ab;
+    lqr_vjp_prep_kernel<<<(T + 127) / 128, 128, 0, s>>>(K, Si, vbar, T, N, MC, b.c, b.kx);
+    compose_kernel<N, MC, true><<<pl.n_chunks, 32, fsb, s>>>(M, C, nullptr, nullptr, nullptr, b.c, T, pl.C, ab.fc,
+                                                             ab.maps);
+    boundaries_kernel<N, true><<<1, 32, mpb, s>>>(ab.maps, pl.n_chunks, C, nullptr, b.zero, T, ab.bnd);
+    fill_kernel<N, MC, true><<<pl.n_chunks, 32, 0, s>>>(M, Nt, ab.fc, nullptr, ab.bnd, b.kx, T, pl.C, ab.k, nullptr,
+                                                        nullptr);
+    compose_kernel<N, MC, false><<<pl.n_chunks, 32, fsb, s>>>(M, C, nullptr, B, ab.k, nullptr, T, pl.C, ab.fe,
+                                                              ab.maps);
+    boundaries_kernel<N, false><<<1, 32, mpb, s>>>(ab.maps, pl.n_chunks, C, nullptr, nullptr, T, ab.bnd);
+    fill_kernel<N, MC, false><<<pl.n_chunks, 32, 0, s>>>(M, K, ab.fe, ab.k, ab.bnd, nullptr, T, pl.C, b.vtmp, b.z,
+                                                         nullptr);
+    lqr_vjp_out_kernel<<<(T + 127) / 128, 128, 0, s>>>(C, b.z, T, N, out);
+}
+
+template <int N, int MC>
+static void launch_rollout_vjp_t(const double* A, const double* B, const double* sbar, int T, const ScanPlan& pl,
+                                 const AdjScanBufs& b, double* ubar, double* s0bar, cudaStream_t s) {
+    const size_t fsb = sizeof(double) * pl.C * N;
+    const size_t mpb = sizeof(double) * pl.n_chunks * N * (N + 1);
+    const AffineBufs& ab = b.ab;
+    const LqrConst C{};
+    transpose_steps_kernel<<<(T * N * MC + 255) / 256, 256, 0, s>>>(B, T, N, MC, b.Bt);
+    compose_kernel<N, MC, true><<<pl.n_chunks, 32, fsb, s>>>(A, C, nullptr, nullptr, nullptr, sbar, T, pl.C, ab.fc,
+                                                             ab.maps);
+    boundaries_kernel<N, true><<<1, 32, mpb, s>>>(ab.maps, pl.n_chunks, C, nullptr, sbar + (size_t)T * N, T, ab.bnd);
+    fill_kernel<N, MC, true><<<pl.n_chunks, 32, 0, s>>>(A, b.Bt, ab.fc, nullptr, ab.bnd, nullptr, T, pl.C, ubar,
+                                                        nullptr, s0bar);
+}
+
+cov_status lqr_vjp_ws(cov_ctx* ctx, void* ws, size_t ws_bytes, int n, int m, const double* B, const double* gains,
+                      const double* Q, const double* vbar, int T, double* abar_bar, cudaStream_t stream) {
+    LqrConst C;
+    const double R1[COV_MAX_M * COV_MAX_M] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+    if (!make_lqr_const(Q, R1, n, m, &C)) return COV_ERR_INVALID_ARG;
+    ScanPlan pl;
+    if (!scan_plan(T, &pl)) return COV_ERR_UNSUPPORTED;
+    Carver cv(ws);
+    const AdjScanBufs b = carve_adj_scan(cv, T, n, m);
+    if (!ws || cv.off > ws_bytes) return COV_ERR_WORKSPACE;
+    if (cuda_failed(ctx, cudaMemsetAsync(b.zero, 0, sizeof(double) * COV_MAX_N, stream))) return COV_ERR_CUDA;
+#define COV_LVJP_CASE(NN, MM)                                                            \
+    if (n == NN && m == MM) {                                                            \
+        launch_lqr_vjp_t<NN, MM>(B, gains, C, vbar, T, pl, b, abar_bar, stream);         \
+        return cuda_failed(ctx, cudaGetLastError()) ? COV_ERR_CUDA : COV_OK;            \
+    }
+    COV_LQR_DISPATCH(COV_LVJP_CASE)
+#undef COV_LVJP_CASE
+    return COV_ERR_UNSUPPORTED;
+}
+
+cov_status rollout_vjp_ws(cov_ctx* ctx, void* ws, size_t ws_bytes, int n, int m, const double* A, const double* B,
+                          const double* sbar, int T, double* ubar, double* s0bar, cudaStream_t stream) {
+    ScanPlan pl;
+    if (!scan_plan(T, &pl)) return COV_ERR_UNSUPPORTED;
+    Carver cv(ws);
+    const AdjScanBufs b = carve_adj_scan(cv, T, n, m);
+    if (!ws || cv.off > ws_bytes) return COV_ERR_WORKSPACE;
+#define COV_RVJP_CASE(NN, MM)                                                              \
+    if (n == NN && m == MM) {                                                              \
+        launch_rollout_vjp_t<NN, MM>(A, B, sbar, T, pl, b, ubar, s0bar, stream);           \
+        return cuda_failed(ctx, cudaGetLastError()) ? COV_ERR_CUDA : COV_OK;              \
+    }
+    COV_LQR_DISPATCH(COV_RVJP_CASE)
+#undef COV_RVJP_CASE
+    return COV_ERR_UNSUPPORTED;
+}
+
 cov_status update_rollout(cov_ctx* ctx, int model, const double* s0, double* u, const double* v, double eta, int T,
                           double dt, double* s, cudaStream_t stream) {
     int n, m;
@@ -773,4 +944,48 @@ extern "C" cov_status cov_lqr_track(cov_ctx* ctx, const double* A, const double*
     if (cudaSetDevice(ctx->device) != cudaSuccess) return COV_ERR_CUDA;
     return cov::lqr_track_ws(ctx, ctx->ws, ctx->ws_bytes, A, B, Q, R, abar, T, n, m, v_out, z_out,
                              (cudaStream_t)stream);
+}
+
+extern "C" size_t cov_workspace_size_lqr_vjp(int T, int n, int m) {
+    if (T < 1 || n < 1 || n > COV_MAX_N || m < 1 || m > COV_MAX_M) return 0;
+    const size_t gains = cov::round_up(sizeof(double) * cov::lqr_gain_doubles(T, n, m), 256);
+    const size_t lin = cov::round_up(sizeof(double) * (size_t)T * n * n, 256) +
+                       cov::round_up(sizeof(double) * (size_t)T * n * m, 256);
+    return std::max(gains, lin) + cov::lqr_adj_ws_bytes(T, n, m) + 4096;
+}
+
+extern "C" cov_status cov_lqr_vjp(cov_ctx* ctx, const double* A, const double* B, const double* Q, const double* R,
+                                  const double* vbar, int T, int n, int m, double* abar_bar, cov_stream_t stream) {
+    if (!ctx || !A || !B || !Q || !R || !vbar || !abar_bar || T < 1 || n < 1 || n > COV_MAX_N || m < 1 ||
+        m > COV_MAX_M)
+        return COV_ERR_INVALID_ARG;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return COV_ERR_CUDA;
+    cov::Carver cv(ctx->ws);
+    double* gains = cv.take<double>(cov::lqr_gain_doubles(T, n, m));
+    const size_t used = cov::round_up(cv.off, 256);
+    if (!ctx->ws || used > ctx->ws_bytes) return COV_ERR_WORKSPACE;
+    cudaStream_t st = (cudaStream_t)stream;
+    cov_status s = cov::lqr_riccati(ctx, n, m, A, B, Q, R, T, gains, st);
+    if (s != COV_OK) return s;
+    return cov::lqr_vjp_ws(ctx, static_cast<char*>(ctx->ws) + used, ctx->ws_bytes - used, n, m, B, gains, Q, vbar, T,
+                           abar_bar, st);
+}
+
+extern "C" cov_status cov_rollout_vjp(cov_ctx* ctx, int model, const double* s, const double* u, int T, double dt,
+                                      const double* sbar, double* ubar, double* s0bar, cov_stream_t stream) {
+    int n, m;
+    if (!ctx || !s || !u || !sbar || !ubar || !s0bar || T < 1 || !isfinite(dt) ||
+        cov::model_dims(model, &n, &m) != 0)
+        return COV_ERR_INVALID_ARG;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return COV_ERR_CUDA;
+    cov::Carver cv(ctx->ws);
+    double* A = cv.take<double>((size_t)T * n * n);
+    double* B = cv.take<double>((size_t)T * n * m);
+    const size_t used = cov::round_up(cv.off, 256);
+    if (!ctx->ws || used > ctx->ws_bytes) return COV_ERR_WORKSPACE;
+    cudaStream_t st = (cudaStream_t)stream;
+    cov_status r = cov::linearize_launch(ctx, model, s, u, T, dt, A, B, st);
+    if (r != COV_OK) return r;
+    return cov::rollout_vjp_ws(ctx, static_cast<char*>(ctx->ws) + used, ctx->ws_bytes - used, n, m, A, B, sbar, T,
+                               ubar, s0bar, st);
 }

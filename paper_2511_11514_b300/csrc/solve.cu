@@ -135,7 +135,7 @@ static cov_status enqueue_iteration(cov_ctx* ctx, const cov_problem* P, int n, i
 
 namespace cov {
 static cov_status solve_impl(cov_ctx* ctx, const cov_problem* prob, int n_outer, double* u, double* s_out,
-                             cudaStream_t stream, bool initial_rollout);
+                             cudaStream_t stream, bool initial_rollout, double* s_hist = nullptr);
 }
 
 extern "C" cov_status cov_solve(cov_ctx* ctx, const cov_problem* prob, int n_outer, double* u, double* s_out,
@@ -148,8 +148,14 @@ extern "C" cov_status cov_solve_continue(cov_ctx* ctx, const cov_problem* prob, 
     return cov::solve_impl(ctx, prob, n_outer, u, s, (cudaStream_t)stream, false);
 }
 
+extern "C" cov_status cov_solve_checkpointed(cov_ctx* ctx, const cov_problem* prob, int n_outer, double* u,
+                                             double* s_out, double* s_hist, cov_stream_t stream) {
+    if (!s_hist && n_outer > 0) return COV_ERR_INVALID_ARG;
+    return cov::solve_impl(ctx, prob, n_outer, u, s_out, (cudaStream_t)stream, true, s_hist);
+}
+
 static cov_status cov::solve_impl(cov_ctx* ctx, const cov_problem* prob, int n_outer, double* u, double* s_out,
-                                  cudaStream_t stream, bool initial_rollout) {
+                                  cudaStream_t stream, bool initial_rollout, double* s_hist) {
     using namespace cov;
     int n, m;
     if (!ctx || !u || !s_out || n_outer < 0) return COV_ERR_INVALID_ARG;
@@ -195,8 +201,16 @@ static cov_status cov::solve_impl(cov_ctx* ctx, const cov_problem* prob, int n_o
         }
     }
 
+    // checkpoint k: the trajectory entering outer iteration k
+    const size_t ss_bytes = sizeof(double) * (size_t)(prob->T + 1) * n;
+    auto checkpoint = [&](int k) {
+        return s_hist ? cuda_failed(ctx, cudaMemcpyAsync(s_hist + (size_t)k * (prob->T + 1) * n, s_out, ss_bytes,
+                                                         cudaMemcpyDeviceToDevice, st))
+                      : false;
+    };
     if (!ctx->use_graph) {
         for (int k = 0; k < n_outer; ++k) {
+            if (checkpoint(k)) return COV_ERR_CUDA;
             r = enqueue_iteration(ctx, prob, n, m, b, rest, rest_bytes, u, s_out, st);
             if (r != COV_OK) return r;
         }
@@ -237,8 +251,10 @@ static cov_status cov::solve_impl(cov_ctx* ctx, const cov_problem* prob, int n_o
         ctx->solve_graph.exec = ex;
         ctx->solve_graph.key = key;
     }
-    for (int k = 0; k < n_outer; ++k)
+    for (int k = 0; k < n_outer; ++k) {
+        if (checkpoint(k)) return COV_ERR_CUDA;
         if (cuda_failed(ctx, cudaGraphLaunch(ctx->solve_graph.exec, st))) return COV_ERR_CUDA;
+    }
     return COV_OK;
 }
 
@@ -418,5 +434,175 @@ extern "C" cov_status cov_solve_batched(cov_ctx* ctx, const cov_problem* probs, 
     }
     for (int k = 0; k < n_outer; ++k)
         if (cuda_failed(ctx, cudaGraphLaunch(ctx->batch_graph.exec, st))) return COV_ERR_CUDA;
+    return COV_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Gradient through the outer iteration (reverse mode, checkpointed).  For a
+// time-invariant model A, B do not depend on the trajectory, so v^k depends
+// on the previous trajectory s^{k-1} only through the field, and
+//   ubar^K = rollout_vjp(sbar_K),
+//   k = K..1:  abar_bar = lqr_vjp(eta ubar^k);
+//              (xbar, ybar, bbar) += field_vjp(x^{k-1}; abar_bar);
+//              ubar^{k-1} = ubar^k + rollout_vjp(lift(xbar)),
+//   s0bar = sum of the rollout adjoints' lambda_0, u0bar = ubar^0.
+// The trajectories s^0..s^{K-1} are the checkpoints (given, or rebuilt by
+// replaying the forward from u0); the field VJP recomputes its Sinkhorn
+// iterations from each checkpoint.
+// ---------------------------------------------------------------------------
+namespace cov {
+size_t lqr_adj_ws_bytes(int T, int n, int m);
+size_t lqr_ws_bytes(int T, int n, int m);
+cov_status lqr_vjp_ws(cov_ctx* ctx, void* ws, size_t ws_bytes, int n, int m, const double* B, const double* gains,
+                      const double* Q, const double* vbar, int T, double* abar_bar, cudaStream_t stream);
+cov_status rollout_vjp_ws(cov_ctx* ctx, void* ws, size_t ws_bytes, int n, int m, const double* A, const double* B,
+                          const double* sbar, int T, double* ubar, double* s0bar, cudaStream_t stream);
+
+struct BackBufs {
+    float *xbar, *abf;
+    double *abb, *sbar, *ubar, *ub2, *vbar, *lam0, *u, *hist;
+};
+
+static BackBufs carve_back(Carver& cv, int T, int d, int n, int m, int n_hist) {
+    BackBufs b{};
+    b.xbar = cv.take<float>((size_t)T * d);
+    b.abf = cv.take<float>((size_t)T * d);
+    b.abb = cv.take<double>((size_t)T * n);
+    b.sbar = cv.take<double>((size_t)(T + 1) * n);
+    b.ubar = cv.take<double>((size_t)T * m);
+    b.ub2 = cv.take<double>((size_t)T * m);
+    b.vbar = cv.take<double>((size_t)T * m);
+    b.lam0 = cv.take<double>(COV_MAX_N);
+    b.u = cv.take<double>((size_t)T * m);
+    b.hist = n_hist > 0 ? cv.take<double>((size_t)n_hist * (T + 1) * n) : nullptr;
+    return b;
+}
+
+static bool backward_supported(const cov_problem* P) {
+    return P->field == COV_FIELD_SINKHORN && model_is_lti(P->model) && P->d <= 3;
+}
+
+static size_t backward_ws_bytes(const cov_problem* P, int n, int m, int K, bool replay) {
+    Carver cv(nullptr);
+    carve_solve(cv, P->T, P->d, n, m);
+    carve_back(cv, P->T, P->d, n, m, replay ? K : 0);
+    const size_t used = round_up(cv.off, 256);
+    size_t rest = std::max(sinkhorn_vjp_bytes(P->T, P->M, P->d, P->n_iter), lqr_adj_ws_bytes(P->T, n, m));
+    if (replay) rest = std::max(rest, std::max(sinkhorn_ws_bytes(P->T, P->M, P->d), lqr_ws_bytes(P->T, n, m)));
+    return used + rest + 4096;
+}
+
+// vbar = eta ubar
+__global__ void back_scale_kernel(const double* __restrict__ ubar, double eta, int N, double* __restrict__ vbar) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N) vbar[i] = eta * ubar[i];
+}
+// abf = the coverage components of abar_bar, in FP32
+__global__ void narrow_kernel(const double* __restrict__ abb, int T, int n, int d, float* __restrict__ abf) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= T) return;
+    for (int k = 0; k < d; ++k) abf[(size_t)i * d + k] = (float)abb[(size_t)i * n + k];
+}
+// sbar = the sample adjoint lifted to the trajectory (s_0 does not move)
+__global__ void lift_bar_kernel(const float* __restrict__ xbar, int T, int n, int d, double* __restrict__ sbar) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i > T) return;
+    for (int r = 0; r < n; ++r)
+        sbar[(size_t)i * n + r] = (i >= 1 && r < d) ? (double)xbar[(size_t)(i - 1) * d + r] : 0.0;
+}
+// ubar += ub2; s0bar += lam0
+__global__ void back_accum_kernel(double* __restrict__ ubar, const double* __restrict__ ub2, int N,
+                                  double* __restrict__ s0bar, const double* __restrict__ lam0, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N) ubar[i] += ub2[i];
+    if (i < n) s0bar[i] += lam0[i];
+}
+
+}  // namespace cov
+
+extern "C" size_t cov_workspace_size_backward(const cov_problem* prob, int n_outer, int replay) {
+    int n, m;
+    if (!prob || n_outer < 0 || cov::validate(prob, &n, &m) != COV_OK || !cov::backward_supported(prob)) return 0;
+    return cov::backward_ws_bytes(prob, n, m, n_outer, replay != 0);
+}
+
+extern "C" cov_status cov_solve_backward(cov_ctx* ctx, const cov_problem* prob, int n_outer, const double* u0,
+                                         const double* s_hist, const double* sbar_K, float* ybar, float* bbar,
+                                         double* s0bar, double* u0bar, cov_stream_t stream) {
+    using namespace cov;
+    int n, m;
+    if (!ctx || n_outer < 0 || !u0 || !sbar_K || !ybar || !s0bar) return COV_ERR_INVALID_ARG;
+    cov_status r = validate(prob, &n, &m);
+    if (r != COV_OK) return r;
+    if (!backward_supported(prob)) return COV_ERR_UNSUPPORTED;
+    if (prob->b && !bbar) return COV_ERR_INVALID_ARG;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return COV_ERR_CUDA;
+    const int T = prob->T, d = prob->d, K = n_outer;
+    const bool replay = (s_hist == nullptr);
+    Carver cv(ctx->ws);
+    SolveBufs sb = carve_solve(cv, T, d, n, m);
+    BackBufs bb = carve_back(cv, T, d, n, m, replay ? K : 0);
+    const size_t used = round_up(cv.off, 256);
+    if (!ctx->ws || used > ctx->ws_bytes) return COV_ERR_WORKSPACE;
+    void* rest = static_cast<char*>(ctx->ws) + used;
+    const size_t rest_bytes = ctx->ws_bytes - used;
+    if (backward_ws_bytes(prob, n, m, K, replay) > ctx->ws_bytes) return COV_ERR_WORKSPACE;
+    ctx->gains_key = 0;  // the solve buffers are reused here
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t ss = (size_t)(T + 1) * n;
+    const int nb = (T + 256) / 256;
+
+    sinkhorn_reference_stats(prob->y, prob->M, d, prob->b, sb.scal, st);
+    const double* hist = s_hist;
+    if (replay) {
+        // rebuild the checkpoints s^0..s^{K-1} from u0
+        if (cuda_failed(ctx, cudaMemcpyAsync(bb.u, u0, sizeof(double) * T * m, cudaMemcpyDeviceToDevice, st)))
+            return COV_ERR_CUDA;
+        if (K > 0) {
+            r = update_rollout(ctx, prob->model, prob->s0, bb.u, nullptr, 0.0, T, prob->dt, bb.hist, st);
+            if (r != COV_OK) return r;
+        }
+        hist = bb.hist;
+    }
+    // A, B (time-invariant: any state will do) and the Riccati gains
+    r = linearize_launch(ctx, prob->model, K > 0 ? hist : sbar_K, u0, T, prob->dt, sb.A, sb.B, st);
+    if (r != COV_OK) return r;
+    r = lqr_riccati(ctx, n, m, sb.A, sb.B, prob->Q, prob->R, T, sb.gains, st);
+    if (r != COV_OK) return r;
+    if (replay) {
+        for (int k = 1; k < K; ++k) {
+            double* sk = bb.hist + (size_t)k * ss;
+            if (cuda_failed(ctx, cudaMemcpyAsync(sk, sk - ss, sizeof(double) * ss, cudaMemcpyDeviceToDevice, st)))
+                return COV_ERR_CUDA;
+            r = enqueue_iteration(ctx, prob, n, m, sb, rest, rest_bytes, bb.u, sk, st);
+            if (r != COV_OK) return r;
+        }
+    }
+    // final rollout adjoint
+    r = rollout_vjp_ws(ctx, rest, rest_bytes, n, m, sb.A, sb.B, sbar_K, T, bb.ubar, s0bar, st);
+    if (r != COV_OK) return r;
+    if (K == 0) {
+        if (cuda_failed(ctx, cudaMemsetAsync(ybar, 0, sizeof(float) * prob->M * d, st))) return COV_ERR_CUDA;
+        if (bbar && cuda_failed(ctx, cudaMemsetAsync(bbar, 0, sizeof(float) * prob->M, st))) return COV_ERR_CUDA;
+    }
+    const int Tm = T * m;
+    for (int k = K; k >= 1; --k) {
+        back_scale_kernel<<<(Tm + 255) / 256, 256, 0, st>>>(bb.ubar, prob->eta, Tm, bb.vbar);
+        r = lqr_vjp_ws(ctx, rest, rest_bytes, n, m, sb.B, sb.gains, prob->Q, bb.vbar, T, bb.abb, st);
+        if (r != COV_OK) return r;
+        narrow_kernel<<<nb, 256, 0, st>>>(bb.abb, T, n, d, bb.abf);
+        extract_kernel<<<nb, 256, 0, st>>>(hist + (size_t)(k - 1) * ss, T, n, d, sb.x);
+        r = sinkhorn_vjp_ws(ctx, rest, rest_bytes, sb.x, d, T, prob->y, prob->b, prob->M, d, prob->eps,
+                            prob->n_iter, sb.scal, bb.abf, d, bb.xbar, d, ybar, prob->b ? bbar : nullptr,
+                            k != K ? 1 : 0, st);
+        if (r != COV_OK) return r;
+        lift_bar_kernel<<<nb, 256, 0, st>>>(bb.xbar, T, n, d, bb.sbar);
+        r = rollout_vjp_ws(ctx, rest, rest_bytes, n, m, sb.A, sb.B, bb.sbar, T, bb.ub2, bb.lam0, st);
+        if (r != COV_OK) return r;
+        back_accum_kernel<<<(Tm + 255) / 256, 256, 0, st>>>(bb.ubar, bb.ub2, Tm, s0bar, bb.lam0, n);
+    }
+    if (u0bar && cuda_failed(ctx, cudaMemcpyAsync(u0bar, bb.ubar, sizeof(double) * Tm, cudaMemcpyDeviceToDevice, st)))
+        return COV_ERR_CUDA;
+    if (cuda_failed(ctx, cudaGetLastError())) return COV_ERR_CUDA;
     return COV_OK;
 }
