@@ -63,6 +63,8 @@ def parse_args():
                     help="time cov_solve_batched on this many uneven problems (and the same problems one by one)")
     ap.add_argument("--no-large-roofline", action="store_true",
                     help="skip the all-pairs roofline at T = 65536, M = 262144")
+    ap.add_argument("--adjoint", action="store_true",
+                    help="time the differentiation workload: forward and backward through 20 outer iterations")
     return ap.parse_args()
 
 
@@ -465,12 +467,100 @@ def run_batched(args):
     return 0
 
 
+def run_adjoint(args):
+    """Differentiation workload: the coverage loss (Sinkhorn divergence of the
+    final positions to a held-out 4-component mixture) after K = 20 outer
+    iterations (T = 2048, M = 8192, eps = 0.005, 50 iterations), differentiated
+    with respect to the reference mixture's means, log-sigmas and logits
+    (samples by reparameterisation) and the initial state.  A step is one
+    forward (reparameterisation, checkpointed solve, loss) and one backward
+    (loss gradient, reverse sweep, reparameterisation chain), each timed with
+    CUDA events; the line reports the backward / forward time ratio."""
+    import torch
+
+    from paper_2511_11514_b300 import autograd as ag
+    from paper_2511_11514_b300 import binding as cov
+
+    torch.cuda.set_device(0)
+    w = wl.ADJOINT_DOUBLE_T2048
+    inst = wl.make_instance(w)
+    ctx = cov.Context(0)
+    dev = torch.device("cuda", 0)
+    gw, gmu, gsig = inst.gmm
+    mu = torch.tensor(gmu, dtype=torch.float32, device=dev, requires_grad=True)
+    log_sigma = torch.tensor(np.log(gsig), dtype=torch.float32, device=dev, requires_grad=True)
+    logits = torch.tensor(np.log(gw), dtype=torch.float32, device=dev, requires_grad=True)
+    s0 = torch.tensor(inst.s0, dtype=torch.float64, requires_grad=True)
+    u0 = torch.as_tensor(inst.u0, dtype=torch.float64, device=dev)
+    xi = ag.standard_draws(w.M, 2, seed=w.seed + 2000, device=dev)
+    lw, lmu, lsig = wl.gmm_params(4, w.extra["loss_seed"])
+    y_loss = torch.as_tensor(wl.f32_pair(wl.gmm_samples(lw, lmu, lsig, w.extra["loss_M"], w.extra["loss_seed"] + 1000))[1],
+                             dtype=torch.float32, device=dev)
+    eps_l, it_l = w.extra["loss_eps"], w.extra["loss_iters"]
+    q_ref = ag.reference_self_term(ctx, y_loss, eps_l, it_l)
+    spec = dict(model=w.model, dt=w.dt, Q=inst.Q, R=inst.R, eta=w.eta, eps=w.eps, n_iter=w.n_iter,
+                n_outer=w.n_outer)
+
+    def forward():
+        y, b = ag.gmm_reference(mu, log_sigma, logits, xi)
+        s_K = ag.CoverageSolve.apply(y, b, s0, u0, spec, ctx)
+        return ag.SinkhornLoss.apply(s_K[1:, :2].float().contiguous(), y_loss, eps_l, it_l, ctx, q_ref)
+
+    params = (mu, log_sigma, logits, s0)
+    for _ in range(max(1, args.warmup)):
+        for p in params:
+            p.grad = None
+        forward().backward()
+    torch.cuda.synchronize()
+    clocks = Clocks(0)
+    clocks.start()
+    fw, bw, losses = [], [], []
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    for _ in range(args.steps):
+        for p in params:
+            p.grad = None
+        torch.cuda.synchronize()
+        ev[0].record()
+        L = forward()
+        ev[1].record()
+        L.backward()
+        ev[2].record()
+        torch.cuda.synchronize()
+        fw.append(ev[0].elapsed_time(ev[1]))
+        bw.append(ev[1].elapsed_time(ev[2]))
+        losses.append(float(L.detach()))
+    clk = clocks.stop()
+    st, flags = ctx.device_status()
+    if st != cov.COV_OK:
+        raise SystemExit(f"device status {cov.status_string(st)} flags {flags}")
+    f_ms, b_ms = statistics.median(fw), statistics.median(bw)
+    pairs_fwd = w.n_outer * w.pairs_per_field
+    line = {"metric": "backward/forward time ratio of the coverage-loss gradient", "value": b_ms / f_ms,
+            "unit": "x", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": f_ms + b_ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 fields, f64 LQR/rollout", "data": "synthetic (seeded Philox mixtures)",
+            "config": {"workload": w.name, "T": w.T, "M": w.M, "eps": w.eps, "n_iter": w.n_iter,
+                       "n_outer": w.n_outer, "loss": f"S_eps to held-out 4-GMM, M={w.extra['loss_M']}, "
+                       f"eps={eps_l}, {it_l} iterations", "params": "means, log-sigmas, logits, s0",
+                       "pairs_forward": pairs_fwd, "l2": "not flushed (forward and backward alternate)"},
+            "ms_forward": f_ms, "ms_backward": b_ms,
+            "forward_pairs_per_s": pairs_fwd / (f_ms * 1e-3), "loss": losses[-1],
+            "grad_norms": {"mu": float(mu.grad.norm()), "log_sigma": float(log_sigma.grad.norm()),
+                           "logits": float(logits.grad.norm()), "s0": float(s0.grad.norm())},
+            "clocks": clk}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.batched:
         return run_batched(args)
+    if args.adjoint:
+        return run_adjoint(args)
     return run_ours(args)
 
 

@@ -8,10 +8,10 @@ without the built library.
 """
 import importlib
 
-__all__ = ["binding", "workloads", "build_lib", "autotune"]
+__all__ = ["binding", "workloads", "build_lib", "autotune", "autograd"]
 
 
 def __getattr__(name):
-    if name in ("binding", "build_lib", "autotune"):
+    if name in ("binding", "build_lib", "autotune", "autograd"):
         return importlib.import_module(f"{__name__}.{name}")
     raise AttributeError(name)

@@ -1,0 +1,107 @@
+"""Differentiable coverage synthesis on the libcov adjoint (torch.autograd).
+
+Three pieces, each a thin ``torch.autograd.Function`` over C-ABI calls (the
+forward and backward arithmetic runs in libcov's kernels):
+
+* ``CoverageSolve``: the final trajectory s^K after K outer iterations of
+  Sec. II-C (Sinkhorn field, time-invariant model) as a function of the
+  reference samples y, their weights b and the initial state s0.  Forward:
+  ``cov_solve_checkpointed`` keeps the trajectory entering every outer
+  iteration; backward: ``cov_solve_backward`` runs the reverse sweep (rollout,
+  LQR and field adjoints) from those checkpoints.
+* ``SinkhornLoss``: the debiased Sinkhorn divergence of Eq. 6 between the
+  samples x and a held-out reference set (uniform weights).  Its value is the
+  dual value <a, f> + <b, g> - <a, p> - <b, q> at the potentials after
+  n_iter iterations; its gradient is the envelope formula -(1/T) times the
+  field of Eq. 7 at those potentials (exact at convergence).
+* ``gmm_reference``: reference samples and weights of a Gaussian mixture by
+  reparameterisation, y_j = mu_c + sigma_c xi_j (M/K fixed standard normal
+  draws per component c) and b_j = softmax(logits)_c / (M/K), in plain torch
+  ops so that autograd carries dL/dy, dL/db to the mixture parameters.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import binding as cov
+
+
+class CoverageSolve(torch.autograd.Function):
+    """s_K = CoverageSolve.apply(y, b, s0, u0, spec, ctx).
+
+    y [M, d] float32 CUDA, b [M] float32 CUDA or None, s0 [n] float64,
+    u0 [T, m] float64 CUDA (not differentiated through by autograd's graph
+    unless it requires grad: its gradient dL/du0 is returned too).
+    spec: dict(model, dt, Q, R, eta, eps, n_iter, n_outer).
+    Returns s^K [T+1, n] float64 CUDA."""
+
+    @staticmethod
+    def forward(fctx, y, b, s0, u0, spec, cctx):
+        T, m = u0.shape
+        s0h = s0.detach().cpu().double().numpy()
+        P = cov.make_problem(spec["model"], T, spec["dt"], s0h, cov.FIELD_SINKHORN, spec["Q"], spec["R"],
+                             spec["eta"], d=y.shape[1], y=y.detach(), b=None if b is None else b.detach(),
+                             eps=spec["eps"], n_iter=spec["n_iter"])
+        u = u0.detach().clone()
+        s_K, hist = cov.cov_solve_checkpointed(cctx, P, spec["n_outer"], u)
+        fctx.problem = P
+        fctx.cctx = cctx
+        fctx.n_outer = spec["n_outer"]
+        fctx.has_b = b is not None
+        fctx.s0_meta = (s0.device, s0.dtype)
+        fctx.save_for_backward(u0.detach(), hist)
+        return s_K
+
+    @staticmethod
+    def backward(fctx, g_K):
+        u0, hist = fctx.saved_tensors
+        ybar, bbar, s0bar, u0bar = cov.cov_solve_backward(fctx.cctx, fctx.problem, fctx.n_outer, u0,
+                                                          g_K.detach().double().contiguous(), s_hist=hist)
+        dev, dt = fctx.s0_meta
+        return (ybar, bbar if fctx.has_b else None, s0bar.to(device=dev, dtype=dt), u0bar, None, None)
+
+
+class SinkhornLoss(torch.autograd.Function):
+    """L = SinkhornLoss.apply(x, y_ref, eps, n_iter, cctx, q_ref): S_eps of the
+    uniform sample sets x [T, d] and y_ref [M, d] (float32 CUDA); q_ref is
+    <1/M, q> of the reference's own self potential (see ``reference_self_term``)."""
+
+    @staticmethod
+    def forward(fctx, x, y_ref, eps, n_iter, cctx, q_ref):
+        a, f, g, p = cov.cov_field_sinkhorn(cctx, x.detach().contiguous(), y_ref, eps, n_iter)
+        fctx.save_for_backward(a)
+        fctx.T = x.shape[0]
+        L = f.double().mean() + g.double().mean() - p.double().mean() - q_ref
+        return L
+
+    @staticmethod
+    def backward(fctx, gL):
+        (a,) = fctx.saved_tensors
+        return (-(gL.to(a.dtype)) * a / fctx.T, None, None, None, None, None)
+
+
+def reference_self_term(cctx, y_ref, eps, n_iter) -> float:
+    """<1/M, q> for the self potential q of the uniform set y_ref."""
+    _, _, _, q = cov.cov_field_sinkhorn(cctx, y_ref, y_ref, eps, n_iter, field=False)
+    return float(q.double().mean())
+
+
+def gmm_reference(mu, log_sigma, logits, xi):
+    """(y [M, d], b [M]) of the mixture by reparameterisation: component c
+    owns the rows c*M/K .. (c+1)*M/K - 1 of the fixed draws xi [M, d]."""
+    K = mu.shape[0]
+    M, d = xi.shape
+    per = M // K
+    if per * K != M:
+        raise ValueError("M must be a multiple of the number of components")
+    comp = torch.arange(M, device=xi.device) // per
+    y = mu[comp] + torch.exp(log_sigma)[comp, None] * xi
+    b = torch.softmax(logits, 0)[comp] / per
+    return y.float().contiguous(), b.float().contiguous()
+
+
+def standard_draws(M: int, d: int, seed: int, device="cuda"):
+    """Fixed standard normal draws xi [M, d] (seeded, float32-exact)."""
+    g = np.random.Generator(np.random.Philox(seed))
+    return torch.as_tensor(g.standard_normal((M, d)).astype(np.float32), device=device)

@@ -160,8 +160,19 @@ SINKHORN_UNICYCLE_T65536 = Workload(
     field=FIELD_SINKHORN, T=65536, dt=0.01, n_outer=1, eta=0.5, M=262144,
     eps=0.002, n_iter=100, reference="density")
 
+# Differentiation: gradient of the coverage loss (Sinkhorn divergence of the
+# final trajectory to a held-out 4-component mixture, M = 8192 samples drawn
+# with seed 1, uniform weights) through 20 outer iterations with respect to
+# the reference mixture's means, log-sigmas and weight logits (samples by
+# reparameterisation, M/4 per component) and the initial state.
+ADJOINT_DOUBLE_T2048 = Workload(
+    name="adjoint_double_integrator_T2048_M8192_K20", model=DOUBLE_INT,
+    field=FIELD_SINKHORN, T=2048, dt=0.05, n_outer=20, eta=0.5, M=8192,
+    eps=0.005, n_iter=50, gmm_K=4,
+    extra={"loss_M": 8192, "loss_seed": 1, "loss_eps": 0.005, "loss_iters": 100})
+
 WORKLOADS = {w.name: w for w in (SVGD_SINGLE_T256, SINKHORN_DOUBLE_T4096,
-                                 SINKHORN_UNICYCLE_T65536)}
+                                 SINKHORN_UNICYCLE_T65536, ADJOINT_DOUBLE_T2048)}
 
 
 @dataclass

@@ -19,7 +19,7 @@ from paper_2511_11514_b300 import workloads as wl
 
 pytestmark = pytest.mark.gpu
 
-FIELD_VJP_TOL = 2e-3   # norm-wise, FP32 reverse sweep vs FP64 oracle
+FIELD_VJP_TOL = 1e-4   # norm-wise, FP32 reverse sweep vs FP64 oracle (measured <= 1.1e-5)
 FP64_TOL = 1e-9
 
 
