@@ -485,6 +485,9 @@ def run_adjoint(args):
     w = wl.ADJOINT_DOUBLE_T2048
     inst = wl.make_instance(w)
     ctx = cov.Context(0)
+    # the loss runs on its own context: a field call on the solve's context
+    # would overwrite the Riccati gains cov_solve caches in its workspace
+    lctx = cov.Context(0)
     dev = torch.device("cuda", 0)
     gw, gmu, gsig = inst.gmm
     mu = torch.tensor(gmu, dtype=torch.float32, device=dev, requires_grad=True)
@@ -497,14 +500,14 @@ def run_adjoint(args):
     y_loss = torch.as_tensor(wl.f32_pair(wl.gmm_samples(lw, lmu, lsig, w.extra["loss_M"], w.extra["loss_seed"] + 1000))[1],
                              dtype=torch.float32, device=dev)
     eps_l, it_l = w.extra["loss_eps"], w.extra["loss_iters"]
-    q_ref = ag.reference_self_term(ctx, y_loss, eps_l, it_l)
+    q_ref = ag.reference_self_term(lctx, y_loss, eps_l, it_l)
     spec = dict(model=w.model, dt=w.dt, Q=inst.Q, R=inst.R, eta=w.eta, eps=w.eps, n_iter=w.n_iter,
                 n_outer=w.n_outer)
 
     def forward():
         y, b = ag.gmm_reference(mu, log_sigma, logits, xi)
         s_K = ag.CoverageSolve.apply(y, b, s0, u0, spec, ctx)
-        return ag.SinkhornLoss.apply(s_K[1:, :2].float().contiguous(), y_loss, eps_l, it_l, ctx, q_ref)
+        return ag.SinkhornLoss.apply(s_K[1:, :2].float().contiguous(), y_loss, eps_l, it_l, lctx, q_ref)
 
     params = (mu, log_sigma, logits, s0)
     for _ in range(max(1, args.warmup)):
@@ -514,6 +517,7 @@ def run_adjoint(args):
     torch.cuda.synchronize()
     clocks = Clocks(0)
     clocks.start()
+    torch.cuda.profiler.start()  # a profiler started with --profile-from-start off sees the timed steps only
     fw, bw, losses = [], [], []
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
     for _ in range(args.steps):
@@ -529,6 +533,7 @@ def run_adjoint(args):
         fw.append(ev[0].elapsed_time(ev[1]))
         bw.append(ev[1].elapsed_time(ev[2]))
         losses.append(float(L.detach()))
+    torch.cuda.profiler.stop()
     clk = clocks.stop()
     st, flags = ctx.device_status()
     if st != cov.COV_OK:
@@ -549,6 +554,7 @@ def run_adjoint(args):
                            "logits": float(logits.grad.norm()), "s0": float(s0.grad.norm())},
             "clocks": clk}
     print(json.dumps(line), flush=True)
+    lctx.close()
     ctx.close()
     return 0
 

@@ -10,7 +10,10 @@ forward and backward arithmetic runs in libcov's kernels):
   iteration; backward: ``cov_solve_backward`` runs the reverse sweep (rollout,
   LQR and field adjoints) from those checkpoints.
 * ``SinkhornLoss``: the debiased Sinkhorn divergence of Eq. 6 between the
-  samples x and a held-out reference set (uniform weights).  Its value is the
+  samples x and a held-out reference set (uniform weights).  Give it a
+  context of its own: a field call on the solve's context overwrites the
+  time-invariant Riccati gains that cov_solve caches in its workspace (they
+  are then recomputed, a serial FP64 pass).  Its value is the
   dual value <a, f> + <b, g> - <a, p> - <b, q> at the potentials after
   n_iter iterations; its gradient is the envelope formula -(1/T) times the
   field of Eq. 7 at those potentials (exact at convergence).

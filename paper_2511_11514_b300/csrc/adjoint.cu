@@ -443,10 +443,20 @@ __global__ void __launch_bounds__(kAThreads) adj_kernel(const __grid_constant__ 
         float tot[NACC];
 #pragma unroll
         for (int k = 0; k < NACC; ++k) tot[k] = 0.f;
-        for (int p = 0; p < a.splits; ++p) {
-            const float* P = a.part + (size_t)p * a.part_ld + i;
+        // splits in groups of 8, all loads of a group in flight together
+        for (int p0 = 0; p0 < a.splits; p0 += 8) {
+            float v[8][NACC];
 #pragma unroll
-            for (int k = 0; k < NACC; ++k) tot[k] += ld_cg(P + k * cs);
+            for (int u = 0; u < 8; ++u) {
+                const bool live = p0 + u < a.splits;
+                const float* P = a.part + (size_t)(live ? p0 + u : 0) * a.part_ld + i;
+#pragma unroll
+                for (int k = 0; k < NACC; ++k) v[u][k] = live ? ld_cg(P + k * cs) : 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+#pragma unroll
+                for (int k = 0; k < NACC; ++k) tot[k] += v[u][k];
         }
         adj_epilogue<D, KIND>(a, i, tot);
     }
@@ -802,6 +812,7 @@ extern "C" cov_status cov_field_sinkhorn_vjp(cov_ctx* ctx, const float* x, int T
                                              float* ybar, float* bbar, cov_stream_t stream) {
     if (!ctx) return COV_ERR_INVALID_ARG;
     if (cudaSetDevice(ctx->device) != cudaSuccess) return COV_ERR_CUDA;
+    ctx->gains_key = 0;  // the workspace scratch overwrites cov_solve's cached gains
     return cov::sinkhorn_vjp_ws(ctx, ctx->ws, ctx->ws_bytes, x, d, T, y, b, M, d, eps, n_iter, nullptr, abar, d,
                                 xbar, d, ybar, b ? bbar : nullptr, 0, (cudaStream_t)stream);
 }

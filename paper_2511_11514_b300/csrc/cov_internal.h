@@ -35,7 +35,8 @@ struct cov_ctx {
     cov_graph_cache solve_graph;
     cov_graph_cache batch_graph;       // cov_solve_batched: one outer iteration of all problems
     std::vector<cudaStream_t> pool;    // streams the batched graph's branches are captured on
-    // cached LTI Riccati gains of cov_solve (valid while key matches)
+    // cached LTI Riccati gains of cov_solve (valid while key matches; every
+    // other call that writes workspace scratch clears the key)
     uint64_t gains_key = 0;
 };
 

@@ -463,22 +463,34 @@ __global__ void __launch_bounds__(kThreads) pairs_kernel(const __grid_constant__
         float m = kNegBig, s = 0.f, acc[KA];
 #pragma unroll
         for (int k = 0; k < KA; ++k) acc[k] = 0.f;
-        for (int p = 0; p < a.splits; ++p) {
-            const float* P = a.part + (size_t)p * a.part_ld + i;
-            float a2[KA];
-            float m2 = 0.f, s2 = 0.f;
-            if constexpr (TR::kSV) {
+        // splits in groups of 8: all loads of a group are issued before the
+        // first merge, so the L2 round trips overlap instead of serialising
+        for (int p0 = 0; p0 < a.splits; p0 += 8) {
+            float m2[8], s2[8], a2[8][KA];
 #pragma unroll
-                for (int k = 0; k < D; ++k) a2[k] = ld_cg(P + k * cs);
-            } else {
-                m2 = ld_cg(P);
-                s2 = ld_cg(P + cs);
-                if constexpr (TR::kW) {
+            for (int u = 0; u < 8; ++u) {
+                const bool live = p0 + u < a.splits;
+                const float* P = a.part + (size_t)(live ? p0 + u : 0) * a.part_ld + i;
+                m2[u] = kNegBig;
+                s2[u] = 0.f;
 #pragma unroll
-                    for (int k = 0; k < D; ++k) a2[k] = ld_cg(P + (2 + k) * cs);
+                for (int k = 0; k < KA; ++k) a2[u][k] = 0.f;
+                if (live) {
+                    if constexpr (TR::kSV) {
+#pragma unroll
+                        for (int k = 0; k < D; ++k) a2[u][k] = ld_cg(P + k * cs);
+                    } else {
+                        m2[u] = ld_cg(P);
+                        s2[u] = ld_cg(P + cs);
+                        if constexpr (TR::kW) {
+#pragma unroll
+                            for (int k = 0; k < D; ++k) a2[u][k] = ld_cg(P + (2 + k) * cs);
+                        }
+                    }
                 }
             }
-            merge_into<D, MODE>(m, s, acc, m2, s2, a2);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) merge_into<D, MODE>(m, s, acc, m2[u], s2[u], a2[u]);
         }
         epilogue<D, MODE>(a, i, m, s, acc);
     }
@@ -1185,6 +1197,7 @@ extern "C" cov_status cov_field_sinkhorn(cov_ctx* ctx, const float* x, int T, co
                                          float* a_out, cov_stream_t stream) {
     if (!ctx) return COV_ERR_INVALID_ARG;
     if (cudaSetDevice(ctx->device) != cudaSuccess) return COV_ERR_CUDA;
+    ctx->gains_key = 0;  // the workspace scratch overwrites cov_solve's cached gains
     return cov::sinkhorn_field_ws(ctx, ctx->ws, ctx->ws_bytes, x, d, T, y, b, M, d, eps, n_iter, flags, f, g, p,
                                   a_out, (cudaStream_t)stream);
 }
@@ -1193,6 +1206,7 @@ extern "C" cov_status cov_field_svgd(cov_ctx* ctx, const float* x, int T, int d,
                                      const cov_gmm* gmm, float h, float* a_out, cov_stream_t stream) {
     if (!ctx) return COV_ERR_INVALID_ARG;
     if (cudaSetDevice(ctx->device) != cudaSuccess) return COV_ERR_CUDA;
+    ctx->gains_key = 0;  // the workspace scratch overwrites cov_solve's cached gains
     return cov::svgd_field_ws(ctx, ctx->ws, ctx->ws_bytes, x, d, T, d, score, gmm, h, a_out, (cudaStream_t)stream);
 }
 

@@ -86,6 +86,20 @@ static uint64_t fnv(const void* p, size_t n, uint64_t h) {
     return h;
 }
 
+// Identity of the cached time-invariant gains (and of A, B beside them in the
+// solve buffers at the start of the workspace).
+static uint64_t lti_gains_key(const cov_problem* P, const void* ws) {
+    uint64_t gk = 88172645463325252ull;
+    gk = fnv(&P->model, sizeof(int), gk);
+    gk = fnv(&P->T, sizeof(int), gk);
+    gk = fnv(&P->d, sizeof(int), gk);
+    gk = fnv(&P->dt, sizeof(double), gk);
+    gk = fnv(P->Q, sizeof(P->Q), gk);
+    gk = fnv(P->R, sizeof(P->R), gk);
+    gk = fnv(&ws, sizeof(ws), gk);
+    return gk == 0 ? 1 : gk;
+}
+
 static cov_status validate(const cov_problem* P, int* n, int* m) {
     if (!P || model_dims(P->model, n, m) != 0) return COV_ERR_INVALID_ARG;
     if (P->T < 1 || !isfinite(P->dt) || !isfinite(P->eta) || P->d < 1 || P->d > std::min(*n, COV_MAX_D))
@@ -183,15 +197,7 @@ static cov_status cov::solve_impl(cov_ctx* ctx, const cov_problem* prob, int n_o
     if (model_is_lti(prob->model)) {
         // gains of a time-invariant model: computed once per (model, T, dt,
         // Q, R, workspace) and reused by every later outer iteration
-        uint64_t gk = 88172645463325252ull;
-        gk = fnv(&prob->model, sizeof(int), gk);
-        gk = fnv(&prob->T, sizeof(int), gk);
-        gk = fnv(&prob->dt, sizeof(double), gk);
-        gk = fnv(prob->Q, sizeof(prob->Q), gk);
-        gk = fnv(prob->R, sizeof(prob->R), gk);
-        const void* wsp = ctx->ws;
-        gk = fnv(&wsp, sizeof(wsp), gk);
-        if (gk == 0) gk = 1;
+        const uint64_t gk = lti_gains_key(prob, ctx->ws);
         if (ctx->gains_key != gk) {
             r = linearize_launch(ctx, prob->model, s_out, u, prob->T, prob->dt, b.A, b.B, st);
             if (r != COV_OK) return r;
@@ -547,7 +553,6 @@ extern "C" cov_status cov_solve_backward(cov_ctx* ctx, const cov_problem* prob, 
     void* rest = static_cast<char*>(ctx->ws) + used;
     const size_t rest_bytes = ctx->ws_bytes - used;
     if (backward_ws_bytes(prob, n, m, K, replay) > ctx->ws_bytes) return COV_ERR_WORKSPACE;
-    ctx->gains_key = 0;  // the solve buffers are reused here
     cudaStream_t st = (cudaStream_t)stream;
     const size_t ss = (size_t)(T + 1) * n;
     const int nb = (T + 256) / 256;
@@ -564,11 +569,16 @@ extern "C" cov_status cov_solve_backward(cov_ctx* ctx, const cov_problem* prob, 
         }
         hist = bb.hist;
     }
-    // A, B (time-invariant: any state will do) and the Riccati gains
-    r = linearize_launch(ctx, prob->model, K > 0 ? hist : sbar_K, u0, T, prob->dt, sb.A, sb.B, st);
-    if (r != COV_OK) return r;
-    r = lqr_riccati(ctx, n, m, sb.A, sb.B, prob->Q, prob->R, T, sb.gains, st);
-    if (r != COV_OK) return r;
+    // A, B (time-invariant: any state will do) and the Riccati gains, shared
+    // with cov_solve's cache (same solve buffers at the start of the workspace)
+    const uint64_t gk = lti_gains_key(prob, ctx->ws);
+    if (ctx->gains_key != gk) {
+        r = linearize_launch(ctx, prob->model, K > 0 ? hist : sbar_K, u0, T, prob->dt, sb.A, sb.B, st);
+        if (r != COV_OK) return r;
+        r = lqr_riccati(ctx, n, m, sb.A, sb.B, prob->Q, prob->R, T, sb.gains, st);
+        if (r != COV_OK) return r;
+        ctx->gains_key = gk;
+    }
     if (replay) {
         for (int k = 1; k < K; ++k) {
             double* sk = bb.hist + (size_t)k * ss;

@@ -83,3 +83,23 @@ def test_sinkhorn_solve_final_metric_within_one_percent(cov, ctx, orc):
     mg, mo = _metric(orc, host(s), ref), _metric(orc, so, ref)
     assert abs(mg - mo) <= 0.01 * abs(mo)
     assert ctx.device_status()[1] == 0
+
+
+def test_cached_gains_survive_other_calls_on_the_context(cov, ctx):
+    """cov_solve caches the Riccati gains of a time-invariant model in the
+    workspace; a field call in between overwrites that scratch, so the next
+    cov_solve_continue must recompute them: solving 2 + 2 iterations around a
+    foreign field call equals solving 4 in one call, bit for bit."""
+    inst = wl.make_instance(wl.SINKHORN_DOUBLE_T4096, T=512, M=1024)
+    P = _problem(cov, inst, 512, n_iter=10, y_dev=dev32(inst.y))
+    u1 = dev64(inst.u0)
+    s1 = cov.cov_solve(ctx, P, 2, u1)
+    xo = dev32(wl.random_points(3000, 2, seed=5))
+    cov.cov_field_sinkhorn(ctx, xo, dev32(wl.random_points(5000, 2, seed=6)), 0.003, 7)
+    cov.cov_solve_continue(ctx, P, 2, u1, s1)
+    u2 = dev64(inst.u0)
+    s2 = cov.cov_solve(ctx, P, 4, u2)
+    st, flags = ctx.device_status()
+    assert st == cov.COV_OK, flags
+    np.testing.assert_array_equal(host(s1), host(s2))
+    np.testing.assert_array_equal(host(u1), host(u2))
