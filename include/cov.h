@@ -342,10 +342,21 @@ COV_API cov_status cov_rollout_vjp(cov_ctx* ctx, int model, const double* s,
 
 /* cov_solve that also keeps the checkpoints of a later cov_solve_backward:
  * s_hist[k] = the trajectory entering outer iteration k, k = 0..n_outer-1.
- *   s_hist [n_outer][T+1][n] FP64 device (NULL only when n_outer = 0). */
+ *   s_hist [n_outer][T+1][n] FP64 device (NULL only when n_outer = 0).
+ * flags: 0, or COV_CKPT_RECORD to also keep, inside the workspace, the
+ *   record of every outer iteration's Sinkhorn iterations (the potentials
+ *   of each iteration, about 4 (2 + d)(n_iter + 2)(T + M) bytes per outer
+ *   iteration) so that cov_solve_backward need not recompute them (Sinkhorn
+ *   field on a time-invariant model, d <= 3; reserve
+ *   cov_workspace_size_backward(prob, n_outer, COV_BACKWARD_RECORDED)).
+ *   The records stay valid until another call writes workspace scratch
+ *   (any call on this context other than cov_solve_backward with the same
+ *   problem, n_outer and s_hist). */
+enum { COV_CKPT_RECORD = 1 };
 COV_API cov_status cov_solve_checkpointed(cov_ctx* ctx, const cov_problem* prob,
                                           int n_outer, double* u, double* s_out,
-                                          double* s_hist, cov_stream_t stream);
+                                          double* s_hist, int flags,
+                                          cov_stream_t stream);
 
 /* Gradient of a scalar loss L(s^K) through n_outer = K outer iterations of
  * cov_solve started from the control u0 (Sec. II-C), for a Sinkhorn field
@@ -364,8 +375,14 @@ COV_API cov_status cov_solve_checkpointed(cov_ctx* ctx, const cov_problem* prob,
  *          prob->b is NULL), written: dL/dy, dL/db
  *   s0bar [n] FP64 device, written: dL/ds_0;  u0bar [T][m] FP64 device or
  *          NULL, written: dL/du0
- * Workspace: cov_workspace_size_backward(prob, K, s_hist == NULL). */
-COV_API size_t cov_workspace_size_backward(const cov_problem* prob, int n_outer, int replay);
+ * When the last call on the context was cov_solve_checkpointed with
+ * COV_CKPT_RECORD on the same problem, n_outer and s_hist, the recorded
+ * Sinkhorn iterations are used instead of recomputed (same results).
+ * Workspace: cov_workspace_size_backward(prob, K, mode) with mode
+ * COV_BACKWARD_CHECKPOINTS (s_hist given), COV_BACKWARD_REPLAY (s_hist NULL)
+ * or COV_BACKWARD_RECORDED (after a recording forward). */
+enum { COV_BACKWARD_CHECKPOINTS = 0, COV_BACKWARD_REPLAY = 1, COV_BACKWARD_RECORDED = 2 };
+COV_API size_t cov_workspace_size_backward(const cov_problem* prob, int n_outer, int mode);
 COV_API cov_status cov_solve_backward(cov_ctx* ctx, const cov_problem* prob,
                                       int n_outer, const double* u0,
                                       const double* s_hist, const double* sbar_K,

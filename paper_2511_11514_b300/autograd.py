@@ -36,7 +36,10 @@ class CoverageSolve(torch.autograd.Function):
     y [M, d] float32 CUDA, b [M] float32 CUDA or None, s0 [n] float64,
     u0 [T, m] float64 CUDA (not differentiated through by autograd's graph
     unless it requires grad: its gradient dL/du0 is returned too).
-    spec: dict(model, dt, Q, R, eta, eps, n_iter, n_outer).
+    spec: dict(model, dt, Q, R, eta, eps, n_iter, n_outer).  The forward keeps
+    every outer iteration's Sinkhorn record in the workspace and the backward
+    reuses it when no other forward ran on the context in between (else it
+    recomputes from the saved checkpoints); both replay cached CUDA graphs.
     Returns s^K [T+1, n] float64 CUDA."""
 
     @staticmethod
@@ -46,21 +49,22 @@ class CoverageSolve(torch.autograd.Function):
         P = cov.make_problem(spec["model"], T, spec["dt"], s0h, cov.FIELD_SINKHORN, spec["Q"], spec["R"],
                              spec["eta"], d=y.shape[1], y=y.detach(), b=None if b is None else b.detach(),
                              eps=spec["eps"], n_iter=spec["n_iter"])
-        u = u0.detach().clone()
-        s_K, hist = cov.cov_solve_checkpointed(cctx, P, spec["n_outer"], u)
+        s_K, hist, token, P = cov.grad_forward(cctx, P, spec["n_outer"], u0.detach(), y.detach(),
+                                               None if b is None else b.detach())
         fctx.problem = P
         fctx.cctx = cctx
         fctx.n_outer = spec["n_outer"]
+        fctx.token = token
         fctx.has_b = b is not None
         fctx.s0_meta = (s0.device, s0.dtype)
-        fctx.save_for_backward(u0.detach(), hist)
+        fctx.save_for_backward(u0.detach(), hist, y.detach(), None if b is None else b.detach())
         return s_K
 
     @staticmethod
     def backward(fctx, g_K):
-        u0, hist = fctx.saved_tensors
-        ybar, bbar, s0bar, u0bar = cov.cov_solve_backward(fctx.cctx, fctx.problem, fctx.n_outer, u0,
-                                                          g_K.detach().double().contiguous(), s_hist=hist)
+        u0, hist, y, b = fctx.saved_tensors
+        ybar, bbar, s0bar, u0bar = cov.grad_backward(fctx.cctx, fctx.problem, fctx.n_outer, u0,
+                                                     g_K.detach().double().contiguous(), hist, fctx.token, y, b)
         dev, dt = fctx.s0_meta
         return (ybar, bbar if fctx.has_b else None, s0bar.to(device=dev, dtype=dt), u0bar, None, None)
 

@@ -99,7 +99,7 @@ def load(path: str = LIB_PATH):
         "cov_workspace_size_lqr_vjp": (_sz, [_i, _i, _i]),
         "cov_lqr_vjp": (_i, [_P, _P, _P, _P, _P, _P, _i, _i, _i, _P, _P]),
         "cov_rollout_vjp": (_i, [_P, _i, _P, _P, _i, _d, _P, _P, _P, _P]),
-        "cov_solve_checkpointed": (_i, [_P, ctypes.POINTER(cov_problem), _i, _P, _P, _P, _P]),
+        "cov_solve_checkpointed": (_i, [_P, ctypes.POINTER(cov_problem), _i, _P, _P, _P, _i, _P]),
         "cov_workspace_size_backward": (_sz, [ctypes.POINTER(cov_problem), _i, _i]),
         "cov_solve_backward": (_i, [_P, ctypes.POINTER(cov_problem), _i, _P, _P, _P, _P, _P, _P, _P, _P]),
     }
@@ -150,6 +150,8 @@ class Context:
             raise CovError(st, "cov_ctx_create")
         self.h = h
         self._keep = []
+        self._cache = {}        # persistent buffers of the graph-friendly gradient calls
+        self._grad_token = 0    # identifies the latest recording forward of grad_forward
 
     def close(self):
         if getattr(self, "h", None):
@@ -431,18 +433,30 @@ def cov_rollout_vjp(ctx: Context, model, s, u, dt, sbar, stream=None):
     return ubar, s0bar
 
 
-def cov_solve_checkpointed(ctx: Context, problem, n_outer, u, s_out=None, s_hist=None, stream=None):
-    """cov_solve that also returns the checkpoints s_hist [n_outer, T+1, n]."""
+CKPT_RECORD = 1
+BACKWARD_CHECKPOINTS, BACKWARD_REPLAY, BACKWARD_RECORDED = 0, 1, 2
+
+
+def cov_solve_checkpointed(ctx: Context, problem, n_outer, u, s_out=None, s_hist=None, record=False, stream=None):
+    """cov_solve that also returns the checkpoints s_hist [n_outer, T+1, n];
+    record=True also keeps every outer iteration's Sinkhorn record for
+    cov_solve_backward."""
     P, keep = problem
     n, m = MODEL_DIMS[P.model]
     T = P.T
     ctx.reserve_for(T, P.M, P.d, n, m)
+    if record:
+        need = int(load().cov_workspace_size_backward(ctypes.byref(P), int(n_outer), BACKWARD_RECORDED))
+        if need == 0:
+            raise CovError(COV_ERR_UNSUPPORTED, "recording solve (Sinkhorn field, time-invariant model, d <= 3)")
+        ctx.reserve(need)
     s_out = torch.empty((T + 1, n), device=u.device, dtype=torch.float64) if s_out is None else s_out
     if s_hist is None:
         s_hist = torch.empty((max(int(n_outer), 1), T + 1, n), device=u.device, dtype=torch.float64)
     st = load().cov_solve_checkpointed(ctx.h, ctypes.byref(P), int(n_outer), _ptr(u, torch.float64, (T, m), "u"),
                                        _ptr(s_out, torch.float64, (T + 1, n), "s_out"),
-                                       _ptr(s_hist, torch.float64, name="s_hist"), _stream(stream))
+                                       _ptr(s_hist, torch.float64, name="s_hist"), CKPT_RECORD if record else 0,
+                                       _stream(stream))
     ctx._check(st, "cov_solve_checkpointed")
     return s_out, s_hist
 
@@ -453,10 +467,11 @@ def cov_solve_backward(ctx: Context, problem, n_outer, u0, sbar_K, s_hist=None, 
     P, keep = problem
     n, m = MODEL_DIMS[P.model]
     T = P.T
-    need = int(load().cov_workspace_size_backward(ctypes.byref(P), int(n_outer), int(s_hist is None)))
+    mode = BACKWARD_REPLAY if s_hist is None else BACKWARD_CHECKPOINTS
+    need = int(load().cov_workspace_size_backward(ctypes.byref(P), int(n_outer), mode))
     if need == 0:
         raise CovError(COV_ERR_UNSUPPORTED, "cov_solve_backward (Sinkhorn field, time-invariant model, d <= 3)")
-    ctx.reserve(need)
+    ctx.reserve(need)  # never shrinks: a recording forward's workspace (larger) is kept
     dev = u0.device
     ybar = torch.empty((P.M, P.d), device=dev, dtype=torch.float32)
     bbar = torch.empty(P.M, device=dev, dtype=torch.float32) if P.b else None
@@ -474,3 +489,85 @@ def cov_solve_backward(ctx: Context, problem, n_outer, u0, sbar_K, s_hist=None, 
                                    _ptr(u0bar, torch.float64, (T, m), "u0bar"), _stream(stream))
     ctx._check(st, "cov_solve_backward")
     return ybar, bbar, s0bar, u0bar
+
+
+# -- graph-friendly forward/backward pair (used by autograd) -------------------
+# cov_solve_checkpointed and cov_solve_backward replay a cached CUDA graph when
+# called again with the same problem, sizes and pointers.  These two helpers
+# keep their device buffers in the context (copying inputs in and results
+# out), so repeated training steps hit the cached graphs.
+def _cached(ctx: Context, name, shape, dtype, device):
+    key = (name, tuple(int(v) for v in shape), dtype, str(device))
+    t = ctx._cache.get(key)
+    if t is None:
+        t = torch.empty(tuple(shape), dtype=dtype, device=device)
+        ctx._cache[key] = t
+    return t
+
+
+def grad_forward(ctx: Context, problem, n_outer, u0, y, b=None, stream=None):
+    """Recording forward from u0 (not modified) on the reference (y, b):
+    returns (s_K, s_hist, token, problem'), s_K and s_hist fresh tensors;
+    token names this forward and problem' (the problem on the context's copies
+    of y and b) is what grad_backward takes."""
+    P0, keep = problem
+    n, m = MODEL_DIMS[P0.model]
+    T = P0.T
+    dev = u0.device
+    yc = _cached(ctx, "y", tuple(y.shape), torch.float32, dev)
+    yc.copy_(y)
+    P = cov_problem.from_buffer_copy(P0)
+    P.y = _ptr(yc, torch.float32, name="y").value
+    if b is not None:
+        bc = _cached(ctx, "b", tuple(b.shape), torch.float32, dev)
+        bc.copy_(b)
+        P.b = _ptr(bc, torch.float32, name="b").value
+    else:
+        P.b = None
+    pr = (P, keep)
+    u = _cached(ctx, "u", (T, m), torch.float64, dev)
+    s_out = _cached(ctx, "s_out", (T + 1, n), torch.float64, dev)
+    hist = _cached(ctx, "hist", (max(int(n_outer), 1), T + 1, n), torch.float64, dev)
+    u.copy_(u0)
+    cov_solve_checkpointed(ctx, pr, n_outer, u, s_out=s_out, s_hist=hist, record=True, stream=stream)
+    ctx._grad_token += 1
+    return s_out.clone(), hist.clone(), ctx._grad_token, pr
+
+
+def grad_backward(ctx: Context, problem, n_outer, u0, sbar_K, s_hist, token, y, b=None, stream=None):
+    """Reverse sweep after grad_forward (problem = the problem' it returned,
+    y and b = that forward's reference): uses that forward's records when no
+    other grad_forward ran since (token), else recomputes from s_hist.  The
+    context's copies of y and b are restored first (a later forward may have
+    overwritten them)."""
+    P, keep = problem
+    n, m = MODEL_DIMS[P.model]
+    T = P.T
+    dev = u0.device
+    _cached(ctx, "y", tuple(y.shape), torch.float32, dev).copy_(y)
+    if b is not None:
+        _cached(ctx, "b", tuple(b.shape), torch.float32, dev).copy_(b)
+    if token == ctx._grad_token:
+        hist = _cached(ctx, "hist", (max(int(n_outer), 1), T + 1, n), torch.float64, dev)
+    else:
+        hist = s_hist
+    u0c = _cached(ctx, "bu0", (T, m), torch.float64, dev)
+    sb = _cached(ctx, "bsbar", (T + 1, n), torch.float64, dev)
+    u0c.copy_(u0)
+    sb.copy_(sbar_K)
+    mode = BACKWARD_CHECKPOINTS
+    need = int(load().cov_workspace_size_backward(ctypes.byref(P), int(n_outer), mode))
+    if need == 0:
+        raise CovError(COV_ERR_UNSUPPORTED, "cov_solve_backward (Sinkhorn field, time-invariant model, d <= 3)")
+    ctx.reserve(need)
+    ybar = _cached(ctx, "ybar", (P.M, P.d), torch.float32, dev)
+    bbar = _cached(ctx, "bbar", (P.M,), torch.float32, dev) if P.b else None
+    s0bar = _cached(ctx, "s0bar", (n,), torch.float64, dev)
+    u0bar = _cached(ctx, "u0bar", (T, m), torch.float64, dev)
+    st = load().cov_solve_backward(ctx.h, ctypes.byref(P), int(n_outer), _ptr(u0c, torch.float64, (T, m), "u0"),
+                                   _ptr(hist, torch.float64, name="s_hist"), _ptr(sb, torch.float64, (T + 1, n), "sbar"),
+                                   _ptr(ybar, torch.float32, (P.M, P.d), "ybar"),
+                                   _ptr(bbar, torch.float32, (P.M,), "bbar"), _ptr(s0bar, torch.float64, (n,), "s0bar"),
+                                   _ptr(u0bar, torch.float64, (T, m), "u0bar"), _stream(stream))
+    ctx._check(st, "cov_solve_backward")
+    return ybar.clone(), (bbar.clone() if bbar is not None else None), s0bar.clone(), u0bar.clone()

@@ -682,8 +682,11 @@ __global__ void __launch_bounds__(1024) vjp_finish_kernel(VjpBufs v, int T, int 
 }
 
 size_t sinkhorn_vjp_bytes(int T, int M, int d, int n_iter) {
+    return round_up(sinkhorn_tape_bytes(T, M, d, n_iter), 256) + sinkhorn_vjp_bytes_given(T, M, d);
+}
+
+size_t sinkhorn_vjp_bytes_given(int T, int M, int d) {
     Carver cv(nullptr);
-    cv.off = sinkhorn_tape_bytes(T, M, d, n_iter);
     const int Tp = (int)round_up((size_t)T, 1024), Mp = (int)round_up((size_t)M, 1024);
     carve_vjp(cv, d, Tp, Mp);
     return round_up(cv.off, 256);
@@ -692,16 +695,23 @@ size_t sinkhorn_vjp_bytes(int T, int M, int d, int n_iter) {
 cov_status sinkhorn_vjp_ws(cov_ctx* ctx, void* ws, size_t ws_bytes, const float* x, int x_ld, int T,
                            const float* y, const float* b, int M, int d, float eps, int n_iter,
                            const float* scal_given, const float* abar, int abar_ld, float* xbar, int xbar_ld,
-                           float* ybar, float* bbar, int accumulate, cudaStream_t stream) {
+                           float* ybar, float* bbar, int accumulate, cudaStream_t stream,
+                           const SkTape* given_tape) {
     if (!ctx || !x || !y || !abar || !xbar || !ybar || T < 1 || M < 1 || d < 1 || n_iter < 0 || x_ld < d ||
         abar_ld < d || xbar_ld < d || !(eps > 0.f) || !isfinite(eps))
         return COV_ERR_INVALID_ARG;
     if (d > 3) return COV_ERR_UNSUPPORTED;
     SkTape tp{};
     size_t used = 0;
-    cov_status r = sinkhorn_tape_ws(ctx, ws, ws_bytes, x, x_ld, T, y, b, M, d, eps, n_iter, scal_given, &tp,
-                                    &used, stream);
-    if (r != COV_OK) return r;
+    cov_status r = COV_OK;
+    if (given_tape) {
+        tp = *given_tape;
+        if (tp.n_iter != n_iter || tp.T != T || tp.M != M || tp.d != d || tp.eps != eps) return COV_ERR_INVALID_ARG;
+    } else {
+        r = sinkhorn_tape_ws(ctx, ws, ws_bytes, x, x_ld, T, y, b, M, d, eps, n_iter, scal_given, &tp, &used,
+                             stream);
+        if (r != COV_OK) return r;
+    }
     Carver cv(ws);
     cv.off = used;
     VjpBufs v = carve_vjp(cv, d, tp.Tp, tp.Mp);
@@ -812,7 +822,7 @@ extern "C" cov_status cov_field_sinkhorn_vjp(cov_ctx* ctx, const float* x, int T
                                              float* ybar, float* bbar, cov_stream_t stream) {
     if (!ctx) return COV_ERR_INVALID_ARG;
     if (cudaSetDevice(ctx->device) != cudaSuccess) return COV_ERR_CUDA;
-    ctx->gains_key = 0;  // the workspace scratch overwrites cov_solve's cached gains
+    cov::clobber_ws_caches(ctx);  // the workspace scratch overwrites cov_solve's caches
     return cov::sinkhorn_vjp_ws(ctx, ctx->ws, ctx->ws_bytes, x, d, T, y, b, M, d, eps, n_iter, nullptr, abar, d,
                                 xbar, d, ybar, b ? bbar : nullptr, 0, (cudaStream_t)stream);
 }

@@ -19,6 +19,10 @@ struct cov_graph_cache {
 
 #include <vector>
 
+namespace cov {
+struct SkTape;
+}
+
 struct cov_ctx {
     int device = 0;
     int num_sms = 148;
@@ -34,10 +38,16 @@ struct cov_ctx {
     std::string last_cuda_error;
     cov_graph_cache solve_graph;
     cov_graph_cache batch_graph;       // cov_solve_batched: one outer iteration of all problems
+    cov_graph_cache ckpt_graph;        // recording cov_solve_checkpointed: all its outer iterations
+    cov_graph_cache back_graph;        // cov_solve_backward: the whole reverse sweep
     std::vector<cudaStream_t> pool;    // streams the batched graph's branches are captured on
     // cached LTI Riccati gains of cov_solve (valid while key matches; every
     // other call that writes workspace scratch clears the key)
     uint64_t gains_key = 0;
+    // forward records of a taped cov_solve_checkpointed, one per outer
+    // iteration, valid for cov_solve_backward while tape_key matches
+    uint64_t tape_key = 0;
+    std::vector<cov::SkTape> tapes;
 };
 
 namespace cov {
@@ -61,6 +71,13 @@ inline size_t round_up(size_t x, size_t m) { return (x + m - 1) / m * m; }
 
 // Records a CUDA error on the context; returns true if `e` is an error.
 bool cuda_failed(cov_ctx* ctx, cudaError_t e);
+
+// A call is about to write scratch over the workspace: forget what cov_solve
+// cached there (time-invariant gains, forward records).
+inline void clobber_ws_caches(cov_ctx* ctx) {
+    ctx->gains_key = 0;
+    ctx->tape_key = 0;
+}
 
 // ---- per-component entry points used by cov_solve ---------------------------
 // Workspace requirements of each component (bytes, 256-aligned pieces).
@@ -96,21 +113,32 @@ struct SkTape {
     float* Dg;        // [n+1][d][Mp]: slot t = sum_i pi^g_ji (xhat_i - yhat_j) of the g-update t
     float* Dp;        // [n+1][d][Tp]: slot t = sum_k pi^p_ik (xhat_k - xhat_i) of the p-update t
 };
-size_t sinkhorn_tape_bytes(int T, int M, int d, int n_iter);
+size_t sinkhorn_tape_bytes(int T, int M, int d, int n_iter, bool with_part = true);
+// Bytes of the split buffers (partials and tickets) of a Sinkhorn run.
+size_t sinkhorn_split_bytes(int T, int M, int d);
 // Runs the recorded forward; *used = the workspace bytes it occupies (the
-// tape must stay untouched while the adjoint reads it).
+// tape must stay untouched while the adjoint reads it).  split_ws: the split
+// buffers (sinkhorn_split_bytes) kept outside the tape, or nullptr to carve
+// them inside it.  a_out [T][d]: the field of the recorded potentials, or
+// nullptr.
 cov_status sinkhorn_tape_ws(cov_ctx* ctx, void* ws, size_t ws_bytes, const float* x, int x_ld, int T,
                             const float* y, const float* b, int M, int d, float eps, int n_iter,
-                            const float* scal_given, SkTape* tape, size_t* used, cudaStream_t stream);
+                            const float* scal_given, SkTape* tape, size_t* used, cudaStream_t stream,
+                            float* split_ws = nullptr, float* a_out = nullptr);
 // Reverse mode of the field (adjoint.cu).  abar [T][abar_ld] FP32 device (the
 // first d entries of each row are used), xbar [T][xbar_ld] written;
 // ybar [M][d] and bbar [M] (NULL for uniform weights) written, or added to
 // when accumulate != 0.
 size_t sinkhorn_vjp_bytes(int T, int M, int d, int n_iter);
+// given_tape: a forward record of exactly this x (then ws only holds the
+// reverse sweep's buffers, sinkhorn_vjp_bytes_given), or nullptr to record
+// one now at the start of ws.
+size_t sinkhorn_vjp_bytes_given(int T, int M, int d);
 cov_status sinkhorn_vjp_ws(cov_ctx* ctx, void* ws, size_t ws_bytes, const float* x, int x_ld, int T,
                            const float* y, const float* b, int M, int d, float eps, int n_iter,
                            const float* scal_given, const float* abar, int abar_ld, float* xbar, int xbar_ld,
-                           float* ybar, float* bbar, int accumulate, cudaStream_t stream);
+                           float* ybar, float* bbar, int accumulate, cudaStream_t stream,
+                           const SkTape* given_tape = nullptr);
 // Statistics of a reference set that every field evaluation on it needs:
 // scal[0..d) = mean of y, scal[8] = 1 / sum b (0 when b == NULL).
 void sinkhorn_reference_stats(const float* y, int M, int d, const float* b, float* scal, cudaStream_t stream);

@@ -765,7 +765,9 @@ static cov_status run_pairs(cov_ctx* ctx, int d, int family, PairArgs* seg, cons
     return cuda_failed(ctx, e) ? COV_ERR_CUDA : COV_OK;
 }
 
-static SkBufs carve_sinkhorn(Carver& cv, int T, int M, int d) {
+// with_part = false leaves part/counters to the caller (a recorded forward
+// keeps many tapes and shares one split buffer between them).
+static SkBufs carve_sinkhorn(Carver& cv, int T, int M, int d, bool with_part = true) {
     SkBufs B{};
     B.Tp = (int)round_up((size_t)T, kRowPad);
     B.Mp = (int)round_up((size_t)M, kRowPad);
@@ -781,10 +783,20 @@ static SkBufs carve_sinkhorn(Carver& cv, int T, int M, int d) {
     B.bary = cv.take<float>((size_t)d * B.Tp);
     B.scal = cv.take<float>(16);
     B.cnt_ld = cnt_ld_for(B.Tp, B.Mp);
-    B.counters = cv.take<unsigned>((size_t)M_COUNT * B.cnt_ld);
     B.part_floats = (size_t)(2 + d) * (kPartRows + B.Tp + B.Mp);
-    B.part = cv.take<float>(B.part_floats);
+    if (with_part) {
+        B.counters = cv.take<unsigned>((size_t)M_COUNT * B.cnt_ld);
+        B.part = cv.take<float>(B.part_floats);
+    }
     return B;
+}
+
+size_t sinkhorn_split_bytes(int T, int M, int d) {
+    const size_t Tp = round_up((size_t)T, kRowPad), Mp = round_up((size_t)M, kRowPad);
+    Carver cv(nullptr);
+    cv.take<unsigned>((size_t)M_COUNT * cnt_ld_for((int)Tp, (int)Mp));
+    cv.take<float>((size_t)(2 + d) * (kPartRows + Tp + Mp));
+    return round_up(cv.off, 256);
 }
 
 void sinkhorn_reference_stats(const float* y, int M, int d, const float* b, float* scal, cudaStream_t stream) {
@@ -920,9 +932,9 @@ static void carve_tape(Carver& cv, int n_iter, int d, int Tp, int Mp, SkTape* tp
     tp->Dp = cv.take<float>((size_t)(n_iter + 1) * d * Tp);
 }
 
-size_t sinkhorn_tape_bytes(int T, int M, int d, int n_iter) {
+size_t sinkhorn_tape_bytes(int T, int M, int d, int n_iter, bool with_part) {
     Carver cv(nullptr);
-    SkBufs B = carve_sinkhorn(cv, T, M, d);
+    SkBufs B = carve_sinkhorn(cv, T, M, d, with_part);
     SkTape tp{};
     carve_tape(cv, n_iter, d, B.Tp, B.Mp, &tp);
     return round_up(cv.off, 256);
@@ -930,12 +942,18 @@ size_t sinkhorn_tape_bytes(int T, int M, int d, int n_iter) {
 
 cov_status sinkhorn_tape_ws(cov_ctx* ctx, void* ws, size_t ws_bytes, const float* x, int x_ld, int T,
                             const float* y, const float* b, int M, int d, float eps, int n_iter,
-                            const float* scal_given, SkTape* tape, size_t* used, cudaStream_t stream) {
+                            const float* scal_given, SkTape* tape, size_t* used, cudaStream_t stream,
+                            float* split_ws, float* a_out) {
     if (!ctx || !x || !y || !tape || T < 1 || M < 1 || d < 1 || d > COV_MAX_D || x_ld < d || n_iter < 0 ||
         !(eps > 0.f) || !isfinite(eps))
         return COV_ERR_INVALID_ARG;
     Carver cv(ws);
-    SkBufs B = carve_sinkhorn(cv, T, M, d);
+    SkBufs B = carve_sinkhorn(cv, T, M, d, split_ws == nullptr);
+    if (split_ws) {
+        Carver cs(split_ws);
+        B.counters = cs.take<unsigned>((size_t)M_COUNT * B.cnt_ld);
+        B.part = cs.take<float>(B.part_floats);
+    }
     SkTape tp{};
     carve_tape(cv, n_iter, d, B.Tp, B.Mp, &tp);
     if (!ws || cv.off > ws_bytes) return COV_ERR_WORKSPACE;
@@ -1019,8 +1037,26 @@ cov_status sinkhorn_tape_ws(cov_ctx* ctx, void* ws, size_t ws_bytes, const float
         a.rows = B.xs; a.row_ld = B.Tp; a.n_rows = T;
         a.cols = B.xs; a.colh = tp.hp + (size_t)n * B.Tp; a.col_ld = B.Tp;
         a.out_h = tp.hp + (size_t)(n + 1) * B.Tp; a.in_h = a.colh; a.emode = M_P;
+        if (first) a.pre_ok = 0;
+        first = false;
         const int nc[1] = {T}, co[1] = {M_P * B.cnt_ld};
         r = run_pairs(ctx, d, M_G, &a, nc, 1, co, B.counters, stream);
+        if (r != COV_OK) return r;
+    }
+    if (a_out) {  // the field itself (Eq. 7) from the last potentials, as sinkhorn_field_ws
+        PairArgs a = base;
+        a.rows = B.xs; a.row_ld = B.Tp; a.n_rows = T;
+        a.cols = B.ys; a.colh = tp.hy + (size_t)n * B.Mp; a.col_ld = B.Mp;
+        a.bary = B.bary;
+        const int nc1[1] = {M}, co1[1] = {M_WY * B.cnt_ld};
+        r = run_pairs(ctx, d, M_WY, &a, nc1, 1, co1, B.counters, stream);
+        if (r != COV_OK) return r;
+        a = base;
+        a.rows = B.xs; a.row_ld = B.Tp; a.n_rows = T;
+        a.cols = B.xs; a.colh = tp.hp + (size_t)n * B.Tp; a.col_ld = B.Tp;
+        a.bary = B.bary; a.a_out = a_out; a.a_scale = 2.0f * tp.sigma;
+        const int nc2[1] = {T}, co2[1] = {M_WX * B.cnt_ld};
+        r = run_pairs(ctx, d, M_WX, &a, nc2, 1, co2, B.counters, stream);
         if (r != COV_OK) return r;
     }
     tp.scal = B.scal;
@@ -1197,7 +1233,7 @@ extern "C" cov_status cov_field_sinkhorn(cov_ctx* ctx, const float* x, int T, co
                                          float* a_out, cov_stream_t stream) {
     if (!ctx) return COV_ERR_INVALID_ARG;
     if (cudaSetDevice(ctx->device) != cudaSuccess) return COV_ERR_CUDA;
-    ctx->gains_key = 0;  // the workspace scratch overwrites cov_solve's cached gains
+    cov::clobber_ws_caches(ctx);  // the workspace scratch overwrites cov_solve's caches
     return cov::sinkhorn_field_ws(ctx, ctx->ws, ctx->ws_bytes, x, d, T, y, b, M, d, eps, n_iter, flags, f, g, p,
                                   a_out, (cudaStream_t)stream);
 }
@@ -1206,7 +1242,7 @@ extern "C" cov_status cov_field_svgd(cov_ctx* ctx, const float* x, int T, int d,
                                      const cov_gmm* gmm, float h, float* a_out, cov_stream_t stream) {
     if (!ctx) return COV_ERR_INVALID_ARG;
     if (cudaSetDevice(ctx->device) != cudaSuccess) return COV_ERR_CUDA;
-    ctx->gains_key = 0;  // the workspace scratch overwrites cov_solve's cached gains
+    cov::clobber_ws_caches(ctx);  // the workspace scratch overwrites cov_solve's caches
     return cov::svgd_field_ws(ctx, ctx->ws, ctx->ws_bytes, x, d, T, d, score, gmm, h, a_out, (cudaStream_t)stream);
 }
 

@@ -942,7 +942,7 @@ extern "C" cov_status cov_lqr_track(cov_ctx* ctx, const double* A, const double*
                                     double* z_out, cov_stream_t stream) {
     if (!ctx) return COV_ERR_INVALID_ARG;
     if (cudaSetDevice(ctx->device) != cudaSuccess) return COV_ERR_CUDA;
-    ctx->gains_key = 0;  // the workspace scratch overwrites cov_solve's cached gains
+    cov::clobber_ws_caches(ctx);  // the workspace scratch overwrites cov_solve's caches
     return cov::lqr_track_ws(ctx, ctx->ws, ctx->ws_bytes, A, B, Q, R, abar, T, n, m, v_out, z_out,
                              (cudaStream_t)stream);
 }
@@ -961,7 +961,7 @@ extern "C" cov_status cov_lqr_vjp(cov_ctx* ctx, const double* A, const double* B
         m > COV_MAX_M)
         return COV_ERR_INVALID_ARG;
     if (cudaSetDevice(ctx->device) != cudaSuccess) return COV_ERR_CUDA;
-    ctx->gains_key = 0;  // the workspace scratch overwrites cov_solve's cached gains
+    cov::clobber_ws_caches(ctx);  // the workspace scratch overwrites cov_solve's caches
     cov::Carver cv(ctx->ws);
     double* gains = cv.take<double>(cov::lqr_gain_doubles(T, n, m));
     const size_t used = cov::round_up(cv.off, 256);
@@ -980,7 +980,7 @@ extern "C" cov_status cov_rollout_vjp(cov_ctx* ctx, int model, const double* s, 
         cov::model_dims(model, &n, &m) != 0)
         return COV_ERR_INVALID_ARG;
     if (cudaSetDevice(ctx->device) != cudaSuccess) return COV_ERR_CUDA;
-    ctx->gains_key = 0;  // the workspace scratch overwrites cov_solve's cached gains
+    cov::clobber_ws_caches(ctx);  // the workspace scratch overwrites cov_solve's caches
     cov::Carver cv(ctx->ws);
     double* A = cv.take<double>((size_t)T * n * n);
     double* B = cv.take<double>((size_t)T * n * m);

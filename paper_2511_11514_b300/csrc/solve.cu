@@ -55,10 +55,48 @@ void drop_solve_graph(cov_ctx* ctx) {
     if (ctx->solve_graph.exec) cudaGraphExecDestroy(ctx->solve_graph.exec);
     if (ctx->solve_graph.graph) cudaGraphDestroy(ctx->solve_graph.graph);
     ctx->solve_graph = cov_graph_cache{};
-    ctx->gains_key = 0;
-    if (ctx->batch_graph.exec) cudaGraphExecDestroy(ctx->batch_graph.exec);
-    if (ctx->batch_graph.graph) cudaGraphDestroy(ctx->batch_graph.graph);
-    ctx->batch_graph = cov_graph_cache{};
+    clobber_ws_caches(ctx);
+    for (cov_graph_cache* g : {&ctx->batch_graph, &ctx->ckpt_graph, &ctx->back_graph}) {
+        if (g->exec) cudaGraphExecDestroy(g->exec);
+        if (g->graph) cudaGraphDestroy(g->graph);
+        *g = cov_graph_cache{};
+    }
+}
+
+// Enqueue `work` on `st` through a cached CUDA graph: captured (on a private
+// stream) when `key` differs from the cached one, then launched.  With
+// COV_OPT_USE_GRAPH = 0 the work is enqueued directly.
+template <class F>
+static cov_status run_cached_graph(cov_ctx* ctx, cov_graph_cache& gc, uint64_t key, cudaStream_t st, F&& work) {
+    if (!ctx->use_graph) return work(st);
+    if (!gc.exec || gc.key != key) {
+        if (gc.exec) cudaGraphExecDestroy(gc.exec);
+        if (gc.graph) cudaGraphDestroy(gc.graph);
+        gc = cov_graph_cache{};
+        cudaStream_t cap;
+        if (cuda_failed(ctx, cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking))) return COV_ERR_CUDA;
+        if (cuda_failed(ctx, cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal))) {
+            cudaStreamDestroy(cap);
+            return COV_ERR_CUDA;
+        }
+        const cov_status r = work(cap);
+        cudaGraph_t g = nullptr;
+        const cudaError_t ce = cudaStreamEndCapture(cap, &g);
+        cudaStreamDestroy(cap);
+        if (r != COV_OK || cuda_failed(ctx, ce)) {
+            if (g) cudaGraphDestroy(g);
+            return r != COV_OK ? r : COV_ERR_CUDA;
+        }
+        cudaGraphExec_t ex = nullptr;
+        if (cuda_failed(ctx, cudaGraphInstantiate(&ex, g, 0))) {
+            cudaGraphDestroy(g);
+            return COV_ERR_CUDA;
+        }
+        gc.graph = g;
+        gc.exec = ex;
+        gc.key = key;
+    }
+    return cuda_failed(ctx, cudaGraphLaunch(gc.exec, st)) ? COV_ERR_CUDA : COV_OK;
 }
 
 void destroy_stream_pool(cov_ctx* ctx) {
@@ -98,6 +136,21 @@ static uint64_t lti_gains_key(const cov_problem* P, const void* ws) {
     gk = fnv(P->R, sizeof(P->R), gk);
     gk = fnv(&ws, sizeof(ws), gk);
     return gk == 0 ? 1 : gk;
+}
+
+// Gains of a time-invariant model: computed once per (model, T, d, dt, Q, R,
+// workspace) into the solve buffers and reused by every later outer
+// iteration (and by the reverse sweep).  s, u: any state and control.
+static cov_status ensure_lti_gains(cov_ctx* ctx, const cov_problem* P, int n, int m, const SolveBufs& b,
+                                   const double* s, const double* u, cudaStream_t st) {
+    const uint64_t gk = lti_gains_key(P, ctx->ws);
+    if (ctx->gains_key == gk) return COV_OK;
+    cov_status r = linearize_launch(ctx, P->model, s, u, P->T, P->dt, b.A, b.B, st);
+    if (r != COV_OK) return r;
+    r = lqr_riccati(ctx, n, m, b.A, b.B, P->Q, P->R, P->T, b.gains, st);
+    if (r != COV_OK) return r;
+    ctx->gains_key = gk;
+    return COV_OK;
 }
 
 static cov_status validate(const cov_problem* P, int* n, int* m) {
@@ -162,12 +215,6 @@ extern "C" cov_status cov_solve_continue(cov_ctx* ctx, const cov_problem* prob, 
     return cov::solve_impl(ctx, prob, n_outer, u, s, (cudaStream_t)stream, false);
 }
 
-extern "C" cov_status cov_solve_checkpointed(cov_ctx* ctx, const cov_problem* prob, int n_outer, double* u,
-                                             double* s_out, double* s_hist, cov_stream_t stream) {
-    if (!s_hist && n_outer > 0) return COV_ERR_INVALID_ARG;
-    return cov::solve_impl(ctx, prob, n_outer, u, s_out, (cudaStream_t)stream, true, s_hist);
-}
-
 static cov_status cov::solve_impl(cov_ctx* ctx, const cov_problem* prob, int n_outer, double* u, double* s_out,
                                   cudaStream_t stream, bool initial_rollout, double* s_hist) {
     using namespace cov;
@@ -183,6 +230,7 @@ static cov_status cov::solve_impl(cov_ctx* ctx, const cov_problem* prob, int n_o
     if (!ctx->ws || used > ctx->ws_bytes) return COV_ERR_WORKSPACE;
     void* rest = static_cast<char*>(ctx->ws) + used;
     const size_t rest_bytes = ctx->ws_bytes - used;
+    ctx->tape_key = 0;  // the scratch below overwrites forward records
 
     // initial trajectory from s0 and the given controls
     if (initial_rollout) {
@@ -195,16 +243,8 @@ static cov_status cov::solve_impl(cov_ctx* ctx, const cov_problem* prob, int n_o
     if (prob->field == COV_FIELD_SINKHORN) sinkhorn_reference_stats(prob->y, prob->M, prob->d, prob->b, b.scal, st);
 
     if (model_is_lti(prob->model)) {
-        // gains of a time-invariant model: computed once per (model, T, dt,
-        // Q, R, workspace) and reused by every later outer iteration
-        const uint64_t gk = lti_gains_key(prob, ctx->ws);
-        if (ctx->gains_key != gk) {
-            r = linearize_launch(ctx, prob->model, s_out, u, prob->T, prob->dt, b.A, b.B, st);
-            if (r != COV_OK) return r;
-            r = lqr_riccati(ctx, n, m, b.A, b.B, prob->Q, prob->R, prob->T, b.gains, st);
-            if (r != COV_OK) return r;
-            ctx->gains_key = gk;
-        }
+        r = ensure_lti_gains(ctx, prob, n, m, b, s_out, u, st);
+        if (r != COV_OK) return r;
     }
 
     // checkpoint k: the trajectory entering outer iteration k
@@ -346,7 +386,7 @@ extern "C" cov_status cov_solve_batched(cov_ctx* ctx, const cov_problem* probs, 
     }
     if (!ctx->ws || total > ctx->ws_bytes) return COV_ERR_WORKSPACE;
     if (cudaSetDevice(ctx->device) != cudaSuccess) return COV_ERR_CUDA;
-    ctx->gains_key = 0;  // the problem regions overlap what cov_solve cached
+    clobber_ws_caches(ctx);  // the problem regions overlap what cov_solve cached
     cudaStream_t st = (cudaStream_t)stream;
     const int K = std::min(n_probs, kPoolStreams);
     if (ensure_pool(ctx, K) != COV_OK) return COV_ERR_CUDA;
@@ -453,8 +493,14 @@ extern "C" cov_status cov_solve_batched(cov_ctx* ctx, const cov_problem* probs, 
 //              ubar^{k-1} = ubar^k + rollout_vjp(lift(xbar)),
 //   s0bar = sum of the rollout adjoints' lambda_0, u0bar = ubar^0.
 // The trajectories s^0..s^{K-1} are the checkpoints (given, or rebuilt by
-// replaying the forward from u0); the field VJP recomputes its Sinkhorn
-// iterations from each checkpoint.
+// replaying the forward from u0).  The field VJP needs the Sinkhorn
+// iterations of each outer iteration: a taped forward keeps their records
+// in the workspace (HBM is plentiful: (2 + d)(n_iter + 2)(T + M) floats per
+// outer iteration), otherwise they are recomputed from the checkpoint.
+//
+// Workspace layout (shared by the taped forward and the backward):
+//   [solve buffers][records: K slots][split buffers][backward buffers][rest]
+// with the records and split buffers present in mode 2 only.
 // ---------------------------------------------------------------------------
 namespace cov {
 size_t lqr_adj_ws_bytes(int T, int n, int m);
@@ -464,9 +510,22 @@ cov_status lqr_vjp_ws(cov_ctx* ctx, void* ws, size_t ws_bytes, int n, int m, con
 cov_status rollout_vjp_ws(cov_ctx* ctx, void* ws, size_t ws_bytes, int n, int m, const double* A, const double* B,
                           const double* sbar, int T, double* ubar, double* s0bar, cudaStream_t stream);
 
+enum BackMode { BM_GIVEN = 0, BM_REPLAY = 1, BM_TAPED = 2 };
+
 struct BackBufs {
     float *xbar, *abf;
     double *abb, *sbar, *ubar, *ub2, *vbar, *lam0, *u, *hist;
+};
+
+struct BackLayout {
+    SolveBufs sb;
+    char* tape0;       // record slot k at tape0 + k * tape_stride
+    size_t tape_stride;
+    float* split;      // split buffers shared by the records' passes
+    BackBufs bb;
+    char* rest;
+    size_t rest_bytes;
+    size_t needed;     // total bytes the mode needs
 };
 
 static BackBufs carve_back(Carver& cv, int T, int d, int n, int m, int n_hist) {
@@ -488,14 +547,37 @@ static bool backward_supported(const cov_problem* P) {
     return P->field == COV_FIELD_SINKHORN && model_is_lti(P->model) && P->d <= 3;
 }
 
-static size_t backward_ws_bytes(const cov_problem* P, int n, int m, int K, bool replay) {
-    Carver cv(nullptr);
-    carve_solve(cv, P->T, P->d, n, m);
-    carve_back(cv, P->T, P->d, n, m, replay ? K : 0);
+// ws == nullptr only measures (L->needed).
+static void carve_layout(void* ws, size_t ws_bytes, const cov_problem* P, int n, int m, int K, int mode,
+                         BackLayout* L) {
+    const int T = P->T, d = P->d;
+    Carver cv(ws);
+    *L = BackLayout{};
+    L->sb = carve_solve(cv, T, d, n, m);
+    if (mode == BM_TAPED) {
+        L->tape_stride = round_up(sinkhorn_tape_bytes(T, P->M, d, P->n_iter, false), 256);
+        L->tape0 = cv.take<char>(L->tape_stride * (size_t)K);
+        L->split = reinterpret_cast<float*>(cv.take<char>(sinkhorn_split_bytes(T, P->M, d)));
+    }
+    L->bb = carve_back(cv, T, d, n, m, mode == BM_REPLAY ? K : 0);
     const size_t used = round_up(cv.off, 256);
-    size_t rest = std::max(sinkhorn_vjp_bytes(P->T, P->M, P->d, P->n_iter), lqr_adj_ws_bytes(P->T, n, m));
-    if (replay) rest = std::max(rest, std::max(sinkhorn_ws_bytes(P->T, P->M, P->d), lqr_ws_bytes(P->T, n, m)));
-    return used + rest + 4096;
+    size_t rest = std::max(lqr_adj_ws_bytes(T, n, m), lqr_ws_bytes(T, n, m));
+    rest = std::max(rest, mode == BM_TAPED ? sinkhorn_vjp_bytes_given(T, P->M, d)
+                                           : sinkhorn_vjp_bytes(T, P->M, d, P->n_iter));
+    if (mode == BM_REPLAY) rest = std::max(rest, sinkhorn_ws_bytes(T, P->M, d));
+    L->needed = used + rest + 4096;
+    L->rest = ws ? static_cast<char*>(ws) + used : nullptr;
+    L->rest_bytes = ws_bytes > used ? ws_bytes - used : 0;
+}
+
+static uint64_t tape_key_of(const cov_problem* P, int K, const double* s_hist, const cov_ctx* ctx) {
+    uint64_t k = 7809847782465536322ull;
+    k = fnv(P, sizeof(cov_problem), k);
+    k = fnv(&K, sizeof(K), k);
+    k = fnv(&s_hist, sizeof(s_hist), k);
+    k = fnv(&ctx->ws, sizeof(ctx->ws), k);
+    k = fnv(&ctx->ws_bytes, sizeof(ctx->ws_bytes), k);
+    return k == 0 ? 1 : k;
 }
 
 // vbar = eta ubar
@@ -524,12 +606,83 @@ __global__ void back_accum_kernel(double* __restrict__ ubar, const double* __res
     if (i < n) s0bar[i] += lam0[i];
 }
 
+// Taped forward: cov_solve from u (initial rollout included) that keeps the
+// checkpoints s_hist[k] and, per outer iteration, the record of its field's
+// Sinkhorn iterations.
+static cov_status solve_taped(cov_ctx* ctx, const cov_problem* prob, int K, double* u, double* s_out,
+                              double* s_hist, cudaStream_t st) {
+    int n, m;
+    cov_status r = validate(prob, &n, &m);
+    if (r != COV_OK) return r;
+    if (!backward_supported(prob)) return COV_ERR_UNSUPPORTED;
+    BackLayout L;
+    carve_layout(nullptr, 0, prob, n, m, K, BM_TAPED, &L);
+    if (!ctx->ws || L.needed > ctx->ws_bytes) return COV_ERR_WORKSPACE;
+    carve_layout(ctx->ws, ctx->ws_bytes, prob, n, m, K, BM_TAPED, &L);
+    ctx->tape_key = 0;
+    const int T = prob->T, d = prob->d;
+    const size_t ss = (size_t)(T + 1) * n;
+    const int nb = (T + 255) / 256;
+    const SolveBufs& b = L.sb;
+    if (K > 0) {
+        // time-invariant gains first (host-side cache decision); A, B do not
+        // read the trajectory, so s_out's current contents do not matter
+        r = ensure_lti_gains(ctx, prob, n, m, b, s_out, u, st);
+        if (r != COV_OK) return r;
+    }
+    auto work = [&](cudaStream_t ws_st) -> cov_status {
+        cov_status q = cov_rollout(ctx, prob->model, prob->s0, u, T, prob->dt, s_out, (cov_stream_t)ws_st);
+        if (q != COV_OK || K == 0) return q;
+        sinkhorn_reference_stats(prob->y, prob->M, d, prob->b, b.scal, ws_st);
+        ctx->tapes.assign(K, SkTape{});
+        for (int k = 0; k < K; ++k) {
+            if (cuda_failed(ctx, cudaMemcpyAsync(s_hist + (size_t)k * ss, s_out, sizeof(double) * ss,
+                                                 cudaMemcpyDeviceToDevice, ws_st)))
+                return COV_ERR_CUDA;
+            extract_kernel<<<nb, 256, 0, ws_st>>>(s_out, T, n, d, b.x);
+            size_t used = 0;
+            q = sinkhorn_tape_ws(ctx, L.tape0 + (size_t)k * L.tape_stride, L.tape_stride, b.x, d, T, prob->y,
+                                 prob->b, prob->M, d, prob->eps, prob->n_iter, b.scal, &ctx->tapes[k], &used, ws_st,
+                                 L.split, b.a);
+            if (q != COV_OK) return q;
+            lift_kernel<<<nb, 256, 0, ws_st>>>(b.a, T, n, d, b.abar);
+            q = lqr_affine(ctx, L.rest, L.rest_bytes, n, m, b.B, b.gains, prob->Q, b.abar, T, b.v, nullptr, ws_st);
+            if (q != COV_OK) return q;
+            q = update_rollout(ctx, prob->model, prob->s0, u, b.v, prob->eta, T, prob->dt, s_out, ws_st);
+            if (q != COV_OK) return q;
+        }
+        return cuda_failed(ctx, cudaGetLastError()) ? COV_ERR_CUDA : COV_OK;
+    };
+    uint64_t key = 5851236489572341227ull;
+    key = fnv(prob, sizeof(cov_problem), key);
+    key = fnv(&K, sizeof(K), key);
+    const void* ptrs[5] = {u, s_out, s_hist, ctx->ws, reinterpret_cast<const void*>(ctx->ws_bytes)};
+    key = fnv(ptrs, sizeof(ptrs), key);
+    r = run_cached_graph(ctx, ctx->ckpt_graph, key, st, work);
+    if (r != COV_OK) return r;
+    if (K > 0) ctx->tape_key = tape_key_of(prob, K, s_hist, ctx);
+    return COV_OK;
+}
+
 }  // namespace cov
 
-extern "C" size_t cov_workspace_size_backward(const cov_problem* prob, int n_outer, int replay) {
+extern "C" cov_status cov_solve_checkpointed(cov_ctx* ctx, const cov_problem* prob, int n_outer, double* u,
+                                             double* s_out, double* s_hist, int flags, cov_stream_t stream) {
+    if (!ctx || !u || !s_out || n_outer < 0 || (!s_hist && n_outer > 0) || (flags & ~COV_CKPT_RECORD))
+        return COV_ERR_INVALID_ARG;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return COV_ERR_CUDA;
+    if (flags & COV_CKPT_RECORD) return cov::solve_taped(ctx, prob, n_outer, u, s_out, s_hist, (cudaStream_t)stream);
+    return cov::solve_impl(ctx, prob, n_outer, u, s_out, (cudaStream_t)stream, true, s_hist);
+}
+
+extern "C" size_t cov_workspace_size_backward(const cov_problem* prob, int n_outer, int mode) {
     int n, m;
-    if (!prob || n_outer < 0 || cov::validate(prob, &n, &m) != COV_OK || !cov::backward_supported(prob)) return 0;
-    return cov::backward_ws_bytes(prob, n, m, n_outer, replay != 0);
+    if (!prob || n_outer < 0 || mode < 0 || mode > 2 || cov::validate(prob, &n, &m) != COV_OK ||
+        !cov::backward_supported(prob))
+        return 0;
+    cov::BackLayout L;
+    cov::carve_layout(nullptr, 0, prob, n, m, n_outer, mode, &L);
+    return L.needed;
 }
 
 extern "C" cov_status cov_solve_backward(cov_ctx* ctx, const cov_problem* prob, int n_outer, const double* u0,
@@ -544,22 +697,32 @@ extern "C" cov_status cov_solve_backward(cov_ctx* ctx, const cov_problem* prob, 
     if (prob->b && !bbar) return COV_ERR_INVALID_ARG;
     if (cudaSetDevice(ctx->device) != cudaSuccess) return COV_ERR_CUDA;
     const int T = prob->T, d = prob->d, K = n_outer;
-    const bool replay = (s_hist == nullptr);
-    Carver cv(ctx->ws);
-    SolveBufs sb = carve_solve(cv, T, d, n, m);
-    BackBufs bb = carve_back(cv, T, d, n, m, replay ? K : 0);
-    const size_t used = round_up(cv.off, 256);
-    if (!ctx->ws || used > ctx->ws_bytes) return COV_ERR_WORKSPACE;
-    void* rest = static_cast<char*>(ctx->ws) + used;
-    const size_t rest_bytes = ctx->ws_bytes - used;
-    if (backward_ws_bytes(prob, n, m, K, replay) > ctx->ws_bytes) return COV_ERR_WORKSPACE;
-    cudaStream_t st = (cudaStream_t)stream;
+    int mode = s_hist ? BM_GIVEN : BM_REPLAY;
+    if (s_hist && K > 0 && ctx->tape_key == tape_key_of(prob, K, s_hist, ctx) && (int)ctx->tapes.size() == K)
+        mode = BM_TAPED;
+    BackLayout L;
+    carve_layout(nullptr, 0, prob, n, m, K, mode, &L);
+    if (!ctx->ws || L.needed > ctx->ws_bytes) return COV_ERR_WORKSPACE;
+    carve_layout(ctx->ws, ctx->ws_bytes, prob, n, m, K, mode, &L);
+    if (mode != BM_TAPED) ctx->tape_key = 0;  // the backward buffers overlap the record slots
+    const SolveBufs& sb = L.sb;
+    const BackBufs& bb = L.bb;
+    void* rest = L.rest;
+    const size_t rest_bytes = L.rest_bytes;
+    cudaStream_t stream0 = (cudaStream_t)stream;
     const size_t ss = (size_t)(T + 1) * n;
     const int nb = (T + 256) / 256;
 
+    // A, B (time-invariant: any state will do) and the Riccati gains, shared
+    // with cov_solve's cache (same solve buffers at the start of the
+    // workspace); decided on the host before the reverse sweep is enqueued
+    r = ensure_lti_gains(ctx, prob, n, m, sb, sbar_K, u0, stream0);
+    if (r != COV_OK) return r;
+    auto work = [&](cudaStream_t st) -> cov_status {
+    cov_status r = COV_OK;
     sinkhorn_reference_stats(prob->y, prob->M, d, prob->b, sb.scal, st);
     const double* hist = s_hist;
-    if (replay) {
+    if (mode == BM_REPLAY) {
         // rebuild the checkpoints s^0..s^{K-1} from u0
         if (cuda_failed(ctx, cudaMemcpyAsync(bb.u, u0, sizeof(double) * T * m, cudaMemcpyDeviceToDevice, st)))
             return COV_ERR_CUDA;
@@ -569,17 +732,7 @@ extern "C" cov_status cov_solve_backward(cov_ctx* ctx, const cov_problem* prob, 
         }
         hist = bb.hist;
     }
-    // A, B (time-invariant: any state will do) and the Riccati gains, shared
-    // with cov_solve's cache (same solve buffers at the start of the workspace)
-    const uint64_t gk = lti_gains_key(prob, ctx->ws);
-    if (ctx->gains_key != gk) {
-        r = linearize_launch(ctx, prob->model, K > 0 ? hist : sbar_K, u0, T, prob->dt, sb.A, sb.B, st);
-        if (r != COV_OK) return r;
-        r = lqr_riccati(ctx, n, m, sb.A, sb.B, prob->Q, prob->R, T, sb.gains, st);
-        if (r != COV_OK) return r;
-        ctx->gains_key = gk;
-    }
-    if (replay) {
+    if (mode == BM_REPLAY) {
         for (int k = 1; k < K; ++k) {
             double* sk = bb.hist + (size_t)k * ss;
             if (cuda_failed(ctx, cudaMemcpyAsync(sk, sk - ss, sizeof(double) * ss, cudaMemcpyDeviceToDevice, st)))
@@ -601,10 +754,10 @@ extern "C" cov_status cov_solve_backward(cov_ctx* ctx, const cov_problem* prob, 
         r = lqr_vjp_ws(ctx, rest, rest_bytes, n, m, sb.B, sb.gains, prob->Q, bb.vbar, T, bb.abb, st);
         if (r != COV_OK) return r;
         narrow_kernel<<<nb, 256, 0, st>>>(bb.abb, T, n, d, bb.abf);
-        extract_kernel<<<nb, 256, 0, st>>>(hist + (size_t)(k - 1) * ss, T, n, d, sb.x);
+        if (mode != BM_TAPED) extract_kernel<<<nb, 256, 0, st>>>(hist + (size_t)(k - 1) * ss, T, n, d, sb.x);
         r = sinkhorn_vjp_ws(ctx, rest, rest_bytes, sb.x, d, T, prob->y, prob->b, prob->M, d, prob->eps,
                             prob->n_iter, sb.scal, bb.abf, d, bb.xbar, d, ybar, prob->b ? bbar : nullptr,
-                            k != K ? 1 : 0, st);
+                            k != K ? 1 : 0, st, mode == BM_TAPED ? &ctx->tapes[k - 1] : nullptr);
         if (r != COV_OK) return r;
         lift_bar_kernel<<<nb, 256, 0, st>>>(bb.xbar, T, n, d, bb.sbar);
         r = rollout_vjp_ws(ctx, rest, rest_bytes, n, m, sb.A, sb.B, bb.sbar, T, bb.ub2, bb.lam0, st);
@@ -615,4 +768,13 @@ extern "C" cov_status cov_solve_backward(cov_ctx* ctx, const cov_problem* prob, 
         return COV_ERR_CUDA;
     if (cuda_failed(ctx, cudaGetLastError())) return COV_ERR_CUDA;
     return COV_OK;
+    };
+    uint64_t key = 2305843009213693951ull;
+    key = fnv(prob, sizeof(cov_problem), key);
+    key = fnv(&K, sizeof(K), key);
+    key = fnv(&mode, sizeof(mode), key);
+    const void* ptrs[9] = {u0, s_hist, sbar_K, ybar, bbar, s0bar, u0bar, ctx->ws,
+                           reinterpret_cast<const void*>(ctx->ws_bytes)};
+    key = fnv(ptrs, sizeof(ptrs), key);
+    return run_cached_graph(ctx, ctx->back_graph, key, stream0, work);
 }

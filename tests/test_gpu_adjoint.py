@@ -171,3 +171,30 @@ def test_solve_backward_translation_identity_at_full_size(cov, ctx):
     wb = _h(bb) * bh
     assert abs(wb.sum()) <= 1e-3 * np.abs(wb).sum()
     assert np.isfinite(_h(u0b)).all()
+
+
+def test_recorded_forward_gives_the_recomputed_gradient(cov, ctx):
+    """A recording forward keeps every outer iteration's Sinkhorn record; the
+    backward then skips the recomputation and must give, bit for bit, the
+    gradient that recomputing from the same checkpoints gives.  The recorded
+    forward itself follows cov_solve to FP32 rounding."""
+    inst = wl.make_instance(wl.SINKHORN_DOUBLE_T4096, T=700, M=900)
+    K = 4
+    (P, keep), y, b = _problem(cov, inst)
+    u_rec = _dev64(inst.u0)
+    s_rec, hist = cov.cov_solve_checkpointed(ctx, (P, keep), K, u_rec, record=True)
+    sbar = _dev64(wl.rng(503).standard_normal((inst.u0.shape[0] + 1, 4)))
+    u0 = _dev64(inst.u0)
+    g_rec = cov.cov_solve_backward(ctx, (P, keep), K, u0, sbar, s_hist=hist)
+    g_rec2 = cov.cov_solve_backward(ctx, (P, keep), K, u0, sbar, s_hist=hist)  # records still valid
+    hist2 = hist.clone()  # another pointer: the records do not apply, the backward recomputes
+    g_cmp = cov.cov_solve_backward(ctx, (P, keep), K, u0, sbar, s_hist=hist2)
+    st, flags = ctx.device_status()
+    assert st == cov.COV_OK, flags
+    for a, a2, c in zip(g_rec, g_rec2, g_cmp):
+        np.testing.assert_array_equal(_h(a), _h(c))
+        np.testing.assert_array_equal(_h(a2), _h(c))
+    u_pl = _dev64(inst.u0)
+    s_pl = cov.cov_solve(ctx, (P, keep), K, u_pl)
+    s_init = _h(hist[0])
+    assert _rel(_h(s_rec) - s_init, _h(s_pl) - s_init) <= 1e-4

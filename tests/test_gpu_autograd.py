@@ -81,3 +81,34 @@ def test_reparameterised_mixture_gradients_are_the_chain_rule(cov, ctx):
     assert torch.isfinite(log_sigma.grad).all() and torch.isfinite(logits.grad).all()
     # softmax weights: the logits gradient sums to zero (shift invariance)
     assert abs(float(logits.grad.sum())) <= 1e-5 * float(logits.grad.abs().sum() + 1e-12)
+
+
+def test_interleaved_forwards_fall_back_to_recomputation(cov, ctx):
+    """Two forwards, then the first one's backward: the records on the
+    context belong to the second forward, so the first backward must
+    recompute its Sinkhorn iterations -- and give the gradient a plain
+    forward/backward pair gives."""
+    from paper_2511_11514_b300 import autograd as ag
+    T, M, dt, K = 256, 300, 0.05, 2
+    s0h, u0h = wl.double_int_init(T, dt)
+    dev = torch.device("cuda")
+    spec = dict(model=wl.DOUBLE_INT, dt=dt, Q=wl.coverage_Q(wl.DOUBLE_INT), R=0.05 * np.eye(2), eta=0.5, eps=0.05,
+                n_iter=5, n_outer=K)
+    u0 = torch.as_tensor(u0h, device=dev)
+    y_a = torch.tensor(wl.random_points(M, 2, seed=11), dtype=torch.float32, device=dev, requires_grad=True)
+    y_b = torch.tensor(wl.random_points(M, 2, seed=12), dtype=torch.float32, device=dev, requires_grad=True)
+    y_ref = torch.tensor(y_a.detach().cpu().numpy(), dtype=torch.float32, device=dev, requires_grad=True)
+    w = torch.as_tensor(wl.random_points(T + 1, 4, seed=13), device=dev)
+
+    def loss(y):
+        return (ag.CoverageSolve.apply(y, None, torch.tensor(s0h), u0, spec, ctx) * w).sum()
+
+    loss(y_ref).backward()           # forward + backward with the records
+    La = loss(y_a)
+    Lb = loss(y_b)                   # overwrites the records
+    La.backward()                    # recomputes
+    Lb.backward()                    # uses the records
+    st, flags = ctx.device_status()
+    assert st == cov.COV_OK, flags
+    torch.testing.assert_close(y_a.grad, y_ref.grad, rtol=0, atol=0)
+    assert torch.isfinite(y_b.grad).all()
