@@ -19,6 +19,7 @@ row samples of the same workload); it is the reference arm.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import os
 import statistics
@@ -65,6 +66,9 @@ def parse_args():
                     help="skip the all-pairs roofline at T = 65536, M = 262144")
     ap.add_argument("--adjoint", action="store_true",
                     help="time the differentiation workload: forward and backward through 20 outer iterations")
+    ap.add_argument("--adjoint-outer", type=int, default=0,
+                    help="outer iterations of --adjoint (default: the workload's 20; fewer only to keep a "
+                         "profiler's launch list short)")
     return ap.parse_args()
 
 
@@ -483,6 +487,8 @@ def run_adjoint(args):
 
     torch.cuda.set_device(0)
     w = wl.ADJOINT_DOUBLE_T2048
+    if args.adjoint_outer:
+        w = dataclasses.replace(w, n_outer=args.adjoint_outer)
     inst = wl.make_instance(w)
     ctx = cov.Context(0)
     # the loss runs on its own context: a field call on the solve's context
@@ -540,6 +546,49 @@ def run_adjoint(args):
         raise SystemExit(f"device status {cov.status_string(st)} flags {flags}")
     f_ms, b_ms = statistics.median(fw), statistics.median(bw)
     pairs_fwd = w.n_outer * w.pairs_per_field
+
+    # roofline of the reverse all-pairs kernel (adj_kernel, column sums): per
+    # Sinkhorn iteration the reverse sweep evaluates 2TM + T^2 pairs; its time
+    # is the field VJP's per-iteration cost minus the recorded forward's,
+    # both as (t(n_hi) - t(n_lo)) / (n_hi - n_lo) at the workload's sizes
+    xr = torch.as_tensor(wl.random_points(w.T, 2, seed=w.seed + 3000, lo=0.1, hi=0.9), dtype=torch.float32,
+                         device=dev)
+    yr, br = ag.gmm_reference(mu.detach(), log_sigma.detach(), logits.detach(), xi)
+    ar = torch.as_tensor(wl.f32_pair(wl.rng(w.seed + 3001).standard_normal((w.T, 2)))[1], dtype=torch.float32,
+                         device=dev)
+
+    def per_iter_ms(fn, lo=10, hi=50, reps=5):
+        def t(n):
+            ts = []
+            for _ in range(reps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                e0.record()
+                fn(n)
+                e1.record()
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            return statistics.median(ts)
+        fn(lo)
+        fn(hi)
+        return (t(hi) - t(lo)) / (hi - lo)
+
+    vjp_it = per_iter_ms(lambda n: cov.cov_field_sinkhorn_vjp(lctx, xr, yr, w.eps, n, ar, b=br))
+    fwd_it = per_iter_ms(lambda n: cov.cov_field_sinkhorn(lctx, xr, yr, w.eps, n, b=br, field=False))
+    rev_ms = max(vjp_it - fwd_it, 1e-9)
+    rev_pairs = 2 * w.T * w.M + w.T * w.T
+    adj_peak = SM_COUNT_NOMINAL * SM_MAX_MHZ_NOMINAL * 1e6 * FP32_LANES_PER_SM_CLK / 7
+    achieved = rev_pairs / (rev_ms * 1e-3)
+    # the same at a size where a launch is long enough to reach steady state
+    TL, ML = 16384, 65536
+    xl = torch.as_tensor(wl.random_points(TL, 2, seed=w.seed + 3002, lo=0.1, hi=0.9), dtype=torch.float32, device=dev)
+    yl_ = torch.as_tensor(wl.random_points(ML, 2, seed=w.seed + 3003), dtype=torch.float32, device=dev)
+    al_ = torch.as_tensor(wl.f32_pair(wl.rng(w.seed + 3004).standard_normal((TL, 2)))[1], dtype=torch.float32,
+                          device=dev)
+    vjp_l = per_iter_ms(lambda n: cov.cov_field_sinkhorn_vjp(lctx, xl, yl_, w.eps, n, al_), lo=2, hi=6, reps=3)
+    fwd_l = per_iter_ms(lambda n: cov.cov_field_sinkhorn(lctx, xl, yl_, w.eps, n, field=False), lo=2, hi=6, reps=3)
+    rev_l = max(vjp_l - fwd_l, 1e-9)
+    achieved_l = (2 * TL * ML + TL * TL) / (rev_l * 1e-3)
     line = {"metric": "backward/forward time ratio of the coverage-loss gradient", "value": b_ms / f_ms,
             "unit": "x", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": f_ms + b_ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
@@ -549,6 +598,16 @@ def run_adjoint(args):
                        f"eps={eps_l}, {it_l} iterations", "params": "means, log-sigmas, logits, s0",
                        "pairs_forward": pairs_fwd, "l2": "not flushed (forward and backward alternate)"},
             "ms_forward": f_ms, "ms_backward": b_ms,
+            "roofline": {"bound": "alu", "kernel": "adj_kernel (reverse column sums)", "achieved": achieved,
+                         "peak": adj_peak, "unit": "pair-evals/s", "frac": achieved / adj_peak, "traffic": None,
+                         "peak_basis": "148 SMs x 2032 MHz x 128 FP32 lanes / 7 FP32 ops per pair "
+                                       "(derived from unit counts and clocks; ex2 at 32/clk/SM is not binding)",
+                         "how": "(field VJP - forward) per Sinkhorn iteration, (t(50) - t(10)) / 40, "
+                                "2TM + T^2 pairs per reverse iteration"},
+            "ms_per_sinkhorn_iteration": {"forward": fwd_it, "field_vjp": vjp_it, "reverse": rev_ms},
+            "roofline_large": {"bound": "alu", "T": TL, "M": ML, "achieved": achieved_l, "peak": adj_peak,
+                               "unit": "pair-evals/s", "frac": achieved_l / adj_peak,
+                               "ms_per_sinkhorn_iteration": {"forward": fwd_l, "field_vjp": vjp_l, "reverse": rev_l}},
             "forward_pairs_per_s": pairs_fwd / (f_ms * 1e-3), "loss": losses[-1],
             "grad_norms": {"mu": float(mu.grad.norm()), "log_sigma": float(log_sigma.grad.norm()),
                            "logits": float(logits.grad.norm()), "s0": float(s0.grad.norm())},

@@ -102,9 +102,10 @@ def gmm_reference(mu, log_sigma, logits, xi):
     per = M // K
     if per * K != M:
         raise ValueError("M must be a multiple of the number of components")
-    comp = torch.arange(M, device=xi.device) // per
-    y = mu[comp] + torch.exp(log_sigma)[comp, None] * xi
-    b = torch.softmax(logits, 0)[comp] / per
+    # broadcast over the per-component blocks (a gather's backward would be a
+    # scatter-add; this one is a plain reduction)
+    y = (mu[:, None, :] + torch.exp(log_sigma)[:, None, None] * xi.view(K, per, d)).reshape(M, d)
+    b = (torch.softmax(logits, 0)[:, None] / per).expand(K, per).reshape(M)
     return y.float().contiguous(), b.float().contiguous()
 
 
