@@ -115,15 +115,21 @@ struct RicSmem {
     double P[N * N], PA[N * N], PB[N * MC], S[MC * MC], G[MC * N], AtPA[N * N], K[MC * N];
 };
 
+// One warp per block.  Pinit == nullptr: block 0 runs t = T-1..0 from
+// P_T = Q.  Otherwise block c runs its chunk t = min(T, (c+1) Cc) - 1 .. c Cc
+// from the given P entering it, Pinit[c] (the parallel-in-time fill).
 template <int N, int MC>
 __global__ void __launch_bounds__(32, 1) riccati_kernel(const double* __restrict__ A, const double* __restrict__ B,
                                                         LqrConst C, int T, double* __restrict__ Kg,
                                                         double* __restrict__ Mg, double* __restrict__ Ng,
-                                                        double* __restrict__ Sg, unsigned* status) {
+                                                        double* __restrict__ Sg, unsigned* status,
+                                                        const double* __restrict__ Pinit, int Cc) {
     __shared__ __align__(16) RicSmem<N, MC> sm;
     const int lane = threadIdx.x;
     bool spd_ok = true;
-    for (int e = lane; e < N * N; e += 32) sm.P[e] = C.Q[e];
+    const int lo = Pinit ? blockIdx.x * Cc : 0;
+    const int hi = Pinit ? min(T, lo + Cc) - 1 : T - 1;
+    for (int e = lane; e < N * N; e += 32) sm.P[e] = Pinit ? Pinit[(size_t)blockIdx.x * N * N + e] : C.Q[e];
 
     // phase-1 role of this lane: PA = P'A (N*N entries) or PB = P'B (N*MC)
     const bool p1v = lane < N * N + N * MC;
@@ -134,7 +140,7 @@ __global__ void __launch_bounds__(32, 1) riccati_kernel(const double* __restrict
     double* p1dst = p1A ? &sm.PA[p1f] : &sm.PB[p1v ? p1f : 0];
     constexpr int NP2 = MC * MC + MC * N + N * N;
 
-    const SubBlocks sb(0, T - 1, true);
+    const SubBlocks sb(lo, hi, true);
     auto issue = [&](int b, int buf) {
         stream_rows(&sm.A[buf][0][0], A, sb.first(b), sb.count(b), N * N, lane);
         stream_rows(&sm.B[buf][0][0], B, sb.first(b), sb.count(b), N * MC, lane);
@@ -233,6 +239,252 @@ __global__ void __launch_bounds__(32, 1) riccati_kernel(const double* __restrict
         __syncwarp();
     }
     if (!spd_ok) raise_status(status, kDevNotSpd);
+}
+
+// ---------------------------------------------------------------------------
+// Parallel-in-time Riccati.  One step is the map
+//   P_t = F_t(P_{t+1}) = Q_t + A_t' P' (I + G_t P')^-1 A_t,  G_t = B_t R^-1 B_t'
+// (the Riccati update by the push-through identity).  Maps of the form
+// F(P) = J + E' P (I + C P)^-1 E (E square, C and J symmetric PSD) are
+// closed under composition: F1(F2(P)) has
+//   W = (I + C1 J2)^-1,  E = E2 W E1,  C = C2 + E2 W C1 E2',  J = J1 + (W E1)' J2 E1,
+// with every inverse of the form I + (PSD)(PSD), whose eigenvalues are >= 1.
+// Chunks compose their maps (one warp each), one warp chains the chunk maps
+// from P_T = Q to get the P entering every chunk, and each chunk then runs
+// the ordinary Riccati step over its own steps from that P (riccati_kernel).
+// ---------------------------------------------------------------------------
+
+// In-warp inverse of a general N x N matrix (N <= 4) by Gauss-Jordan with
+// partial pivoting.  X is overwritten; the inverse is written to Xi.  aug is
+// N x 2N shared scratch.  Every lane calls it.
+template <int N>
+__device__ void warp_inverse(double* X, double* Xi, double* aug, int* piv, int lane) {
+    constexpr int W2 = 2 * N;
+    for (int e = lane; e < N * W2; e += 32) {
+        const int r = e / W2, c = e % W2;
+        aug[e] = c < N ? X[r * N + c] : (c - N == r ? 1.0 : 0.0);
+    }
+    __syncwarp();
+    for (int k = 0; k < N; ++k) {
+        if (lane == 0) {
+            int p = k;
+            double best = fabs(aug[k * W2 + k]);
+            for (int r = k + 1; r < N; ++r) {
+                const double v = fabs(aug[r * W2 + k]);
+                if (v > best) { best = v; p = r; }
+            }
+            *piv = p;
+        }
+        __syncwarp();
+        const int p = *piv;
+        if (p != k && lane < W2) {
+            const double t = aug[k * W2 + lane];
+            aug[k * W2 + lane] = aug[p * W2 + lane];
+            aug[p * W2 + lane] = t;
+        }
+        __syncwarp();
+        const double inv_piv = 1.0 / aug[k * W2 + k];
+        double v = 0.0, f = 0.0, rk = 0.0;
+        const int r = lane / W2, c = lane % W2;
+        if (lane < N * W2) {
+            v = aug[lane];
+            f = aug[r * W2 + k];
+            rk = aug[k * W2 + c] * inv_piv;
+        }
+        __syncwarp();
+        if (lane < N * W2) aug[lane] = (r == k) ? rk : fma(-f, rk, v);
+        __syncwarp();
+    }
+    for (int e = lane; e < N * N; e += 32) Xi[e] = aug[(e / N) * W2 + N + e % N];
+    __syncwarp();
+}
+
+// Z = X Y (+ Z0), N x N row-major, lanes [off, off + N*N) each one entry.
+template <int N>
+__device__ __forceinline__ double mat_entry(const double* X, const double* Y, int r, int c, bool yT) {
+    double acc = 0.0;
+#pragma unroll
+    for (int q = 0; q < N; ++q) acc = fma(X[r * N + q], yT ? Y[c * N + q] : Y[q * N + c], acc);
+    return acc;
+}
+
+template <int N>
+struct RicMap {
+    double E[N * N], C[N * N], J[N * N];
+};
+
+template <int N, int MC>
+struct ComposeSmem {
+    double A[2][kSB][N * N];
+    double B[2][kSB][N * MC];
+    RicMap<N> acc;
+    double E1[N * N], C1[N * N], J1[N * N], X[N * N], W[N * N], V[N * N], Y[N * N], U[N * N], Z[N * N], BRi[N * MC];
+    double aug[N * 2 * N];
+    int piv;
+};
+
+template <int N, int MC>
+__global__ void __launch_bounds__(32, 1) ric_compose_kernel(const double* __restrict__ A, const double* __restrict__ B,
+                                                            LqrConst Cq, int T, int Cc,
+                                                            double* __restrict__ maps, unsigned* status) {
+    __shared__ __align__(16) ComposeSmem<N, MC> sm;
+    const int lane = threadIdx.x;
+    const int lo = blockIdx.x * Cc, hi = min(T, lo + Cc) - 1;
+    constexpr int NN = N * N;
+    // lanes [0, NN) and [16, 16 + NN) each own one entry (r, c) of an N x N product
+    const bool lo16 = lane < NN, hi16 = lane >= 16 && lane < 16 + NN;
+    const int q16 = lo16 ? lane : (hi16 ? lane - 16 : 0);
+    const int r = q16 / N, c = q16 % N;
+    const SubBlocks sb(lo, hi, true);
+    auto issue = [&](int b, int buf) {
+        stream_rows(&sm.A[buf][0][0], A, sb.first(b), sb.count(b), NN, lane);
+        stream_rows(&sm.B[buf][0][0], B, sb.first(b), sb.count(b), N * MC, lane);
+        cp_async_commit();
+    };
+    issue(0, 0);
+    bool first = true;
+    for (int b = 0; b < sb.n; ++b) {
+        const int buf = b & 1;
+        if (b + 1 < sb.n) {
+            issue(b + 1, buf ^ 1);
+            cp_async_wait_all_but_one();
+        } else {
+            cp_async_wait_all();
+        }
+        __syncwarp();
+        const int t0 = sb.first(b);
+        for (int j = sb.count(b) - 1; j >= 0; --j) {
+            const int t = t0 + j;
+            const double* At = sm.A[buf][j];
+            const double* Bt = sm.B[buf][j];
+            // the step's map: E1 = A_t, C1 = B_t R^-1 B_t', J1 = Q_t
+            if (lane < N * MC) {
+                const int rr = lane / MC, cc = lane % MC;
+                double acc = 0.0;
+                for (int q = 0; q < MC; ++q) acc = fma(Bt[rr * MC + q], Cq.R[q * MC + cc], acc);  // R holds R^-1
+                sm.BRi[lane] = acc;
+            }
+            __syncwarp();
+            if (lo16) {
+                double acc = 0.0;
+                for (int q = 0; q < MC; ++q) acc = fma(sm.BRi[r * MC + q], Bt[c * MC + q], acc);
+                sm.E1[lane] = At[lane];
+                sm.J1[lane] = t >= 1 ? Cq.Q[lane] : 0.0;
+                if (r <= c) {
+                    sm.C1[r * N + c] = acc;
+                    sm.C1[c * N + r] = acc;
+                }
+            }
+            __syncwarp();
+            if (first) {
+                if (lo16) {
+                    sm.acc.E[lane] = sm.E1[lane];
+                    sm.acc.C[lane] = sm.C1[lane];
+                    sm.acc.J[lane] = sm.J1[lane];
+                }
+                first = false;
+                __syncwarp();
+                continue;
+            }
+            // acc <- (step map) o acc
+            if (lo16) sm.X[lane] = (r == c ? 1.0 : 0.0) + mat_entry<N>(sm.C1, sm.acc.J, r, c, false);
+            __syncwarp();
+            warp_inverse<N>(sm.X, sm.W, sm.aug, &sm.piv, lane);
+            if (lo16) sm.V[lane] = mat_entry<N>(sm.W, sm.E1, r, c, false);
+            if (hi16) sm.Y[lane - 16] = mat_entry<N>(sm.W, sm.C1, r, c, false);
+            __syncwarp();
+            double e_new = 0.0, u_new = 0.0;
+            if (lo16) e_new = mat_entry<N>(sm.acc.E, sm.V, r, c, false);
+            if (hi16) u_new = mat_entry<N>(sm.acc.J, sm.E1, r, c, false);
+            __syncwarp();
+            if (hi16) sm.U[lane - 16] = u_new;
+            __syncwarp();
+            double j_new = 0.0, z_new = 0.0;
+            if (lo16) {  // J = J1 + V' U
+                double acc = sm.J1[lane];
+#pragma unroll
+                for (int q = 0; q < N; ++q) acc = fma(sm.V[q * N + r], sm.U[q * N + c], acc);
+                j_new = acc;
+            }
+            if (hi16) z_new = mat_entry<N>(sm.acc.E, sm.Y, r, c, false);
+            __syncwarp();
+            if (lo16 && r <= c) {
+                sm.acc.J[r * N + c] = j_new;
+                sm.acc.J[c * N + r] = j_new;
+            }
+            if (hi16) sm.Z[lane - 16] = z_new;
+            __syncwarp();
+            double c_new = 0.0;
+            if (lo16) c_new = sm.acc.C[lane] + mat_entry<N>(sm.Z, sm.acc.E, r, c, true);  // C2 + Z E2'
+            __syncwarp();
+            if (lo16) {
+                sm.acc.E[lane] = e_new;
+                if (r <= c) {
+                    sm.acc.C[r * N + c] = c_new;
+                    sm.acc.C[c * N + r] = c_new;
+                }
+            }
+            __syncwarp();
+        }
+        __syncwarp();
+    }
+    bool ok = true;
+    if (lo16) {
+        double* m = maps + (size_t)blockIdx.x * 3 * NN;
+        m[lane] = sm.acc.E[lane];
+        m[NN + lane] = sm.acc.C[lane];
+        m[2 * NN + lane] = sm.acc.J[lane];
+        ok = isfinite(sm.acc.E[lane]) && isfinite(sm.acc.C[lane]) && isfinite(sm.acc.J[lane]);
+    }
+    if (!ok) raise_status(status, kDevNonfinite);
+}
+
+// One warp: Pin[c] = the P entering chunk c (P_{hi+1}), from P_T = Q.
+template <int N>
+__global__ void __launch_bounds__(32, 1) ric_chain_kernel(const double* __restrict__ maps, int n_chunks, LqrConst Cq,
+                                                          double* __restrict__ Pin, unsigned* status) {
+    constexpr int NN = N * N;
+    __shared__ double P[NN], X[NN], W[NN], V[NN], aug[N * 2 * N];
+    __shared__ int piv;
+    const int lane = threadIdx.x;
+    const bool lo16 = lane < NN;
+    const int r = lo16 ? lane / N : 0, c = lo16 ? lane % N : 0;
+    if (lo16) P[lane] = Cq.Q[lane];
+    __syncwarp();
+    bool ok = true;
+    for (int k = n_chunks - 1; k >= 0; --k) {
+        const double* E = maps + (size_t)k * 3 * NN;
+        const double* Cm = E + NN;
+        const double* J = E + 2 * NN;
+        if (lo16) {
+            Pin[(size_t)k * NN + lane] = P[lane];
+            X[lane] = (r == c ? 1.0 : 0.0) + mat_entry<N>(Cm, P, r, c, false);
+        }
+        __syncwarp();
+        warp_inverse<N>(X, W, aug, &piv, lane);
+        if (lo16) V[lane] = mat_entry<N>(W, E, r, c, false);  // (I + C P)^-1 E
+        __syncwarp();
+        double x = 0.0;
+        if (lo16) x = mat_entry<N>(P, V, r, c, false);      // P (I + C P)^-1 E
+        __syncwarp();
+        if (lo16) X[lane] = x;
+        __syncwarp();
+        double pn = 0.0;
+        if (lo16) {  // J + E' X
+            double acc = J[lane];
+#pragma unroll
+            for (int q = 0; q < N; ++q) acc = fma(E[q * N + r], X[q * N + c], acc);
+            pn = acc;
+            ok &= isfinite(pn);
+        }
+        __syncwarp();
+        if (lo16 && r <= c) {
+            P[r * N + c] = pn;
+            P[c * N + r] = pn;
+        }
+        __syncwarp();
+    }
+    if (!__all_sync(0xffffffffu, ok) && lane == 0) raise_status(status, kDevNonfinite);
 }
 
 // ---------------------------------------------------------------------------
@@ -652,9 +904,11 @@ static bool scan_plan(int T, ScanPlan* p) {
     return true;
 }
 
-// Gains per step: K [m][n], M [n][n], N [m][n], S^-1 [m][m].
+// Gains per step: K [m][n], M [n][n], N [m][n], S^-1 [m][m]; then the
+// parallel Riccati's scratch: chunk maps [chunks][3][n][n] and the P
+// entering each chunk [chunks][n][n].
 size_t lqr_gain_doubles(int T, int n, int m) {
-    return (size_t)T * (2 * (size_t)m * n + (size_t)n * n + (size_t)m * m);
+    return (size_t)T * (2 * (size_t)m * n + (size_t)n * n + (size_t)m * m) + (size_t)kMaxChunks * 4 * n * n;
 }
 
 struct AffineBufs {
@@ -692,14 +946,50 @@ static bool make_lqr_const(const double* Q, const double* R, int n, int m, LqrCo
     return true;
 }
 
+// Horizons at least this long use the parallel-in-time Riccati.
+constexpr int kParRiccatiMinT = 64;
+
 template <int N, int MC>
-static void launch_riccati_t(const double* A, const double* B, const LqrConst& C, int T, double* gains, unsigned* st,
-                             cudaStream_t s) {
+static void launch_riccati_t(const double* A, const double* B, const LqrConst& C, const LqrConst& Ci, int T,
+                             double* gains, unsigned* st, cudaStream_t s) {
     double* K = gains;
     double* M = gains + (size_t)T * MC * N;
     double* Nt = M + (size_t)T * N * N;
     double* Si = Nt + (size_t)T * MC * N;
-    riccati_kernel<N, MC><<<1, 32, 0, s>>>(A, B, C, T, K, M, Nt, Si, st);
+    ScanPlan pl;
+    if (T < kParRiccatiMinT || !scan_plan(T, &pl)) {
+        riccati_kernel<N, MC><<<1, 32, 0, s>>>(A, B, C, T, K, M, Nt, Si, st, nullptr, T);
+        return;
+    }
+    double* maps = Si + (size_t)T * MC * MC;
+    double* pin = maps + (size_t)kMaxChunks * 3 * N * N;
+    ric_compose_kernel<N, MC><<<pl.n_chunks, 32, 0, s>>>(A, B, Ci, T, pl.C, maps, st);
+    ric_chain_kernel<N><<<1, 32, 0, s>>>(maps, pl.n_chunks, C, pin, st);
+    riccati_kernel<N, MC><<<pl.n_chunks, 32, 0, s>>>(A, B, C, T, K, M, Nt, Si, st, pin, pl.C);
+}
+
+// R^-1 on the host (m <= 3, Gauss-Jordan with partial pivoting).
+static bool invert_small(const double* R, int m, double* Ri) {
+    double a[COV_MAX_M][2 * COV_MAX_M];
+    for (int r = 0; r < m; ++r)
+        for (int c = 0; c < 2 * m; ++c) a[r][c] = c < m ? R[r * m + c] : (c - m == r ? 1.0 : 0.0);
+    for (int k = 0; k < m; ++k) {
+        int p = k;
+        for (int r = k + 1; r < m; ++r)
+            if (fabs(a[r][k]) > fabs(a[p][k])) p = r;
+        if (!(fabs(a[p][k]) > 0.0)) return false;
+        for (int c = 0; c < 2 * m; ++c) std::swap(a[k][c], a[p][c]);
+        const double iv = 1.0 / a[k][k];
+        for (int c = 0; c < 2 * m; ++c) a[k][c] *= iv;
+        for (int r = 0; r < m; ++r) {
+            if (r == k) continue;
+            const double f = a[r][k];
+            for (int c = 0; c < 2 * m; ++c) a[r][c] -= f * a[k][c];
+        }
+    }
+    for (int r = 0; r < m; ++r)
+        for (int c = 0; c < m; ++c) Ri[r * m + c] = a[r][m + c];
+    return true;
 }
 
 template <int N, int MC>
@@ -743,10 +1033,12 @@ cov_status lqr_riccati(cov_ctx* ctx, int n, int m, const double* A, const double
                        const double* R, int T, double* gains, cudaStream_t stream) {
     LqrConst C;
     if (!make_lqr_const(Q, R, n, m, &C)) return COV_ERR_INVALID_ARG;
-#define COV_RIC_CASE(NN, MM)                                                  \
-    if (n == NN && m == MM) {                                                 \
-        launch_riccati_t<NN, MM>(A, B, C, T, gains, ctx->status, stream);     \
-        return cuda_failed(ctx, cudaGetLastError()) ? COV_ERR_CUDA : COV_OK; \
+    LqrConst Ci = C;  // the compose kernel takes R^-1 in place of R
+    if (!invert_small(R, m, Ci.R)) return COV_ERR_INVALID_ARG;
+#define COV_RIC_CASE(NN, MM)                                                      \
+    if (n == NN && m == MM) {                                                     \
+        launch_riccati_t<NN, MM>(A, B, C, Ci, T, gains, ctx->status, stream);     \
+        return cuda_failed(ctx, cudaGetLastError()) ? COV_ERR_CUDA : COV_OK;     \
     }
     COV_LQR_DISPATCH(COV_RIC_CASE)
 #undef COV_RIC_CASE

@@ -51,8 +51,8 @@ def _random_lqr(T, n, m, seed):
     return A, B, Q, R, abar
 
 
-@pytest.mark.parametrize("T,n,m", [(1, 2, 2), (2, 1, 1), (33, 4, 2), (100, 3, 2), (1000, 4, 3), (4096, 4, 2),
-                                   (65, 2, 1), (70, 3, 3)])
+@pytest.mark.parametrize("T,n,m", [(1, 2, 2), (2, 1, 1), (33, 4, 2), (63, 4, 2), (64, 4, 2), (100, 3, 2),
+                                   (1000, 4, 3), (4096, 4, 2), (65, 2, 1), (70, 3, 3), (20000, 4, 2), (65536, 3, 2)])
 def test_lqr_track_matches_oracle(cov, ctx, orc, T, n, m):
     A, B, Q, R, abar = _random_lqr(T, n, m, seed=T + 10 * n + m)
     v, z = cov.cov_lqr_track(ctx, dev64(A), dev64(B), Q, R, dev64(abar))
@@ -78,12 +78,33 @@ def test_lqr_double_integrator_long_horizon(cov, ctx, orc):
     assert ctx.device_status()[1] == 0
 
 
-def test_lqr_reports_non_spd_riccati(cov, ctx):
-    T, n, m = 8, 2, 2
+@pytest.mark.parametrize("T", [8, 200])
+def test_lqr_reports_non_spd_riccati(cov, ctx, T):
+    """Serial (T < 64) and parallel-in-time Riccati both report a control
+    weight that is not positive definite."""
+    n, m = 2, 2
     A, B, Q, R, abar = _random_lqr(T, n, m, seed=1)
     cov.cov_lqr_track(ctx, dev64(A), dev64(B), Q, -np.eye(2), dev64(abar))
     st, fl = ctx.device_status()
-    assert fl & cov.DEV_NOT_SPD and st == cov.COV_ERR_NONFINITE
+    assert fl & (cov.DEV_NOT_SPD | cov.DEV_NONFINITE) and st == cov.COV_ERR_NONFINITE
+
+
+def test_lqr_unicycle_long_horizon(cov, ctx, orc):
+    """T = 65536 time-varying unicycle linearisation (the large workload's
+    LQR), position-only weight, through the parallel-in-time Riccati."""
+    T, dt = 65536, 0.01
+    s0, u = wl.unicycle_init(T, dt)
+    u = u + np.stack([0.05 * np.sin(np.arange(T) / 500.0), 0.5 * np.cos(np.arange(T) / 800.0)], 1)
+    s = orc.rollout(wl.UNICYCLE, s0, u, dt)
+    A, B = orc.linearize(wl.UNICYCLE, s, u, dt)
+    abar = np.zeros((T, 3))
+    abar[:, :2] = wl.rng(7).standard_normal((T, 2)) * 0.05
+    Q, R = wl.coverage_Q(wl.UNICYCLE), 0.01 * np.eye(2)
+    v, z = cov.cov_lqr_track(ctx, dev64(A), dev64(B), Q, R, dev64(abar))
+    vo, zo, _ = orc.lqr_track(A, B, Q, R, abar)
+    np.testing.assert_allclose(host(v), vo, rtol=1e-8, atol=1e-10 * np.abs(vo).max())
+    np.testing.assert_allclose(host(z), zo, rtol=1e-8, atol=1e-10 * np.abs(zo).max())
+    assert ctx.device_status()[1] == 0
 
 
 @pytest.mark.parametrize("model", [wl.SINGLE_INT, wl.DOUBLE_INT, wl.UNICYCLE])
