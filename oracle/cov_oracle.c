@@ -230,6 +230,36 @@ void orc_sinkhorn(const double* x, int T, const double* y, int M,
     free(pn);
 }
 
+/* eps-scaling (annealing; not in the paper, a standard way to speed up
+ * Sinkhorn at small eps): iteration t (0-based) runs the same g, f, p
+ * updates at eps_t = max(eps, eps_start * eps_decay^t); the potentials are
+ * carried over in their natural (cost) units.  eps_start <= eps gives
+ * orc_sinkhorn exactly. */
+double orc_anneal_eps(double eps, double eps_start, double eps_decay, int t) {
+    double e = eps_start;
+    for (int k = 0; k < t; ++k) e *= eps_decay;
+    return e > eps ? e : eps;
+}
+
+void orc_sinkhorn_annealed(const double* x, int T, const double* y, int M,
+                           const double* b, int d, double eps, int n_iter,
+                           double eps_start, double eps_decay, int warm,
+                           double* f, double* g, double* p) {
+    if (!warm) {
+        for (int i = 0; i < T; ++i) f[i] = 0.0, p[i] = 0.0;
+        for (int j = 0; j < M; ++j) g[j] = 0.0;
+    }
+    double* pn = (double*)malloc(sizeof(double) * T);
+    for (int it = 0; it < n_iter; ++it) {
+        const double e = orc_anneal_eps(eps, eps_start, eps_decay, it);
+        orc_sinkhorn_g_update(x, T, y, M, d, e, f, NULL, 0, g);
+        orc_sinkhorn_f_update(x, T, y, M, b, d, e, g, NULL, 0, f);
+        orc_sinkhorn_p_update(x, T, d, e, p, NULL, 0, pn);
+        memcpy(p, pn, sizeof(double) * T);
+    }
+    free(pn);
+}
+
 /* ------------------------------------------------------------------------
  * Sinkhorn-divergence field, Eq. 7.  With the potentials held fixed
  * (envelope theorem), for c = |x - y|^2:
@@ -591,12 +621,32 @@ void orc_lqr_track(const double* A, const double* B, const double* Q,
  * z_0 = 0), the coverage coordinates are the first d state components, the
  * Sinkhorn potentials start cold in every field evaluation.
  * ---------------------------------------------------------------------- */
+int orc_solve_ex(int model, int T, double dt, const double* s0, int field,
+                 int d, const double* y, const double* b, int M, int K,
+                 const double* gw, const double* gmu, const double* gsigma,
+                 double eps, int n_iter, double h, const double* Q,
+                 const double* R, double eta, int n_outer, double* u,
+                 double* s, int warm, double eps_start, double eps_decay);
+
 int orc_solve(int model, int T, double dt, const double* s0, int field,
               int d, const double* y, const double* b, int M, int K,
               const double* gw, const double* gmu, const double* gsigma,
               double eps, int n_iter, double h, const double* Q,
               const double* R, double eta, int n_outer, double* u,
               double* s) {
+    return orc_solve_ex(model, T, dt, s0, field, d, y, b, M, K, gw, gmu, gsigma, eps, n_iter, h, Q, R, eta,
+                        n_outer, u, s, 0, 0.0, 1.0);
+}
+
+/* Variant: warm != 0 keeps the Sinkhorn potentials from one outer iteration
+ * to the next (the first starts cold); eps_start > eps anneals eps within
+ * each field evaluation (orc_sinkhorn_annealed). */
+int orc_solve_ex(int model, int T, double dt, const double* s0, int field,
+                 int d, const double* y, const double* b, int M, int K,
+                 const double* gw, const double* gmu, const double* gsigma,
+                 double eps, int n_iter, double h, const double* Q,
+                 const double* R, double eta, int n_outer, double* u,
+                 double* s, int warm, double eps_start, double eps_decay) {
     int n, m;
     if (orc_model_dims(model, &n, &m) != 0 || d > n) return -1;
     double* x = (double*)malloc(sizeof(double) * (size_t)T * d);
@@ -618,7 +668,7 @@ int orc_solve(int model, int T, double dt, const double* s0, int field,
             orc_gmm_score(x, T, d, K, gw, gmu, gsigma, sc);
             orc_svgd_field(x, T, d, sc, h, NULL, 0, a);
         } else {
-            orc_sinkhorn(x, T, y, M, b, d, eps, n_iter, 0, f, g, p);
+            orc_sinkhorn_annealed(x, T, y, M, b, d, eps, n_iter, eps_start, eps_decay, warm && it > 0, f, g, p);
             orc_sinkhorn_field(x, T, y, M, b, d, eps, g, p, NULL, 0, a);
         }
         for (int i = 0; i < T; ++i)

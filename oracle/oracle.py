@@ -80,6 +80,10 @@ def _declare(L):
         "orc_lqr_track": (None, [_D, _D, _D, _D, _D, _i, _i, _i, _D, _D, _D]),
         "orc_solve": (_i, [_i, _i, _d, _D, _i, _i, _D, _D, _i, _i, _D, _D, _D,
                            _d, _i, _d, _D, _D, _d, _i, _D, _D]),
+        "orc_anneal_eps": (_d, [_d, _d, _d, _i]),
+        "orc_sinkhorn_annealed": (None, [_D, _i, _D, _i, _D, _i, _d, _i, _d, _d, _i, _D, _D, _D]),
+        "orc_solve_ex": (_i, [_i, _i, _d, _D, _i, _i, _D, _D, _i, _i, _D, _D, _D,
+                              _d, _i, _d, _D, _D, _d, _i, _D, _D, _i, _d, _d]),
         "orc_sinkhorn_field_vjp": (None, [_D, _i, _D, _i, _D, _i, _d, _i, _D, _D, _D, _D]),
         "orc_lqr_vjp": (None, [_D, _D, _D, _D, _D, _i, _i, _i, _D]),
         "orc_rollout_vjp": (None, [_i, _D, _D, _i, _d, _D, _D, _D]),
@@ -187,6 +191,25 @@ def sinkhorn(x, y, b, eps, n_iter, f=None, g=None, p=None):
     return f, g, p
 
 
+def anneal_eps(eps, eps_start, eps_decay, t) -> float:
+    return float(lib().orc_anneal_eps(float(eps), float(eps_start), float(eps_decay), int(t)))
+
+
+def sinkhorn_annealed(x, y, b, eps, n_iter, eps_start, eps_decay, f=None, g=None, p=None):
+    """Fixed-iteration Sinkhorn with eps_t = max(eps, eps_start eps_decay^t)."""
+    x, y = _f64(x), _f64(y)
+    b = None if b is None else _f64(b)
+    T, d = x.shape
+    M = y.shape[0]
+    warm = f is not None
+    f = np.zeros(T) if f is None else _f64(f).copy()
+    g = np.zeros(M) if g is None else _f64(g).copy()
+    p = np.zeros(T) if p is None else _f64(p).copy()
+    lib().orc_sinkhorn_annealed(_p(x), T, _p(y), M, _p(b), d, float(eps), int(n_iter), float(eps_start),
+                                float(eps_decay), int(warm), _p(f), _p(g), _p(p))
+    return f, g, p
+
+
 def sinkhorn_field(x, y, b, eps, g, p, rows=None):
     x, y, g, p = _f64(x), _f64(y), _f64(g), _f64(p)
     b = None if b is None else _f64(b)
@@ -267,8 +290,10 @@ def lqr_track(A, B, Q, R, abar):
 
 # -- outer iteration -------------------------------------------------------
 def solve(model, dt, s0, u0, field, Q, R, eta, n_outer, *, d=2, y=None, b=None,
-          gmm=None, eps=0.0, n_iter=0, h=0.0):
-    """Returns (u, s) after n_outer iterations; u0 [T,m] is not modified."""
+          gmm=None, eps=0.0, n_iter=0, h=0.0, warm=False, eps_start=0.0, eps_decay=1.0):
+    """Returns (u, s) after n_outer iterations; u0 [T,m] is not modified.
+    warm: Sinkhorn potentials carried across outer iterations; eps_start >
+    eps: eps-scaling within each field evaluation."""
     n, m = MODEL_DIMS[model]
     u = _f64(u0).copy()
     T = u.shape[0]
@@ -284,9 +309,10 @@ def solve(model, dt, s0, u0, field, Q, R, eta, n_outer, *, d=2, y=None, b=None,
     else:
         gw = gmu = gs = None
         K = 0
-    rc = lib().orc_solve(int(model), T, float(dt), _p(s0), int(field), int(d), _p(yv), _p(bv), M, K,
-                         _p(gw), _p(gmu), _p(gs), float(eps), int(n_iter), float(h), _p(Q), _p(R),
-                         float(eta), int(n_outer), _p(u), _p(s))
+    rc = lib().orc_solve_ex(int(model), T, float(dt), _p(s0), int(field), int(d), _p(yv), _p(bv), M, K,
+                            _p(gw), _p(gmu), _p(gs), float(eps), int(n_iter), float(h), _p(Q), _p(R),
+                            float(eta), int(n_outer), _p(u), _p(s), int(warm), float(eps_start),
+                            float(eps_decay))
     if rc != 0:
         raise ValueError("orc_solve: bad arguments")
     return u, s

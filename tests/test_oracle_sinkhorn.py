@@ -176,3 +176,83 @@ def test_row_updates_match_full_updates(orc):
     np.testing.assert_array_equal(g_full, g4)
     np.testing.assert_array_equal(f_full, f4)
     np.testing.assert_array_equal(p_full, p4)
+
+
+# -- eps-scaling and warm starts (variants beyond the paper's cold fixed-eps loop) --
+def test_anneal_schedule_closed_form(orc):
+    for t in range(12):
+        assert orc.anneal_eps(0.002, 0.05, 0.6, t) == pytest.approx(max(0.002, 0.05 * 0.6 ** t), rel=1e-15)
+    assert orc.anneal_eps(0.01, 0.005, 0.5, 0) == 0.01          # start below target: no scaling
+
+
+def test_annealed_without_scaling_is_the_plain_iteration(orc):
+    x = wl.random_points(23, 2, seed=61)
+    y = wl.random_points(31, 2, seed=62)
+    b = wl.random_weights(31, seed=63)
+    for u, v in zip(orc.sinkhorn_annealed(x, y, b, 0.02, 7, 0.0, 0.5), orc.sinkhorn(x, y, b, 0.02, 7)):
+        np.testing.assert_array_equal(u, v)
+
+
+def test_annealed_iterations_use_the_scheduled_eps(orc):
+    """Iteration t runs the plain g, f, p updates at eps_t (checked for the
+    first three iterations by composing the single updates)."""
+    x = wl.random_points(17, 2, seed=64)
+    y = wl.random_points(19, 2, seed=65)
+    b = wl.random_weights(19, seed=66)
+    eps, e0, dec = 0.01, 0.08, 0.5
+    f, g, p = np.zeros(17), np.zeros(19), np.zeros(17)
+    for t in range(3):
+        e = max(eps, e0 * dec ** t)
+        g = orc.sinkhorn_g_update(x, y, e, f)
+        f = orc.sinkhorn_f_update(x, y, b, e, g)
+        p = orc.sinkhorn_p_update(x, e, p)
+    fa, ga, pa = orc.sinkhorn_annealed(x, y, b, eps, 3, e0, dec)
+    np.testing.assert_allclose(fa, f, atol=1e-13)
+    np.testing.assert_allclose(ga, g, atol=1e-13)
+    np.testing.assert_allclose(pa, p, atol=1e-13)
+
+
+def test_annealed_reaches_the_target_fixed_point_faster(orc):
+    """At small eps the annealed iteration ends at the target problem's fixed
+    point (same field as the converged potentials) and, for the same
+    iteration count, closer to it than the cold iteration."""
+    x = wl.random_points(60, 2, seed=67, lo=0.2, hi=0.8)
+    y = wl.random_points(90, 2, seed=68)
+    eps = 0.003
+    f_c, g_c, p_c, _ = orc.sinkhorn_converge(x, y, None, eps, tol=1e-13)
+    a_conv = orc.sinkhorn_field(x, y, None, eps, g_c, p_c)
+
+    def marg_err(f, g):
+        rs, cs = orc.sinkhorn_marginals(x, y, None, eps, f, g)
+        return np.abs(cs - 1.0 / 90).sum()
+
+    fa, ga, pa = orc.sinkhorn_annealed(x, y, None, eps, 1000, 0.1, 0.8)
+    np.testing.assert_allclose(orc.sinkhorn_field(x, y, None, eps, ga, pa), a_conv, atol=1e-7)
+    n = 40
+    f1, g1, _ = orc.sinkhorn(x, y, None, eps, n)
+    f2, g2, _ = orc.sinkhorn_annealed(x, y, None, eps, n, 0.1, 0.8)
+    assert marg_err(f2, g2) < 0.5 * marg_err(f1, g1)
+
+
+def test_warm_solve_carries_the_potentials(orc):
+    """Two outer iterations with warm potentials = the second field evaluated
+    from the first one's potentials (manual composition)."""
+    inst = wl.make_instance(wl.SINKHORN_DOUBLE_T4096, T=48, M=64)
+    w = inst.wl
+    eps, n_iter = 0.02, 5
+    u2, s2 = orc.solve(w.model, w.dt, inst.s0, inst.u0, wl.FIELD_SINKHORN, inst.Q, inst.R, w.eta, 2, y=inst.y,
+                       eps=eps, n_iter=n_iter, warm=True)
+    u1c, s1c = orc.solve(w.model, w.dt, inst.s0, inst.u0, wl.FIELD_SINKHORN, inst.Q, inst.R, w.eta, 1, y=inst.y,
+                         eps=eps, n_iter=n_iter)
+    u1w, s1w = orc.solve(w.model, w.dt, inst.s0, inst.u0, wl.FIELD_SINKHORN, inst.Q, inst.R, w.eta, 1, y=inst.y,
+                         eps=eps, n_iter=n_iter, warm=True)
+    np.testing.assert_array_equal(s1w, s1c)                   # the first outer iteration starts cold
+    s0tr = orc.rollout(w.model, inst.s0, inst.u0, w.dt)
+    f, g, p = orc.sinkhorn(s0tr[1:, :2], inst.y, None, eps, n_iter)
+    f, g, p = orc.sinkhorn(s1c[1:, :2], inst.y, None, eps, n_iter, f=f, g=g, p=p)
+    a = orc.sinkhorn_field(s1c[1:, :2], inst.y, None, eps, g, p)
+    A, B = orc.linearize(w.model, s1c, u1c, w.dt)
+    abar = np.zeros((48, 4))
+    abar[:, :2] = a
+    v, _, _ = orc.lqr_track(A, B, inst.Q, inst.R, abar)
+    np.testing.assert_allclose(u2, u1c + w.eta * v, atol=1e-12)
