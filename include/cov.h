@@ -176,6 +176,21 @@ COV_API cov_status cov_field_sinkhorn(cov_ctx* ctx, const float* x, int T,
                               float* g, float* p, float* a_out,
                               cov_stream_t stream);
 
+/* The same field with eps-scaling (annealing, a standard acceleration of
+ * Sinkhorn at small eps; not in the paper): iteration t = 0..n_iter-1 runs
+ * the three updates at eps_t = max(eps, eps_start eps_decay^t), carrying
+ * the potentials over in cost units; the field and the returned potentials
+ * are at eps.  eps_start <= eps is cov_field_sinkhorn.  Errors as
+ * cov_field_sinkhorn, plus COV_ERR_INVALID_ARG for eps_decay outside (0, 1)
+ * when eps_start > eps. */
+COV_API cov_status cov_field_sinkhorn_annealed(cov_ctx* ctx, const float* x, int T,
+                                               const float* y, const float* b, int M,
+                                               int d, float eps, int n_iter,
+                                               float eps_start, float eps_decay,
+                                               int flags, float* f, float* g,
+                                               float* p, float* a_out,
+                                               cov_stream_t stream);
+
 /* The same field for callers that must not allocate device memory.  The
  * paper has no counterpart: this is a library convenience.  Programs that
  * cannot call cudaMalloc -- code running while a CUDA graph is captured,
@@ -253,6 +268,15 @@ typedef struct {
     double Q[COV_MAX_N * COV_MAX_N]; /* [n][n] tracking weight, row-major */
     double R[COV_MAX_M * COV_MAX_M]; /* [m][m] control weight, row-major */
     double eta;           /* control step size (u <- u + eta v*) */
+    /* Sinkhorn variants (not in the paper; zero-initialise for the paper's
+     * cold fixed-eps iterations): */
+    float eps_start;      /* eps-scaling: iteration t runs at
+                           * max(eps, eps_start eps_decay^t); <= eps: none */
+    float eps_decay;      /* in (0, 1) when eps_start > eps */
+    int warm;             /* 1: each field evaluation starts from the
+                           * potentials of the previous outer iteration
+                           * (cov_solve starts cold; cov_solve_continue keeps
+                           * them while nothing else ran on the context) */
 } cov_problem;
 
 /* Run n_outer outer iterations: x = first d components of s_1..s_T;
@@ -363,6 +387,8 @@ COV_API cov_status cov_solve_checkpointed(cov_ctx* ctx, const cov_problem* prob,
  * on a time-invariant model (COV_SINGLE_INT, COV_DOUBLE_INT; d <= 3;
  * COV_ERR_UNSUPPORTED otherwise: the unicycle's A_t, B_t depend on the
  * trajectory and would need second derivatives of the dynamics).  Reverse
+ * (cold fixed-eps iterations only: warm or eps_start > eps is
+ * COV_ERR_UNSUPPORTED).  Reverse
  * sweep over k = K..1: rollout adjoint, LQR adjoint (cov_lqr_vjp), field
  * adjoint (cov_field_sinkhorn_vjp, recomputing the inner Sinkhorn
  * iterations from the checkpoint s^{k-1}).

@@ -36,7 +36,7 @@ EXPORTS = (
     "cov_lqr_track", "cov_solve", "cov_solve_continue", "cov_solve_batched", "cov_workspace_size_batched",
     "cov_probe_peaks", "cov_workspace_size_vjp", "cov_field_sinkhorn_vjp", "cov_workspace_size_lqr_vjp",
     "cov_lqr_vjp", "cov_rollout_vjp", "cov_solve_checkpointed", "cov_workspace_size_backward",
-    "cov_solve_backward",
+    "cov_solve_backward", "cov_field_sinkhorn_annealed",
 )
 
 
@@ -57,7 +57,8 @@ class cov_gmm(ctypes.Structure):
 class cov_problem(ctypes.Structure):
     _fields_ = [("model", _i), ("T", _i), ("dt", _d), ("s0", _d * MAX_N), ("field", _i), ("d", _i),
                 ("y", _P), ("b", _P), ("M", _i), ("eps", _f), ("n_iter", _i), ("gmm", cov_gmm), ("h", _f),
-                ("Q", _d * (MAX_N * MAX_N)), ("R", _d * (MAX_M * MAX_M)), ("eta", _d)]
+                ("Q", _d * (MAX_N * MAX_N)), ("R", _d * (MAX_M * MAX_M)), ("eta", _d),
+                ("eps_start", _f), ("eps_decay", _f), ("warm", _i)]
 
 
 _lib = None
@@ -94,6 +95,7 @@ def load(path: str = LIB_PATH):
                                    ctypes.POINTER(_P), _P]),
         "cov_workspace_size_batched": (_sz, [ctypes.POINTER(cov_problem), _i]),
         "cov_probe_peaks": (_i, [_P, _i, ctypes.POINTER(_d), _P]),
+        "cov_field_sinkhorn_annealed": (_i, [_P, _P, _i, _P, _P, _i, _i, _f, _i, _f, _f, _i, _P, _P, _P, _P, _P]),
         "cov_workspace_size_vjp": (_sz, [_i, _i, _i, _i]),
         "cov_field_sinkhorn_vjp": (_i, [_P, _P, _i, _P, _P, _i, _i, _f, _i, _P, _P, _P, _P, _P]),
         "cov_workspace_size_lqr_vjp": (_sz, [_i, _i, _i]),
@@ -256,6 +258,28 @@ def cov_field_sinkhorn(ctx: Context, x, y, eps, n_iter, b=None, f=None, g=None, 
     return (out if field else None), f, g, p
 
 
+def cov_field_sinkhorn_annealed(ctx: Context, x, y, eps, n_iter, eps_start, eps_decay, b=None, f=None, g=None,
+                                p=None, warm=False, field=True, out=None, stream=None):
+    """cov_field_sinkhorn with eps-scaling: iteration t at max(eps, eps_start eps_decay^t)."""
+    T, d = x.shape
+    M = y.shape[0]
+    ctx.reserve_for(T, M, d)
+    dev = x.device
+    f = torch.empty(T, device=dev, dtype=torch.float32) if f is None else f
+    g = torch.empty(M, device=dev, dtype=torch.float32) if g is None else g
+    p = torch.empty(T, device=dev, dtype=torch.float32) if p is None else p
+    if field and out is None:
+        out = torch.empty_like(x)
+    st = load().cov_field_sinkhorn_annealed(
+        ctx.h, _ptr(x, torch.float32, name="x"), T, _ptr(y, torch.float32, (M, d), "y"),
+        _ptr(b, torch.float32, (M,), "b"), M, d, float(eps), int(n_iter), float(eps_start), float(eps_decay),
+        WARM_START if warm else 0, _ptr(f, torch.float32, (T,), "f"), _ptr(g, torch.float32, (M,), "g"),
+        _ptr(p, torch.float32, (T,), "p"), _ptr(out, torch.float32, (T, d), "out") if field else None,
+        _stream(stream))
+    ctx._check(st, "cov_field_sinkhorn_annealed")
+    return (out if field else None), f, g, p
+
+
 def cov_linearize(ctx: Context, model, s, u, dt, A=None, B=None, stream=None):
     n, m = MODEL_DIMS[model]
     T = u.shape[0]
@@ -298,8 +322,11 @@ def cov_lqr_track(ctx: Context, A, B, Q, R, abar, want_z=True, stream=None):
     return v, z
 
 
-def make_problem(model, T, dt, s0, field, Q, R, eta, *, d=2, y=None, b=None, eps=0.0, n_iter=0, gmm=None, h=0.0):
-    """Build a cov_problem; returns (struct, keep-alive list)."""
+def make_problem(model, T, dt, s0, field, Q, R, eta, *, d=2, y=None, b=None, eps=0.0, n_iter=0, gmm=None, h=0.0,
+                 eps_start=0.0, eps_decay=1.0, warm=False):
+    """Build a cov_problem; returns (struct, keep-alive list).  eps_start >
+    eps turns on eps-scaling; warm carries the Sinkhorn potentials between
+    outer iterations."""
     n, m = MODEL_DIMS[model]
     P = cov_problem()
     P.model, P.T, P.dt, P.field, P.d = int(model), int(T), float(dt), int(field), int(d)
@@ -312,6 +339,7 @@ def make_problem(model, T, dt, s0, field, Q, R, eta, *, d=2, y=None, b=None, eps
     for e in range(m * m):
         P.R[e] = float(R.flat[e])
     P.eta = float(eta)
+    P.eps_start, P.eps_decay, P.warm = float(eps_start), float(eps_decay), int(bool(warm))
     keep = []
     if y is not None:
         P.y = _ptr(y, torch.float32, name="y").value

@@ -47,6 +47,8 @@ struct cov_ctx {
     // forward records of a taped cov_solve_checkpointed, one per outer
     // iteration, valid for cov_solve_backward while tape_key matches
     uint64_t tape_key = 0;
+    // warm-started Sinkhorn potentials of cov_solve (valid while key matches)
+    uint64_t pot_key = 0;
     std::vector<cov::SkTape> tapes;
 };
 
@@ -77,6 +79,7 @@ bool cuda_failed(cov_ctx* ctx, cudaError_t e);
 inline void clobber_ws_caches(cov_ctx* ctx) {
     ctx->gains_key = 0;
     ctx->tape_key = 0;
+    ctx->pot_key = 0;
 }
 
 // ---- per-component entry points used by cov_solve ---------------------------
@@ -92,7 +95,7 @@ size_t lqr_ws_bytes(int T, int n, int m);
 cov_status sinkhorn_field_ws(cov_ctx* ctx, void* ws, size_t ws_bytes, const float* x, int x_ld, int T,
                              const float* y, const float* b, int M, int d, float eps, int n_iter, int flags,
                              float* f, float* g, float* p, float* a_out, cudaStream_t stream,
-                             const float* scal_given = nullptr);
+                             const float* scal_given = nullptr, float eps_start = 0.f, float eps_decay = 1.f);
 // Forward record of a fixed-iteration, cold-start Sinkhorn run (device
 // arrays inside the workspace), everything the adjoint needs.  Column terms
 // are in the base-2 prescaled form of the forward kernels:

@@ -15,7 +15,7 @@ bool cov::cuda_failed(cov_ctx* ctx, cudaError_t e) {
 }
 
 namespace cov {
-size_t solve_buffers_bytes(int T, int d, int n, int m);
+size_t solve_buffers_bytes(int T, int d, int n, int m, int M);
 void drop_solve_graph(cov_ctx* ctx);
 void destroy_stream_pool(cov_ctx* ctx);
 void lqr_set_attributes();
@@ -104,7 +104,7 @@ extern "C" size_t cov_workspace_size(int T, int M, int d, int n, int m) {
     size_t lqr = 0, solve = 0;
     if (n > 0 && m > 0) {
         lqr = cov::lqr_ws_bytes(T, n, m);
-        solve = cov::solve_buffers_bytes(T, d, n, m);
+        solve = cov::solve_buffers_bytes(T, d, n, m, M);
     }
     return solve + std::max(field, lqr) + 4096;
 }

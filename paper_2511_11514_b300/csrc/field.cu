@@ -635,6 +635,56 @@ __global__ void sk_finish_kernel(int T, int M, float epsln2, float log2a, SkBufs
     if (!ok) raise_status(status, kDevNonfinite);
 }
 
+// eps-scaling stage change: every base-2 quantity depends on eps through the
+// prescale xhat = (x - c)/sqrt(eps ln 2) and the potential units eps ln 2.
+// Moving from eps_old to eps_new multiplies the coordinates by
+// ratio = sqrt(eps_old/eps_new) and converts each potential term, e.g.
+//   f/(eps_new ln2) = (hx - log2 a + |xhat_old|^2) eps_old/eps_new,
+//   hx_new = log2 a + f/(eps_new ln2) - |xhat_new|^2  (likewise hy with log2 b, hp).
+__global__ void sk_rescale_kernel(SkBufs B, int T, int M, int d, float ratio, float erat, float log2a,
+                                  float* __restrict__ hp, unsigned* status) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    bool ok = true;
+    if (i < B.Tp) {
+        float n2 = 0.f;
+        for (int k = 0; k < d; ++k) {
+            const float v = B.xs[(size_t)k * B.Tp + i] * ratio;
+            B.xs[(size_t)k * B.Tp + i] = v;
+            n2 = fmaf(v, v, n2);
+        }
+        const float n_old = B.nx[i];
+        B.nx[i] = n2;
+        if (i < T) {
+            B.hx[i] = log2a + (B.hx[i] - log2a + n_old) * erat - n2;
+            hp[i] = log2a + (hp[i] - log2a + n_old) * erat - n2;
+            ok &= finitef(B.hx[i]) && finitef(hp[i]);
+        }
+    }
+    if (i < B.Mp) {
+        float n2 = 0.f;
+        for (int k = 0; k < d; ++k) {
+            const float v = B.ys[(size_t)k * B.Mp + i] * ratio;
+            B.ys[(size_t)k * B.Mp + i] = v;
+            n2 = fmaf(v, v, n2);
+        }
+        const float n_old = B.ny[i];
+        B.ny[i] = n2;
+        if (i < M) {
+            B.hy[i] = B.lb[i] + (B.hy[i] - B.lb[i] + n_old) * erat - n2;
+            ok &= finitef(B.hy[i]);
+        }
+    }
+    if (!ok) raise_status(status, kDevNonfinite);
+}
+
+// eps of iteration t under the scaling schedule (the same product as the
+// oracle's): max(eps, eps_start eps_decay^t); eps_start <= eps: no scaling.
+static double anneal_eps(double eps, double eps_start, double eps_decay, int t) {
+    double e = eps_start;
+    for (int k = 0; k < t; ++k) e *= eps_decay;
+    return e > eps ? e : eps;
+}
+
 // ---------------------------------------------------------------------------
 // Launch dispatch.  Kernel families: M_G (log-sum-exp updates; the epilogue
 // g/f/p is chosen per segment at run time), M_WY, M_WX, M_SVGD.  Launches use
@@ -812,10 +862,12 @@ size_t sinkhorn_ws_bytes(int T, int M, int d) {
 cov_status sinkhorn_field_ws(cov_ctx* ctx, void* ws, size_t ws_bytes, const float* x, int x_ld, int T,
                              const float* y, const float* b, int M, int d, float eps, int n_iter, int flags,
                              float* f, float* g, float* p, float* a_out, cudaStream_t stream,
-                             const float* scal_given) {
+                             const float* scal_given, float eps_start, float eps_decay) {
     if (!ctx || !x || !y || T < 1 || M < 1 || d < 1 || d > COV_MAX_D || x_ld < d || n_iter < 0 ||
         !(eps > 0.f) || !isfinite(eps))
         return COV_ERR_INVALID_ARG;
+    const bool scaled = eps_start > eps;
+    if (scaled && (!isfinite(eps_start) || !(eps_decay > 0.f) || !(eps_decay < 1.f))) return COV_ERR_INVALID_ARG;
     const int warm = (flags & COV_WARM_START) ? 1 : 0;
     if (warm && (!f || !g || !p)) return COV_ERR_INVALID_ARG;
     Carver cv(ws);
@@ -824,8 +876,10 @@ cov_status sinkhorn_field_ws(cov_ctx* ctx, void* ws, size_t ws_bytes, const floa
     if (cuda_failed(ctx, cudaMemsetAsync(B.counters, 0, sizeof(unsigned) * M_COUNT * B.cnt_ld, stream)))
         return COV_ERR_CUDA;
 
+    // stage eps: the first iteration's (eps-scaling), else eps throughout
+    double eps_cur = scaled ? anneal_eps(eps, eps_start, eps_decay, 0) : (double)eps;
+    const double epsln2_0 = eps_cur * 0.69314718055994531;
     const double epsln2 = (double)eps * 0.69314718055994531;
-    const float inv_sigma = (float)(1.0 / sqrt(epsln2));
     const float sigma = (float)sqrt(epsln2);
     const float log2a = (float)(-log2((double)T));
     if (scal_given)
@@ -833,8 +887,9 @@ cov_status sinkhorn_field_ws(cov_ctx* ctx, void* ws, size_t ws_bytes, const floa
     else
         sk_centre_kernel<<<1, 1024, 0, stream>>>(y, M, d, b, B.scal);
     const int np = std::max(B.Tp, B.Mp);
-    sk_prep_kernel<<<(np + 255) / 256, 256, 0, stream>>>(x, x_ld, T, y, M, b, d, inv_sigma, (float)(1.0 / epsln2),
-                                                         log2a, warm, f, g, p, B, ctx->status);
+    sk_prep_kernel<<<(np + 255) / 256, 256, 0, stream>>>(x, x_ld, T, y, M, b, d, (float)(1.0 / sqrt(epsln2_0)),
+                                                         (float)(1.0 / epsln2_0), log2a, warm, f, g, p, B,
+                                                         ctx->status);
     PairArgs base{};
     base.status = ctx->status;
     base.spin_limit = ctx->spin_limit;
@@ -845,7 +900,18 @@ cov_status sinkhorn_field_ws(cov_ctx* ctx, void* ws, size_t ws_bytes, const floa
     float* hp_nxt = B.hp1;
     bool first = true;  // the first pass reads what the prep kernel just wrote
     cov_status r = COV_OK;
+    // move the state to another eps (coordinates and potential terms), on
+    // the stream before the next pass; that pass then waits for it
+    auto to_eps = [&](double e_new) {
+        if (e_new == eps_cur) return;
+        const int nb = (np + 255) / 256;
+        sk_rescale_kernel<<<nb, 256, 0, stream>>>(B, T, M, d, (float)sqrt(eps_cur / e_new), (float)(eps_cur / e_new),
+                                                  log2a, hp_cur, ctx->status);
+        eps_cur = e_new;
+        first = true;
+    };
     for (int it = 0; it < n_iter && r == COV_OK; ++it) {
+        if (scaled) to_eps(anneal_eps(eps, eps_start, eps_decay, it));
         // launch A: g-update (rows y, columns x) and self p-update (rows x,
         // columns x) -- independent, same column set
         PairArgs sg[2] = {base, base};
@@ -870,6 +936,7 @@ cov_status sinkhorn_field_ws(cov_ctx* ctx, void* ws, size_t ws_bytes, const floa
         std::swap(hp_cur, hp_nxt);
     }
     if (r != COV_OK) return r;
+    to_eps((double)eps);  // the field and the returned potentials are at the target eps
     if (a_out) {
         PairArgs a = base;  // cross barycentre: (sum_j pi_ij yhat_j) - xhat_i
         a.rows = B.xs; a.row_ld = B.Tp; a.n_rows = T;
@@ -1228,6 +1295,17 @@ cov_status svgd_field_ws(cov_ctx* ctx, void* ws, size_t ws_bytes, const float* x
 // ---------------------------------------------------------------------------
 // C-ABI entry points
 // ---------------------------------------------------------------------------
+extern "C" cov_status cov_field_sinkhorn_annealed(cov_ctx* ctx, const float* x, int T, const float* y,
+                                                  const float* b, int M, int d, float eps, int n_iter,
+                                                  float eps_start, float eps_decay, int flags, float* f, float* g,
+                                                  float* p, float* a_out, cov_stream_t stream) {
+    if (!ctx) return COV_ERR_INVALID_ARG;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return COV_ERR_CUDA;
+    cov::clobber_ws_caches(ctx);  // the workspace scratch overwrites cov_solve's caches
+    return cov::sinkhorn_field_ws(ctx, ctx->ws, ctx->ws_bytes, x, d, T, y, b, M, d, eps, n_iter, flags, f, g, p,
+                                  a_out, (cudaStream_t)stream, nullptr, eps_start, eps_decay);
+}
+
 extern "C" cov_status cov_field_sinkhorn(cov_ctx* ctx, const float* x, int T, const float* y, const float* b, int M,
                                          int d, float eps, int n_iter, int flags, float* f, float* g, float* p,
                                          float* a_out, cov_stream_t stream) {

@@ -23,16 +23,22 @@ cov_status update_rollout(cov_ctx* ctx, int model, const double* s0, double* u, 
 cov_status linearize_launch(cov_ctx* ctx, int model, const double* s, const double* u, int T, double dt, double* A,
                             double* B, cudaStream_t stream);
 
+// Reference samples of a Sinkhorn problem (0 for the Stein field).
+static int prob_M(const cov_problem* P) { return P->field == COV_FIELD_SINKHORN ? P->M : 0; }
+
 // Time-invariant models: A_t, B_t do not depend on the trajectory, so the
 // Riccati gains are the same in every outer iteration.
 static bool model_is_lti(int model) { return model == COV_SINGLE_INT || model == COV_DOUBLE_INT; }
 
 struct SolveBufs {
     float *x, *a, *scal;
+    float *f, *g, *p;  // Sinkhorn potentials carried between outer iterations (warm)
     double *abar, *A, *B, *v, *gains;
 };
 
-static SolveBufs carve_solve(Carver& cv, int T, int d, int n, int m) {
+// The potentials come last, so that the cached gains sit at an offset that
+// does not depend on M.
+static SolveBufs carve_solve(Carver& cv, int T, int d, int n, int m, int M) {
     SolveBufs b{};
     b.x = cv.take<float>((size_t)T * d);
     b.a = cv.take<float>((size_t)T * d);
@@ -42,12 +48,15 @@ static SolveBufs carve_solve(Carver& cv, int T, int d, int n, int m) {
     b.v = cv.take<double>((size_t)T * m);
     b.gains = cv.take<double>(lqr_gain_doubles(T, n, m));
     b.scal = cv.take<float>(16);
+    b.f = cv.take<float>((size_t)T);
+    b.p = cv.take<float>((size_t)T);
+    b.g = cv.take<float>((size_t)(M > 0 ? M : 1));
     return b;
 }
 
-size_t solve_buffers_bytes(int T, int d, int n, int m) {
+size_t solve_buffers_bytes(int T, int d, int n, int m, int M) {
     Carver cv(nullptr);
-    carve_solve(cv, T, d, n, m);
+    carve_solve(cv, T, d, n, m, M);
     return round_up(cv.off, 256);
 }
 
@@ -159,8 +168,12 @@ static cov_status validate(const cov_problem* P, int* n, int* m) {
         return COV_ERR_INVALID_ARG;
     for (int r = 0; r < *n; ++r)
         if (!isfinite(P->s0[r])) return COV_ERR_INVALID_ARG;
+    if (P->warm != 0 && P->warm != 1) return COV_ERR_INVALID_ARG;
     if (P->field == COV_FIELD_SINKHORN) {
         if (!P->y || P->M < 1 || !(P->eps > 0.f) || P->n_iter < 0) return COV_ERR_INVALID_ARG;
+        if (P->eps_start > P->eps &&
+            (!isfinite(P->eps_start) || !(P->eps_decay > 0.f) || !(P->eps_decay < 1.f)))
+            return COV_ERR_INVALID_ARG;
     } else if (P->field == COV_FIELD_SVGD) {
         GmmParams G;
         if (!(P->h > 0.f) || make_gmm_params(&P->gmm, P->d, &G) != COV_OK) return COV_ERR_INVALID_ARG;
@@ -177,9 +190,12 @@ static cov_status enqueue_iteration(cov_ctx* ctx, const cov_problem* P, int n, i
     const int nb = (T + 255) / 256;
     extract_kernel<<<nb, 256, 0, st>>>(s, T, n, d, b.x);
     cov_status r;
-    if (P->field == COV_FIELD_SINKHORN)
-        r = sinkhorn_field_ws(ctx, rest, rest_bytes, b.x, d, T, P->y, P->b, P->M, d, P->eps, P->n_iter, 0, nullptr,
-                              nullptr, nullptr, b.a, st, b.scal);
+    if (P->field == COV_FIELD_SINKHORN) {
+        const bool warm = P->warm == 1;
+        r = sinkhorn_field_ws(ctx, rest, rest_bytes, b.x, d, T, P->y, P->b, P->M, d, P->eps, P->n_iter,
+                              warm ? COV_WARM_START : 0, warm ? b.f : nullptr, warm ? b.g : nullptr,
+                              warm ? b.p : nullptr, b.a, st, b.scal, P->eps_start, P->eps_decay);
+    }
     else
         r = svgd_field_ws(ctx, rest, rest_bytes, b.x, d, T, d, nullptr, &P->gmm, P->h, b.a, st);
     if (r != COV_OK) return r;
@@ -225,12 +241,31 @@ static cov_status cov::solve_impl(cov_ctx* ctx, const cov_problem* prob, int n_o
     if (cudaSetDevice(ctx->device) != cudaSuccess) return COV_ERR_CUDA;
     cudaStream_t st = stream;
     Carver cv(ctx->ws);
-    SolveBufs b = carve_solve(cv, prob->T, prob->d, n, m);
+    SolveBufs b = carve_solve(cv, prob->T, prob->d, n, m, prob_M(prob));
     const size_t used = round_up(cv.off, 256);
     if (!ctx->ws || used > ctx->ws_bytes) return COV_ERR_WORKSPACE;
     void* rest = static_cast<char*>(ctx->ws) + used;
     const size_t rest_bytes = ctx->ws_bytes - used;
     ctx->tape_key = 0;  // the scratch below overwrites forward records
+
+    // warm-started potentials: a fresh solve starts cold (zero potentials
+    // with the warm flag are exactly the cold start); a continuation keeps
+    // them while nothing else has run on the context
+    const bool warm = prob->field == COV_FIELD_SINKHORN && prob->warm == 1;
+    uint64_t pk = 0;
+    if (warm) {
+        pk = 9650029242287828579ull;
+        pk = fnv(prob, sizeof(cov_problem), pk);
+        const void* ptrs[3] = {u, s_out, ctx->ws};
+        pk = fnv(ptrs, sizeof(ptrs), pk);
+        if (initial_rollout || ctx->pot_key != pk) {
+            ctx->pot_key = 0;
+            if (cuda_failed(ctx, cudaMemsetAsync(b.f, 0, sizeof(float) * prob->T, st)) ||
+                cuda_failed(ctx, cudaMemsetAsync(b.p, 0, sizeof(float) * prob->T, st)) ||
+                cuda_failed(ctx, cudaMemsetAsync(b.g, 0, sizeof(float) * prob->M, st)))
+                return COV_ERR_CUDA;
+        }
+    }
 
     // initial trajectory from s0 and the given controls
     if (initial_rollout) {
@@ -260,6 +295,7 @@ static cov_status cov::solve_impl(cov_ctx* ctx, const cov_problem* prob, int n_o
             r = enqueue_iteration(ctx, prob, n, m, b, rest, rest_bytes, u, s_out, st);
             if (r != COV_OK) return r;
         }
+        if (warm) ctx->pot_key = pk;
         return COV_OK;
     }
     uint64_t key = 1469598103934665603ull;
@@ -301,6 +337,7 @@ static cov_status cov::solve_impl(cov_ctx* ctx, const cov_problem* prob, int n_o
         if (checkpoint(k)) return COV_ERR_CUDA;
         if (cuda_failed(ctx, cudaGraphLaunch(ctx->solve_graph.exec, st))) return COV_ERR_CUDA;
     }
+    if (warm) ctx->pot_key = pk;
     return COV_OK;
 }
 
@@ -317,7 +354,7 @@ namespace cov {
 static constexpr int kPoolStreams = 32;
 
 static size_t problem_ws_bytes(const cov_problem* P, int n, int m) {
-    const size_t solve = solve_buffers_bytes(P->T, P->d, n, m);
+    const size_t solve = solve_buffers_bytes(P->T, P->d, n, m, prob_M(P));
     const size_t field =
         P->field == COV_FIELD_SINKHORN ? sinkhorn_ws_bytes(P->T, P->M, P->d) : svgd_ws_bytes(P->T, P->d);
     const size_t lqr = lqr_ws_bytes(P->T, n, m);
@@ -397,7 +434,7 @@ extern "C" cov_status cov_solve_batched(cov_ctx* ctx, const cov_problem* probs, 
     for (int p = 0; p < n_probs; ++p) {
         char* base = static_cast<char*>(ctx->ws) + off[p];
         Carver cv(base);
-        bufs[p] = carve_solve(cv, probs[p].T, probs[p].d, nn[p], mm[p]);
+        bufs[p] = carve_solve(cv, probs[p].T, probs[p].d, nn[p], mm[p], prob_M(&probs[p]));
         const size_t used = round_up(cv.off, 256);
         rest[p] = base + used;
         rest_bytes[p] = problem_ws_bytes(&probs[p], nn[p], mm[p]) - used;
@@ -412,7 +449,14 @@ extern "C" cov_status cov_solve_batched(cov_ctx* ctx, const cov_problem* probs, 
         cudaStream_t sp = ctx->pool[p % K];
         r = cov_rollout(ctx, P->model, P->s0, u[p], P->T, P->dt, s_out[p], (cov_stream_t)sp);
         if (r != COV_OK || n_outer == 0) continue;
-        if (P->field == COV_FIELD_SINKHORN) sinkhorn_reference_stats(P->y, P->M, P->d, P->b, bufs[p].scal, sp);
+        if (P->field == COV_FIELD_SINKHORN) {
+            sinkhorn_reference_stats(P->y, P->M, P->d, P->b, bufs[p].scal, sp);
+            if (P->warm == 1 &&
+                (cuda_failed(ctx, cudaMemsetAsync(bufs[p].f, 0, sizeof(float) * P->T, sp)) ||
+                 cuda_failed(ctx, cudaMemsetAsync(bufs[p].p, 0, sizeof(float) * P->T, sp)) ||
+                 cuda_failed(ctx, cudaMemsetAsync(bufs[p].g, 0, sizeof(float) * P->M, sp))))
+                r = COV_ERR_CUDA;
+        }
         if (model_is_lti(P->model)) {
             r = linearize_launch(ctx, P->model, s_out[p], u[p], P->T, P->dt, bufs[p].A, bufs[p].B, sp);
             if (r == COV_OK) r = lqr_riccati(ctx, nn[p], mm[p], bufs[p].A, bufs[p].B, P->Q, P->R, P->T,
@@ -544,7 +588,8 @@ static BackBufs carve_back(Carver& cv, int T, int d, int n, int m, int n_hist) {
 }
 
 static bool backward_supported(const cov_problem* P) {
-    return P->field == COV_FIELD_SINKHORN && model_is_lti(P->model) && P->d <= 3;
+    return P->field == COV_FIELD_SINKHORN && model_is_lti(P->model) && P->d <= 3 && P->warm == 0 &&
+           !(P->eps_start > P->eps);
 }
 
 // ws == nullptr only measures (L->needed).
@@ -553,7 +598,7 @@ static void carve_layout(void* ws, size_t ws_bytes, const cov_problem* P, int n,
     const int T = P->T, d = P->d;
     Carver cv(ws);
     *L = BackLayout{};
-    L->sb = carve_solve(cv, T, d, n, m);
+    L->sb = carve_solve(cv, T, d, n, m, prob_M(P));
     if (mode == BM_TAPED) {
         L->tape_stride = round_up(sinkhorn_tape_bytes(T, P->M, d, P->n_iter, false), 256);
         L->tape0 = cv.take<char>(L->tape_stride * (size_t)K);
