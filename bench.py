@@ -66,6 +66,9 @@ def parse_args():
                     help="skip the all-pairs roofline at T = 65536, M = 262144")
     ap.add_argument("--adjoint", action="store_true",
                     help="time the differentiation workload: forward and backward through 20 outer iterations")
+    ap.add_argument("--variants", action="store_true",
+                    help="measure the Sinkhorn variants at eps = 0.002: iterations to a field accuracy, "
+                         "cold vs eps-scaled vs warm-started")
     ap.add_argument("--adjoint-outer", type=int, default=0,
                     help="outer iterations of --adjoint (default: the workload's 20; fewer only to keep a "
                          "profiler's launch list short)")
@@ -339,8 +342,23 @@ def run_ours(args):
 
         tb = (big_ms(3) - big_ms(1)) / 2
         ach_b = (2 * wb.T * wb.M + wb.T * wb.T) / (tb * 1e-3)
+        # the LQR step of that workload (time-varying unicycle linearisation:
+        # parallel-in-time Riccati + the two affine scans), CUDA events
+        sbig = cov.cov_rollout(ctx, wb.model, ib.s0, ub, wb.dt)
+        Ab, Bb = cov.cov_linearize(ctx, wb.model, sbig, ub, wb.dt)
+        abar_b = torch.zeros((wb.T, Ab.shape[1]), dtype=torch.float64, device=dev)
+        abar_b[:, :2] = 0.05
+        cov.cov_lqr_track(ctx, Ab, Bb, ib.Q, ib.R, abar_b)
+        la = torch.cuda.Event(enable_timing=True)
+        lb = torch.cuda.Event(enable_timing=True)
+        la.record(stream)
+        for _ in range(3):
+            cov.cov_lqr_track(ctx, Ab, Bb, ib.Q, ib.R, abar_b)
+        lb.record(stream)
+        torch.cuda.synchronize()
         big = {"bound": "alu", "achieved": ach_b / 1e9, "peak": peak / 1e9, "unit": "Gpair/s", "frac": ach_b / peak,
-               "traffic": None, "workload": wb.name, "ms_per_sinkhorn_iteration": tb}
+               "traffic": None, "workload": wb.name, "ms_per_sinkhorn_iteration": tb,
+               "lqr_track_ms": la.elapsed_time(lb) / 3}
         if not args.no_tune:
             apply_choice = {"R": tiling["R"], "ctas_per_sm": tiling["ctas_per_sm"]}
             autotune.apply(ctx, apply_choice)
@@ -618,8 +636,94 @@ def run_adjoint(args):
     return 0
 
 
+def run_variants(args):
+    """Equal-accuracy comparison of the Sinkhorn variants at eps = 0.002 on the
+    benchmark's sizes (T = 4096 samples of the initial double-integrator
+    trajectory, M = 16384 mixture samples): the field after n iterations is
+    compared with the converged field (4000 cold iterations), for the paper's
+    cold iteration, eps-scaling (eps_t = max(eps, 0.08 * 0.85^t)) and a warm
+    start from the converged potentials of the trajectory one outer
+    iteration earlier.  Reports, per variant, the iterations needed to reach
+    a relative field error of 1e-2 and 1e-3 and the time per iteration."""
+    import torch
+
+    from paper_2511_11514_b300 import binding as cov
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    w = wl.SINKHORN_DOUBLE_T4096
+    inst = wl.make_instance(w)
+    ctx = cov.Context(0)
+    eps, e0, dec = 0.002, 0.08, 0.85
+    y = torch.as_tensor(inst.y, dtype=torch.float32, device=dev)
+    P = cov.make_problem(w.model, w.T, w.dt, inst.s0, w.field, inst.Q, inst.R, w.eta, y=y, eps=eps, n_iter=50)
+    u = torch.as_tensor(inst.u0, dtype=torch.float64, device=dev)
+    s_prev = cov.cov_solve(ctx, P, 4, u).clone()                  # a trajectory a few iterations in
+    s_cur = cov.cov_solve_continue(ctx, P, 1, u, s_prev.clone())  # and the one after it
+    x_prev = s_prev[1:, :2].float().contiguous()
+    x = s_cur[1:, :2].float().contiguous()
+    a_ref, _, _, _ = cov.cov_field_sinkhorn(ctx, x, y, eps, 4000)
+    _, f_w, g_w, p_w = cov.cov_field_sinkhorn(ctx, x_prev, y, eps, 4000)
+    ref_norm = float(a_ref.double().norm())
+
+    def err(a):
+        return float((a.double() - a_ref.double()).norm()) / ref_norm
+
+    grid = [5, 10, 15, 20, 25, 30, 40, 50, 60, 80, 100, 130, 160, 200, 260, 330, 420, 540, 700, 900, 1200]
+    curves = {"cold": [], "eps_scaling": [], "warm": []}
+    for n in grid:
+        curves["cold"].append(err(cov.cov_field_sinkhorn(ctx, x, y, eps, n)[0]))
+        curves["eps_scaling"].append(err(cov.cov_field_sinkhorn_annealed(ctx, x, y, eps, n, e0, dec)[0]))
+        curves["warm"].append(err(cov.cov_field_sinkhorn(ctx, x, y, eps, n, f=f_w.clone(), g=g_w.clone(),
+                                                          p=p_w.clone(), warm=True)[0]))
+
+    def first_below(c, tol):
+        for n, e in zip(grid, c):
+            if e <= tol:
+                return n
+        return None
+
+    stream = torch.cuda.current_stream()
+
+    def per_iter_ms(fn):
+        ts = []
+        for n in (20, 120):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            fn(n)
+            a.record(stream)
+            fn(n)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return (ts[1] - ts[0]) / 100
+
+    t_cold = per_iter_ms(lambda n: cov.cov_field_sinkhorn(ctx, x, y, eps, n, field=False))
+    t_scaled = per_iter_ms(lambda n: cov.cov_field_sinkhorn_annealed(ctx, x, y, eps, n, e0, dec, field=False))
+    st, flags = ctx.device_status()
+    if st != cov.COV_OK:
+        raise SystemExit(f"device status {cov.status_string(st)} flags {flags}")
+    res = {v: {"iters_to_1e-2": first_below(c, 1e-2), "iters_to_1e-3": first_below(c, 1e-3)}
+           for v, c in curves.items()}
+    n_c, n_s, n_w = (res[v]["iters_to_1e-3"] for v in ("cold", "eps_scaling", "warm"))
+    line = {"metric": "Sinkhorn iterations to a 1e-3 field error at eps = 0.002 (cold / eps-scaled / warm)",
+            "value": {"cold": n_c, "eps_scaling": n_s, "warm": n_w}, "unit": "iterations",
+            "higher_is_better": False, "n_gpus": 1, "dtype": "f32", "data": "synthetic (seeded Philox mixture)",
+            "config": {"workload": f"{w.name} trajectory, eps = 0.002", "T": w.T, "M": w.M,
+                       "eps_schedule": f"max(eps, {e0} * {dec}^t)",
+                       "warm": "converged potentials of the previous outer iteration's trajectory",
+                       "reference": "4000 cold iterations"},
+            "variants": res, "grid": grid, "relative_field_error": curves,
+            "ms_per_iteration": {"cold": t_cold, "eps_scaling": t_scaled}}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
 def main():
     args = parse_args()
+    if args.variants:
+        return run_variants(args)
     if args.impl == "reference":
         return run_reference(args)
     if args.batched:
