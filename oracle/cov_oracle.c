@@ -230,6 +230,52 @@ void orc_sinkhorn(const double* x, int T, const double* y, int M,
     free(pn);
 }
 
+/* ------------------------------------------------------------------------
+ * Reference given as a density on a pixel grid (Sec. II-A: q may be a
+ * continuous function; the Stein field needs only its score).  Reading: q is
+ * the bilinear interpolant of the pixel values map[iy][ix] (iy the row /
+ * second coordinate), pixel centres at ((ix + 1/2)/W, (iy + 1/2)/H) on
+ * [0,1]^2, each coordinate clamped to the outermost centres (constant
+ * extension: no pull from outside the map).  score = grad q / q.
+ * ---------------------------------------------------------------------- */
+static void density_cell(int n, double xc, int* i0, double* f, int* inside) {
+    double u = xc * n - 0.5;
+    *inside = (u > 0.0 && u < n - 1.0);
+    if (u < 0.0) u = 0.0;
+    if (u > n - 1.0) u = n - 1.0;
+    int i = (int)floor(u);
+    if (i > n - 2) i = n - 2;
+    *i0 = i;
+    *f = u - i;
+}
+
+double orc_density_value(const double* map, int H, int W, const double* x) {
+    int ix, iy, inx, iny;
+    double fx, fy;
+    density_cell(W, x[0], &ix, &fx, &inx);
+    density_cell(H, x[1], &iy, &fy, &iny);
+    const double q00 = map[(size_t)iy * W + ix], q10 = map[(size_t)iy * W + ix + 1];
+    const double q01 = map[(size_t)(iy + 1) * W + ix], q11 = map[(size_t)(iy + 1) * W + ix + 1];
+    return (1 - fx) * (1 - fy) * q00 + fx * (1 - fy) * q10 + (1 - fx) * fy * q01 + fx * fy * q11;
+}
+
+void orc_density_score(const double* map, int H, int W, const double* x, int T, double* score) {
+    for (int i = 0; i < T; ++i) {
+        const double* xi = x + (size_t)i * 2;
+        int ix, iy, inx, iny;
+        double fx, fy;
+        density_cell(W, xi[0], &ix, &fx, &inx);
+        density_cell(H, xi[1], &iy, &fy, &iny);
+        const double q00 = map[(size_t)iy * W + ix], q10 = map[(size_t)iy * W + ix + 1];
+        const double q01 = map[(size_t)(iy + 1) * W + ix], q11 = map[(size_t)(iy + 1) * W + ix + 1];
+        const double q = (1 - fx) * (1 - fy) * q00 + fx * (1 - fy) * q10 + (1 - fx) * fy * q01 + fx * fy * q11;
+        const double gx = inx ? W * ((1 - fy) * (q10 - q00) + fy * (q11 - q01)) : 0.0;
+        const double gy = iny ? H * ((1 - fx) * (q01 - q00) + fx * (q11 - q10)) : 0.0;
+        score[(size_t)i * 2] = gx / q;
+        score[(size_t)i * 2 + 1] = gy / q;
+    }
+}
+
 /* eps-scaling (annealing; not in the paper, a standard way to speed up
  * Sinkhorn at small eps): iteration t (0-based) runs the same g, f, p
  * updates at eps_t = max(eps, eps_start * eps_decay^t); the potentials are
@@ -626,7 +672,8 @@ int orc_solve_ex(int model, int T, double dt, const double* s0, int field,
                  const double* gw, const double* gmu, const double* gsigma,
                  double eps, int n_iter, double h, const double* Q,
                  const double* R, double eta, int n_outer, double* u,
-                 double* s, int warm, double eps_start, double eps_decay);
+                 double* s, int warm, double eps_start, double eps_decay,
+                 const double* density, int dens_h, int dens_w);
 
 int orc_solve(int model, int T, double dt, const double* s0, int field,
               int d, const double* y, const double* b, int M, int K,
@@ -635,18 +682,20 @@ int orc_solve(int model, int T, double dt, const double* s0, int field,
               const double* R, double eta, int n_outer, double* u,
               double* s) {
     return orc_solve_ex(model, T, dt, s0, field, d, y, b, M, K, gw, gmu, gsigma, eps, n_iter, h, Q, R, eta,
-                        n_outer, u, s, 0, 0.0, 1.0);
+                        n_outer, u, s, 0, 0.0, 1.0, NULL, 0, 0);
 }
 
 /* Variant: warm != 0 keeps the Sinkhorn potentials from one outer iteration
  * to the next (the first starts cold); eps_start > eps anneals eps within
- * each field evaluation (orc_sinkhorn_annealed). */
+ * each field evaluation (orc_sinkhorn_annealed); density (dens_h x dens_w,
+ * d = 2) replaces the mixture as the Stein field's reference. */
 int orc_solve_ex(int model, int T, double dt, const double* s0, int field,
                  int d, const double* y, const double* b, int M, int K,
                  const double* gw, const double* gmu, const double* gsigma,
                  double eps, int n_iter, double h, const double* Q,
                  const double* R, double eta, int n_outer, double* u,
-                 double* s, int warm, double eps_start, double eps_decay) {
+                 double* s, int warm, double eps_start, double eps_decay,
+                 const double* density, int dens_h, int dens_w) {
     int n, m;
     if (orc_model_dims(model, &n, &m) != 0 || d > n) return -1;
     double* x = (double*)malloc(sizeof(double) * (size_t)T * d);
@@ -665,7 +714,10 @@ int orc_solve_ex(int model, int T, double dt, const double* s0, int field,
         for (int i = 0; i < T; ++i)
             for (int c = 0; c < d; ++c) x[(size_t)i * d + c] = s[(size_t)(i + 1) * n + c];
         if (field == ORC_FIELD_SVGD) {
-            orc_gmm_score(x, T, d, K, gw, gmu, gsigma, sc);
+            if (density)
+                orc_density_score(density, dens_h, dens_w, x, T, sc);
+            else
+                orc_gmm_score(x, T, d, K, gw, gmu, gsigma, sc);
             orc_svgd_field(x, T, d, sc, h, NULL, 0, a);
         } else {
             orc_sinkhorn_annealed(x, T, y, M, b, d, eps, n_iter, eps_start, eps_decay, warm && it > 0, f, g, p);

@@ -90,7 +90,9 @@ void orc_lqr_track(const double* A, const double* B, const double* Q,
 enum { ORC_FIELD_SVGD = 0, ORC_FIELD_SINKHORN = 1 };
 double orc_anneal_eps(double eps, double eps_start, double eps_decay, int t);
 void orc_sinkhorn_annealed(const double* x, int T, const double* y, int M, const double* b, int d, double eps, int n_iter, double eps_start, double eps_decay, int warm, double* f, double* g, double* p);
-int orc_solve_ex(int model, int T, double dt, const double* s0, int field, int d, const double* y, const double* b, int M, int K, const double* gw, const double* gmu, const double* gsigma, double eps, int n_iter, double h, const double* Q, const double* R, double eta, int n_outer, double* u, double* s, int warm, double eps_start, double eps_decay);
+int orc_solve_ex(int model, int T, double dt, const double* s0, int field, int d, const double* y, const double* b, int M, int K, const double* gw, const double* gmu, const double* gsigma, double eps, int n_iter, double h, const double* Q, const double* R, double eta, int n_outer, double* u, double* s, int warm, double eps_start, double eps_decay, const double* density, int dens_h, int dens_w);
+double orc_density_value(const double* map, int H, int W, const double* x);
+void orc_density_score(const double* map, int H, int W, const double* x, int T, double* score);
 int orc_solve(int model, int T, double dt, const double* s0, int field,
               int d, const double* y, const double* b, int M, int K,
               const double* gw, const double* gmu, const double* gsigma,

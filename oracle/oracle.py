@@ -83,7 +83,9 @@ def _declare(L):
         "orc_anneal_eps": (_d, [_d, _d, _d, _i]),
         "orc_sinkhorn_annealed": (None, [_D, _i, _D, _i, _D, _i, _d, _i, _d, _d, _i, _D, _D, _D]),
         "orc_solve_ex": (_i, [_i, _i, _d, _D, _i, _i, _D, _D, _i, _i, _D, _D, _D,
-                              _d, _i, _d, _D, _D, _d, _i, _D, _D, _i, _d, _d]),
+                              _d, _i, _d, _D, _D, _d, _i, _D, _D, _i, _d, _d, _D, _i, _i]),
+        "orc_density_value": (_d, [_D, _i, _i, _D]),
+        "orc_density_score": (None, [_D, _i, _i, _D, _i, _D]),
         "orc_sinkhorn_field_vjp": (None, [_D, _i, _D, _i, _D, _i, _d, _i, _D, _D, _D, _D]),
         "orc_lqr_vjp": (None, [_D, _D, _D, _D, _D, _i, _i, _i, _D]),
         "orc_rollout_vjp": (None, [_i, _D, _D, _i, _d, _D, _D, _D]),
@@ -210,6 +212,21 @@ def sinkhorn_annealed(x, y, b, eps, n_iter, eps_start, eps_decay, f=None, g=None
     return f, g, p
 
 
+def density_value(density, x) -> float:
+    m = _f64(density)
+    xv = _f64(x)
+    return float(lib().orc_density_value(_p(m), int(m.shape[0]), int(m.shape[1]), _p(xv)))
+
+
+def density_score(density, x):
+    """grad log q of the bilinear interpolant of the pixel density [H, W] at x [T, 2]."""
+    m, xv = _f64(density), _f64(x)
+    T = xv.shape[0]
+    out = np.empty((T, 2))
+    lib().orc_density_score(_p(m), int(m.shape[0]), int(m.shape[1]), _p(xv), T, _p(out))
+    return out
+
+
 def sinkhorn_field(x, y, b, eps, g, p, rows=None):
     x, y, g, p = _f64(x), _f64(y), _f64(g), _f64(p)
     b = None if b is None else _f64(b)
@@ -290,10 +307,13 @@ def lqr_track(A, B, Q, R, abar):
 
 # -- outer iteration -------------------------------------------------------
 def solve(model, dt, s0, u0, field, Q, R, eta, n_outer, *, d=2, y=None, b=None,
-          gmm=None, eps=0.0, n_iter=0, h=0.0, warm=False, eps_start=0.0, eps_decay=1.0):
+          gmm=None, eps=0.0, n_iter=0, h=0.0, warm=False, eps_start=0.0, eps_decay=1.0, density=None):
     """Returns (u, s) after n_outer iterations; u0 [T,m] is not modified.
     warm: Sinkhorn potentials carried across outer iterations; eps_start >
-    eps: eps-scaling within each field evaluation."""
+    eps: eps-scaling within each field evaluation; density [H, W]: the Stein
+    field's reference as a pixel density (instead of gmm)."""
+    dens = None if density is None else _f64(density)
+    dh, dw = (0, 0) if dens is None else (int(dens.shape[0]), int(dens.shape[1]))
     n, m = MODEL_DIMS[model]
     u = _f64(u0).copy()
     T = u.shape[0]
@@ -312,7 +332,7 @@ def solve(model, dt, s0, u0, field, Q, R, eta, n_outer, *, d=2, y=None, b=None,
     rc = lib().orc_solve_ex(int(model), T, float(dt), _p(s0), int(field), int(d), _p(yv), _p(bv), M, K,
                             _p(gw), _p(gmu), _p(gs), float(eps), int(n_iter), float(h), _p(Q), _p(R),
                             float(eta), int(n_outer), _p(u), _p(s), int(warm), float(eps_start),
-                            float(eps_decay))
+                            float(eps_decay), _p(dens), dh, dw)
     if rc != 0:
         raise ValueError("orc_solve: bad arguments")
     return u, s

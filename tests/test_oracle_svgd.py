@@ -124,3 +124,64 @@ def test_svgd_row_subset_matches_full(orc):
     full = orc.svgd_field(x, sc, 0.05)
     rows = np.array([0, 5, 32, 7])
     np.testing.assert_array_equal(orc.svgd_field(x, sc, 0.05, rows=rows), full[rows])
+
+
+# -- reference as a pixel density (bilinear interpolant) ----------------------------
+def _centres(n):
+    return (np.arange(n) + 0.5) / n
+
+
+def test_density_value_reproduces_bilinear_functions(orc):
+    """The bilinear interpolant is exact for q(x) = (1 + a x0)(1 + b x1)
+    between the outermost pixel centres, and equals the pixel values at the
+    centres."""
+    H, W, a, b = 7, 11, 0.8, -0.4
+    cx, cy = _centres(W), _centres(H)
+    m = (1 + a * cx)[None, :] * (1 + b * cy)[:, None]
+    r = wl.rng(3)
+    for _ in range(50):
+        x = np.array([r.uniform(cx[0], cx[-1]), r.uniform(cy[0], cy[-1])])
+        assert orc.density_value(m, x) == pytest.approx((1 + a * x[0]) * (1 + b * x[1]), rel=1e-13)
+    assert orc.density_value(m, np.array([cx[3], cy[5]])) == pytest.approx(m[5, 3], rel=1e-14)
+
+
+def test_density_score_closed_form(orc):
+    H, W, a, b = 9, 6, 0.8, -0.4
+    cx, cy = _centres(W), _centres(H)
+    m = (1 + a * cx)[None, :] * (1 + b * cy)[:, None]
+    r = wl.rng(4)
+    x = np.stack([r.uniform(cx[0] + 1e-3, cx[-1] - 1e-3, 40), r.uniform(cy[0] + 1e-3, cy[-1] - 1e-3, 40)], 1)
+    sc = orc.density_score(m, x)
+    np.testing.assert_allclose(sc[:, 0], a / (1 + a * x[:, 0]), rtol=1e-12)
+    np.testing.assert_allclose(sc[:, 1], b / (1 + b * x[:, 1]), rtol=1e-12)
+
+
+def test_density_score_is_gradient_of_log_value(orc):
+    """Central differences of log q (the value pinned above) on a random map,
+    away from cell edges; outside the centre range the score is zero."""
+    m = wl.density_map(seed=5, n=64)
+    r = wl.rng(6)
+    x = r.uniform(0.05, 0.95, size=(60, 2))
+    sc = orc.density_score(m, x)
+    h = 1e-7
+    for i in range(60):
+        for c in range(2):
+            e = np.zeros(2)
+            e[c] = h
+            fd = (np.log(orc.density_value(m, x[i] + e)) - np.log(orc.density_value(m, x[i] - e))) / (2 * h)
+            assert sc[i, c] == pytest.approx(fd, rel=1e-5, abs=1e-6)
+    out = np.array([[-0.2, 0.5], [0.5, 1.3], [1.2, -0.1]])
+    so = orc.density_score(m, out)
+    assert so[0, 0] == 0 and so[1, 1] == 0 and np.all(so[2] == 0)
+
+
+def test_density_score_of_a_fine_gaussian_map(orc):
+    """A 512^2 map of an isotropic Gaussian: the score approaches
+    -(x - mu)/sigma^2 (discretisation error O(pixel^2 / sigma^2))."""
+    n, mu, sig = 512, np.array([0.45, 0.55]), 0.12
+    c = _centres(n)
+    m = np.exp(-((c[None, :] - mu[0]) ** 2 + (c[:, None] - mu[1]) ** 2) / (2 * sig ** 2))
+    x = wl.rng(7).uniform(0.25, 0.75, size=(200, 2))
+    sc = orc.density_score(m, x)
+    want = -(x - mu) / sig ** 2
+    assert np.linalg.norm(sc - want) <= 2e-2 * np.linalg.norm(want)
