@@ -135,6 +135,17 @@ COV_API cov_status cov_gmm_score(cov_ctx* ctx, const float* x, int T, int d,
                          const cov_gmm* gmm, float* score,
                          cov_stream_t stream);
 
+/* Score of a reference given as a density on a pixel grid (Sec. II-A: q as
+ * a continuous function), d = 2: q is the bilinear interpolant of
+ * map[iy][ix] with pixel centres at ((ix + 1/2)/W, (iy + 1/2)/H) on [0,1]^2,
+ * each coordinate clamped to the outermost centres (outside them that
+ * component of the score is 0), and score = grad q / q.
+ *   map [H][W] FP32 device, positive (row iy = second coordinate), H, W >= 2
+ *   x [T][2] FP32 device;  score [T][2] FP32 device */
+COV_API cov_status cov_density_score(cov_ctx* ctx, const float* map, int H, int W,
+                                     const float* x, int T, float* score,
+                                     cov_stream_t stream);
+
 /* ---- Stein variational field, Eq. 4 ------------------------------------- */
 
 /* a_out[i] = 1/T sum_j [ k(x_j, x_i) score_j + grad_{x_j} k(x_j, x_i) ],
@@ -277,6 +288,10 @@ typedef struct {
                            * potentials of the previous outer iteration
                            * (cov_solve starts cold; cov_solve_continue keeps
                            * them while nothing else ran on the context) */
+    /* Stein field with a pixel-density reference instead of gmm (d = 2):
+     * [density_h][density_w] FP32 device map, as cov_density_score; NULL: gmm */
+    const float* density;
+    int density_h, density_w;
 } cov_problem;
 
 /* Run n_outer outer iterations: x = first d components of s_1..s_T;

@@ -36,7 +36,7 @@ EXPORTS = (
     "cov_lqr_track", "cov_solve", "cov_solve_continue", "cov_solve_batched", "cov_workspace_size_batched",
     "cov_probe_peaks", "cov_workspace_size_vjp", "cov_field_sinkhorn_vjp", "cov_workspace_size_lqr_vjp",
     "cov_lqr_vjp", "cov_rollout_vjp", "cov_solve_checkpointed", "cov_workspace_size_backward",
-    "cov_solve_backward", "cov_field_sinkhorn_annealed",
+    "cov_solve_backward", "cov_field_sinkhorn_annealed", "cov_density_score",
 )
 
 
@@ -58,7 +58,8 @@ class cov_problem(ctypes.Structure):
     _fields_ = [("model", _i), ("T", _i), ("dt", _d), ("s0", _d * MAX_N), ("field", _i), ("d", _i),
                 ("y", _P), ("b", _P), ("M", _i), ("eps", _f), ("n_iter", _i), ("gmm", cov_gmm), ("h", _f),
                 ("Q", _d * (MAX_N * MAX_N)), ("R", _d * (MAX_M * MAX_M)), ("eta", _d),
-                ("eps_start", _f), ("eps_decay", _f), ("warm", _i)]
+                ("eps_start", _f), ("eps_decay", _f), ("warm", _i), ("density", _P), ("density_h", _i),
+                ("density_w", _i)]
 
 
 _lib = None
@@ -95,6 +96,7 @@ def load(path: str = LIB_PATH):
                                    ctypes.POINTER(_P), _P]),
         "cov_workspace_size_batched": (_sz, [ctypes.POINTER(cov_problem), _i]),
         "cov_probe_peaks": (_i, [_P, _i, ctypes.POINTER(_d), _P]),
+        "cov_density_score": (_i, [_P, _P, _i, _i, _P, _i, _P, _P]),
         "cov_field_sinkhorn_annealed": (_i, [_P, _P, _i, _P, _P, _i, _i, _f, _i, _f, _f, _i, _P, _P, _P, _P, _P]),
         "cov_workspace_size_vjp": (_sz, [_i, _i, _i, _i]),
         "cov_field_sinkhorn_vjp": (_i, [_P, _P, _i, _P, _P, _i, _i, _f, _i, _P, _P, _P, _P, _P]),
@@ -205,6 +207,18 @@ def _gmm_struct(gmm, d):
     g = cov_gmm(K=int(w.size), d=int(d), w=w.ctypes.data_as(_P), mu=mu.ctypes.data_as(_P),
                 sigma=sigma.ctypes.data_as(_P))
     return g, (w, mu, sigma)
+
+
+def cov_density_score(ctx: Context, density, x, out=None, stream=None):
+    """grad log q of the bilinear interpolant of the pixel density [H, W] at x [T, 2]."""
+    T = x.shape[0]
+    H, W = density.shape
+    out = torch.empty((T, 2), device=x.device, dtype=torch.float32) if out is None else out
+    st = load().cov_density_score(ctx.h, _ptr(density, torch.float32, name="density"), int(H), int(W),
+                                  _ptr(x, torch.float32, (T, 2), "x"), T, _ptr(out, torch.float32, (T, 2), "out"),
+                                  _stream(stream))
+    ctx._check(st, "cov_density_score")
+    return out
 
 
 def cov_gmm_score(ctx: Context, x, gmm, out=None, stream=None):
@@ -323,7 +337,7 @@ def cov_lqr_track(ctx: Context, A, B, Q, R, abar, want_z=True, stream=None):
 
 
 def make_problem(model, T, dt, s0, field, Q, R, eta, *, d=2, y=None, b=None, eps=0.0, n_iter=0, gmm=None, h=0.0,
-                 eps_start=0.0, eps_decay=1.0, warm=False):
+                 eps_start=0.0, eps_decay=1.0, warm=False, density=None):
     """Build a cov_problem; returns (struct, keep-alive list).  eps_start >
     eps turns on eps-scaling; warm carries the Sinkhorn potentials between
     outer iterations."""
@@ -353,6 +367,11 @@ def make_problem(model, T, dt, s0, field, Q, R, eta, *, d=2, y=None, b=None, eps
         P.gmm = g
         keep.append(arrs)
         P.h = float(h)
+    if density is not None:
+        P.density = _ptr(density, torch.float32, name="density").value
+        P.density_h, P.density_w = int(density.shape[0]), int(density.shape[1])
+        P.h = float(h)
+        keep.append(density)
     return P, keep
 
 

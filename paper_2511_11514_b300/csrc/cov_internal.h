@@ -145,6 +145,9 @@ cov_status sinkhorn_vjp_ws(cov_ctx* ctx, void* ws, size_t ws_bytes, const float*
 // Statistics of a reference set that every field evaluation on it needs:
 // scal[0..d) = mean of y, scal[8] = 1 / sum b (0 when b == NULL).
 void sinkhorn_reference_stats(const float* y, int M, int d, const float* b, float* scal, cudaStream_t stream);
+// Score of a pixel-density reference at x [T][x_ld] (d = 2) into score [T][2].
+cov_status density_score_launch(cov_ctx* ctx, const float* map, int H, int W, const float* x, int x_ld, int T,
+                                float* score, cudaStream_t stream);
 cov_status svgd_field_ws(cov_ctx* ctx, void* ws, size_t ws_bytes, const float* x, int x_ld, int T, int d,
                          const float* score, const cov_gmm* gmm, float h, float* a_out, cudaStream_t stream);
 cov_status lqr_track_ws(cov_ctx* ctx, void* ws, size_t ws_bytes, const double* A, const double* B,

@@ -1204,6 +1204,48 @@ __global__ void gmm_score_kernel(const float* __restrict__ x, int T, int d, GmmP
     if (!ok) raise_status(status, kDevNonfinite);
 }
 
+// Score of a pixel-density reference (d = 2): q is the bilinear interpolant
+// of map[iy][ix] with pixel centres at ((ix + 1/2)/W, (iy + 1/2)/H), each
+// coordinate clamped to the outermost centres (constant extension, zero
+// gradient outside), score = grad q / q.  One thread per point; the map
+// (1 MB at 512^2) stays in L2.
+__device__ __forceinline__ void density_score_at(const float* __restrict__ map, int H, int W, float x0, float x1,
+                                                 float* sc) {
+    float u = fmaf(x0, (float)W, -0.5f), v = fmaf(x1, (float)H, -0.5f);
+    const bool inx = u > 0.f && u < (float)(W - 1), iny = v > 0.f && v < (float)(H - 1);
+    u = fminf(fmaxf(u, 0.f), (float)(W - 1));
+    v = fminf(fmaxf(v, 0.f), (float)(H - 1));
+    const int ix = min((int)floorf(u), W - 2), iy = min((int)floorf(v), H - 2);
+    const float fx = u - (float)ix, fy = v - (float)iy;
+    const float q00 = __ldg(map + (size_t)iy * W + ix), q10 = __ldg(map + (size_t)iy * W + ix + 1);
+    const float q01 = __ldg(map + (size_t)(iy + 1) * W + ix), q11 = __ldg(map + (size_t)(iy + 1) * W + ix + 1);
+    const float q0 = fmaf(fx, q10 - q00, q00), q1 = fmaf(fx, q11 - q01, q01);
+    const float q = fmaf(fy, q1 - q0, q0);
+    const float gx = inx ? (float)W * fmaf(fy, (q11 - q01) - (q10 - q00), q10 - q00) : 0.f;
+    const float gy = iny ? (float)H * (q1 - q0) : 0.f;
+    const float iq = 1.0f / q;
+    sc[0] = gx * iq;
+    sc[1] = gy * iq;
+}
+
+__global__ void density_score_kernel(const float* __restrict__ map, int H, int W, const float* __restrict__ x,
+                                     int x_ld, int T, float* __restrict__ score, unsigned* status) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= T) return;
+    float sc[2];
+    density_score_at(map, H, W, x[(size_t)i * x_ld], x[(size_t)i * x_ld + 1], sc);
+    score[(size_t)i * 2] = sc[0];
+    score[(size_t)i * 2 + 1] = sc[1];
+    if (!(finitef(sc[0]) && finitef(sc[1]))) raise_status(status, kDevNonfinite);
+}
+
+cov_status density_score_launch(cov_ctx* ctx, const float* map, int H, int W, const float* x, int x_ld, int T,
+                                float* score, cudaStream_t stream) {
+    if (!ctx || !map || !x || !score || T < 1 || H < 2 || W < 2 || x_ld < 2) return COV_ERR_INVALID_ARG;
+    density_score_kernel<<<(T + 255) / 256, 256, 0, stream>>>(map, H, W, x, x_ld, T, score, ctx->status);
+    return cuda_failed(ctx, cudaGetLastError()) ? COV_ERR_CUDA : COV_OK;
+}
+
 // xt = x / (h sqrt(2 ln 2)),  st = score h / sqrt(2 ln 2); padding: xt far away, st = 0.
 __global__ void svgd_prep_kernel(const float* __restrict__ x, int x_ld, int T, int d, int Tp,
                                  const float* __restrict__ score, GmmParams G, int use_gmm, float inv_hs, float hs,
@@ -1322,6 +1364,13 @@ extern "C" cov_status cov_field_svgd(cov_ctx* ctx, const float* x, int T, int d,
     if (cudaSetDevice(ctx->device) != cudaSuccess) return COV_ERR_CUDA;
     cov::clobber_ws_caches(ctx);  // the workspace scratch overwrites cov_solve's caches
     return cov::svgd_field_ws(ctx, ctx->ws, ctx->ws_bytes, x, d, T, d, score, gmm, h, a_out, (cudaStream_t)stream);
+}
+
+extern "C" cov_status cov_density_score(cov_ctx* ctx, const float* map, int H, int W, const float* x, int T,
+                                        float* score, cov_stream_t stream) {
+    if (!ctx) return COV_ERR_INVALID_ARG;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return COV_ERR_CUDA;
+    return cov::density_score_launch(ctx, map, H, W, x, 2, T, score, (cudaStream_t)stream);
 }
 
 extern "C" cov_status cov_gmm_score(cov_ctx* ctx, const float* x, int T, int d, const cov_gmm* gmm, float* score,

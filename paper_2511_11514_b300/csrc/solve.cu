@@ -176,7 +176,12 @@ static cov_status validate(const cov_problem* P, int* n, int* m) {
             return COV_ERR_INVALID_ARG;
     } else if (P->field == COV_FIELD_SVGD) {
         GmmParams G;
-        if (!(P->h > 0.f) || make_gmm_params(&P->gmm, P->d, &G) != COV_OK) return COV_ERR_INVALID_ARG;
+        if (!(P->h > 0.f)) return COV_ERR_INVALID_ARG;
+        if (P->density) {
+            if (P->d != 2 || P->density_h < 2 || P->density_w < 2) return COV_ERR_INVALID_ARG;
+        } else if (make_gmm_params(&P->gmm, P->d, &G) != COV_OK) {
+            return COV_ERR_INVALID_ARG;
+        }
     } else {
         return COV_ERR_INVALID_ARG;
     }
@@ -196,8 +201,15 @@ static cov_status enqueue_iteration(cov_ctx* ctx, const cov_problem* P, int n, i
                               warm ? COV_WARM_START : 0, warm ? b.f : nullptr, warm ? b.g : nullptr,
                               warm ? b.p : nullptr, b.a, st, b.scal, P->eps_start, P->eps_decay);
     }
-    else
+    else if (P->density) {
+        // the score of the density reference, then the field (b.abar is free
+        // until the lift below: the score is kept there in FP32)
+        float* score = reinterpret_cast<float*>(b.abar);
+        r = density_score_launch(ctx, P->density, P->density_h, P->density_w, b.x, d, T, score, st);
+        if (r == COV_OK) r = svgd_field_ws(ctx, rest, rest_bytes, b.x, d, T, d, score, nullptr, P->h, b.a, st);
+    } else {
         r = svgd_field_ws(ctx, rest, rest_bytes, b.x, d, T, d, nullptr, &P->gmm, P->h, b.a, st);
+    }
     if (r != COV_OK) return r;
     lift_kernel<<<nb, 256, 0, st>>>(b.a, T, n, d, b.abar);
     if (!model_is_lti(P->model)) {

@@ -104,3 +104,35 @@ def test_invalid_decay_is_rejected(cov, ctx):
     x = dev32(wl.random_points(16, 2, seed=1))
     with pytest.raises(cov.CovError):
         cov.cov_field_sinkhorn_annealed(ctx, x, x, 0.01, 3, 0.1, 1.5)
+
+
+# -- Stein field with a pixel-density reference --------------------------------------
+DENSITY_TOL = 1e-4   # norm-wise; FP32 cell coordinate u = x W - 1/2 resolves 2^-24 W of a pixel
+
+
+def test_density_score_matches_oracle(cov, ctx, orc):
+    m = wl.f32_pair(wl.density_map(seed=3))[1]
+    x = wl.random_points(20000, 2, seed=801, lo=-0.05, hi=1.05)   # includes the clamped border strip
+    sc = cov.cov_density_score(ctx, dev32(m), dev32(x))
+    st, flags = ctx.device_status()
+    assert st == cov.COV_OK, flags
+    so = orc.density_score(m, x)
+    assert rel_norm(host(sc), so) <= DENSITY_TOL
+
+
+@pytest.mark.parametrize("use_graph", [0, 1])
+def test_svgd_solve_with_density_matches_oracle(cov, ctx, orc, use_graph):
+    inst = wl.make_instance(wl.SVGD_SINGLE_T256)
+    w = inst.wl
+    m = wl.f32_pair(wl.density_map(seed=4, n=128))[1]
+    eta = 1e-3
+    P = cov.make_problem(w.model, w.T, w.dt, inst.s0, w.field, inst.Q, inst.R, eta, density=dev32(m), h=w.h)
+    ctx.set_option(cov.OPT_USE_GRAPH, use_graph)
+    try:
+        u = dev64(inst.u0)
+        s = cov.cov_solve(ctx, P, 3, u)
+    finally:
+        ctx.set_option(cov.OPT_USE_GRAPH, 1)
+    uo, so = orc.solve(w.model, w.dt, inst.s0, inst.u0, w.field, inst.Q, inst.R, eta, 3, h=w.h, density=m)
+    s_init = orc.rollout(w.model, inst.s0, inst.u0, w.dt)
+    assert rel_norm(host(s) - s_init, so - s_init) <= 1e-4
