@@ -757,88 +757,173 @@ struct RolloutArgs {
     double s0[COV_MAX_N];
 };
 
-// Inclusive prefix sum of a[0], a[st], ..., a[(L-1) st] in place (one CTA).
-__device__ void cta_inclusive_scan(double* a, int st, int L, double* sh) {
-    const int tid = threadIdx.x, nt = blockDim.x;
-    const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
-    const int S = (L + nt - 1) / nt;
-    const int b = min(tid * S, L), e = min(b + S, L);
-    double run = 0.0;
-    for (int i = b; i < e; ++i) {
-        run += a[(size_t)i * st];
-        a[(size_t)i * st] = run;
-    }
-    double x = run;
+// Block-wide exclusive scan of NV values per thread (1024 threads): on
+// return x[c] holds the sum over lower threads and tot[c] the block total.
+template <int NV>
+__device__ __forceinline__ void block_exclusive_scan(double (&x)[NV], double (&tot)[NV], double (*sh)[NV]) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    double inc[NV];
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const double y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) sh[warp] = x;
-    __syncthreads();
-    if (warp == 0) {
-        double v = lane < nw ? sh[lane] : 0.0;
+    for (int c = 0; c < NV; ++c) {
+        inc[c] = x[c];
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const double y = __shfl_up_sync(0xffffffffu, v, o);
-            if (lane >= o) v += y;
+            const double y = __shfl_up_sync(0xffffffffu, inc[c], o);
+            if (lane >= o) inc[c] += y;
         }
-        sh[lane] = v;
+    }
+    if (lane == 31)
+#pragma unroll
+        for (int c = 0; c < NV; ++c) sh[warp][c] = inc[c];
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int c = 0; c < NV; ++c) {
+            double w = lane < nw ? sh[lane][c] : 0.0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const double y = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w += y;
+            }
+            sh[lane][c] = w;  // inclusive over warps
+        }
     }
     __syncthreads();
-    const double off = (x - run) + (warp > 0 ? sh[warp - 1] : 0.0);
-    for (int i = b; i < e; ++i) a[(size_t)i * st] += off;
-    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < NV; ++c) {
+        tot[c] = sh[nw - 1][c];
+        x[c] = (inc[c] - x[c]) + (warp > 0 ? sh[warp - 1][c] : 0.0);
+    }
+    __syncthreads();  // sh is reused by the next scan
 }
+
+// u_t += eta v_t and the Euler rollout from s0, in tiles of blockDim x kRK
+// steps: each thread owns kRK consecutive steps of a tile (loaded and stored
+// as whole rows), the nested prefix sums of the model run in registers
+// (thread-serial prefix + block scan of the thread totals) and carry from
+// tile to tile.  Increments: single integrator p += dt u; double integrator
+// vel += dt u, p += dt vel (vel before its update); unicycle theta += dt
+// omega, (x, y) += dt v (cos, sin)(theta before its update).
+constexpr int kRK = 4;
 
 __global__ void __launch_bounds__(1024) update_rollout_kernel(RolloutArgs ro, double* __restrict__ u,
                                                                const double* __restrict__ v, int T, int n, int m,
                                                                double* __restrict__ s) {
-    __shared__ double sh[32];
-    const int tid = threadIdx.x, nt = blockDim.x;
-    if (v)
-        for (int i = tid; i < T * m; i += nt) u[i] = fma(ro.eta, v[i], u[i]);
-    for (int r = tid; r < n; r += nt) s[r] = ro.s0[r];
-    __syncthreads();
+    __shared__ double sh[32][2];
+    const int tid = threadIdx.x;
     const double dt = ro.dt;
-    switch (ro.model) {
-        case COV_SINGLE_INT:
-            for (int i = tid; i < T * 2; i += nt) s[(size_t)(i / 2 + 1) * n + i % 2] = dt * u[i];
-            __syncthreads();
-            for (int r = 0; r < 2; ++r) cta_inclusive_scan(s + n + r, n, T, sh);
-            for (int i = tid; i < T * 2; i += nt) s[(size_t)(i / 2 + 1) * n + i % 2] += ro.s0[i % 2];
-            break;
-        case COV_DOUBLE_INT:
-            for (int i = tid; i < T * 2; i += nt) s[(size_t)(i / 2 + 1) * n + 2 + i % 2] = dt * u[i];
-            __syncthreads();
-            for (int r = 0; r < 2; ++r) cta_inclusive_scan(s + n + 2 + r, n, T, sh);
-            for (int i = tid; i < T * 2; i += nt) s[(size_t)(i / 2 + 1) * n + 2 + i % 2] += ro.s0[2 + i % 2];
-            __syncthreads();
-            // positions: increments dt vel_t (vel_t = state at time t)
-            for (int i = tid; i < T * 2; i += nt) {
-                const int t = i / 2, r = i % 2;
-                s[(size_t)(t + 1) * n + r] = dt * s[(size_t)t * n + 2 + r];
+    for (int r = tid; r < n; r += blockDim.x) s[r] = ro.s0[r];
+    // carries: state at the start of the tile
+    double c0 = ro.s0[0], c1 = ro.s0[1], c2 = n > 2 ? ro.s0[2] : 0.0, c3 = n > 3 ? ro.s0[3] : 0.0;
+    const int per_tile = blockDim.x * kRK;
+    for (int base = 0; base < T; base += per_tile) {
+        const int t0 = base + tid * kRK;
+        double uk[kRK][2];
+#pragma unroll
+        for (int k = 0; k < kRK; ++k) {
+            const int t = t0 + k;
+            uk[k][0] = uk[k][1] = 0.0;
+            if (t < T) {
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    double w = u[(size_t)t * m + c];
+                    if (v) {
+                        w = fma(ro.eta, v[(size_t)t * m + c], w);
+                        u[(size_t)t * m + c] = w;
+                    }
+                    uk[k][c] = w;
+                }
             }
-            __syncthreads();
-            for (int r = 0; r < 2; ++r) cta_inclusive_scan(s + n + r, n, T, sh);
-            for (int i = tid; i < T * 2; i += nt) s[(size_t)(i / 2 + 1) * n + i % 2] += ro.s0[i % 2];
-            break;
-        default:  // unicycle
-            for (int t = tid; t < T; t += nt) s[(size_t)(t + 1) * n + 2] = dt * u[(size_t)t * m + 1];
-            __syncthreads();
-            cta_inclusive_scan(s + n + 2, n, T, sh);
-            for (int t = tid; t < T; t += nt) s[(size_t)(t + 1) * n + 2] += ro.s0[2];
-            __syncthreads();
-            for (int t = tid; t < T; t += nt) {
+        }
+        double out[kRK][COV_MAX_N];
+        if (ro.model == COV_SINGLE_INT || ro.model == COV_DOUBLE_INT) {
+            // first level: a_t = dt u_t (positions of the single integrator,
+            // velocities of the double integrator)
+            double run[2] = {0.0, 0.0}, incl[kRK][2], excl[kRK][2];
+#pragma unroll
+            for (int k = 0; k < kRK; ++k)
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    excl[k][c] = run[c];
+                    run[c] += dt * uk[k][c];
+                    incl[k][c] = run[c];
+                }
+            double off[2] = {run[0], run[1]}, tot[2];
+            block_exclusive_scan<2>(off, tot, sh);
+            const double b0 = ro.model == COV_SINGLE_INT ? c0 : c2, b1 = ro.model == COV_SINGLE_INT ? c1 : c3;
+            if (ro.model == COV_SINGLE_INT) {
+#pragma unroll
+                for (int k = 0; k < kRK; ++k) {
+                    out[k][0] = b0 + (off[0] + incl[k][0]);
+                    out[k][1] = b1 + (off[1] + incl[k][1]);
+                }
+                c0 += tot[0];
+                c1 += tot[1];
+            } else {
+                // second level: positions += dt vel_t, vel_t the velocity at time t
+                double run2[2] = {0.0, 0.0}, incl2[kRK][2];
+#pragma unroll
+                for (int k = 0; k < kRK; ++k) {
+                    out[k][2] = b0 + (off[0] + incl[k][0]);
+                    out[k][3] = b1 + (off[1] + incl[k][1]);
+                    run2[0] += dt * (b0 + (off[0] + excl[k][0]));
+                    run2[1] += dt * (b1 + (off[1] + excl[k][1]));
+                    incl2[k][0] = run2[0];
+                    incl2[k][1] = run2[1];
+                }
+                double off2[2] = {run2[0], run2[1]}, tot2[2];
+                block_exclusive_scan<2>(off2, tot2, sh);
+#pragma unroll
+                for (int k = 0; k < kRK; ++k) {
+                    out[k][0] = c0 + (off2[0] + incl2[k][0]);
+                    out[k][1] = c1 + (off2[1] + incl2[k][1]);
+                }
+                c0 += tot2[0];
+                c1 += tot2[1];
+                c2 += tot[0];
+                c3 += tot[1];
+            }
+        } else {  // unicycle: heading first, then the position increments along it
+            double run = 0.0, incl[kRK], excl[kRK];
+#pragma unroll
+            for (int k = 0; k < kRK; ++k) {
+                excl[k] = run;
+                run += dt * uk[k][1];
+                incl[k] = run;
+            }
+            double off[1] = {run}, tot[1];
+            block_exclusive_scan<1>(off, tot, reinterpret_cast<double(*)[1]>(&sh[0][0]));
+            double run2[2] = {0.0, 0.0}, incl2[kRK][2];
+#pragma unroll
+            for (int k = 0; k < kRK; ++k) {
+                out[k][2] = c2 + (off[0] + incl[k]);
                 double sn, cs;
-                sincos(s[(size_t)t * n + 2], &sn, &cs);
-                const double sp = dt * u[(size_t)t * m];
-                s[(size_t)(t + 1) * n + 0] = sp * cs;
-                s[(size_t)(t + 1) * n + 1] = sp * sn;
+                sincos(c2 + (off[0] + excl[k]), &sn, &cs);
+                const double sp = dt * uk[k][0];
+                run2[0] += sp * cs;
+                run2[1] += sp * sn;
+                incl2[k][0] = run2[0];
+                incl2[k][1] = run2[1];
             }
-            __syncthreads();
-            for (int r = 0; r < 2; ++r) cta_inclusive_scan(s + n + r, n, T, sh);
-            for (int i = tid; i < T * 2; i += nt) s[(size_t)(i / 2 + 1) * n + i % 2] += ro.s0[i % 2];
+            double off2[2] = {run2[0], run2[1]}, tot2[2];
+            block_exclusive_scan<2>(off2, tot2, sh);
+#pragma unroll
+            for (int k = 0; k < kRK; ++k) {
+                out[k][0] = c0 + (off2[0] + incl2[k][0]);
+                out[k][1] = c1 + (off2[1] + incl2[k][1]);
+            }
+            c0 += tot2[0];
+            c1 += tot2[1];
+            c2 += tot[0];
+        }
+#pragma unroll
+        for (int k = 0; k < kRK; ++k) {
+            const int t = t0 + k;
+            if (t < T)
+#pragma unroll
+                for (int r = 0; r < COV_MAX_N; ++r)
+                    if (r < n) s[(size_t)(t + 1) * n + r] = out[k][r];
+        }
     }
 }
 

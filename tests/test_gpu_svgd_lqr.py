@@ -107,10 +107,13 @@ def test_lqr_unicycle_long_horizon(cov, ctx, orc):
     assert ctx.device_status()[1] == 0
 
 
+@pytest.mark.parametrize("T", [1, 513, 4096, 10001])
 @pytest.mark.parametrize("model", [wl.SINGLE_INT, wl.DOUBLE_INT, wl.UNICYCLE])
-def test_linearize_and_rollout_match_oracle(cov, ctx, orc, model):
+def test_linearize_and_rollout_match_oracle(cov, ctx, orc, model, T):
+    """The rollout runs in tiles of 4096 steps with carries; T spans one,
+    several and a ragged last tile."""
     n, m = wl.MODEL_DIMS[model]
-    T, dt = 513, 0.03
+    dt = 0.03
     g = wl.rng(model)
     s0 = g.standard_normal(n)
     u = g.standard_normal((T, m))
