@@ -47,6 +47,10 @@ FP32_OPS_PER_PAIR = 5
 SM_COUNT_NOMINAL = 148
 SM_MAX_MHZ_NOMINAL = 2032.0
 FP32_LANES_PER_SM_CLK = 128
+# DRAM bytes (read + write) per launch of pairs_kernel at the benchmark
+# workload from one ncu capture of the current kernel: 280 KB (g + p launch)
+# and 247 KB (f launch), no writes.
+PAIRS_TRAFFIC_BYTES = 263424
 
 
 def parse_args():
@@ -130,10 +134,11 @@ class Clocks:
 
 
 # -- CPU oracle timing (reference arm and cpu_baseline) ---------------------------
-def oracle_sample(inst, rows, seed=0):
-    """One bounded sample of the workload on the oracle: `rows` rows of each
-    Sinkhorn update (g, f, p) from the initial trajectory.  Returns (pairs,
-    seconds)."""
+def oracle_sample(inst, rows, seed=0, iters=1):
+    """A bounded sample of the workload on the oracle: `iters` chained
+    Sinkhorn iterations from the initial trajectory, each over `rows` rows
+    of every update (g, f, p; all rows once `rows` reaches the set size).
+    Returns (pairs, seconds)."""
     import oracle as orc
     w = inst.wl
     s = orc.rollout(w.model, inst.s0, inst.u0, w.dt)
@@ -143,35 +148,42 @@ def oracle_sample(inst, rows, seed=0):
     r = wl.rng(seed)
     ry = r.choice(M, size=min(rows, M), replace=False)
     rx = r.choice(T, size=min(rows, T), replace=False)
-    f = np.zeros(T)
+    f, g, p = np.zeros(T), np.zeros(M), np.zeros(T)
     t0 = time.perf_counter()
-    g = orc.sinkhorn_g_update(x, y, w.eps, f, rows=ry)
-    gf = np.zeros(M)
-    gf[ry] = g
-    orc.sinkhorn_f_update(x, y, None, w.eps, gf, rows=rx)
-    orc.sinkhorn_p_update(x, w.eps, np.zeros(T), rows=rx)
+    for _ in range(iters):
+        g[ry] = orc.sinkhorn_g_update(x, y, w.eps, f, rows=ry)
+        f[rx] = orc.sinkhorn_f_update(x, y, None, w.eps, g, rows=rx)
+        p[rx] = orc.sinkhorn_p_update(x, w.eps, p, rows=rx)
     dt = time.perf_counter() - t0
-    return len(ry) * T + len(rx) * M + len(rx) * T, dt
+    return iters * (len(ry) * T + len(rx) * M + len(rx) * T), dt
 
 
-def calibrate_rows(inst, seconds):
+def calibrate(inst, seconds):
+    """(rows, iterations) of a sample that takes about `seconds`."""
     import oracle as orc
     orc.set_threads(os.cpu_count() or 1)
     pairs, dt = oracle_sample(inst, 64)
     rate = pairs / max(dt, 1e-9)
     per_row = pairs / 64
-    return max(64, int(seconds * rate / per_row))
+    rows = max(64, int(seconds * rate / per_row))
+    T, M = inst.wl.T, inst.wl.M
+    if rows <= min(T, M):
+        return rows, 1
+    _, dt_full = oracle_sample(inst, max(T, M))  # one full iteration: the small sample underrates the cores
+    return max(T, M), max(1, int(round(seconds / max(dt_full, 1e-9))))
 
 
 def cpu_baseline(inst, seconds):
     import oracle as orc
     orc.set_threads(os.cpu_count() or 1)
-    rows = calibrate_rows(inst, seconds)
-    pairs, dt = oracle_sample(inst, rows, seed=1)
+    rows, iters = calibrate(inst, seconds)
+    pairs, dt = oracle_sample(inst, rows, seed=1, iters=iters)
     T, M = inst.wl.T, inst.wl.M
+    what = (f"{rows} rows of each Sinkhorn update" if iters == 1 else
+            f"{iters} full Sinkhorn iterations (g over T={T}, f over M={M}, p over T)")
     return {"value": pairs / dt, "unit": UNIT, "cores": orc.get_threads(), "kind": "oracle",
-            "sample": f"FP64 oracle: {rows} rows of each Sinkhorn update (g over T={T}, f over M={M}, p over T) "
-                      f"of the workload, {pairs:.3e} pair evaluations in {dt:.1f} s, {orc.get_threads()} threads"}
+            "sample": f"FP64 oracle: {what} of the workload from its initial trajectory, {pairs:.3e} pair "
+                      f"evaluations in {dt:.1f} s, {orc.get_threads()} threads"}
 
 
 def workload_config(w, extra=None):
@@ -194,22 +206,25 @@ def run_reference(args):
     w = wl.WORKLOADS[args.workload]
     inst = wl.make_instance(w)
     orc.set_threads(os.cpu_count() or 1)
-    rows = calibrate_rows(inst, 3.0)
+    # each step a bounded sample, sized so that the whole run stays within
+    # about two and a half minutes whatever --steps/--warmup are
+    per_step_s = min(3.0, max(0.05, 150.0 / max(1, args.steps + args.warmup)))
+    rows, iters = calibrate(inst, per_step_s)
     for k in range(args.warmup):
-        oracle_sample(inst, rows, seed=100 + k)
+        oracle_sample(inst, rows, seed=100 + k, iters=iters)
     tot_pairs, tot_s = 0, 0.0
     for k in range(args.steps):
-        p, dt = oracle_sample(inst, rows, seed=k)
+        p, dt = oracle_sample(inst, rows, seed=k, iters=iters)
         tot_pairs += p
         tot_s += dt
     value = tot_pairs / tot_s
-    sample = (f"FP64 oracle, per step {rows} rows of each Sinkhorn update (g, f, p) of the workload, "
-              f"{orc.get_threads()} threads")
+    sample = (f"FP64 oracle, per step {iters} chained Sinkhorn iteration(s) over {rows} rows of each update "
+              f"(g, f, p) of the workload, {orc.get_threads()} threads")
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1000.0 * tot_s / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded Philox)",
             "impl": "reference",
-            "config": workload_config(w, {"sample_rows_per_update": rows}),
+            "config": workload_config(w, {"sample_rows_per_update": rows, "sample_iterations": iters}),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": orc.get_threads(), "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -271,6 +286,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     clocks.start()
     time.sleep(0.2)
+    torch.cuda.profiler.start()  # a profiler started with --profile-from-start off sees the timed steps only
     t0 = time.perf_counter()
     for k in range(args.steps):
         flush.zero_()  # L2 flush between steps (outside the step events)
@@ -278,6 +294,7 @@ def run_ours(args):
         cov.cov_solve_continue(ctx, prob, 1, u, s)
         ev1[k].record(stream)
     torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
     if world > 1:
         dist.barrier()
     wall = time.perf_counter() - t0
@@ -400,7 +417,10 @@ def run_ours(args):
                 "tiling": tiling,
                 "wall_s_timed_region": wall}),
             "roofline": {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Gpair/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak, "traffic": PAIRS_TRAFFIC_BYTES,
+                         "traffic_note": "dram read + write bytes per launch of pairs_kernel at this workload, "
+                                         "one ncu capture (profiles/pairs_kernel_sinkhorn_double_integrator_"
+                                         "T4096.md)",
                          "kernel": "pairs_kernel (Sinkhorn g/f/p soft-c-transform), per iteration of 3 launches",
                          "peak_basis": "derived: 148 SMs x 2032 MHz x min(MUFU ex2 width, 128 FP32 lanes / "
                                        f"{FP32_OPS_PER_PAIR} ops per pair)",

@@ -127,6 +127,20 @@ enum {
 };
 COV_API cov_status cov_ctx_set_option(cov_ctx* ctx, int key, long long value);
 
+/* Tile-shape autotuner of the all-pairs kernels: times the Sinkhorn
+ * iteration on these inputs (as cov_field_sinkhorn, uniform start) for each
+ * candidate (rows per thread, resident-CTA cap) in {(2,8), (4,8), (8,8),
+ * (4,6), (2,6), (8,4)} with CUDA events on `stream`, as (t(6 iterations) -
+ * t(2)) / 4 (median of 3), and applies the fastest to the context.
+ * Synchronises the stream.  best_R, best_ctas_per_sm: host outputs (may be
+ * NULL); sweep: host [6][3] (R, cap, microseconds per iteration) or NULL.
+ * Workspace as cov_field_sinkhorn. */
+COV_API cov_status cov_autotune_sinkhorn(cov_ctx* ctx, const float* x, int T,
+                                         const float* y, const float* b, int M,
+                                         int d, float eps, int* best_R,
+                                         int* best_ctas_per_sm, double* sweep,
+                                         cov_stream_t stream);
+
 /* ---- reference score ----------------------------------------------------- */
 
 /* score[i] = grad log q(x_i) for the mixture q (Eq. 4 needs only the score,

@@ -5,9 +5,10 @@ The all-pairs kernel has two knobs (C-ABI options): rows per thread R
 resident CTAs per SM that the column-split planner fills
 (COV_OPT_CTAS_PER_SM).  The best pair depends on the problem shape: small
 problems want many short CTAs, large ones more rows per thread.  `tune_*`
-times every candidate on the caller's own inputs through the C-ABI, with CUDA
-events, as the per-iteration time (t(n_hi) - t(n_lo)) / (n_hi - n_lo) so that
-prep and launch costs cancel; the winner is cached in a JSON file keyed by
+times every candidate on the caller's own inputs (for the Sinkhorn field in the
+library, cov_autotune_sinkhorn; for the Stein field here through the C-ABI),
+with CUDA events, as the per-iteration time (t(n_hi) - t(n_lo)) / (n_hi - n_lo)
+so that prep and launch costs cancel; the winner is cached in a JSON file keyed by
 GPU name, field kind, d and the power-of-two buckets of T and M, and applied
 to the context.
 
@@ -72,16 +73,11 @@ def _timed(fn, reps: int) -> float:
     return statistics.median(ts)
 
 
-def sweep_sinkhorn(ctx, x, y, eps, candidates=CANDIDATES, n_lo=2, n_hi=6, reps=3):
-    """[(R, ctas_per_sm, us per Sinkhorn iteration)] on these inputs."""
-    out = []
-    for R, cps in candidates:
-        apply(ctx, {"R": R, "ctas_per_sm": cps})
-        cov.cov_field_sinkhorn(ctx, x, y, eps, 1, field=False)
-        hi = _timed(lambda: cov.cov_field_sinkhorn(ctx, x, y, eps, n_hi, field=False), reps)
-        lo = _timed(lambda: cov.cov_field_sinkhorn(ctx, x, y, eps, n_lo, field=False), reps)
-        out.append((R, cps, 1e3 * (hi - lo) / (n_hi - n_lo)))
-    return out
+def sweep_sinkhorn(ctx, x, y, eps):
+    """[(R, ctas_per_sm, us per Sinkhorn iteration)] on these inputs: the
+    library's own sweep (cov_autotune_sinkhorn), which also applies the best."""
+    _, _, rows = cov.cov_autotune_sinkhorn(ctx, x, y, eps)
+    return rows
 
 
 def sweep_svgd(ctx, x, h, score, candidates=CANDIDATES, reps=5):

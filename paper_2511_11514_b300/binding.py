@@ -36,7 +36,7 @@ EXPORTS = (
     "cov_lqr_track", "cov_solve", "cov_solve_continue", "cov_solve_batched", "cov_workspace_size_batched",
     "cov_probe_peaks", "cov_workspace_size_vjp", "cov_field_sinkhorn_vjp", "cov_workspace_size_lqr_vjp",
     "cov_lqr_vjp", "cov_rollout_vjp", "cov_solve_checkpointed", "cov_workspace_size_backward",
-    "cov_solve_backward", "cov_field_sinkhorn_annealed", "cov_density_score",
+    "cov_solve_backward", "cov_field_sinkhorn_annealed", "cov_density_score", "cov_autotune_sinkhorn",
 )
 
 
@@ -97,6 +97,8 @@ def load(path: str = LIB_PATH):
         "cov_workspace_size_batched": (_sz, [ctypes.POINTER(cov_problem), _i]),
         "cov_probe_peaks": (_i, [_P, _i, ctypes.POINTER(_d), _P]),
         "cov_density_score": (_i, [_P, _P, _i, _i, _P, _i, _P, _P]),
+        "cov_autotune_sinkhorn": (_i, [_P, _P, _i, _P, _P, _i, _i, _f, ctypes.POINTER(_i), ctypes.POINTER(_i),
+                                       ctypes.POINTER(_d), _P]),
         "cov_field_sinkhorn_annealed": (_i, [_P, _P, _i, _P, _P, _i, _i, _f, _i, _f, _f, _i, _P, _P, _P, _P, _P]),
         "cov_workspace_size_vjp": (_sz, [_i, _i, _i, _i]),
         "cov_field_sinkhorn_vjp": (_i, [_P, _P, _i, _P, _P, _i, _i, _f, _i, _P, _P, _P, _P, _P]),
@@ -207,6 +209,22 @@ def _gmm_struct(gmm, d):
     g = cov_gmm(K=int(w.size), d=int(d), w=w.ctypes.data_as(_P), mu=mu.ctypes.data_as(_P),
                 sigma=sigma.ctypes.data_as(_P))
     return g, (w, mu, sigma)
+
+
+def cov_autotune_sinkhorn(ctx: Context, x, y, eps, b=None, stream=None):
+    """Sweep the tile shapes on these inputs (C side), apply the fastest;
+    returns (R, ctas_per_sm, [(R, cap, us per iteration), ...])."""
+    T, d = x.shape
+    M = y.shape[0]
+    ctx.reserve_for(T, M, d)
+    bR, bC = ctypes.c_int(0), ctypes.c_int(0)
+    sw = (ctypes.c_double * 18)()
+    st = load().cov_autotune_sinkhorn(ctx.h, _ptr(x, torch.float32, name="x"), T, _ptr(y, torch.float32, (M, d), "y"),
+                                      _ptr(b, torch.float32, (M,), "b"), M, d, float(eps), ctypes.byref(bR),
+                                      ctypes.byref(bC), sw, _stream(stream))
+    ctx._check(st, "cov_autotune_sinkhorn")
+    rows = [(int(sw[3 * k]), int(sw[3 * k + 1]), float(sw[3 * k + 2])) for k in range(6)]
+    return bR.value, bC.value, rows
 
 
 def cov_density_score(ctx: Context, density, x, out=None, stream=None):

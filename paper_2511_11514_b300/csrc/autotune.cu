@@ -1,0 +1,91 @@
+// autotune.cu -- tile-shape sweep of the all-pairs kernels through the
+// library's own calls: rows per lane R and the resident-CTA cap are timed
+// on the caller's inputs with CUDA events on the caller's stream, as the
+// per-iteration cost (t(6 iterations) - t(2 iterations)) / 4 so that the
+// prep and gradient launches cancel, and the fastest pair is applied to the
+// context.
+#include <math.h>
+
+#include <algorithm>
+
+#include "cov_device.cuh"
+#include "cov_internal.h"
+
+namespace {
+
+struct Candidate {
+    int R, cps;
+};
+constexpr Candidate kCandidates[] = {{2, 8}, {4, 8}, {8, 8}, {4, 6}, {2, 6}, {8, 4}};
+constexpr int kNumCandidates = sizeof(kCandidates) / sizeof(kCandidates[0]);
+
+}  // namespace
+
+extern "C" cov_status cov_autotune_sinkhorn(cov_ctx* ctx, const float* x, int T, const float* y, const float* b,
+                                            int M, int d, float eps, int* best_R, int* best_ctas_per_sm,
+                                            double* sweep, cov_stream_t stream) {
+    if (!ctx || !x || !y || T < 1 || M < 1 || d < 1 || d > COV_MAX_D || !(eps > 0.f)) return COV_ERR_INVALID_ARG;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return COV_ERR_CUDA;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int R0 = ctx->rows_per_thread, c0 = ctx->ctas_per_sm;
+    cudaEvent_t e0, e1;
+    if (cov::cuda_failed(ctx, cudaEventCreate(&e0))) return COV_ERR_CUDA;
+    if (cov::cuda_failed(ctx, cudaEventCreate(&e1))) {
+        cudaEventDestroy(e0);
+        return COV_ERR_CUDA;
+    }
+    cov::clobber_ws_caches(ctx);
+    cov_status r = COV_OK;
+    double best = 1e300;
+    int bR = R0, bC = c0;
+    auto run = [&](int n) {
+        return cov::sinkhorn_field_ws(ctx, ctx->ws, ctx->ws_bytes, x, d, T, y, b, M, d, eps, n, 0, nullptr, nullptr,
+                                      nullptr, nullptr, st);
+    };
+    auto timed = [&](int n, float* ms) -> cov_status {
+        if (cov::cuda_failed(ctx, cudaEventRecord(e0, st))) return COV_ERR_CUDA;
+        const cov_status q = run(n);
+        if (q != COV_OK) return q;
+        if (cov::cuda_failed(ctx, cudaEventRecord(e1, st)) || cov::cuda_failed(ctx, cudaEventSynchronize(e1)) ||
+            cov::cuda_failed(ctx, cudaEventElapsedTime(ms, e0, e1)))
+            return COV_ERR_CUDA;
+        return COV_OK;
+    };
+    for (int k = 0; k < kNumCandidates && r == COV_OK; ++k) {
+        const Candidate c = kCandidates[k];
+        ctx->rows_per_thread = c.R;  // the planner maps R to the built shapes for this d
+        ctx->ctas_per_sm = c.cps;
+        r = run(1);
+        float lo[3], hi[3];
+        for (int rep = 0; rep < 3 && r == COV_OK; ++rep) {
+            r = timed(2, &lo[rep]);
+            if (r == COV_OK) r = timed(6, &hi[rep]);
+        }
+        if (r != COV_OK) break;
+        std::sort(lo, lo + 3);
+        std::sort(hi, hi + 3);
+        const double us = 1e3 * (hi[1] - lo[1]) / 4.0;
+        if (sweep) {
+            sweep[3 * k] = c.R;
+            sweep[3 * k + 1] = c.cps;
+            sweep[3 * k + 2] = us;
+        }
+        if (us < best) {
+            best = us;
+            bR = c.R;
+            bC = c.cps;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (r != COV_OK) {
+        ctx->rows_per_thread = R0;
+        ctx->ctas_per_sm = c0;
+        return r;
+    }
+    cov_ctx_set_option(ctx, COV_OPT_ROWS_PER_THREAD, bR);  // also drops graphs planned with other shapes
+    cov_ctx_set_option(ctx, COV_OPT_CTAS_PER_SM, bC);
+    if (best_R) *best_R = bR;
+    if (best_ctas_per_sm) *best_ctas_per_sm = bC;
+    return COV_OK;
+}

@@ -81,3 +81,27 @@ def test_ragged_and_degenerate_sizes(cov, ctx, orc):
     xs = np.tile([[0.25, 0.75]], (17, 1))
     a, f, g, p = cov.cov_field_sinkhorn(ctx, dev32(xs), dev32(np.array([[0.5, 0.25]])), 0.01, 3)
     np.testing.assert_allclose(host(a), np.tile(2 * (np.array([0.5, 0.25]) - [0.25, 0.75]), (17, 1)), rtol=1e-5)
+
+
+def test_autotuner_sweeps_and_applies_a_tile_shape(cov, orc, tmp_path):
+    """cov_autotune_sinkhorn times every candidate, applies the fastest, and
+    the field computed with the tuned shape still matches the oracle; the
+    Python cache round-trips the choice."""
+    from paper_2511_11514_b300 import autotune
+    T, M, eps = 2048, 4096, 0.01
+    x = wl.random_points(T, 2, seed=901)
+    y = wl.random_points(M, 2, seed=902)
+    ctx = cov.Context(0)
+    try:
+        R, cps, rows = cov.cov_autotune_sinkhorn(ctx, dev32(x), dev32(y), eps)
+        assert (R, cps) in [(r[0], r[1]) for r in rows]
+        assert all(r[2] > 0 for r in rows)
+        assert min(rows, key=lambda r: r[2])[:2] == (R, cps)
+        a, f, g, p = cov.cov_field_sinkhorn(ctx, dev32(x), dev32(y), eps, 5)
+        fo, go, po = orc.sinkhorn(x, y, None, eps, 5)
+        assert np.abs(host(f) - fo).max() / eps <= 1e-4
+        ch = autotune.tune_sinkhorn(ctx, dev32(x), dev32(y), eps, cache_path=str(tmp_path / "c.json"))
+        ch2 = autotune.tune_sinkhorn(ctx, dev32(x), dev32(y), eps, cache_path=str(tmp_path / "c.json"))
+        assert (ch["R"], ch["ctas_per_sm"]) == (ch2["R"], ch2["ctas_per_sm"])
+    finally:
+        ctx.close()
