@@ -418,9 +418,8 @@ def run_ours(args):
                 "wall_s_timed_region": wall}),
             "roofline": {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Gpair/s",
                          "frac": achieved / peak, "traffic": PAIRS_TRAFFIC_BYTES,
-                         "traffic_note": "dram read + write bytes per launch of pairs_kernel at this workload, "
-                                         "one ncu capture (profiles/pairs_kernel_sinkhorn_double_integrator_"
-                                         "T4096.md)",
+                         "traffic_note": "dram__bytes_read.sum + dram__bytes_write.sum per launch of "
+                                         "pairs_kernel at this workload, one ncu capture of the current kernel",
                          "kernel": "pairs_kernel (Sinkhorn g/f/p soft-c-transform), per iteration of 3 launches",
                          "peak_basis": "derived: 148 SMs x 2032 MHz x min(MUFU ex2 width, 128 FP32 lanes / "
                                        f"{FP32_OPS_PER_PAIR} ops per pair)",
