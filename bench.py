@@ -83,6 +83,22 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
 
 
+def max_over_ranks(value, world, device="cpu"):
+    """The largest `value` over all ranks (the job's time is its slowest rank's)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world, pairs_per_step, steps, max_total_ms):
+    """Whole-job pair evaluations per second: every rank solves its own
+    problem of the same size (weak scaling), timed by the slowest rank."""
+    return world * pairs_per_step * steps / (max_total_ms * 1e-3)
+
+
 # -- clocks sampled during the timed region ------------------------------------
 class Clocks:
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
@@ -300,15 +316,12 @@ def run_ours(args):
     wall = time.perf_counter() - t0
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
-    total_ms = torch.tensor([sum(step_ms)], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(total_ms, op=dist.ReduceOp.MAX)
-    total_ms = float(total_ms.item())
+    total_ms = max_over_ranks(sum(step_ms), world, dev)
     st, flags = ctx.device_status()
     if st != cov.COV_OK:
         raise SystemExit(f"device status {cov.status_string(st)} flags {flags}")
     pairs_step = w.pairs_per_field
-    value = world * pairs_step * args.steps / (total_ms * 1e-3)
+    value = job_value(world, pairs_step, args.steps, total_ms)
     ms_per_step = total_ms / args.steps
 
     # ---- roofline of the dominant kernel (the all-pairs soft-c-transform) -------
