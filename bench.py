@@ -627,7 +627,7 @@ def run_adjoint(args):
     fwd_it = per_iter_ms(lambda n: cov.cov_field_sinkhorn(lctx, xr, yr, w.eps, n, b=br, field=False))
     rev_ms = max(vjp_it - fwd_it, 1e-9)
     rev_pairs = 2 * w.T * w.M + w.T * w.T
-    adj_peak = SM_COUNT_NOMINAL * SM_MAX_MHZ_NOMINAL * 1e6 * FP32_LANES_PER_SM_CLK / 7
+    adj_peak = SM_COUNT_NOMINAL * SM_MAX_MHZ_NOMINAL * 1e6 * FP32_LANES_PER_SM_CLK / 6
     achieved = rev_pairs / (rev_ms * 1e-3)
     # the same at a size where a launch is long enough to reach steady state
     TL, ML = 16384, 65536
@@ -650,8 +650,9 @@ def run_adjoint(args):
             "ms_forward": f_ms, "ms_backward": b_ms,
             "roofline": {"bound": "alu", "kernel": "adj_kernel (reverse column sums)", "achieved": achieved,
                          "peak": adj_peak, "unit": "pair-evals/s", "frac": achieved / adj_peak, "traffic": None,
-                         "peak_basis": "148 SMs x 2032 MHz x 128 FP32 lanes / 7 FP32 ops per pair "
-                                       "(derived from unit counts and clocks; ex2 at 32/clk/SM is not binding)",
+                         "peak_basis": "148 SMs x 2032 MHz x 128 FP32 lanes / 6 FP32 ops per pair (add of the "
+                                       "row term, 2 FMA exponent, 3 FMA accumulation; derived from unit counts and "
+                                       "clocks; ex2 at 32/clk/SM is not binding)",
                          "how": "(field VJP - forward) per Sinkhorn iteration, (t(50) - t(10)) / 40, "
                                 "2TM + T^2 pairs per reverse iteration"},
             "ms_per_sinkhorn_iteration": {"forward": fwd_it, "field_vjp": vjp_it, "reverse": rev_ms},

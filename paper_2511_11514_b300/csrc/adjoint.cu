@@ -12,6 +12,7 @@
 // without a running maximum (the exponent never exceeds 0 beyond rounding).
 // With the adjoints in natural units (fbar = dL/df etc.) the reverse
 // iteration t = n..1 is
+// (V is staged pre-multiplied, so a pair costs the exponent and 1 + d FMAs)
 //   f-step (rows j over columns i, V_i = fbar_i [1, xhat_i]):
 //     gbar_j = -W_j,  lbbar_j -= eps W_j,
 //     ybar_j += 2 sigma (yhat_j W_j - X_j) - 2 sigma gbar_j Dg^t_j
@@ -53,7 +54,7 @@ template <int D, int KIND>
 struct AdjTraits;
 template <int D>
 struct AdjTraits<D, A_COL> {
-    static constexpr int R = 4, NC = D + 2, NACC = D + 1;
+    static constexpr int R = 4, NC = 2 * D + 2, NACC = D + 1;
 };
 template <int D>
 struct AdjTraits<D, A_MOM> {
@@ -73,7 +74,8 @@ struct AdjArgs {
     const float* rb;
     float ca, cb, c0;
     // columns: coordinates [D][col_ld], exponent term cbeta [col_ld];
-    //   A_COL: weight cw [col_ld];  A_FCOL: cw = A [D][col_ld], cgam = Gamma [col_ld]
+    //   A_COL: cw = V [D+1][col_ld], the weight w and its moments w xhat;
+    //   A_FCOL: cw = A [D][col_ld], cgam = Gamma [col_ld]
     const float* cols;
     const float* cbeta;
     const float* cw;
@@ -119,6 +121,14 @@ __device__ __forceinline__ constexpr int sym_idx(int k, int l) {
 
 constexpr float kTwoLn2 = 1.3862943611198906f;
 
+// The staged column values of the next reverse pass: V = w [1, xhat].
+template <int D>
+__device__ __forceinline__ void write_v(float* V, size_t ld, int i, float w, const float* xh) {
+    V[i] = w;
+#pragma unroll
+    for (int k = 0; k < D; ++k) V[(1 + k) * ld + i] = w * xh[k];
+}
+
 template <int D, int KIND>
 __device__ void adj_epilogue(const AdjArgs& a, int i, const float* acc) {
     if (i >= a.n_rows) return;
@@ -141,7 +151,7 @@ __device__ void adj_epilogue(const AdjArgs& a, int i, const float* acc) {
             const float l = a.lbbar[i] - a.eps * W;
             a.lbbar[i] = l;
             ok &= finitef(l);
-            a.w_out[i] = gb;
+            write_v<D>(a.w_out, ld, i, gb, xh);
             a.beta_out[i] = a.h0[i] - a.h1[i];
         } else if (a.epi == E_GREV) {
             const float fb = -W;
@@ -152,9 +162,9 @@ __device__ void adj_epilogue(const AdjArgs& a, int i, const float* acc) {
                 a.xbar[k * ld + i] = v;
                 ok &= finitef(v);
             }
-            if (a.w_out) a.w_out[i] = fb;
+            if (a.w_out) write_v<D>(a.w_out, ld, i, fb, xh);
         } else {  // E_PREV
-            const float pt = 2.0f * a.w_in[i];
+            const float pt = 2.0f * a.w_in[i];  // row 0 of the staged V: pbar^t / 2
             const float pm = 0.5f * pt - W;
 #pragma unroll
             for (int k = 0; k < D; ++k) {
@@ -164,7 +174,7 @@ __device__ void adj_epilogue(const AdjArgs& a, int i, const float* acc) {
                 ok &= finitef(v);
             }
             if (a.w_out) {
-                a.w_out[i] = 0.5f * pm;
+                write_v<D>(a.w_out, ld, i, 0.5f * pm, xh);
                 a.beta_out[i] = 2.0f * a.h0[i] - a.log2a - a.h1[i];
             }
         }
@@ -209,7 +219,7 @@ __device__ void adj_epilogue(const AdjArgs& a, int i, const float* acc) {
             const float l = a.lbbar[i] + a.sig * W1;
             a.lbbar[i] = l;
             ok &= finitef(l);
-            a.w_out[i] = gb;
+            write_v<D>(a.w_out, ld, i, gb, xh);
             a.beta_out[i] = a.h0[i] - a.h1[i];
         } else {  // E_FCOL_SELF
 #pragma unroll
@@ -219,7 +229,7 @@ __device__ void adj_epilogue(const AdjArgs& a, int i, const float* acc) {
                 ok &= finitef(v);
             }
             if (a.w_out) {
-                a.w_out[i] = 0.5f * a.sig * W1 / a.eps;
+                write_v<D>(a.w_out, ld, i, 0.5f * a.sig * W1 / a.eps, xh);
                 a.beta_out[i] = 2.0f * a.h0[i] - a.log2a - a.h1[i];
             }
         }
@@ -257,11 +267,10 @@ __device__ __forceinline__ void adj_chunk(const float* __restrict__ st, int j, c
         }
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            if constexpr (KIND == A_COL) {
-                const float2 ew = mul2(e[q], make_float2(c[D + 1][2 * q], c[D + 1][2 * q + 1]));
-                acc[r][0] = add2(acc[r][0], ew);
+            if constexpr (KIND == A_COL) {  // staged [D coords][beta][V: w, w xhat]
 #pragma unroll
-                for (int k = 0; k < D; ++k) acc[r][1 + k] = fma2(ew, make_float2(c[k][2 * q], c[k][2 * q + 1]), acc[r][1 + k]);
+                for (int k = 0; k <= D; ++k)
+                    acc[r][k] = fma2(e[q], make_float2(c[D + 1 + k][2 * q], c[D + 1 + k][2 * q + 1]), acc[r][k]);
             } else if constexpr (KIND == A_MOM) {
                 float2 dk[D], ek[D];
                 acc[r][0] = add2(acc[r][0], e[q]);
@@ -355,7 +364,9 @@ __global__ void __launch_bounds__(kAThreads) adj_kernel(const __grid_constant__ 
         const unsigned bytes = (unsigned)min(kATile, c1 - tc) * 4u;
         bulk_g2s(&sm[stg][D * kATile], a.cbeta + tc, bytes, &bar[stg]);
         if constexpr (KIND == A_COL) {
-            bulk_g2s(&sm[stg][(D + 1) * kATile], a.cw + tc, bytes, &bar[stg]);
+#pragma unroll
+            for (int k = 0; k <= D; ++k)
+                bulk_g2s(&sm[stg][(D + 1 + k) * kATile], a.cw + (size_t)k * a.col_ld + tc, bytes, &bar[stg]);
         } else if constexpr (KIND == A_FCOL) {
 #pragma unroll
             for (int k = 0; k < D; ++k)
@@ -569,9 +580,9 @@ struct VjpBufs {
     float *xbar, *xbarp;   // [d][Tp]: x adjoint of the cross/g-f chain and of the self/p chain
     float* ybar;           // [d][Mp]
     float* lbbar;          // [Mp]: d/d log b (normalised)
-    float *gw, *gbeta;     // [Mp]: g-step column weights and exponent terms
-    float* fw;             // [Tp]: f-step column weights (fbar)
-    float *pw[2], *pbeta[2];  // [Tp]: p-step column weights (pbar/2) and terms, ping-pong
+    float *gw, *gbeta;     // g-step columns: V = gbar [1, yhat] [d+1][Mp], exponent terms [Mp]
+    float* fw;             // f-step columns: V = fbar [1, xhat] [d+1][Tp]
+    float *pw[2], *pbeta[2];  // p-step columns: V = pbar/2 [1, xhat] [d+1][Tp], terms [Tp]; ping-pong
     float *gam_c, *gam_s, *sbeta;  // [Tp]
     float* part;
     unsigned* counters;    // [2][cnt_ld]
@@ -586,11 +597,11 @@ static VjpBufs carve_vjp(Carver& cv, int d, int Tp, int Mp) {
     v.xbarp = cv.take<float>((size_t)d * Tp);
     v.ybar = cv.take<float>((size_t)d * Mp);
     v.lbbar = cv.take<float>(Mp);
-    v.gw = cv.take<float>(Mp);
+    v.gw = cv.take<float>((size_t)(d + 1) * Mp);
     v.gbeta = cv.take<float>(Mp);
-    v.fw = cv.take<float>(Tp);
+    v.fw = cv.take<float>((size_t)(d + 1) * Tp);
     for (int q = 0; q < 2; ++q) {
-        v.pw[q] = cv.take<float>(Tp);
+        v.pw[q] = cv.take<float>((size_t)(d + 1) * Tp);
         v.pbeta[q] = cv.take<float>(Tp);
     }
     v.gam_c = cv.take<float>(Tp);
@@ -617,9 +628,11 @@ __global__ void vjp_init_kernel(const float* __restrict__ abar, int abar_ld, int
             v.xbarp[(size_t)k * Tp + i] = 0.f;
         }
         if (!ok) raise_status(status, kDevNonfinite);
-        v.fw[i] = 0.f;
-        v.pw[0][i] = 0.f;
-        v.pw[1][i] = 0.f;
+        for (int k = 0; k <= d; ++k) {
+            v.fw[(size_t)k * Tp + i] = 0.f;
+            v.pw[0][(size_t)k * Tp + i] = 0.f;
+            v.pw[1][(size_t)k * Tp + i] = 0.f;
+        }
         v.pbeta[0][i] = kPadH;
         v.pbeta[1][i] = kPadH;
         v.gam_c[i] = 0.f;
@@ -629,7 +642,7 @@ __global__ void vjp_init_kernel(const float* __restrict__ abar, int abar_ld, int
     if (i < Mp) {
         for (int k = 0; k < d; ++k) v.ybar[(size_t)k * Mp + i] = 0.f;
         v.lbbar[i] = 0.f;
-        v.gw[i] = 0.f;
+        for (int k = 0; k <= d; ++k) v.gw[(size_t)k * Mp + i] = 0.f;
         v.gbeta[i] = kPadH;
     }
     if (i < 2 * v.cnt_ld) v.counters[i] = 0u;
