@@ -36,7 +36,19 @@ namespace cov {
 // M_GW: a log-sum-exp update (epilogue as M_G) that also writes the
 // barycentric offset sum_j pi_ij (c_j - r_i) of its own softmax (the forward
 // record the adjoint needs).
-enum PairMode { M_G = 0, M_F = 1, M_P = 2, M_WY = 3, M_WX = 4, M_SVGD = 5, M_GW = 6, M_COUNT = 7 };
+// M_GO: the same update as M_G with a FIXED per-row offset instead of a
+// running maximum: the previous iteration's log-sum-exp of the row, o_i,
+// which the new one differs from by little once the iteration has started,
+//   LSE2_j(w_ij) = o_i + log2 sum_j 2^(w_ij - o_i)   (exact for any o_i).
+// That drops the per-chunk maximum, compare and warp vote from the inner
+// loop.  Guards: a CTA whose partial sum overflowed (> 2^100) redoes its
+// columns with the running maximum; a row whose merged sum is tiny
+// (< 2^-60, so terms may have flushed to zero) is recomputed over all
+// columns with the running maximum by the merging CTA.
+enum PairMode { M_G = 0, M_F = 1, M_P = 2, M_WY = 3, M_WX = 4, M_SVGD = 5, M_GW = 6, M_GO = 7, M_COUNT = 8 };
+
+constexpr float kOffsetHi = 1.2676506e30f;   // 2^100
+constexpr float kOffsetLo = 8.6736174e-19f;  // 2^-60
 
 constexpr int kTile = 256;   // columns per staged tile
 constexpr int kWarps = 4;    // warps per CTA, each takes a quarter of a tile
@@ -64,6 +76,12 @@ struct PairArgs {
     float* out_h;
     const float* in_h;
     float log2a;
+    // M_GO: row offset o_i = oca oa[i] + ocb ob[i] + oc0 (ob may be null);
+    // fixed == 0 runs this segment with the running maximum instead
+    const float* oa;
+    const float* ob;
+    float oca, ocb, oc0;
+    int fixed;
     float* bary;         // [D][row_ld]
     float* a_out;        // [n_rows][D]
     float a_scale;
@@ -75,6 +93,7 @@ template <int D, int MODE>
 struct PairTraits {
     static constexpr bool kW = (MODE == M_WY || MODE == M_WX || MODE == M_GW);
     static constexpr bool kSV = (MODE == M_SVGD);
+    static constexpr bool kO = (MODE == M_GO);
     static constexpr int NC = kSV ? 2 * D : D + 1;             // staged components per column
     static constexpr int NACC = kSV ? D : (kW ? 2 + D : 2);    // partial components per row
 };
@@ -129,7 +148,30 @@ __device__ __forceinline__ void tile_compute(const float* __restrict__ st, int j
                 }
             }
         }
-        if constexpr (!TR::kSV) {
+        if constexpr (TR::kO) {
+            // fixed offset (held in m): 2^(w - o), no maximum
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                float2 w[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) w[q] = make_float2(c[D][2 * q], c[D][2 * q + 1]);
+#pragma unroll
+                for (int k = 0; k < D; ++k) {
+                    const float2 xk = make_float2(X[r][k], X[r][k]);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) w[q] = fma2(xk, make_float2(c[k][2 * q], c[k][2 * q + 1]), w[q]);
+                }
+                const float2 oo = make_float2(ra[r].m, ra[r].m);
+                float2 e[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const float2 dd = sub2(w[q], oo);
+                    e[q] = make_float2(ex2(dd.x), ex2(dd.y));
+                }
+                ra[r].s = add2(ra[r].s, add2(add2(e[0], e[1]), add2(e[2], e[3])));
+            }
+        }
+        if constexpr (!TR::kSV && !TR::kO) {
             // exponents of this chunk for all R rows, and each row's new running max
             float2 w[R][4];
             float mn[R];
@@ -311,24 +353,34 @@ __global__ void __launch_bounds__(kThreads) pairs_kernel(const __grid_constant__
         for (int k = 0; k < D; ++k) ra[r].acc[k] = make_float2(0.f, 0.f);
     }
 
+    const bool fixed = TR::kO && a.fixed;
+    if (fixed) {
+        // the fixed offsets: the previous iteration's log-sum-exp of each row
+        // (written two launches ago, so readable before the dependency wait)
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int i = row0 + r * 32 + lane;
+            ra[r].m = a.oca * a.oa[i] + (a.ob ? a.ocb * a.ob[i] : 0.f) + a.oc0;
+        }
+    }
+
     const int c0 = sp * a.cols_per_split;
     const int c1 = min(c0 + a.cols_per_split, a.n_cols8);
-    const int n_tiles = c1 > c0 ? (c1 - c0 + kTile - 1) / kTile : 0;
     __syncthreads();
 
     // A tile is the column coordinates (constant over the Sinkhorn loop) and
     // the per-column term h (written by the previous launch).
-    auto issue_coords = [&](int t, int stg) {
-        const int tc = c0 + t * kTile;
-        const int nc = min(kTile, c1 - tc);
+    auto issue_coords = [&](int cb, int ce, int t, int stg) {
+        const int tc = cb + t * kTile;
+        const int nc = min(kTile, ce - tc);
         const unsigned bytes = (unsigned)nc * 4u;
         mbar_arrive_expect_tx(&bar[stg], bytes * NC);
 #pragma unroll
         for (int k = 0; k < D; ++k) bulk_g2s(&sm[stg][k * kTile], a.cols + (size_t)k * a.col_ld + tc, bytes, &bar[stg]);
     };
-    auto issue_h = [&](int t, int stg) {
-        const int tc = c0 + t * kTile;
-        const int nc = min(kTile, c1 - tc);
+    auto issue_h = [&](int cb, int ce, int t, int stg) {
+        const int tc = cb + t * kTile;
+        const int nc = min(kTile, ce - tc);
         const unsigned bytes = (unsigned)nc * 4u;
         if constexpr (TR::kSV) {
 #pragma unroll
@@ -338,42 +390,153 @@ __global__ void __launch_bounds__(kThreads) pairs_kernel(const __grid_constant__
             bulk_g2s(&sm[stg][D * kTile], a.colh + tc, bytes, &bar[stg]);
         }
     };
-    auto issue = [&](int t, int stg) {
-        issue_coords(t, stg);
-        issue_h(t, stg);
-    };
 
-    if (threadIdx.x == 0 && n_tiles > 0) issue_coords(0, 0);
-    if (a.pre_ok) grid_dep_wait();
-    grid_dep_launch();
-    if (threadIdx.x == 0 && n_tiles > 0) issue_h(0, 0);
-    int bad_tile = -1;
-    for (int t = 0; t < n_tiles; ++t) {
-        const int stg = t & 1;
-        if (threadIdx.x == 0 && t + 1 < n_tiles) issue(t + 1, stg ^ 1);
-        const bool ok = mbar_wait_bounded(&bar[stg], (unsigned)((t >> 1) & 1), a.spin_limit);
-        if (__syncthreads_or(!ok)) {
-            bad_tile = t;
-            break;
+    // One pass over the columns [cb, ce).  Tiles alternate between the two
+    // stages by a running count over all passes (which also gives each
+    // mbarrier's phase parity).  The first pass overlaps its first column
+    // copies with the previous launch (programmatic dependent launch).
+    int gtile = 0;
+    bool timed_out = false;
+    auto run_pass = [&](int cb, int ce, bool first, bool fixed) {
+        const int nt = ce > cb ? (ce - cb + kTile - 1) / kTile : 0;
+        if (first) {
+            if (threadIdx.x == 0 && nt > 0) issue_coords(cb, ce, 0, gtile & 1);
+            if (a.pre_ok) grid_dep_wait();
+            grid_dep_launch();
+            if (threadIdx.x == 0 && nt > 0) issue_h(cb, ce, 0, gtile & 1);
+        } else if (threadIdx.x == 0 && nt > 0) {
+            issue_coords(cb, ce, 0, gtile & 1);
+            issue_h(cb, ce, 0, gtile & 1);
         }
-        const int nc = min(kTile, c1 - (c0 + t * kTile));
-        const int per = ((nc / 8 + kWarps - 1) / kWarps) * 8;
-        const int jb = min(nc, warp * per), je = min(nc, jb + per);
-        tile_compute<D, R, MODE>(sm[stg], jb, je, X, Xr, ra);
-        __syncthreads();
-    }
-    if (bad_tile >= 0) {
-        // A tile never arrived: record it, drain the copies still in flight
-        // (bounded) so no bulk copy lands after the CTA exits, and fall
-        // through with whatever was accumulated (the status marks it invalid).
-        if (threadIdx.x == 0) {
-            raise_status(a.status, kDevTimeout);
-            const long long drain = a.spin_limit > (1LL << 20) ? a.spin_limit : (1LL << 20);
-            mbar_wait_bounded(&bar[bad_tile & 1], (unsigned)((bad_tile >> 1) & 1), drain);
-            if (bad_tile + 1 < n_tiles)
-                mbar_wait_bounded(&bar[(bad_tile + 1) & 1], (unsigned)(((bad_tile + 1) >> 1) & 1), drain);
+        int bad_tile = -1;
+        for (int t = 0; t < nt; ++t) {
+            const int g = gtile + t, stg = g & 1;
+            if (threadIdx.x == 0 && t + 1 < nt) {
+                issue_coords(cb, ce, t + 1, stg ^ 1);
+                issue_h(cb, ce, t + 1, stg ^ 1);
+            }
+            const bool ok = mbar_wait_bounded(&bar[stg], (unsigned)((g >> 1) & 1), a.spin_limit);
+            if (__syncthreads_or(!ok)) {
+                bad_tile = t;
+                break;
+            }
+            const int nc = min(kTile, ce - (cb + t * kTile));
+            const int per = ((nc / 8 + kWarps - 1) / kWarps) * 8;
+            const int jb = min(nc, warp * per), je = min(nc, jb + per);
+            if constexpr (TR::kO) {
+                if (fixed)
+                    tile_compute<D, R, M_GO>(sm[stg], jb, je, X, Xr, ra);
+                else
+                    tile_compute<D, R, M_G>(sm[stg], jb, je, X, Xr, ra);
+            } else {
+                tile_compute<D, R, MODE>(sm[stg], jb, je, X, Xr, ra);
+            }
+            __syncthreads();
         }
-        __syncthreads();
+        if (bad_tile >= 0) {
+            // A tile never arrived: record it, drain the copies still in
+            // flight (bounded) so no bulk copy lands after the CTA exits, and
+            // fall through with whatever was accumulated (the status marks it
+            // invalid); no further pass runs.
+            if (threadIdx.x == 0) {
+                raise_status(a.status, kDevTimeout);
+                const long long drain = a.spin_limit > (1LL << 20) ? a.spin_limit : (1LL << 20);
+                const int g = gtile + bad_tile;
+                mbar_wait_bounded(&bar[g & 1], (unsigned)((g >> 1) & 1), drain);
+                if (bad_tile + 1 < nt) mbar_wait_bounded(&bar[(g + 1) & 1], (unsigned)(((g + 1) >> 1) & 1), drain);
+            }
+            timed_out = true;
+            __syncthreads();
+        }
+        gtile += nt;
+    };
+    run_pass(c0, c1, true, fixed);
+
+    if constexpr (TR::kO) {
+        __shared__ float fin_m[RB], fin_s[RB];
+        auto reset_rows = [&]() {
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                ra[r].m = kNegBig;
+                ra[r].s = make_float2(0.f, 0.f);
+            }
+        };
+        // a partial that overflowed: redo this CTA's columns with the running maximum
+        bool over = false;
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+            if (fixed && row0 + r * 32 + lane < a.n_rows) over |= !(ra[r].s.x + ra[r].s.y <= kOffsetHi);
+        if (__syncthreads_or(over) && !timed_out) {
+            reset_rows();
+            run_pass(c0, c1, false, false);
+        }
+        // the 4 warps' (m, s) of each row -> fin
+        auto reduce_warps = [&]() {
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                red[warp][0][r * 32 + lane] = ra[r].m;
+                red[warp][1][r * 32 + lane] = ra[r].s.x + ra[r].s.y;
+            }
+            __syncthreads();
+            for (int q = threadIdx.x; q < RB; q += kThreads) {
+                float m = red[0][0][q], sv = red[0][1][q];
+#pragma unroll
+                for (int w = 1; w < kWarps; ++w) merge_into<D, MODE>(m, sv, nullptr, red[w][0][q], red[w][1][q], nullptr);
+                fin_m[q] = m;
+                fin_s[q] = sv;
+            }
+            __syncthreads();
+        };
+        reduce_warps();
+        if (a.splits > 1) {
+            const size_t cs = (size_t)a.splits * a.part_ld;
+            for (int q = threadIdx.x; q < RB; q += kThreads) {
+                float* P = a.part + (size_t)sp * a.part_ld + row0 + q;
+                P[0] = fin_m[q];
+                P[cs] = fin_s[q];
+            }
+            __threadfence();
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                const unsigned prev = atomicAdd(&a.counters[rb], 1u);
+                s_last = (prev == (unsigned)(a.splits - 1));
+            }
+            __syncthreads();
+            if (!s_last) return;
+            __threadfence();
+            for (int q = threadIdx.x; q < RB; q += kThreads) {
+                const int i = row0 + q;
+                float m = kNegBig, sv = 0.f;
+                for (int p0 = 0; p0 < a.splits; p0 += 8) {
+                    float m2[8], s2[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const bool live = p0 + u < a.splits;
+                        const float* P = a.part + (size_t)(live ? p0 + u : 0) * a.part_ld + i;
+                        m2[u] = live ? ld_cg(P) : kNegBig;
+                        s2[u] = live ? ld_cg(P + cs) : 0.f;
+                    }
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) merge_into<D, MODE>(m, sv, nullptr, m2[u], s2[u], nullptr);
+                }
+                fin_m[q] = m;
+                fin_s[q] = sv;
+            }
+            __syncthreads();
+        }
+        // a row whose sum is tiny may have lost terms to underflow: recompute
+        // the whole row block over all columns with the running maximum
+        bool tiny = false;
+        for (int q = threadIdx.x; q < RB; q += kThreads)
+            if (fixed && row0 + q < a.n_rows) tiny |= !(fin_s[q] >= kOffsetLo);
+        if (__syncthreads_or(tiny) && !timed_out) {
+            reset_rows();
+            run_pass(0, a.n_cols8, false, false);
+            reduce_warps();
+        }
+        for (int q = threadIdx.x; q < RB; q += kThreads) epilogue<D, MODE>(a, row0 + q, fin_m[q], fin_s[q], nullptr);
+        if (a.splits > 1 && threadIdx.x == 0) a.counters[rb] = 0u;  // ready for the next launch
+        return;
     }
 
     // ---- reduce the 4 warps' partials of each row in shared memory ----------
@@ -736,6 +899,7 @@ static cudaError_t launch_pairs_mode(int family, const PairLaunch& L, int n, cud
         case M_WX: return launch_pairs_t<D, R, M_WX>(L, n, st, occ);
         case M_SVGD: return launch_pairs_t<D, R, M_SVGD>(L, n, st, occ);
         case M_GW: return launch_pairs_t<D, R, M_GW>(L, n, st, occ);
+        case M_GO: return launch_pairs_t<D, R, M_GO>(L, n, st, occ);
     }
     return cudaErrorInvalidValue;
 }
@@ -910,30 +1074,55 @@ cov_status sinkhorn_field_ws(cov_ctx* ctx, void* ws, size_t ws_bytes, const floa
         eps_cur = e_new;
         first = true;
     };
+    int stable = 0;            // iterations run at the current eps
+    bool warm_origin = warm;   // the warm-start potentials are still at the current eps
     for (int it = 0; it < n_iter && r == COV_OK; ++it) {
-        if (scaled) to_eps(anneal_eps(eps, eps_start, eps_decay, it));
+        if (scaled) {
+            const double e_it = anneal_eps(eps, eps_start, eps_decay, it);
+            if (e_it != eps_cur) {
+                stable = 0;
+                warm_origin = false;
+            }
+            to_eps(e_it);
+        }
+        // An update runs with the previous log-sum-exp of its rows as a fixed
+        // offset (M_GO) once that value exists at the current eps: for g and
+        // f from the third iteration on (or at once from warm-start
+        // potentials); for p, which needs the two previous self potentials,
+        // from the third iteration on (the second, from a warm start).
+        const bool gf_fixed = stable >= 2 || warm_origin;
+        const bool p_fixed = stable >= 2 || (warm_origin && stable >= 1);
+        const int fam = (gf_fixed || p_fixed) ? M_GO : M_G;
         // launch A: g-update (rows y, columns x) and self p-update (rows x,
         // columns x) -- independent, same column set
         PairArgs sg[2] = {base, base};
         sg[0].rows = B.ys; sg[0].row_ld = B.Mp; sg[0].n_rows = M;
         sg[0].cols = B.xs; sg[0].colh = B.hx; sg[0].col_ld = B.Tp;
         sg[0].out_h = B.hy; sg[0].in_h = B.lb; sg[0].emode = M_G;
+        sg[0].oa = B.lb; sg[0].oca = 1.f; sg[0].ob = B.hy; sg[0].ocb = -1.f; sg[0].oc0 = 0.f;  // lb - hy
+        sg[0].fixed = gf_fixed;
         sg[1].rows = B.xs; sg[1].row_ld = B.Tp; sg[1].n_rows = T;
         sg[1].cols = B.xs; sg[1].colh = hp_cur; sg[1].col_ld = B.Tp;
         sg[1].out_h = hp_nxt; sg[1].in_h = hp_cur; sg[1].emode = M_P;
+        // log2 a + hp^{t-2} - 2 hp^{t-1} (hp_nxt still holds hp^{t-2})
+        sg[1].oa = hp_nxt; sg[1].oca = 1.f; sg[1].ob = hp_cur; sg[1].ocb = -2.f; sg[1].oc0 = log2a;
+        sg[1].fixed = p_fixed;
         if (first) sg[0].pre_ok = sg[1].pre_ok = 0;
         first = false;
         const int ncA[2] = {T, T}, coA[2] = {M_G * B.cnt_ld, M_P * B.cnt_ld};
-        r = run_pairs(ctx, d, M_G, sg, ncA, 2, coA, B.counters, stream);
+        r = run_pairs(ctx, d, fam, sg, ncA, 2, coA, B.counters, stream);
         if (r != COV_OK) break;
         // launch B: f-update (rows x, columns y)
         PairArgs a = base;
         a.rows = B.xs; a.row_ld = B.Tp; a.n_rows = T;
         a.cols = B.ys; a.colh = B.hy; a.col_ld = B.Mp;
         a.out_h = B.hx; a.emode = M_F;
+        a.oa = B.hx; a.oca = -1.f; a.ob = nullptr; a.oc0 = log2a;  // log2 a - hx
+        a.fixed = gf_fixed;
         const int ncB[1] = {M}, coB[1] = {M_F * B.cnt_ld};
-        r = run_pairs(ctx, d, M_G, &a, ncB, 1, coB, B.counters, stream);
+        r = run_pairs(ctx, d, fam, &a, ncB, 1, coB, B.counters, stream);
         std::swap(hp_cur, hp_nxt);
+        ++stable;
     }
     if (r != COV_OK) return r;
     to_eps((double)eps);  // the field and the returned potentials are at the target eps

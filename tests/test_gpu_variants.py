@@ -136,3 +136,50 @@ def test_svgd_solve_with_density_matches_oracle(cov, ctx, orc, use_graph):
     uo, so = orc.solve(w.model, w.dt, inst.s0, inst.u0, w.field, inst.Q, inst.R, eta, 3, h=w.h, density=m)
     s_init = orc.rollout(w.model, inst.s0, inst.u0, w.dt)
     assert rel_norm(host(s) - s_init, so - s_init) <= 1e-4
+
+
+# -- fixed-offset updates: the overflow and underflow fallbacks -----------------------
+_CONVERGED = {}
+
+
+def _converged(orc, T, M, eps):
+    """Points, weights and 30-iteration potentials of one seeded problem."""
+    key = (T, M, eps)
+    if key not in _CONVERGED:
+        x = wl.random_points(T, 2, seed=721)
+        y = wl.random_points(M, 2, seed=722)
+        b = wl.random_weights(M, seed=723)
+        _CONVERGED[key] = (x, y, b) + orc.sinkhorn(x, y, b, eps, 30)
+    return _CONVERGED[key]
+
+
+@pytest.mark.parametrize("T,M", [(300, 517), (3000, 5000)])
+@pytest.mark.parametrize("which,shift", [("g", 0.8), ("g", 5.0), ("f", 0.8)])
+@pytest.mark.parametrize("n_iter", [1, 5])
+def test_warm_offsets_far_from_the_update(cov, ctx, orc, T, M, which, shift, n_iter):
+    """Warm-started updates take the log-sum-exp implied by the given
+    potentials as their fixed row offset.  Per-row shifts of the given g (or
+    f) by -shift, 0 or +shift move that offset by shift / (eps ln 2) bits
+    (115 bits for 0.8 at eps = 0.01, 721 for 5.0) from the update's own
+    log-sum-exp: some rows' fixed-offset sums overflow (above 2^100, finite or
+    infinite: the CTA redoes its columns with a running maximum), others
+    underflow (below 2^-60, or zero: the row block is recomputed over all
+    columns).  The given g enters only the offsets, so with shifted g the
+    result is the unshifted warm start's; in both cases it is the oracle's
+    warm-started iteration, whose arithmetic has no offsets."""
+    eps = 0.01
+    x, y, b, fc, gc, pc = _converged(orc, T, M, eps)
+    rng = wl.rng(724)
+    if which == "g":
+        gc = gc + shift * rng.integers(-1, 2, size=M)
+    else:
+        fc = fc + shift * rng.integers(-1, 2, size=T)
+    f0, g0, p0 = (wl.f32_pair(v)[1] for v in (fc, gc, pc))
+    a, f, g, p = cov.cov_field_sinkhorn(ctx, dev32(x), dev32(y), eps, n_iter, b=dev32(b), f=dev32(f0), g=dev32(g0),
+                                        p=dev32(p0), warm=True)
+    st, flags = ctx.device_status()
+    assert st == cov.COV_OK, flags
+    fo, go, po = orc.sinkhorn(x, y, b, eps, n_iter, f=f0, g=g0, p=p0)
+    for u, v in ((f, fo), (g, go), (p, po)):
+        assert np.abs(host(u) - v).max() / eps <= POT_TOL
+    assert rel_norm(host(a), orc.sinkhorn_field(x, y, b, eps, go, po)) <= FIELD_TOL
