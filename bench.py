@@ -598,46 +598,46 @@ def run_adjoint(args):
     pairs_fwd = w.n_outer * w.pairs_per_field
 
     # roofline of the reverse all-pairs kernel (adj_kernel, column sums): per
-    # Sinkhorn iteration the reverse sweep evaluates 2TM + T^2 pairs; its time
-    # is the field VJP's per-iteration cost minus the recorded forward's,
-    # both as (t(n_hi) - t(n_lo)) / (n_hi - n_lo) at the workload's sizes
-    xr = torch.as_tensor(wl.random_points(w.T, 2, seed=w.seed + 3000, lo=0.1, hi=0.9), dtype=torch.float32,
-                         device=dev)
-    yr, br = ag.gmm_reference(mu.detach(), log_sigma.detach(), logits.detach(), xi)
-    ar = torch.as_tensor(wl.f32_pair(wl.rng(w.seed + 3001).standard_normal((w.T, 2)))[1], dtype=torch.float32,
-                         device=dev)
-
-    def per_iter_ms(fn, lo=10, hi=50, reps=5):
-        def t(n):
-            ts = []
+    # Sinkhorn iteration the reverse sweep evaluates 2TM + T^2 pairs.  Its time
+    # per iteration is that of the backward of one recorded outer iteration
+    # (no forward Sinkhorn inside: the records are replayed) as
+    # (t(n_hi) - t(n_lo)) / (n_hi - n_lo) in the Sinkhorn iteration count.
+    def reverse_per_iter_ms(T, M, lo, hi, reps):
+        inst_r = wl.make_instance(wl.SINKHORN_DOUBLE_T4096, T=T, M=M)
+        wr = inst_r.wl
+        yr = torch.as_tensor(inst_r.y, dtype=torch.float32, device=dev)
+        u0r = torch.as_tensor(inst_r.u0, dtype=torch.float64, device=dev)
+        sbar = torch.as_tensor(wl.rng(w.seed + 3001).standard_normal((T + 1, 4)), dtype=torch.float64, device=dev)
+        rctx = cov.Context(0)
+        ts = {}
+        for n in (lo, hi):
+            P = cov.make_problem(wr.model, T, wr.dt, inst_r.s0, wr.field, inst_r.Q, inst_r.R, wr.eta, y=yr,
+                                 eps=w.eps, n_iter=n)
+            _, hist, token, P2 = cov.grad_forward(rctx, P, 1, u0r, yr)
+            cov.grad_backward(rctx, P2, 1, u0r, sbar, hist, token, yr)   # warm (graph capture)
+            samples = []
             for _ in range(reps):
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 torch.cuda.synchronize()
                 e0.record()
-                fn(n)
+                cov.grad_backward(rctx, P2, 1, u0r, sbar, hist, token, yr)
                 e1.record()
                 torch.cuda.synchronize()
-                ts.append(e0.elapsed_time(e1))
-            return statistics.median(ts)
-        fn(lo)
-        fn(hi)
-        return (t(hi) - t(lo)) / (hi - lo)
+                samples.append(e0.elapsed_time(e1))
+            ts[n] = statistics.median(samples)
+        st_r, fl_r = rctx.device_status()
+        if st_r != cov.COV_OK:
+            raise SystemExit(f"device status {cov.status_string(st_r)} flags {fl_r}")
+        rctx.close()
+        return (ts[hi] - ts[lo]) / (hi - lo)
 
-    vjp_it = per_iter_ms(lambda n: cov.cov_field_sinkhorn_vjp(lctx, xr, yr, w.eps, n, ar, b=br))
-    fwd_it = per_iter_ms(lambda n: cov.cov_field_sinkhorn(lctx, xr, yr, w.eps, n, b=br, field=False))
-    rev_ms = max(vjp_it - fwd_it, 1e-9)
+    rev_ms = max(reverse_per_iter_ms(w.T, w.M, 10, 50, 5), 1e-9)
     rev_pairs = 2 * w.T * w.M + w.T * w.T
     adj_peak = SM_COUNT_NOMINAL * SM_MAX_MHZ_NOMINAL * 1e6 * FP32_LANES_PER_SM_CLK / 6
     achieved = rev_pairs / (rev_ms * 1e-3)
     # the same at a size where a launch is long enough to reach steady state
     TL, ML = 16384, 65536
-    xl = torch.as_tensor(wl.random_points(TL, 2, seed=w.seed + 3002, lo=0.1, hi=0.9), dtype=torch.float32, device=dev)
-    yl_ = torch.as_tensor(wl.random_points(ML, 2, seed=w.seed + 3003), dtype=torch.float32, device=dev)
-    al_ = torch.as_tensor(wl.f32_pair(wl.rng(w.seed + 3004).standard_normal((TL, 2)))[1], dtype=torch.float32,
-                          device=dev)
-    vjp_l = per_iter_ms(lambda n: cov.cov_field_sinkhorn_vjp(lctx, xl, yl_, w.eps, n, al_), lo=2, hi=6, reps=3)
-    fwd_l = per_iter_ms(lambda n: cov.cov_field_sinkhorn(lctx, xl, yl_, w.eps, n, field=False), lo=2, hi=6, reps=3)
-    rev_l = max(vjp_l - fwd_l, 1e-9)
+    rev_l = max(reverse_per_iter_ms(TL, ML, 2, 6, 3), 1e-9)
     achieved_l = (2 * TL * ML + TL * TL) / (rev_l * 1e-3)
     line = {"metric": "backward/forward time ratio of the coverage-loss gradient", "value": b_ms / f_ms,
             "unit": "x", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
@@ -653,12 +653,12 @@ def run_adjoint(args):
                          "peak_basis": "148 SMs x 2032 MHz x 128 FP32 lanes / 6 FP32 ops per pair (add of the "
                                        "row term, 2 FMA exponent, 3 FMA accumulation; derived from unit counts and "
                                        "clocks; ex2 at 32/clk/SM is not binding)",
-                         "how": "(field VJP - forward) per Sinkhorn iteration, (t(50) - t(10)) / 40, "
-                                "2TM + T^2 pairs per reverse iteration"},
-            "ms_per_sinkhorn_iteration": {"forward": fwd_it, "field_vjp": vjp_it, "reverse": rev_ms},
+                         "how": "backward of one recorded outer iteration, (t(50) - t(10)) / 40 Sinkhorn "
+                                "iterations; 2TM + T^2 pairs per reverse iteration"},
+            "ms_per_reverse_sinkhorn_iteration": rev_ms,
             "roofline_large": {"bound": "alu", "T": TL, "M": ML, "achieved": achieved_l, "peak": adj_peak,
                                "unit": "pair-evals/s", "frac": achieved_l / adj_peak,
-                               "ms_per_sinkhorn_iteration": {"forward": fwd_l, "field_vjp": vjp_l, "reverse": rev_l}},
+                               "ms_per_reverse_sinkhorn_iteration": rev_l, "how": "(t(6) - t(2)) / 4"},
             "forward_pairs_per_s": pairs_fwd / (f_ms * 1e-3), "loss": losses[-1],
             "grad_norms": {"mu": float(mu.grad.norm()), "log_sigma": float(log_sigma.grad.norm()),
                            "logits": float(logits.grad.norm()), "s0": float(s0.grad.norm())},

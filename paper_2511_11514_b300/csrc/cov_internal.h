@@ -34,6 +34,7 @@ struct cov_ctx {
     int threads = 128;
     int ctas_per_sm = 8;
     int use_graph = 1;
+    int use_tc = 0;            // tensor-core exponents for the fixed-offset Sinkhorn updates
     long long spin_limit = 1LL << 22;
     std::string last_cuda_error;
     cov_graph_cache solve_graph;
@@ -158,9 +159,9 @@ cov_status lqr_track_ws(cov_ctx* ctx, void* ws, size_t ws_bytes, const double* A
 struct SplitPlan {
     int n_rb;        // row blocks
     int splits;      // column splits
-    int cols_per_split;  // multiple of 8
+    int cols_per_split;  // multiple of the planning unit (8 columns; 128 for the tensor-core kernel)
 };
-SplitPlan plan_splits(int n_rows, int n_cols, int rows_per_cta, int slots);
+SplitPlan plan_splits(int n_rows, int n_cols, int rows_per_cta, int slots, int unit = 8, int fixed = 64);
 
 // GMM descriptor passed by value to kernels.
 struct GmmParams {

@@ -30,6 +30,7 @@
 
 #include "cov_device.cuh"
 #include "cov_internal.h"
+#include "tc_records.cuh"
 
 namespace cov {
 
@@ -82,6 +83,12 @@ struct PairArgs {
     const float* ob;
     float oca, ocb, oc0;
     int fixed;
+    // tensor-core path (lse_tc.cuh): the columns' coordinate and h records;
+    // out_rec (any log-sum-exp mode, may be null): the rows' h records,
+    // rewritten with out_h for the next update that has these points as columns
+    const float* rec0;
+    const float* rech;
+    float* out_rec;
     float* bary;         // [D][row_ld]
     float* a_out;        // [n_rows][D]
     float a_scale;
@@ -286,6 +293,8 @@ __device__ __forceinline__ void epilogue(const PairArgs& a, int i, float m, floa
         else v = 0.5f * (a.log2a + a.in_h[i] - L);
         ok &= finitef(v);
         a.out_h[i] = v;
+        if (a.out_rec)
+            reinterpret_cast<float4*>(a.out_rec)[i] = tc_hrec<D>(v, D == 3 ? a.rows[(size_t)2 * a.row_ld + i] : 0.f);
         if constexpr (MODE == M_GW) {
             if (a.bary) {
                 const float inv = 1.0f / s;
@@ -660,16 +669,19 @@ __global__ void __launch_bounds__(kThreads) pairs_kernel(const __grid_constant__
     if (threadIdx.x == 0) a.counters[rb] = 0u;  // ready for the next launch
 }
 
+}  // namespace cov
+
+#include "lse_tc.cuh"
+
 // ---------------------------------------------------------------------------
 // Split planning: pick the number of column splits per row block that
 // minimises (waves of CTAs) x (columns per CTA + fixed cost) + merge cost.
+// Splits are whole multiples of `unit` columns.
 // ---------------------------------------------------------------------------
-}  // namespace cov
-
-cov::SplitPlan cov::plan_splits(int n_rows, int n_cols, int rows_per_cta, int slots) {
+cov::SplitPlan cov::plan_splits(int n_rows, int n_cols, int rows_per_cta, int slots, int unit, int fixed) {
     SplitPlan best{};
     const int n_rb = (n_rows + rows_per_cta - 1) / rows_per_cta;
-    const int units = (n_cols + 7) / 8;
+    const int units = (n_cols + unit - 1) / unit;
     const int smax = std::max(1, std::min(units, (2 * slots + n_rb - 1) / n_rb));
     double best_cost = 1e300;
     for (int s = 1; s <= smax; ++s) {
@@ -677,10 +689,10 @@ cov::SplitPlan cov::plan_splits(int n_rows, int n_cols, int rows_per_cta, int sl
         const int s_eff = (units + cpu - 1) / cpu;
         const long long ctas = (long long)n_rb * s_eff;
         const long long waves = (ctas + slots - 1) / slots;
-        const double cost = (double)waves * (cpu * 8 + 64) + (s_eff > 1 ? 4.0 * s_eff : 0.0);
+        const double cost = (double)waves * ((double)cpu * unit + fixed) + (s_eff > 1 ? 4.0 * s_eff : 0.0);
         if (cost < best_cost - 1e-9) {
             best_cost = cost;
-            best = SplitPlan{n_rb, s_eff, cpu * 8};
+            best = SplitPlan{n_rb, s_eff, cpu * unit};
         }
     }
     return best;
@@ -721,6 +733,9 @@ __global__ void sk_centre_kernel(const float* __restrict__ y, int M, int d, cons
 
 struct SkBufs {
     float *xs, *ys, *hx, *hy, *hp0, *hp1, *lb, *nx, *ny, *bary, *scal, *part;
+    // tensor-core records (tc_records.cuh; null when not carved): coordinate
+    // records of x and y, h records of hx, hp (two buffers) and hy
+    float *c0x, *c0y, *hrx, *hrp0, *hrp1, *hry;
     unsigned* counters;  // [M_COUNT][cnt_ld]
     int Tp, Mp, cnt_ld;
     size_t part_floats;
@@ -925,6 +940,55 @@ static cudaError_t launch_pairs_d(int d, int R, int family, const PairLaunch& L,
     return cudaErrorInvalidValue;
 }
 
+template <int D>
+static cudaError_t launch_tc_t(const PairLaunch& L, int n_ctas, cudaStream_t st, int* occ) {
+    if (occ) {
+        static int cached = 0;
+        if (cached == 0) {
+            // resident CTAs per SM from the kernel's own resources: registers
+            // (allocated per warp in units of 256), static shared memory (plus
+            // 1 KB the system reserves per CTA; largest carveout requested)
+            // and tensor memory (512 columns per SM)
+            cudaFuncSetAttribute(lse_tc_kernel<D>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared);
+            cudaFuncAttributes fa{};
+            int v = 1;
+            if (cudaFuncGetAttributes(&fa, lse_tc_kernel<D>) == cudaSuccess && fa.numRegs > 0) {
+                const int warps = kTcThreads / 32;
+                const int regs_cta = warps * (((fa.numRegs * 32) + 255) / 256 * 256);
+                const int by_regs = 65536 / regs_cta;
+                const int by_smem = (228 * 1024) / ((int)fa.sharedSizeBytes + 1024);
+                v = std::max(1, std::min(by_regs, by_smem));
+            } else {
+                cudaGetLastError();
+            }
+            cached = std::min(v, kTcMinBlocks);
+        }
+        *occ = cached;
+        return cudaSuccess;
+    }
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)n_ctas);
+    cfg.blockDim = dim3(kTcThreads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, lse_tc_kernel<D>, L);
+}
+
+static cudaError_t launch_tc_d(int d, const PairLaunch& L, int n, cudaStream_t st, int* occ) {
+    switch (d) {
+        case 1: return launch_tc_t<1>(L, n, st, occ);
+        case 2: return launch_tc_t<2>(L, n, st, occ);
+        case 3: return launch_tc_t<3>(L, n, st, occ);
+    }
+    return cudaErrorInvalidValue;
+}
+
 static int effective_R(int d, int R) { return (d == 2 && (R == 2 || R == 8)) ? R : 4; }
 
 constexpr int kMaxSlots = 1536;           // CTA slots assumed by the workspace bound
@@ -932,9 +996,10 @@ constexpr size_t kPartRows = (size_t)2 * kMaxSlots * 256 + 256;
 
 static int cnt_ld_for(int Tp, int Mp) { return std::max(Tp, Mp) / 64 + 1; }
 
-static void plan_segment(PairArgs& a, int n_cols, int RB, int slots, unsigned* counters) {
-    const SplitPlan pl = plan_splits(a.n_rows, n_cols, RB, slots);
-    a.n_cols8 = (int)round_up((size_t)n_cols, 8);
+static void plan_segment(PairArgs& a, int n_cols, int RB, int slots, unsigned* counters, int unit = 8,
+                         int fixed = 64) {
+    const SplitPlan pl = plan_splits(a.n_rows, n_cols, RB, slots, unit, fixed);
+    a.n_cols8 = (int)round_up((size_t)n_cols, (size_t)unit);
     a.cols_per_split = pl.cols_per_split;
     a.splits = pl.splits;
     a.n_rb = pl.n_rb;
@@ -948,17 +1013,27 @@ static void plan_segment(PairArgs& a, int n_cols, int RB, int slots, unsigned* c
 // and seg[1]'s partials follow seg[0]'s in the partial buffer.
 static cov_status run_pairs(cov_ctx* ctx, int d, int family, PairArgs* seg, const int* n_cols, int nseg,
                             const int* cnt_off, unsigned* counters, cudaStream_t st) {
+    // Fixed-offset updates of every segment with records: exponents on the
+    // tensor cores (128-row CTAs, 128-column tiles)
+    bool tc = family == M_GO && ctx->use_tc && d <= 3;
+    for (int k = 0; k < nseg; ++k) tc = tc && seg[k].fixed && seg[k].rec0 && seg[k].rech;
     const int R = effective_R(d, ctx->rows_per_thread);
-    const int RB = 32 * R;
-    // one wave: as many CTAs as can be resident (the register budget decides
-    // how many per SM), capped by the tuning option
+    const int RB = tc ? kTcRows : 32 * R;
+    const int unit = tc ? kTcCols : 8;
+    const int fixed_cost = tc ? 2 * kTcCols : 64;
+    // one wave: as many CTAs as can be resident (the register budget, and
+    // for the tensor-core kernel its tensor memory, decides how many per SM),
+    // capped by the tuning option
     int occ = 1;
-    launch_pairs_d(d, R, family, PairLaunch{}, 0, st, &occ);
+    if (tc)
+        launch_tc_d(d, PairLaunch{}, 0, st, &occ);
+    else
+        launch_pairs_d(d, R, family, PairLaunch{}, 0, st, &occ);
     const int slots = std::max(1, std::min(ctx->num_sms * std::min(occ, ctx->ctas_per_sm), kMaxSlots));
     const int nacc = family == M_SVGD ? d : ((family == M_WY || family == M_WX || family == M_GW) ? 2 + d : 2);
     PairLaunch L{};
     if (nseg == 1) {
-        plan_segment(seg[0], n_cols[0], RB, slots, counters + cnt_off[0]);
+        plan_segment(seg[0], n_cols[0], RB, slots, counters + cnt_off[0], unit, fixed_cost);
         L.seg[0] = seg[0];
         L.seg[1] = seg[0];
         L.ctas0 = seg[0].n_rb * seg[0].splits;
@@ -967,21 +1042,21 @@ static cov_status run_pairs(cov_ctx* ctx, int d, int family, PairArgs* seg, cons
         int s0 = (int)llround(slots * w0 / (w0 + w1));
         s0 = std::max(1, std::min(s0, slots - 1));
         const int s1 = std::max(1, slots - s0);
-        plan_segment(seg[0], n_cols[0], RB, s0, counters + cnt_off[0]);
-        plan_segment(seg[1], n_cols[1], RB, s1, counters + cnt_off[1]);
+        plan_segment(seg[0], n_cols[0], RB, s0, counters + cnt_off[0], unit, fixed_cost);
+        plan_segment(seg[1], n_cols[1], RB, s1, counters + cnt_off[1], unit, fixed_cost);
         seg[1].part = seg[0].part + (size_t)nacc * seg[0].splits * seg[0].part_ld;
         L.seg[0] = seg[0];
         L.seg[1] = seg[1];
         L.ctas0 = seg[0].n_rb * seg[0].splits;
     }
     const int total = L.ctas0 + (nseg == 2 ? seg[1].n_rb * seg[1].splits : 0);
-    const cudaError_t e = launch_pairs_d(d, R, family, L, total, st, nullptr);
+    const cudaError_t e = tc ? launch_tc_d(d, L, total, st, nullptr) : launch_pairs_d(d, R, family, L, total, st, nullptr);
     return cuda_failed(ctx, e) ? COV_ERR_CUDA : COV_OK;
 }
 
 // with_part = false leaves part/counters to the caller (a recorded forward
 // keeps many tapes and shares one split buffer between them).
-static SkBufs carve_sinkhorn(Carver& cv, int T, int M, int d, bool with_part = true) {
+static SkBufs carve_sinkhorn(Carver& cv, int T, int M, int d, bool with_part = true, bool with_rec = false) {
     SkBufs B{};
     B.Tp = (int)round_up((size_t)T, kRowPad);
     B.Mp = (int)round_up((size_t)M, kRowPad);
@@ -1002,6 +1077,14 @@ static SkBufs carve_sinkhorn(Carver& cv, int T, int M, int d, bool with_part = t
         B.counters = cv.take<unsigned>((size_t)M_COUNT * B.cnt_ld);
         B.part = cv.take<float>(B.part_floats);
     }
+    if (with_rec && d <= 3) {
+        B.c0x = cv.take<float>((size_t)kTcRecC * B.Tp);
+        B.c0y = cv.take<float>((size_t)kTcRecC * B.Mp);
+        B.hrx = cv.take<float>((size_t)kTcRecH * B.Tp);
+        B.hrp0 = cv.take<float>((size_t)kTcRecH * B.Tp);
+        B.hrp1 = cv.take<float>((size_t)kTcRecH * B.Tp);
+        B.hry = cv.take<float>((size_t)kTcRecH * B.Mp);
+    }
     return B;
 }
 
@@ -1019,7 +1102,7 @@ void sinkhorn_reference_stats(const float* y, int M, int d, const float* b, floa
 
 size_t sinkhorn_ws_bytes(int T, int M, int d) {
     Carver cv(nullptr);
-    carve_sinkhorn(cv, T, M, d);
+    carve_sinkhorn(cv, T, M, d, true, true);
     return round_up(cv.off, 256);
 }
 
@@ -1035,7 +1118,7 @@ cov_status sinkhorn_field_ws(cov_ctx* ctx, void* ws, size_t ws_bytes, const floa
     const int warm = (flags & COV_WARM_START) ? 1 : 0;
     if (warm && (!f || !g || !p)) return COV_ERR_INVALID_ARG;
     Carver cv(ws);
-    SkBufs B = carve_sinkhorn(cv, T, M, d);
+    SkBufs B = carve_sinkhorn(cv, T, M, d, true, true);
     if (!ws || cv.off > ws_bytes) return COV_ERR_WORKSPACE;
     if (cuda_failed(ctx, cudaMemsetAsync(B.counters, 0, sizeof(unsigned) * M_COUNT * B.cnt_ld, stream)))
         return COV_ERR_CUDA;
@@ -1062,8 +1145,29 @@ cov_status sinkhorn_field_ws(cov_ctx* ctx, void* ws, size_t ws_bytes, const floa
     base.pre_ok = 1;
     float* hp_cur = B.hp0;
     float* hp_nxt = B.hp1;
+    float* hrp_cur = B.hrp0;  // h records of hp_cur / hp_nxt (tensor-core path)
+    float* hrp_nxt = B.hrp1;
     bool first = true;  // the first pass reads what the prep kernel just wrote
     cov_status r = COV_OK;
+    // the tensor-core records of the current state (after the prep or a
+    // rescale; every update's epilogue then keeps its rows' h records current)
+    // records are kept only while the tensor-core path is enabled
+    const bool recs = B.c0x != nullptr && ctx->use_tc;
+    auto build_records = [&]() {
+        if (!recs) return;
+        const int nb = (np + 255) / 256;
+        if (d == 1)
+            tc_records_kernel<1><<<nb, 256, 0, stream>>>(B.xs, B.Tp, B.ys, B.Mp, B.hx, hp_cur, hp_nxt, B.hy, B.c0x,
+                                                         B.c0y, B.hrx, hrp_cur, hrp_nxt, B.hry);
+        else if (d == 2)
+            tc_records_kernel<2><<<nb, 256, 0, stream>>>(B.xs, B.Tp, B.ys, B.Mp, B.hx, hp_cur, hp_nxt, B.hy, B.c0x,
+                                                         B.c0y, B.hrx, hrp_cur, hrp_nxt, B.hry);
+        else
+            tc_records_kernel<3><<<nb, 256, 0, stream>>>(B.xs, B.Tp, B.ys, B.Mp, B.hx, hp_cur, hp_nxt, B.hy, B.c0x,
+                                                         B.c0y, B.hrx, hrp_cur, hrp_nxt, B.hry);
+        first = true;
+    };
+    build_records();
     // move the state to another eps (coordinates and potential terms), on
     // the stream before the next pass; that pass then waits for it
     auto to_eps = [&](double e_new) {
@@ -1073,6 +1177,7 @@ cov_status sinkhorn_field_ws(cov_ctx* ctx, void* ws, size_t ws_bytes, const floa
                                                   log2a, hp_cur, ctx->status);
         eps_cur = e_new;
         first = true;
+        build_records();
     };
     int stable = 0;            // iterations run at the current eps
     bool warm_origin = warm;   // the warm-start potentials are still at the current eps
@@ -1085,14 +1190,15 @@ cov_status sinkhorn_field_ws(cov_ctx* ctx, void* ws, size_t ws_bytes, const floa
             }
             to_eps(e_it);
         }
-        // An update runs with the previous log-sum-exp of its rows as a fixed
-        // offset (M_GO) once that value exists at the current eps: for g and
-        // f from the third iteration on (or at once from warm-start
-        // potentials); for p, which needs the two previous self potentials,
-        // from the third iteration on (the second, from a warm start).
-        const bool gf_fixed = stable >= 2 || warm_origin;
-        const bool p_fixed = stable >= 2 || (warm_origin && stable >= 1);
-        const int fam = (gf_fixed || p_fixed) ? M_GO : M_G;
+        // The updates run with a fixed row offset (M_GO) from the third
+        // iteration at one eps on, or at once from warm-start potentials: the
+        // previous log-sum-exp of the row, read back from the potentials it
+        // produced (g: lb - hy, f: log2 a - hx, p: log2 a + hp^(t-2) -
+        // 2 hp^(t-1)); before the first p-update of a warm start, the fixed
+        // point of that update, log2 a - hp (exact at convergence).
+        const bool fixed = stable >= 2 || warm_origin;
+        const bool p_prev = stable >= 1;
+        const int fam = fixed ? M_GO : M_G;
         // launch A: g-update (rows y, columns x) and self p-update (rows x,
         // columns x) -- independent, same column set
         PairArgs sg[2] = {base, base};
@@ -1100,13 +1206,18 @@ cov_status sinkhorn_field_ws(cov_ctx* ctx, void* ws, size_t ws_bytes, const floa
         sg[0].cols = B.xs; sg[0].colh = B.hx; sg[0].col_ld = B.Tp;
         sg[0].out_h = B.hy; sg[0].in_h = B.lb; sg[0].emode = M_G;
         sg[0].oa = B.lb; sg[0].oca = 1.f; sg[0].ob = B.hy; sg[0].ocb = -1.f; sg[0].oc0 = 0.f;  // lb - hy
-        sg[0].fixed = gf_fixed;
+        sg[0].fixed = fixed;
+        if (recs) { sg[0].rec0 = B.c0x; sg[0].rech = B.hrx; sg[0].out_rec = B.hry; }
         sg[1].rows = B.xs; sg[1].row_ld = B.Tp; sg[1].n_rows = T;
         sg[1].cols = B.xs; sg[1].colh = hp_cur; sg[1].col_ld = B.Tp;
         sg[1].out_h = hp_nxt; sg[1].in_h = hp_cur; sg[1].emode = M_P;
-        // log2 a + hp^{t-2} - 2 hp^{t-1} (hp_nxt still holds hp^{t-2})
-        sg[1].oa = hp_nxt; sg[1].oca = 1.f; sg[1].ob = hp_cur; sg[1].ocb = -2.f; sg[1].oc0 = log2a;
-        sg[1].fixed = p_fixed;
+        if (p_prev) {  // log2 a + hp^{t-2} - 2 hp^{t-1} (hp_nxt still holds hp^{t-2})
+            sg[1].oa = hp_nxt; sg[1].oca = 1.f; sg[1].ob = hp_cur; sg[1].ocb = -2.f; sg[1].oc0 = log2a;
+        } else {       // log2 a - hp^{t-1}
+            sg[1].oa = hp_cur; sg[1].oca = -1.f; sg[1].ob = nullptr; sg[1].ocb = 0.f; sg[1].oc0 = log2a;
+        }
+        sg[1].fixed = fixed;
+        if (recs) { sg[1].rec0 = B.c0x; sg[1].rech = hrp_cur; sg[1].out_rec = hrp_nxt; }
         if (first) sg[0].pre_ok = sg[1].pre_ok = 0;
         first = false;
         const int ncA[2] = {T, T}, coA[2] = {M_G * B.cnt_ld, M_P * B.cnt_ld};
@@ -1118,10 +1229,12 @@ cov_status sinkhorn_field_ws(cov_ctx* ctx, void* ws, size_t ws_bytes, const floa
         a.cols = B.ys; a.colh = B.hy; a.col_ld = B.Mp;
         a.out_h = B.hx; a.emode = M_F;
         a.oa = B.hx; a.oca = -1.f; a.ob = nullptr; a.oc0 = log2a;  // log2 a - hx
-        a.fixed = gf_fixed;
+        a.fixed = fixed;
+        if (recs) { a.rec0 = B.c0y; a.rech = B.hry; a.out_rec = B.hrx; }
         const int ncB[1] = {M}, coB[1] = {M_F * B.cnt_ld};
         r = run_pairs(ctx, d, fam, &a, ncB, 1, coB, B.counters, stream);
         std::swap(hp_cur, hp_nxt);
+        std::swap(hrp_cur, hrp_nxt);
         ++stable;
     }
     if (r != COV_OK) return r;

@@ -53,21 +53,23 @@ def test_nonfinite_input_sets_status(cov, ctx):
     assert ctx.device_status() == (cov.COV_OK, 0)   # read clears
 
 
-def test_bounded_wait_gives_up_and_reports_timeout(cov, ctx, orc):
+@pytest.mark.parametrize("n_iter", [1, 4])
+def test_bounded_wait_gives_up_and_reports_timeout(cov, ctx, orc, n_iter):
     """A wait limit of zero polls makes every tile wait give up at once; the
-    kernel drains its copies, raises the timeout bit and returns, and the
-    context stays usable."""
+    kernel drains its copies (and, in the tensor-core kernel of the later
+    iterations, its MMAs) with a limit of its own, raises the timeout bit and
+    returns, and the context stays usable."""
     x = wl.random_points(300, 2, 1)
     y = wl.random_points(400, 2, 2)
     ctx.set_option(cov.OPT_SPIN_LIMIT, 0)
     try:
-        cov.cov_field_sinkhorn(ctx, dev32(x), dev32(y), 0.05, 1)
+        cov.cov_field_sinkhorn(ctx, dev32(x), dev32(y), 0.05, n_iter)
         st, fl = ctx.device_status()
     finally:
         ctx.set_option(cov.OPT_SPIN_LIMIT, 1 << 22)
     assert fl & cov.DEV_TIMEOUT and st == cov.COV_ERR_TIMEOUT
-    a, f, g, p = cov.cov_field_sinkhorn(ctx, dev32(x), dev32(y), 0.05, 1)
-    fo, go, po = orc.sinkhorn(x, y, None, 0.05, 1)
+    a, f, g, p = cov.cov_field_sinkhorn(ctx, dev32(x), dev32(y), 0.05, n_iter)
+    fo, go, po = orc.sinkhorn(x, y, None, 0.05, n_iter)
     assert np.abs(host(f) - fo).max() / 0.05 <= 1e-4
     assert ctx.device_status() == (cov.COV_OK, 0)
 
