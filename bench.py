@@ -41,16 +41,18 @@ UNIT = "pair-evals/s"
 DEFAULT_WORKLOAD = wl.SINKHORN_DOUBLE_T4096.name
 L2_FLUSH_BYTES = 256 << 20
 # Algorithmic FP32-pipe instructions per Sinkhorn pair evaluation (base-2,
-# prescaled, column term folded): 2 FMA for the d = 2 inner product, the max,
-# the max subtraction and the accumulation; one exponential (MUFU ex2).
-FP32_OPS_PER_PAIR = 5
+# prescaled, column term folded) in the fixed-offset form the iteration runs
+# in from its third step: 2 FMA for the d = 2 inner product, the offset
+# subtraction and the accumulation; one exponential (MUFU ex2).  With 128
+# FP32 lanes and 32 ex2 per SM and clock both pipes bound at 32 pairs/clk/SM.
+FP32_OPS_PER_PAIR = 4
 SM_COUNT_NOMINAL = 148
 SM_MAX_MHZ_NOMINAL = 2032.0
 FP32_LANES_PER_SM_CLK = 128
 # DRAM bytes (read + write) per launch of pairs_kernel at the benchmark
-# workload from one ncu capture of the current kernel: 280 KB (g + p launch)
-# and 247 KB (f launch), no writes.
-PAIRS_TRAFFIC_BYTES = 263424
+# workload from one ncu capture of the current kernel (fixed-offset form):
+# 379 KB (g + p launch) and 280 KB (f launch), no writes.
+PAIRS_TRAFFIC_BYTES = 329344
 
 
 def parse_args():
@@ -73,10 +75,24 @@ def parse_args():
     ap.add_argument("--variants", action="store_true",
                     help="measure the Sinkhorn variants at eps = 0.002: iterations to a field accuracy, "
                          "cold vs eps-scaled vs warm-started")
+    ap.add_argument("--tensor-cores", action="store_true",
+                    help="form the fixed-offset updates' exponents on the tensor cores (COV_OPT_TENSOR_CORES)")
     ap.add_argument("--adjoint-outer", type=int, default=0,
                     help="outer iterations of --adjoint (default: the workload's 20; fewer only to keep a "
                          "profiler's launch list short)")
     return ap.parse_args()
+
+
+def count_library_launches(step) -> int:
+    """Kernels of libcov (names in namespace cov::) that one call of `step`
+    launches, counted from CUDA activity records of one untimed run."""
+    import torch
+    from torch.profiler import ProfilerActivity, profile
+    torch.cuda.synchronize()
+    with profile(activities=[ProfilerActivity.CUDA]) as prof:
+        step()
+        torch.cuda.synchronize()
+    return int(sum(e.count for e in prof.key_averages() if "cov::" in e.key))
 
 
 def dist_env():
@@ -185,8 +201,11 @@ def calibrate(inst, seconds):
     T, M = inst.wl.T, inst.wl.M
     if rows <= min(T, M):
         return rows, 1
-    _, dt_full = oracle_sample(inst, max(T, M))  # one full iteration: the small sample underrates the cores
-    return max(T, M), max(1, int(round(seconds / max(dt_full, 1e-9))))
+    # full iterations: the small sample underrates the cores, and the first
+    # full one (thread start-up, first touch of its buffers) overrates the time
+    oracle_sample(inst, max(T, M))
+    _, dt_two = oracle_sample(inst, max(T, M), iters=2)
+    return max(T, M), max(1, int(round(seconds / max(dt_two / 2, 1e-9))))
 
 
 def cpu_baseline(inst, seconds):
@@ -278,6 +297,8 @@ def run_ours(args):
         raise SystemExit("bench.py times the Sinkhorn workloads")
     inst = wl.make_instance(w, seed=w.seed + rank)
     ctx = cov.Context(local_rank)
+    if args.tensor_cores:
+        ctx.set_option(cov.OPT_TENSOR_CORES, 1)
     dev = torch.device("cuda", local_rank)
     y = torch.as_tensor(inst.y, dtype=torch.float32, device=dev).contiguous()
     prob = cov.make_problem(w.model, w.T, w.dt, inst.s0, w.field, inst.Q, inst.R, w.eta, y=y, eps=w.eps,
@@ -370,8 +391,15 @@ def run_ours(args):
             torch.cuda.synchronize()
             return a.elapsed_time(b)
 
-        tb = (big_ms(3) - big_ms(1)) / 2
+        # iterations 3 and 4: the fixed-offset form all but the first two run in
+        tb = (big_ms(5) - big_ms(3)) / 2
         ach_b = (2 * wb.T * wb.M + wb.T * wb.T) / (tb * 1e-3)
+        # the same iterations on the tensor-core exponent path
+        ctx.set_option(cov.OPT_TENSOR_CORES, 1)
+        cov.cov_field_sinkhorn(ctx, xb, yb, wb.eps, 1, field=False)
+        tb_tc = (big_ms(5) - big_ms(3)) / 2
+        ctx.set_option(cov.OPT_TENSOR_CORES, 1 if args.tensor_cores else 0)
+        ach_tc = (2 * wb.T * wb.M + wb.T * wb.T) / (tb_tc * 1e-3)
         # the LQR step of that workload (time-varying unicycle linearisation:
         # parallel-in-time Riccati + the two affine scans), CUDA events
         sbig = cov.cov_rollout(ctx, wb.model, ib.s0, ub, wb.dt)
@@ -388,7 +416,15 @@ def run_ours(args):
         torch.cuda.synchronize()
         big = {"bound": "alu", "achieved": ach_b / 1e9, "peak": peak / 1e9, "unit": "Gpair/s", "frac": ach_b / peak,
                "traffic": None, "workload": wb.name, "ms_per_sinkhorn_iteration": tb,
+               "exponents": "tensor cores" if args.tensor_cores else "CUDA cores",
+               "tensor_core_path": {"achieved": ach_tc / 1e9, "frac": ach_tc / peak,
+                                    "ms_per_sinkhorn_iteration": tb_tc},
                "lqr_track_ms": la.elapsed_time(lb) / 3}
+        if args.tensor_cores:
+            big.update({"achieved": ach_tc / 1e9, "frac": ach_tc / peak, "ms_per_sinkhorn_iteration": tb_tc,
+                        "cuda_core_path": {"achieved": ach_b / 1e9, "frac": ach_b / peak,
+                                           "ms_per_sinkhorn_iteration": tb}})
+            del big["tensor_core_path"]
         if not args.no_tune:
             apply_choice = {"R": tiling["R"], "ctas_per_sm": tiling["ctas_per_sm"]}
             autotune.apply(ctx, apply_choice)
@@ -417,7 +453,7 @@ def run_ours(args):
     h2d = u_h.numel() * 8 + y_h.numel() * 4
     d2h = u_out.numel() * 8 + s_out.numel() * 8
 
-    launches_per_step = 3 * w.n_iter + 8
+    launches_per_step = count_library_launches(lambda: cov.cov_solve_continue(ctx, prob, 1, u, s))
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -428,12 +464,15 @@ def run_ours(args):
                 "l2": "flushed between steps (256 MiB write outside the per-step CUDA events)",
                 "ms_per_coverage_solve": ms_per_step * w.n_outer,
                 "tiling": tiling,
+                "exponents": "tensor cores (tcgen05 kind::tf32)" if args.tensor_cores else "CUDA cores (FP32 FMA)",
                 "wall_s_timed_region": wall}),
             "roofline": {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Gpair/s",
-                         "frac": achieved / peak, "traffic": PAIRS_TRAFFIC_BYTES,
+                         "frac": achieved / peak, "traffic": None if args.tensor_cores else PAIRS_TRAFFIC_BYTES,
                          "traffic_note": "dram__bytes_read.sum + dram__bytes_write.sum per launch of "
                                          "pairs_kernel at this workload, one ncu capture of the current kernel",
-                         "kernel": "pairs_kernel (Sinkhorn g/f/p soft-c-transform), per iteration of 3 launches",
+                         "kernel": ("lse_tc_kernel (tcgen05 exponents) for the fixed-offset iterations, "
+                                    "pairs_kernel for the rest" if args.tensor_cores else
+                                    "pairs_kernel (Sinkhorn g/f/p soft-c-transform)") + ", per iteration of 3 launches",
                          "peak_basis": "derived: 148 SMs x 2032 MHz x min(MUFU ex2 width, 128 FP32 lanes / "
                                        f"{FP32_OPS_PER_PAIR} ops per pair)",
                          "peak_detail": peak_info, "probe": probe},
