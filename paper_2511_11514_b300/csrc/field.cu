@@ -67,7 +67,9 @@ struct PairArgs {
     int col_ld;
     int n_cols8;         // columns rounded up to 8 (padding holds neutral values)
     int cols_per_split;  // multiple of 8
-    int splits;
+    int splits;          // column splits of row blocks [0, n_hi); the others have splits - 1
+    int n_hi;            // row blocks with `splits` splits (== n_rb: every row block)
+    int cps_lo;          // columns per split of the row blocks with splits - 1
     float* part;         // [NACC][splits][part_ld]
     int part_ld;         // n_rb * rows per CTA
     unsigned* counters;  // [n_rb]
@@ -257,6 +259,36 @@ __device__ __forceinline__ void merge_into(float& m, float& s, float* acc, float
     }
 }
 
+// Merge the (max, sum) partials of row i over all column splits into
+// (m, s): CH partials are loaded at once (one L2 round trip per CH splits),
+// then one maximum and a sum of independent rescaled terms -- no serial
+// max/rescale chain through the partials.
+template <int CH>
+__device__ __forceinline__ void merge_lse_splits(const float* part, size_t part_ld, int splits, int ns, int i,
+                                                 float& m, float& s) {
+    const size_t cs = (size_t)splits * part_ld;  // component stride of the layout (the plan's largest count)
+    m = kNegBig;
+    s = 0.f;
+    for (int p0 = 0; p0 < ns; p0 += CH) {
+        float m2[CH], s2[CH];
+#pragma unroll
+        for (int u = 0; u < CH; ++u) {
+            const bool live = p0 + u < ns;
+            const float* P = part + (size_t)(live ? p0 + u : 0) * part_ld + i;
+            m2[u] = live ? ld_cg(P) : kNegBig;
+            s2[u] = live ? ld_cg(P + cs) : 0.f;
+        }
+        float M = m;
+#pragma unroll
+        for (int u = 0; u < CH; ++u) M = fmaxf(M, m2[u]);
+        float t[4] = {s * ex2(m - M), 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int u = 0; u < CH; ++u) t[u & 3] = fmaf(s2[u], ex2(m2[u] - M), t[u & 3]);
+        s = (t[0] + t[1]) + (t[2] + t[3]);
+        m = M;
+    }
+}
+
 template <int D, int MODE>
 __device__ __forceinline__ void epilogue(const PairArgs& a, int i, float m, float s, const float* acc) {
     using TR = PairTraits<D, MODE>;
@@ -334,7 +366,21 @@ __global__ void __launch_bounds__(kThreads) pairs_kernel(const __grid_constant__
     const int segi = ((int)blockIdx.x >= L.ctas0) ? 1 : 0;
     const PairArgs a = segi ? L.seg[1] : L.seg[0];
     const int lb = (int)blockIdx.x - (segi ? L.ctas0 : 0);
-    const int rb = lb / a.splits, sp = lb % a.splits;
+    // this CTA's row block, split index, the row block's split count and
+    // its columns (a plan may give some row blocks one split fewer)
+    int rb, sp, ns, cps;
+    if (lb < a.n_hi * a.splits) {
+        rb = lb / a.splits;
+        sp = lb % a.splits;
+        ns = a.splits;
+        cps = a.cols_per_split;
+    } else {
+        const int l2 = lb - a.n_hi * a.splits;
+        ns = a.splits - 1;
+        rb = a.n_hi + l2 / ns;
+        sp = l2 % ns;
+        cps = a.cps_lo;
+    }
     const int row0 = rb * RB;
 
     if (threadIdx.x == 0) {
@@ -373,8 +419,8 @@ __global__ void __launch_bounds__(kThreads) pairs_kernel(const __grid_constant__
         }
     }
 
-    const int c0 = sp * a.cols_per_split;
-    const int c1 = min(c0 + a.cols_per_split, a.n_cols8);
+    const int c0 = sp * cps;
+    const int c1 = min(c0 + cps, a.n_cols8);
     __syncthreads();
 
     // A tile is the column coordinates (constant over the Sinkhorn loop) and
@@ -497,7 +543,7 @@ __global__ void __launch_bounds__(kThreads) pairs_kernel(const __grid_constant__
             __syncthreads();
         };
         reduce_warps();
-        if (a.splits > 1) {
+        if (ns > 1) {
             const size_t cs = (size_t)a.splits * a.part_ld;
             for (int q = threadIdx.x; q < RB; q += kThreads) {
                 float* P = a.part + (size_t)sp * a.part_ld + row0 + q;
@@ -508,26 +554,14 @@ __global__ void __launch_bounds__(kThreads) pairs_kernel(const __grid_constant__
             __syncthreads();
             if (threadIdx.x == 0) {
                 const unsigned prev = atomicAdd(&a.counters[rb], 1u);
-                s_last = (prev == (unsigned)(a.splits - 1));
+                s_last = (prev == (unsigned)(ns - 1));
             }
             __syncthreads();
             if (!s_last) return;
             __threadfence();
             for (int q = threadIdx.x; q < RB; q += kThreads) {
-                const int i = row0 + q;
-                float m = kNegBig, sv = 0.f;
-                for (int p0 = 0; p0 < a.splits; p0 += 8) {
-                    float m2[8], s2[8];
-#pragma unroll
-                    for (int u = 0; u < 8; ++u) {
-                        const bool live = p0 + u < a.splits;
-                        const float* P = a.part + (size_t)(live ? p0 + u : 0) * a.part_ld + i;
-                        m2[u] = live ? ld_cg(P) : kNegBig;
-                        s2[u] = live ? ld_cg(P + cs) : 0.f;
-                    }
-#pragma unroll
-                    for (int u = 0; u < 8; ++u) merge_into<D, MODE>(m, sv, nullptr, m2[u], s2[u], nullptr);
-                }
+                float m, sv;
+                merge_lse_splits<16>(a.part, (size_t)a.part_ld, a.splits, ns, row0 + q, m, sv);
                 fin_m[q] = m;
                 fin_s[q] = sv;
             }
@@ -544,7 +578,7 @@ __global__ void __launch_bounds__(kThreads) pairs_kernel(const __grid_constant__
             reduce_warps();
         }
         for (int q = threadIdx.x; q < RB; q += kThreads) epilogue<D, MODE>(a, row0 + q, fin_m[q], fin_s[q], nullptr);
-        if (a.splits > 1 && threadIdx.x == 0) a.counters[rb] = 0u;  // ready for the next launch
+        if (ns > 1 && threadIdx.x == 0) a.counters[rb] = 0u;  // ready for the next launch
         return;
     }
 
@@ -599,7 +633,7 @@ __global__ void __launch_bounds__(kThreads) pairs_kernel(const __grid_constant__
             merge_into<D, MODE>(m, s, acc, m2, s2, a2);
         }
         const int i = row0 + q;
-        if (a.splits == 1) {
+        if (ns == 1) {
             epilogue<D, MODE>(a, i, m, s, acc);
         } else {
             float* P = a.part + (size_t)sp * a.part_ld + i;
@@ -617,14 +651,14 @@ __global__ void __launch_bounds__(kThreads) pairs_kernel(const __grid_constant__
             }
         }
     }
-    if (a.splits == 1) return;
+    if (ns == 1) return;
 
     // ---- last CTA of this row block merges the splits ------------------------
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) {
         const unsigned prev = atomicAdd(&a.counters[rb], 1u);
-        s_last = (prev == (unsigned)(a.splits - 1));
+        s_last = (prev == (unsigned)(ns - 1));
     }
     __syncthreads();
     if (!s_last) return;
@@ -632,16 +666,22 @@ __global__ void __launch_bounds__(kThreads) pairs_kernel(const __grid_constant__
     const size_t cs = (size_t)a.splits * a.part_ld;
     for (int q = threadIdx.x; q < RB; q += kThreads) {
         const int i = row0 + q;
+        if constexpr (!TR::kW && !TR::kSV) {
+            float m, s;
+            merge_lse_splits<16>(a.part, (size_t)a.part_ld, a.splits, ns, i, m, s);
+            epilogue<D, MODE>(a, i, m, s, nullptr);
+            continue;
+        }
         float m = kNegBig, s = 0.f, acc[KA];
 #pragma unroll
         for (int k = 0; k < KA; ++k) acc[k] = 0.f;
         // splits in groups of 8: all loads of a group are issued before the
         // first merge, so the L2 round trips overlap instead of serialising
-        for (int p0 = 0; p0 < a.splits; p0 += 8) {
+        for (int p0 = 0; p0 < ns; p0 += 8) {
             float m2[8], s2[8], a2[8][KA];
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
-                const bool live = p0 + u < a.splits;
+                const bool live = p0 + u < ns;
                 const float* P = a.part + (size_t)(live ? p0 + u : 0) * a.part_ld + i;
                 m2[u] = kNegBig;
                 s2[u] = 0.f;
@@ -1003,9 +1043,39 @@ static void plan_segment(PairArgs& a, int n_cols, int RB, int slots, unsigned* c
     a.cols_per_split = pl.cols_per_split;
     a.splits = pl.splits;
     a.n_rb = pl.n_rb;
+    a.n_hi = pl.n_rb;
+    a.cps_lo = pl.cols_per_split;
     a.part_ld = pl.n_rb * RB;
     a.counters = counters;
 }
+
+// A one-wave plan that uses exactly `budget` CTAs: every row block gets s or
+// s + 1 column splits (the first n_hi row blocks s + 1), so that with budget
+// = resident capacity every SM holds the same number of CTAs of nearly the
+// same work.  (With a uniform split count the grid falls short of the
+// capacity, and the SMs that hold a full complement finish last.)
+static void fill_segment(PairArgs& a, int n_cols, int budget, int unit) {
+    const int units = (n_cols + unit - 1) / unit;
+    const long long total = std::min<long long>(budget, (long long)a.n_rb * units);
+    const int s = (int)(total / a.n_rb);
+    const int extra = (int)(total - (long long)s * a.n_rb);
+    // with few splits per row block, s and s + 1 splits differ too much in
+    // work per CTA (measured slower for s = 1); keep the uniform plan there
+    if (s < 3) return;
+    if (extra == 0) {
+        a.splits = s;
+        a.n_hi = a.n_rb;
+        a.cols_per_split = (units + s - 1) / s * unit;
+        a.cps_lo = a.cols_per_split;
+    } else {
+        a.splits = s + 1;
+        a.n_hi = extra;
+        a.cols_per_split = (units + s) / (s + 1) * unit;
+        a.cps_lo = (units + s - 1) / s * unit;
+    }
+}
+
+static int seg_ctas(const PairArgs& a) { return a.n_hi * a.splits + (a.n_rb - a.n_hi) * (a.splits - 1); }
 
 // Plans and launches one or two all-pairs passes of one kernel family in a
 // single grid.  seg[k] covers seg[k].n_rows rows x n_cols[k] columns; with
@@ -1031,25 +1101,32 @@ static cov_status run_pairs(cov_ctx* ctx, int d, int family, PairArgs* seg, cons
         launch_pairs_d(d, R, family, PairLaunch{}, 0, st, &occ);
     const int slots = std::max(1, std::min(ctx->num_sms * std::min(occ, ctx->ctas_per_sm), kMaxSlots));
     const int nacc = family == M_SVGD ? d : ((family == M_WY || family == M_WX || family == M_GW) ? 2 + d : 2);
+    // uniform plan; when it is one wave that already fills at least half the
+    // slots, re-plan to fill them exactly (CUDA-core kernel)
+    auto plan = [&](PairArgs& a, int nc, int budget, unsigned* cnt) {
+        plan_segment(a, nc, RB, budget, cnt, unit, fixed_cost);
+        const long long ctas = (long long)a.n_rb * a.splits;
+        if (!tc && ctas <= budget && 2 * ctas >= budget && budget > a.n_rb) fill_segment(a, nc, budget, unit);
+    };
     PairLaunch L{};
     if (nseg == 1) {
-        plan_segment(seg[0], n_cols[0], RB, slots, counters + cnt_off[0], unit, fixed_cost);
+        plan(seg[0], n_cols[0], slots, counters + cnt_off[0]);
         L.seg[0] = seg[0];
         L.seg[1] = seg[0];
-        L.ctas0 = seg[0].n_rb * seg[0].splits;
+        L.ctas0 = seg_ctas(seg[0]);
     } else {
         const double w0 = (double)seg[0].n_rows * n_cols[0], w1 = (double)seg[1].n_rows * n_cols[1];
         int s0 = (int)llround(slots * w0 / (w0 + w1));
         s0 = std::max(1, std::min(s0, slots - 1));
         const int s1 = std::max(1, slots - s0);
-        plan_segment(seg[0], n_cols[0], RB, s0, counters + cnt_off[0], unit, fixed_cost);
-        plan_segment(seg[1], n_cols[1], RB, s1, counters + cnt_off[1], unit, fixed_cost);
+        plan(seg[0], n_cols[0], s0, counters + cnt_off[0]);
+        plan(seg[1], n_cols[1], s1, counters + cnt_off[1]);
         seg[1].part = seg[0].part + (size_t)nacc * seg[0].splits * seg[0].part_ld;
         L.seg[0] = seg[0];
         L.seg[1] = seg[1];
-        L.ctas0 = seg[0].n_rb * seg[0].splits;
+        L.ctas0 = seg_ctas(seg[0]);
     }
-    const int total = L.ctas0 + (nseg == 2 ? seg[1].n_rb * seg[1].splits : 0);
+    const int total = L.ctas0 + (nseg == 2 ? seg_ctas(seg[1]) : 0);
     const cudaError_t e = tc ? launch_tc_d(d, L, total, st, nullptr) : launch_pairs_d(d, R, family, L, total, st, nullptr);
     return cuda_failed(ctx, e) ? COV_ERR_CUDA : COV_OK;
 }
