@@ -457,7 +457,10 @@ COV_API cov_status cov_solve_backward(cov_ctx* ctx, const cov_problem* prob,
  * results, synchronises).  out[0] = FP32 FFMA lane-ops/s, out[1] = packed
  * f32x2 FMA lane-ops/s (two per instruction), out[2] = ex2.approx lane-ops/s,
  * out[3] = FP64 DFMA lane-ops/s, out[4] = FP64 DFMA dependent latency in
- * SM clock cycles, out[5] = SM clock (MHz) estimated over the probe. */
+ * SM clock cycles, out[5] = SM clock (MHz) estimated over the probe,
+ * out[6] = 2^x values/s computed on the FMA pipe (polynomial, no MUFU),
+ * out[7] = that polynomial's largest relative error against FP64 exp2 on
+ * [-125, 127].  out: 8 doubles. */
 COV_API cov_status cov_probe_peaks(cov_ctx* ctx, int iters, double* out, cov_stream_t stream);
 
 #ifdef __cplusplus

@@ -441,11 +441,11 @@ def cov_solve_batched(ctx: Context, problems, n_outer, us, ss=None, stream=None)
 
 
 def cov_probe_peaks(ctx: Context, iters=4096, stream=None):
-    out = (ctypes.c_double * 6)()
+    out = (ctypes.c_double * 8)()
     st = load().cov_probe_peaks(ctx.h, int(iters), out, _stream(stream))
     ctx._check(st, "cov_probe_peaks")
     keys = ("ffma_lane_ops_s", "ffma2_lane_ops_s", "ex2_lane_ops_s", "dfma_lane_ops_s", "dfma_latency_cycles",
-            "sm_clock_mhz")
+            "sm_clock_mhz", "exp2_fma_values_s", "exp2_fma_max_rel_err")
     return dict(zip(keys, list(out)))
 
 

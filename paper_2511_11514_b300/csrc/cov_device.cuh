@@ -32,6 +32,7 @@ __device__ __forceinline__ float ex2(float x) {
 }
 
 // ---- packed FP32x2 arithmetic (one instruction, two lanes of work) -------
+// (exp2_fma2, 2^x on the FMA pipe, follows the packed helpers below)
 __device__ __forceinline__ uint64_t pk(float2 a) {
     uint64_t r;
     asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a.x), "f"(a.y));
@@ -62,6 +63,30 @@ __device__ __forceinline__ float2 mul2(float2 a, float2 b) {
     asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pk(a)), "l"(pk(b)));
     return upk(d);
 }
+// 2^x for two values on the FMA pipe (no MUFU): Cody–Waite range reduction,
+// x = n + f with n = round(x) found by adding and subtracting 1.5 * 2^23
+// (the sum's low mantissa bits then hold n) and f in [-1/2, 1/2]; 2^f by a
+// degree-5 polynomial whose coefficients interpolate 2^f at the six
+// Chebyshev nodes of [-1/2, 1/2] (max relative error 1.0e-7 with exact
+// coefficients, 2.4e-7 evaluated in FP32, about that of ex2.approx); 2^n
+// added to the exponent field as an integer.  x is clamped to [-125, 127]:
+// below, the result is 2^-125 instead of a smaller number (negligible in
+// the sums it feeds); above, 2^127 (finite but past any overflow guard).
+__device__ __forceinline__ float2 exp2_fma2(float2 x) {
+    x.x = fminf(fmaxf(x.x, -125.f), 127.f);
+    x.y = fminf(fmaxf(x.y, -125.f), 127.f);
+    const float2 shift = make_float2(12582912.f, 12582912.f);
+    const float2 t = add2(x, shift);
+    const float2 f = sub2(x, sub2(t, shift));
+    float2 p = fma2(make_float2(1.3390863e-3f, 1.3390863e-3f), f, make_float2(9.6760318e-3f, 9.6760318e-3f));
+    p = fma2(p, f, make_float2(5.5503570e-2f, 5.5503570e-2f));
+    p = fma2(p, f, make_float2(2.4022107e-1f, 2.4022107e-1f));
+    p = fma2(p, f, make_float2(6.9314718e-1f, 6.9314718e-1f));
+    p = fma2(p, f, make_float2(1.0000001f, 1.0000001f));
+    return make_float2(__int_as_float(__float_as_int(p.x) + (__float_as_int(t.x) << 23)),
+                       __int_as_float(__float_as_int(p.y) + (__float_as_int(t.y) << 23)));
+}
+
 __device__ __forceinline__ float max3f(float a, float b, float c) {
     float d;
     asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));

@@ -16,6 +16,15 @@ constexpr int kTcColGroups = kTcSoftWarps / 4;     // column groups of a tile, 6
 constexpr int kTcThreads = 32 * (kTcSoftWarps + 1);
 constexpr int kTcTmemCols = 2 * kTcCols;           // two accumulator buffers (all 512 columns of the SM)
 constexpr int kTcMinBlocks = 512 / kTcTmemCols;    // resident CTAs per SM that tensor memory allows
+// Of every 8 exponentials in the tensor-core kernel, how many pairs are
+// taken on the FMA pipe (exp2_fma2) instead of MUFU.  Default 0: measured
+// slower on B300 (its MUFU issues 32 ex2/clk/SM; the polynomial costs ~8
+// more instructions per value than it frees); a build flag
+// -DCOV_TC_POLY_PAIRS=1..4 selects 25..100 %.
+#ifndef COV_TC_POLY_PAIRS
+#define COV_TC_POLY_PAIRS 0
+#endif
+constexpr int kTcPolyPairs = COV_TC_POLY_PAIRS;
 constexpr int kTcRecC = 8;                         // floats per point in the coordinate record
 constexpr int kTcRecH = 4;                         // floats per point in the h record
 constexpr unsigned kTcTileBytes = kTcCols * (kTcRecC + kTcRecH) * 4;

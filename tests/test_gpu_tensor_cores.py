@@ -107,3 +107,14 @@ def test_full_size_double_integrator_workload_sampled_rows_tensor_cores(cov, ctx
 def test_option_is_validated(cov, ctx):
     with pytest.raises(cov.CovError):
         ctx.set_option(cov.OPT_TENSOR_CORES, 2)
+
+
+def test_fma_pipe_exp2_accuracy_and_rate(cov, ctx):
+    """2^x on the FMA pipe (the alternative to MUFU ex2 the tensor-core
+    kernel can take for part of its exponentials): largest relative error
+    against FP64 exp2 on [-125, 127] within 3e-7 (its degree-5 Chebyshev
+    fit is 1.0e-7 in exact arithmetic, 2.4e-7 evaluated in FP32; MUFU
+    ex2.approx is of the same order), and both rates are measured."""
+    pr = cov.cov_probe_peaks(ctx, 256)
+    assert 0.0 < pr["exp2_fma_max_rel_err"] <= 3e-7, pr
+    assert pr["exp2_fma_values_s"] > 0 and pr["ex2_lane_ops_s"] > 0
