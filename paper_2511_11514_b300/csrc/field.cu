@@ -748,9 +748,15 @@ __global__ void sk_centre_kernel(const float* __restrict__ y, int M, int d, cons
                                  float* __restrict__ scal) {
     __shared__ float sh[32][COV_MAX_D + 1];
     float acc[COV_MAX_D + 1];
+#pragma unroll
     for (int k = 0; k <= COV_MAX_D; ++k) acc[k] = 0.f;
+    // components unrolled to the compile-time maximum (registers, not a
+    // stack array), four points per thread in flight
+#pragma unroll 4
     for (int j = threadIdx.x; j < M; j += blockDim.x) {
-        for (int k = 0; k < d; ++k) acc[k] += y[(size_t)j * d + k];
+#pragma unroll
+        for (int k = 0; k < COV_MAX_D; ++k)
+            if (k < d) acc[k] += y[(size_t)j * d + k];
         if (b) acc[COV_MAX_D] += b[j];
     }
     for (int k = 0; k <= COV_MAX_D; ++k)
