@@ -124,11 +124,12 @@ enum {
     COV_OPT_CTAS_PER_SM = 3,     /* cap on resident CTAs per SM planned for, 1..8 (default 8; the register budget may allow fewer) */
     COV_OPT_USE_GRAPH = 4,       /* cov_solve: capture one outer iteration in a CUDA graph (default 1) */
     COV_OPT_SPIN_LIMIT = 5,      /* bounded-wait iteration limit, >= 0 (default 1<<22) */
-    COV_OPT_TENSOR_CORES = 6     /* 1: Sinkhorn updates with a fixed row offset form their exponents with
-                                    tcgen05 kind::tf32 MMAs on TF32-split operands (d <= 3); 0: FP32 FMAs
-                                    on the CUDA cores (default 0).  The tensor-core path is faster for
-                                    launches of ~1e9 pairs and more; its exponent error grows with the
-                                    size of the exponent terms, (extent / sqrt(eps ln 2))^2 */
+    COV_OPT_TENSOR_CORES = 6     /* Exponents of the Sinkhorn updates with a fixed row offset (d <= 3):
+                                    1: tcgen05 kind::tf32 MMAs on TF32-split operands; 0: FP32 FMAs on
+                                    the CUDA cores; 2 (default): the tensor cores for field evaluations
+                                    whose launches are all of at least 2^30 pair evaluations (where they
+                                    are faster), the CUDA cores otherwise.  The tensor-core exponent error
+                                    grows with the size of the exponent terms, (extent / sqrt(eps ln 2))^2 */
 };
 COV_API cov_status cov_ctx_set_option(cov_ctx* ctx, int key, long long value);
 

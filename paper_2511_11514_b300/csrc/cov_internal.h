@@ -34,7 +34,7 @@ struct cov_ctx {
     int threads = 128;
     int ctas_per_sm = 8;
     int use_graph = 1;
-    int use_tc = 0;            // tensor-core exponents for the fixed-offset Sinkhorn updates
+    int use_tc = 2;            // tensor-core exponents: 0 off, 1 on, 2 for launches of >= 2^30 pairs
     long long spin_limit = 1LL << 22;
     std::string last_cuda_error;
     cov_graph_cache solve_graph;

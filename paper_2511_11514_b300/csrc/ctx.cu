@@ -155,7 +155,7 @@ extern "C" cov_status cov_ctx_set_option(cov_ctx* ctx, int key, long long value)
             ctx->spin_limit = value;
             break;
         case COV_OPT_TENSOR_CORES:
-            if (value != 0 && value != 1) return COV_ERR_INVALID_ARG;
+            if (value < 0 || value > 2) return COV_ERR_INVALID_ARG;
             ctx->use_tc = (int)value;
             break;
         default:

@@ -1234,8 +1234,12 @@ cov_status sinkhorn_field_ws(cov_ctx* ctx, void* ws, size_t ws_bytes, const floa
     cov_status r = COV_OK;
     // the tensor-core records of the current state (after the prep or a
     // rescale; every update's epilogue then keeps its rows' h records current)
-    // records are kept only while the tensor-core path is enabled
-    const bool recs = B.c0x != nullptr && ctx->use_tc;
+    // records are kept only when the tensor-core path will run: always with
+    // the option at 1; with it at 2 when both launches of an iteration
+    // (g + p: M T + T^2 pairs, f: T M pairs) are of at least 2^30 pairs
+    const long long pairs_min = std::min((long long)M * T + (long long)T * T, (long long)T * M);
+    const bool want_tc = ctx->use_tc == 1 || (ctx->use_tc == 2 && pairs_min >= kTcAutoPairs);
+    const bool recs = B.c0x != nullptr && want_tc;
     auto build_records = [&]() {
         if (!recs) return;
         const int nb = (np + 255) / 256;

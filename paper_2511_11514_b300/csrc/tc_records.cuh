@@ -16,6 +16,10 @@ constexpr int kTcColGroups = kTcSoftWarps / 4;     // column groups of a tile, 6
 constexpr int kTcThreads = 32 * (kTcSoftWarps + 1);
 constexpr int kTcTmemCols = 2 * kTcCols;           // two accumulator buffers (all 512 columns of the SM)
 constexpr int kTcMinBlocks = 512 / kTcTmemCols;    // resident CTAs per SM that tensor memory allows
+// Launch size from which the automatic setting takes the tensor cores: there
+// the tensor-core kernel measured 7-10 % faster than the CUDA-core one, below
+// it slower (one 544-thread CTA per SM is too coarse for short launches).
+constexpr long long kTcAutoPairs = 1LL << 30;
 // Of every 8 exponentials in the tensor-core kernel, how many pairs are
 // taken on the FMA pipe (exp2_fma2) instead of MUFU.  Default 0: measured
 // slower on B300 (its MUFU issues 32 ex2/clk/SM; the polynomial costs ~8

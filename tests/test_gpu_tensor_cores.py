@@ -7,8 +7,9 @@ bars are those of the plain field (potentials max|f - f_orc| / eps <= 1e-4,
 field norm-wise 1e-4): the split keeps every product exact and the tensor
 core's FP32 accumulation adds an error of about 1e-5 bits per exponent at
 these magnitudes, below the MUFU ex2.approx error budget the bars allow.
-The CUDA-core path (COV_OPT_TENSOR_CORES = 0, the default) is held to the
-same bars, and the two paths to each other.
+The CUDA-core path (COV_OPT_TENSOR_CORES = 0; the default, 2, takes it for
+launches under 2^30 pairs) is held to the same bars, and the two paths to
+each other.
 """
 import numpy as np
 import pytest
@@ -38,7 +39,7 @@ def _run(cov, ctx, x, y, b, eps, n_iter, tc, **kw):
     try:
         out = cov.cov_field_sinkhorn(ctx, dev32(x), dev32(y), eps, n_iter, b=None if b is None else dev32(b), **kw)
     finally:
-        ctx.set_option(cov.OPT_TENSOR_CORES, 0)
+        ctx.set_option(cov.OPT_TENSOR_CORES, cov.TENSOR_CORES_AUTO)
     st, flags = ctx.device_status()
     assert st == cov.COV_OK, flags
     return out
@@ -99,14 +100,14 @@ def test_full_size_double_integrator_workload_sampled_rows_tensor_cores(cov, ctx
     try:
         errs = _sampled_rows_check(cov, ctx, orc, x, inst.y, w.eps, w.n_iter - 1, 512, seed=3)
     finally:
-        ctx.set_option(cov.OPT_TENSOR_CORES, 0)
+        ctx.set_option(cov.OPT_TENSOR_CORES, cov.TENSOR_CORES_AUTO)
     assert max(errs[:3]) <= POT_TOL, errs
     assert errs[3] <= FIELD_TOL, errs
 
 
 def test_option_is_validated(cov, ctx):
     with pytest.raises(cov.CovError):
-        ctx.set_option(cov.OPT_TENSOR_CORES, 2)
+        ctx.set_option(cov.OPT_TENSOR_CORES, 3)
 
 
 def test_fma_pipe_exp2_accuracy_and_rate(cov, ctx):
