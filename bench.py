@@ -75,6 +75,10 @@ def parse_args():
     ap.add_argument("--variants", action="store_true",
                     help="measure the Sinkhorn variants at eps = 0.002: iterations to a field accuracy, "
                          "cold vs eps-scaled vs warm-started")
+    ap.add_argument("--horizon-sweep", action="store_true",
+                    help="solve time against the horizon T in the shape of the paper's timing study: Stein field "
+                         "(unicycle, T = 100..10000) and Sinkhorn field (double integrator, M = T, T = 100..2500), "
+                         "on the GPU and on the FP64 oracle (context, not the headline)")
     ap.add_argument("--tensor-cores", action="store_true",
                     help="form the fixed-offset updates' exponents on the tensor cores (COV_OPT_TENSOR_CORES)")
     ap.add_argument("--adjoint-outer", type=int, default=0,
@@ -800,8 +804,94 @@ def run_variants(args):
     return 0
 
 
+def run_horizon_sweep(args):
+    """Coverage-solve time against the horizon T, GPU (this library, one
+    B300) against the FP64 oracle on the host cores, in the shape of the
+    paper's timing study (solve time vs horizon, GPU vs CPU).  The paper's
+    differential-drive and aircraft models are not specified; the Stein
+    points use the unicycle (the differential drive's kinematic form) with a
+    3-component mixture, h = 0.05, eta = 1e-3, K = 100 outer iterations; the
+    Sinkhorn points the double integrator with M = T reference samples of an
+    8-component mixture, eps = 0.005, 50 iterations, eta = 0.5, K = 20 outer
+    iterations.  GPU: `cov_solve` for K outer iterations (CUDA events, after
+    an untimed call that captures the graph and caches the gains).  Oracle
+    (the CPU baseline of this sweep): timed over k <= K outer iterations,
+    k chosen so that each point costs ~1 s of host time, and scaled to K
+    ("extrapolated" where k < K)."""
+    import torch
+
+    import oracle as orc
+    from paper_2511_11514_b300 import binding as cov
+
+    orc.build()
+    orc.set_threads(os.cpu_count() or 1)
+    torch.cuda.set_device(0)
+    ctx = cov.Context(0)
+    dev = torch.device("cuda", 0)
+    points = []
+    specs = [("svgd", T) for T in (100, 256, 500, 1000, 2000, 5000, 10000)] + \
+            [("sinkhorn", T) for T in (100, 200, 500, 1000, 2500)]
+    for kind, T in specs:
+        if kind == "svgd":
+            w = dataclasses.replace(wl.SVGD_SINGLE_T256, name=f"svgd_unicycle_T{T}", model=wl.UNICYCLE, T=T,
+                                    dt=0.01, n_outer=100)
+            inst = wl.make_instance(w)
+            gmm = tuple(wl.f32_pair(v)[1] for v in inst.gmm)
+            prob = cov.make_problem(w.model, T, w.dt, inst.s0, w.field, inst.Q, inst.R, w.eta, gmm=gmm, h=w.h)
+            oracle_kw = dict(gmm=gmm, h=w.h)
+            pairs_outer = T * T
+        else:
+            w = dataclasses.replace(wl.SINKHORN_DOUBLE_T4096, name=f"sinkhorn_double_integrator_T{T}", T=T, M=T,
+                                    n_outer=20)
+            inst = wl.make_instance(w)
+            y = torch.as_tensor(inst.y, dtype=torch.float32, device=dev)
+            prob = cov.make_problem(w.model, T, w.dt, inst.s0, w.field, inst.Q, inst.R, w.eta, y=y, eps=w.eps,
+                                    n_iter=w.n_iter)
+            oracle_kw = dict(y=inst.y, eps=w.eps, n_iter=w.n_iter)
+            pairs_outer = w.n_iter * (2 * T * T + T * T) + (T * T + T * T)
+        K = w.n_outer
+        u0 = torch.as_tensor(inst.u0, dtype=torch.float64, device=dev)
+        u = u0.clone()
+        cov.cov_solve(ctx, prob, K, u)        # graph capture, gains
+        ts = []
+        for _ in range(3):
+            u.copy_(u0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            cov.cov_solve(ctx, prob, K, u)
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        gpu_ms = statistics.median(ts)
+        # oracle: one outer iteration to size the sample, then k of them
+        t0 = time.perf_counter()
+        orc.solve(w.model, w.dt, inst.s0, inst.u0, w.field, inst.Q, inst.R, w.eta, 1, **oracle_kw)
+        one = time.perf_counter() - t0
+        k = int(max(1, min(K, round(1.0 / max(one, 1e-6)))))
+        t0 = time.perf_counter()
+        orc.solve(w.model, w.dt, inst.s0, inst.u0, w.field, inst.Q, inst.R, w.eta, k, **oracle_kw)
+        cpu_ms = (time.perf_counter() - t0) * 1e3 * K / k
+        points.append({"field": kind, "T": T, "M": T if kind == "sinkhorn" else 0, "outer_iterations": K,
+                       "gpu_ms_per_solve": gpu_ms, "cpu_ms_per_solve": cpu_ms,
+                       "cpu_outer_iterations_timed": k, "cpu_extrapolated": k < K,
+                       "speedup": cpu_ms / gpu_ms, "gpu_pair_evals_per_s": K * pairs_outer / (gpu_ms * 1e-3)})
+        print(json.dumps(points[-1]), file=sys.stderr, flush=True)
+    st, flags = ctx.device_status()
+    if st != cov.COV_OK:
+        raise SystemExit(f"device status {cov.status_string(st)} flags {flags}")
+    ctx.close()
+    line = {"metric": "coverage solve time vs horizon, GPU vs FP64 oracle (context)", "value": None, "unit": "ms",
+            "higher_is_better": False, "n_gpus": 1, "dtype": "f32 fields, f64 LQR/rollout",
+            "data": "synthetic (seeded Philox mixtures)", "cpu_cores": orc.get_threads(), "points": points}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse_args()
+    if args.horizon_sweep:
+        return run_horizon_sweep(args)
     if args.variants:
         return run_variants(args)
     if args.impl == "reference":
