@@ -304,7 +304,7 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     w = wl.WORKLOADS[args.workload]
     if w.field != wl.FIELD_SINKHORN:
-        raise SystemExit("bench.py times the Sinkhorn workloads")
+        return run_svgd(args, w, rank, local_rank, world)
     inst = wl.make_instance(w, seed=w.seed + rank)
     ctx = cov.Context(local_rank)
     if args.tensor_cores:
@@ -496,6 +496,134 @@ def run_ours(args):
         }
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(inst, args.cpu_seconds)
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def run_svgd(args, w, rank, local_rank, world):
+    """The Stein-field workload (latency-bound: T^2 pair evaluations per
+    field).  A step is one outer iteration through `cov_solve_continue`;
+    the line reports pair-evals/s and ms per coverage solve (100 outer
+    iterations).  The roofline of its all-pairs pass (8 FP32 operations and
+    one exponential per pair: 2 subtractions and 2 FMA for the distance, 4
+    FMA to accumulate) is reported for context; a field of 65536 pairs is a
+    few microseconds, far from steady state."""
+    import torch
+    import torch.distributed as dist
+
+    import oracle as orc
+    from paper_2511_11514_b300 import binding as cov
+
+    inst = wl.make_instance(w, seed=w.seed + rank)
+    ctx = cov.Context(local_rank)
+    dev = torch.device("cuda", local_rank)
+    gmm = tuple(wl.f32_pair(v)[1] for v in inst.gmm)
+    prob = cov.make_problem(w.model, w.T, w.dt, inst.s0, w.field, inst.Q, inst.R, w.eta, gmm=gmm, h=w.h)
+    u = torch.as_tensor(inst.u0, dtype=torch.float64, device=dev).contiguous()
+    s = cov.cov_solve(ctx, prob, 0, u)
+    stream = torch.cuda.current_stream()
+    for _ in range(max(3, args.warmup)):
+        cov.cov_solve_continue(ctx, prob, 1, u, s)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clocks = Clocks(local_rank)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.2)
+    torch.cuda.profiler.start()
+    for k in range(args.steps):
+        flush.zero_()
+        ev0[k].record(stream)
+        cov.cov_solve_continue(ctx, prob, 1, u, s)
+        ev1[k].record(stream)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    total_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in zip(ev0, ev1)), world, dev)
+    st, flags = ctx.device_status()
+    if st != cov.COV_OK:
+        raise SystemExit(f"device status {cov.status_string(st)} flags {flags}")
+    pairs_step = w.T * w.T
+    ms_per_step = total_ms / args.steps
+    # the all-pairs pass alone
+    x = s[1:, :2].float().contiguous()
+    cov.cov_field_svgd(ctx, x, w.h, gmm=gmm)
+    ts = []
+    for _ in range(20):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        cov.cov_field_svgd(ctx, x, w.h, gmm=gmm)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    field_ms = statistics.median(ts)
+    probe = cov.cov_probe_peaks(ctx, 4096)
+    clk_hz = SM_MAX_MHZ_NOMINAL * 1e6
+    fp32 = SM_COUNT_NOMINAL * FP32_LANES_PER_SM_CLK * clk_hz / 8
+    mufu = SM_COUNT_NOMINAL * 32 * clk_hz
+    peak = min(fp32, mufu)
+    # end to end: controls and reference parameters from pinned host memory
+    u_h = torch.as_tensor(inst.u0, dtype=torch.float64).pin_memory()
+    u_out = torch.empty_like(u_h).pin_memory()
+    s_out = torch.empty((w.T + 1, s.shape[1]), dtype=torch.float64).pin_memory()
+    e_ms = []
+    for k in range(args.e2e_steps + 2):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush.zero_()
+        a.record(stream)
+        u.copy_(u_h, non_blocking=True)
+        cov.cov_solve(ctx, prob, 1, u, s)
+        u_out.copy_(u, non_blocking=True)
+        s_out.copy_(s, non_blocking=True)
+        b.record(stream)
+        b.synchronize()
+        if k >= 2:
+            e_ms.append(a.elapsed_time(b))
+    e2e_ms = statistics.mean(e_ms)
+    launches = count_library_launches(lambda: cov.cov_solve_continue(ctx, prob, 1, u, s))
+    if rank == 0:
+        line = {"metric": METRIC, "value": job_value(world, pairs_step, args.steps, total_ms), "unit": UNIT,
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic (seeded Philox Gaussian-mixture reference)",
+                "config": {"workload": w.name, "T": w.T, "d": 2, "h": w.h, "model": "single_integrator",
+                           "reference": f"{w.gmm_K}-component Gaussian mixture (score in closed form)",
+                           "pairs_per_step": pairs_step, "outer_iterations_per_solve": w.n_outer,
+                           "ms_per_coverage_solve": ms_per_step * w.n_outer,
+                           "precision": "f32 field, f64 LQR and rollout",
+                           "parallelism": f"{world} independent problems (one per GPU)" if world > 1 else "single GPU",
+                           "l2": "flushed between steps (256 MiB write outside the per-step CUDA events)"},
+                "roofline": {"bound": "alu", "achieved": pairs_step / (field_ms * 1e-3) / 1e9, "peak": peak / 1e9,
+                             "unit": "Gpair/s", "frac": pairs_step / (field_ms * 1e-3) / peak, "traffic": None,
+                             "kernel": "pairs_kernel<2, R, M_SVGD> with the mixture score (cov_field_svgd)",
+                             "peak_basis": "148 SMs x 2032 MHz x min(32 ex2, 128 FP32 lanes / 8 ops per pair)",
+                             "note": f"one field = {pairs_step} pairs in {field_ms * 1e3:.1f} us: launch- and "
+                                     "latency-bound, not graded against the roofline", "probe": probe},
+                "clocks": clk,
+                "e2e": {"value": pairs_step / (e2e_ms * 1e-3), "unit": UNIT,
+                        "h2d_bytes_per_step": u_h.numel() * 8,
+                        "d2h_bytes_per_step": u_out.numel() * 8 + s_out.numel() * 8, "ms_per_step": e2e_ms},
+                "gpu_launches": launches * args.steps}
+        if world == 1 and not args.no_cpu_baseline:
+            orc.build()
+            orc.set_threads(os.cpu_count() or 1)
+            orc.solve(w.model, w.dt, inst.s0, inst.u0, w.field, inst.Q, inst.R, w.eta, 2, gmm=gmm, h=w.h)
+            t0 = time.perf_counter()
+            orc.solve(w.model, w.dt, inst.s0, inst.u0, w.field, inst.Q, inst.R, w.eta, w.n_outer, gmm=gmm, h=w.h)
+            dt = time.perf_counter() - t0
+            line["cpu_baseline"] = {"value": w.n_outer * pairs_step / dt, "unit": UNIT, "cores": orc.get_threads(),
+                                    "kind": "oracle",
+                                    "sample": f"FP64 oracle: the whole coverage solve ({w.n_outer} outer "
+                                              f"iterations) in {dt:.2f} s, {orc.get_threads()} threads",
+                                    "ms_per_coverage_solve": dt * 1e3}
         print(json.dumps(line), flush=True)
     ctx.close()
     if world > 1:

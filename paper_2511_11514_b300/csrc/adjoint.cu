@@ -616,6 +616,7 @@ static VjpBufs carve_vjp(Carver& cv, int d, int Tp, int Mp) {
 
 __global__ void vjp_init_kernel(const float* __restrict__ abar, int abar_ld, int T, int M, int d, int Tp, int Mp,
                                 VjpBufs v, unsigned* status) {
+    pdl_prologue();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < Tp) {
         bool ok = true;
@@ -655,6 +656,7 @@ __global__ void __launch_bounds__(1024) vjp_finish_kernel(VjpBufs v, int T, int 
                                                           float* __restrict__ xbar, int xbar_ld,
                                                           float* __restrict__ ybar, float* __restrict__ bbar,
                                                           int accumulate, unsigned* status) {
+    pdl_prologue();
     __shared__ double sh[32];
     const int tid = threadIdx.x, nt = blockDim.x;
     bool ok = true;
@@ -731,7 +733,7 @@ cov_status sinkhorn_vjp_ws(cov_ctx* ctx, void* ws, size_t ws_bytes, const float*
     if (cv.off > ws_bytes) return COV_ERR_WORKSPACE;
     const int n = n_iter, Tp = tp.Tp, Mp = tp.Mp;
     const int np = std::max(std::max(Tp, Mp), 2 * v.cnt_ld);
-    vjp_init_kernel<<<(np + 255) / 256, 256, 0, stream>>>(abar, abar_ld, T, M, d, Tp, Mp, v, ctx->status);
+    launch_pdl(vjp_init_kernel, dim3((np + 255) / 256), dim3(256), 0, stream, abar, abar_ld, T, M, d, Tp, Mp, v, ctx->status);
     if (cuda_failed(ctx, cudaGetLastError())) return COV_ERR_CUDA;
 
     auto hx = [&](int t) { return tp.hx + (size_t)t * Tp; };
@@ -817,7 +819,7 @@ cov_status sinkhorn_vjp_ws(cov_ctx* ctx, void* ws, size_t ws_bytes, const float*
         if (r != COV_OK) return r;
         cur ^= 1;
     }
-    vjp_finish_kernel<<<1, 1024, 0, stream>>>(v, T, M, d, Tp, Mp, b, tp.scal, xbar, xbar_ld, ybar, bbar,
+    launch_pdl(vjp_finish_kernel, dim3(1), dim3(1024), 0, stream, v, T, M, d, Tp, Mp, b, tp.scal, xbar, xbar_ld, ybar, bbar,
                                               accumulate, ctx->status);
     if (cuda_failed(ctx, cudaGetLastError())) return COV_ERR_CUDA;
     return COV_OK;

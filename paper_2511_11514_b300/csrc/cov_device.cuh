@@ -221,6 +221,16 @@ __device__ __forceinline__ void tmem_wait_ld(uint32_t (&v)[32]) {
                  : "memory");
 }
 
+// Programmatic dependent launch, first statement of a kernel launched with
+// launch_pdl: wait until the previous grid in the stream has completed and
+// its writes are visible, then let the next grid start launching.  Waiting
+// first keeps the chain's guarantee: once a grid has started, the grid two
+// launches back has completed.
+__device__ __forceinline__ void pdl_prologue() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" :::);
+}
+
 // L2-coherent loads for data written by other CTAs of the same launch.
 __device__ __forceinline__ float ld_cg(const float* p) { return __ldcg(p); }
 

@@ -75,6 +75,25 @@ inline size_t round_up(size_t x, size_t m) { return (x + m - 1) / m * m; }
 // Records a CUDA error on the context; returns true if `e` is an error.
 bool cuda_failed(cov_ctx* ctx, cudaError_t e);
 
+// Launch with programmatic stream serialisation allowed: the kernel may
+// start while the previous grid in the stream finishes, and must begin with
+// pdl_prologue() (cov_device.cuh) before touching global memory.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                       Args&&... args) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // A call is about to write scratch over the workspace: forget what cov_solve
 // cached there (time-invariant gains, forward records).
 inline void clobber_ws_caches(cov_ctx* ctx) {

@@ -746,6 +746,7 @@ namespace cov {
 // scal layout: [0..5] centre, [8] 1/sum(b) (or 0 when b == NULL)
 __global__ void sk_centre_kernel(const float* __restrict__ y, int M, int d, const float* __restrict__ b,
                                  float* __restrict__ scal) {
+    pdl_prologue();
     __shared__ float sh[32][COV_MAX_D + 1];
     float acc[COV_MAX_D + 1];
 #pragma unroll
@@ -791,6 +792,7 @@ __global__ void sk_prep_kernel(const float* __restrict__ x, int x_ld, int T, con
                                const float* __restrict__ b, int d, float inv_sigma, float inv_epsln2,
                                float log2a, int warm, const float* __restrict__ f, const float* __restrict__ g,
                                const float* __restrict__ p, SkBufs B, unsigned* status) {
+    pdl_prologue();
     const float* c = B.scal;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < B.Tp) {
@@ -837,6 +839,7 @@ __global__ void sk_prep_kernel(const float* __restrict__ x, int x_ld, int T, con
 __global__ void sk_finish_kernel(int T, int M, float epsln2, float log2a, SkBufs B, const float* __restrict__ hp,
                                  float* __restrict__ f, float* __restrict__ g, float* __restrict__ p,
                                  unsigned* status) {
+    pdl_prologue();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     bool ok = true;
     if (i < T) {
@@ -867,6 +870,7 @@ __global__ void sk_finish_kernel(int T, int M, float epsln2, float log2a, SkBufs
 //   hx_new = log2 a + f/(eps_new ln2) - |xhat_new|^2  (likewise hy with log2 b, hp).
 __global__ void sk_rescale_kernel(SkBufs B, int T, int M, int d, float ratio, float erat, float log2a,
                                   float* __restrict__ hp, unsigned* status) {
+    pdl_prologue();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     bool ok = true;
     if (i < B.Tp) {
@@ -1180,7 +1184,7 @@ size_t sinkhorn_split_bytes(int T, int M, int d) {
 }
 
 void sinkhorn_reference_stats(const float* y, int M, int d, const float* b, float* scal, cudaStream_t stream) {
-    sk_centre_kernel<<<1, 1024, 0, stream>>>(y, M, d, b, scal);
+    launch_pdl(sk_centre_kernel, dim3(1), dim3(1024), 0, stream, y, M, d, b, scal);
 }
 
 size_t sinkhorn_ws_bytes(int T, int M, int d) {
@@ -1215,9 +1219,9 @@ cov_status sinkhorn_field_ws(cov_ctx* ctx, void* ws, size_t ws_bytes, const floa
     if (scal_given)
         B.scal = const_cast<float*>(scal_given);
     else
-        sk_centre_kernel<<<1, 1024, 0, stream>>>(y, M, d, b, B.scal);
+        launch_pdl(sk_centre_kernel, dim3(1), dim3(1024), 0, stream, y, M, d, b, B.scal);
     const int np = std::max(B.Tp, B.Mp);
-    sk_prep_kernel<<<(np + 255) / 256, 256, 0, stream>>>(x, x_ld, T, y, M, b, d, (float)(1.0 / sqrt(epsln2_0)),
+    launch_pdl(sk_prep_kernel, dim3((np + 255) / 256), dim3(256), 0, stream, x, x_ld, T, y, M, b, d, (float)(1.0 / sqrt(epsln2_0)),
                                                          (float)(1.0 / epsln2_0), log2a, warm, f, g, p, B,
                                                          ctx->status);
     PairArgs base{};
@@ -1244,13 +1248,13 @@ cov_status sinkhorn_field_ws(cov_ctx* ctx, void* ws, size_t ws_bytes, const floa
         if (!recs) return;
         const int nb = (np + 255) / 256;
         if (d == 1)
-            tc_records_kernel<1><<<nb, 256, 0, stream>>>(B.xs, B.Tp, B.ys, B.Mp, B.hx, hp_cur, hp_nxt, B.hy, B.c0x,
+            launch_pdl(tc_records_kernel<1>, dim3(nb), dim3(256), 0, stream, B.xs, B.Tp, B.ys, B.Mp, B.hx, hp_cur, hp_nxt, B.hy, B.c0x,
                                                          B.c0y, B.hrx, hrp_cur, hrp_nxt, B.hry);
         else if (d == 2)
-            tc_records_kernel<2><<<nb, 256, 0, stream>>>(B.xs, B.Tp, B.ys, B.Mp, B.hx, hp_cur, hp_nxt, B.hy, B.c0x,
+            launch_pdl(tc_records_kernel<2>, dim3(nb), dim3(256), 0, stream, B.xs, B.Tp, B.ys, B.Mp, B.hx, hp_cur, hp_nxt, B.hy, B.c0x,
                                                          B.c0y, B.hrx, hrp_cur, hrp_nxt, B.hry);
         else
-            tc_records_kernel<3><<<nb, 256, 0, stream>>>(B.xs, B.Tp, B.ys, B.Mp, B.hx, hp_cur, hp_nxt, B.hy, B.c0x,
+            launch_pdl(tc_records_kernel<3>, dim3(nb), dim3(256), 0, stream, B.xs, B.Tp, B.ys, B.Mp, B.hx, hp_cur, hp_nxt, B.hy, B.c0x,
                                                          B.c0y, B.hrx, hrp_cur, hrp_nxt, B.hry);
         first = true;
     };
@@ -1260,7 +1264,7 @@ cov_status sinkhorn_field_ws(cov_ctx* ctx, void* ws, size_t ws_bytes, const floa
     auto to_eps = [&](double e_new) {
         if (e_new == eps_cur) return;
         const int nb = (np + 255) / 256;
-        sk_rescale_kernel<<<nb, 256, 0, stream>>>(B, T, M, d, (float)sqrt(eps_cur / e_new), (float)(eps_cur / e_new),
+        launch_pdl(sk_rescale_kernel, dim3(nb), dim3(256), 0, stream, B, T, M, d, (float)sqrt(eps_cur / e_new), (float)(eps_cur / e_new),
                                                   log2a, hp_cur, ctx->status);
         eps_cur = e_new;
         first = true;
@@ -1346,7 +1350,7 @@ cov_status sinkhorn_field_ws(cov_ctx* ctx, void* ws, size_t ws_bytes, const floa
     }
     if (f || g || p) {
         const int nf = std::max(T, M);
-        sk_finish_kernel<<<(nf + 255) / 256, 256, 0, stream>>>(T, M, (float)epsln2, log2a, B, hp_cur, f, g, p,
+        launch_pdl(sk_finish_kernel, dim3((nf + 255) / 256), dim3(256), 0, stream, T, M, (float)epsln2, log2a, B, hp_cur, f, g, p,
                                                                ctx->status);
     }
     if (cuda_failed(ctx, cudaGetLastError())) return COV_ERR_CUDA;
@@ -1360,6 +1364,7 @@ cov_status sinkhorn_field_ws(cov_ctx* ctx, void* ws, size_t ws_bytes, const floa
 // self update whose log-sum-exp normalises the self term of the field.
 // ---------------------------------------------------------------------------
 __global__ void tape_pad_kernel(SkTape tp) {
+    pdl_prologue();
     // padding entries of every history slot: hx (n+1 slots) and hp (n+2
     // slots) over [T, Tp), hy (n+1 slots) over [M, Mp)
     const int n = tp.n_iter;
@@ -1431,12 +1436,12 @@ cov_status sinkhorn_tape_ws(cov_ctx* ctx, void* ws, size_t ws_bytes, const float
     if (scal_given)
         B.scal = const_cast<float*>(scal_given);
     else
-        sk_centre_kernel<<<1, 1024, 0, stream>>>(y, M, d, b, B.scal);
+        launch_pdl(sk_centre_kernel, dim3(1), dim3(1024), 0, stream, y, M, d, b, B.scal);
     const int np = std::max(B.Tp, B.Mp);
-    sk_prep_kernel<<<(np + 255) / 256, 256, 0, stream>>>(x, x_ld, T, y, M, b, d, (float)(1.0 / tp.sigma),
+    launch_pdl(sk_prep_kernel, dim3((np + 255) / 256), dim3(256), 0, stream, x, x_ld, T, y, M, b, d, (float)(1.0 / tp.sigma),
                                                          (float)(1.0 / epsln2), tp.log2a, 0, nullptr, nullptr,
                                                          nullptr, B, ctx->status);
-    tape_pad_kernel<<<std::min(1024, (int)((2LL * n + 2) * B.Tp / 256 + 1)), 256, 0, stream>>>(tp);
+    launch_pdl(tape_pad_kernel, dim3(std::min(1024, (int)((2LL * n + 2) * B.Tp / 256 + 1))), dim3(256), 0, stream, tp);
     if (cuda_failed(ctx, cudaGetLastError())) return COV_ERR_CUDA;
     PairArgs base{};
     base.status = ctx->status;
@@ -1580,6 +1585,7 @@ __device__ __forceinline__ void gmm_score_at(const GmmParams& G, const float* xv
 
 __global__ void gmm_score_kernel(const float* __restrict__ x, int T, int d, GmmParams G, float* __restrict__ out,
                                  unsigned* status) {
+    pdl_prologue();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= T) return;
     float xv[COV_MAX_D], sc[COV_MAX_D];
@@ -1619,6 +1625,7 @@ __device__ __forceinline__ void density_score_at(const float* __restrict__ map, 
 
 __global__ void density_score_kernel(const float* __restrict__ map, int H, int W, const float* __restrict__ x,
                                      int x_ld, int T, float* __restrict__ score, unsigned* status) {
+    pdl_prologue();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= T) return;
     float sc[2];
@@ -1631,7 +1638,7 @@ __global__ void density_score_kernel(const float* __restrict__ map, int H, int W
 cov_status density_score_launch(cov_ctx* ctx, const float* map, int H, int W, const float* x, int x_ld, int T,
                                 float* score, cudaStream_t stream) {
     if (!ctx || !map || !x || !score || T < 1 || H < 2 || W < 2 || x_ld < 2) return COV_ERR_INVALID_ARG;
-    density_score_kernel<<<(T + 255) / 256, 256, 0, stream>>>(map, H, W, x, x_ld, T, score, ctx->status);
+    launch_pdl(density_score_kernel, dim3((T + 255) / 256), dim3(256), 0, stream, map, H, W, x, x_ld, T, score, ctx->status);
     return cuda_failed(ctx, cudaGetLastError()) ? COV_ERR_CUDA : COV_OK;
 }
 
@@ -1639,6 +1646,7 @@ cov_status density_score_launch(cov_ctx* ctx, const float* map, int H, int W, co
 __global__ void svgd_prep_kernel(const float* __restrict__ x, int x_ld, int T, int d, int Tp,
                                  const float* __restrict__ score, GmmParams G, int use_gmm, float inv_hs, float hs,
                                  float* __restrict__ xt, float* __restrict__ st, unsigned* status) {
+    pdl_prologue();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= Tp) return;
     if (i >= T) {
@@ -1702,7 +1710,7 @@ cov_status svgd_field_ws(cov_ctx* ctx, void* ws, size_t ws_bytes, const float* x
     if (cuda_failed(ctx, cudaMemsetAsync(B.counters, 0, sizeof(unsigned) * (B.Tp / 64 + 1), stream)))
         return COV_ERR_CUDA;
     const double r2l = sqrt(2.0 * 0.69314718055994531);
-    svgd_prep_kernel<<<(B.Tp + 255) / 256, 256, 0, stream>>>(x, x_ld, T, d, B.Tp, score, G, use_gmm,
+    launch_pdl(svgd_prep_kernel, dim3((B.Tp + 255) / 256), dim3(256), 0, stream, x, x_ld, T, d, B.Tp, score, G, use_gmm,
                                                              (float)(1.0 / (h * r2l)), (float)(h / r2l), B.xt,
                                                              B.st, ctx->status);
     PairArgs a{};
@@ -1769,7 +1777,7 @@ extern "C" cov_status cov_gmm_score(cov_ctx* ctx, const float* x, int T, int d, 
     const cov_status s = cov::make_gmm_params(gmm, d, &G);
     if (s != COV_OK) return s;
     if (cudaSetDevice(ctx->device) != cudaSuccess) return COV_ERR_CUDA;
-    cov::gmm_score_kernel<<<(T + 255) / 256, 256, 0, (cudaStream_t)stream>>>(x, T, d, G, score, ctx->status);
+    launch_pdl(cov::gmm_score_kernel, dim3((T + 255) / 256), dim3(256), 0, (cudaStream_t)stream, x, T, d, G, score, ctx->status);
     if (cov::cuda_failed(ctx, cudaGetLastError())) return COV_ERR_CUDA;
     return COV_OK;
 }

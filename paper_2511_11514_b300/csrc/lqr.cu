@@ -124,6 +124,7 @@ __global__ void __launch_bounds__(32, 1) riccati_kernel(const double* __restrict
                                                         double* __restrict__ Mg, double* __restrict__ Ng,
                                                         double* __restrict__ Sg, unsigned* status,
                                                         const double* __restrict__ Pinit, int Cc) {
+    pdl_prologue();
     __shared__ __align__(16) RicSmem<N, MC> sm;
     const int lane = threadIdx.x;
     bool spd_ok = true;
@@ -327,6 +328,7 @@ template <int N, int MC>
 __global__ void __launch_bounds__(32, 1) ric_compose_kernel(const double* __restrict__ A, const double* __restrict__ B,
                                                             LqrConst Cq, int T, int Cc,
                                                             double* __restrict__ maps, unsigned* status) {
+    pdl_prologue();
     __shared__ __align__(16) ComposeSmem<N, MC> sm;
     const int lane = threadIdx.x;
     const int lo = blockIdx.x * Cc, hi = min(T, lo + Cc) - 1;
@@ -443,6 +445,7 @@ __global__ void __launch_bounds__(32, 1) ric_compose_kernel(const double* __rest
 template <int N>
 __global__ void __launch_bounds__(32, 1) ric_chain_kernel(const double* __restrict__ maps, int n_chunks, LqrConst Cq,
                                                           double* __restrict__ Pin, unsigned* status) {
+    pdl_prologue();
     constexpr int NN = N * N;
     __shared__ double P[NN], X[NN], W[NN], V[NN], aug[N * 2 * N];
     __shared__ int piv;
@@ -503,6 +506,7 @@ __global__ void __launch_bounds__(32) compose_kernel(const double* __restrict__ 
                                                      const double* __restrict__ kg, const double* __restrict__ cin,
                                                      int T, int C, double* __restrict__ force,
                                                      double* __restrict__ maps) {
+    pdl_prologue();
     extern __shared__ __align__(16) double dyn[];
     __shared__ __align__(16) double Ms[2][kSB][N * N];
     __shared__ double X[N * (N + 1)];
@@ -574,6 +578,7 @@ __global__ void __launch_bounds__(32, 1) boundaries_kernel(const double* __restr
                                                            const double* __restrict__ abar,
                                                            const double* __restrict__ w0, int T,
                                                            double* __restrict__ bnd) {
+    pdl_prologue();
     extern __shared__ __align__(16) double mp[];  // [n_chunks][N][N+1]
     __shared__ double w[N];
     const int lane = threadIdx.x;
@@ -620,6 +625,7 @@ __global__ void __launch_bounds__(32) fill_kernel(const double* __restrict__ Mg,
                                                   const double* __restrict__ bnd, const double* __restrict__ kx,
                                                   int T, int C, double* __restrict__ out_m,
                                                   double* __restrict__ z_out, double* __restrict__ p0_out) {
+    pdl_prologue();
     __shared__ __align__(16) double Ms[2][kSB][N * N];
     __shared__ __align__(16) double Ws[2][kSB][MC * N];  // BWD: N_t, FWD: K_t
     __shared__ __align__(16) double Fs[2][kSB][N];
@@ -708,6 +714,7 @@ __global__ void __launch_bounds__(32) fill_kernel(const double* __restrict__ Mg,
 __global__ void lqr_vjp_prep_kernel(const double* __restrict__ K, const double* __restrict__ Si,
                                     const double* __restrict__ vbar, int T, int n, int m, double* __restrict__ c,
                                     double* __restrict__ kx) {
+    pdl_prologue();
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= T) return;
     const double* Kt = K + (size_t)t * m * n;
@@ -726,6 +733,7 @@ __global__ void lqr_vjp_prep_kernel(const double* __restrict__ K, const double* 
 }
 
 __global__ void lqr_vjp_out_kernel(LqrConst C, const double* __restrict__ z, int T, int n, double* __restrict__ out) {
+    pdl_prologue();
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= T) return;
     const double* zt = z + (size_t)(t + 1) * n;
@@ -737,6 +745,7 @@ __global__ void lqr_vjp_out_kernel(LqrConst C, const double* __restrict__ z, int
 }
 
 __global__ void transpose_steps_kernel(const double* __restrict__ B, int T, int n, int m, double* __restrict__ Bt) {
+    pdl_prologue();
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= T * n * m) return;
     const int t = e / (n * m), f = e % (n * m), r = f / m, q = f % m;  // B_t[r][q] -> Bt_t[q][r]
@@ -809,6 +818,7 @@ constexpr int kRK = 4;
 __global__ void __launch_bounds__(1024) update_rollout_kernel(RolloutArgs ro, double* __restrict__ u,
                                                                const double* __restrict__ v, int T, int n, int m,
                                                                double* __restrict__ s) {
+    pdl_prologue();
     __shared__ double sh[32][2];
     const int tid = threadIdx.x;
     const double dt = ro.dt;
@@ -929,6 +939,7 @@ __global__ void __launch_bounds__(1024) update_rollout_kernel(RolloutArgs ro, do
 
 __global__ void linearize_kernel(int model, const double* __restrict__ s, const double* __restrict__ u, int T,
                                  int n, int m, double dt, double* __restrict__ A, double* __restrict__ B) {
+    pdl_prologue();
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= T) return;
     double* At = A + (size_t)t * n * n;
@@ -1043,14 +1054,14 @@ static void launch_riccati_t(const double* A, const double* B, const LqrConst& C
     double* Si = Nt + (size_t)T * MC * N;
     ScanPlan pl;
     if (T < kParRiccatiMinT || !scan_plan(T, &pl)) {
-        riccati_kernel<N, MC><<<1, 32, 0, s>>>(A, B, C, T, K, M, Nt, Si, st, nullptr, T);
+        launch_pdl(riccati_kernel<N, MC>, dim3(1), dim3(32), 0, s, A, B, C, T, K, M, Nt, Si, st, nullptr, T);
         return;
     }
     double* maps = Si + (size_t)T * MC * MC;
     double* pin = maps + (size_t)kMaxChunks * 3 * N * N;
-    ric_compose_kernel<N, MC><<<pl.n_chunks, 32, 0, s>>>(A, B, Ci, T, pl.C, maps, st);
-    ric_chain_kernel<N><<<1, 32, 0, s>>>(maps, pl.n_chunks, C, pin, st);
-    riccati_kernel<N, MC><<<pl.n_chunks, 32, 0, s>>>(A, B, C, T, K, M, Nt, Si, st, pin, pl.C);
+    launch_pdl(ric_compose_kernel<N, MC>, dim3(pl.n_chunks), dim3(32), 0, s, A, B, Ci, T, pl.C, maps, st);
+    launch_pdl(ric_chain_kernel<N>, dim3(1), dim3(32), 0, s, maps, pl.n_chunks, C, pin, st);
+    launch_pdl(riccati_kernel<N, MC>, dim3(pl.n_chunks), dim3(32), 0, s, A, B, C, T, K, M, Nt, Si, st, pin, pl.C);
 }
 
 // R^-1 on the host (m <= 3, Gauss-Jordan with partial pivoting).
@@ -1085,15 +1096,15 @@ static void launch_affine_t(const double* B, const double* gains, const LqrConst
     const double* Nt = M + (size_t)T * N * N;
     const size_t fsb = sizeof(double) * pl.C * N;
     const size_t mpb = sizeof(double) * pl.n_chunks * N * (N + 1);
-    compose_kernel<N, MC, true><<<pl.n_chunks, 32, fsb, s>>>(M, C, abar, nullptr, nullptr, nullptr, T, pl.C, ab.fc,
+    launch_pdl(compose_kernel<N, MC, true>, dim3(pl.n_chunks), dim3(32), fsb, s, M, C, abar, nullptr, nullptr, nullptr, T, pl.C, ab.fc,
                                                              ab.maps);
-    boundaries_kernel<N, true><<<1, 32, mpb, s>>>(ab.maps, pl.n_chunks, C, abar, nullptr, T, ab.bnd);
-    fill_kernel<N, MC, true><<<pl.n_chunks, 32, 0, s>>>(M, Nt, ab.fc, nullptr, ab.bnd, nullptr, T, pl.C, ab.k, nullptr,
+    launch_pdl(boundaries_kernel<N, true>, dim3(1), dim3(32), mpb, s, ab.maps, pl.n_chunks, C, abar, nullptr, T, ab.bnd);
+    launch_pdl(fill_kernel<N, MC, true>, dim3(pl.n_chunks), dim3(32), 0, s, M, Nt, ab.fc, nullptr, ab.bnd, nullptr, T, pl.C, ab.k, nullptr,
                                                         nullptr);
-    compose_kernel<N, MC, false><<<pl.n_chunks, 32, fsb, s>>>(M, C, nullptr, B, ab.k, nullptr, T, pl.C, ab.fe,
+    launch_pdl(compose_kernel<N, MC, false>, dim3(pl.n_chunks), dim3(32), fsb, s, M, C, nullptr, B, ab.k, nullptr, T, pl.C, ab.fe,
                                                               ab.maps);
-    boundaries_kernel<N, false><<<1, 32, mpb, s>>>(ab.maps, pl.n_chunks, C, nullptr, nullptr, T, ab.bnd);
-    fill_kernel<N, MC, false><<<pl.n_chunks, 32, 0, s>>>(M, K, ab.fe, ab.k, ab.bnd, nullptr, T, pl.C, v, z, nullptr);
+    launch_pdl(boundaries_kernel<N, false>, dim3(1), dim3(32), mpb, s, ab.maps, pl.n_chunks, C, nullptr, nullptr, T, ab.bnd);
+    launch_pdl(fill_kernel<N, MC, false>, dim3(pl.n_chunks), dim3(32), 0, s, M, K, ab.fe, ab.k, ab.bnd, nullptr, T, pl.C, v, z, nullptr);
 }
 
 template <int N, int MC>
@@ -1203,18 +1214,18 @@ static void launch_lqr_vjp_t(const double* B, const double* gains, const LqrCons
     const size_t fsb = sizeof(double) * pl.C * N;
     const size_t mpb = sizeof(double) * pl.n_chunks * N * (N + 1);
     const AffineBufs& ab = b.ab;
-    lqr_vjp_prep_kernel<<<(T + 127) / 128, 128, 0, s>>>(K, Si, vbar, T, N, MC, b.c, b.kx);
-    compose_kernel<N, MC, true><<<pl.n_chunks, 32, fsb, s>>>(M, C, nullptr, nullptr, nullptr, b.c, T, pl.C, ab.fc,
+    launch_pdl(lqr_vjp_prep_kernel, dim3((T + 127) / 128), dim3(128), 0, s, K, Si, vbar, T, N, MC, b.c, b.kx);
+    launch_pdl(compose_kernel<N, MC, true>, dim3(pl.n_chunks), dim3(32), fsb, s, M, C, nullptr, nullptr, nullptr, b.c, T, pl.C, ab.fc,
                                                              ab.maps);
-    boundaries_kernel<N, true><<<1, 32, mpb, s>>>(ab.maps, pl.n_chunks, C, nullptr, b.zero, T, ab.bnd);
-    fill_kernel<N, MC, true><<<pl.n_chunks, 32, 0, s>>>(M, Nt, ab.fc, nullptr, ab.bnd, b.kx, T, pl.C, ab.k, nullptr,
+    launch_pdl(boundaries_kernel<N, true>, dim3(1), dim3(32), mpb, s, ab.maps, pl.n_chunks, C, nullptr, b.zero, T, ab.bnd);
+    launch_pdl(fill_kernel<N, MC, true>, dim3(pl.n_chunks), dim3(32), 0, s, M, Nt, ab.fc, nullptr, ab.bnd, b.kx, T, pl.C, ab.k, nullptr,
                                                         nullptr);
-    compose_kernel<N, MC, false><<<pl.n_chunks, 32, fsb, s>>>(M, C, nullptr, B, ab.k, nullptr, T, pl.C, ab.fe,
+    launch_pdl(compose_kernel<N, MC, false>, dim3(pl.n_chunks), dim3(32), fsb, s, M, C, nullptr, B, ab.k, nullptr, T, pl.C, ab.fe,
                                                               ab.maps);
-    boundaries_kernel<N, false><<<1, 32, mpb, s>>>(ab.maps, pl.n_chunks, C, nullptr, nullptr, T, ab.bnd);
-    fill_kernel<N, MC, false><<<pl.n_chunks, 32, 0, s>>>(M, K, ab.fe, ab.k, ab.bnd, nullptr, T, pl.C, b.vtmp, b.z,
+    launch_pdl(boundaries_kernel<N, false>, dim3(1), dim3(32), mpb, s, ab.maps, pl.n_chunks, C, nullptr, nullptr, T, ab.bnd);
+    launch_pdl(fill_kernel<N, MC, false>, dim3(pl.n_chunks), dim3(32), 0, s, M, K, ab.fe, ab.k, ab.bnd, nullptr, T, pl.C, b.vtmp, b.z,
                                                          nullptr);
-    lqr_vjp_out_kernel<<<(T + 127) / 128, 128, 0, s>>>(C, b.z, T, N, out);
+    launch_pdl(lqr_vjp_out_kernel, dim3((T + 127) / 128), dim3(128), 0, s, C, b.z, T, N, out);
 }
 
 template <int N, int MC>
@@ -1224,11 +1235,11 @@ static void launch_rollout_vjp_t(const double* A, const double* B, const double*
     const size_t mpb = sizeof(double) * pl.n_chunks * N * (N + 1);
     const AffineBufs& ab = b.ab;
     const LqrConst C{};
-    transpose_steps_kernel<<<(T * N * MC + 255) / 256, 256, 0, s>>>(B, T, N, MC, b.Bt);
-    compose_kernel<N, MC, true><<<pl.n_chunks, 32, fsb, s>>>(A, C, nullptr, nullptr, nullptr, sbar, T, pl.C, ab.fc,
+    launch_pdl(transpose_steps_kernel, dim3((T * N * MC + 255) / 256), dim3(256), 0, s, B, T, N, MC, b.Bt);
+    launch_pdl(compose_kernel<N, MC, true>, dim3(pl.n_chunks), dim3(32), fsb, s, A, C, nullptr, nullptr, nullptr, sbar, T, pl.C, ab.fc,
                                                              ab.maps);
-    boundaries_kernel<N, true><<<1, 32, mpb, s>>>(ab.maps, pl.n_chunks, C, nullptr, sbar + (size_t)T * N, T, ab.bnd);
-    fill_kernel<N, MC, true><<<pl.n_chunks, 32, 0, s>>>(A, b.Bt, ab.fc, nullptr, ab.bnd, nullptr, T, pl.C, ubar,
+    launch_pdl(boundaries_kernel<N, true>, dim3(1), dim3(32), mpb, s, ab.maps, pl.n_chunks, C, nullptr, sbar + (size_t)T * N, T, ab.bnd);
+    launch_pdl(fill_kernel<N, MC, true>, dim3(pl.n_chunks), dim3(32), 0, s, A, b.Bt, ab.fc, nullptr, ab.bnd, nullptr, T, pl.C, ubar,
                                                         nullptr, s0bar);
 }
 
@@ -1279,7 +1290,10 @@ cov_status update_rollout(cov_ctx* ctx, int model, const double* s0, double* u, 
     ro.dt = dt;
     ro.eta = eta;
     for (int r = 0; r < n; ++r) ro.s0[r] = s0[r];
-    update_rollout_kernel<<<1, 1024, 0, stream>>>(ro, u, v, T, n, m, s);
+    // as many warps as the horizon fills (kRK steps per thread), up to 1024
+    // threads: short horizons scan over fewer warps
+    const int threads = std::min(1024, std::max(32, ((T + kRK - 1) / kRK + 31) / 32 * 32));
+    launch_pdl(update_rollout_kernel, dim3(1), dim3(threads), 0, stream, ro, u, v, T, n, m, s);
     return cuda_failed(ctx, cudaGetLastError()) ? COV_ERR_CUDA : COV_OK;
 }
 
@@ -1287,7 +1301,7 @@ cov_status linearize_launch(cov_ctx* ctx, int model, const double* s, const doub
                             double* B, cudaStream_t stream) {
     int n, m;
     if (model_dims(model, &n, &m) != 0) return COV_ERR_INVALID_ARG;
-    linearize_kernel<<<(T + 127) / 128, 128, 0, stream>>>(model, s, u, T, n, m, dt, A, B);
+    launch_pdl(linearize_kernel, dim3((T + 127) / 128), dim3(128), 0, stream, model, s, u, T, n, m, dt, A, B);
     if (cuda_failed(ctx, cudaGetLastError())) return COV_ERR_CUDA;
     return COV_OK;
 }

@@ -352,6 +352,7 @@ __global__ void tc_records_kernel(const float* __restrict__ xs, int Tp, const fl
                                   const float* __restrict__ hp2, const float* __restrict__ hy,
                                   float* __restrict__ c0x, float* __restrict__ c0y, float* __restrict__ hrx,
                                   float* __restrict__ hrp, float* __restrict__ hrp2, float* __restrict__ hry) {
+    pdl_prologue();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     float c[3] = {0.f, 0.f, 0.f};
     float s[8];

@@ -115,6 +115,7 @@ void destroy_stream_pool(cov_ctx* ctx) {
 
 // x_i = first d components of s_{i+1} (FP32 coverage coordinates).
 __global__ void extract_kernel(const double* __restrict__ s, int T, int n, int d, float* __restrict__ x) {
+    pdl_prologue();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= T) return;
     for (int k = 0; k < d; ++k) x[(size_t)i * d + k] = (float)s[(size_t)(i + 1) * n + k];
@@ -122,6 +123,7 @@ __global__ void extract_kernel(const double* __restrict__ s, int T, int n, int d
 
 // abar_t = P' a_t: the field on the coverage coordinates, zero elsewhere.
 __global__ void lift_kernel(const float* __restrict__ a, int T, int n, int d, double* __restrict__ abar) {
+    pdl_prologue();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= T) return;
     for (int r = 0; r < n; ++r) abar[(size_t)i * n + r] = r < d ? (double)a[(size_t)i * d + r] : 0.0;
@@ -193,7 +195,7 @@ static cov_status enqueue_iteration(cov_ctx* ctx, const cov_problem* P, int n, i
                                     size_t rest_bytes, double* u, double* s, cudaStream_t st) {
     const int T = P->T, d = P->d;
     const int nb = (T + 255) / 256;
-    extract_kernel<<<nb, 256, 0, st>>>(s, T, n, d, b.x);
+    launch_pdl(extract_kernel, dim3(nb), dim3(256), 0, st, s, T, n, d, b.x);
     cov_status r;
     if (P->field == COV_FIELD_SINKHORN) {
         const bool warm = P->warm == 1;
@@ -211,7 +213,7 @@ static cov_status enqueue_iteration(cov_ctx* ctx, const cov_problem* P, int n, i
         r = svgd_field_ws(ctx, rest, rest_bytes, b.x, d, T, d, nullptr, &P->gmm, P->h, b.a, st);
     }
     if (r != COV_OK) return r;
-    lift_kernel<<<nb, 256, 0, st>>>(b.a, T, n, d, b.abar);
+    launch_pdl(lift_kernel, dim3(nb), dim3(256), 0, st, b.a, T, n, d, b.abar);
     if (!model_is_lti(P->model)) {
         r = linearize_launch(ctx, P->model, s, u, T, P->dt, b.A, b.B, st);
         if (r != COV_OK) return r;
@@ -639,17 +641,20 @@ static uint64_t tape_key_of(const cov_problem* P, int K, const double* s_hist, c
 
 // vbar = eta ubar
 __global__ void back_scale_kernel(const double* __restrict__ ubar, double eta, int N, double* __restrict__ vbar) {
+    pdl_prologue();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < N) vbar[i] = eta * ubar[i];
 }
 // abf = the coverage components of abar_bar, in FP32
 __global__ void narrow_kernel(const double* __restrict__ abb, int T, int n, int d, float* __restrict__ abf) {
+    pdl_prologue();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= T) return;
     for (int k = 0; k < d; ++k) abf[(size_t)i * d + k] = (float)abb[(size_t)i * n + k];
 }
 // sbar = the sample adjoint lifted to the trajectory (s_0 does not move)
 __global__ void lift_bar_kernel(const float* __restrict__ xbar, int T, int n, int d, double* __restrict__ sbar) {
+    pdl_prologue();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i > T) return;
     for (int r = 0; r < n; ++r)
@@ -658,6 +663,7 @@ __global__ void lift_bar_kernel(const float* __restrict__ xbar, int T, int n, in
 // ubar += ub2; s0bar += lam0
 __global__ void back_accum_kernel(double* __restrict__ ubar, const double* __restrict__ ub2, int N,
                                   double* __restrict__ s0bar, const double* __restrict__ lam0, int n) {
+    pdl_prologue();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < N) ubar[i] += ub2[i];
     if (i < n) s0bar[i] += lam0[i];
@@ -696,13 +702,13 @@ static cov_status solve_taped(cov_ctx* ctx, const cov_problem* prob, int K, doub
             if (cuda_failed(ctx, cudaMemcpyAsync(s_hist + (size_t)k * ss, s_out, sizeof(double) * ss,
                                                  cudaMemcpyDeviceToDevice, ws_st)))
                 return COV_ERR_CUDA;
-            extract_kernel<<<nb, 256, 0, ws_st>>>(s_out, T, n, d, b.x);
+            launch_pdl(extract_kernel, dim3(nb), dim3(256), 0, ws_st, s_out, T, n, d, b.x);
             size_t used = 0;
             q = sinkhorn_tape_ws(ctx, L.tape0 + (size_t)k * L.tape_stride, L.tape_stride, b.x, d, T, prob->y,
                                  prob->b, prob->M, d, prob->eps, prob->n_iter, b.scal, &ctx->tapes[k], &used, ws_st,
                                  L.split, b.a);
             if (q != COV_OK) return q;
-            lift_kernel<<<nb, 256, 0, ws_st>>>(b.a, T, n, d, b.abar);
+            launch_pdl(lift_kernel, dim3(nb), dim3(256), 0, ws_st, b.a, T, n, d, b.abar);
             q = lqr_affine(ctx, L.rest, L.rest_bytes, n, m, b.B, b.gains, prob->Q, b.abar, T, b.v, nullptr, ws_st);
             if (q != COV_OK) return q;
             q = update_rollout(ctx, prob->model, prob->s0, u, b.v, prob->eta, T, prob->dt, s_out, ws_st);
@@ -807,19 +813,19 @@ extern "C" cov_status cov_solve_backward(cov_ctx* ctx, const cov_problem* prob, 
     }
     const int Tm = T * m;
     for (int k = K; k >= 1; --k) {
-        back_scale_kernel<<<(Tm + 255) / 256, 256, 0, st>>>(bb.ubar, prob->eta, Tm, bb.vbar);
+        launch_pdl(back_scale_kernel, dim3((Tm + 255) / 256), dim3(256), 0, st, bb.ubar, prob->eta, Tm, bb.vbar);
         r = lqr_vjp_ws(ctx, rest, rest_bytes, n, m, sb.B, sb.gains, prob->Q, bb.vbar, T, bb.abb, st);
         if (r != COV_OK) return r;
-        narrow_kernel<<<nb, 256, 0, st>>>(bb.abb, T, n, d, bb.abf);
-        if (mode != BM_TAPED) extract_kernel<<<nb, 256, 0, st>>>(hist + (size_t)(k - 1) * ss, T, n, d, sb.x);
+        launch_pdl(narrow_kernel, dim3(nb), dim3(256), 0, st, bb.abb, T, n, d, bb.abf);
+        if (mode != BM_TAPED) launch_pdl(extract_kernel, dim3(nb), dim3(256), 0, st, hist + (size_t)(k - 1) * ss, T, n, d, sb.x);
         r = sinkhorn_vjp_ws(ctx, rest, rest_bytes, sb.x, d, T, prob->y, prob->b, prob->M, d, prob->eps,
                             prob->n_iter, sb.scal, bb.abf, d, bb.xbar, d, ybar, prob->b ? bbar : nullptr,
                             k != K ? 1 : 0, st, mode == BM_TAPED ? &ctx->tapes[k - 1] : nullptr);
         if (r != COV_OK) return r;
-        lift_bar_kernel<<<nb, 256, 0, st>>>(bb.xbar, T, n, d, bb.sbar);
+        launch_pdl(lift_bar_kernel, dim3(nb), dim3(256), 0, st, bb.xbar, T, n, d, bb.sbar);
         r = rollout_vjp_ws(ctx, rest, rest_bytes, n, m, sb.A, sb.B, bb.sbar, T, bb.ub2, bb.lam0, st);
         if (r != COV_OK) return r;
-        back_accum_kernel<<<(Tm + 255) / 256, 256, 0, st>>>(bb.ubar, bb.ub2, Tm, s0bar, bb.lam0, n);
+        launch_pdl(back_accum_kernel, dim3((Tm + 255) / 256), dim3(256), 0, st, bb.ubar, bb.ub2, Tm, s0bar, bb.lam0, n);
     }
     if (u0bar && cuda_failed(ctx, cudaMemcpyAsync(u0bar, bb.ubar, sizeof(double) * Tm, cudaMemcpyDeviceToDevice, st)))
         return COV_ERR_CUDA;
