@@ -1070,8 +1070,9 @@ static void fill_segment(PairArgs& a, int n_cols, int budget, int unit) {
     const int s = (int)(total / a.n_rb);
     const int extra = (int)(total - (long long)s * a.n_rb);
     // with few splits per row block, s and s + 1 splits differ too much in
-    // work per CTA (measured slower for s = 1); keep the uniform plan there
-    if (s < 3) return;
+    // work per CTA (measured slower for s = 1); with few columns per split,
+    // rounding would leave whole CTAs without columns: keep the uniform plan
+    if (s < 3 || units / (s + 1) < kTile / unit) return;
     if (extra == 0) {
         a.splits = s;
         a.n_hi = a.n_rb;
