@@ -764,6 +764,7 @@ struct RolloutArgs {
     double dt;
     double eta;
     double s0[COV_MAX_N];
+    int heading_only;  // unicycle: stop after the heading (the positions follow in two more kernels)
 };
 
 // Block-wide exclusive scan of NV values per thread (1024 threads): on
@@ -814,6 +815,7 @@ __device__ __forceinline__ void block_exclusive_scan(double (&x)[NV], double (&t
 // vel += dt u, p += dt vel (vel before its update); unicycle theta += dt
 // omega, (x, y) += dt v (cos, sin)(theta before its update).
 constexpr int kRK = 4;
+constexpr int kUnicycleSplitT = 2048;  // longer unicycle horizons take the three-kernel rollout
 
 __global__ void __launch_bounds__(1024) update_rollout_kernel(RolloutArgs ro, double* __restrict__ u,
                                                                const double* __restrict__ v, int T, int n, int m,
@@ -903,6 +905,15 @@ __global__ void __launch_bounds__(1024) update_rollout_kernel(RolloutArgs ro, do
             }
             double off[1] = {run}, tot[1];
             block_exclusive_scan<1>(off, tot, reinterpret_cast<double(*)[1]>(&sh[0][0]));
+            if (ro.heading_only) {
+#pragma unroll
+                for (int k = 0; k < kRK; ++k) {
+                    const int t = t0 + k;
+                    if (t < T) s[(size_t)(t + 1) * n + 2] = c2 + (off[0] + incl[k]);
+                }
+                c2 += tot[0];
+                continue;
+            }
             double run2[2] = {0.0, 0.0}, incl2[kRK][2];
 #pragma unroll
             for (int k = 0; k < kRK; ++k) {
@@ -934,6 +945,61 @@ __global__ void __launch_bounds__(1024) update_rollout_kernel(RolloutArgs ro, do
                 for (int r = 0; r < COV_MAX_N; ++r)
                     if (r < n) s[(size_t)(t + 1) * n + r] = out[k][r];
         }
+    }
+}
+
+// Unicycle rollout for long horizons, second part: the position increments
+// dt v_t (cos, sin)(theta_t) of every step in parallel over the whole GPU
+// (FP64 sincos is the costly part; one SM would take it serially), written
+// into the position slots of row t + 1 for the scan that follows.
+__global__ void unicycle_increments_kernel(const double* __restrict__ u, int T, int m, double dt,
+                                           double* __restrict__ s) {
+    pdl_prologue();
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= T) return;
+    double sn, cs;
+    sincos(s[(size_t)t * 3 + 2], &sn, &cs);
+    const double sp = dt * u[(size_t)t * m];
+    s[(size_t)(t + 1) * 3 + 0] = sp * cs;
+    s[(size_t)(t + 1) * 3 + 1] = sp * sn;
+}
+
+// Third part: positions as the prefix sums of those increments from the
+// initial position (one CTA of tiled block scans, in place).
+__global__ void __launch_bounds__(1024) unicycle_positions_kernel(RolloutArgs ro, int T, double* __restrict__ s) {
+    pdl_prologue();
+    __shared__ double sh[32][2];
+    double c0 = ro.s0[0], c1 = ro.s0[1];
+    const int per_tile = blockDim.x * kRK;
+    for (int base = 0; base < T; base += per_tile) {
+        const int t0 = base + threadIdx.x * kRK;
+        double inc[kRK][2];
+#pragma unroll
+        for (int k = 0; k < kRK; ++k) {
+            const int t = t0 + k;
+            inc[k][0] = t < T ? s[(size_t)(t + 1) * 3 + 0] : 0.0;
+            inc[k][1] = t < T ? s[(size_t)(t + 1) * 3 + 1] : 0.0;
+        }
+        double run[2] = {0.0, 0.0}, incl[kRK][2];
+#pragma unroll
+        for (int k = 0; k < kRK; ++k) {
+            run[0] += inc[k][0];
+            run[1] += inc[k][1];
+            incl[k][0] = run[0];
+            incl[k][1] = run[1];
+        }
+        double off[2] = {run[0], run[1]}, tot[2];
+        block_exclusive_scan<2>(off, tot, sh);
+#pragma unroll
+        for (int k = 0; k < kRK; ++k) {
+            const int t = t0 + k;
+            if (t < T) {
+                s[(size_t)(t + 1) * 3 + 0] = c0 + (off[0] + incl[k][0]);
+                s[(size_t)(t + 1) * 3 + 1] = c1 + (off[1] + incl[k][1]);
+            }
+        }
+        c0 += tot[0];
+        c1 += tot[1];
     }
 }
 
@@ -1293,7 +1359,15 @@ cov_status update_rollout(cov_ctx* ctx, int model, const double* s0, double* u, 
     // as many warps as the horizon fills (kRK steps per thread), up to 1024
     // threads: short horizons scan over fewer warps
     const int threads = std::min(1024, std::max(32, ((T + kRK - 1) / kRK + 31) / 32 * 32));
+    // long unicycle horizons: the heading scan, then the sincos of every
+    // step spread over the GPU, then the position scan
+    ro.heading_only = model == COV_UNICYCLE && T > kUnicycleSplitT;
     launch_pdl(update_rollout_kernel, dim3(1), dim3(threads), 0, stream, ro, u, v, T, n, m, s);
+    if (ro.heading_only) {
+        launch_pdl(unicycle_increments_kernel, dim3((T + 255) / 256), dim3(256), 0, stream, (const double*)u, T, m,
+                   dt, s);
+        launch_pdl(unicycle_positions_kernel, dim3(1), dim3(threads), 0, stream, ro, T, s);
+    }
     return cuda_failed(ctx, cudaGetLastError()) ? COV_ERR_CUDA : COV_OK;
 }
 
