@@ -178,9 +178,12 @@ cov_status lqr_track_ws(cov_ctx* ctx, void* ws, size_t ws_bytes, const double* A
 struct SplitPlan {
     int n_rb;        // row blocks
     int splits;      // column splits
-    int cols_per_split;  // multiple of the planning unit (8 columns; 128 for the tensor-core kernel)
+    int cols_per_split;  // multiple of the planning unit (8 columns; 256 for the tensor-core kernel)
 };
-SplitPlan plan_splits(int n_rows, int n_cols, int rows_per_cta, int slots, int unit = 8, int fixed = 64);
+// max_waves bounds the split count searched: at most about max_waves waves
+// of CTAs over the slots.
+SplitPlan plan_splits(int n_rows, int n_cols, int rows_per_cta, int slots, int unit = 8, int fixed = 64,
+                      int max_waves = 2);
 
 // GMM descriptor passed by value to kernels.
 struct GmmParams {

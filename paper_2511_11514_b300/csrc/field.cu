@@ -718,11 +718,12 @@ __global__ void __launch_bounds__(kThreads) pairs_kernel(const __grid_constant__
 // minimises (waves of CTAs) x (columns per CTA + fixed cost) + merge cost.
 // Splits are whole multiples of `unit` columns.
 // ---------------------------------------------------------------------------
-cov::SplitPlan cov::plan_splits(int n_rows, int n_cols, int rows_per_cta, int slots, int unit, int fixed) {
+cov::SplitPlan cov::plan_splits(int n_rows, int n_cols, int rows_per_cta, int slots, int unit, int fixed,
+                                int max_waves) {
     SplitPlan best{};
     const int n_rb = (n_rows + rows_per_cta - 1) / rows_per_cta;
     const int units = (n_cols + unit - 1) / unit;
-    const int smax = std::max(1, std::min(units, (2 * slots + n_rb - 1) / n_rb));
+    const int smax = std::max(1, std::min(units, (max_waves * slots + n_rb - 1) / n_rb));
     double best_cost = 1e300;
     for (int s = 1; s <= smax; ++s) {
         const int cpu = (units + s - 1) / s;
@@ -1047,8 +1048,8 @@ constexpr size_t kPartRows = (size_t)2 * kMaxSlots * 256 + 256;
 static int cnt_ld_for(int Tp, int Mp) { return std::max(Tp, Mp) / 64 + 1; }
 
 static void plan_segment(PairArgs& a, int n_cols, int RB, int slots, unsigned* counters, int unit = 8,
-                         int fixed = 64) {
-    const SplitPlan pl = plan_splits(a.n_rows, n_cols, RB, slots, unit, fixed);
+                         int fixed = 64, int max_waves = 2) {
+    const SplitPlan pl = plan_splits(a.n_rows, n_cols, RB, slots, unit, fixed, max_waves);
     a.n_cols8 = (int)round_up((size_t)n_cols, (size_t)unit);
     a.cols_per_split = pl.cols_per_split;
     a.splits = pl.splits;
@@ -1114,8 +1115,14 @@ static cov_status run_pairs(cov_ctx* ctx, int d, int family, PairArgs* seg, cons
     const int nacc = family == M_SVGD ? d : ((family == M_WY || family == M_WX || family == M_GW) ? 2 + d : 2);
     // uniform plan; when it is one wave that already fills at least half the
     // slots, re-plan to fill them exactly (CUDA-core kernel)
+    // The tensor-core kernel holds one CTA per SM, so row blocks alone often
+    // end in a part-filled last wave (512 row blocks on 148 SMs: 3.46 waves);
+    // its split search reaches up to 8 waves to square them off, within the
+    // partial-buffer bound (splits x row blocks x RB <= waves x slots x RB +
+    // the rows, against kPartRows)
+    const int max_waves = tc ? (int)std::min<long long>(8, 2LL * kMaxSlots * 256 / ((long long)slots * RB)) : 2;
     auto plan = [&](PairArgs& a, int nc, int budget, unsigned* cnt) {
-        plan_segment(a, nc, RB, budget, cnt, unit, fixed_cost);
+        plan_segment(a, nc, RB, budget, cnt, unit, fixed_cost, std::max(2, max_waves));
         const long long ctas = (long long)a.n_rb * a.splits;
         if (!tc && ctas <= budget && 2 * ctas >= budget && budget > a.n_rb) fill_segment(a, nc, budget, unit);
     };

@@ -4,7 +4,7 @@
 //       min sum_{t=1..T} |z_t - abar_t|_Q^2 + sum_{t=0..T-1} |v_t|_R^2,
 //       z_{t+1} = A_t z_t + B_t v_t, z_0 = 0,
 //     with value function z'P_t z + 2 p_t'z:
-//       Riccati (backward, nonlinear in P; one warp, serial):
+//       Riccati (backward, nonlinear in P; per step, one warp):
 //         S = R + B'P'B, G = B'P'A, K = S^-1 G, P = Q_t + A'P'A - G'K
 //         (P and S kept exactly symmetric: upper triangle computed, mirrored),
 //         and the closed loop M_t = A_t - B_t K_t, N_t = S^-1 B_t'
@@ -17,12 +17,12 @@
 //   * the control update u <- u + eta v and the Euler rollout.
 //
 // FP64 on B300 has a ~65-cycle dependent-FMA latency and ~1.6 FMA/clk per
-// SM, so the serial chains are what cost time.  The design keeps only the
-// Riccati recursion serial (and caches it for time-invariant models), and
-// runs the two affine recursions as chunked parallel-in-time scans: each
-// chunk of C steps composes its affine map (one warp per chunk, spread over
-// the SMs), one warp chains the chunk maps, and each chunk then fills in its
-// steps from its boundary value.  The rollout of every model is a sum of
+// SM, so the serial chains are what cost time.  The Riccati recursion runs
+// parallel in time by composing its step maps (below; cached for
+// time-invariant models), and the two affine recursions as chunked scans:
+// each chunk of C steps composes its affine map (one warp per chunk, spread
+// over the SMs), one warp chains the chunk maps, and each chunk then fills
+// in its steps from its boundary value.  The rollout of every model is a sum of
 // Euler increments, done as block-wide prefix sums.  Inside a warp every
 // lane runs the same dot product on different operands, so no phase
 // diverges.
@@ -250,57 +250,69 @@ __global__ void __launch_bounds__(32, 1) riccati_kernel(const double* __restrict
 // closed under composition: F1(F2(P)) has
 //   W = (I + C1 J2)^-1,  E = E2 W E1,  C = C2 + E2 W C1 E2',  J = J1 + (W E1)' J2 E1,
 // with every inverse of the form I + (PSD)(PSD), whose eigenvalues are >= 1.
-// Chunks compose their maps (one warp each), one warp chains the chunk maps
-// from P_T = Q to get the P entering every chunk, and each chunk then runs
-// the ordinary Riccati step over its own steps from that P (riccati_kernel).
+// Chunks compose their maps (one warp each), the chunk maps are chained
+// from P_T = Q to get the P entering every chunk (for long horizons through
+// a second level: groups of chunk maps composed again, the group maps
+// chained, each group's chunk maps chained from the P entering the group),
+// and each chunk then runs the ordinary Riccati step over its own steps from
+// that P (riccati_kernel).
 // ---------------------------------------------------------------------------
 
-// In-warp inverse of a general N x N matrix (N <= 4) by Gauss-Jordan with
-// partial pivoting.  X is overwritten; the inverse is written to Xi.  aug is
-// N x 2N shared scratch.  Every lane calls it.
-template <int N>
-__device__ void warp_inverse(double* X, double* Xi, double* aug, int* piv, int lane) {
-    constexpr int W2 = 2 * N;
-    for (int e = lane; e < N * W2; e += 32) {
-        const int r = e / W2, c = e % W2;
-        aug[e] = c < N ? X[r * N + c] : (c - N == r ? 1.0 : 0.0);
+// Solve X Z = Y for a general N x N matrix X (N <= 4) and an N x K
+// right-hand side Y by Gauss-Jordan elimination with partial pivoting on
+// [X | Y]; Z (N x K) is written.  aug is N x (N + K) shared scratch.  The
+// pivot search runs across lanes 0..3 and each elimination pass folds the
+// row swap in, so a pivot costs one reciprocal, one FMA and two warp
+// syncs.  Every lane calls it.
+template <int N, int K>
+__device__ void warp_solve(const double* X, const double* Y, double* Z, double* aug, int lane) {
+    static_assert(N <= 4, "pivot search spans lanes 0..3");
+    constexpr int W = N + K, E = N * W, PER = (E + 31) / 32;
+    for (int e = lane; e < E; e += 32) {
+        const int r = e / W, c = e % W;
+        aug[e] = c < N ? X[r * N + c] : Y[r * K + (c - N)];
     }
     __syncwarp();
+#pragma unroll
     for (int k = 0; k < N; ++k) {
-        if (lane == 0) {
-            int p = k;
-            double best = fabs(aug[k * W2 + k]);
-            for (int r = k + 1; r < N; ++r) {
-                const double v = fabs(aug[r * W2 + k]);
-                if (v > best) { best = v; p = r; }
+        // pivot row p: the largest |aug[r][k]| over rows r >= k, the first on ties
+        double v = (lane >= k && lane < N) ? fabs(aug[lane * W + k]) : -1.0;
+        int p = lane;
+#pragma unroll
+        for (int o = 1; o < 4; o <<= 1) {
+            const double v2 = __shfl_xor_sync(0xffffffffu, v, o);
+            const int p2 = __shfl_xor_sync(0xffffffffu, p, o);
+            if (v2 > v || (v2 == v && p2 < p)) {
+                v = v2;
+                p = p2;
             }
-            *piv = p;
+        }
+        p = __shfl_sync(0xffffffffu, p, 0);
+        const double inv_piv = 1.0 / aug[p * W + k];
+        // rows k and p trade places; the pivot row is scaled, the others reduced
+        double nv[PER];
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+            const int e = lane + 32 * q;
+            nv[q] = 0.0;
+            if (e < E) {
+                const int r = e / W, c = e % W;
+                const double pr = aug[p * W + c] * inv_piv;
+                const int src = r == p ? k : r;
+                nv[q] = r == k ? pr : fma(-aug[src * W + k], pr, aug[src * W + c]);
+            }
         }
         __syncwarp();
-        const int p = *piv;
-        if (p != k && lane < W2) {
-            const double t = aug[k * W2 + lane];
-            aug[k * W2 + lane] = aug[p * W2 + lane];
-            aug[p * W2 + lane] = t;
-        }
-        __syncwarp();
-        const double inv_piv = 1.0 / aug[k * W2 + k];
-        double v = 0.0, f = 0.0, rk = 0.0;
-        const int r = lane / W2, c = lane % W2;
-        if (lane < N * W2) {
-            v = aug[lane];
-            f = aug[r * W2 + k];
-            rk = aug[k * W2 + c] * inv_piv;
-        }
-        __syncwarp();
-        if (lane < N * W2) aug[lane] = (r == k) ? rk : fma(-f, rk, v);
+#pragma unroll
+        for (int q = 0; q < PER; ++q)
+            if (lane + 32 * q < E) aug[lane + 32 * q] = nv[q];
         __syncwarp();
     }
-    for (int e = lane; e < N * N; e += 32) Xi[e] = aug[(e / N) * W2 + N + e % N];
+    for (int e = lane; e < N * K; e += 32) Z[e] = aug[(e / K) * W + N + e % K];
     __syncwarp();
 }
 
-// Z = X Y (+ Z0), N x N row-major, lanes [off, off + N*N) each one entry.
+// Entry (r, c) of X Y (yT: X Y'), N x N row-major.
 template <int N>
 __device__ __forceinline__ double mat_entry(const double* X, const double* Y, int r, int c, bool yT) {
     double acc = 0.0;
@@ -314,16 +326,96 @@ struct RicMap {
     double E[N * N], C[N * N], J[N * N];
 };
 
+template <int N>
+struct ComposeScratch {
+    double X[N * N], R2[N * N], U[N * N], VY[N * 2 * N];
+    double aug[N * 3 * N];
+};
+
+// acc <- F1 o acc, where F1 = (E1, C1, J1) is the map of the earlier steps
+// and acc = (E2, C2, J2) that of the later ones.  With X = I + C1 J2 and
+// [V | Y] = X^-1 [E1 | C1 E2'] (one Gauss-Jordan solve):
+//   E = E2 V,  C = C2 + E2 Y,  J = J1 + V' (J2 E1)
+// (the composition rule above with Y = W C1 E2'), so a step is one product
+// level, the solve, and one more product level.  C and J are symmetric in
+// exact arithmetic and are kept so (upper triangle, mirrored).  Every lane
+// calls it.
+template <int N>
+__device__ void compose_into(RicMap<N>& acc, const double* E1, const double* C1, const double* J1,
+                             ComposeScratch<N>& sc, int lane) {
+    constexpr int NN = N * N;
+    // X = I + C1 J2, R2 = C1 E2', U = J2 E1: independent, 3 NN entries
+#pragma unroll
+    for (int q = 0; q < (3 * NN + 31) / 32; ++q) {
+        const int e = lane + 32 * q;
+        if (e < 3 * NN) {
+            const int which = e / NN, f = e % NN, r = f / N, c = f % N;
+            if (which == 0)
+                sc.X[f] = (r == c ? 1.0 : 0.0) + mat_entry<N>(C1, acc.J, r, c, false);
+            else if (which == 1)
+                sc.R2[f] = mat_entry<N>(C1, acc.E, r, c, true);
+            else
+                sc.U[f] = mat_entry<N>(acc.J, E1, r, c, false);
+        }
+    }
+    __syncwarp();
+    // [E1 | R2] side by side as the right-hand side
+    for (int e = lane; e < 2 * NN; e += 32) {
+        const int r = e / (2 * N), c = e % (2 * N);
+        sc.VY[e] = c < N ? E1[r * N + c] : sc.R2[r * N + c - N];
+    }
+    __syncwarp();
+    warp_solve<N, 2 * N>(sc.X, sc.VY, sc.VY, sc.aug, lane);
+    // E = E2 V, C = C2 + E2 Y, J = J1 + V' U
+    double nv[(3 * NN + 31) / 32];
+#pragma unroll
+    for (int q = 0; q < (3 * NN + 31) / 32; ++q) {
+        const int e = lane + 32 * q;
+        nv[q] = 0.0;
+        if (e < 3 * NN) {
+            const int which = e / NN, f = e % NN, r = f / N, c = f % N;
+            double a = which == 0 ? 0.0 : (which == 1 ? acc.C[f] : J1[f]);
+#pragma unroll
+            for (int k = 0; k < N; ++k) {
+                if (which == 0) a = fma(acc.E[r * N + k], sc.VY[k * 2 * N + c], a);
+                else if (which == 1) a = fma(acc.E[r * N + k], sc.VY[k * 2 * N + N + c], a);
+                else a = fma(sc.VY[k * 2 * N + r], sc.U[k * N + c], a);
+            }
+            nv[q] = a;
+        }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int q = 0; q < (3 * NN + 31) / 32; ++q) {
+        const int e = lane + 32 * q;
+        if (e < 3 * NN) {
+            const int which = e / NN, f = e % NN, r = f / N, c = f % N;
+            if (which == 0) {
+                acc.E[f] = nv[q];
+            } else if (r <= c) {
+                double* m = which == 1 ? acc.C : acc.J;
+                m[r * N + c] = nv[q];
+                m[c * N + r] = nv[q];
+            }
+        }
+    }
+    __syncwarp();
+}
+
 template <int N, int MC>
 struct ComposeSmem {
     double A[2][kSB][N * N];
     double B[2][kSB][N * MC];
+    double G[kSB][N * N];  // B_t R^-1 B_t' of the sub-block's steps
+    double Qs[N * N], Z0[N * N];
     RicMap<N> acc;
-    double E1[N * N], C1[N * N], J1[N * N], X[N * N], W[N * N], V[N * N], Y[N * N], U[N * N], Z[N * N], BRi[N * MC];
-    double aug[N * 2 * N];
-    int piv;
+    ComposeScratch<N> sc;
 };
 
+// Level 1: block c composes the step maps of chunk c (steps [c Cc,
+// min((c+1) Cc, T) - 1]).  The step map is E1 = A_t, C1 = B_t R^-1 B_t',
+// J1 = Q_t; the C1 of a whole streamed sub-block are formed together
+// before the serial loop, which then only composes.
 template <int N, int MC>
 __global__ void __launch_bounds__(32, 1) ric_compose_kernel(const double* __restrict__ A, const double* __restrict__ B,
                                                             LqrConst Cq, int T, int Cc,
@@ -333,10 +425,10 @@ __global__ void __launch_bounds__(32, 1) ric_compose_kernel(const double* __rest
     const int lane = threadIdx.x;
     const int lo = blockIdx.x * Cc, hi = min(T, lo + Cc) - 1;
     constexpr int NN = N * N;
-    // lanes [0, NN) and [16, 16 + NN) each own one entry (r, c) of an N x N product
-    const bool lo16 = lane < NN, hi16 = lane >= 16 && lane < 16 + NN;
-    const int q16 = lo16 ? lane : (hi16 ? lane - 16 : 0);
-    const int r = q16 / N, c = q16 % N;
+    for (int e = lane; e < NN; e += 32) {
+        sm.Qs[e] = Cq.Q[e];
+        sm.Z0[e] = 0.0;
+    }
     const SubBlocks sb(lo, hi, true);
     auto issue = [&](int b, int buf) {
         stream_rows(&sm.A[buf][0][0], A, sb.first(b), sb.count(b), NN, lane);
@@ -354,130 +446,154 @@ __global__ void __launch_bounds__(32, 1) ric_compose_kernel(const double* __rest
             cp_async_wait_all();
         }
         __syncwarp();
-        const int t0 = sb.first(b);
-        for (int j = sb.count(b) - 1; j >= 0; --j) {
-            const int t = t0 + j;
-            const double* At = sm.A[buf][j];
+        const int t0 = sb.first(b), cnt = sb.count(b);
+        // G_t = B_t R^-1 B_t' (Cq.R holds R^-1), upper triangle mirrored
+        for (int e = lane; e < cnt * NN; e += 32) {
+            const int j = e / NN, f = e % NN, r = f / N, c = f % N;
+            if (r > c) continue;
             const double* Bt = sm.B[buf][j];
-            // the step's map: E1 = A_t, C1 = B_t R^-1 B_t', J1 = Q_t
-            if (lane < N * MC) {
-                const int rr = lane / MC, cc = lane % MC;
-                double acc = 0.0;
-                for (int q = 0; q < MC; ++q) acc = fma(Bt[rr * MC + q], Cq.R[q * MC + cc], acc);  // R holds R^-1
-                sm.BRi[lane] = acc;
+            double acc = 0.0;
+#pragma unroll
+            for (int q = 0; q < MC; ++q) {
+                double bq = 0.0;
+#pragma unroll
+                for (int s = 0; s < MC; ++s) bq = fma(Cq.R[q * MC + s], Bt[c * MC + s], bq);
+                acc = fma(Bt[r * MC + q], bq, acc);
             }
-            __syncwarp();
-            if (lo16) {
-                double acc = 0.0;
-                for (int q = 0; q < MC; ++q) acc = fma(sm.BRi[r * MC + q], Bt[c * MC + q], acc);
-                sm.E1[lane] = At[lane];
-                sm.J1[lane] = t >= 1 ? Cq.Q[lane] : 0.0;
-                if (r <= c) {
-                    sm.C1[r * N + c] = acc;
-                    sm.C1[c * N + r] = acc;
-                }
-            }
-            __syncwarp();
+            sm.G[j][r * N + c] = acc;
+            sm.G[j][c * N + r] = acc;
+        }
+        __syncwarp();
+        for (int j = cnt - 1; j >= 0; --j) {
+            const int t = t0 + j;
+            const double* J1 = t >= 1 ? sm.Qs : sm.Z0;
             if (first) {
-                if (lo16) {
-                    sm.acc.E[lane] = sm.E1[lane];
-                    sm.acc.C[lane] = sm.C1[lane];
-                    sm.acc.J[lane] = sm.J1[lane];
+                for (int e = lane; e < NN; e += 32) {
+                    sm.acc.E[e] = sm.A[buf][j][e];
+                    sm.acc.C[e] = sm.G[j][e];
+                    sm.acc.J[e] = J1[e];
                 }
                 first = false;
                 __syncwarp();
                 continue;
             }
-            // acc <- (step map) o acc
-            if (lo16) sm.X[lane] = (r == c ? 1.0 : 0.0) + mat_entry<N>(sm.C1, sm.acc.J, r, c, false);
-            __syncwarp();
-            warp_inverse<N>(sm.X, sm.W, sm.aug, &sm.piv, lane);
-            if (lo16) sm.V[lane] = mat_entry<N>(sm.W, sm.E1, r, c, false);
-            if (hi16) sm.Y[lane - 16] = mat_entry<N>(sm.W, sm.C1, r, c, false);
-            __syncwarp();
-            double e_new = 0.0, u_new = 0.0;
-            if (lo16) e_new = mat_entry<N>(sm.acc.E, sm.V, r, c, false);
-            if (hi16) u_new = mat_entry<N>(sm.acc.J, sm.E1, r, c, false);
-            __syncwarp();
-            if (hi16) sm.U[lane - 16] = u_new;
-            __syncwarp();
-            double j_new = 0.0, z_new = 0.0;
-            if (lo16) {  // J = J1 + V' U
-                double acc = sm.J1[lane];
-#pragma unroll
-                for (int q = 0; q < N; ++q) acc = fma(sm.V[q * N + r], sm.U[q * N + c], acc);
-                j_new = acc;
-            }
-            if (hi16) z_new = mat_entry<N>(sm.acc.E, sm.Y, r, c, false);
-            __syncwarp();
-            if (lo16 && r <= c) {
-                sm.acc.J[r * N + c] = j_new;
-                sm.acc.J[c * N + r] = j_new;
-            }
-            if (hi16) sm.Z[lane - 16] = z_new;
-            __syncwarp();
-            double c_new = 0.0;
-            if (lo16) c_new = sm.acc.C[lane] + mat_entry<N>(sm.Z, sm.acc.E, r, c, true);  // C2 + Z E2'
-            __syncwarp();
-            if (lo16) {
-                sm.acc.E[lane] = e_new;
-                if (r <= c) {
-                    sm.acc.C[r * N + c] = c_new;
-                    sm.acc.C[c * N + r] = c_new;
-                }
-            }
-            __syncwarp();
+            compose_into<N>(sm.acc, sm.A[buf][j], sm.G[j], J1, sm.sc, lane);
         }
         __syncwarp();
     }
     bool ok = true;
-    if (lo16) {
+    for (int e = lane; e < NN; e += 32) {
         double* m = maps + (size_t)blockIdx.x * 3 * NN;
-        m[lane] = sm.acc.E[lane];
-        m[NN + lane] = sm.acc.C[lane];
-        m[2 * NN + lane] = sm.acc.J[lane];
-        ok = isfinite(sm.acc.E[lane]) && isfinite(sm.acc.C[lane]) && isfinite(sm.acc.J[lane]);
+        m[e] = sm.acc.E[e];
+        m[NN + e] = sm.acc.C[e];
+        m[2 * NN + e] = sm.acc.J[e];
+        ok &= isfinite(sm.acc.E[e]) && isfinite(sm.acc.C[e]) && isfinite(sm.acc.J[e]);
     }
-    if (!ok) raise_status(status, kDevNonfinite);
+    if (!__all_sync(0xffffffffu, ok) && lane == 0) raise_status(status, kDevNonfinite);
 }
 
-// One warp: Pin[c] = the P entering chunk c (P_{hi+1}), from P_T = Q.
+// Level 2 (long horizons): block g composes the chunk maps [g G, min((g+1)
+// G, n_maps) - 1] into one group map, the next map streaming into shared
+// memory while the current one is composed.
 template <int N>
-__global__ void __launch_bounds__(32, 1) ric_chain_kernel(const double* __restrict__ maps, int n_chunks, LqrConst Cq,
+__global__ void __launch_bounds__(32, 1) ric_group_kernel(const double* __restrict__ maps, int n_maps, int G,
+                                                          double* __restrict__ out, unsigned* status) {
+    pdl_prologue();
+    constexpr int NN = N * N;
+    __shared__ __align__(16) RicMap<N> acc;
+    __shared__ __align__(16) double Mb[2][3 * NN];
+    __shared__ __align__(16) ComposeScratch<N> sc;
+    const int lane = threadIdx.x;
+    const int lo = blockIdx.x * G, hi = min(n_maps, lo + G) - 1;
+    auto fetch = [&](int k, int buf) {
+        for (int e = lane; e < 3 * NN; e += 32) cp_async8(&Mb[buf][e], maps + (size_t)k * 3 * NN + e);
+        cp_async_commit();
+    };
+    fetch(hi, 0);
+    for (int k = hi, it = 0; k >= lo; --k, ++it) {
+        const int buf = it & 1;
+        if (k > lo) {
+            fetch(k - 1, buf ^ 1);
+            cp_async_wait_all_but_one();
+        } else {
+            cp_async_wait_all();
+        }
+        __syncwarp();
+        const double* m = Mb[buf];
+        if (k == hi) {
+            for (int e = lane; e < NN; e += 32) {
+                acc.E[e] = m[e];
+                acc.C[e] = m[NN + e];
+                acc.J[e] = m[2 * NN + e];
+            }
+            __syncwarp();
+        } else {
+            compose_into<N>(acc, m, m + NN, m + 2 * NN, sc, lane);
+        }
+    }
+    bool ok = true;
+    for (int e = lane; e < NN; e += 32) {
+        double* o = out + (size_t)blockIdx.x * 3 * NN;
+        o[e] = acc.E[e];
+        o[NN + e] = acc.C[e];
+        o[2 * NN + e] = acc.J[e];
+        ok &= isfinite(acc.E[e]) && isfinite(acc.C[e]) && isfinite(acc.J[e]);
+    }
+    if (!__all_sync(0xffffffffu, ok) && lane == 0) raise_status(status, kDevNonfinite);
+}
+
+// Chain maps backward: block b takes the maps [b seg, min((b+1) seg,
+// n_maps) - 1] from the P entering its last one (Pstart[b], or P_T = Q when
+// Pstart is null) and writes Pin[k] = the P entering map k.  A map is
+// applied as P <- J + E' (I + P C)^-1 (P E) (the same value as
+// J + E' P (I + C P)^-1 E by the push-through identity; one product level,
+// the solve, one more), the next map streaming into shared memory
+// meanwhile.
+template <int N>
+__global__ void __launch_bounds__(32, 1) ric_chain_kernel(const double* __restrict__ maps, int n_maps, int seg,
+                                                          const double* __restrict__ Pstart, LqrConst Cq,
                                                           double* __restrict__ Pin, unsigned* status) {
     pdl_prologue();
     constexpr int NN = N * N;
-    __shared__ double P[NN], X[NN], W[NN], V[NN], aug[N * 2 * N];
-    __shared__ int piv;
+    __shared__ __align__(16) double Mb[2][3 * NN];
+    __shared__ double P[NN], X[NN], PE[NN], V[NN], aug[N * 2 * N];
     const int lane = threadIdx.x;
-    const bool lo16 = lane < NN;
-    const int r = lo16 ? lane / N : 0, c = lo16 ? lane % N : 0;
-    if (lo16) P[lane] = Cq.Q[lane];
-    __syncwarp();
+    const int lo = blockIdx.x * seg, hi = min(n_maps, lo + seg) - 1;
+    const bool lo16 = lane < NN, hi16 = lane >= 16 && lane < 16 + NN;
+    const int q16 = lo16 ? lane : (hi16 ? lane - 16 : 0);
+    const int r = q16 / N, c = q16 % N;
+    if (lo16) P[lane] = Pstart ? Pstart[(size_t)blockIdx.x * NN + lane] : Cq.Q[lane];
+    auto fetch = [&](int k, int buf) {
+        for (int e = lane; e < 3 * NN; e += 32) cp_async8(&Mb[buf][e], maps + (size_t)k * 3 * NN + e);
+        cp_async_commit();
+    };
+    fetch(hi, 0);
     bool ok = true;
-    for (int k = n_chunks - 1; k >= 0; --k) {
-        const double* E = maps + (size_t)k * 3 * NN;
+    for (int k = hi, it = 0; k >= lo; --k, ++it) {
+        const int buf = it & 1;
+        if (k > lo) {
+            fetch(k - 1, buf ^ 1);
+            cp_async_wait_all_but_one();
+        } else {
+            cp_async_wait_all();
+        }
+        __syncwarp();
+        const double* E = Mb[buf];
         const double* Cm = E + NN;
         const double* J = E + 2 * NN;
         if (lo16) {
             Pin[(size_t)k * NN + lane] = P[lane];
-            X[lane] = (r == c ? 1.0 : 0.0) + mat_entry<N>(Cm, P, r, c, false);
+            X[lane] = (r == c ? 1.0 : 0.0) + mat_entry<N>(P, Cm, r, c, false);  // I + P C
         }
+        if (hi16) PE[q16] = mat_entry<N>(P, E, r, c, false);
         __syncwarp();
-        warp_inverse<N>(X, W, aug, &piv, lane);
-        if (lo16) V[lane] = mat_entry<N>(W, E, r, c, false);  // (I + C P)^-1 E
-        __syncwarp();
-        double x = 0.0;
-        if (lo16) x = mat_entry<N>(P, V, r, c, false);      // P (I + C P)^-1 E
-        __syncwarp();
-        if (lo16) X[lane] = x;
-        __syncwarp();
+        warp_solve<N, N>(X, PE, V, aug, lane);
         double pn = 0.0;
-        if (lo16) {  // J + E' X
-            double acc = J[lane];
+        if (lo16) {  // J + E' V
+            double a = J[lane];
 #pragma unroll
-            for (int q = 0; q < N; ++q) acc = fma(E[q * N + r], X[q * N + c], acc);
-            pn = acc;
+            for (int q = 0; q < N; ++q) a = fma(E[q * N + r], V[q * N + c], a);
+            pn = a;
             ok &= isfinite(pn);
         }
         __syncwarp();
@@ -1066,11 +1182,67 @@ static bool scan_plan(int T, ScanPlan* p) {
     return true;
 }
 
+// Parallel-in-time Riccati plan.  Level 1: chunks of C1 steps compose
+// their step maps (nc1 warps).  Two levels (G == 0): one warp chains the
+// nc1 chunk maps.  Three levels, for long horizons: groups of G chunk maps
+// are composed again (ng warps), one warp chains the ng group maps, and one
+// warp per group then chains its own chunk maps from the P entering it.
+// Last, every chunk runs the ordinary Riccati step over its steps.  Serial
+// depth: C1 + nc1 + C1 steps (two levels) or C1 + G + ng + G + C1 (three).
+struct RicPlan {
+    int C1, nc1, G, ng;
+};
+constexpr int kRicMinChunk = 8;  // C1 >= 8 and G >= 2 bound the scratch below
+
+// Scratch maps (each 3 n x n for the map and n x n for the P entering it)
+// for a horizon of T steps: chunk maps plus group maps.
+static size_t ric_scratch_maps(int T) {
+    const size_t nc = ((size_t)T + kRicMinChunk - 1) / kRicMinChunk;
+    return nc + (nc + 1) / 2;
+}
+
+// Cost model (ns) of one serial step of each level: its dependent latency,
+// and for the levels that run one warp per chunk the FP64 pipe time a warp
+// needs per step (B300: ~1.6 DFMA lanes per clock per SM), which bounds a
+// level once several warps share an SM.
+constexpr double kRicComposeNs = 2000, kRicComposeWarpNs = 600;
+constexpr double kRicStepNs = 1500, kRicStepWarpNs = 350;
+constexpr double kRicGroupNs = 2000, kRicChainNs = 1700, kRicLaunchNs = 2000;
+
+static RicPlan ric_plan(int T, int sms) {
+    RicPlan best{T, 1, 0, 0};
+    double best_cost = 1e300;
+    const int c_max = std::min(T, 4096);
+    for (int C1 = std::min(T, kRicMinChunk); C1 <= c_max; ++C1) {
+        const int nc1 = (T + C1 - 1) / C1;
+        if (C1 > kRicMinChunk && (T + C1 - 2) / (C1 - 1) == nc1) continue;  // same chunk count, longer chunks
+        const double w1 = (double)((nc1 + sms - 1) / sms);
+        const double lvl1 = C1 * (std::max(kRicComposeNs, w1 * kRicComposeWarpNs) +
+                                  std::max(kRicStepNs, w1 * kRicStepWarpNs));
+        const double two = lvl1 + nc1 * kRicChainNs + 3 * kRicLaunchNs;
+        if (two < best_cost) {
+            best_cost = two;
+            best = RicPlan{C1, nc1, 0, 0};
+        }
+        const int g0 = (int)sqrt(kRicChainNs * nc1 / (kRicGroupNs + kRicChainNs));
+        for (int G = std::max(2, g0 - 1); G <= std::min(nc1, g0 + 1); ++G) {
+            const int ng = (nc1 + G - 1) / G;
+            const double three = lvl1 + G * (kRicGroupNs + kRicChainNs) + ng * kRicChainNs + 5 * kRicLaunchNs;
+            if (three < best_cost) {
+                best_cost = three;
+                best = RicPlan{C1, nc1, G, ng};
+            }
+        }
+    }
+    return best;
+}
+
 // Gains per step: K [m][n], M [n][n], N [m][n], S^-1 [m][m]; then the
-// parallel Riccati's scratch: chunk maps [chunks][3][n][n] and the P
-// entering each chunk [chunks][n][n].
+// parallel Riccati's scratch: chunk maps [nc1][3][n][n], the P entering
+// each chunk [nc1][n][n], group maps [ng][3][n][n] and the P entering each
+// group [ng][n][n].
 size_t lqr_gain_doubles(int T, int n, int m) {
-    return (size_t)T * (2 * (size_t)m * n + (size_t)n * n + (size_t)m * m) + (size_t)kMaxChunks * 4 * n * n;
+    return (size_t)T * (2 * (size_t)m * n + (size_t)n * n + (size_t)m * m) + ric_scratch_maps(T) * 4 * n * n;
 }
 
 struct AffineBufs {
@@ -1113,21 +1285,40 @@ constexpr int kParRiccatiMinT = 64;
 
 template <int N, int MC>
 static void launch_riccati_t(const double* A, const double* B, const LqrConst& C, const LqrConst& Ci, int T,
-                             double* gains, unsigned* st, cudaStream_t s) {
+                             double* gains, int sms, unsigned* st, cudaStream_t s) {
     double* K = gains;
     double* M = gains + (size_t)T * MC * N;
     double* Nt = M + (size_t)T * N * N;
     double* Si = Nt + (size_t)T * MC * N;
-    ScanPlan pl;
-    if (T < kParRiccatiMinT || !scan_plan(T, &pl)) {
+    if (T < kParRiccatiMinT) {
         launch_pdl(riccati_kernel<N, MC>, dim3(1), dim3(32), 0, s, A, B, C, T, K, M, Nt, Si, st, nullptr, T);
         return;
     }
-    double* maps = Si + (size_t)T * MC * MC;
-    double* pin = maps + (size_t)kMaxChunks * 3 * N * N;
-    launch_pdl(ric_compose_kernel<N, MC>, dim3(pl.n_chunks), dim3(32), 0, s, A, B, Ci, T, pl.C, maps, st);
-    launch_pdl(ric_chain_kernel<N>, dim3(1), dim3(32), 0, s, maps, pl.n_chunks, C, pin, st);
-    launch_pdl(riccati_kernel<N, MC>, dim3(pl.n_chunks), dim3(32), 0, s, A, B, C, T, K, M, Nt, Si, st, pin, pl.C);
+    static thread_local int memo_T = -1, memo_sms = -1;
+    static thread_local RicPlan pl;
+    if (memo_T != T || memo_sms != sms) {
+        pl = ric_plan(T, sms);
+        memo_T = T;
+        memo_sms = sms;
+    }
+    constexpr size_t NN = (size_t)N * N;
+    double* maps1 = Si + (size_t)T * MC * MC;
+    double* pin1 = maps1 + (size_t)pl.nc1 * 3 * NN;
+    double* maps2 = pin1 + (size_t)pl.nc1 * NN;
+    double* pin2 = maps2 + (size_t)pl.ng * 3 * NN;
+    launch_pdl(ric_compose_kernel<N, MC>, dim3(pl.nc1), dim3(32), 0, s, A, B, Ci, T, pl.C1, maps1, st);
+    if (pl.G == 0) {
+        launch_pdl(ric_chain_kernel<N>, dim3(1), dim3(32), 0, s, (const double*)maps1, pl.nc1, pl.nc1,
+                   (const double*)nullptr, C, pin1, st);
+    } else {
+        launch_pdl(ric_group_kernel<N>, dim3(pl.ng), dim3(32), 0, s, (const double*)maps1, pl.nc1, pl.G, maps2, st);
+        launch_pdl(ric_chain_kernel<N>, dim3(1), dim3(32), 0, s, (const double*)maps2, pl.ng, pl.ng,
+                   (const double*)nullptr, C, pin2, st);
+        launch_pdl(ric_chain_kernel<N>, dim3(pl.ng), dim3(32), 0, s, (const double*)maps1, pl.nc1, pl.G,
+                   (const double*)pin2, C, pin1, st);
+    }
+    launch_pdl(riccati_kernel<N, MC>, dim3(pl.nc1), dim3(32), 0, s, A, B, C, T, K, M, Nt, Si, st,
+               (const double*)pin1, pl.C1);
 }
 
 // R^-1 on the host (m <= 3, Gauss-Jordan with partial pivoting).
@@ -1199,7 +1390,7 @@ cov_status lqr_riccati(cov_ctx* ctx, int n, int m, const double* A, const double
     if (!invert_small(R, m, Ci.R)) return COV_ERR_INVALID_ARG;
 #define COV_RIC_CASE(NN, MM)                                                      \
     if (n == NN && m == MM) {                                                     \
-        launch_riccati_t<NN, MM>(A, B, C, Ci, T, gains, ctx->status, stream);     \
+        launch_riccati_t<NN, MM>(A, B, C, Ci, T, gains, ctx->num_sms, ctx->status, stream);     \
         return cuda_failed(ctx, cudaGetLastError()) ? COV_ERR_CUDA : COV_OK;     \
     }
     COV_LQR_DISPATCH(COV_RIC_CASE)
