@@ -86,10 +86,11 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait_all_but_one() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
-// Copy rows t0 .. t0+cnt-1 (each `e` doubles) of src into dst.
+// Copy rows t0 .. t0+cnt-1 (each `e` doubles) of src into dst; thread
+// `lane` of `nthreads` takes every nthreads-th double.
 __device__ __forceinline__ void stream_rows(double* dst, const double* __restrict__ src, int t0, int cnt, int e,
-                                            int lane) {
-    for (int i = lane; i < cnt * e; i += 32) cp_async8(dst + i, src + (size_t)t0 * e + i);
+                                            int lane, int nthreads = 32) {
+    for (int i = lane; i < cnt * e; i += nthreads) cp_async8(dst + i, src + (size_t)t0 * e + i);
 }
 
 // Sub-blocks of a step range [lo, hi] (inclusive), visited backward or
@@ -258,67 +259,92 @@ __global__ void __launch_bounds__(32, 1) riccati_kernel(const double* __restrict
 // that P (riccati_kernel).
 // ---------------------------------------------------------------------------
 
-// Solve X Z = Y for a general N x N matrix X (N <= 4) and an N x K
-// right-hand side Y by Gauss-Jordan elimination with partial pivoting on
-// [X | Y]; Z (N x K) is written.  aug is N x (N + K) shared scratch.  The
-// pivot search runs across lanes 0..3 and each elimination pass folds the
-// row swap in, so a pivot costs one reciprocal, one FMA and two warp
-// syncs.  Every lane calls it.
-template <int N, int K>
-__device__ void warp_solve(const double* X, const double* Y, double* Z, double* aug, int lane) {
-    static_assert(N <= 4, "pivot search spans lanes 0..3");
-    constexpr int W = N + K, E = N * W, PER = (E + 31) / 32;
-    for (int e = lane; e < E; e += 32) {
-        const int r = e / W, c = e % W;
-        aug[e] = c < N ? X[r * N + c] : Y[r * K + (c - N)];
-    }
-    __syncwarp();
+// B300's FP64 pipe takes one warp-wide FP64 instruction per ~64 clocks per
+// warp however many lanes are active (two warps of an SM run in parallel,
+// four nearly so), so the serial steps below are written for few FP64
+// instructions per warp: each product entry is one lane's dot product, the
+// lanes of a warp all work, and where a phase has more than 32 entries a
+// second warp takes the rest.
+template <int N>
+struct RicThreads {
+    static constexpr int value = N == 4 ? 64 : 32;
+};
+template <int NT>
+__device__ __forceinline__ void ric_sync() {
+    if constexpr (NT == 32)
+        __syncwarp();
+    else
+        __syncthreads();
+}
+
+// |x| as an integer key: IEEE magnitudes order like their bit patterns.
+__device__ __forceinline__ unsigned long long mag_key(double x) {
+    return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+}
+
+// Solve X Z = Y (X: N x N, N <= 4; Y: N x K) by Gauss-Jordan elimination
+// with partial pivoting in division-free form, with the NT threads of the
+// block.  aug (N x (N + K), row-major, shared) holds [X | Y] on entry.  At
+// pivot k (row p, the largest |aug[r][k]| over r >= k, the first on ties;
+// every thread finds it with integer compares) rows k and p trade places
+// and every other row r becomes row_r * piv - row_r[k] * row_p: the
+// textbook elimination row times piv, the same factor for every row, so the
+// pivot choices match the textbook's.  X's part ends diagonal, and
+// Z[r][c] = aug[r][N + c] / aug[r][r]: one division per row, all rows at
+// once, instead of a reciprocal per pivot on the critical path.  A pivot
+// step is two dependent FP64 instructions per thread.  Rows grow by at
+// most the pivots' product (for N = 4 bounded by 2^15 M^16 when the entries
+// are at most M); a result out of range ends nonfinite and is reported.
+template <int N, int K, int NT>
+__device__ void block_solve(double* aug, double* Z, int tid) {
+    static_assert(N <= 4, "small systems only");
+    constexpr int W = N + K, E = N * W, PER = (E + NT - 1) / NT;
 #pragma unroll
     for (int k = 0; k < N; ++k) {
-        // pivot row p: the largest |aug[r][k]| over rows r >= k, the first on ties
-        double v = (lane >= k && lane < N) ? fabs(aug[lane * W + k]) : -1.0;
-        int p = lane;
+        int p = k;
+        unsigned long long best = mag_key(aug[k * W + k]);
 #pragma unroll
-        for (int o = 1; o < 4; o <<= 1) {
-            const double v2 = __shfl_xor_sync(0xffffffffu, v, o);
-            const int p2 = __shfl_xor_sync(0xffffffffu, p, o);
-            if (v2 > v || (v2 == v && p2 < p)) {
-                v = v2;
-                p = p2;
+        for (int r = k + 1; r < N; ++r) {
+            const unsigned long long v = mag_key(aug[r * W + k]);
+            if (v > best) {
+                best = v;
+                p = r;
             }
         }
-        p = __shfl_sync(0xffffffffu, p, 0);
-        const double inv_piv = 1.0 / aug[p * W + k];
-        // rows k and p trade places; the pivot row is scaled, the others reduced
+        const double piv = aug[p * W + k];
         double nv[PER];
 #pragma unroll
         for (int q = 0; q < PER; ++q) {
-            const int e = lane + 32 * q;
+            const int e = tid + NT * q;
             nv[q] = 0.0;
             if (e < E) {
                 const int r = e / W, c = e % W;
-                const double pr = aug[p * W + c] * inv_piv;
                 const int src = r == p ? k : r;
-                nv[q] = r == k ? pr : fma(-aug[src * W + k], pr, aug[src * W + c]);
+                const double pc = aug[p * W + c];
+                const double o = fma(aug[src * W + c], piv, -(aug[src * W + k] * pc));
+                nv[q] = r == k ? pc : o;
             }
         }
-        __syncwarp();
+        ric_sync<NT>();
 #pragma unroll
         for (int q = 0; q < PER; ++q)
-            if (lane + 32 * q < E) aug[lane + 32 * q] = nv[q];
-        __syncwarp();
+            if (tid + NT * q < E) aug[tid + NT * q] = nv[q];
+        ric_sync<NT>();
     }
-    for (int e = lane; e < N * K; e += 32) Z[e] = aug[(e / K) * W + N + e % K];
-    __syncwarp();
+    for (int e = tid; e < N * K; e += NT) {
+        const int r = e / K;
+        Z[e] = aug[r * W + N + e % K] / aug[r * W + r];
+    }
+    ric_sync<NT>();
 }
 
-// Entry (r, c) of X Y (yT: X Y'), N x N row-major.
+// a0 + sum over q < N of X[q xs] Y[q ys].
 template <int N>
-__device__ __forceinline__ double mat_entry(const double* X, const double* Y, int r, int c, bool yT) {
-    double acc = 0.0;
+__device__ __forceinline__ double dotn(const double* X, int xs, const double* Y, int ys, double a0) {
+    double a = a0;
 #pragma unroll
-    for (int q = 0; q < N; ++q) acc = fma(X[r * N + q], yT ? Y[c * N + q] : Y[q * N + c], acc);
-    return acc;
+    for (int q = 0; q < N; ++q) a = fma(X[q * xs], Y[q * ys], a);
+    return a;
 }
 
 template <int N>
@@ -328,66 +354,59 @@ struct RicMap {
 
 template <int N>
 struct ComposeScratch {
-    double X[N * N], R2[N * N], U[N * N], VY[N * 2 * N];
-    double aug[N * 3 * N];
+    double aug[N * 3 * N];  // [X | E1 | C1 E2'] for the solve
+    double U[N * N];        // J2 E1
+    double VY[N * 2 * N];   // X^-1 [E1 | C1 E2']
 };
 
 // acc <- F1 o acc, where F1 = (E1, C1, J1) is the map of the earlier steps
 // and acc = (E2, C2, J2) that of the later ones.  With X = I + C1 J2 and
-// [V | Y] = X^-1 [E1 | C1 E2'] (one Gauss-Jordan solve):
+// [V | Y] = X^-1 [E1 | C1 E2'] (one solve):
 //   E = E2 V,  C = C2 + E2 Y,  J = J1 + V' (J2 E1)
 // (the composition rule above with Y = W C1 E2'), so a step is one product
-// level, the solve, and one more product level.  C and J are symmetric in
-// exact arithmetic and are kept so (upper triangle, mirrored).  Every lane
-// calls it.
-template <int N>
+// level, the solve, and one more product level.  Each product entry is one
+// thread's dot product with thread-selected operands (no divergent
+// branches).  C and J are symmetric in exact arithmetic and are kept so
+// (upper triangle, mirrored).  All NT threads of the block call it.
+template <int N, int NT>
 __device__ void compose_into(RicMap<N>& acc, const double* E1, const double* C1, const double* J1,
-                             ComposeScratch<N>& sc, int lane) {
-    constexpr int NN = N * N;
-    // X = I + C1 J2, R2 = C1 E2', U = J2 E1: independent, 3 NN entries
+                             ComposeScratch<N>& sc, int tid) {
+    constexpr int NN = N * N, W = 3 * N, P = (3 * NN + NT - 1) / NT;
+    // X = I + C1 J2 -> aug[:, 0:N], C1 E2' -> aug[:, 2N:3N], U = J2 E1; E1 -> aug[:, N:2N]
+    for (int e = tid; e < NN; e += NT) sc.aug[(e / N) * W + N + e % N] = E1[e];
 #pragma unroll
-    for (int q = 0; q < (3 * NN + 31) / 32; ++q) {
-        const int e = lane + 32 * q;
+    for (int q = 0; q < P; ++q) {
+        const int e = tid + NT * q;
         if (e < 3 * NN) {
             const int which = e / NN, f = e % NN, r = f / N, c = f % N;
-            if (which == 0)
-                sc.X[f] = (r == c ? 1.0 : 0.0) + mat_entry<N>(C1, acc.J, r, c, false);
-            else if (which == 1)
-                sc.R2[f] = mat_entry<N>(C1, acc.E, r, c, true);
-            else
-                sc.U[f] = mat_entry<N>(acc.J, E1, r, c, false);
+            const double* x = which == 2 ? acc.J + r * N : C1 + r * N;
+            const double* y = which == 0 ? acc.J + c : (which == 1 ? acc.E + c * N : E1 + c);
+            const int ys = which == 1 ? 1 : N;
+            double* dst = which == 2 ? sc.U + f : sc.aug + r * W + (which == 0 ? c : 2 * N + c);
+            *dst = dotn<N>(x, 1, y, ys, which == 0 && r == c ? 1.0 : 0.0);
         }
     }
-    __syncwarp();
-    // [E1 | R2] side by side as the right-hand side
-    for (int e = lane; e < 2 * NN; e += 32) {
-        const int r = e / (2 * N), c = e % (2 * N);
-        sc.VY[e] = c < N ? E1[r * N + c] : sc.R2[r * N + c - N];
-    }
-    __syncwarp();
-    warp_solve<N, 2 * N>(sc.X, sc.VY, sc.VY, sc.aug, lane);
+    ric_sync<NT>();
+    block_solve<N, 2 * N, NT>(sc.aug, sc.VY, tid);
     // E = E2 V, C = C2 + E2 Y, J = J1 + V' U
-    double nv[(3 * NN + 31) / 32];
+    double nv[P];
 #pragma unroll
-    for (int q = 0; q < (3 * NN + 31) / 32; ++q) {
-        const int e = lane + 32 * q;
+    for (int q = 0; q < P; ++q) {
+        const int e = tid + NT * q;
         nv[q] = 0.0;
         if (e < 3 * NN) {
             const int which = e / NN, f = e % NN, r = f / N, c = f % N;
-            double a = which == 0 ? 0.0 : (which == 1 ? acc.C[f] : J1[f]);
-#pragma unroll
-            for (int k = 0; k < N; ++k) {
-                if (which == 0) a = fma(acc.E[r * N + k], sc.VY[k * 2 * N + c], a);
-                else if (which == 1) a = fma(acc.E[r * N + k], sc.VY[k * 2 * N + N + c], a);
-                else a = fma(sc.VY[k * 2 * N + r], sc.U[k * N + c], a);
-            }
-            nv[q] = a;
+            const double* x = which == 2 ? sc.VY + r : acc.E + r * N;
+            const int xs = which == 2 ? 2 * N : 1;
+            const double* y = which == 2 ? sc.U + c : sc.VY + (which == 1 ? N : 0) + c;
+            const int ys = which == 2 ? N : 2 * N;
+            nv[q] = dotn<N>(x, xs, y, ys, which == 0 ? 0.0 : (which == 1 ? acc.C[f] : J1[f]));
         }
     }
-    __syncwarp();
+    ric_sync<NT>();
 #pragma unroll
-    for (int q = 0; q < (3 * NN + 31) / 32; ++q) {
-        const int e = lane + 32 * q;
+    for (int q = 0; q < P; ++q) {
+        const int e = tid + NT * q;
         if (e < 3 * NN) {
             const int which = e / NN, f = e % NN, r = f / N, c = f % N;
             if (which == 0) {
@@ -399,7 +418,7 @@ __device__ void compose_into(RicMap<N>& acc, const double* E1, const double* C1,
             }
         }
     }
-    __syncwarp();
+    ric_sync<NT>();
 }
 
 template <int N, int MC>
@@ -415,24 +434,25 @@ struct ComposeSmem {
 // Level 1: block c composes the step maps of chunk c (steps [c Cc,
 // min((c+1) Cc, T) - 1]).  The step map is E1 = A_t, C1 = B_t R^-1 B_t',
 // J1 = Q_t; the C1 of a whole streamed sub-block are formed together
-// before the serial loop, which then only composes.
+// before the serial loop, which then only composes.  Launched with
+// RicThreads<N>::value threads.
 template <int N, int MC>
-__global__ void __launch_bounds__(32, 1) ric_compose_kernel(const double* __restrict__ A, const double* __restrict__ B,
-                                                            LqrConst Cq, int T, int Cc,
-                                                            double* __restrict__ maps, unsigned* status) {
+__global__ void __launch_bounds__(RicThreads<N>::value, 1)
+    ric_compose_kernel(const double* __restrict__ A, const double* __restrict__ B, LqrConst Cq, int T, int Cc,
+                       double* __restrict__ maps, unsigned* status) {
     pdl_prologue();
+    constexpr int NT = RicThreads<N>::value, NN = N * N;
     __shared__ __align__(16) ComposeSmem<N, MC> sm;
-    const int lane = threadIdx.x;
+    const int tid = threadIdx.x;
     const int lo = blockIdx.x * Cc, hi = min(T, lo + Cc) - 1;
-    constexpr int NN = N * N;
-    for (int e = lane; e < NN; e += 32) {
+    for (int e = tid; e < NN; e += NT) {
         sm.Qs[e] = Cq.Q[e];
         sm.Z0[e] = 0.0;
     }
     const SubBlocks sb(lo, hi, true);
     auto issue = [&](int b, int buf) {
-        stream_rows(&sm.A[buf][0][0], A, sb.first(b), sb.count(b), NN, lane);
-        stream_rows(&sm.B[buf][0][0], B, sb.first(b), sb.count(b), N * MC, lane);
+        stream_rows(&sm.A[buf][0][0], A, sb.first(b), sb.count(b), NN, tid, NT);
+        stream_rows(&sm.B[buf][0][0], B, sb.first(b), sb.count(b), N * MC, tid, NT);
         cp_async_commit();
     };
     issue(0, 0);
@@ -445,10 +465,10 @@ __global__ void __launch_bounds__(32, 1) ric_compose_kernel(const double* __rest
         } else {
             cp_async_wait_all();
         }
-        __syncwarp();
+        ric_sync<NT>();
         const int t0 = sb.first(b), cnt = sb.count(b);
         // G_t = B_t R^-1 B_t' (Cq.R holds R^-1), upper triangle mirrored
-        for (int e = lane; e < cnt * NN; e += 32) {
+        for (int e = tid; e < cnt * NN; e += NT) {
             const int j = e / NN, f = e % NN, r = f / N, c = f % N;
             if (r > c) continue;
             const double* Bt = sm.B[buf][j];
@@ -463,50 +483,52 @@ __global__ void __launch_bounds__(32, 1) ric_compose_kernel(const double* __rest
             sm.G[j][r * N + c] = acc;
             sm.G[j][c * N + r] = acc;
         }
-        __syncwarp();
+        ric_sync<NT>();
         for (int j = cnt - 1; j >= 0; --j) {
             const int t = t0 + j;
             const double* J1 = t >= 1 ? sm.Qs : sm.Z0;
             if (first) {
-                for (int e = lane; e < NN; e += 32) {
+                for (int e = tid; e < NN; e += NT) {
                     sm.acc.E[e] = sm.A[buf][j][e];
                     sm.acc.C[e] = sm.G[j][e];
                     sm.acc.J[e] = J1[e];
                 }
                 first = false;
-                __syncwarp();
+                ric_sync<NT>();
                 continue;
             }
-            compose_into<N>(sm.acc, sm.A[buf][j], sm.G[j], J1, sm.sc, lane);
+            compose_into<N, NT>(sm.acc, sm.A[buf][j], sm.G[j], J1, sm.sc, tid);
         }
-        __syncwarp();
+        ric_sync<NT>();
     }
     bool ok = true;
-    for (int e = lane; e < NN; e += 32) {
+    for (int e = tid; e < NN; e += NT) {
         double* m = maps + (size_t)blockIdx.x * 3 * NN;
         m[e] = sm.acc.E[e];
         m[NN + e] = sm.acc.C[e];
         m[2 * NN + e] = sm.acc.J[e];
         ok &= isfinite(sm.acc.E[e]) && isfinite(sm.acc.C[e]) && isfinite(sm.acc.J[e]);
     }
-    if (!__all_sync(0xffffffffu, ok) && lane == 0) raise_status(status, kDevNonfinite);
+    if (__syncthreads_or(!ok) && tid == 0) raise_status(status, kDevNonfinite);
 }
 
 // Level 2 (long horizons): block g composes the chunk maps [g G, min((g+1)
 // G, n_maps) - 1] into one group map, the next map streaming into shared
-// memory while the current one is composed.
+// memory while the current one is composed.  Launched with
+// RicThreads<N>::value threads.
 template <int N>
-__global__ void __launch_bounds__(32, 1) ric_group_kernel(const double* __restrict__ maps, int n_maps, int G,
-                                                          double* __restrict__ out, unsigned* status) {
+__global__ void __launch_bounds__(RicThreads<N>::value, 1)
+    ric_group_kernel(const double* __restrict__ maps, int n_maps, int G, double* __restrict__ out,
+                     unsigned* status) {
     pdl_prologue();
-    constexpr int NN = N * N;
+    constexpr int NT = RicThreads<N>::value, NN = N * N;
     __shared__ __align__(16) RicMap<N> acc;
     __shared__ __align__(16) double Mb[2][3 * NN];
     __shared__ __align__(16) ComposeScratch<N> sc;
-    const int lane = threadIdx.x;
+    const int tid = threadIdx.x;
     const int lo = blockIdx.x * G, hi = min(n_maps, lo + G) - 1;
     auto fetch = [&](int k, int buf) {
-        for (int e = lane; e < 3 * NN; e += 32) cp_async8(&Mb[buf][e], maps + (size_t)k * 3 * NN + e);
+        for (int e = tid; e < 3 * NN; e += NT) cp_async8(&Mb[buf][e], maps + (size_t)k * 3 * NN + e);
         cp_async_commit();
     };
     fetch(hi, 0);
@@ -518,28 +540,28 @@ __global__ void __launch_bounds__(32, 1) ric_group_kernel(const double* __restri
         } else {
             cp_async_wait_all();
         }
-        __syncwarp();
+        ric_sync<NT>();
         const double* m = Mb[buf];
         if (k == hi) {
-            for (int e = lane; e < NN; e += 32) {
+            for (int e = tid; e < NN; e += NT) {
                 acc.E[e] = m[e];
                 acc.C[e] = m[NN + e];
                 acc.J[e] = m[2 * NN + e];
             }
-            __syncwarp();
+            ric_sync<NT>();
         } else {
-            compose_into<N>(acc, m, m + NN, m + 2 * NN, sc, lane);
+            compose_into<N, NT>(acc, m, m + NN, m + 2 * NN, sc, tid);
         }
     }
     bool ok = true;
-    for (int e = lane; e < NN; e += 32) {
+    for (int e = tid; e < NN; e += NT) {
         double* o = out + (size_t)blockIdx.x * 3 * NN;
         o[e] = acc.E[e];
         o[NN + e] = acc.C[e];
         o[2 * NN + e] = acc.J[e];
         ok &= isfinite(acc.E[e]) && isfinite(acc.C[e]) && isfinite(acc.J[e]);
     }
-    if (!__all_sync(0xffffffffu, ok) && lane == 0) raise_status(status, kDevNonfinite);
+    if (__syncthreads_or(!ok) && tid == 0) raise_status(status, kDevNonfinite);
 }
 
 // Chain maps backward: block b takes the maps [b seg, min((b+1) seg,
@@ -556,12 +578,11 @@ __global__ void __launch_bounds__(32, 1) ric_chain_kernel(const double* __restri
     pdl_prologue();
     constexpr int NN = N * N;
     __shared__ __align__(16) double Mb[2][3 * NN];
-    __shared__ double P[NN], X[NN], PE[NN], V[NN], aug[N * 2 * N];
+    __shared__ double P[NN], V[NN], aug[N * 2 * N];
     const int lane = threadIdx.x;
     const int lo = blockIdx.x * seg, hi = min(n_maps, lo + seg) - 1;
-    const bool lo16 = lane < NN, hi16 = lane >= 16 && lane < 16 + NN;
-    const int q16 = lo16 ? lane : (hi16 ? lane - 16 : 0);
-    const int r = q16 / N, c = q16 % N;
+    const bool lo16 = lane < NN;
+    const int f = lane % NN, r = f / N, c = f % N;
     if (lo16) P[lane] = Pstart ? Pstart[(size_t)blockIdx.x * NN + lane] : Cq.Q[lane];
     auto fetch = [&](int k, int buf) {
         for (int e = lane; e < 3 * NN; e += 32) cp_async8(&Mb[buf][e], maps + (size_t)k * 3 * NN + e);
@@ -581,19 +602,18 @@ __global__ void __launch_bounds__(32, 1) ric_chain_kernel(const double* __restri
         const double* E = Mb[buf];
         const double* Cm = E + NN;
         const double* J = E + 2 * NN;
-        if (lo16) {
-            Pin[(size_t)k * NN + lane] = P[lane];
-            X[lane] = (r == c ? 1.0 : 0.0) + mat_entry<N>(P, Cm, r, c, false);  // I + P C
+        // [I + P C | P E] -> aug (lanes [0, NN) the left block, [NN, 2 NN) the right)
+        if (lane < 2 * NN) {
+            const bool left = lane < NN;
+            aug[r * 2 * N + (left ? c : N + c)] =
+                dotn<N>(P + r * N, 1, (left ? Cm : E) + c, N, left && r == c ? 1.0 : 0.0);
         }
-        if (hi16) PE[q16] = mat_entry<N>(P, E, r, c, false);
+        if (lo16) Pin[(size_t)k * NN + lane] = P[lane];
         __syncwarp();
-        warp_solve<N, N>(X, PE, V, aug, lane);
+        block_solve<N, N, 32>(aug, V, lane);
         double pn = 0.0;
         if (lo16) {  // J + E' V
-            double a = J[lane];
-#pragma unroll
-            for (int q = 0; q < N; ++q) a = fma(E[q * N + r], V[q * N + c], a);
-            pn = a;
+            pn = dotn<N>(E + r, N, V + c, N, J[f]);
             ok &= isfinite(pn);
         }
         __syncwarp();
@@ -1306,12 +1326,12 @@ static void launch_riccati_t(const double* A, const double* B, const LqrConst& C
     double* pin1 = maps1 + (size_t)pl.nc1 * 3 * NN;
     double* maps2 = pin1 + (size_t)pl.nc1 * NN;
     double* pin2 = maps2 + (size_t)pl.ng * 3 * NN;
-    launch_pdl(ric_compose_kernel<N, MC>, dim3(pl.nc1), dim3(32), 0, s, A, B, Ci, T, pl.C1, maps1, st);
+    launch_pdl(ric_compose_kernel<N, MC>, dim3(pl.nc1), dim3(RicThreads<N>::value), 0, s, A, B, Ci, T, pl.C1, maps1, st);
     if (pl.G == 0) {
         launch_pdl(ric_chain_kernel<N>, dim3(1), dim3(32), 0, s, (const double*)maps1, pl.nc1, pl.nc1,
                    (const double*)nullptr, C, pin1, st);
     } else {
-        launch_pdl(ric_group_kernel<N>, dim3(pl.ng), dim3(32), 0, s, (const double*)maps1, pl.nc1, pl.G, maps2, st);
+        launch_pdl(ric_group_kernel<N>, dim3(pl.ng), dim3(RicThreads<N>::value), 0, s, (const double*)maps1, pl.nc1, pl.G, maps2, st);
         launch_pdl(ric_chain_kernel<N>, dim3(1), dim3(32), 0, s, (const double*)maps2, pl.ng, pl.ng,
                    (const double*)nullptr, C, pin2, st);
         launch_pdl(ric_chain_kernel<N>, dim3(pl.ng), dim3(32), 0, s, (const double*)maps1, pl.nc1, pl.G,
