@@ -223,13 +223,13 @@ __device__ __forceinline__ void tmem_wait_ld(uint32_t (&v)[32]) {
 
 // Programmatic dependent launch, first statement of a kernel launched with
 // launch_pdl: wait until the previous grid in the stream has completed and
-// its writes are visible, then let the next grid start launching.  Waiting
-// first keeps the chain's guarantee: once a grid has started, the grid two
-// launches back has completed.
-__device__ __forceinline__ void pdl_prologue() {
-    asm volatile("griddepcontrol.wait;" ::: "memory");
-    asm volatile("griddepcontrol.launch_dependents;" :::);
-}
+// its writes are visible.  The next grid's launch is triggered implicitly
+// as this grid's CTAs exit, which still overlaps its launch with this
+// grid's tail.  (Triggering at the start let the next grid's CTAs take up
+// residence and wait beside long grids of small blocks, and slowed the LQR
+// scans at T = 65536 from 528 to 793 us; the all-pairs kernels, which place
+// their own trigger, were unaffected either way.)
+__device__ __forceinline__ void pdl_prologue() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 // L2-coherent loads for data written by other CTAs of the same launch.
 __device__ __forceinline__ float ld_cg(const float* p) { return __ldcg(p); }

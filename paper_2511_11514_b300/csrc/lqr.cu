@@ -706,24 +706,31 @@ __global__ void __launch_bounds__(32) compose_kernel(const double* __restrict__ 
     if (lane < NX) maps[(size_t)blockIdx.x * NX + lane] = X[lane];
 }
 
-// Chain the chunk maps (one warp): bnd[c] = the value entering chunk c
-// (BWD: p_{hi+1}, starting from p_T = -Q abar_T or the given w0; FWD: z_lo,
-// starting from 0).
+// Chain chunk maps (one warp per block): block b takes the maps [b seg,
+// min((b+1) seg, n_maps) - 1] in the scan's direction and writes bnd[c] =
+// the value entering chunk c (BWD: p_{hi+1}; FWD: z_lo).  The first value is
+// start[b] when start is given (the value entering the block's group), else
+// that of the whole recursion: BWD p_T = -Q abar_T or the given w0, FWD 0.
+// The block's maps are staged in dynamic shared memory (seg x N x (N+1)).
 template <int N, bool BWD>
-__global__ void __launch_bounds__(32, 1) boundaries_kernel(const double* __restrict__ maps, int n_chunks, LqrConst Cq,
+__global__ void __launch_bounds__(32, 1) boundaries_kernel(const double* __restrict__ maps, int n_maps, int seg,
+                                                           const double* __restrict__ start, LqrConst Cq,
                                                            const double* __restrict__ abar,
                                                            const double* __restrict__ w0, int T,
                                                            double* __restrict__ bnd) {
     pdl_prologue();
-    extern __shared__ __align__(16) double mp[];  // [n_chunks][N][N+1]
+    extern __shared__ __align__(16) double mp[];  // [seg][N][N+1]
     __shared__ double w[N];
     const int lane = threadIdx.x;
     constexpr int NX = N * (N + 1);
-    for (int i = lane; i < n_chunks * NX; i += 32) cp_async8(mp + i, maps + i);
+    const int lo = blockIdx.x * seg, cnt = min(n_maps, lo + seg) - lo;
+    for (int i = lane; i < cnt * NX; i += 32) cp_async8(mp + i, maps + (size_t)lo * NX + i);
     cp_async_commit();
     if (lane < N) {
         double acc = 0.0;
-        if constexpr (BWD) {
+        if (start) {
+            acc = start[(size_t)blockIdx.x * N + lane];
+        } else if constexpr (BWD) {
             if (w0) {
                 acc = w0[lane];
             } else {
@@ -735,20 +742,58 @@ __global__ void __launch_bounds__(32, 1) boundaries_kernel(const double* __restr
     }
     cp_async_wait_all();
     __syncwarp();
-    for (int k = 0; k < n_chunks; ++k) {
-        const int c = BWD ? n_chunks - 1 - k : k;
+    for (int k = 0; k < cnt; ++k) {
+        const int c = BWD ? cnt - 1 - k : k;
         const double* m = mp + (size_t)c * NX;
         double acc = 0.0;
         if (lane < N) {
-            bnd[(size_t)c * N + lane] = w[lane];
-            acc = m[lane * (N + 1) + N];
-#pragma unroll
-            for (int q = 0; q < N; ++q) acc = fma(m[lane * (N + 1) + q], w[q], acc);
+            bnd[(size_t)(lo + c) * N + lane] = w[lane];
+            acc = dotn<N>(m + lane * (N + 1), 1, w, 1, m[lane * (N + 1) + N]);
         }
         __syncwarp();
         if (lane < N) w[lane] = acc;
         __syncwarp();
     }
+}
+
+// Level 2 of a long scan: block g composes the chunk maps [g G, min((g+1)
+// G, n_maps) - 1] in the scan's direction into one group map (map c after
+// the maps before it: (Phi_c Phi | Phi_c phi + phi_c)), the next map
+// streaming into shared memory meanwhile.  One warp.
+template <int N, bool BWD>
+__global__ void __launch_bounds__(32, 1) affine_group_kernel(const double* __restrict__ maps, int n_maps, int G,
+                                                             double* __restrict__ out) {
+    pdl_prologue();
+    constexpr int NX = N * (N + 1);
+    __shared__ __align__(16) double Mb[2][NX];
+    __shared__ double X[NX];
+    const int lane = threadIdx.x;
+    const int lo = blockIdx.x * G, cnt = min(n_maps, lo + G) - lo;
+    const int xr = lane / (N + 1), xc = lane % (N + 1);
+    auto fetch = [&](int k, int buf) {
+        const int c = lo + (BWD ? cnt - 1 - k : k);
+        if (lane < NX) cp_async8(&Mb[buf][lane], maps + (size_t)c * NX + lane);
+        cp_async_commit();
+    };
+    fetch(0, 0);
+    for (int k = 0; k < cnt; ++k) {
+        const int buf = k & 1;
+        if (k + 1 < cnt) {
+            fetch(k + 1, buf ^ 1);
+            cp_async_wait_all_but_one();
+        } else {
+            cp_async_wait_all();
+        }
+        __syncwarp();
+        const double* m = Mb[buf];
+        double acc = 0.0;
+        if (lane < NX)
+            acc = k == 0 ? m[lane] : dotn<N>(m + xr * (N + 1), 1, X + xc, N + 1, xc == N ? m[xr * (N + 1) + N] : 0.0);
+        __syncwarp();
+        if (lane < NX) X[lane] = acc;
+        __syncwarp();
+    }
+    if (lane < NX) out[(size_t)blockIdx.x * NX + lane] = X[lane];
 }
 
 // Fill the steps of one chunk from its boundary value.
@@ -1185,21 +1230,70 @@ int model_dims(int model, int* n, int* m) {
 // ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
+// Chunked scan plan for the affine recursions.  Level 1: chunks of C steps
+// compose their maps and later fill their steps (one warp each).  Two
+// levels (G == 0): one warp chains the n_chunks chunk maps.  Three levels:
+// groups of G chunk maps are composed (n_groups warps), one warp chains the
+// group maps, one warp per group chains its chunk maps from the value
+// entering the group.  Serial depth C + n_chunks + C or C + G + n_groups +
+// G + C steps.
 struct ScanPlan {
-    int C, n_chunks;
+    int C, n_chunks, G, n_groups;
 };
+// Most chunks a plan for T steps may use (chunks of 8 steps and more, or
+// up to 64 chunks for short horizons); with G >= 2 at most half as many
+// groups.  The scratch is sized by it.
+static int scan_chunk_cap(int T) {
+    return std::max((T + 7) / 8, std::min(T, 64));
+}
+
+// Cost (us) of one serial step of each scan level, and of a launch; the
+// chunk levels also pay the FP64 pipe time of the warps sharing an SM
+// (~N and ~N + 1 FP64 warp-instructions per step at ~9.4 ns each).
+constexpr double kScanComposeUs = 0.25, kScanFillUs = 0.38, kScanGroupUs = 0.3, kScanChainUs = 0.2,
+                 kScanLaunchUs = 1.5, kScanComposeWarpUs = 0.037, kScanFillWarpUs = 0.047;
+constexpr int kScanSms = 148;  // SMs the cost model assumes
+
+static bool scan_plan_search(int T, ScanPlan* p) {
+    double best = 1e300;
+    const int c_max = std::min(T, kMaxChunk), cap = scan_chunk_cap(T);
+    for (int C = 1; C <= c_max; ++C) {
+        const int nc = (T + C - 1) / C;
+        if (nc > cap || (C > 1 && (T + C - 2) / (C - 1) == nc)) continue;  // too many, or longer chunks for the same count
+        const double w = (double)((nc + kScanSms - 1) / kScanSms);
+        const double base = C * (std::max(kScanComposeUs, w * kScanComposeWarpUs) +
+                                 std::max(kScanFillUs, w * kScanFillWarpUs));
+        if (nc <= kMaxChunks) {
+            const double two = base + nc * kScanChainUs + 3 * kScanLaunchUs;
+            if (two < best) {
+                best = two;
+                *p = ScanPlan{C, nc, 0, 0};
+            }
+        }
+        const int g0 = (int)sqrt(kScanChainUs * nc / (kScanGroupUs + kScanChainUs));
+        for (int G = std::max(2, g0 - 1); G <= std::min(std::min(nc, kMaxChunks), g0 + 1); ++G) {
+            const int ng = (nc + G - 1) / G;
+            if (ng > kMaxChunks) continue;
+            const double three = base + G * (kScanGroupUs + kScanChainUs) + ng * kScanChainUs + 5 * kScanLaunchUs;
+            if (three < best) {
+                best = three;
+                *p = ScanPlan{C, nc, G, ng};
+            }
+        }
+    }
+    return best < 1e300;
+}
 
 static bool scan_plan(int T, ScanPlan* p) {
-    int C = (int)ceil(sqrt(T / 2.0));
-    C = std::max(1, std::min(C, kMaxChunk));
-    int nc = (T + C - 1) / C;
-    if (nc > kMaxChunks) {
-        C = (T + kMaxChunks - 1) / kMaxChunks;
-        nc = (T + C - 1) / C;
+    static thread_local int memo_T = -1;
+    static thread_local ScanPlan memo;
+    static thread_local bool memo_ok = false;
+    if (T != memo_T) {
+        memo_ok = scan_plan_search(T, &memo);
+        memo_T = T;
     }
-    if (C > kMaxChunk) return false;
-    *p = ScanPlan{C, nc};
-    return true;
+    *p = memo;
+    return memo_ok;
 }
 
 // Parallel-in-time Riccati plan.  Level 1: chunks of C1 steps compose
@@ -1212,12 +1306,17 @@ static bool scan_plan(int T, ScanPlan* p) {
 struct RicPlan {
     int C1, nc1, G, ng;
 };
-constexpr int kRicMinChunk = 8;  // C1 >= 8 and G >= 2 bound the scratch below
+// Most chunks a plan for T steps may use (chunks of 8 steps and more, or
+// up to 64 chunks for short horizons); with G >= 2 at most half as many
+// groups.  The scratch is sized by it.
+static int ric_chunk_cap(int T) {
+    return std::max((T + 7) / 8, std::min(T, 64));
+}
 
 // Scratch maps (each 3 n x n for the map and n x n for the P entering it)
 // for a horizon of T steps: chunk maps plus group maps.
 static size_t ric_scratch_maps(int T) {
-    const size_t nc = ((size_t)T + kRicMinChunk - 1) / kRicMinChunk;
+    const size_t nc = (size_t)ric_chunk_cap(T);
     return nc + (nc + 1) / 2;
 }
 
@@ -1225,17 +1324,21 @@ static size_t ric_scratch_maps(int T) {
 // and for the levels that run one warp per chunk the FP64 pipe time a warp
 // needs per step (B300: ~1.6 DFMA lanes per clock per SM), which bounds a
 // level once several warps share an SM.
-constexpr double kRicComposeNs = 2000, kRicComposeWarpNs = 600;
-constexpr double kRicStepNs = 1500, kRicStepWarpNs = 350;
-constexpr double kRicGroupNs = 2000, kRicChainNs = 1700, kRicLaunchNs = 2000;
+// (Measured on B300 at 2032 MHz: a composition step ~1.3 us, a group
+// composition ~1.2 us, a chain step ~1.15 us, a Riccati step ~1.45 us; an
+// SM retires one FP64 warp-instruction per ~19 clocks, ~20 of them per
+// composition step and ~26 per Riccati step.)
+constexpr double kRicComposeNs = 1300, kRicComposeWarpNs = 190;
+constexpr double kRicStepNs = 1450, kRicStepWarpNs = 245;
+constexpr double kRicGroupNs = 1200, kRicChainNs = 1150, kRicLaunchNs = 1500;
 
 static RicPlan ric_plan(int T, int sms) {
     RicPlan best{T, 1, 0, 0};
     double best_cost = 1e300;
-    const int c_max = std::min(T, 4096);
-    for (int C1 = std::min(T, kRicMinChunk); C1 <= c_max; ++C1) {
+    const int c_max = std::min(T, 4096), cap = ric_chunk_cap(T);
+    for (int C1 = 1; C1 <= c_max; ++C1) {
         const int nc1 = (T + C1 - 1) / C1;
-        if (C1 > kRicMinChunk && (T + C1 - 2) / (C1 - 1) == nc1) continue;  // same chunk count, longer chunks
+        if (nc1 > cap || (C1 > 1 && (T + C1 - 2) / (C1 - 1) == nc1)) continue;  // too many, or longer chunks for the same count
         const double w1 = (double)((nc1 + sms - 1) / sms);
         const double lvl1 = C1 * (std::max(kRicComposeNs, w1 * kRicComposeWarpNs) +
                                   std::max(kRicStepNs, w1 * kRicStepWarpNs));
@@ -1265,17 +1368,22 @@ size_t lqr_gain_doubles(int T, int n, int m) {
     return (size_t)T * (2 * (size_t)m * n + (size_t)n * n + (size_t)m * m) + ric_scratch_maps(T) * 4 * n * n;
 }
 
+// Affine scan buffers: forcing terms, k, and the scan scratch (chunk maps
+// and boundary values, then group maps and group boundary values).
 struct AffineBufs {
-    double *fc, *fe, *k, *maps, *bnd;
+    double *fc, *fe, *k, *maps, *bnd, *maps2, *bnd2;
 };
 
 static AffineBufs carve_affine(Carver& cv, int T, int n, int m) {
     AffineBufs b{};
+    const size_t nc = (size_t)scan_chunk_cap(T), ng = (nc + 1) / 2;
     b.fc = cv.take<double>((size_t)T * n);
     b.fe = cv.take<double>((size_t)T * n);
     b.k = cv.take<double>((size_t)T * m);
-    b.maps = cv.take<double>((size_t)kMaxChunks * n * (n + 1));
-    b.bnd = cv.take<double>((size_t)kMaxChunks * n);
+    b.maps = cv.take<double>(nc * n * (n + 1));
+    b.bnd = cv.take<double>(nc * n);
+    b.maps2 = cv.take<double>(ng * n * (n + 1));
+    b.bnd2 = cv.take<double>(ng * n);
     return b;
 }
 
@@ -1365,6 +1473,25 @@ static bool invert_small(const double* R, int m, double* Ri) {
     return true;
 }
 
+// The boundary values of one chunked scan from its chunk maps (ab.maps ->
+// ab.bnd), in two or three levels as planned.
+template <int N, bool BWD>
+static void launch_boundaries(const ScanPlan& pl, const AffineBufs& ab, const LqrConst& C, const double* abar,
+                              const double* w0, int T, cudaStream_t s) {
+    constexpr size_t NX = (size_t)N * (N + 1);
+    if (pl.G == 0) {
+        launch_pdl(boundaries_kernel<N, BWD>, dim3(1), dim3(32), sizeof(double) * pl.n_chunks * NX, s,
+                   (const double*)ab.maps, pl.n_chunks, pl.n_chunks, (const double*)nullptr, C, abar, w0, T, ab.bnd);
+        return;
+    }
+    launch_pdl(affine_group_kernel<N, BWD>, dim3(pl.n_groups), dim3(32), 0, s, (const double*)ab.maps, pl.n_chunks,
+               pl.G, ab.maps2);
+    launch_pdl(boundaries_kernel<N, BWD>, dim3(1), dim3(32), sizeof(double) * pl.n_groups * NX, s,
+               (const double*)ab.maps2, pl.n_groups, pl.n_groups, (const double*)nullptr, C, abar, w0, T, ab.bnd2);
+    launch_pdl(boundaries_kernel<N, BWD>, dim3(pl.n_groups), dim3(32), sizeof(double) * pl.G * NX, s,
+               (const double*)ab.maps, pl.n_chunks, pl.G, (const double*)ab.bnd2, C, abar, w0, T, ab.bnd);
+}
+
 template <int N, int MC>
 static void launch_affine_t(const double* B, const double* gains, const LqrConst& C, const double* abar, int T,
                             const ScanPlan& pl, const AffineBufs& ab, double* v, double* z, cudaStream_t s) {
@@ -1372,15 +1499,14 @@ static void launch_affine_t(const double* B, const double* gains, const LqrConst
     const double* M = gains + (size_t)T * MC * N;
     const double* Nt = M + (size_t)T * N * N;
     const size_t fsb = sizeof(double) * pl.C * N;
-    const size_t mpb = sizeof(double) * pl.n_chunks * N * (N + 1);
     launch_pdl(compose_kernel<N, MC, true>, dim3(pl.n_chunks), dim3(32), fsb, s, M, C, abar, nullptr, nullptr, nullptr, T, pl.C, ab.fc,
                                                              ab.maps);
-    launch_pdl(boundaries_kernel<N, true>, dim3(1), dim3(32), mpb, s, ab.maps, pl.n_chunks, C, abar, nullptr, T, ab.bnd);
+    launch_boundaries<N, true>(pl, ab, C, abar, nullptr, T, s);
     launch_pdl(fill_kernel<N, MC, true>, dim3(pl.n_chunks), dim3(32), 0, s, M, Nt, ab.fc, nullptr, ab.bnd, nullptr, T, pl.C, ab.k, nullptr,
                                                         nullptr);
     launch_pdl(compose_kernel<N, MC, false>, dim3(pl.n_chunks), dim3(32), fsb, s, M, C, nullptr, B, ab.k, nullptr, T, pl.C, ab.fe,
                                                               ab.maps);
-    launch_pdl(boundaries_kernel<N, false>, dim3(1), dim3(32), mpb, s, ab.maps, pl.n_chunks, C, nullptr, nullptr, T, ab.bnd);
+    launch_boundaries<N, false>(pl, ab, C, nullptr, nullptr, T, s);
     launch_pdl(fill_kernel<N, MC, false>, dim3(pl.n_chunks), dim3(32), 0, s, M, K, ab.fe, ab.k, ab.bnd, nullptr, T, pl.C, v, z, nullptr);
 }
 
@@ -1489,17 +1615,16 @@ static void launch_lqr_vjp_t(const double* B, const double* gains, const LqrCons
     const double* Nt = M + (size_t)T * N * N;
     const double* Si = Nt + (size_t)T * MC * N;
     const size_t fsb = sizeof(double) * pl.C * N;
-    const size_t mpb = sizeof(double) * pl.n_chunks * N * (N + 1);
     const AffineBufs& ab = b.ab;
     launch_pdl(lqr_vjp_prep_kernel, dim3((T + 127) / 128), dim3(128), 0, s, K, Si, vbar, T, N, MC, b.c, b.kx);
     launch_pdl(compose_kernel<N, MC, true>, dim3(pl.n_chunks), dim3(32), fsb, s, M, C, nullptr, nullptr, nullptr, b.c, T, pl.C, ab.fc,
                                                              ab.maps);
-    launch_pdl(boundaries_kernel<N, true>, dim3(1), dim3(32), mpb, s, ab.maps, pl.n_chunks, C, nullptr, b.zero, T, ab.bnd);
+    launch_boundaries<N, true>(pl, ab, C, nullptr, b.zero, T, s);
     launch_pdl(fill_kernel<N, MC, true>, dim3(pl.n_chunks), dim3(32), 0, s, M, Nt, ab.fc, nullptr, ab.bnd, b.kx, T, pl.C, ab.k, nullptr,
                                                         nullptr);
     launch_pdl(compose_kernel<N, MC, false>, dim3(pl.n_chunks), dim3(32), fsb, s, M, C, nullptr, B, ab.k, nullptr, T, pl.C, ab.fe,
                                                               ab.maps);
-    launch_pdl(boundaries_kernel<N, false>, dim3(1), dim3(32), mpb, s, ab.maps, pl.n_chunks, C, nullptr, nullptr, T, ab.bnd);
+    launch_boundaries<N, false>(pl, ab, C, nullptr, nullptr, T, s);
     launch_pdl(fill_kernel<N, MC, false>, dim3(pl.n_chunks), dim3(32), 0, s, M, K, ab.fe, ab.k, ab.bnd, nullptr, T, pl.C, b.vtmp, b.z,
                                                          nullptr);
     launch_pdl(lqr_vjp_out_kernel, dim3((T + 127) / 128), dim3(128), 0, s, C, b.z, T, N, out);
@@ -1509,13 +1634,12 @@ template <int N, int MC>
 static void launch_rollout_vjp_t(const double* A, const double* B, const double* sbar, int T, const ScanPlan& pl,
                                  const AdjScanBufs& b, double* ubar, double* s0bar, cudaStream_t s) {
     const size_t fsb = sizeof(double) * pl.C * N;
-    const size_t mpb = sizeof(double) * pl.n_chunks * N * (N + 1);
     const AffineBufs& ab = b.ab;
     const LqrConst C{};
     launch_pdl(transpose_steps_kernel, dim3((T * N * MC + 255) / 256), dim3(256), 0, s, B, T, N, MC, b.Bt);
     launch_pdl(compose_kernel<N, MC, true>, dim3(pl.n_chunks), dim3(32), fsb, s, A, C, nullptr, nullptr, nullptr, sbar, T, pl.C, ab.fc,
                                                              ab.maps);
-    launch_pdl(boundaries_kernel<N, true>, dim3(1), dim3(32), mpb, s, ab.maps, pl.n_chunks, C, nullptr, sbar + (size_t)T * N, T, ab.bnd);
+    launch_boundaries<N, true>(pl, ab, C, nullptr, sbar + (size_t)T * N, T, s);
     launch_pdl(fill_kernel<N, MC, true>, dim3(pl.n_chunks), dim3(32), 0, s, A, b.Bt, ab.fc, nullptr, ab.bnd, nullptr, T, pl.C, ubar,
                                                         nullptr, s0bar);
 }
