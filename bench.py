@@ -79,6 +79,9 @@ def parse_args():
                     help="solve time against the horizon T in the shape of the paper's timing study: Stein field "
                          "(unicycle, T = 100..10000) and Sinkhorn field (double integrator, M = T, T = 100..2500), "
                          "on the GPU and on the FP64 oracle (context, not the headline)")
+    ap.add_argument("--lqr-sweep", default="",
+                    help="comma-separated horizons: time the LQR step (cov_lqr_track: parallel-in-time Riccati + "
+                         "the two affine scans) on the unicycle linearisation at each T (context)")
     ap.add_argument("--tensor-cores", action="store_true",
                     help="form the fixed-offset updates' exponents on the tensor cores (COV_OPT_TENSOR_CORES)")
     ap.add_argument("--adjoint-outer", type=int, default=0,
@@ -1016,8 +1019,54 @@ def run_horizon_sweep(args):
     return 0
 
 
+def run_lqr_sweep(args):
+    """The LQR step alone against the horizon: `cov_lqr_track` (the
+    parallel-in-time Riccati recursion and the two affine scans, FP64) on the
+    linearisation of a unicycle trajectory (speeds and turn rates varying
+    along the horizon, dt = 0.01, position-only Q, R = 0.01 I), CUDA events
+    over `--steps` calls after `--warmup` untimed ones."""
+    import torch
+
+    from paper_2511_11514_b300 import binding as cov
+
+    torch.cuda.set_device(0)
+    ctx = cov.Context(0)
+    dev = torch.device("cuda", 0)
+    points = []
+    for T in (int(t) for t in args.lqr_sweep.split(",") if t.strip()):
+        dt = 0.01
+        s0, u = wl.unicycle_init(T, dt)
+        ts = np.arange(T)
+        u = u + np.stack([0.05 * np.sin(ts / 500.0), 0.5 * np.cos(ts / 800.0)], 1)
+        ud = torch.as_tensor(u, dtype=torch.float64, device=dev)
+        s = cov.cov_rollout(ctx, wl.UNICYCLE, s0, ud, dt)
+        A, B = cov.cov_linearize(ctx, wl.UNICYCLE, s, ud, dt)
+        abar = torch.zeros((T, 3), dtype=torch.float64, device=dev)
+        abar[:, :2] = 0.05
+        Q, R = wl.coverage_Q(wl.UNICYCLE), 0.01 * np.eye(2)
+        for _ in range(max(1, args.warmup)):
+            cov.cov_lqr_track(ctx, A, B, Q, R, abar)
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(args.steps):
+            cov.cov_lqr_track(ctx, A, B, Q, R, abar)
+        b.record()
+        torch.cuda.synchronize()
+        points.append({"T": T, "us_per_lqr_step": a.elapsed_time(b) / args.steps * 1e3})
+    st, flags = ctx.device_status()
+    if st != cov.COV_OK:
+        raise SystemExit(f"device status {cov.status_string(st)} flags {flags}")
+    print(json.dumps({"metric": "LQR step time vs horizon (context)", "value": None, "unit": "us",
+                      "higher_is_better": False, "n_gpus": 1, "dtype": "f64", "data": "synthetic unicycle trajectory",
+                      "steps": args.steps, "warmup": args.warmup, "points": points}))
+
+
 def main():
     args = parse_args()
+    if args.lqr_sweep:
+        return run_lqr_sweep(args)
     if args.horizon_sweep:
         return run_horizon_sweep(args)
     if args.variants:
