@@ -52,6 +52,7 @@ constexpr float kOffsetHi = 1.2676506e30f;   // 2^100
 constexpr float kOffsetLo = 8.6736174e-19f;  // 2^-60
 
 constexpr int kTile = 256;   // columns per staged tile
+constexpr unsigned kRedoTicket = 1u << 16;  // split-ticket increment of a split that redid its columns
 constexpr int kWarps = 4;    // warps per CTA, each takes a quarter of a tile
 constexpr int kThreads = 32 * kWarps;
 constexpr int kRowPad = 1024;  // point arrays are padded to this multiple
@@ -257,6 +258,24 @@ __device__ __forceinline__ void merge_into(float& m, float& s, float* acc, float
         }
         m = M;
     }
+}
+
+// Sum of the partial sums of row i over all column splits when every split
+// summed against the same fixed offset: the sums alone, CH loaded at once
+// (one L2 round trip for up to CH splits), added in split order into four
+// interleaved accumulators (deterministic).
+template <int CH>
+__device__ __forceinline__ float sum_lse_splits(const float* part, size_t part_ld, int splits, int ns, int i) {
+    const float* S = part + (size_t)splits * part_ld + i;  // the sum component of the layout
+    float t[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int p0 = 0; p0 < ns; p0 += CH) {
+        float s2[CH];
+#pragma unroll
+        for (int u = 0; u < CH; ++u) s2[u] = p0 + u < ns ? ld_cg(S + (size_t)(p0 + u) * part_ld) : 0.f;
+#pragma unroll
+        for (int u = 0; u < CH; ++u) t[u & 3] += s2[u];
+    }
+    return (t[0] + t[1]) + (t[2] + t[3]);
 }
 
 // Merge the (max, sum) partials of row i over all column splits into
@@ -521,7 +540,8 @@ __global__ void __launch_bounds__(kThreads) pairs_kernel(const __grid_constant__
 #pragma unroll
         for (int r = 0; r < R; ++r)
             if (fixed && row0 + r * 32 + lane < a.n_rows) over |= !(ra[r].s.x + ra[r].s.y <= kOffsetHi);
-        if (__syncthreads_or(over) && !timed_out) {
+        const bool redid = __syncthreads_or(over) && !timed_out;
+        if (redid) {
             reset_rows();
             run_pass(c0, c1, false, false);
         }
@@ -553,17 +573,27 @@ __global__ void __launch_bounds__(kThreads) pairs_kernel(const __grid_constant__
             __threadfence();
             __syncthreads();
             if (threadIdx.x == 0) {
-                const unsigned prev = atomicAdd(&a.counters[rb], 1u);
-                s_last = (prev == (unsigned)(ns - 1));
+                // the ticket also counts, above bit 16, the splits that redid
+                // their columns with the running maximum
+                const unsigned add = 1u + (redid ? kRedoTicket : 0u);
+                const unsigned prev = atomicAdd(&a.counters[rb], add);
+                s_last = (prev & (kRedoTicket - 1u)) != (unsigned)(ns - 1) ? 0 : (prev + add >= kRedoTicket ? 2 : 1);
             }
             __syncthreads();
             if (!s_last) return;
             __threadfence();
+            // every split against the same fixed offset (this CTA's fin_m):
+            // a plain sum; otherwise the general merge
+            const bool plain = fixed && s_last == 1;
             for (int q = threadIdx.x; q < RB; q += kThreads) {
-                float m, sv;
-                merge_lse_splits<16>(a.part, (size_t)a.part_ld, a.splits, ns, row0 + q, m, sv);
-                fin_m[q] = m;
-                fin_s[q] = sv;
+                if (plain) {
+                    fin_s[q] = sum_lse_splits<32>(a.part, (size_t)a.part_ld, a.splits, ns, row0 + q);
+                } else {
+                    float m, sv;
+                    merge_lse_splits<16>(a.part, (size_t)a.part_ld, a.splits, ns, row0 + q, m, sv);
+                    fin_m[q] = m;
+                    fin_s[q] = sv;
+                }
             }
             __syncthreads();
         }
