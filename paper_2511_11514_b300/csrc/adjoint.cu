@@ -439,15 +439,13 @@ __global__ void __launch_bounds__(kAThreads) adj_kernel(const __grid_constant__ 
     if (a.splits == 1) return;
 
     // ---- last CTA of this row block merges the splits ------------------------
-    __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) {
-        const unsigned prev = atomicAdd(&a.counters[rb], 1u);
+        const unsigned prev = ticket_add(&a.counters[rb], 1u);
         s_last = (prev == (unsigned)(a.splits - 1));
     }
     __syncthreads();
     if (!s_last) return;
-    __threadfence();
     const size_t cs = (size_t)a.splits * a.part_ld;
     for (int q = threadIdx.x; q < RB; q += kAThreads) {
         const int i = row0 + q;

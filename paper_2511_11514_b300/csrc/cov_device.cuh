@@ -231,6 +231,18 @@ __device__ __forceinline__ void tmem_wait_ld(uint32_t (&v)[32]) {
 // their own trigger, were unaffected either way.)
 __device__ __forceinline__ void pdl_prologue() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
+// Split ticket of a CTA whose threads wrote partials before a CTA barrier:
+// one thread's acquire-release atomic add at GPU scope publishes them
+// (release, cumulative over the barrier) and, for the CTA that draws the
+// last ticket, makes the other CTAs' partials visible to the reads that
+// follow its next barrier (acquire) -- the ordering of a fence on each side
+// of a relaxed atomic, in one operation.
+__device__ __forceinline__ unsigned ticket_add(unsigned* p, unsigned v) {
+    unsigned old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+
 // L2-coherent loads for data written by other CTAs of the same launch.
 __device__ __forceinline__ float ld_cg(const float* p) { return __ldcg(p); }
 

@@ -570,18 +570,16 @@ __global__ void __launch_bounds__(kThreads) pairs_kernel(const __grid_constant__
                 P[0] = fin_m[q];
                 P[cs] = fin_s[q];
             }
-            __threadfence();
             __syncthreads();
             if (threadIdx.x == 0) {
                 // the ticket also counts, above bit 16, the splits that redid
                 // their columns with the running maximum
                 const unsigned add = 1u + (redid ? kRedoTicket : 0u);
-                const unsigned prev = atomicAdd(&a.counters[rb], add);
+                const unsigned prev = ticket_add(&a.counters[rb], add);
                 s_last = (prev & (kRedoTicket - 1u)) != (unsigned)(ns - 1) ? 0 : (prev + add >= kRedoTicket ? 2 : 1);
             }
             __syncthreads();
             if (!s_last) return;
-            __threadfence();
             // every split against the same fixed offset (this CTA's fin_m):
             // a plain sum; otherwise the general merge
             const bool plain = fixed && s_last == 1;
@@ -684,15 +682,13 @@ __global__ void __launch_bounds__(kThreads) pairs_kernel(const __grid_constant__
     if (ns == 1) return;
 
     // ---- last CTA of this row block merges the splits ------------------------
-    __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) {
-        const unsigned prev = atomicAdd(&a.counters[rb], 1u);
+        const unsigned prev = ticket_add(&a.counters[rb], 1u);
         s_last = (prev == (unsigned)(ns - 1));
     }
     __syncthreads();
     if (!s_last) return;
-    __threadfence();
     const size_t cs = (size_t)a.splits * a.part_ld;
     for (int q = threadIdx.x; q < RB; q += kThreads) {
         const int i = row0 + q;

@@ -304,15 +304,13 @@ __global__ void __launch_bounds__(kTcThreads, kTcMinBlocks) lse_tc_kernel(const 
             P[0] = S.fin_m[tid];
             P[cs] = S.fin_s[tid];
         }
-        __threadfence();
         __syncthreads();
         if (tid == 0) {
-            const unsigned prev = atomicAdd(&a.counters[rb], 1u);
+            const unsigned prev = ticket_add(&a.counters[rb], 1u);
             S.last = (prev == (unsigned)(a.splits - 1));
         }
         __syncthreads();
         if (!S.last) return;
-        __threadfence();
         if (tid < kTcRows) {
             const int i = row0 + tid;
             float m = kNegBig, sv = 0.f;
