@@ -257,7 +257,10 @@ COV_API cov_status cov_linearize(cov_ctx* ctx, int model, const double* s,
                          const double* u, int T, double dt, double* A,
                          double* B, cov_stream_t stream);
 /* s_0 = s0 (host [n]), s_{t+1} = s_t + dt f(s_t, u_t).
- *   u [T][m], s [T+1][n]: FP64 device. */
+ *   u [T][m], s [T+1][n]: FP64 device.  For the linear models at T > 256
+ *   the rollout runs chunked over the GPU and keeps its chunk totals in the
+ *   context workspace when one is reserved (overwriting what cov_solve
+ *   cached there, as the other workspace calls do). */
 COV_API cov_status cov_rollout(cov_ctx* ctx, int model, const double* s0,
                        const double* u, int T, double dt, double* s,
                        cov_stream_t stream);

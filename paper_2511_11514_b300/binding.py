@@ -329,6 +329,7 @@ def cov_linearize(ctx: Context, model, s, u, dt, A=None, B=None, stream=None):
 def cov_rollout(ctx: Context, model, s0, u, dt, out=None, stream=None):
     n, m = MODEL_DIMS[model]
     T = u.shape[0]
+    ctx.reserve_for(T, 0, 1, n, m)
     s0h = np.ascontiguousarray(np.asarray(s0, dtype=np.float64))
     out = torch.empty((T + 1, n), device=u.device, dtype=torch.float64) if out is None else out
     st = load().cov_rollout(ctx.h, int(model), s0h.ctypes.data_as(_P), _ptr(u, torch.float64, (T, m), "u"), T,

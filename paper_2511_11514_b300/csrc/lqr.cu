@@ -1184,6 +1184,157 @@ __global__ void __launch_bounds__(1024) unicycle_positions_kernel(RolloutArgs ro
     }
 }
 
+// ---------------------------------------------------------------------------
+// Long horizons of the linear models (single and double integrator) spread
+// over the GPU instead of one CTA's FP64 pipe: chunks of kLinChunk steps,
+// one CTA each, two kernels.  The first applies u += eta v on its chunk and
+// writes the chunk's totals with zero state entering it: A = sum dt u_t (the
+// position increment of the single integrator, the velocity increment of
+// the double integrator) and, for the double integrator, B = sum dt w_t with
+// w_t the velocity gained inside the chunk before step t.  The second
+// recovers the state entering its chunk from the earlier chunks' totals
+// (V_c = v_0 + sum_{c' < c} A_c', P_c = p_0 + sum_{c' < c} (dt len_c' V_c' +
+// B_c'), in one warp) and writes the chunk's states.
+// ---------------------------------------------------------------------------
+constexpr int kLinThreads = 64;
+constexpr int kLinChunk = kLinThreads * kRK;  // steps per chunk
+constexpr int kLinSplitT = kLinChunk;         // longer horizons take the chunked rollout
+
+__global__ void __launch_bounds__(kLinThreads) linear_totals_kernel(RolloutArgs ro, double* __restrict__ u,
+                                                                    const double* __restrict__ v, int T, int m,
+                                                                    double* __restrict__ tot) {
+    pdl_prologue();
+    __shared__ double sh[32][2];
+    const double dt = ro.dt;
+    const int t0 = blockIdx.x * kLinChunk + threadIdx.x * kRK;
+    double run[2] = {0.0, 0.0}, ex[2] = {0.0, 0.0};
+#pragma unroll
+    for (int k = 0; k < kRK; ++k) {
+        const int t = t0 + k;
+        if (t < T) {
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                double w = u[(size_t)t * m + c];
+                if (v) {
+                    w = fma(ro.eta, v[(size_t)t * m + c], w);
+                    u[(size_t)t * m + c] = w;
+                }
+                ex[c] += run[c];  // velocity gained before step t (this thread's part)
+                run[c] += dt * w;
+            }
+        }
+    }
+    double off[2] = {run[0], run[1]}, totA[2];
+    block_exclusive_scan<2>(off, totA, sh);
+    const int nv = max(0, min(kRK, T - t0));
+    double b[2] = {nv * off[0] + ex[0], nv * off[1] + ex[1]}, totB[2];
+    block_exclusive_scan<2>(b, totB, sh);
+    if (threadIdx.x == 0) {
+        double* o = tot + (size_t)blockIdx.x * 4;
+        o[0] = totA[0];
+        o[1] = totA[1];
+        o[2] = dt * totB[0];
+        o[3] = dt * totB[1];
+    }
+}
+
+__global__ void __launch_bounds__(kLinThreads) linear_fill_kernel(RolloutArgs ro, const double* __restrict__ u,
+                                                                  const double* __restrict__ tot, int T, int n, int m,
+                                                                  double* __restrict__ s) {
+    pdl_prologue();
+    __shared__ double sh[32][2];
+    __shared__ double carry[4];  // p0 p1 (v0 v1) entering this chunk
+    const bool di = ro.model == COV_DOUBLE_INT;
+    const double dt = ro.dt;
+    const int cidx = blockIdx.x, cs = cidx * kLinChunk;
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        double P[2] = {ro.s0[0], ro.s0[1]}, V[2] = {di ? ro.s0[2] : 0.0, di ? ro.s0[3] : 0.0};
+        for (int base = 0; base < cidx; base += 32) {
+            const int cc = base + lane;
+            const bool live = cc < cidx;
+            const double len = live ? (double)min(kLinChunk, T - cc * kLinChunk) : 0.0;
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                const double A = live ? tot[(size_t)cc * 4 + c] : 0.0;
+                const double Bt = live ? tot[(size_t)cc * 4 + 2 + c] : 0.0;
+                double incl = A;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const double y = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += y;
+                }
+                // the single integrator's A moves the position; the double
+                // integrator's the velocity, and the position moves by
+                // dt len V + B over the chunk
+                double term = di ? dt * len * (V[c] + (incl - A)) + Bt : A;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) term += __shfl_xor_sync(0xffffffffu, term, o);
+                P[c] += term;
+                if (di) V[c] += __shfl_sync(0xffffffffu, incl, 31);
+            }
+        }
+        if (lane == 0) {
+            carry[0] = P[0];
+            carry[1] = P[1];
+            carry[2] = V[0];
+            carry[3] = V[1];
+        }
+    }
+    if (cidx == 0)
+        for (int r = threadIdx.x; r < n; r += blockDim.x) s[r] = ro.s0[r];
+    __syncthreads();
+    const int t0 = cs + threadIdx.x * kRK;
+    double run[2] = {0.0, 0.0}, incl[kRK][2], excl[kRK][2];
+#pragma unroll
+    for (int k = 0; k < kRK; ++k) {
+        const int t = t0 + k;
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            excl[k][c] = run[c];
+            run[c] += t < T ? dt * u[(size_t)t * m + c] : 0.0;
+            incl[k][c] = run[c];
+        }
+    }
+    double off[2] = {run[0], run[1]}, totA[2];
+    block_exclusive_scan<2>(off, totA, sh);
+    if (!di) {
+#pragma unroll
+        for (int k = 0; k < kRK; ++k) {
+            const int t = t0 + k;
+            if (t < T) {
+                s[(size_t)(t + 1) * n + 0] = carry[0] + (off[0] + incl[k][0]);
+                s[(size_t)(t + 1) * n + 1] = carry[1] + (off[1] + incl[k][1]);
+            }
+        }
+        return;
+    }
+    // position: p_{t+1} = P_c + dt (i + 1) V_c + sum_{tau <= i} dt w_tau,
+    // w_tau the velocity gained inside the chunk before step tau
+    double run2[2] = {0.0, 0.0}, incl2[kRK][2];
+#pragma unroll
+    for (int k = 0; k < kRK; ++k)
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            run2[c] += t0 + k < T ? dt * (off[c] + excl[k][c]) : 0.0;
+            incl2[k][c] = run2[c];
+        }
+    double off2[2] = {run2[0], run2[1]}, tot2[2];
+    block_exclusive_scan<2>(off2, tot2, sh);
+#pragma unroll
+    for (int k = 0; k < kRK; ++k) {
+        const int t = t0 + k;
+        if (t < T) {
+            const double steps = (double)(t - cs + 1);
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                s[(size_t)(t + 1) * n + c] = carry[c] + (dt * steps * carry[2 + c] + (off2[c] + incl2[k][c]));
+                s[(size_t)(t + 1) * n + 2 + c] = carry[2 + c] + (off[c] + incl[k][c]);
+            }
+        }
+    }
+}
+
 __global__ void linearize_kernel(int model, const double* __restrict__ s, const double* __restrict__ u, int T,
                                  int n, int m, double dt, double* __restrict__ A, double* __restrict__ B) {
     pdl_prologue();
@@ -1682,8 +1833,13 @@ cov_status rollout_vjp_ws(cov_ctx* ctx, void* ws, size_t ws_bytes, int n, int m,
     return COV_ERR_UNSUPPORTED;
 }
 
+size_t rollout_scratch_doubles(int T) { return (size_t)4 * ((T + kLinChunk - 1) / kLinChunk); }
+
+// scratch (rollout_scratch_doubles(T), may be null): the chunk totals of the
+// chunked rollout of the linear models at long horizons (without it they
+// roll out in one CTA).
 cov_status update_rollout(cov_ctx* ctx, int model, const double* s0, double* u, const double* v, double eta, int T,
-                          double dt, double* s, cudaStream_t stream) {
+                          double dt, double* s, cudaStream_t stream, double* scratch) {
     int n, m;
     if (model_dims(model, &n, &m) != 0) return COV_ERR_INVALID_ARG;
     RolloutArgs ro{};
@@ -1691,6 +1847,13 @@ cov_status update_rollout(cov_ctx* ctx, int model, const double* s0, double* u, 
     ro.dt = dt;
     ro.eta = eta;
     for (int r = 0; r < n; ++r) ro.s0[r] = s0[r];
+    if (model != COV_UNICYCLE && T > kLinSplitT && scratch) {
+        const int nc = (T + kLinChunk - 1) / kLinChunk;
+        launch_pdl(linear_totals_kernel, dim3(nc), dim3(kLinThreads), 0, stream, ro, u, v, T, m, scratch);
+        launch_pdl(linear_fill_kernel, dim3(nc), dim3(kLinThreads), 0, stream, ro, (const double*)u,
+                   (const double*)scratch, T, n, m, s);
+        return cuda_failed(ctx, cudaGetLastError()) ? COV_ERR_CUDA : COV_OK;
+    }
     // as many warps as the horizon fills (kRK steps per thread), up to 1024
     // threads: short horizons scan over fewer warps
     const int threads = std::min(1024, std::max(32, ((T + kRK - 1) / kRK + 31) / 32 * 32));
@@ -1734,7 +1897,14 @@ extern "C" cov_status cov_rollout(cov_ctx* ctx, int model, const double* s0, con
     for (int r = 0; r < n; ++r)
         if (!isfinite(s0[r])) return COV_ERR_INVALID_ARG;
     if (cudaSetDevice(ctx->device) != cudaSuccess) return COV_ERR_CUDA;
-    return cov::update_rollout(ctx, model, s0, const_cast<double*>(u), nullptr, 0.0, T, dt, s, (cudaStream_t)stream);
+    // the workspace, when reserved, holds the chunked rollout's totals
+    double* scratch = nullptr;
+    if (ctx->ws && ctx->ws_bytes >= sizeof(double) * cov::rollout_scratch_doubles(T)) {
+        cov::clobber_ws_caches(ctx);
+        scratch = static_cast<double*>(ctx->ws);
+    }
+    return cov::update_rollout(ctx, model, s0, const_cast<double*>(u), nullptr, 0.0, T, dt, s, (cudaStream_t)stream,
+                               scratch);
 }
 
 extern "C" cov_status cov_lqr_track(cov_ctx* ctx, const double* A, const double* B, const double* Q,

@@ -19,7 +19,8 @@ cov_status lqr_riccati(cov_ctx* ctx, int n, int m, const double* A, const double
 cov_status lqr_affine(cov_ctx* ctx, void* ws, size_t ws_bytes, int n, int m, const double* B, const double* gains,
                       const double* Q, const double* abar, int T, double* v_out, double* z_out, cudaStream_t stream);
 cov_status update_rollout(cov_ctx* ctx, int model, const double* s0, double* u, const double* v, double eta, int T,
-                          double dt, double* s, cudaStream_t stream);
+                          double dt, double* s, cudaStream_t stream, double* scratch = nullptr);
+size_t rollout_scratch_doubles(int T);
 cov_status linearize_launch(cov_ctx* ctx, int model, const double* s, const double* u, int T, double dt, double* A,
                             double* B, cudaStream_t stream);
 
@@ -34,6 +35,7 @@ struct SolveBufs {
     float *x, *a, *scal;
     float *f, *g, *p;  // Sinkhorn potentials carried between outer iterations (warm)
     double *abar, *A, *B, *v, *gains;
+    double* rtot;  // chunk totals of the long-horizon rollout of the linear models
 };
 
 // The potentials come last, so that the cached gains sit at an offset that
@@ -47,6 +49,7 @@ static SolveBufs carve_solve(Carver& cv, int T, int d, int n, int m, int M) {
     b.B = cv.take<double>((size_t)T * n * m);
     b.v = cv.take<double>((size_t)T * m);
     b.gains = cv.take<double>(lqr_gain_doubles(T, n, m));
+    b.rtot = cv.take<double>(rollout_scratch_doubles(T));
     b.scal = cv.take<float>(16);
     b.f = cv.take<float>((size_t)T);
     b.p = cv.take<float>((size_t)T);
@@ -222,7 +225,7 @@ static cov_status enqueue_iteration(cov_ctx* ctx, const cov_problem* P, int n, i
     }
     r = lqr_affine(ctx, rest, rest_bytes, n, m, b.B, b.gains, P->Q, b.abar, T, b.v, nullptr, st);
     if (r != COV_OK) return r;
-    r = update_rollout(ctx, P->model, P->s0, u, b.v, P->eta, T, P->dt, s, st);
+    r = update_rollout(ctx, P->model, P->s0, u, b.v, P->eta, T, P->dt, s, st, b.rtot);
     if (r != COV_OK) return r;
     if (cuda_failed(ctx, cudaGetLastError())) return COV_ERR_CUDA;
     return COV_OK;
@@ -711,7 +714,7 @@ static cov_status solve_taped(cov_ctx* ctx, const cov_problem* prob, int K, doub
             launch_pdl(lift_kernel, dim3(nb), dim3(256), 0, ws_st, b.a, T, n, d, b.abar);
             q = lqr_affine(ctx, L.rest, L.rest_bytes, n, m, b.B, b.gains, prob->Q, b.abar, T, b.v, nullptr, ws_st);
             if (q != COV_OK) return q;
-            q = update_rollout(ctx, prob->model, prob->s0, u, b.v, prob->eta, T, prob->dt, s_out, ws_st);
+            q = update_rollout(ctx, prob->model, prob->s0, u, b.v, prob->eta, T, prob->dt, s_out, ws_st, b.rtot);
             if (q != COV_OK) return q;
         }
         return cuda_failed(ctx, cudaGetLastError()) ? COV_ERR_CUDA : COV_OK;
