@@ -51,8 +51,8 @@ SM_MAX_MHZ_NOMINAL = 2032.0
 FP32_LANES_PER_SM_CLK = 128
 # DRAM bytes (read + write) per launch of pairs_kernel at the benchmark
 # workload from one ncu capture of the current kernel (fixed-offset form):
-# 379 KB (g + p launch) and 280 KB (f launch), no writes.
-PAIRS_TRAFFIC_BYTES = 329344
+# 388 KB (g + p launch) and 291 KB (f launch), no writes.
+PAIRS_TRAFFIC_BYTES = 339456
 
 
 def parse_args():
