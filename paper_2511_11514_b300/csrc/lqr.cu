@@ -1185,24 +1185,39 @@ __global__ void __launch_bounds__(1024) unicycle_positions_kernel(RolloutArgs ro
 }
 
 // ---------------------------------------------------------------------------
-// Long horizons of the linear models (single and double integrator) spread
-// over the GPU instead of one CTA's FP64 pipe: chunks of kLinChunk steps,
-// one CTA each, two kernels.  The first applies u += eta v on its chunk and
-// writes the chunk's totals with zero state entering it: A = sum dt u_t (the
-// position increment of the single integrator, the velocity increment of
-// the double integrator) and, for the double integrator, B = sum dt w_t with
-// w_t the velocity gained inside the chunk before step t.  The second
-// recovers the state entering its chunk from the earlier chunks' totals
-// (V_c = v_0 + sum_{c' < c} A_c', P_c = p_0 + sum_{c' < c} (dt len_c' V_c' +
-// B_c'), in one warp) and writes the chunk's states.
+// Long horizons: the rollout's prefix sums chunked over the GPU instead of
+// one CTA's FP64 pipe, chunks of kLinChunk steps, one CTA each, two kernels
+// per sum.  The sums (`mode`):
+//   LIN_SI  single integrator: positions += dt u_t;
+//   LIN_DI  double integrator: velocities += dt u_t, positions += dt v_t;
+//   UNI_HEAD unicycle heading: theta += dt omega_t;
+//   UNI_POS  unicycle positions: += the increments dt v_t (cos, sin)(theta_t)
+//            already in s (unicycle_increments_kernel), summed in place.
+// The first kernel (applying u += eta v on its chunk where the sum reads u)
+// writes the chunk's totals with zero state entering it: A = the sum of its
+// increments and, for the double integrator, B = sum dt w_t with w_t the
+// velocity gained inside the chunk before step t.  The second recovers the
+// state entering its chunk from the earlier chunks' totals (P_c = p_0 +
+// sum_{c' < c} A_c', or for the double integrator V_c = v_0 + sum A_c',
+// P_c = p_0 + sum (dt len_c' V_c' + B_c'), in one warp) and writes the
+// chunk's states.
 // ---------------------------------------------------------------------------
 constexpr int kLinThreads = 64;
 constexpr int kLinChunk = kLinThreads * kRK;  // steps per chunk
 constexpr int kLinSplitT = kLinChunk;         // longer horizons take the chunked rollout
+enum LinMode { LIN_SI = 0, LIN_DI = 1, UNI_HEAD = 2, UNI_POS = 3 };
 
-__global__ void __launch_bounds__(kLinThreads) linear_totals_kernel(RolloutArgs ro, double* __restrict__ u,
-                                                                    const double* __restrict__ v, int T, int m,
-                                                                    double* __restrict__ tot) {
+// Increment of component c at step t (u already updated).
+__device__ __forceinline__ double lin_increment(int mode, const double* __restrict__ u, const double* s, int t, int m,
+                                                int n, int c, double dt) {
+    if (mode == UNI_POS) return s[(size_t)(t + 1) * n + c];
+    if (mode == UNI_HEAD) return c == 0 ? dt * u[(size_t)t * m + 1] : 0.0;
+    return dt * u[(size_t)t * m + c];
+}
+
+__global__ void __launch_bounds__(kLinThreads) linear_totals_kernel(RolloutArgs ro, int mode, double* __restrict__ u,
+                                                                    const double* __restrict__ v, const double* s,
+                                                                    int T, int n, int m, double* __restrict__ tot) {
     pdl_prologue();
     __shared__ double sh[32][2];
     const double dt = ro.dt;
@@ -1212,23 +1227,22 @@ __global__ void __launch_bounds__(kLinThreads) linear_totals_kernel(RolloutArgs 
     for (int k = 0; k < kRK; ++k) {
         const int t = t0 + k;
         if (t < T) {
+            if (v && mode != UNI_POS)
+#pragma unroll
+                for (int c = 0; c < 2; ++c)
+                    u[(size_t)t * m + c] = fma(ro.eta, v[(size_t)t * m + c], u[(size_t)t * m + c]);
 #pragma unroll
             for (int c = 0; c < 2; ++c) {
-                double w = u[(size_t)t * m + c];
-                if (v) {
-                    w = fma(ro.eta, v[(size_t)t * m + c], w);
-                    u[(size_t)t * m + c] = w;
-                }
                 ex[c] += run[c];  // velocity gained before step t (this thread's part)
-                run[c] += dt * w;
+                run[c] += lin_increment(mode, u, s, t, m, n, c, dt);
             }
         }
     }
     double off[2] = {run[0], run[1]}, totA[2];
     block_exclusive_scan<2>(off, totA, sh);
     const int nv = max(0, min(kRK, T - t0));
-    double b[2] = {nv * off[0] + ex[0], nv * off[1] + ex[1]}, totB[2];
-    block_exclusive_scan<2>(b, totB, sh);
+    double b[2] = {nv * off[0] + ex[0], nv * off[1] + ex[1]}, totB[2] = {0.0, 0.0};
+    if (mode == LIN_DI) block_exclusive_scan<2>(b, totB, sh);
     if (threadIdx.x == 0) {
         double* o = tot + (size_t)blockIdx.x * 4;
         o[0] = totA[0];
@@ -1238,18 +1252,21 @@ __global__ void __launch_bounds__(kLinThreads) linear_totals_kernel(RolloutArgs 
     }
 }
 
-__global__ void __launch_bounds__(kLinThreads) linear_fill_kernel(RolloutArgs ro, const double* __restrict__ u,
+__global__ void __launch_bounds__(kLinThreads) linear_fill_kernel(RolloutArgs ro, int mode, const double* __restrict__ u,
                                                                   const double* __restrict__ tot, int T, int n, int m,
-                                                                  double* __restrict__ s) {
+                                                                  double* s) {
     pdl_prologue();
     __shared__ double sh[32][2];
-    __shared__ double carry[4];  // p0 p1 (v0 v1) entering this chunk
-    const bool di = ro.model == COV_DOUBLE_INT;
+    __shared__ double carry[4];  // p0 p1 (v0 v1) entering this chunk; the heading in p0
+    const bool di = mode == LIN_DI;
     const double dt = ro.dt;
     const int cidx = blockIdx.x, cs = cidx * kLinChunk;
+    // the state columns this sum writes: positions (0, 1), or the heading (2)
+    const int col0 = mode == UNI_HEAD ? 2 : 0, ncomp = mode == UNI_HEAD ? 1 : 2;
     if (threadIdx.x < 32) {
         const int lane = threadIdx.x;
-        double P[2] = {ro.s0[0], ro.s0[1]}, V[2] = {di ? ro.s0[2] : 0.0, di ? ro.s0[3] : 0.0};
+        double P[2] = {ro.s0[col0], ncomp > 1 ? ro.s0[col0 + 1] : 0.0};
+        double V[2] = {di ? ro.s0[2] : 0.0, di ? ro.s0[3] : 0.0};
         for (int base = 0; base < cidx; base += 32) {
             const int cc = base + lane;
             const bool live = cc < cidx;
@@ -1264,9 +1281,9 @@ __global__ void __launch_bounds__(kLinThreads) linear_fill_kernel(RolloutArgs ro
                     const double y = __shfl_up_sync(0xffffffffu, incl, o);
                     if (lane >= o) incl += y;
                 }
-                // the single integrator's A moves the position; the double
-                // integrator's the velocity, and the position moves by
-                // dt len V + B over the chunk
+                // A moves the written columns, except for the double
+                // integrator, whose A moves the velocity and whose position
+                // moves by dt len V + B over the chunk
                 double term = di ? dt * len * (V[c] + (incl - A)) + Bt : A;
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) term += __shfl_xor_sync(0xffffffffu, term, o);
@@ -1281,7 +1298,7 @@ __global__ void __launch_bounds__(kLinThreads) linear_fill_kernel(RolloutArgs ro
             carry[3] = V[1];
         }
     }
-    if (cidx == 0)
+    if (cidx == 0 && mode != UNI_POS)
         for (int r = threadIdx.x; r < n; r += blockDim.x) s[r] = ro.s0[r];
     __syncthreads();
     const int t0 = cs + threadIdx.x * kRK;
@@ -1292,20 +1309,18 @@ __global__ void __launch_bounds__(kLinThreads) linear_fill_kernel(RolloutArgs ro
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
             excl[k][c] = run[c];
-            run[c] += t < T ? dt * u[(size_t)t * m + c] : 0.0;
+            run[c] += t < T ? lin_increment(mode, u, s, t, m, n, c, dt) : 0.0;
             incl[k][c] = run[c];
         }
     }
     double off[2] = {run[0], run[1]}, totA[2];
-    block_exclusive_scan<2>(off, totA, sh);
+    block_exclusive_scan<2>(off, totA, sh);  // (its barrier also orders the in-place reads before the writes)
     if (!di) {
 #pragma unroll
         for (int k = 0; k < kRK; ++k) {
             const int t = t0 + k;
-            if (t < T) {
-                s[(size_t)(t + 1) * n + 0] = carry[0] + (off[0] + incl[k][0]);
-                s[(size_t)(t + 1) * n + 1] = carry[1] + (off[1] + incl[k][1]);
-            }
+            if (t < T)
+                for (int c = 0; c < ncomp; ++c) s[(size_t)(t + 1) * n + col0 + c] = carry[c] + (off[c] + incl[k][c]);
         }
         return;
     }
@@ -1847,11 +1862,23 @@ cov_status update_rollout(cov_ctx* ctx, int model, const double* s0, double* u, 
     ro.dt = dt;
     ro.eta = eta;
     for (int r = 0; r < n; ++r) ro.s0[r] = s0[r];
-    if (model != COV_UNICYCLE && T > kLinSplitT && scratch) {
+    if (T > kLinSplitT && scratch) {
         const int nc = (T + kLinChunk - 1) / kLinChunk;
-        launch_pdl(linear_totals_kernel, dim3(nc), dim3(kLinThreads), 0, stream, ro, u, v, T, m, scratch);
-        launch_pdl(linear_fill_kernel, dim3(nc), dim3(kLinThreads), 0, stream, ro, (const double*)u,
-                   (const double*)scratch, T, n, m, s);
+        auto sum = [&](int mode, const double* vv) {
+            launch_pdl(linear_totals_kernel, dim3(nc), dim3(kLinThreads), 0, stream, ro, mode, u, vv, (const double*)s,
+                       T, n, m, scratch);
+            launch_pdl(linear_fill_kernel, dim3(nc), dim3(kLinThreads), 0, stream, ro, mode, (const double*)u,
+                       (const double*)scratch, T, n, m, s);
+        };
+        if (model == COV_UNICYCLE) {
+            // heading, then the increments along it, then their sums
+            sum(UNI_HEAD, v);
+            launch_pdl(unicycle_increments_kernel, dim3((T + 255) / 256), dim3(256), 0, stream, (const double*)u, T, m,
+                       dt, s);
+            sum(UNI_POS, nullptr);
+        } else {
+            sum(model == COV_DOUBLE_INT ? LIN_DI : LIN_SI, v);
+        }
         return cuda_failed(ctx, cudaGetLastError()) ? COV_ERR_CUDA : COV_OK;
     }
     // as many warps as the horizon fills (kRK steps per thread), up to 1024
