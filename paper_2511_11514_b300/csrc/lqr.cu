@@ -253,8 +253,9 @@ __global__ void __launch_bounds__(32, 1) riccati_kernel(const double* __restrict
 // with every inverse of the form I + (PSD)(PSD), whose eigenvalues are >= 1.
 // Chunks compose their maps (one warp each), the chunk maps are chained
 // from P_T = Q to get the P entering every chunk (for long horizons through
-// a second level: groups of chunk maps composed again, the group maps
-// chained, each group's chunk maps chained from the P entering the group),
+// grouping levels: groups of maps composed again, level by level, the top
+// maps chained, then each group's maps chained from the P entering the
+// group, level by level down),
 // and each chunk then runs the ordinary Riccati step over its own steps from
 // that P (riccati_kernel).
 // ---------------------------------------------------------------------------
@@ -1462,29 +1463,34 @@ static bool scan_plan(int T, ScanPlan* p) {
     return memo_ok;
 }
 
-// Parallel-in-time Riccati plan.  Level 1: chunks of C1 steps compose
-// their step maps (nc1 warps).  Two levels (G == 0): one warp chains the
-// nc1 chunk maps.  Three levels, for long horizons: groups of G chunk maps
-// are composed again (ng warps), one warp chains the ng group maps, and one
-// warp per group then chains its own chunk maps from the P entering it.
-// Last, every chunk runs the ordinary Riccati step over its steps.  Serial
-// depth: C1 + nc1 + C1 steps (two levels) or C1 + G + ng + G + C1 (three).
+// Parallel-in-time Riccati plan.  Level 0: chunks of C1 steps compose
+// their step maps (nc1 blocks).  Without grouping one warp chains the nc1
+// chunk maps.  With `depth` grouping levels, groups of G[l] maps of level l
+// are composed again into the maps of level l + 1 (one block per group),
+// one warp chains the top level's maps, and then, level by level down, one
+// warp per group chains its own maps from the P entering the group.  Last,
+// every chunk runs the ordinary Riccati step over its steps.  Serial depth
+// C1 + sum_l G[l] + n[depth] + sum_l G[l] + C1 steps.
+// Levels of grouping above the chunks (so up to four levels in all).
+constexpr int kRicMaxGroupLevels = 3;
+
 struct RicPlan {
-    int C1, nc1, G, ng;
+    int C1, nc1;                   // chunks of C1 steps
+    int depth;                     // grouping levels: 0 (the chunk maps chained directly) .. kRicMaxGroupLevels
+    int G[kRicMaxGroupLevels];     // maps per group at each level
+    int n[kRicMaxGroupLevels + 1]; // maps at each level (n[0] = nc1)
 };
 // Most chunks a plan for T steps may use (chunks of 8 steps and more, or
-// up to 64 chunks for short horizons); with G >= 2 at most half as many
-// groups.  The scratch is sized by it.
+// up to 64 chunks for short horizons); with G >= 2 every grouping level has
+// at most half the maps of the level below, so all levels together at most
+// twice the chunks.  The scratch is sized by it.
 static int ric_chunk_cap(int T) {
     return std::max((T + 7) / 8, std::min(T, 64));
 }
 
 // Scratch maps (each 3 n x n for the map and n x n for the P entering it)
-// for a horizon of T steps: chunk maps plus group maps.
-static size_t ric_scratch_maps(int T) {
-    const size_t nc = (size_t)ric_chunk_cap(T);
-    return nc + (nc + 1) / 2;
-}
+// for a horizon of T steps: chunk maps plus the maps of every grouping level.
+static size_t ric_scratch_maps(int T) { return (size_t)2 * ric_chunk_cap(T) + kRicMaxGroupLevels; }
 
 // Cost model (ns) of one serial step of each level: its dependent latency,
 // and for the levels that run one warp per chunk the FP64 pipe time a warp
@@ -1498,8 +1504,26 @@ constexpr double kRicComposeNs = 1300, kRicComposeWarpNs = 190;
 constexpr double kRicStepNs = 1450, kRicStepWarpNs = 245;
 constexpr double kRicGroupNs = 1200, kRicChainNs = 1150, kRicLaunchNs = 1500;
 
+// Serial cost of chaining nc1 chunk maps through `depth` grouping levels of
+// (about) equal group size g: each level composes g maps (group) and later
+// chains them again (expand), and the top chains what is left.
+static double ric_group_cost(int nc1, int depth, int g, RicPlan* pl) {
+    double cost = 0.0;
+    int n = nc1;
+    for (int l = 0; l < depth; ++l) {
+        const int G = std::max(2, std::min(g, n));
+        pl->G[l] = G;
+        pl->n[l] = n;
+        n = (n + G - 1) / G;
+        cost += G * (kRicGroupNs + kRicChainNs) + 2 * kRicLaunchNs;
+    }
+    pl->n[depth] = n;
+    pl->depth = depth;
+    return cost + n * kRicChainNs;
+}
+
 static RicPlan ric_plan(int T, int sms) {
-    RicPlan best{T, 1, 0, 0};
+    RicPlan best{};
     double best_cost = 1e300;
     const int c_max = std::min(T, 4096), cap = ric_chunk_cap(T);
     for (int C1 = 1; C1 <= c_max; ++C1) {
@@ -1507,19 +1531,19 @@ static RicPlan ric_plan(int T, int sms) {
         if (nc1 > cap || (C1 > 1 && (T + C1 - 2) / (C1 - 1) == nc1)) continue;  // too many, or longer chunks for the same count
         const double w1 = (double)((nc1 + sms - 1) / sms);
         const double lvl1 = C1 * (std::max(kRicComposeNs, w1 * kRicComposeWarpNs) +
-                                  std::max(kRicStepNs, w1 * kRicStepWarpNs));
-        const double two = lvl1 + nc1 * kRicChainNs + 3 * kRicLaunchNs;
-        if (two < best_cost) {
-            best_cost = two;
-            best = RicPlan{C1, nc1, 0, 0};
-        }
-        const int g0 = (int)sqrt(kRicChainNs * nc1 / (kRicGroupNs + kRicChainNs));
-        for (int G = std::max(2, g0 - 1); G <= std::min(nc1, g0 + 1); ++G) {
-            const int ng = (nc1 + G - 1) / G;
-            const double three = lvl1 + G * (kRicGroupNs + kRicChainNs) + ng * kRicChainNs + 5 * kRicLaunchNs;
-            if (three < best_cost) {
-                best_cost = three;
-                best = RicPlan{C1, nc1, G, ng};
+                                  std::max(kRicStepNs, w1 * kRicStepWarpNs)) + 3 * kRicLaunchNs;
+        for (int depth = 0; depth <= kRicMaxGroupLevels; ++depth) {
+            // group size near the depth-th root of the chunk count, and its neighbours
+            const int g0 = depth ? (int)pow((double)nc1, 1.0 / (depth + 1)) : 0;
+            for (int g = std::max(2, g0 - 1); g <= (depth ? g0 + 1 : 2); ++g) {
+                RicPlan pl{};
+                pl.C1 = C1;
+                pl.nc1 = nc1;
+                const double cost = lvl1 + ric_group_cost(nc1, depth, g, &pl);
+                if (cost < best_cost) {
+                    best_cost = cost;
+                    best = pl;
+                }
             }
         }
     }
@@ -1527,9 +1551,8 @@ static RicPlan ric_plan(int T, int sms) {
 }
 
 // Gains per step: K [m][n], M [n][n], N [m][n], S^-1 [m][m]; then the
-// parallel Riccati's scratch: chunk maps [nc1][3][n][n], the P entering
-// each chunk [nc1][n][n], group maps [ng][3][n][n] and the P entering each
-// group [ng][n][n].
+// parallel Riccati's scratch: per level (chunks, then each grouping level)
+// its maps [count][3][n][n] and the P entering each [count][n][n].
 size_t lqr_gain_doubles(int T, int n, int m) {
     return (size_t)T * (2 * (size_t)m * n + (size_t)n * n + (size_t)m * m) + ric_scratch_maps(T) * 4 * n * n;
 }
@@ -1595,24 +1618,29 @@ static void launch_riccati_t(const double* A, const double* B, const LqrConst& C
         memo_T = T;
         memo_sms = sms;
     }
+    // maps and entering P of each level: level 0 the chunks, level l the
+    // groups of G[l-1] maps of level l - 1
     constexpr size_t NN = (size_t)N * N;
-    double* maps1 = Si + (size_t)T * MC * MC;
-    double* pin1 = maps1 + (size_t)pl.nc1 * 3 * NN;
-    double* maps2 = pin1 + (size_t)pl.nc1 * NN;
-    double* pin2 = maps2 + (size_t)pl.ng * 3 * NN;
-    launch_pdl(ric_compose_kernel<N, MC>, dim3(pl.nc1), dim3(RicThreads<N>::value), 0, s, A, B, Ci, T, pl.C1, maps1, st);
-    if (pl.G == 0) {
-        launch_pdl(ric_chain_kernel<N>, dim3(1), dim3(32), 0, s, (const double*)maps1, pl.nc1, pl.nc1,
-                   (const double*)nullptr, C, pin1, st);
-    } else {
-        launch_pdl(ric_group_kernel<N>, dim3(pl.ng), dim3(RicThreads<N>::value), 0, s, (const double*)maps1, pl.nc1, pl.G, maps2, st);
-        launch_pdl(ric_chain_kernel<N>, dim3(1), dim3(32), 0, s, (const double*)maps2, pl.ng, pl.ng,
-                   (const double*)nullptr, C, pin2, st);
-        launch_pdl(ric_chain_kernel<N>, dim3(pl.ng), dim3(32), 0, s, (const double*)maps1, pl.nc1, pl.G,
-                   (const double*)pin2, C, pin1, st);
+    double* maps[kRicMaxGroupLevels + 1];
+    double* pin[kRicMaxGroupLevels + 1];
+    double* p = Si + (size_t)T * MC * MC;
+    for (int l = 0; l <= pl.depth; ++l) {
+        maps[l] = p;
+        pin[l] = maps[l] + (size_t)pl.n[l] * 3 * NN;
+        p = pin[l] + (size_t)pl.n[l] * NN;
     }
+    launch_pdl(ric_compose_kernel<N, MC>, dim3(pl.nc1), dim3(RicThreads<N>::value), 0, s, A, B, Ci, T, pl.C1, maps[0], st);
+    for (int l = 0; l < pl.depth; ++l)
+        launch_pdl(ric_group_kernel<N>, dim3(pl.n[l + 1]), dim3(RicThreads<N>::value), 0, s, (const double*)maps[l],
+                   pl.n[l], pl.G[l], maps[l + 1], st);
+    const int top = pl.depth;
+    launch_pdl(ric_chain_kernel<N>, dim3(1), dim3(32), 0, s, (const double*)maps[top], pl.n[top], pl.n[top],
+               (const double*)nullptr, C, pin[top], st);
+    for (int l = top - 1; l >= 0; --l)
+        launch_pdl(ric_chain_kernel<N>, dim3(pl.n[l + 1]), dim3(32), 0, s, (const double*)maps[l], pl.n[l], pl.G[l],
+                   (const double*)pin[l + 1], C, pin[l], st);
     launch_pdl(riccati_kernel<N, MC>, dim3(pl.nc1), dim3(32), 0, s, A, B, C, T, K, M, Nt, Si, st,
-               (const double*)pin1, pl.C1);
+               (const double*)pin[0], pl.C1);
 }
 
 // R^-1 on the host (m <= 3, Gauss-Jordan with partial pivoting).
