@@ -1397,19 +1397,25 @@ int model_dims(int model, int* n, int* m) {
 // ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
-// Chunked scan plan for the affine recursions.  Level 1: chunks of C steps
-// compose their maps and later fill their steps (one warp each).  Two
-// levels (G == 0): one warp chains the n_chunks chunk maps.  Three levels:
-// groups of G chunk maps are composed (n_groups warps), one warp chains the
-// group maps, one warp per group chains its chunk maps from the value
-// entering the group.  Serial depth C + n_chunks + C or C + G + n_groups +
-// G + C steps.
+// Chunked scan plan for the affine recursions, with the level structure of
+// the parallel Riccati: chunks of C steps compose their maps and later fill
+// their steps (one warp each); without grouping one warp chains the chunk
+// maps; with `depth` grouping levels groups of G[l] maps of level l are
+// composed into level l + 1, one warp chains the top level, and level by
+// level down one warp per group chains its maps from the value entering the
+// group.  Serial depth C + sum_l G[l] + n[depth] + sum_l G[l] + C steps.
+constexpr int kScanMaxGroupLevels = 3;  // grouping levels above the chunks
+
 struct ScanPlan {
-    int C, n_chunks, G, n_groups;
+    int C, n_chunks;                 // chunks of C steps
+    int depth;                       // grouping levels: 0 (one warp chains the chunk maps) .. kScanMaxGroupLevels
+    int G[kScanMaxGroupLevels];      // maps per group at each level
+    int n[kScanMaxGroupLevels + 1];  // maps at each level (n[0] = n_chunks)
 };
 // Most chunks a plan for T steps may use (chunks of 8 steps and more, or
-// up to 64 chunks for short horizons); with G >= 2 at most half as many
-// groups.  The scratch is sized by it.
+// up to 64 chunks for short horizons); with G >= 2 the grouping levels
+// together hold at most as many maps again (plus one per level).  The
+// scratch is sized by it.
 static int scan_chunk_cap(int T) {
     return std::max((T + 7) / 8, std::min(T, 64));
 }
@@ -1429,22 +1435,32 @@ static bool scan_plan_search(int T, ScanPlan* p) {
         if (nc > cap || (C > 1 && (T + C - 2) / (C - 1) == nc)) continue;  // too many, or longer chunks for the same count
         const double w = (double)((nc + kScanSms - 1) / kScanSms);
         const double base = C * (std::max(kScanComposeUs, w * kScanComposeWarpUs) +
-                                 std::max(kScanFillUs, w * kScanFillWarpUs));
-        if (nc <= kMaxChunks) {
-            const double two = base + nc * kScanChainUs + 3 * kScanLaunchUs;
-            if (two < best) {
-                best = two;
-                *p = ScanPlan{C, nc, 0, 0};
-            }
-        }
-        const int g0 = (int)sqrt(kScanChainUs * nc / (kScanGroupUs + kScanChainUs));
-        for (int G = std::max(2, g0 - 1); G <= std::min(std::min(nc, kMaxChunks), g0 + 1); ++G) {
-            const int ng = (nc + G - 1) / G;
-            if (ng > kMaxChunks) continue;
-            const double three = base + G * (kScanGroupUs + kScanChainUs) + ng * kScanChainUs + 5 * kScanLaunchUs;
-            if (three < best) {
-                best = three;
-                *p = ScanPlan{C, nc, G, ng};
+                                 std::max(kScanFillUs, w * kScanFillWarpUs)) + 3 * kScanLaunchUs;
+        for (int depth = 0; depth <= kScanMaxGroupLevels; ++depth) {
+            const int g0 = depth ? (int)pow((double)nc, 1.0 / (depth + 1)) : 0;
+            for (int g = std::max(2, g0 - 1); g <= (depth ? g0 + 1 : 2); ++g) {
+                ScanPlan pl{};
+                pl.C = C;
+                pl.n_chunks = nc;
+                pl.depth = depth;
+                double cost = base;
+                int n = nc;
+                bool fits = true;
+                for (int l = 0; l < depth; ++l) {
+                    const int G = std::max(2, std::min(g, n));
+                    pl.G[l] = G;
+                    pl.n[l] = n;
+                    fits &= G <= kMaxChunks;
+                    n = (n + G - 1) / G;
+                    cost += G * (kScanGroupUs + kScanChainUs) + 2 * kScanLaunchUs;
+                }
+                pl.n[depth] = n;
+                cost += n * kScanChainUs;
+                // the one-warp chains stage their maps in shared memory
+                if (fits && n <= kMaxChunks && cost < best) {
+                    best = cost;
+                    *p = pl;
+                }
             }
         }
     }
@@ -1558,21 +1574,22 @@ size_t lqr_gain_doubles(int T, int n, int m) {
 }
 
 // Affine scan buffers: forcing terms, k, and the scan scratch (chunk maps
-// and boundary values, then group maps and group boundary values).
+// and boundary values, then the maps and boundary values of the grouping
+// levels one after another).
 struct AffineBufs {
-    double *fc, *fe, *k, *maps, *bnd, *maps2, *bnd2;
+    double *fc, *fe, *k, *maps, *bnd, *mapsg, *bndg;
 };
 
 static AffineBufs carve_affine(Carver& cv, int T, int n, int m) {
     AffineBufs b{};
-    const size_t nc = (size_t)scan_chunk_cap(T), ng = (nc + 1) / 2;
+    const size_t nc = (size_t)scan_chunk_cap(T), ng = nc + kScanMaxGroupLevels;
     b.fc = cv.take<double>((size_t)T * n);
     b.fe = cv.take<double>((size_t)T * n);
     b.k = cv.take<double>((size_t)T * m);
     b.maps = cv.take<double>(nc * n * (n + 1));
     b.bnd = cv.take<double>(nc * n);
-    b.maps2 = cv.take<double>(ng * n * (n + 1));
-    b.bnd2 = cv.take<double>(ng * n);
+    b.mapsg = cv.take<double>(ng * n * (n + 1));
+    b.bndg = cv.take<double>(ng * n);
     return b;
 }
 
@@ -1673,17 +1690,26 @@ template <int N, bool BWD>
 static void launch_boundaries(const ScanPlan& pl, const AffineBufs& ab, const LqrConst& C, const double* abar,
                               const double* w0, int T, cudaStream_t s) {
     constexpr size_t NX = (size_t)N * (N + 1);
-    if (pl.G == 0) {
-        launch_pdl(boundaries_kernel<N, BWD>, dim3(1), dim3(32), sizeof(double) * pl.n_chunks * NX, s,
-                   (const double*)ab.maps, pl.n_chunks, pl.n_chunks, (const double*)nullptr, C, abar, w0, T, ab.bnd);
-        return;
+    // maps and boundary values of each level: level 0 the chunks
+    double* maps[kScanMaxGroupLevels + 1] = {ab.maps};
+    double* bnd[kScanMaxGroupLevels + 1] = {ab.bnd};
+    double* pm = ab.mapsg;
+    double* pb = ab.bndg;
+    for (int l = 1; l <= pl.depth; ++l) {
+        maps[l] = pm;
+        bnd[l] = pb;
+        pm += (size_t)pl.n[l] * NX;
+        pb += (size_t)pl.n[l] * N;
     }
-    launch_pdl(affine_group_kernel<N, BWD>, dim3(pl.n_groups), dim3(32), 0, s, (const double*)ab.maps, pl.n_chunks,
-               pl.G, ab.maps2);
-    launch_pdl(boundaries_kernel<N, BWD>, dim3(1), dim3(32), sizeof(double) * pl.n_groups * NX, s,
-               (const double*)ab.maps2, pl.n_groups, pl.n_groups, (const double*)nullptr, C, abar, w0, T, ab.bnd2);
-    launch_pdl(boundaries_kernel<N, BWD>, dim3(pl.n_groups), dim3(32), sizeof(double) * pl.G * NX, s,
-               (const double*)ab.maps, pl.n_chunks, pl.G, (const double*)ab.bnd2, C, abar, w0, T, ab.bnd);
+    for (int l = 0; l < pl.depth; ++l)
+        launch_pdl(affine_group_kernel<N, BWD>, dim3(pl.n[l + 1]), dim3(32), 0, s, (const double*)maps[l], pl.n[l],
+                   pl.G[l], maps[l + 1]);
+    const int top = pl.depth;
+    launch_pdl(boundaries_kernel<N, BWD>, dim3(1), dim3(32), sizeof(double) * pl.n[top] * NX, s,
+               (const double*)maps[top], pl.n[top], pl.n[top], (const double*)nullptr, C, abar, w0, T, bnd[top]);
+    for (int l = top - 1; l >= 0; --l)
+        launch_pdl(boundaries_kernel<N, BWD>, dim3(pl.n[l + 1]), dim3(32), sizeof(double) * pl.G[l] * NX, s,
+                   (const double*)maps[l], pl.n[l], pl.G[l], (const double*)bnd[l + 1], C, abar, w0, T, bnd[l]);
 }
 
 template <int N, int MC>
