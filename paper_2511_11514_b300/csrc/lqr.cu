@@ -44,36 +44,38 @@ constexpr int kSB = 32;          // steps per streamed sub-block
 constexpr int kMaxChunk = 512;   // steps per scan chunk
 constexpr int kMaxChunks = 1024; // scan chunks
 
-// Inverse of a small SPD matrix (MC <= 3) by the adjugate; returns false if
-// a leading principal minor is not positive.
+// Entry (r, c) of the adjugate of a small symmetric matrix S (MC <= 3):
+// (-1)^(r+c) times the minor of S without row c and column r.
 template <int MC>
-__device__ __forceinline__ bool spd_inverse(const double* S, double* Si) {
+__device__ __forceinline__ double adj_entry(const double* S, int r, int c) {
     if constexpr (MC == 1) {
-        Si[0] = 1.0 / S[0];
-        return S[0] > 0.0;
+        return 1.0;
     } else if constexpr (MC == 2) {
-        const double det = S[0] * S[3] - S[1] * S[2];
-        const double inv = 1.0 / det;
-        Si[0] = S[3] * inv;
-        Si[1] = -S[1] * inv;
-        Si[2] = -S[2] * inv;
-        Si[3] = S[0] * inv;
-        return S[0] > 0.0 && det > 0.0;
+        const double v = S[(1 - c) * 2 + (1 - r)];
+        return r == c ? v : -v;
     } else {
-        const double a = S[0], b = S[1], c = S[2], d = S[3], e = S[4], f = S[5], g = S[6], h = S[7], i = S[8];
-        const double A = e * i - f * h, B = -(d * i - f * g), C = d * h - e * g;
-        const double det = a * A + b * B + c * C;
-        const double inv = 1.0 / det;
-        Si[0] = A * inv;
-        Si[1] = -(b * i - c * h) * inv;
-        Si[2] = (b * f - c * e) * inv;
-        Si[3] = B * inv;
-        Si[4] = (a * i - c * g) * inv;
-        Si[5] = -(a * f - c * d) * inv;
-        Si[6] = C * inv;
-        Si[7] = -(a * h - b * g) * inv;
-        Si[8] = (a * e - b * d) * inv;
-        return a > 0.0 && (a * e - b * d) > 0.0 && det > 0.0;
+        const int r0 = c == 0 ? 1 : 0, r1 = c == 2 ? 1 : 2;  // rows of the minor
+        const int c0 = r == 0 ? 1 : 0, c1 = r == 2 ? 1 : 2;  // its columns
+        const double m = fma(S[r0 * 3 + c0], S[r1 * 3 + c1], -S[r0 * 3 + c1] * S[r1 * 3 + c0]);
+        return ((r + c) & 1) ? -m : m;
+    }
+}
+// det(S) of a small SPD matrix; ok &= every leading principal minor > 0.
+template <int MC>
+__device__ __forceinline__ double spd_det(const double* S, bool& ok) {
+    if constexpr (MC == 1) {
+        ok &= S[0] > 0.0;
+        return S[0];
+    } else if constexpr (MC == 2) {
+        const double det = fma(S[0], S[3], -S[1] * S[2]);
+        ok &= S[0] > 0.0 && det > 0.0;
+        return det;
+    } else {
+        double det = 0.0;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) det = fma(S[q], adj_entry<3>(S, q, 0), det);
+        ok &= S[0] > 0.0 && fma(S[0], S[4], -S[1] * S[3]) > 0.0 && det > 0.0;
+        return det;
     }
 }
 
@@ -192,23 +194,41 @@ __global__ void __launch_bounds__(32, 1) riccati_kernel(const double* __restrict
                 if (role == 0 && r < c) sm.S[c * MC + r] = acc;
             }
             __syncwarp();
-            // phase 3: K = S^-1 G, N_t = S^-1 B'
+            // phase 3: K = S^-1 G, N_t = S^-1 B', S^-1 -- from the adjugate
+            // (adj S) S = det(S) I: each lane forms only the adjugate row its
+            // entry needs, its dot product, and one product with 1/det at the
+            // end (FP64 instructions are what a step costs on this GPU)
             {
-                double Si[MC * MC];
-                spd_ok &= spd_inverse<MC>(sm.S, Si);
-                if (lane < MC * MC) Sg[(size_t)t * MC * MC + lane] = Si[lane];
-                if (lane < 2 * MC * N) {
+                const double det = spd_det<MC>(sm.S, spd_ok);
+                const double inv = 1.0 / det;
+                // lanes: K (MC N), N_t (MC N), then S^-1's upper triangle
+                // (MC (MC + 1) / 2, mirrored; 30 lanes at most)
+                constexpr int NS = MC * (MC + 1) / 2;
+                const bool isS = lane >= 2 * MC * N && lane < 2 * MC * N + NS;
+                if (lane < 2 * MC * N + NS) {
                     const bool isK = lane < MC * N;
-                    const int f = isK ? lane : lane - MC * N;
-                    const int r = f / N, c = f % N;
-                    const double* W = isK ? sm.G : Bt;
-                    const int ws = isK ? N : 1, wo = isK ? c : c * MC;
+                    const int f = isK ? lane : (isS ? lane - 2 * MC * N : lane - MC * N);
+                    // upper-triangle index f -> (r, c), r <= c
+                    const int r = isS ? (f < MC ? 0 : (f < 2 * MC - 1 ? 1 : 2)) : f / N;
+                    const int c = isS ? f - (r == 0 ? 0 : (r == 1 ? MC - 1 : 2 * MC - 3)) : f % N;
                     double acc = 0.0;
+                    if (isS) {
+                        acc = adj_entry<MC>(sm.S, r, c);
+                    } else {
+                        const double* W = isK ? sm.G : Bt;
+                        const int ws = isK ? N : 1, wo = isK ? c : c * MC;
 #pragma unroll
-                    for (int q = 0; q < MC; ++q) acc = fma(Si[r * MC + q], W[q * ws + wo], acc);
-                    double* g = isK ? Kg : Ng;
-                    g[(size_t)t * MC * N + f] = acc;
-                    if (isK) sm.K[f] = acc;
+                        for (int q = 0; q < MC; ++q) acc = fma(adj_entry<MC>(sm.S, r, q), W[q * ws + wo], acc);
+                    }
+                    const double val = acc * inv;
+                    if (isS) {
+                        Sg[(size_t)t * MC * MC + r * MC + c] = val;
+                        Sg[(size_t)t * MC * MC + c * MC + r] = val;
+                    } else {
+                        double* g = isK ? Kg : Ng;
+                        g[(size_t)t * MC * N + f] = val;
+                        if (isK) sm.K[f] = val;
+                    }
                 }
             }
             __syncwarp();
