@@ -9,8 +9,8 @@ times every candidate on the caller's own inputs (for the Sinkhorn field in the
 library, cov_autotune_sinkhorn; for the Stein field here through the C-ABI),
 with CUDA events, as the per-iteration time (t(n_hi) - t(n_lo)) / (n_hi - n_lo)
 so that prep and launch costs cancel; the winner is cached in a JSON file keyed by
-GPU name, field kind, d and the power-of-two buckets of T and M, and applied
-to the context.
+GPU name, field kind, d, the power-of-two buckets of T and M and the exponent
+path, and applied to the context.
 
     python -m paper_2511_11514_b300.autotune --workload NAME   # prints the sweep
 """
@@ -34,9 +34,11 @@ def _bucket(n: int) -> int:
     return 1 << max(0, (int(n) - 1).bit_length())
 
 
-def cache_key(kind: str, d: int, T: int, M: int = 0) -> str:
+def cache_key(kind: str, d: int, T: int, M: int = 0, tc: int = cov.TENSOR_CORES_AUTO) -> str:
+    """GPU, field kind, d, the power-of-two buckets of T and M, and the
+    exponent path (COV_OPT_TENSOR_CORES) the sweep ran with."""
     name = torch.cuda.get_device_name().replace(" ", "_")
-    return f"{name}|{kind}|d{d}|T{_bucket(T)}|M{_bucket(M) if M else 0}"
+    return f"{name}|{kind}|d{d}|T{_bucket(T)}|M{_bucket(M) if M else 0}|tc{tc}"
 
 
 def load_cache(path: str = DEFAULT_CACHE) -> dict:
@@ -91,7 +93,8 @@ def sweep_svgd(ctx, x, h, score, candidates=CANDIDATES, reps=5):
 
 def tune_sinkhorn(ctx, x, y, eps, cache_path: str = DEFAULT_CACHE, force: bool = False) -> dict:
     """Pick (and apply) the fastest tiling for a Sinkhorn field of this shape."""
-    key = cache_key("sinkhorn", x.shape[1], x.shape[0], y.shape[0])
+    key = cache_key("sinkhorn", x.shape[1], x.shape[0], y.shape[0],
+                    ctx.option(cov.OPT_TENSOR_CORES, cov.TENSOR_CORES_AUTO))
     cache = load_cache(cache_path)
     if not force and key in cache:
         apply(ctx, cache[key])

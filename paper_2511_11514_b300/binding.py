@@ -157,6 +157,7 @@ class Context:
             raise CovError(st, "cov_ctx_create")
         self.h = h
         self._keep = []
+        self._options = {}      # options set through set_option (the tuner's cache keys read them)
         self._cache = {}        # persistent buffers of the graph-friendly gradient calls
         self._grad_token = 0    # identifies the latest recording forward of grad_forward
 
@@ -192,6 +193,11 @@ class Context:
 
     def set_option(self, key: int, value: int):
         self._check(load().cov_ctx_set_option(self.h, int(key), int(value)), "cov_ctx_set_option")
+        self._options[int(key)] = int(value)
+
+    def option(self, key: int, default: int):
+        """The value last set for `key` through set_option, else `default`."""
+        return self._options.get(int(key), default)
 
     def device_status(self, stream=None):
         """(status code, COV_DEV_* bits); synchronises the stream, clears the bits."""
