@@ -1017,7 +1017,7 @@ __device__ __forceinline__ void block_exclusive_scan(double (&x)[NV], double (&t
 // vel += dt u, p += dt vel (vel before its update); unicycle theta += dt
 // omega, (x, y) += dt v (cos, sin)(theta before its update).
 constexpr int kRK = 4;
-constexpr int kUnicycleSplitT = 2048;  // longer unicycle horizons take the three-kernel rollout
+constexpr int kUnicycleSplitT = 2048;  // longer unicycle horizons take the three-kernel rollout (without scratch)
 
 __global__ void __launch_bounds__(1024) update_rollout_kernel(RolloutArgs ro, double* __restrict__ u,
                                                                const double* __restrict__ v, int T, int n, int m,
@@ -1958,8 +1958,9 @@ cov_status update_rollout(cov_ctx* ctx, int model, const double* s0, double* u, 
     // as many warps as the horizon fills (kRK steps per thread), up to 1024
     // threads: short horizons scan over fewer warps
     const int threads = std::min(1024, std::max(32, ((T + kRK - 1) / kRK + 31) / 32 * 32));
-    // long unicycle horizons: the heading scan, then the sincos of every
-    // step spread over the GPU, then the position scan
+    // without scratch for the chunked sums, long unicycle horizons still
+    // spread the per-step sincos over the GPU: the heading scan, the
+    // increments, then the position scan, each scan in one CTA
     ro.heading_only = model == COV_UNICYCLE && T > kUnicycleSplitT;
     launch_pdl(update_rollout_kernel, dim3(1), dim3(threads), 0, stream, ro, u, v, T, n, m, s);
     if (ro.heading_only) {
