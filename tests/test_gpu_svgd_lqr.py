@@ -1,5 +1,7 @@
 """GPU parity of the Stein field (Eq. 4), the mixture score, linearisation
 (Eq. 8), rollout and the FP64 LQR step (Eq. 9-10) with the FP64 oracle."""
+import dataclasses
+
 import numpy as np
 import pytest
 import torch
@@ -107,11 +109,13 @@ def test_lqr_unicycle_long_horizon(cov, ctx, orc):
     assert ctx.device_status()[1] == 0
 
 
-@pytest.mark.parametrize("T", [1, 513, 4096, 10001])
+@pytest.mark.parametrize("T", [1, 255, 256, 257, 513, 1024, 1025, 4096, 10001])
 @pytest.mark.parametrize("model", [wl.SINGLE_INT, wl.DOUBLE_INT, wl.UNICYCLE])
 def test_linearize_and_rollout_match_oracle(cov, ctx, orc, model, T):
-    """The rollout runs in tiles of 4096 steps with carries; T spans one,
-    several and a ragged last tile."""
+    """Up to 256 steps the rollout is one CTA's block scans; longer horizons
+    chunk its sums over the GPU (256 steps per chunk, the state entering
+    each chunk from the earlier chunks' totals): T spans one chunk, its
+    edge, several chunks and a ragged last one."""
     n, m = wl.MODEL_DIMS[model]
     dt = 0.03
     g = wl.rng(model)
@@ -124,3 +128,24 @@ def test_linearize_and_rollout_match_oracle(cov, ctx, orc, model, T):
     Ao, Bo = orc.linearize(model, so, u, dt)
     np.testing.assert_allclose(host(A), Ao, rtol=1e-13, atol=1e-15)
     np.testing.assert_allclose(host(B), Bo, rtol=1e-13, atol=1e-15)
+
+
+@pytest.mark.parametrize("model", [wl.SINGLE_INT, wl.DOUBLE_INT, wl.UNICYCLE])
+def test_rollout_update_in_solve_matches_oracle(cov, ctx, orc, model):
+    """The update u += eta v fused into the chunked rollout (the cov_solve
+    path, T = 1000 > one chunk): one outer iteration of the Stein field
+    against the oracle's, controls and trajectory."""
+    w = dataclasses.replace(wl.SVGD_SINGLE_T256, name="svgd_rollout_check", model=model, T=1000, dt=0.01,
+                            n_outer=1)
+    inst = wl.make_instance(w)
+    gmm = tuple(wl.f32_pair(v)[1] for v in inst.gmm)
+    prob = cov.make_problem(w.model, w.T, w.dt, inst.s0, w.field, inst.Q, inst.R, w.eta, gmm=gmm, h=w.h)
+    u = dev64(inst.u0)
+    s = cov.cov_solve(ctx, prob, 1, u)
+    st, flags = ctx.device_status()
+    assert st == cov.COV_OK, flags
+    uo, so = orc.solve(w.model, w.dt, inst.s0, inst.u0, w.field, inst.Q, inst.R, w.eta, 1, gmm=gmm, h=w.h)
+    s_init = orc.rollout(w.model, inst.s0, inst.u0, w.dt)
+    # the step is eta * z(field); FP32 field error bounds its relative error
+    assert rel_norm(host(s) - s_init, so - s_init) <= 1e-4
+    assert rel_norm(host(u) - inst.u0, uo - inst.u0) <= 1e-4
