@@ -286,7 +286,7 @@ static cov_status cov::solve_impl(cov_ctx* ctx, const cov_problem* prob, int n_o
 
     // initial trajectory from s0 and the given controls
     if (initial_rollout) {
-        r = cov_rollout(ctx, prob->model, prob->s0, u, prob->T, prob->dt, s_out, (cov_stream_t)stream);
+        r = update_rollout(ctx, prob->model, prob->s0, u, nullptr, 0.0, prob->T, prob->dt, s_out, st, b.rtot);
         if (r != COV_OK) return r;
     }
     if (n_outer == 0) return COV_OK;
@@ -464,7 +464,7 @@ extern "C" cov_status cov_solve_batched(cov_ctx* ctx, const cov_problem* probs, 
     for (int p = 0; p < n_probs && r == COV_OK; ++p) {
         const cov_problem* P = &probs[p];
         cudaStream_t sp = ctx->pool[p % K];
-        r = cov_rollout(ctx, P->model, P->s0, u[p], P->T, P->dt, s_out[p], (cov_stream_t)sp);
+        r = update_rollout(ctx, P->model, P->s0, u[p], nullptr, 0.0, P->T, P->dt, s_out[p], sp, bufs[p].rtot);
         if (r != COV_OK || n_outer == 0) continue;
         if (P->field == COV_FIELD_SINKHORN) {
             sinkhorn_reference_stats(P->y, P->M, P->d, P->b, bufs[p].scal, sp);
@@ -697,7 +697,7 @@ static cov_status solve_taped(cov_ctx* ctx, const cov_problem* prob, int K, doub
         if (r != COV_OK) return r;
     }
     auto work = [&](cudaStream_t ws_st) -> cov_status {
-        cov_status q = cov_rollout(ctx, prob->model, prob->s0, u, T, prob->dt, s_out, (cov_stream_t)ws_st);
+        cov_status q = update_rollout(ctx, prob->model, prob->s0, u, nullptr, 0.0, T, prob->dt, s_out, ws_st, b.rtot);
         if (q != COV_OK || K == 0) return q;
         sinkhorn_reference_stats(prob->y, prob->M, d, prob->b, b.scal, ws_st);
         ctx->tapes.assign(K, SkTape{});
