@@ -254,29 +254,17 @@ __global__ void __launch_bounds__(kTcThreads, kTcMinBlocks) lse_tc_kernel(const 
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&S.tempty[b]);
-            // of every 8 values kTcPolyPairs pairs take 2^x on the FMA pipe,
-            // the rest on MUFU
+            // of the 64 values the last 2 kTcPolyPairs take 2^x on the FMA
+            // pipe (exp2_fma2, two at a time), the rest MUFU.EX2
 #pragma unroll
-            for (int k = 0; k < 32; k += 8) {
+            for (int j = 0; j < 64 - 2 * kTcPolyPairs; ++j)
+                acc[j & 7] += ex2(__uint_as_float(j < 32 ? v0[j] : v1[j - 32]));
 #pragma unroll
-                for (int j = 0; j < 8 - 2 * kTcPolyPairs; ++j) acc[j] += ex2(__uint_as_float(v0[k + j]));
-#pragma unroll
-                for (int j = 8 - 2 * kTcPolyPairs; j < 8; j += 2) {
-                    const float2 e = exp2_fma2(make_float2(__uint_as_float(v0[k + j]), __uint_as_float(v0[k + j + 1])));
-                    acc[j] += e.x;
-                    acc[j + 1] += e.y;
-                }
-            }
-#pragma unroll
-            for (int k = 0; k < 32; k += 8) {
-#pragma unroll
-                for (int j = 0; j < 8 - 2 * kTcPolyPairs; ++j) acc[j] += ex2(__uint_as_float(v1[k + j]));
-#pragma unroll
-                for (int j = 8 - 2 * kTcPolyPairs; j < 8; j += 2) {
-                    const float2 e = exp2_fma2(make_float2(__uint_as_float(v1[k + j]), __uint_as_float(v1[k + j + 1])));
-                    acc[j] += e.x;
-                    acc[j + 1] += e.y;
-                }
+            for (int j = 64 - 2 * kTcPolyPairs; j < 64; j += 2) {
+                const float2 e = exp2_fma2(make_float2(__uint_as_float(j < 32 ? v0[j] : v1[j - 32]),
+                                                       __uint_as_float(j < 32 ? v0[j + 1] : v1[j - 31])));
+                acc[j & 7] += e.x;
+                acc[(j + 1) & 7] += e.y;
             }
         }
         S.red_s[hf][q * 32 + lane] = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));

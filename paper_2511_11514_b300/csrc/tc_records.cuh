@@ -20,11 +20,12 @@ constexpr int kTcMinBlocks = 512 / kTcTmemCols;    // resident CTAs per SM that 
 // the tensor-core kernel measured 7-10 % faster than the CUDA-core one, below
 // it slower (one 544-thread CTA per SM is too coarse for short launches).
 constexpr long long kTcAutoPairs = 1LL << 30;
-// Of every 8 exponentials in the tensor-core kernel, how many pairs are
-// taken on the FMA pipe (exp2_fma2) instead of MUFU.  Default 0: measured
-// slower on B300 (its MUFU issues 32 ex2/clk/SM; the polynomial costs ~8
-// more instructions per value than it frees); a build flag
-// -DCOV_TC_POLY_PAIRS=1..4 selects 25..100 %.
+// Of the 64 exponentials a reader thread takes per tile, how many pairs go
+// to the FMA pipe (exp2_fma2) instead of MUFU (build flag
+// -DCOV_TC_POLY_PAIRS=0..32).  Default 0: at T = 65536, M = 262144 the
+// kernel ran at 0.727 of the roofline with none, 0.729 with 2 pairs (6 %),
+// 0.699 with 4 and 0.643 with 6 -- the readers are not bound by MUFU alone,
+// and the polynomial's ~8 instructions per value cost more than they free.
 #ifndef COV_TC_POLY_PAIRS
 #define COV_TC_POLY_PAIRS 0
 #endif
