@@ -54,8 +54,12 @@ def _random_lqr(T, n, m, seed):
 
 
 @pytest.mark.parametrize("T,n,m", [(1, 2, 2), (2, 1, 1), (33, 4, 2), (63, 4, 2), (64, 4, 2), (100, 3, 2),
-                                   (1000, 4, 3), (4096, 4, 2), (65, 2, 1), (70, 3, 3), (20000, 4, 2), (65536, 3, 2)])
+                                   (150, 4, 2), (300, 3, 3), (700, 2, 2), (1000, 4, 3), (2500, 3, 2), (4096, 4, 2),
+                                   (7000, 4, 3), (65, 2, 1), (70, 3, 3), (20000, 4, 2), (65536, 3, 2)])
 def test_lqr_track_matches_oracle(cov, ctx, orc, T, n, m):
+    """Horizons across the parallel plans: the serial pass (T < 64), and
+    the Riccati recursion and affine scans with 0 to 3 grouping levels above
+    their chunks (the depth grows with T)."""
     A, B, Q, R, abar = _random_lqr(T, n, m, seed=T + 10 * n + m)
     v, z = cov.cov_lqr_track(ctx, dev64(A), dev64(B), Q, R, dev64(abar))
     vo, zo, _ = orc.lqr_track(A, B, Q, R, abar)
