@@ -1306,6 +1306,7 @@ cov_status sinkhorn_field_ws(cov_ctx* ctx, void* ws, size_t ws_bytes, const floa
     };
     int stable = 0;            // iterations run at the current eps
     bool warm_origin = warm;   // the warm-start potentials are still at the current eps
+    bool bary_done = false;    // the last f-update already formed the cross barycentre
     for (int it = 0; it < n_iter && r == COV_OK; ++it) {
         if (scaled) {
             const double e_it = anneal_eps(eps, eps_start, eps_decay, it);
@@ -1356,8 +1357,15 @@ cov_status sinkhorn_field_ws(cov_ctx* ctx, void* ws, size_t ws_bytes, const floa
         a.oa = B.hx; a.oca = -1.f; a.ob = nullptr; a.oc0 = log2a;  // log2 a - hx
         a.fixed = fixed;
         if (recs) { a.rec0 = B.c0y; a.rech = B.hry; a.out_rec = B.hrx; }
-        const int ncB[1] = {M}, coB[1] = {M_F * B.cnt_ld};
-        r = run_pairs(ctx, d, fam, &a, ncB, 1, coB, B.counters, stream);
+        // the last f-update, at the target eps on the CUDA cores, also forms
+        // the cross barycentre of its own softmax (the gradient pass's first
+        // half reads the same columns and the same final g, and normalises by
+        // its own sum): one pass fewer
+        const bool with_bary = a_out && it == n_iter - 1 && !recs && eps_cur == (double)eps;
+        if (with_bary) a.bary = B.bary;
+        const int ncB[1] = {M}, coB[1] = {(with_bary ? M_GW : M_F) * B.cnt_ld};
+        r = run_pairs(ctx, d, with_bary ? M_GW : fam, &a, ncB, 1, coB, B.counters, stream);
+        bary_done = with_bary;
         std::swap(hp_cur, hp_nxt);
         std::swap(hrp_cur, hrp_nxt);
         ++stable;
@@ -1365,19 +1373,23 @@ cov_status sinkhorn_field_ws(cov_ctx* ctx, void* ws, size_t ws_bytes, const floa
     if (r != COV_OK) return r;
     to_eps((double)eps);  // the field and the returned potentials are at the target eps
     if (a_out) {
-        PairArgs a = base;  // cross barycentre: (sum_j pi_ij yhat_j) - xhat_i
-        a.rows = B.xs; a.row_ld = B.Tp; a.n_rows = T;
-        a.cols = B.ys; a.colh = B.hy; a.col_ld = B.Mp;
-        a.bary = B.bary;
-        if (first) a.pre_ok = 0;
-        first = false;
-        const int nc1[1] = {M}, co1[1] = {M_WY * B.cnt_ld};
-        r = run_pairs(ctx, d, M_WY, &a, nc1, 1, co1, B.counters, stream);
-        if (r != COV_OK) return r;
-        a = base;           // self barycentre and the field 2 sigma (ybar - xbar)
+        if (!bary_done) {
+            PairArgs a = base;  // cross barycentre: (sum_j pi_ij yhat_j) - xhat_i
+            a.rows = B.xs; a.row_ld = B.Tp; a.n_rows = T;
+            a.cols = B.ys; a.colh = B.hy; a.col_ld = B.Mp;
+            a.bary = B.bary;
+            if (first) a.pre_ok = 0;
+            first = false;
+            const int nc1[1] = {M}, co1[1] = {M_WY * B.cnt_ld};
+            r = run_pairs(ctx, d, M_WY, &a, nc1, 1, co1, B.counters, stream);
+            if (r != COV_OK) return r;
+        }
+        PairArgs a = base;  // self barycentre and the field 2 sigma (ybar - xbar)
         a.rows = B.xs; a.row_ld = B.Tp; a.n_rows = T;
         a.cols = B.xs; a.colh = hp_cur; a.col_ld = B.Tp;
         a.bary = B.bary; a.a_out = a_out; a.a_scale = 2.0f * sigma;
+        if (first) a.pre_ok = 0;
+        first = false;
         const int nc2[1] = {T}, co2[1] = {M_WX * B.cnt_ld};
         r = run_pairs(ctx, d, M_WX, &a, nc2, 1, co2, B.counters, stream);
         if (r != COV_OK) return r;
