@@ -308,8 +308,10 @@ __device__ __forceinline__ void merge_lse_splits(const float* part, size_t part_
     }
 }
 
+// `hin`, when given, holds a.in_h[i] (fetched early by the caller).
 template <int D, int MODE>
-__device__ __forceinline__ void epilogue(const PairArgs& a, int i, float m, float s, const float* acc) {
+__device__ __forceinline__ void epilogue(const PairArgs& a, int i, float m, float s, const float* acc,
+                                         const float* hin = nullptr) {
     using TR = PairTraits<D, MODE>;
     if (i >= a.n_rows) return;
     bool ok = true;
@@ -339,9 +341,9 @@ __device__ __forceinline__ void epilogue(const PairArgs& a, int i, float m, floa
     } else {
         const float L = m + log2f(s);
         float v;
-        if (a.emode == M_G) v = a.in_h[i] - L;
+        if (a.emode == M_G) v = (hin ? *hin : a.in_h[i]) - L;
         else if (a.emode == M_F) v = a.log2a - L;
-        else v = 0.5f * (a.log2a + a.in_h[i] - L);
+        else v = 0.5f * (a.log2a + (hin ? *hin : a.in_h[i]) - L);
         ok &= finitef(v);
         a.out_h[i] = v;
         if (a.out_rec)
@@ -379,6 +381,7 @@ __global__ void __launch_bounds__(kThreads) pairs_kernel(const __grid_constant__
     __shared__ __align__(128) float sm[2][NC * kTile];
     __shared__ __align__(8) uint64_t bar[2];
     __shared__ float red[kWarps][NACC][RB];
+    __shared__ float epi_h[TR::kO ? RB : 1];  // the rows' in_h, for the epilogue
     __shared__ int s_last;
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -465,6 +468,19 @@ __global__ void __launch_bounds__(kThreads) pairs_kernel(const __grid_constant__
         }
     };
 
+    // The epilogue's per-row input (log2 b of a g-update, the previous
+    // potential of a p-update) is copied to shared memory once the
+    // dependency wait has passed, so that the merging CTA does not start an
+    // L2 round trip of its own after the merge; each thread later reads the
+    // rows it copied itself.
+    const bool epi_pre = TR::kO && a.in_h && a.emode != M_F;
+    auto prefetch_epi = [&]() {
+        if (!epi_pre) return;
+        for (int q = threadIdx.x; q < RB; q += kThreads)
+            if (row0 + q < a.n_rows) cp_async4(&epi_h[q], a.in_h + row0 + q);
+        cp_async_commit();
+    };
+
     // One pass over the columns [cb, ce).  Tiles alternate between the two
     // stages by a running count over all passes (which also gives each
     // mbarrier's phase parity).  The first pass overlaps its first column
@@ -478,6 +494,7 @@ __global__ void __launch_bounds__(kThreads) pairs_kernel(const __grid_constant__
             if (a.pre_ok) grid_dep_wait();
             grid_dep_launch();
             if (threadIdx.x == 0 && nt > 0) issue_h(cb, ce, 0, gtile & 1);
+            prefetch_epi();
         } else if (threadIdx.x == 0 && nt > 0) {
             issue_coords(cb, ce, 0, gtile & 1);
             issue_h(cb, ce, 0, gtile & 1);
@@ -579,7 +596,10 @@ __global__ void __launch_bounds__(kThreads) pairs_kernel(const __grid_constant__
                 s_last = (prev & (kRedoTicket - 1u)) != (unsigned)(ns - 1) ? 0 : (prev + add >= kRedoTicket ? 2 : 1);
             }
             __syncthreads();
-            if (!s_last) return;
+            if (!s_last) {
+                if (epi_pre) cp_async_wait_all();  // no copy lands after the CTA exits
+                return;
+            }
             // every split against the same fixed offset (this CTA's fin_m):
             // a plain sum; otherwise the general merge
             const bool plain = fixed && s_last == 1;
@@ -605,7 +625,9 @@ __global__ void __launch_bounds__(kThreads) pairs_kernel(const __grid_constant__
             run_pass(0, a.n_cols8, false, false);
             reduce_warps();
         }
-        for (int q = threadIdx.x; q < RB; q += kThreads) epilogue<D, MODE>(a, row0 + q, fin_m[q], fin_s[q], nullptr);
+        if (epi_pre) cp_async_wait_all();
+        for (int q = threadIdx.x; q < RB; q += kThreads)
+            epilogue<D, MODE>(a, row0 + q, fin_m[q], fin_s[q], nullptr, epi_pre ? &epi_h[q] : nullptr);
         if (ns > 1 && threadIdx.x == 0) a.counters[rb] = 0u;  // ready for the next launch
         return;
     }

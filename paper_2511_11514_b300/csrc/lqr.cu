@@ -79,15 +79,6 @@ __device__ __forceinline__ double spd_det(const double* S, bool& ok) {
     }
 }
 
-// Asynchronous 8-byte global->shared copies (cp.async): the next sub-block
-// of per-step matrices streams in while the current one is processed.
-__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all_but_one() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
-
 // Copy rows t0 .. t0+cnt-1 (each `e` doubles) of src into dst; thread
 // `lane` of `nthreads` takes every nthreads-th double.
 __device__ __forceinline__ void stream_rows(double* dst, const double* __restrict__ src, int t0, int cnt, int e,
