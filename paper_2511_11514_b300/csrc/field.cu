@@ -475,10 +475,13 @@ __global__ void __launch_bounds__(kThreads) pairs_kernel(const __grid_constant__
     // rows it copied itself.
     const bool epi_pre = TR::kO && a.in_h && a.emode != M_F;
     auto prefetch_epi = [&]() {
-        if (!epi_pre) return;
-        for (int q = threadIdx.x; q < RB; q += kThreads)
-            if (row0 + q < a.n_rows) cp_async4(&epi_h[q], a.in_h + row0 + q);
-        cp_async_commit();
+        if constexpr (TR::kO) {
+            if (epi_pre) {
+                for (int q = threadIdx.x; q < RB; q += kThreads)
+                    if (row0 + q < a.n_rows) cp_async4(&epi_h[q], a.in_h + row0 + q);
+                cp_async_commit();
+            }
+        }
     };
 
     // One pass over the columns [cb, ce).  Tiles alternate between the two
@@ -793,37 +796,79 @@ namespace cov {
 // Prep kernels
 // ---------------------------------------------------------------------------
 // scal layout: [0..5] centre, [8] 1/sum(b) (or 0 when b == NULL)
-__global__ void sk_centre_kernel(const float* __restrict__ y, int M, int d, const float* __restrict__ b,
-                                 float* __restrict__ scal) {
+//
+// One CTA.  The points are read as float4 runs of the flat [M][d] array:
+// with 960 threads a thread's run advances by 3840 floats, a multiple of
+// every d <= 6, so lane e of each of its float4 loads holds component
+// (4 tid + e) mod d and four running sums suffice; eight loads per thread
+// are in flight at a time.  A pointer that is not 16-byte aligned, and the
+// last few floats, take scalar loads.  Warp totals are added in warp order.
+constexpr int kCentreThreads = 960;
+constexpr int kCentreUnroll = 8;
+
+__device__ __forceinline__ void add_component(float (&acc)[COV_MAX_D + 1], int c, float v) {
+#pragma unroll
+    for (int k = 0; k <= COV_MAX_D; ++k)
+        if (k == c) acc[k] += v;
+}
+
+// Sum of n floats of p from flat index 0 as float4 runs (when aligned): the
+// four lane sums of this thread, and the scalar tail added to acc[c(f)].
+__device__ __forceinline__ size_t sum_runs(const float* __restrict__ p, size_t n, float (&ls)[4]) {
+    const size_t nvec = (reinterpret_cast<uintptr_t>(p) & 15u) == 0 ? n / 4 : 0;
+    const float4* p4 = reinterpret_cast<const float4*>(p);
+    for (size_t q0 = threadIdx.x; q0 < nvec; q0 += (size_t)kCentreThreads * kCentreUnroll) {
+        float4 v[kCentreUnroll];
+#pragma unroll
+        for (int u = 0; u < kCentreUnroll; ++u) {
+            const size_t q = q0 + (size_t)u * kCentreThreads;
+            v[u] = q < nvec ? p4[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < kCentreUnroll; ++u) {
+            ls[0] += v[u].x;
+            ls[1] += v[u].y;
+            ls[2] += v[u].z;
+            ls[3] += v[u].w;
+        }
+    }
+    return 4 * nvec;  // first flat index left to the scalar tail
+}
+
+__global__ void __launch_bounds__(kCentreThreads) sk_centre_kernel(const float* __restrict__ y, int M, int d,
+                                                                   const float* __restrict__ b,
+                                                                   float* __restrict__ scal) {
     pdl_prologue();
-    __shared__ float sh[32][COV_MAX_D + 1];
+    __shared__ float sh[kCentreThreads / 32][COV_MAX_D + 1];
+    const int tid = threadIdx.x;
     float acc[COV_MAX_D + 1];
 #pragma unroll
     for (int k = 0; k <= COV_MAX_D; ++k) acc[k] = 0.f;
-    // components unrolled to the compile-time maximum (registers, not a
-    // stack array), four points per thread in flight
-#pragma unroll 4
-    for (int j = threadIdx.x; j < M; j += blockDim.x) {
+    const size_t ny = (size_t)M * d;
+    float ls[4] = {0.f, 0.f, 0.f, 0.f};
+    const size_t ty = sum_runs(y, ny, ls);
 #pragma unroll
-        for (int k = 0; k < COV_MAX_D; ++k)
-            if (k < d) acc[k] += y[(size_t)j * d + k];
-        if (b) acc[COV_MAX_D] += b[j];
+    for (int e = 0; e < 4; ++e) add_component(acc, (4 * tid + e) % d, ls[e]);
+    for (size_t f = ty + tid; f < ny; f += kCentreThreads) add_component(acc, (int)(f % (size_t)d), y[f]);
+    if (b) {
+        float lb[4] = {0.f, 0.f, 0.f, 0.f};
+        const size_t tb = sum_runs(b, (size_t)M, lb);
+        acc[COV_MAX_D] += (lb[0] + lb[1]) + (lb[2] + lb[3]);
+        for (size_t f = tb + tid; f < (size_t)M; f += kCentreThreads) acc[COV_MAX_D] += b[f];
     }
+#pragma unroll
     for (int k = 0; k <= COV_MAX_D; ++k)
         for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    const int w = tid >> 5, l = tid & 31;
     if (l == 0)
+#pragma unroll
         for (int k = 0; k <= COV_MAX_D; ++k) sh[w][k] = acc[k];
     __syncthreads();
-    if (threadIdx.x == 0) {
-        const int nw = blockDim.x >> 5;
-        for (int k = 0; k <= COV_MAX_D; ++k) {
-            float t = 0.f;
-            for (int i = 0; i < nw; ++i) t += sh[i][k];
-            acc[k] = t;
-        }
-        for (int k = 0; k < COV_MAX_D; ++k) scal[k] = k < d ? acc[k] / (float)M : 0.f;
-        scal[8] = b ? 1.0f / acc[COV_MAX_D] : 0.f;
+    if (tid <= COV_MAX_D) {
+        float t = 0.f;
+        for (int i = 0; i < kCentreThreads / 32; ++i) t += sh[i][tid];
+        if (tid < COV_MAX_D) scal[tid] = tid < d ? t / (float)M : 0.f;
+        else scal[8] = b ? 1.0f / t : 0.f;
     }
 }
 
@@ -1240,7 +1285,7 @@ size_t sinkhorn_split_bytes(int T, int M, int d) {
 }
 
 void sinkhorn_reference_stats(const float* y, int M, int d, const float* b, float* scal, cudaStream_t stream) {
-    launch_pdl(sk_centre_kernel, dim3(1), dim3(1024), 0, stream, y, M, d, b, scal);
+    launch_pdl(sk_centre_kernel, dim3(1), dim3(kCentreThreads), 0, stream, y, M, d, b, scal);
 }
 
 size_t sinkhorn_ws_bytes(int T, int M, int d) {
@@ -1275,7 +1320,7 @@ cov_status sinkhorn_field_ws(cov_ctx* ctx, void* ws, size_t ws_bytes, const floa
     if (scal_given)
         B.scal = const_cast<float*>(scal_given);
     else
-        launch_pdl(sk_centre_kernel, dim3(1), dim3(1024), 0, stream, y, M, d, b, B.scal);
+        launch_pdl(sk_centre_kernel, dim3(1), dim3(kCentreThreads), 0, stream, y, M, d, b, B.scal);
     const int np = std::max(B.Tp, B.Mp);
     launch_pdl(sk_prep_kernel, dim3((np + 255) / 256), dim3(256), 0, stream, x, x_ld, T, y, M, b, d, (float)(1.0 / sqrt(epsln2_0)),
                                                          (float)(1.0 / epsln2_0), log2a, warm, f, g, p, B,
@@ -1504,7 +1549,7 @@ cov_status sinkhorn_tape_ws(cov_ctx* ctx, void* ws, size_t ws_bytes, const float
     if (scal_given)
         B.scal = const_cast<float*>(scal_given);
     else
-        launch_pdl(sk_centre_kernel, dim3(1), dim3(1024), 0, stream, y, M, d, b, B.scal);
+        launch_pdl(sk_centre_kernel, dim3(1), dim3(kCentreThreads), 0, stream, y, M, d, b, B.scal);
     const int np = std::max(B.Tp, B.Mp);
     launch_pdl(sk_prep_kernel, dim3((np + 255) / 256), dim3(256), 0, stream, x, x_ld, T, y, M, b, d, (float)(1.0 / tp.sigma),
                                                          (float)(1.0 / epsln2), tp.log2a, 0, nullptr, nullptr,

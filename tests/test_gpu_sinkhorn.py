@@ -49,6 +49,27 @@ def test_fixed_iterations_match_oracle(cov, ctx, orc, T, M, d, eps, weighted, n_
     assert ctx.device_status()[1] == 0
 
 
+@pytest.mark.parametrize("T,M,d,eps", [(300, 517, 3, 0.01), (200, 4099, 2, 0.02), (100, 2000, 5, 0.05)])
+def test_reference_at_unaligned_addresses(cov, ctx, orc, T, M, d, eps):
+    """The reference points and weights handed over one float past a 16-byte
+    boundary (views into larger buffers): the reference statistics take their
+    scalar path there, and the potentials and field still match the oracle."""
+    x, y, b = _inputs(T, M, d, True, seed=11 * T + M)
+    ybuf = torch.zeros(M * d + 4, dtype=torch.float32, device="cuda")
+    bbuf = torch.zeros(M + 4, dtype=torch.float32, device="cuda")
+    ybuf[1:1 + M * d] = dev32(y).reshape(-1)
+    bbuf[1:1 + M] = dev32(b)
+    yv, bv = ybuf[1:1 + M * d].view(M, d), bbuf[1:1 + M]
+    assert yv.data_ptr() % 16 == 4 and bv.data_ptr() % 16 == 4
+    a, f, g, p = cov.cov_field_sinkhorn(ctx, dev32(x), yv, eps, 6, b=bv)
+    fo, go, po = orc.sinkhorn(x, y, b, eps, 6)
+    ao = orc.sinkhorn_field(x, y, b, eps, go, po)
+    for u, v in ((f, fo), (g, go), (p, po)):
+        assert np.abs(host(u) - v).max() / eps <= POT_TOL
+    assert rel_norm(host(a), ao) <= FIELD_TOL
+    assert ctx.device_status()[1] == 0
+
+
 @pytest.mark.parametrize("T,M,d,eps,weighted", CASES[2:6])
 def test_single_update_from_identical_potentials(cov, ctx, orc, T, M, d, eps, weighted):
     """Teacher-forced: one GPU iteration from potentials the oracle produced
