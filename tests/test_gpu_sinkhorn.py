@@ -154,3 +154,16 @@ def test_full_size_unicycle_density_workload_sampled_rows(cov, ctx, orc):
     errs = _sampled_rows_check(cov, ctx, orc, x, inst.y, w.eps, 3, 128, seed=2)
     assert max(errs[:3]) <= POT_TOL, errs
     assert errs[3] <= FIELD_TOL, errs
+
+
+def test_repeated_calls_are_bitwise_identical(cov, ctx):
+    """Column splits are merged in split order (no float atomics), so the
+    same inputs give the same bits, at a size with 30+ splits per row block."""
+    T, M, eps = 4096, 16384, 0.005
+    x, y, b = _inputs(T, M, 2, True, seed=77)
+    xd, yd, bd = dev32(x), dev32(y), dev32(b)
+    r1 = [host(t) for t in cov.cov_field_sinkhorn(ctx, xd, yd, eps, 8, b=bd)]
+    r2 = [host(t) for t in cov.cov_field_sinkhorn(ctx, xd, yd, eps, 8, b=bd)]
+    for u, v in zip(r1, r2):
+        np.testing.assert_array_equal(u, v)
+    assert ctx.device_status()[1] == 0
