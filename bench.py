@@ -392,10 +392,7 @@ def run_ours(args):
         yb = torch.as_tensor(ib.y, dtype=torch.float32, device=dev).contiguous()
         if not args.no_tune:
             from paper_2511_11514_b300 import autotune
-            # the tile shape only matters on the CUDA cores (the tensor-core
-            # kernel has one shape): tune that path
-            ctx.set_option(cov.OPT_TENSOR_CORES, cov.TENSOR_CORES_OFF)
-            chb = autotune.tune_sinkhorn(ctx, xb, yb, wb.eps)
+            chb = autotune.tune_sinkhorn(ctx, xb, yb, wb.eps)  # tunes the CUDA-core path
         cov.cov_field_sinkhorn(ctx, xb, yb, wb.eps, 1, field=False)
 
         def big_ms(n):

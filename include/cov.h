@@ -138,6 +138,8 @@ COV_API cov_status cov_ctx_set_option(cov_ctx* ctx, int key, long long value);
  * candidate (rows per thread, resident-CTA cap) in {(2,8), (4,8), (8,8),
  * (4,6), (2,6), (8,4)} with CUDA events on `stream`, as (t(6 iterations) -
  * t(2)) / 4 (median of 3), and applies the fastest to the context.
+ * The shape only concerns the CUDA-core kernel, so the sweep runs with
+ * COV_OPT_TENSOR_CORES off and restores the context's setting after it.
  * Synchronises the stream.  best_R, best_ctas_per_sm: host outputs (may be
  * NULL); sweep: host [6][3] (R, cap, microseconds per iteration) or NULL.
  * Workspace as cov_field_sinkhorn. */

@@ -92,9 +92,13 @@ def sweep_svgd(ctx, x, h, score, candidates=CANDIDATES, reps=5):
 
 
 def tune_sinkhorn(ctx, x, y, eps, cache_path: str = DEFAULT_CACHE, force: bool = False) -> dict:
-    """Pick (and apply) the fastest tiling for a Sinkhorn field of this shape."""
-    key = cache_key("sinkhorn", x.shape[1], x.shape[0], y.shape[0],
-                    ctx.option(cov.OPT_TENSOR_CORES, cov.TENSOR_CORES_AUTO))
+    """Pick (and apply) the fastest tiling for a Sinkhorn field of this shape.
+
+    The tile shape only shapes the CUDA-core kernel (the tensor-core kernel
+    has one shape; the CUDA cores still run the first iteration, the
+    gradient passes and any recompute), so the library's sweep runs with
+    the tensor cores off whatever the context's setting."""
+    key = cache_key("sinkhorn", x.shape[1], x.shape[0], y.shape[0], cov.TENSOR_CORES_OFF)
     cache = load_cache(cache_path)
     if not force and key in cache:
         apply(ctx, cache[key])

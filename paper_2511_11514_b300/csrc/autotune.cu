@@ -28,6 +28,10 @@ extern "C" cov_status cov_autotune_sinkhorn(cov_ctx* ctx, const float* x, int T,
     if (cudaSetDevice(ctx->device) != cudaSuccess) return COV_ERR_CUDA;
     cudaStream_t st = (cudaStream_t)stream;
     const int R0 = ctx->rows_per_thread, c0 = ctx->ctas_per_sm;
+    // the shapes are those of the CUDA-core kernel: sweep that path whatever
+    // the exponent setting (the tensor-core kernel has a single shape)
+    const int tc0 = ctx->use_tc;
+    ctx->use_tc = 0;
     cudaEvent_t e0, e1;
     if (cov::cuda_failed(ctx, cudaEventCreate(&e0))) return COV_ERR_CUDA;
     if (cov::cuda_failed(ctx, cudaEventCreate(&e1))) {
@@ -78,6 +82,7 @@ extern "C" cov_status cov_autotune_sinkhorn(cov_ctx* ctx, const float* x, int T,
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    ctx->use_tc = tc0;
     if (r != COV_OK) {
         ctx->rows_per_thread = R0;
         ctx->ctas_per_sm = c0;
