@@ -53,6 +53,9 @@ FP32_LANES_PER_SM_CLK = 128
 # workload from one ncu capture of the current kernel (fixed-offset form):
 # 388 KB (g + p launch) and 291 KB (f launch), no writes.
 PAIRS_TRAFFIC_BYTES = 339456
+# The same for lse_tc_kernel at T = 65536, M = 262144 (the default path at
+# that size): 9.47 MB (g + p launch) and 13.41 MB (f launch), no writes.
+TC_LARGE_TRAFFIC_BYTES = 11440512
 
 
 def parse_args():
@@ -469,6 +472,14 @@ def run_ours(args):
     d2h = u_out.numel() * 8 + s_out.numel() * 8
 
     launches_per_step = count_library_launches(lambda: cov.cov_solve_continue(ctx, prob, 1, u, s))
+    # the exponent path the default setting takes (launches of >= 2^30 pairs
+    # on the tensor cores) and the DRAM traffic captured for it, where known
+    tc_path = args.tensor_cores or min(w.M * w.T + w.T * w.T, w.T * w.M) >= 2 ** 30
+    traffic = None
+    if w.name == wl.SINKHORN_DOUBLE_T4096.name and not tc_path:
+        traffic = PAIRS_TRAFFIC_BYTES
+    elif w.name == wl.SINKHORN_UNICYCLE_T65536.name and tc_path:
+        traffic = TC_LARGE_TRAFFIC_BYTES
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -479,15 +490,17 @@ def run_ours(args):
                 "l2": "flushed between steps (256 MiB write outside the per-step CUDA events)",
                 "ms_per_coverage_solve": ms_per_step * w.n_outer,
                 "tiling": tiling,
-                "exponents": "tensor cores (tcgen05 kind::tf32)" if args.tensor_cores else "CUDA cores (FP32 FMA)",
+                "exponents": "tensor cores (tcgen05 kind::tf32)" if tc_path else "CUDA cores (FP32 FMA)",
                 "wall_s_timed_region": wall}),
             "roofline": {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Gpair/s",
-                         "frac": achieved / peak, "traffic": None if args.tensor_cores else PAIRS_TRAFFIC_BYTES,
-                         "traffic_note": "dram__bytes_read.sum + dram__bytes_write.sum per launch of "
-                                         "pairs_kernel at this workload, one ncu capture of the current kernel",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "traffic_note": "dram__bytes_read.sum + dram__bytes_write.sum per launch of the "
+                                         "fixed-offset kernel at this workload, one ncu capture of the current "
+                                         "kernel (null where none was taken)",
                          "kernel": ("lse_tc_kernel (tcgen05 exponents) for the fixed-offset iterations, "
-                                    "pairs_kernel for the rest" if args.tensor_cores else
-                                    "pairs_kernel (Sinkhorn g/f/p soft-c-transform)") + ", per iteration of 3 launches",
+                                    "pairs_kernel for the rest" if tc_path else
+                                    "pairs_kernel (Sinkhorn g/f/p soft-c-transform)")
+                                   + ", per Sinkhorn iteration of 2 launches (g + p, f)",
                          "peak_basis": "derived: 148 SMs x 2032 MHz x min(MUFU ex2 width, 128 FP32 lanes / "
                                        f"{FP32_OPS_PER_PAIR} ops per pair)",
                          "peak_detail": peak_info, "probe": probe},
