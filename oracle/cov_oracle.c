@@ -105,7 +105,7 @@ void orc_gmm_score(const double* x, int T, int d, int K, const double* w,
 /* ------------------------------------------------------------------------
  * Stein variational gradient field, Eq. 4:
  *   g(x_i) = 1/T sum_j [ k(x_j, x_i) grad log q(x_j) + grad_{x_j} k(x_j, x_i) ]
- * Reading of "radial basis kernel": k(x, x') = exp(-|x - x'|^2 / (2 h^2)),
+ * Reading of the radial basis kernel: k(x, x') = exp(-|x - x'|^2 / (2 h^2)),
  * so grad_{x_j} k(x_j, x_i) = k(x_j, x_i) (x_i - x_j) / h^2.  The j = i term
  * is part of the sum.
  * ---------------------------------------------------------------------- */
