@@ -1,9 +1,11 @@
 #!/usr/bin/env python
 """Benchmark of the coverage hot path: one outer iteration (a "step") of the
-Sinkhorn coverage solve on the double-integrator workload -- T = 4096
-trajectory samples, M = 16384 reference samples from an 8-component
-Gaussian mixture, eps = 0.005, 50 log-domain Sinkhorn iterations per field,
-FP32 field + FP64 LQR/rollout -- through the C-ABI (cov_solve_continue).
+Sinkhorn coverage solve on the large unicycle workload -- T = 65536
+trajectory samples, M = 262144 reference samples from a 512 x 512 density
+map, eps = 0.002, 100 log-domain Sinkhorn iterations per field, FP32 field +
+FP64 LQR/rollout -- through the C-ABI (cov_solve_continue).  The
+double-integrator workload (T = 4096, M = 16384, 50 iterations) is measured
+beside it as a secondary figure.
 
 Prints ONE JSON line (rank 0).  `value` is pair evaluations per second over
 all ranks (one independent coverage problem per rank, weak scaling); one
@@ -38,7 +40,7 @@ from paper_2511_11514_b300 import workloads as wl  # noqa: E402
 
 METRIC = "pair-evals/s & ms per coverage solve (field % of FP32/SFU roofline) vs FP64 oracle"
 UNIT = "pair-evals/s"
-DEFAULT_WORKLOAD = wl.SINKHORN_DOUBLE_T4096.name
+DEFAULT_WORKLOAD = wl.SINKHORN_UNICYCLE_T65536.name
 L2_FLUSH_BYTES = 256 << 20
 # Algorithmic FP32-pipe instructions per Sinkhorn pair evaluation (base-2,
 # prescaled, column term folded) in the fixed-offset form the iteration runs
@@ -71,8 +73,8 @@ def parse_args():
     ap.add_argument("--no-tune", action="store_true", help="skip the tile-shape autotuner")
     ap.add_argument("--batched", type=int, default=0,
                     help="time cov_solve_batched on this many uneven problems (and the same problems one by one)")
-    ap.add_argument("--no-large-roofline", action="store_true",
-                    help="skip the all-pairs roofline at T = 65536, M = 262144")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="skip the secondary measurement of the other Sinkhorn workload")
     ap.add_argument("--adjoint", action="store_true",
                     help="time the differentiation workload: forward and backward through 20 outer iterations")
     ap.add_argument("--variants", action="store_true",
@@ -218,9 +220,15 @@ def calibrate(inst, seconds):
     return max(T, M), max(1, int(round(seconds / max(dt_two / 2, 1e-9))))
 
 
-def cpu_baseline(inst, seconds):
+def cpu_baseline(inst, seconds, single_thread_seconds=None):
+    """The FP64 oracle's pair-evaluation rate on a bounded sample of the
+    workload (rows of each Sinkhorn update, or whole iterations when they
+    fit), on all host cores and, for about a third of the time, on one
+    thread.  The rate is per pair evaluation, so it extrapolates to the whole
+    workload (the oracle's work per pair does not depend on the sample)."""
     import oracle as orc
-    orc.set_threads(os.cpu_count() or 1)
+    cores = os.cpu_count() or 1
+    orc.set_threads(cores)
     rows, iters = calibrate(inst, seconds)
     pairs, dt = oracle_sample(inst, rows, seed=1, iters=iters)
     # the host cores' speed varies between the calibration and the sample
@@ -232,9 +240,28 @@ def cpu_baseline(inst, seconds):
     T, M = inst.wl.T, inst.wl.M
     what = (f"{rows} rows of each Sinkhorn update" if iters == 1 else
             f"{iters} full Sinkhorn iterations (g over T={T}, f over M={M}, p over T)")
-    return {"value": pairs / dt, "unit": UNIT, "cores": orc.get_threads(), "kind": "oracle",
-            "sample": f"FP64 oracle: {what} of the workload from its initial trajectory, {pairs:.3e} pair "
-                      f"evaluations in {dt:.1f} s, {orc.get_threads()} threads"}
+    w = inst.wl
+    rate = pairs / dt
+    out = {"value": rate, "unit": UNIT, "cores": orc.get_threads(), "kind": "oracle",
+           "sample": f"FP64 oracle: {what} of the workload from its initial trajectory, {pairs:.3e} pair "
+                     f"evaluations in {dt:.1f} s, {orc.get_threads()} threads",
+           "extrapolated": {"ms_per_step": w.pairs_per_field / rate * 1e3,
+                            "ms_per_coverage_solve": w.n_outer * w.pairs_per_field / rate * 1e3,
+                            "how": "the sample's pair rate applied to the whole step / solve"}}
+    st = seconds / 3 if single_thread_seconds is None else single_thread_seconds
+    if st > 0:
+        orc.set_threads(1)
+        try:
+            p1, d1 = oracle_sample(inst, 16)
+            r1 = max(16, min(min(T, M), int(16 * st / max(d1, 1e-9))))
+            p1, d1 = oracle_sample(inst, r1, seed=3)
+        finally:
+            orc.set_threads(cores)
+        out["single_thread"] = {"value": p1 / d1, "unit": UNIT, "cores": 1,
+                                "sample": f"{r1} rows of each Sinkhorn update, {p1:.3e} pair evaluations in "
+                                          f"{d1:.1f} s, 1 thread",
+                                "ms_per_step_extrapolated": w.pairs_per_field / (p1 / d1) * 1e3}
+    return out
 
 
 def workload_config(w, extra=None):
@@ -275,7 +302,8 @@ def run_reference(args):
             "warmup": args.warmup, "ms_per_step": 1000.0 * tot_s / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded Philox)",
             "impl": "reference",
-            "config": workload_config(w, {"sample_rows_per_update": rows, "sample_iterations": iters}),
+            "config": workload_config(w, {"sample_rows_per_update": rows, "sample_iterations": iters,
+                                          "precision": "f64 throughout (the oracle)"}),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": orc.get_threads(), "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -284,18 +312,86 @@ def run_reference(args):
 
 
 # -- our arm ------------------------------------------------------------------------
-def alu_peak(probe, num_sms):
-    """ALU roofline in pair evaluations/s at the maximum SM clock: min of the
-    MUFU ex2 rate (one exponential per pair) and the FP32 lane rate divided
-    by the algorithmic FP32 ops per pair.  The per-SM per-clock MUFU width is
-    read from the probe (rounded to a power of two)."""
+def sinkhorn_iteration_ms(cov, ctx, x, y, eps, n_lo, n_hi, reps, flush, stream):
+    """Time of one fixed-offset Sinkhorn iteration (two all-pairs launches:
+    g + p, then f) on the context's current exponent path, with CUDA events
+    on the launching stream: the median over `reps` of
+    (t(n_hi iterations) - t(n_lo)) / (n_hi - n_lo), so that the prep, the
+    first (running-maximum) iteration and the finish cancel."""
+    import torch
+
+    def field_ms(n):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        cov.cov_field_sinkhorn(ctx, x, y, eps, n, field=False)
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b)
+
+    cov.cov_field_sinkhorn(ctx, x, y, eps, 1, field=False)
+    return statistics.median((field_ms(n_hi) - field_ms(n_lo)) / (n_hi - n_lo) for _ in range(reps))
+
+
+def time_steps(cov, ctx, prob, u, s, steps, flush, stream):
+    """Per-step CUDA-event times (ms) of `steps` outer iterations through
+    cov_solve_continue, the L2 flushed between steps outside the events."""
+    import torch
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    for k in range(steps):
+        flush.zero_()
+        ev0[k].record(stream)
+        cov.cov_solve_continue(ctx, prob, 1, u, s)
+        ev1[k].record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
+
+
+def sinkhorn_setup(cov, ctx, w, dev, seed, tune):
+    """Instance, device inputs, problem, controls and initial rollout of a
+    Sinkhorn workload; the autotuned tile shape applied to ctx when `tune`."""
+    import torch
+    inst = wl.make_instance(w, seed=seed)
+    y = torch.as_tensor(inst.y, dtype=torch.float32, device=dev).contiguous()
+    prob = cov.make_problem(w.model, w.T, w.dt, inst.s0, w.field, inst.Q, inst.R, w.eta, y=y, eps=w.eps,
+                            n_iter=w.n_iter)
+    u = torch.as_tensor(inst.u0, dtype=torch.float64, device=dev).contiguous()
+    s = cov.cov_solve(ctx, prob, 0, u)  # trajectory of the initial controls
+    tiling = {"R": ctx.option(cov.OPT_ROWS_PER_THREAD, 4), "ctas_per_sm": ctx.option(cov.OPT_CTAS_PER_SM, 8),
+              "source": "default"}
+    if tune:
+        from paper_2511_11514_b300 import autotune
+        ch = autotune.tune_sinkhorn(ctx, s[1:, :2].float().contiguous(), y, w.eps)
+        tiling = {"R": ch["R"], "ctas_per_sm": ch["ctas_per_sm"], "source": "autotune (before the timed region)"}
+    return inst, y, prob, u, s, tiling
+
+
+def uses_tensor_cores(w, forced):
+    """The exponent path the default setting takes: the tensor cores when
+    both launches of a Sinkhorn iteration hold at least 2^30 pairs."""
+    return forced or min(w.M * w.T + w.T * w.T, w.T * w.M) >= 2 ** 30
+
+
+def roofline_peaks(probe, num_sms):
+    """ALU roofline in pair evaluations/s at the maximum SM clock on two
+    bases: (a) the log-sum-exp with a running maximum, 5 FP32-pipe operations
+    and one exponential per pair, min(128 FP32 lanes / 5, MUFU ex2 width) per
+    SM and clock; (b) the fixed-row-offset form the iterations 2.. run in,
+    4 FP32 operations and one exponential, min(128 / 4, MUFU width).  The
+    MUFU ex2 width per SM and clock is read from the probe (rounded to a
+    power of two)."""
     clk = probe["sm_clock_mhz"] * 1e6
     ex2_per_sm_clk = probe["ex2_lane_ops_s"] / (num_sms * clk)
     width = 2 ** round(np.log2(max(ex2_per_sm_clk, 1.0)))
-    mufu = SM_COUNT_NOMINAL * width * SM_MAX_MHZ_NOMINAL * 1e6
-    fp32 = SM_COUNT_NOMINAL * FP32_LANES_PER_SM_CLK * SM_MAX_MHZ_NOMINAL * 1e6 / FP32_OPS_PER_PAIR
-    return min(mufu, fp32), {"mufu_ex2_per_sm_clk": width, "mufu_pairs_s": mufu, "fp32_pairs_s": fp32,
-                             "probe_ex2_per_sm_clk_measured": ex2_per_sm_clk}
+    base = SM_COUNT_NOMINAL * SM_MAX_MHZ_NOMINAL * 1e6
+    mufu = base * width
+    fp32_5 = base * FP32_LANES_PER_SM_CLK / 5
+    fp32_4 = base * FP32_LANES_PER_SM_CLK / FP32_OPS_PER_PAIR
+    return min(fp32_5, mufu), min(fp32_4, mufu), {
+        "mufu_ex2_per_sm_clk": width, "mufu_pairs_s": mufu, "fp32_pairs_s_5_ops": fp32_5,
+        "fp32_pairs_s_4_ops": fp32_4, "probe_ex2_per_sm_clk_measured": ex2_per_sm_clk}
 
 
 def run_ours(args):
@@ -311,28 +407,16 @@ def run_ours(args):
     w = wl.WORKLOADS[args.workload]
     if w.field != wl.FIELD_SINKHORN:
         return run_svgd(args, w, rank, local_rank, world)
-    inst = wl.make_instance(w, seed=w.seed + rank)
     ctx = cov.Context(local_rank)
     if args.tensor_cores:
         ctx.set_option(cov.OPT_TENSOR_CORES, cov.TENSOR_CORES_ON)
     dev = torch.device("cuda", local_rank)
-    y = torch.as_tensor(inst.y, dtype=torch.float32, device=dev).contiguous()
-    prob = cov.make_problem(w.model, w.T, w.dt, inst.s0, w.field, inst.Q, inst.R, w.eta, y=y, eps=w.eps,
-                            n_iter=w.n_iter)
-    u = torch.as_tensor(inst.u0, dtype=torch.float64, device=dev).contiguous()
-    s = cov.cov_solve(ctx, prob, 0, u)  # trajectory of the initial controls
-    tiling = {"R": 4, "ctas_per_sm": 8, "source": "default"}
-    if not args.no_tune:
-        from paper_2511_11514_b300 import autotune
-        ch = autotune.tune_sinkhorn(ctx, s[1:, :2].float().contiguous(), y, w.eps)
-        tiling = {"R": ch["R"], "ctas_per_sm": ch["ctas_per_sm"], "source": "autotune (before the timed region)"}
+    inst, y, prob, u, s, tiling = sinkhorn_setup(cov, ctx, w, dev, w.seed + rank, not args.no_tune)
     stream = torch.cuda.current_stream()
     for _ in range(max(3, args.warmup)):
         cov.cov_solve_continue(ctx, prob, 1, u, s)
     torch.cuda.synchronize()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     clocks = Clocks(local_rank)
     if world > 1:
         dist.barrier()
@@ -341,18 +425,12 @@ def run_ours(args):
     time.sleep(0.2)
     torch.cuda.profiler.start()  # a profiler started with --profile-from-start off sees the timed steps only
     t0 = time.perf_counter()
-    for k in range(args.steps):
-        flush.zero_()  # L2 flush between steps (outside the step events)
-        ev0[k].record(stream)
-        cov.cov_solve_continue(ctx, prob, 1, u, s)
-        ev1[k].record(stream)
-    torch.cuda.synchronize()
+    step_ms = time_steps(cov, ctx, prob, u, s, args.steps, flush, stream)
     torch.cuda.profiler.stop()
     if world > 1:
         dist.barrier()
     wall = time.perf_counter() - t0
     clk = clocks.stop()
-    step_ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
     total_ms = max_over_ranks(sum(step_ms), world, dev)
     st, flags = ctx.device_status()
     if st != cov.COV_OK:
@@ -360,100 +438,87 @@ def run_ours(args):
     pairs_step = w.pairs_per_field
     value = job_value(world, pairs_step, args.steps, total_ms)
     ms_per_step = total_ms / args.steps
+    tc_path = uses_tensor_cores(w, args.tensor_cores)
 
-    # ---- roofline of the dominant kernel (the all-pairs soft-c-transform) -------
+    # ---- roofline of the dominant kernel: the Sinkhorn iteration's two
+    # all-pairs launches on the path the default setting takes, right after
+    # the timed region on the same inputs and stream ----------------------------
+    large = w.T * w.M >= 1 << 30
+    n_lo, n_hi, reps = (3, 5, 3) if large else (4, 24, 5)
     x = s[1:, :2].float().contiguous()
-    n_lo, n_hi = 4, 24
-
-    def field_ms(n_iter, reps=5):
-        ts = []
-        for _ in range(reps):
-            flush.zero_()
-            a = torch.cuda.Event(enable_timing=True)
-            b = torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            cov.cov_field_sinkhorn(ctx, x, y, w.eps, n_iter, field=False)
-            b.record(stream)
-            torch.cuda.synchronize()
-            ts.append(a.elapsed_time(b))
-        return statistics.median(ts)
-
-    t_iter_ms = (field_ms(n_hi) - field_ms(n_lo)) / (n_hi - n_lo)
+    t_iter_ms = sinkhorn_iteration_ms(cov, ctx, x, y, w.eps, n_lo, n_hi, reps, flush, stream)
+    other_mode = cov.TENSOR_CORES_OFF if tc_path else cov.TENSOR_CORES_ON
+    ctx.set_option(cov.OPT_TENSOR_CORES, other_mode)
+    t_other_ms = sinkhorn_iteration_ms(cov, ctx, x, y, w.eps, n_lo, n_hi, reps, flush, stream)
+    ctx.set_option(cov.OPT_TENSOR_CORES, cov.TENSOR_CORES_ON if args.tensor_cores else cov.TENSOR_CORES_AUTO)
+    if not args.no_tune:
+        from paper_2511_11514_b300 import autotune
+        autotune.apply(ctx, {"R": tiling["R"], "ctas_per_sm": tiling["ctas_per_sm"]})
     pairs_iter = 2 * w.T * w.M + w.T * w.T
     achieved = pairs_iter / (t_iter_ms * 1e-3)
     probe = cov.cov_probe_peaks(ctx, 4096)
-    peak, peak_info = alu_peak(probe, torch.cuda.get_device_properties(dev).multi_processor_count)
+    peak, peak_fixed, peak_info = roofline_peaks(probe, torch.cuda.get_device_properties(dev).multi_processor_count)
+    traffic = None
+    if w.name == wl.SINKHORN_DOUBLE_T4096.name and not tc_path:
+        traffic = PAIRS_TRAFFIC_BYTES
+    elif w.name == wl.SINKHORN_UNICYCLE_T65536.name and tc_path:
+        traffic = TC_LARGE_TRAFFIC_BYTES
 
-    # the same kernel at the large workload (T = 65536, M = 262144), where the
-    # per-launch fixed costs are amortised: (t(5 iterations) - t(3)) / 2
-    big = None
-    if rank == 0 and not args.no_large_roofline:
-        wb = wl.SINKHORN_UNICYCLE_T65536
-        ib = wl.make_instance(wb)
-        ub = torch.as_tensor(ib.u0, dtype=torch.float64, device=dev)
-        xb = cov.cov_rollout(ctx, wb.model, ib.s0, ub, wb.dt)[1:, :2].float().contiguous()
-        yb = torch.as_tensor(ib.y, dtype=torch.float32, device=dev).contiguous()
+    # ---- the LQR step of this workload (linearisation at the current
+    # trajectory, parallel-in-time Riccati + the two affine scans) ---------------
+    A, B = cov.cov_linearize(ctx, w.model, s, u, w.dt)
+    abar = torch.zeros((w.T, A.shape[1]), dtype=torch.float64, device=dev)
+    abar[:, :2] = 0.05
+    cov.cov_lqr_track(ctx, A, B, inst.Q, inst.R, abar)
+    la, lb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    la.record(stream)
+    for _ in range(5):
+        cov.cov_lqr_track(ctx, A, B, inst.Q, inst.R, abar)
+    lb.record(stream)
+    torch.cuda.synchronize()
+    lqr_ms = la.elapsed_time(lb) / 5
+    del A, B, abar
+
+    # ---- one whole coverage solve from the initial controls on a context of
+    # its own (workspace reserved before the clock starts): initial rollout,
+    # Riccati gains of a time-invariant model, graph capture, every outer
+    # iteration -------------------------------------------------------------------
+    solve = None
+    if rank == 0:
+        c2 = cov.Context(local_rank)
+        n, m = wl.MODEL_DIMS[w.model]
+        c2.reserve_for(w.T, w.M, 2, n, m)
         if not args.no_tune:
             from paper_2511_11514_b300 import autotune
-            chb = autotune.tune_sinkhorn(ctx, xb, yb, wb.eps)  # tunes the CUDA-core path
-        cov.cov_field_sinkhorn(ctx, xb, yb, wb.eps, 1, field=False)
-
-        def big_ms(n):
-            a = torch.cuda.Event(enable_timing=True)
-            b = torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            cov.cov_field_sinkhorn(ctx, xb, yb, wb.eps, n, field=False)
-            b.record(stream)
-            torch.cuda.synchronize()
-            return a.elapsed_time(b)
-
-        # iterations 4 and 5 (the fixed-offset form, which all but the first
-        # run in), once with the exponents on the CUDA cores and once on the
-        # tensor cores, median of three; the default setting takes the tensor
-        # cores at this size (launches of >= 2^30 pairs)
-        def iteration_ms(mode):
-            ctx.set_option(cov.OPT_TENSOR_CORES, mode)
-            cov.cov_field_sinkhorn(ctx, xb, yb, wb.eps, 1, field=False)
-            return statistics.median((big_ms(5) - big_ms(3)) / 2 for _ in range(3))
-
-        tb = iteration_ms(cov.TENSOR_CORES_OFF)
-        tb_tc = iteration_ms(cov.TENSOR_CORES_ON)
-        ctx.set_option(cov.OPT_TENSOR_CORES, cov.TENSOR_CORES_ON if args.tensor_cores else cov.TENSOR_CORES_AUTO)
-        ach_b = (2 * wb.T * wb.M + wb.T * wb.T) / (tb * 1e-3)
-        ach_tc = (2 * wb.T * wb.M + wb.T * wb.T) / (tb_tc * 1e-3)
-        big_tc = min(wb.M * wb.T + wb.T * wb.T, wb.T * wb.M) >= 2 ** 30 or args.tensor_cores
-        # the LQR step of that workload (time-varying unicycle linearisation:
-        # parallel-in-time Riccati + the two affine scans), CUDA events
-        sbig = cov.cov_rollout(ctx, wb.model, ib.s0, ub, wb.dt)
-        Ab, Bb = cov.cov_linearize(ctx, wb.model, sbig, ub, wb.dt)
-        abar_b = torch.zeros((wb.T, Ab.shape[1]), dtype=torch.float64, device=dev)
-        abar_b[:, :2] = 0.05
-        cov.cov_lqr_track(ctx, Ab, Bb, ib.Q, ib.R, abar_b)
-        la = torch.cuda.Event(enable_timing=True)
-        lb = torch.cuda.Event(enable_timing=True)
-        la.record(stream)
-        for _ in range(3):
-            cov.cov_lqr_track(ctx, Ab, Bb, ib.Q, ib.R, abar_b)
-        lb.record(stream)
+            autotune.apply(c2, {"R": tiling["R"], "ctas_per_sm": tiling["ctas_per_sm"]})
+        if args.tensor_cores:
+            c2.set_option(cov.OPT_TENSOR_CORES, cov.TENSOR_CORES_ON)
+        u2 = torch.as_tensor(inst.u0, dtype=torch.float64, device=dev).contiguous()
+        s2 = torch.empty_like(s)
         torch.cuda.synchronize()
-        main_ach, main_ms = (ach_tc, tb_tc) if big_tc else (ach_b, tb)
-        big = {"bound": "alu", "achieved": main_ach / 1e9, "peak": peak / 1e9, "unit": "Gpair/s",
-               "frac": main_ach / peak, "traffic": None, "workload": wb.name, "ms_per_sinkhorn_iteration": main_ms,
-               "kernel": "lse_tc_kernel (tcgen05 exponents; the default at this size)" if big_tc else "pairs_kernel",
-               "lqr_track_ms": la.elapsed_time(lb) / 3}
-        other = ("cuda_core_path", ach_b, tb) if big_tc else ("tensor_core_path", ach_tc, tb_tc)
-        big[other[0]] = {"achieved": other[1] / 1e9, "frac": other[1] / peak, "ms_per_sinkhorn_iteration": other[2]}
-        if not args.no_tune:
-            apply_choice = {"R": tiling["R"], "ctas_per_sm": tiling["ctas_per_sm"]}
-            autotune.apply(ctx, apply_choice)
+        sa, sb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        h0 = time.perf_counter()
+        sa.record(stream)
+        cov.cov_solve(c2, prob, w.n_outer, u2, s2)
+        sb.record(stream)
+        torch.cuda.synchronize()
+        solve = {"outer_iterations": w.n_outer, "ms": sa.elapsed_time(sb),
+                 "host_wall_ms": (time.perf_counter() - h0) * 1e3,
+                 "how": "cov_solve from the initial controls on a fresh context (workspace reserved beforehand): "
+                        "initial rollout, graph capture, every outer iteration; CUDA events on the stream"}
+        st2, fl2 = c2.device_status()
+        c2.close()
+        if st2 != cov.COV_OK:
+            raise SystemExit(f"device status {cov.status_string(st2)} flags {fl2}")
 
     # ---- end to end through the C-ABI with host buffers ---------------------------
     u_h = torch.as_tensor(inst.u0, dtype=torch.float64).pin_memory()
     y_h = torch.as_tensor(inst.y, dtype=torch.float32).pin_memory()
     u_out = torch.empty_like(u_h).pin_memory()
     s_out = torch.empty((w.T + 1, s.shape[1]), dtype=torch.float64).pin_memory()
+    e2e_steps = max(3, min(args.e2e_steps, int(8000.0 / max(ms_per_step, 1e-3))))
     e_ms = []
-    for k in range(args.e2e_steps + 2):
+    for k in range(e2e_steps + 2):
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
         flush.zero_()
@@ -472,42 +537,79 @@ def run_ours(args):
     d2h = u_out.numel() * 8 + s_out.numel() * 8
 
     launches_per_step = count_library_launches(lambda: cov.cov_solve_continue(ctx, prob, 1, u, s))
-    # the exponent path the default setting takes (launches of >= 2^30 pairs
-    # on the tensor cores) and the DRAM traffic captured for it, where known
-    tc_path = args.tensor_cores or min(w.M * w.T + w.T * w.T, w.T * w.M) >= 2 ** 30
-    traffic = None
-    if w.name == wl.SINKHORN_DOUBLE_T4096.name and not tc_path:
-        traffic = PAIRS_TRAFFIC_BYTES
-    elif w.name == wl.SINKHORN_UNICYCLE_T65536.name and tc_path:
-        traffic = TC_LARGE_TRAFFIC_BYTES
+
+    # ---- the other Sinkhorn workload, as a secondary figure (rank 0) --------------
+    secondary = None
+    if rank == 0 and not args.no_secondary:
+        w2 = (wl.SINKHORN_DOUBLE_T4096 if w.name == wl.SINKHORN_UNICYCLE_T65536.name
+              else wl.SINKHORN_UNICYCLE_T65536)
+        c3 = cov.Context(local_rank)
+        if args.tensor_cores:
+            c3.set_option(cov.OPT_TENSOR_CORES, cov.TENSOR_CORES_ON)
+        inst2, y2, prob2, u3, s3, tiling2 = sinkhorn_setup(cov, c3, w2, dev, w2.seed, not args.no_tune)
+        for _ in range(3):
+            cov.cov_solve_continue(c3, prob2, 1, u3, s3)
+        k2 = 20 if w2.T * w2.M < 1 << 30 else 3
+        ms2 = time_steps(cov, c3, prob2, u3, s3, k2, flush, stream)
+        large2 = w2.T * w2.M >= 1 << 30
+        lo2, hi2, reps2 = (3, 5, 3) if large2 else (4, 24, 5)
+        x3 = s3[1:, :2].float().contiguous()
+        ti2 = sinkhorn_iteration_ms(cov, c3, x3, y2, w2.eps, lo2, hi2, reps2, flush, stream)
+        ach2 = (2 * w2.T * w2.M + w2.T * w2.T) / (ti2 * 1e-3)
+        tc2 = uses_tensor_cores(w2, args.tensor_cores)
+        secondary = {"workload": w2.name, "T": w2.T, "M": w2.M, "eps": w2.eps, "n_iter": w2.n_iter,
+                     "steps": k2, "ms_per_step": statistics.mean(ms2),
+                     "value": w2.pairs_per_field / (statistics.mean(ms2) * 1e-3), "unit": UNIT,
+                     "tiling": tiling2,
+                     "roofline": {"achieved": ach2 / 1e9, "unit": "Gpair/s", "frac": ach2 / peak,
+                                  "frac_fixed_offset_basis": ach2 / peak_fixed,
+                                  "ms_per_sinkhorn_iteration": ti2,
+                                  "kernel": "lse_tc_kernel" if tc2 else "pairs_kernel"}}
+        st3, fl3 = c3.device_status()
+        c3.close()
+        if st3 != cov.COV_OK:
+            raise SystemExit(f"device status {cov.status_string(st3)} flags {fl3}")
+
     if rank == 0:
+        kernel = ("lse_tc_kernel (tcgen05 exponents) for the fixed-offset iterations, pairs_kernel for the rest"
+                  if tc_path else "pairs_kernel (Sinkhorn g/f/p soft-c-transform)")
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded Philox Gaussian-mixture reference)",
+            "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded Philox; " + ("density-map samples)" if w.reference == "density" else
+                                                   "Gaussian-mixture samples)"),
             "config": workload_config(w, {
                 "parallelism": f"{world} independent problems (one per GPU)" if world > 1 else "single GPU",
                 "l2": "flushed between steps (256 MiB write outside the per-step CUDA events)",
-                "ms_per_coverage_solve": ms_per_step * w.n_outer,
+                "ms_per_coverage_solve": solve["ms"] if solve else None,
+                "coverage_solve": solve,
+                "lqr_track_ms": lqr_ms,
                 "tiling": tiling,
                 "exponents": "tensor cores (tcgen05 kind::tf32)" if tc_path else "CUDA cores (FP32 FMA)",
                 "wall_s_timed_region": wall}),
             "roofline": {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Gpair/s",
                          "frac": achieved / peak, "traffic": traffic,
+                         "frac_fixed_offset_basis": achieved / peak_fixed,
+                         "peak_fixed_offset_basis": peak_fixed / 1e9,
+                         "ms_per_sinkhorn_iteration": t_iter_ms,
+                         "other_exponent_path": {
+                             "path": "CUDA cores (pairs_kernel)" if tc_path else "tensor cores (lse_tc_kernel)",
+                             "ms_per_sinkhorn_iteration": t_other_ms,
+                             "frac": pairs_iter / (t_other_ms * 1e-3) / peak},
                          "traffic_note": "dram__bytes_read.sum + dram__bytes_write.sum per launch of the "
                                          "fixed-offset kernel at this workload, one ncu capture of the current "
                                          "kernel (null where none was taken)",
-                         "kernel": ("lse_tc_kernel (tcgen05 exponents) for the fixed-offset iterations, "
-                                    "pairs_kernel for the rest" if tc_path else
-                                    "pairs_kernel (Sinkhorn g/f/p soft-c-transform)")
-                                   + ", per Sinkhorn iteration of 2 launches (g + p, f)",
-                         "peak_basis": "derived: 148 SMs x 2032 MHz x min(MUFU ex2 width, 128 FP32 lanes / "
-                                       f"{FP32_OPS_PER_PAIR} ops per pair)",
+                         "kernel": kernel + ", per Sinkhorn iteration of 2 launches (g + p, f), "
+                                   f"(t({n_hi} iterations) - t({n_lo})) / {n_hi - n_lo}, median of {reps}",
+                         "peak_basis": "148 SMs x 2032 MHz x min(MUFU ex2 width, 128 FP32 lanes / 5 operations "
+                                       "per pair of the log-sum-exp with a running maximum); "
+                                       "peak_fixed_offset_basis: / 4 operations of the fixed-offset form",
                          "peak_detail": peak_info, "probe": probe},
-            "roofline_large": big,
+            "secondary": secondary,
             "clocks": clk,
             "e2e": {"value": pairs_step / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+                    "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms, "steps": e2e_steps},
             "gpu_launches": launches_per_step * args.steps,
         }
         if world == 1 and not args.no_cpu_baseline:
@@ -751,7 +853,7 @@ def run_adjoint(args):
     y_loss = torch.as_tensor(wl.f32_pair(wl.gmm_samples(lw, lmu, lsig, w.extra["loss_M"], w.extra["loss_seed"] + 1000))[1],
                              dtype=torch.float32, device=dev)
     eps_l, it_l = w.extra["loss_eps"], w.extra["loss_iters"]
-    q_ref = ag.reference_self_term(lctx, y_loss, eps_l, it_l)
+    q_ref = ag.reference_self_potential(lctx, y_loss, eps_l, it_l)
     spec = dict(model=w.model, dt=w.dt, Q=inst.Q, R=inst.R, eta=w.eta, eps=w.eps, n_iter=w.n_iter,
                 n_outer=w.n_outer)
 

@@ -209,6 +209,34 @@ COV_API cov_status cov_field_sinkhorn(cov_ctx* ctx, const float* x, int T,
                               float* g, float* p, float* a_out,
                               cov_stream_t stream);
 
+/* Debiased Sinkhorn divergence of Eq. 6 after n_iter fixed iterations,
+ * as its dual value, and its gradient with respect to the samples x:
+ *   S = OT(p_s, q) - OT(p_s, p_s)/2 - OT(q, q)/2
+ *     = <a, f> + <b, g> - <a, p> - <b, q_self>,
+ * with f, g, p the potentials of cov_field_sinkhorn (cold start, n_iter
+ * iterations) and q_self the reference's self potential after n_iter
+ * averaged self updates over y; the sums run in FP64.  The gradient is the
+ * envelope formula dS/dx_i = -(1/T) field_i (field of Eq. 7, exact at
+ * convergence; at finite n_iter it is the gradient through the final
+ * potentials held fixed).
+ *   x [T][d], y [M][d] FP32 device;  b [M] FP32 device weights or NULL
+ *   q_ref [M] FP32 device: with q_given = 1 the reference self potential
+ *          of an earlier call on the same y, eps, n_iter (read, not
+ *          recomputed: OT(q, q) does not depend on x); with q_given = 0 it
+ *          is computed (an M x M self iteration) and written to q_ref, or
+ *          kept in the workspace when q_ref is NULL
+ *   value [1] FP64 device, written;  grad [T][d] FP32 device or NULL
+ * Workspace: cov_workspace_size_divergence(T, M, d).  Errors as
+ * cov_field_sinkhorn; COV_ERR_INVALID_ARG for q_given without q_ref or a
+ * NULL value; COV_ERR_UNSUPPORTED for q_given = 0 with weights b (the self
+ * potential of a weighted reference is not built: pass it in). */
+COV_API size_t cov_workspace_size_divergence(int T, int M, int d);
+COV_API cov_status cov_sinkhorn_divergence(cov_ctx* ctx, const float* x, int T,
+                                           const float* y, const float* b, int M,
+                                           int d, float eps, int n_iter, float* q_ref,
+                                           int q_given, double* value, float* grad,
+                                           cov_stream_t stream);
+
 /* The same field with eps-scaling (annealing, a standard acceleration of
  * Sinkhorn at small eps; not in the paper): iteration t = 0..n_iter-1 runs
  * the three updates at eps_t = max(eps, eps_start eps_decay^t), carrying
@@ -225,22 +253,24 @@ COV_API cov_status cov_field_sinkhorn_annealed(cov_ctx* ctx, const float* x, int
                                                cov_stream_t stream);
 
 /* The same field for callers that must not allocate device memory.  The
- * paper has no counterpart: this is a library convenience.  Programs that
- * cannot call cudaMalloc -- code running while a CUDA graph is captured,
- * plugins whose host hands out all device memory from its own arena,
- * real-time loops that cannot take the device synchronisation of
- * cudaMalloc/cudaFree -- get the scratch from one fixed 32 MiB array
- * compiled into the library (held on every GPU that loads it, until the
- * process exits) instead of a context workspace.  No context is needed and
- * nothing is allocated; the caller still passes x, y, b, f, g, p and a_out
- * exactly as for cov_field_sinkhorn, with the same meaning, and the results
- * are those of cov_field_sinkhorn with default options.
+ * paper has no counterpart: this is a library convenience.  Some programs
+ * cannot call cudaMalloc: plugins whose host application owns every device
+ * byte and hands it out from its own arena, or real-time loops that cannot
+ * take the device-wide synchronisation that cudaMalloc/cudaFree imply.  This
+ * entry point takes its scratch from one fixed 48 MiB array compiled into
+ * the library (held on every GPU that loads it, until the process exits)
+ * instead of a context workspace.  No context is needed and nothing is
+ * allocated; the caller still passes x, y, b, f, g, p and a_out exactly as
+ * for cov_field_sinkhorn, with the same meaning, and the results are those
+ * of cov_field_sinkhorn with default options.
  *   - The first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress) with that device current; make that first call
  *     before any stream capture begins.  Later calls use the cached address.
- *   - Sizes whose scratch exceeds the array are rejected with
- *     COV_ERR_WORKSPACE before anything is launched (d = 2 fits up to about
- *     T = 65536 with M = 262144).
+ *   - A call needs at most cov_workspace_size(T, M, d, 0, 0) bytes of the
+ *     array; sizes whose scratch exceeds it are rejected with
+ *     COV_ERR_WORKSPACE before anything is launched.  T = 65536 with
+ *     M = 262144 fits at every d from 1 to COV_MAX_D (47.2 MiB at d = 6);
+ *     at T = 65536 and d = 2, M up to 347136 fits.
  *   - Every call reuses the same array; the call clears what must start at
  *     zero on `stream` itself.  Calls that overlap on the GPU (different
  *     streams, or several host threads) race on the array: serialise them.
@@ -273,7 +303,9 @@ COV_API cov_status cov_rollout(cov_ctx* ctx, int model, const double* s0,
  * grid; the common dt weight cancels):
  *   min_v sum_{t=1..T} |z_t - abar_t|_Q^2 + sum_{t=0..T-1} |v_t|_R^2,
  *   z_{t+1} = A_t z_t + B_t v_t, z_0 = 0,
- * by the backward Riccati recursion and a forward rollout, in FP64, one warp.
+ * by the backward Riccati recursion and a forward rollout, in FP64, both as
+ * parallel-in-time scans over chunks of the horizon (horizons under 64 steps
+ * run the serial recursion in one warp).
  *   A [T][n][n], B [T][n][m]  FP64 device
  *   Q [n][n] (PSD), R [m][m] (SPD)  FP64 HOST
  *   abar [T][n] FP64 device: row t-1 holds the target at time t = 1..T

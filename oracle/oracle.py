@@ -268,6 +268,18 @@ def sinkhorn_divergence(x, y, b, eps, tol=1e-10, max_iter=100000) -> float:
                                                float(tol), int(max_iter)))
 
 
+def sinkhorn_divergence_iter(x, y, eps, n_iter) -> float:
+    """Debiased Sinkhorn divergence of Eq. 6 as the dual value after n_iter
+    cold-start iterations, uniform weights on both sets:
+        S = <a, f> + <b, g> - <a, p> - <b, q>
+    with f, g, p the potentials of sinkhorn(x, y, None, eps, n_iter) and q the
+    self potential of y after n_iter averaged self updates (the p output of
+    the same iteration run on y against itself)."""
+    f, g, p = sinkhorn(x, y, None, eps, n_iter)
+    q = sinkhorn(y, y, None, eps, n_iter)[2]
+    return float(np.mean(f) + np.mean(g) - np.mean(p) - np.mean(q))
+
+
 # -- dynamics, linearisation, rollout (Eq. 3, 8) ---------------------------
 def step(model, s, u, dt):
     s, u = _f64(s), _f64(u)

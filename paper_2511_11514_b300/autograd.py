@@ -13,10 +13,10 @@ forward and backward arithmetic runs in libcov's kernels):
   samples x and a held-out reference set (uniform weights).  Give it a
   context of its own: a field call on the solve's context overwrites the
   time-invariant Riccati gains that cov_solve caches in its workspace (they
-  are then recomputed, a serial FP64 pass).  Its value is the
+  are then recomputed).  ``cov_sinkhorn_divergence`` computes the value, the
   dual value <a, f> + <b, g> - <a, p> - <b, q> at the potentials after
-  n_iter iterations; its gradient is the envelope formula -(1/T) times the
-  field of Eq. 7 at those potentials (exact at convergence).
+  n_iter iterations, and the gradient, the envelope formula -(1/T) times
+  the field of Eq. 7 at those potentials (exact at convergence).
 * ``gmm_reference``: reference samples and weights of a Gaussian mixture by
   reparameterisation, y_j = mu_c + sigma_c xi_j (M/K fixed standard normal
   draws per component c) and b_j = softmax(logits)_c / (M/K), in plain torch
@@ -71,27 +71,30 @@ class CoverageSolve(torch.autograd.Function):
 
 class SinkhornLoss(torch.autograd.Function):
     """L = SinkhornLoss.apply(x, y_ref, eps, n_iter, cctx, q_ref): S_eps of the
-    uniform sample sets x [T, d] and y_ref [M, d] (float32 CUDA); q_ref is
-    <1/M, q> of the reference's own self potential (see ``reference_self_term``)."""
+    uniform sample sets x [T, d] and y_ref [M, d] (float32 CUDA), computed by
+    ``cov_sinkhorn_divergence`` (value and gradient in the library); q_ref is
+    the reference's self potential from ``reference_self_potential`` (or
+    None: recomputed by every call)."""
 
     @staticmethod
-    def forward(fctx, x, y_ref, eps, n_iter, cctx, q_ref):
-        a, f, g, p = cov.cov_field_sinkhorn(cctx, x.detach().contiguous(), y_ref, eps, n_iter)
-        fctx.save_for_backward(a)
-        fctx.T = x.shape[0]
-        L = f.double().mean() + g.double().mean() - p.double().mean() - q_ref
-        return L
+    def forward(fctx, x, y_ref, eps, n_iter, cctx, q_ref=None):
+        value, grad, _ = cov.cov_sinkhorn_divergence(cctx, x.detach().contiguous(), y_ref, eps, n_iter,
+                                                     q_ref=q_ref, q_given=q_ref is not None)
+        fctx.save_for_backward(grad)
+        return value
 
     @staticmethod
     def backward(fctx, gL):
-        (a,) = fctx.saved_tensors
-        return (-(gL.to(a.dtype)) * a / fctx.T, None, None, None, None, None)
+        (grad,) = fctx.saved_tensors
+        return (gL.to(grad.dtype) * grad, None, None, None, None, None)
 
 
-def reference_self_term(cctx, y_ref, eps, n_iter) -> float:
-    """<1/M, q> for the self potential q of the uniform set y_ref."""
+def reference_self_potential(cctx, y_ref, eps, n_iter):
+    """Self potential q [M] of the uniform set y_ref after n_iter averaged
+    self updates (the p output of a field evaluation of y_ref against
+    itself), for SinkhornLoss's q_ref."""
     _, _, _, q = cov.cov_field_sinkhorn(cctx, y_ref, y_ref, eps, n_iter, field=False)
-    return float(q.double().mean())
+    return q
 
 
 def gmm_reference(mu, log_sigma, logits, xi):

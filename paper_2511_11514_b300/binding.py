@@ -38,6 +38,7 @@ EXPORTS = (
     "cov_probe_peaks", "cov_workspace_size_vjp", "cov_field_sinkhorn_vjp", "cov_workspace_size_lqr_vjp",
     "cov_lqr_vjp", "cov_rollout_vjp", "cov_solve_checkpointed", "cov_workspace_size_backward",
     "cov_solve_backward", "cov_field_sinkhorn_annealed", "cov_density_score", "cov_autotune_sinkhorn",
+    "cov_workspace_size_divergence", "cov_sinkhorn_divergence",
 )
 
 
@@ -109,6 +110,8 @@ def load(path: str = LIB_PATH):
         "cov_solve_checkpointed": (_i, [_P, ctypes.POINTER(cov_problem), _i, _P, _P, _P, _i, _P]),
         "cov_workspace_size_backward": (_sz, [ctypes.POINTER(cov_problem), _i, _i]),
         "cov_solve_backward": (_i, [_P, ctypes.POINTER(cov_problem), _i, _P, _P, _P, _P, _P, _P, _P, _P]),
+        "cov_workspace_size_divergence": (_sz, [_i, _i, _i]),
+        "cov_sinkhorn_divergence": (_i, [_P, _P, _i, _P, _P, _i, _i, _f, _i, _P, _i, _P, _P, _P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -295,6 +298,36 @@ def cov_field_sinkhorn(ctx: Context, x, y, eps, n_iter, b=None, f=None, g=None, 
         _ptr(out, torch.float32, (T, d), "out") if field else None, _stream(stream))
     ctx._check(st, "cov_field_sinkhorn")
     return (out if field else None), f, g, p
+
+
+def cov_sinkhorn_divergence(ctx: Context, x, y, eps, n_iter, b=None, q_ref=None, q_given=False, grad=True,
+                            stream=None):
+    """Debiased Sinkhorn divergence of Eq. 6 after n_iter iterations (dual
+    value) and its gradient -(1/T) field with respect to x.  Returns
+    (value: 0-dim float64 CUDA tensor, grad [T, d] or None, q_ref [M]): q_ref
+    is the reference's self potential, computed here unless q_given (then
+    the given tensor is read; pass the q_ref of an earlier call on the same
+    y, eps, n_iter)."""
+    T, d = x.shape
+    M = y.shape[0]
+    need = int(load().cov_workspace_size_divergence(T, M, d))
+    if need == 0:
+        raise CovError(COV_ERR_INVALID_ARG, "cov_workspace_size_divergence")
+    ctx._check(load().cov_ctx_reserve(ctx.h, need), "cov_ctx_reserve")
+    dev = x.device
+    if q_ref is None:
+        if q_given:
+            raise CovError(COV_ERR_INVALID_ARG, "cov_sinkhorn_divergence", "q_given without q_ref")
+        q_ref = torch.empty(M, device=dev, dtype=torch.float32)
+    value = torch.empty((), device=dev, dtype=torch.float64)
+    g_out = torch.empty_like(x) if grad else None
+    st = load().cov_sinkhorn_divergence(
+        ctx.h, _ptr(x, torch.float32, name="x"), T, _ptr(y, torch.float32, (M, d), "y"),
+        _ptr(b, torch.float32, (M,), "b"), M, d, float(eps), int(n_iter), _ptr(q_ref, torch.float32, (M,), "q_ref"),
+        1 if q_given else 0, _ptr(value, torch.float64, (), "value"),
+        _ptr(g_out, torch.float32, (T, d), "grad") if grad else None, _stream(stream))
+    ctx._check(st, "cov_sinkhorn_divergence")
+    return value, g_out, q_ref
 
 
 def cov_field_sinkhorn_annealed(ctx: Context, x, y, eps, n_iter, eps_start, eps_decay, b=None, f=None, g=None,

@@ -31,13 +31,13 @@ extern "C" cov_status cov_autotune_sinkhorn(cov_ctx* ctx, const float* x, int T,
     // the shapes are those of the CUDA-core kernel: sweep that path whatever
     // the exponent setting (the tensor-core kernel has a single shape)
     const int tc0 = ctx->use_tc;
-    ctx->use_tc = 0;
     cudaEvent_t e0, e1;
     if (cov::cuda_failed(ctx, cudaEventCreate(&e0))) return COV_ERR_CUDA;
     if (cov::cuda_failed(ctx, cudaEventCreate(&e1))) {
         cudaEventDestroy(e0);
         return COV_ERR_CUDA;
     }
+    ctx->use_tc = 0;  // restored below on every path from here
     cov::clobber_ws_caches(ctx);
     cov_status r = COV_OK;
     double best = 1e300;

@@ -157,7 +157,7 @@ SINKHORN_DOUBLE_T4096 = Workload(
 
 SINKHORN_UNICYCLE_T65536 = Workload(
     name="sinkhorn_unicycle_T65536_M262144", model=UNICYCLE,
-    field=FIELD_SINKHORN, T=65536, dt=0.01, n_outer=1, eta=0.5, M=262144,
+    field=FIELD_SINKHORN, T=65536, dt=0.01, n_outer=10, eta=0.5, M=262144,
     eps=0.002, n_iter=100, reference="density")
 
 # Differentiation: gradient of the coverage loss (Sinkhorn divergence of the

@@ -40,7 +40,7 @@ def test_autograd_gradient_matches_oracle(cov, ctx, orc):
     u0 = torch.as_tensor(u0h, dtype=torch.float64, device=dev)
     y_loss = torch.as_tensor(ylh, dtype=torch.float32, device=dev)
     spec = dict(model=wl.DOUBLE_INT, dt=dt, Q=Q, R=R, eta=eta, eps=eps, n_iter=n_iter, n_outer=K)
-    q_ref = ag.reference_self_term(ctx, y_loss, eps_l, it_l)
+    q_ref = ag.reference_self_potential(ctx, y_loss, eps_l, it_l)
     s_K = ag.CoverageSolve.apply(y, b, s0, u0, spec, ctx)
     L = ag.SinkhornLoss.apply(s_K[1:, :2].float().contiguous(), y_loss, eps_l, it_l, ctx, q_ref)
     L.backward()
@@ -73,7 +73,7 @@ def test_reparameterised_mixture_gradients_are_the_chain_rule(cov, ctx):
                 n_iter=5, n_outer=K)
     y_loss = torch.as_tensor(wl.random_points(200, 2, seed=8), dtype=torch.float32, device=dev)
     s_K = ag.CoverageSolve.apply(y, b, torch.tensor(s0h), torch.as_tensor(u0h, device=dev), spec, ctx)
-    L = ag.SinkhornLoss.apply(s_K[1:, :2].float().contiguous(), y_loss, 0.05, 200, ctx, 0.0)
+    L = ag.SinkhornLoss.apply(s_K[1:, :2].float().contiguous(), y_loss, 0.05, 200, ctx, None)
     L.backward()
     per = M // 4
     gy = y.grad.view(4, per, 2).sum(1)

@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 import torch
 
-from conftest import dev32, dev64, host
+from conftest import dev32, dev64, host, rel_norm
 from paper_2511_11514_b300 import workloads as wl
 
 pytestmark = pytest.mark.gpu
@@ -53,25 +53,34 @@ def test_nonfinite_input_sets_status(cov, ctx):
     assert ctx.device_status() == (cov.COV_OK, 0)   # read clears
 
 
+@pytest.mark.parametrize("tensor_cores", [0, 1])
 @pytest.mark.parametrize("n_iter", [1, 4])
-def test_bounded_wait_gives_up_and_reports_timeout(cov, ctx, orc, n_iter):
+def test_bounded_wait_gives_up_and_reports_timeout(cov, ctx, orc, n_iter, tensor_cores):
     """A wait limit of zero polls makes every tile wait give up at once; the
-    kernel drains its copies (and, in the tensor-core kernel of the later
-    iterations, its MMAs) with a limit of its own, raises the timeout bit and
-    returns, and the context stays usable."""
+    kernel drains its copies (and, in the tensor-core kernel that the fixed-
+    offset iterations 2.. run on when tensor_cores = 1, its MMAs, before it
+    frees its tensor memory) with a limit of its own, raises the timeout bit
+    and returns, and the context stays usable: the next call on the same
+    exponent path matches the oracle."""
     x = wl.random_points(300, 2, 1)
     y = wl.random_points(400, 2, 2)
-    ctx.set_option(cov.OPT_SPIN_LIMIT, 0)
+    ctx.set_option(cov.OPT_TENSOR_CORES, tensor_cores)
     try:
-        cov.cov_field_sinkhorn(ctx, dev32(x), dev32(y), 0.05, n_iter)
-        st, fl = ctx.device_status()
+        ctx.set_option(cov.OPT_SPIN_LIMIT, 0)
+        try:
+            cov.cov_field_sinkhorn(ctx, dev32(x), dev32(y), 0.05, n_iter)
+            st, fl = ctx.device_status()
+        finally:
+            ctx.set_option(cov.OPT_SPIN_LIMIT, 1 << 22)
+        assert fl & cov.DEV_TIMEOUT and st == cov.COV_ERR_TIMEOUT
+        a, f, g, p = cov.cov_field_sinkhorn(ctx, dev32(x), dev32(y), 0.05, n_iter)
+        fo, go, po = orc.sinkhorn(x, y, None, 0.05, n_iter)
+        for u, v in ((f, fo), (g, go), (p, po)):
+            assert np.abs(host(u) - v).max() / 0.05 <= 1e-4
+        assert rel_norm(host(a), orc.sinkhorn_field(x, y, None, 0.05, go, po)) <= 1e-4
+        assert ctx.device_status() == (cov.COV_OK, 0)
     finally:
-        ctx.set_option(cov.OPT_SPIN_LIMIT, 1 << 22)
-    assert fl & cov.DEV_TIMEOUT and st == cov.COV_ERR_TIMEOUT
-    a, f, g, p = cov.cov_field_sinkhorn(ctx, dev32(x), dev32(y), 0.05, n_iter)
-    fo, go, po = orc.sinkhorn(x, y, None, 0.05, n_iter)
-    assert np.abs(host(f) - fo).max() / 0.05 <= 1e-4
-    assert ctx.device_status() == (cov.COV_OK, 0)
+        ctx.set_option(cov.OPT_TENSOR_CORES, cov.TENSOR_CORES_AUTO)
 
 
 def test_ragged_and_degenerate_sizes(cov, ctx, orc):

@@ -145,13 +145,62 @@ def test_full_size_double_integrator_workload_sampled_rows(cov, ctx, orc):
     assert errs[3] <= FIELD_TOL, errs
 
 
-def test_full_size_unicycle_density_workload_sampled_rows(cov, ctx, orc):
-    """T = 65536, M = 262144, eps = 0.002 (density-map reference)."""
+def _cold_iteration_check(cov, ctx, orc, x, y, eps, k, n_rows, seed, field):
+    """Iteration k of a cold-start field evaluation (the schedule the solve
+    runs), checked on sampled rows: the GPU's state after k - 1 iterations
+    (zeros for k = 1) is the input, its state after k iterations the output,
+    and the oracle recomputes the sampled rows of the g-, f- and p-updates of
+    iteration k from the GPU's own inputs (g from f^(k-1), f from the new g,
+    p from p^(k-1)) and, with `field`, the sampled rows of the Eq. 7 field
+    from the final g and p.  Exact per row: a row depends only on the other
+    side's potentials and the points."""
+    T, M = len(x), len(y)
+    X, Y = dev32(x), dev32(y)
+    if k == 1:
+        fin, pin = np.zeros(T), np.zeros(T)
+    else:
+        _, f0, _, p0 = cov.cov_field_sinkhorn(ctx, X, Y, eps, k - 1, field=False)
+        fin, pin = host(f0), host(p0)
+    a, f1, g1, p1 = cov.cov_field_sinkhorn(ctx, X, Y, eps, k, field=field)
+    torch.cuda.synchronize()
+    rng = wl.rng(seed)
+    ry = np.sort(rng.choice(M, size=min(n_rows, M), replace=False))
+    rx = np.sort(rng.choice(T, size=min(n_rows, T), replace=False))
+    g1h, f1h, p1h = host(g1), host(f1), host(p1)
+    ge = np.abs(orc.sinkhorn_g_update(x, y, eps, fin, rows=ry) - g1h[ry]).max() / eps
+    fe = np.abs(orc.sinkhorn_f_update(x, y, None, eps, g1h, rows=rx) - f1h[rx]).max() / eps
+    pe = np.abs(orc.sinkhorn_p_update(x, eps, pin, rows=rx) - p1h[rx]).max() / eps
+    ae = rel_norm(host(a)[rx], orc.sinkhorn_field(x, y, None, eps, g1h, p1h, rows=rx)) if field else 0.0
+    assert ctx.device_status()[1] == 0
+    return ge, fe, pe, ae
+
+
+@pytest.fixture(scope="module")
+def unicycle_density_inputs(orc):
     inst = wl.make_instance(wl.SINKHORN_UNICYCLE_T65536)
     w = inst.wl
     s = orc.rollout(w.model, inst.s0, inst.u0, w.dt)
-    x = wl.f32_pair(s[1:, :2])[1]
-    errs = _sampled_rows_check(cov, ctx, orc, x, inst.y, w.eps, 3, 128, seed=2)
+    return wl.f32_pair(s[1:, :2])[1], inst.y, w
+
+
+@pytest.mark.parametrize("k", [1, 50, 100])
+def test_full_size_unicycle_density_workload_iterations(cov, ctx, orc, unicycle_density_inputs, k):
+    """T = 65536, M = 262144, eps = 0.002 (density-map reference), iterations
+    1, n_iter/2 and n_iter of the 100-iteration cold schedule on the default
+    exponent path (at this size the fixed-offset iterations 2..100 take the
+    tensor-core kernel; iteration 1 the running-maximum CUDA-core form), 4096
+    sampled rows of every update and, at iteration 100, of the field."""
+    x, y, w = unicycle_density_inputs
+    assert k <= w.n_iter
+    errs = _cold_iteration_check(cov, ctx, orc, x, y, w.eps, k, 4096, seed=10 + k, field=k == w.n_iter)
+    assert max(errs[:3]) <= POT_TOL, errs
+    assert errs[3] <= FIELD_TOL, errs
+
+
+def test_full_size_unicycle_density_workload_warm_update(cov, ctx, orc, unicycle_density_inputs):
+    """The same workload, one warm-started iteration after three cold ones."""
+    x, y, w = unicycle_density_inputs
+    errs = _sampled_rows_check(cov, ctx, orc, x, y, w.eps, 3, 128, seed=2)
     assert max(errs[:3]) <= POT_TOL, errs
     assert errs[3] <= FIELD_TOL, errs
 

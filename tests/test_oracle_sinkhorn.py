@@ -256,3 +256,36 @@ def test_warm_solve_carries_the_potentials(orc):
     abar[:, :2] = a
     v, _, _ = orc.lqr_track(A, B, inst.Q, inst.R, abar)
     np.testing.assert_allclose(u2, u1c + w.eta * v, atol=1e-12)
+
+
+def test_fixed_iteration_divergence_single_pair(orc):
+    """T = M = 1 (Eq. 6 by hand): after any n >= 1 the cross potentials are
+    f = 0, g = c(x, y) and both self potentials are 0, so the dual value is
+    |x - y|^2 exactly."""
+    x, y = np.array([[0.2, 0.7]]), np.array([[0.5, 0.3]])
+    for n in (1, 2, 9):
+        assert orc.sinkhorn_divergence_iter(x, y, 0.03, n) == pytest.approx(0.25, abs=1e-14)
+
+
+def test_fixed_iteration_divergence_matches_scaling_form(orc):
+    """The dual value <a, f> + <b, g> - <a, p> - <b, q> from the kernel-matrix
+    (scaling-domain) iterations with the same schedule, q from the self
+    iteration of y."""
+    x = wl.random_points(19, 2, seed=71)
+    y = wl.random_points(27, 2, seed=72)
+    eps, n = 0.05, 7
+    f, g, p = _scaling_sinkhorn(x, y, np.ones(len(y)), eps, n)
+    q = _scaling_sinkhorn(y, y, np.ones(len(y)), eps, n)[2]
+    ref = f.mean() + g.mean() - p.mean() - q.mean()
+    assert orc.sinkhorn_divergence_iter(x, y, eps, n) == pytest.approx(ref, rel=1e-11, abs=1e-14)
+
+
+def test_fixed_iteration_divergence_converges_to_the_divergence(orc):
+    """Many iterations reach the converged divergence of Eq. 6; y = x gives
+    zero (debiasing)."""
+    x = wl.random_points(9, 2, seed=73)
+    y = wl.random_points(11, 2, seed=74)
+    eps = 0.1
+    conv = orc.sinkhorn_divergence(x, y, None, eps, tol=1e-14)
+    assert orc.sinkhorn_divergence_iter(x, y, eps, 3000) == pytest.approx(conv, rel=1e-9, abs=1e-12)
+    assert abs(orc.sinkhorn_divergence_iter(x, x, eps, 3000)) <= 1e-10
