@@ -130,6 +130,119 @@ void orc_svgd_field(const double* x, int T, int d, const double* score,
 }
 
 /* ------------------------------------------------------------------------
+ * Reverse mode of the Stein field (Eq. 4) for a scalar L = <abar, g>:
+ *   L = 1/T sum_i sum_j k_ij [ abar_i . s_j + abar_i . (x_i - x_j) / h^2 ],
+ *   k_ij = exp(-|x_i - x_j|^2 / (2 h^2)),
+ *   dk_ij/dx_i = -k_ij (x_i - x_j) / h^2 = -dk_ij/dx_j.
+ * Product rule term by term, with phi_ij = abar_i . s_j + abar_i . (x_i - x_j) / h^2:
+ *   sbar_j  = 1/T sum_i k_ij abar_i
+ *   xbar_i += 1/T sum_j [ -k_ij (x_i - x_j) phi_ij / h^2 + k_ij abar_i / h^2 ]   (x_i as the row)
+ *   xbar_j += 1/T sum_i [  k_ij (x_i - x_j) phi_ij / h^2 - k_ij abar_i / h^2 ]   (x_j as the column)
+ * The score s is an input here (its own dependence on x is the mixture
+ * score's reverse mode below).  Two plain passes, one per role of the
+ * point, so that each output row is written by one loop iteration.
+ * ---------------------------------------------------------------------- */
+void orc_svgd_field_vjp(const double* x, int T, int d, const double* score,
+                        double h, const double* abar, double* xbar,
+                        double* sbar) {
+    const double h2 = h * h;
+#pragma omp parallel for schedule(static)
+    for (int l = 0; l < T; ++l) {
+        const double* xl = x + (size_t)l * d;
+        double xr[16], xc[16], sc[16];
+        for (int c = 0; c < d; ++c) xr[c] = xc[c] = sc[c] = 0.0;
+        /* point l as the row i = l (sum over j) */
+        for (int j = 0; j < T; ++j) {
+            const double* xj = x + (size_t)j * d;
+            double kij = exp(-sqdist(xl, xj, d) / (2.0 * h2));
+            double phi = 0.0;
+            for (int c = 0; c < d; ++c)
+                phi += abar[(size_t)l * d + c] * (score[(size_t)j * d + c] + (xl[c] - xj[c]) / h2);
+            for (int c = 0; c < d; ++c)
+                xr[c] += -kij * (xl[c] - xj[c]) * phi / h2 + kij * abar[(size_t)l * d + c] / h2;
+        }
+        /* point l as the column j = l (sum over i) */
+        for (int i = 0; i < T; ++i) {
+            const double* xi = x + (size_t)i * d;
+            double kil = exp(-sqdist(xi, xl, d) / (2.0 * h2));
+            double phi = 0.0;
+            for (int c = 0; c < d; ++c)
+                phi += abar[(size_t)i * d + c] * (score[(size_t)l * d + c] + (xi[c] - xl[c]) / h2);
+            for (int c = 0; c < d; ++c) {
+                xc[c] += kil * (xi[c] - xl[c]) * phi / h2 - kil * abar[(size_t)i * d + c] / h2;
+                sc[c] += kil * abar[(size_t)i * d + c];
+            }
+        }
+        for (int c = 0; c < d; ++c) {
+            xbar[(size_t)l * d + c] = (xr[c] + xc[c]) / T;
+            if (sbar) sbar[(size_t)l * d + c] = sc[c] / T;
+        }
+    }
+}
+
+/* Reverse mode of the mixture score for the cotangents sbar_i of
+ * score(x_i), i = 1..T.  With the component log terms
+ *   t_k = log w_k - (d/2) log(2 pi sigma_k^2) - |x - mu_k|^2 / (2 sigma_k^2),
+ * r = softmax(t), u_k = (mu_k - x) / sigma_k^2 and S = sum_k r_k u_k, a
+ * change dt_k moves S by sum_k r_k (dt_k - sum_m r_m dt_m) u_k and a change
+ * du_k by r_k du_k, so with c = sbar_i and beta_k = r_k (c . u_k - c . S):
+ *   dt_k/dx = u_k, du_k/dx = -I / sigma_k^2:
+ *     xbar += sum_k [ beta_k u_k - r_k c / sigma_k^2 ]
+ *   dt_k/dmu_k = -u_k, du_k/dmu_k = I / sigma_k^2:
+ *     mubar_k += -beta_k u_k + r_k c / sigma_k^2
+ *   dt_k/dsigma_k = -d / sigma_k + |x - mu_k|^2 / sigma_k^3, du_k/dsigma_k = -2 u_k / sigma_k:
+ *     sigmabar_k += beta_k (-d / sigma_k + |x - mu_k|^2 / sigma_k^3) - 2 r_k (c . u_k) / sigma_k
+ *   dt_k/dw_k = 1 / w_k (the normalisation of w cancels in the softmax):
+ *     wbar_k += beta_k / w_k
+ * (sum_k beta_k u_k = sum_k r_k (c . u_k) (u_k - S), the Hessian of log q
+ * applied to c.)  xbar_add, wbar, mubar, sigmabar may each be NULL; the
+ * mixture gradients are sums over the T points. */
+void orc_gmm_score_vjp(const double* x, int T, int d, int K, const double* w,
+                       const double* mu, const double* sigma,
+                       const double* sbar, double* xbar_add, double* wbar,
+                       double* mubar, double* sigmabar) {
+    if (wbar) for (int k = 0; k < K; ++k) wbar[k] = 0.0;
+    if (mubar) for (int k = 0; k < K * d; ++k) mubar[k] = 0.0;
+    if (sigmabar) for (int k = 0; k < K; ++k) sigmabar[k] = 0.0;
+    double* t = (double*)malloc(sizeof(double) * K);
+    double* u = (double*)malloc(sizeof(double) * (size_t)K * d);
+    for (int i = 0; i < T; ++i) {
+        const double* xi = x + (size_t)i * d;
+        const double* c = sbar + (size_t)i * d;
+        gmm_log_terms(xi, d, K, w, mu, sigma, t);
+        double L = lse(t, K);
+        double S[16], cS = 0.0;
+        for (int a = 0; a < d; ++a) S[a] = 0.0;
+        for (int k = 0; k < K; ++k) {
+            double s2 = sigma[k] * sigma[k];
+            t[k] = exp(t[k] - L); /* r_k */
+            for (int a = 0; a < d; ++a) {
+                u[(size_t)k * d + a] = (mu[(size_t)k * d + a] - xi[a]) / s2;
+                S[a] += t[k] * u[(size_t)k * d + a];
+            }
+        }
+        for (int a = 0; a < d; ++a) cS += c[a] * S[a];
+        for (int k = 0; k < K; ++k) {
+            double s2 = sigma[k] * sigma[k];
+            double cu = 0.0, dist2 = 0.0;
+            for (int a = 0; a < d; ++a) cu += c[a] * u[(size_t)k * d + a];
+            dist2 = sqdist(xi, mu + (size_t)k * d, d);
+            double beta = t[k] * (cu - cS);
+            for (int a = 0; a < d; ++a) {
+                double uka = u[(size_t)k * d + a];
+                if (xbar_add) xbar_add[(size_t)i * d + a] += beta * uka - t[k] * c[a] / s2;
+                if (mubar) mubar[(size_t)k * d + a] += -beta * uka + t[k] * c[a] / s2;
+            }
+            if (sigmabar)
+                sigmabar[k] += beta * (-d / sigma[k] + dist2 / (s2 * sigma[k])) - 2.0 * t[k] * cu / sigma[k];
+            if (wbar) wbar[k] += beta / w[k];
+        }
+    }
+    free(t);
+    free(u);
+}
+
+/* ------------------------------------------------------------------------
  * Entropic OT between p_s = sum_i a_i delta_{x_i} (a_i = 1/T, Eq. 1) and
  * q = sum_j b_j delta_{y_j} (Eq. 5), solved by the log-domain Sinkhorn
  * algorithm the paper cites for Eq. 6.  Reading of the garbled marginal

@@ -40,6 +40,19 @@ void orc_gmm_score(const double* x, int T, int d, int K, const double* w,
 /* ---- Stein variational field, Eq. 4 ------------------------------------ */
 void orc_svgd_field(const double* x, int T, int d, const double* score,
                     double h, const int* rows, int n_rows, double* out);
+/* Reverse mode of Eq. 4 for L = <abar, field>: xbar [T][d] (the score held
+ * fixed) and sbar [T][d] = dL/dscore (may be NULL). */
+void orc_svgd_field_vjp(const double* x, int T, int d, const double* score,
+                        double h, const double* abar, double* xbar,
+                        double* sbar);
+/* Reverse mode of the mixture score for cotangents sbar [T][d] of
+ * score(x_i): adds J(x_i)' sbar_i to xbar_add [T][d]; writes the gradients
+ * of sum_i sbar_i . score(x_i) with respect to w [K] (raw weights),
+ * mu [K][d], sigma [K].  Any output may be NULL. */
+void orc_gmm_score_vjp(const double* x, int T, int d, int K, const double* w,
+                       const double* mu, const double* sigma,
+                       const double* sbar, double* xbar_add, double* wbar,
+                       double* mubar, double* sigmabar);
 
 /* ---- log-domain Sinkhorn, Eq. 5-6 -------------------------------------- */
 void orc_sinkhorn_g_update(const double* x, int T, const double* y, int M,

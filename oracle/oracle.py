@@ -65,6 +65,8 @@ def _declare(L):
         "orc_gmm_logpdf": (_d, [_D, _i, _i, _D, _D, _D]),
         "orc_gmm_score": (None, [_D, _i, _i, _i, _D, _D, _D, _D]),
         "orc_svgd_field": (None, [_D, _i, _i, _D, _d, _I, _i, _D]),
+        "orc_svgd_field_vjp": (None, [_D, _i, _i, _D, _d, _D, _D, _D]),
+        "orc_gmm_score_vjp": (None, [_D, _i, _i, _i, _D, _D, _D, _D, _D, _D, _D, _D]),
         "orc_sinkhorn_g_update": (None, [_D, _i, _D, _i, _i, _d, _D, _I, _i, _D]),
         "orc_sinkhorn_f_update": (None, [_D, _i, _D, _i, _D, _i, _d, _D, _I, _i, _D]),
         "orc_sinkhorn_p_update": (None, [_D, _i, _i, _d, _D, _I, _i, _D]),
@@ -145,6 +147,38 @@ def svgd_field(x, score, h, rows=None):
     out = np.empty((nr if rows is not None else T, d))
     lib().orc_svgd_field(_p(x), T, d, _p(score), float(h), rp, nr, _p(out))
     return out
+
+
+def svgd_field_vjp(x, score, h, abar):
+    """Gradient of <abar, svgd_field(x, score, h)>: (xbar [T,d] with the score
+    held fixed, sbar [T,d] = d/dscore)."""
+    x, score, abar = _f64(x), _f64(score), _f64(abar)
+    T, d = x.shape
+    xbar, sbar = np.empty((T, d)), np.empty((T, d))
+    lib().orc_svgd_field_vjp(_p(x), T, d, _p(score), float(h), _p(abar), _p(xbar), _p(sbar))
+    return xbar, sbar
+
+
+def gmm_score_vjp(x, w, mu, sigma, sbar):
+    """Reverse mode of gmm_score for cotangents sbar [T,d]: (xbar [T,d] =
+    J' sbar per point, wbar [K], mubar [K,d], sigmabar [K])."""
+    x, w, mu, sigma, sbar = _f64(x), _f64(w), _f64(mu), _f64(sigma), _f64(sbar)
+    T, d = x.shape
+    K = w.size
+    xbar = np.zeros((T, d))
+    wbar, mubar, sbar_s = np.empty(K), np.empty((K, d)), np.empty(K)
+    lib().orc_gmm_score_vjp(_p(x), T, d, K, _p(w), _p(mu), _p(sigma), _p(sbar), _p(xbar), _p(wbar), _p(mubar),
+                            _p(sbar_s))
+    return xbar, wbar, mubar, sbar_s
+
+
+def svgd_gmm_field_vjp(x, w, mu, sigma, h, abar):
+    """Gradient of <abar, svgd_field(x, gmm_score(x), h)> with respect to x
+    (through the kernel and the score) and the mixture (w, mu, sigma)."""
+    score = gmm_score(x, w, mu, sigma)
+    xk, sb = svgd_field_vjp(x, score, h, abar)
+    xs, wbar, mubar, sigbar = gmm_score_vjp(x, w, mu, sigma, sb)
+    return xk + xs, wbar, mubar, sigbar
 
 
 # -- Sinkhorn (Eq. 5-7) ----------------------------------------------------

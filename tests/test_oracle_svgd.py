@@ -185,3 +185,77 @@ def test_density_score_of_a_fine_gaussian_map(orc):
     sc = orc.density_score(m, x)
     want = -(x - mu) / sig ** 2
     assert np.linalg.norm(sc - want) <= 2e-2 * np.linalg.norm(want)
+
+
+# -- reverse mode of the Stein field and of the mixture score -----------------
+def _fd(fun, v, step=1e-6):
+    """Central differences of the scalar fun at every entry of the array v."""
+    g = np.zeros_like(v)
+    for idx in np.ndindex(v.shape):
+        vp, vm = v.copy(), v.copy()
+        vp[idx] += step
+        vm[idx] -= step
+        g[idx] = (fun(vp) - fun(vm)) / (2 * step)
+    return g
+
+
+@pytest.mark.parametrize("T,d,h", [(7, 2, 0.3), (5, 3, 0.5)])
+def test_svgd_vjp_matches_central_differences(orc, T, d, h):
+    """<abar, field(x, s)> differentiated by central differences (step 1e-6)
+    in every coordinate of x (score held fixed) and of s."""
+    rng = wl.rng(20 + T)
+    x = rng.uniform(0, 1, size=(T, d))
+    s = rng.standard_normal((T, d))
+    abar = rng.standard_normal((T, d))
+    xbar, sbar = orc.svgd_field_vjp(x, s, h, abar)
+    L = lambda xx, ss: float(np.sum(abar * orc.svgd_field(xx, ss, h)))
+    np.testing.assert_allclose(xbar, _fd(lambda v: L(v, s), x), rtol=1e-6, atol=1e-8)
+    np.testing.assert_allclose(sbar, _fd(lambda v: L(x, v), s), rtol=1e-6, atol=1e-8)
+
+
+def test_svgd_vjp_single_point_and_translation(orc):
+    """T = 1: the field is the score itself, so xbar = 0 and sbar = abar.
+    With the score held fixed the field depends on x only through
+    differences x_i - x_j, so the x-gradient sums to zero over the points."""
+    x = np.array([[0.3, 0.6]])
+    ab = np.array([[0.7, -1.1]])
+    xbar, sbar = orc.svgd_field_vjp(x, np.array([[2.0, -3.0]]), 0.2, ab)
+    np.testing.assert_array_equal(xbar, 0.0)
+    np.testing.assert_allclose(sbar, ab, rtol=0, atol=0)
+    rng = wl.rng(31)
+    x = rng.uniform(0, 1, size=(40, 2))
+    xbar, _ = orc.svgd_field_vjp(x, rng.standard_normal((40, 2)), 0.1, rng.standard_normal((40, 2)))
+    assert np.abs(xbar.sum(0)).max() <= 1e-10 * np.abs(xbar).sum()
+
+
+def test_gmm_score_vjp_matches_central_differences(orc):
+    """sum_i sbar_i . score(x_i) differentiated by central differences in x,
+    the raw weights, the means and the standard deviations; the weight
+    gradient is orthogonal to the weights (the score depends on w / sum w)."""
+    w, mu, sigma = wl.gmm_params(4, seed=41)
+    rng = wl.rng(42)
+    x = rng.uniform(0.1, 0.9, size=(6, 2))
+    sb = rng.standard_normal((6, 2))
+    xbar, wbar, mubar, sigbar = orc.gmm_score_vjp(x, w, mu, sigma, sb)
+    Ls = lambda xx, ww, mm, ss: float(np.sum(sb * orc.gmm_score(xx, ww, mm, ss)))
+    np.testing.assert_allclose(xbar, _fd(lambda v: Ls(v, w, mu, sigma), x), rtol=1e-6, atol=1e-6)
+    np.testing.assert_allclose(wbar, _fd(lambda v: Ls(x, v, mu, sigma), w), rtol=1e-6, atol=1e-6)
+    np.testing.assert_allclose(mubar, _fd(lambda v: Ls(x, w, v, sigma), mu), rtol=1e-6, atol=1e-6)
+    np.testing.assert_allclose(sigbar, _fd(lambda v: Ls(x, w, mu, v), sigma), rtol=1e-6, atol=1e-5)
+    assert abs(float(w @ wbar)) <= 1e-10 * float(np.abs(w * wbar).sum())
+
+
+def test_svgd_with_mixture_score_vjp_is_the_total_derivative(orc):
+    """The chained reverse mode (kernel part + score part) against central
+    differences of <abar, field(x, score(x))> through both paths."""
+    w, mu, sigma = wl.gmm_params(3, seed=51)
+    rng = wl.rng(52)
+    x = rng.uniform(0.2, 0.8, size=(8, 2))
+    abar = rng.standard_normal((8, 2))
+    h = 0.15
+    xbar, wbar, mubar, sigbar = orc.svgd_gmm_field_vjp(x, w, mu, sigma, h, abar)
+    L = lambda xx, ww, mm, ss: float(np.sum(abar * orc.svgd_field(xx, orc.gmm_score(xx, ww, mm, ss), h)))
+    np.testing.assert_allclose(xbar, _fd(lambda v: L(v, w, mu, sigma), x), rtol=1e-6, atol=1e-6)
+    np.testing.assert_allclose(mubar, _fd(lambda v: L(x, w, v, sigma), mu), rtol=1e-6, atol=1e-6)
+    np.testing.assert_allclose(sigbar, _fd(lambda v: L(x, w, mu, v), sigma), rtol=1e-6, atol=1e-5)
+    np.testing.assert_allclose(wbar, _fd(lambda v: L(x, v, mu, sigma), w), rtol=1e-6, atol=1e-6)
