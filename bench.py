@@ -127,6 +127,21 @@ def job_value(world, pairs_per_step, steps, max_total_ms):
     return world * pairs_per_step * steps / (max_total_ms * 1e-3)
 
 
+def assign_problems(costs, world):
+    """Independent problems to ranks by cost (longest first, each to the rank
+    with the least work so far, ties to the lower rank): a deterministic
+    partition every rank computes identically, so no collective is needed
+    to agree on it.  Returns one list of problem indices per rank, each in
+    increasing order."""
+    load = [0.0] * world
+    out = [[] for _ in range(world)]
+    for p in sorted(range(len(costs)), key=lambda k: (-costs[k], k)):
+        r = min(range(world), key=lambda q: (load[q], q))
+        out[r].append(p)
+        load[r] += costs[p]
+    return [sorted(o) for o in out]
+
+
 # -- clocks sampled during the timed region ------------------------------------
 class Clocks:
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
@@ -750,18 +765,27 @@ def run_svgd(args, w, rank, local_rank, world):
 
 
 def run_batched(args):
-    """Batched form: N independent double-integrator problems, T ~ U{128..4096},
+    """Batched form: independent double-integrator problems, T ~ U{128..4096},
     M ~ U{512..16384}, half Stein / half Sinkhorn (50 iterations), advanced by
     one CUDA-graph launch per outer iteration, against the same problems solved
-    one by one with cov_solve on the same GPU."""
+    one by one with cov_solve on the same GPU.  Under N ranks every rank takes
+    the problems `assign_problems` gives it (by pair count) and advances them
+    as its own batch; the job is timed by the slowest rank (weak scaling: the
+    batch grows with N, `args.batched` problems per rank)."""
     import torch
+    import torch.distributed as dist
 
     from paper_2511_11514_b300 import binding as cov
 
-    torch.cuda.set_device(0)
-    insts = wl.make_batch(args.batched, seed=0)
-    ctx = cov.Context(0)
-    dev = torch.device("cuda", 0)
+    rank, local_rank, world = dist_env()
+    torch.cuda.set_device(local_rank)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    all_insts = wl.make_batch(args.batched * world, seed=0)
+    mine = assign_problems([i.wl.pairs_per_field for i in all_insts], world)[rank]
+    insts = [all_insts[k] for k in mine]
+    ctx = cov.Context(local_rank)
+    dev = torch.device("cuda", local_rank)
     ys = [torch.as_tensor(i.y, dtype=torch.float32, device=dev) if i.y is not None else None for i in insts]
     probs = []
     for i, y in zip(insts, ys):
@@ -772,12 +796,16 @@ def run_batched(args):
             probs.append(cov.make_problem(w.model, w.T, w.dt, i.s0, w.field, i.Q, i.R, w.eta, y=y, eps=w.eps,
                                           n_iter=w.n_iter))
     pairs = sum(i.wl.pairs_per_field for i in insts)
+    pairs_job = sum(i.wl.pairs_per_field for i in all_insts)
     us = [torch.as_tensor(i.u0, dtype=torch.float64, device=dev) for i in insts]
     t0 = time.perf_counter()
     ss = cov.cov_solve_batched(ctx, probs, max(1, args.warmup), us)  # includes graph capture
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t0
-    clocks = Clocks(0)
+    clocks = Clocks(local_rank)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
     clocks.start()
     a = torch.cuda.Event(enable_timing=True)
     b = torch.cuda.Event(enable_timing=True)
@@ -785,7 +813,9 @@ def run_batched(args):
     cov.cov_solve_batched(ctx, probs, args.steps, us, ss)
     b.record()
     torch.cuda.synchronize()
-    batched_ms = a.elapsed_time(b)
+    if world > 1:
+        dist.barrier()
+    batched_ms = max_over_ranks(a.elapsed_time(b), world, dev)
     clk = clocks.stop()
     st, flags = ctx.device_status()
     if st != cov.COV_OK:
@@ -800,21 +830,31 @@ def run_batched(args):
         b.record()
         torch.cuda.synchronize()
         one_ms += a.elapsed_time(b)
-    value = pairs * args.steps / (batched_ms * 1e-3)
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": batched_ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded Philox mixtures, uneven sizes)",
-            "config": {"workload": f"batched_double_integrator_{args.batched}_problems",
-                       "problems": args.batched, "T": "U{128..4096}", "M": "U{512..16384}",
-                       "fields": "half Stein (h = 0.05), half Sinkhorn (eps = 0.005, 50 iterations)",
-                       "pairs_per_step": pairs, "graph_capture_and_setup_s": setup_s,
-                       "l2": "not flushed (the batch working set, ~GBs, exceeds L2)"},
-            "one_by_one": {"value": pairs * args.steps / (one_ms * 1e-3), "unit": UNIT,
-                           "ms_per_step": one_ms / args.steps,
-                           "how": "cov_solve on each problem in turn, same GPU, same context, graphs pre-captured"},
-            "batched_speedup": one_ms / batched_ms, "clocks": clk}
-    print(json.dumps(line), flush=True)
+    one_ms = max_over_ranks(one_ms, world, dev)
+    value = pairs_job * args.steps / (batched_ms * 1e-3)
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": batched_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic (seeded Philox mixtures, uneven sizes)",
+                "config": {"workload": f"batched_double_integrator_{args.batched}_problems_per_gpu",
+                           "problems": args.batched * world, "problems_rank0": len(insts),
+                           "T": "U{128..4096}", "M": "U{512..16384}",
+                           "fields": "half Stein (h = 0.05), half Sinkhorn (eps = 0.005, 50 iterations)",
+                           "pairs_per_step": pairs_job, "pairs_per_step_rank0": pairs,
+                           "graph_capture_and_setup_s": setup_s,
+                           "parallelism": (f"{world} ranks, problems assigned by pair count (longest first), no "
+                                           "data-path collective" if world > 1 else "single GPU"),
+                           "l2": "not flushed (the batch working set, ~GBs, exceeds L2)"},
+                "one_by_one": {"value": pairs_job * args.steps / (one_ms * 1e-3), "unit": UNIT,
+                               "ms_per_step": one_ms / args.steps,
+                               "how": "cov_solve on each problem in turn, same GPU, same context, graphs "
+                                      "pre-captured"},
+                "batched_speedup": one_ms / batched_ms, "clocks": clk}
+        print(json.dumps(line), flush=True)
     ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
     return 0
 
 

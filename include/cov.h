@@ -181,6 +181,32 @@ COV_API cov_status cov_field_svgd(cov_ctx* ctx, const float* x, int T, int d,
                           const float* score, const cov_gmm* gmm, float h,
                           float* a_out, cov_stream_t stream);
 
+/* Reverse mode of the Stein field for L = <abar, a> (Eq. 4; the product rule
+ * over both roles of every point, row and column, of the all-pairs sum):
+ *   sbar_l = dL/dscore_l = 1/T sum_j k_lj abar_j,
+ *   xbar_l = 1/(T h^2) sum_j k_lj [ (abar_l - abar_j) - r_lj psi_lj ],
+ *   r_lj = x_l - x_j, psi_lj = abar_l . s_j + abar_j . s_l + (abar_l - abar_j) . r_lj / h^2,
+ * one all-pairs pass (one exponential and 6d + 3 FP32 operations per pair).
+ *   x, abar [T][d] FP32 device;  h > 0
+ *   score [T][d] FP32 device: then xbar is the gradient with the score held
+ *          fixed and gmm, wbar, mubar, sigmabar are ignored; or NULL: the
+ *          score is the mixture's (gmm, host descriptor, as cov_field_svgd)
+ *          at x, xbar is the total gradient (kernel and score paths: the
+ *          Hessian of log q applied to sbar is added), and the mixture
+ *          gradients are written where the pointers are non-NULL:
+ *          wbar [K] (raw weights; sum_k w_k wbar_k = 0), mubar [K][d],
+ *          sigmabar [K], FP32 device (sums over the points in FP64)
+ *   xbar [T][d] FP32 device, written;  sbar [T][d] FP32 device or NULL
+ * Workspace: cov_workspace_size_svgd_vjp(T, d, K) (K = 0 with a given
+ * score).  Errors: COV_ERR_INVALID_ARG for T < 1, d outside 1..COV_MAX_D,
+ * h <= 0, NULL x/abar/xbar, or a NULL score without a valid mixture. */
+COV_API size_t cov_workspace_size_svgd_vjp(int T, int d, int K);
+COV_API cov_status cov_field_svgd_vjp(cov_ctx* ctx, const float* x, int T, int d,
+                                      const float* score, const cov_gmm* gmm, float h,
+                                      const float* abar, float* xbar, float* sbar,
+                                      float* wbar, float* mubar, float* sigmabar,
+                                      cov_stream_t stream);
+
 /* ---- Sinkhorn-divergence field, Eq. 5-7 ---------------------------------- */
 
 /* Log-domain Sinkhorn between p_s = (1/T) sum delta_{x_i} and

@@ -38,7 +38,8 @@ EXPORTS = (
     "cov_probe_peaks", "cov_workspace_size_vjp", "cov_field_sinkhorn_vjp", "cov_workspace_size_lqr_vjp",
     "cov_lqr_vjp", "cov_rollout_vjp", "cov_solve_checkpointed", "cov_workspace_size_backward",
     "cov_solve_backward", "cov_field_sinkhorn_annealed", "cov_density_score", "cov_autotune_sinkhorn",
-    "cov_workspace_size_divergence", "cov_sinkhorn_divergence",
+    "cov_workspace_size_divergence", "cov_sinkhorn_divergence", "cov_workspace_size_svgd_vjp",
+    "cov_field_svgd_vjp",
 )
 
 
@@ -112,6 +113,9 @@ def load(path: str = LIB_PATH):
         "cov_solve_backward": (_i, [_P, ctypes.POINTER(cov_problem), _i, _P, _P, _P, _P, _P, _P, _P, _P]),
         "cov_workspace_size_divergence": (_sz, [_i, _i, _i]),
         "cov_sinkhorn_divergence": (_i, [_P, _P, _i, _P, _P, _i, _i, _f, _i, _P, _i, _P, _P, _P]),
+        "cov_workspace_size_svgd_vjp": (_sz, [_i, _i, _i]),
+        "cov_field_svgd_vjp": (_i, [_P, _P, _i, _i, _P, ctypes.POINTER(cov_gmm), _f, _P, _P, _P, _P, _P, _P,
+                                    _P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -276,6 +280,44 @@ def cov_field_svgd(ctx: Context, x, h, score=None, gmm=None, out=None, stream=No
                                _ptr(out, torch.float32, (T, d), "out"), _stream(stream))
     ctx._check(st, "cov_field_svgd")
     return out
+
+
+def cov_field_svgd_vjp(ctx: Context, x, h, abar, score=None, gmm=None, want_sbar=True, want_gmm=True,
+                       stream=None):
+    """Reverse mode of the Stein field (Eq. 4) for L = <abar, field>.  With
+    a score tensor: (xbar, sbar) with the score held fixed.  With gmm = (w,
+    mu, sigma): (xbar, sbar, (wbar, mubar, sigmabar)), xbar the total
+    gradient through the kernel and the mixture score."""
+    T, d = x.shape
+    K = 0 if score is not None else len(gmm[0])
+    need = int(load().cov_workspace_size_svgd_vjp(T, d, K))
+    if need == 0:
+        raise CovError(COV_ERR_INVALID_ARG, "cov_workspace_size_svgd_vjp")
+    ctx._check(load().cov_ctx_reserve(ctx.h, need), "cov_ctx_reserve")
+    dev = x.device
+    xbar = torch.empty_like(x)
+    sbar = torch.empty_like(x) if want_sbar else None
+    g = arrs = None
+    wb = mb = sb = None
+    if score is None:
+        g, arrs = _gmm_struct(gmm, d)
+        if want_gmm:
+            wb = torch.empty(K, device=dev, dtype=torch.float32)
+            mb = torch.empty((K, d), device=dev, dtype=torch.float32)
+            sb = torch.empty(K, device=dev, dtype=torch.float32)
+    st = load().cov_field_svgd_vjp(
+        ctx.h, _ptr(x, torch.float32, name="x"), T, d,
+        _ptr(score, torch.float32, (T, d), "score") if score is not None else None,
+        ctypes.byref(g) if g is not None else None, float(h), _ptr(abar, torch.float32, (T, d), "abar"),
+        _ptr(xbar, torch.float32, (T, d), "xbar"), _ptr(sbar, torch.float32, (T, d), "sbar") if want_sbar else None,
+        _ptr(wb, torch.float32, (K,), "wbar") if wb is not None else None,
+        _ptr(mb, torch.float32, (K, d), "mubar") if mb is not None else None,
+        _ptr(sb, torch.float32, (K,), "sigmabar") if sb is not None else None, _stream(stream))
+    ctx._check(st, "cov_field_svgd_vjp")
+    del arrs
+    if score is not None:
+        return xbar, sbar
+    return xbar, sbar, (wb, mb, sb)
 
 
 def cov_field_sinkhorn(ctx: Context, x, y, eps, n_iter, b=None, f=None, g=None, p=None, warm=False,
