@@ -56,15 +56,15 @@ FP32_LANES_PER_SM_CLK = 128
 # 388 KB (g + p launch) and 291 KB (f launch), no writes.
 PAIRS_TRAFFIC_BYTES = 339456
 # The same for lse_tc_kernel at T = 65536, M = 262144 (the default path at
-# that size): 9.47 MB (g + p launch) and 13.41 MB (f launch), no writes.
-TC_LARGE_TRAFFIC_BYTES = 11440512
+# that size): 9.47 MB (g + p launch) and 13.43 MB (f launch), no writes.
+TC_LARGE_TRAFFIC_BYTES = 11454208
 
 
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=400)
-    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(wl.WORKLOADS))
     ap.add_argument("--e2e-steps", type=int, default=20)
@@ -87,8 +87,15 @@ def parse_args():
     ap.add_argument("--lqr-sweep", default="",
                     help="comma-separated horizons: time the LQR step (cov_lqr_track: parallel-in-time Riccati + "
                          "the two affine scans) on the unicycle linearisation at each T (context)")
+    ap.add_argument("--batch-share", type=int, default=0,
+                    help="--batched: percent of the GPU each problem's all-pairs launches plan for "
+                         "(COV_OPT_BATCH_SHARE; 0 keeps the library default)")
     ap.add_argument("--tensor-cores", action="store_true",
                     help="form the fixed-offset updates' exponents on the tensor cores (COV_OPT_TENSOR_CORES)")
+    ap.add_argument("--field-profile", default="",
+                    help="T,M: run only Sinkhorn field evaluations (--steps of them, 8 iterations each, on the "
+                         "default exponent path) of the workload's trajectory and reference at this size, with "
+                         "the profiler range around them: a short target for ncu")
     ap.add_argument("--adjoint-outer", type=int, default=0,
                     help="outer iterations of --adjoint (default: the workload's 20; fewer only to keep a "
                          "profiler's launch list short)")
@@ -636,6 +643,46 @@ def run_ours(args):
     return 0
 
 
+def run_field_profile(args):
+    """Sinkhorn field evaluations alone (8 iterations each) at a chosen size
+    of the workload (its initial trajectory's positions, its reference
+    generator), bracketed by the profiler range: with ncu's
+    --profile-from-start off only these launches are seen."""
+    import torch
+
+    from paper_2511_11514_b300 import binding as cov
+
+    w = wl.WORKLOADS[args.workload]
+    T, M = (int(v) for v in args.field_profile.split(","))
+    torch.cuda.set_device(0)
+    inst = wl.make_instance(w, T=T, M=M)
+    ctx = cov.Context(0)
+    dev = torch.device("cuda", 0)
+    u = torch.as_tensor(inst.u0, dtype=torch.float64, device=dev)
+    x = cov.cov_rollout(ctx, w.model, inst.s0, u, w.dt)[1:, :2].float().contiguous()
+    y = torch.as_tensor(inst.y, dtype=torch.float32, device=dev).contiguous()
+    cov.cov_field_sinkhorn(ctx, x, y, w.eps, 8, field=False)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.profiler.start()
+    a.record()
+    for _ in range(args.steps):
+        cov.cov_field_sinkhorn(ctx, x, y, w.eps, 8, field=False)
+    b.record()
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    st, flags = ctx.device_status()
+    ctx.close()
+    if st != cov.COV_OK:
+        raise SystemExit(f"device status {cov.status_string(st)} flags {flags}")
+    ms = a.elapsed_time(b) / args.steps
+    print(json.dumps({"field_profile": {"workload": w.name, "T": T, "M": M, "eps": w.eps, "iterations": 8,
+                                        "ms_per_field": ms, "evaluations": args.steps,
+                                        "tensor_cores": uses_tensor_cores(dataclasses.replace(w, T=T, M=M), False)}}),
+          flush=True)
+    return 0
+
+
 def run_svgd(args, w, rank, local_rank, world):
     """The Stein-field workload (latency-bound: T^2 pair evaluations per
     field).  A step is one outer iteration through `cov_solve_continue`;
@@ -785,6 +832,8 @@ def run_batched(args):
     mine = assign_problems([i.wl.pairs_per_field for i in all_insts], world)[rank]
     insts = [all_insts[k] for k in mine]
     ctx = cov.Context(local_rank)
+    if args.batch_share:
+        ctx.set_option(cov.OPT_BATCH_SHARE, args.batch_share)
     dev = torch.device("cuda", local_rank)
     ys = [torch.as_tensor(i.y, dtype=torch.float32, device=dev) if i.y is not None else None for i in insts]
     probs = []
@@ -1228,6 +1277,8 @@ def main():
         return run_variants(args)
     if args.impl == "reference":
         return run_reference(args)
+    if args.field_profile:
+        return run_field_profile(args)
     if args.batched:
         return run_batched(args)
     if args.adjoint:

@@ -124,20 +124,24 @@ enum {
     COV_OPT_CTAS_PER_SM = 3,     /* cap on resident CTAs per SM planned for, 1..8 (default 8; the register budget may allow fewer) */
     COV_OPT_USE_GRAPH = 4,       /* cov_solve: capture one outer iteration in a CUDA graph (default 1) */
     COV_OPT_SPIN_LIMIT = 5,      /* bounded-wait iteration limit, >= 0 (default 1<<22) */
-    COV_OPT_TENSOR_CORES = 6     /* Exponents of the Sinkhorn updates with a fixed row offset (d <= 3):
+    COV_OPT_TENSOR_CORES = 6,    /* Exponents of the Sinkhorn updates with a fixed row offset (d <= 3):
                                     1: tcgen05 kind::tf32 MMAs on TF32-split operands; 0: FP32 FMAs on
                                     the CUDA cores; 2 (default): the tensor cores for field evaluations
                                     whose launches are all of at least 2^30 pair evaluations (where they
                                     are faster), the CUDA cores otherwise.  The tensor-core exponent error
                                     grows with the size of the exponent terms, (extent / sqrt(eps ln 2))^2 */
+    COV_OPT_BATCH_SHARE = 7      /* cov_solve_batched: percent (1..100) of the GPU's resident CTA slots that
+                                    each problem's all-pairs launches are planned for (its column splits),
+                                    since the batch's problems run side by side (default 12) */
 };
 COV_API cov_status cov_ctx_set_option(cov_ctx* ctx, int key, long long value);
 
 /* Tile-shape autotuner of the all-pairs kernels: times the Sinkhorn
  * iteration on these inputs (as cov_field_sinkhorn, uniform start) for each
  * candidate (rows per thread, resident-CTA cap) in {(2,8), (4,8), (8,8),
- * (4,6), (2,6), (8,4)} with CUDA events on `stream`, as (t(6 iterations) -
- * t(2)) / 4 (median of 3), and applies the fastest to the context.
+ * (4,6), (2,6), (8,4)} with CUDA events on `stream`, as (t(2 + n
+ * iterations) - t(2)) / n (median of 3; n = 20 below 2^30 pair evaluations
+ * per iteration, 4 above), and applies the fastest to the context.
  * The shape only concerns the CUDA-core kernel, so the sweep runs with
  * COV_OPT_TENSOR_CORES off and restores the context's setting after it.
  * Synchronises the stream.  best_R, best_ctas_per_sm: host outputs (may be

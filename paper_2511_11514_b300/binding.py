@@ -25,6 +25,8 @@ WARM_START = 1
 DEV_NONFINITE, DEV_TIMEOUT, DEV_NOT_SPD = 1, 2, 4
 MAX_D, MAX_GMM, MAX_N, MAX_M = 6, 32, 4, 3
 OPT_ROWS_PER_THREAD, OPT_THREADS, OPT_CTAS_PER_SM, OPT_USE_GRAPH, OPT_SPIN_LIMIT, OPT_TENSOR_CORES = 1, 2, 3, 4, 5, 6
+OPT_BATCH_SHARE = 7
+BATCH_SHARE_DEFAULT = 12  # the library's default COV_OPT_BATCH_SHARE
 TENSOR_CORES_OFF, TENSOR_CORES_ON, TENSOR_CORES_AUTO = 0, 1, 2
 MODEL_DIMS = {SINGLE_INT: (2, 2), DOUBLE_INT: (4, 2), UNICYCLE: (3, 2)}
 

@@ -1,9 +1,9 @@
 // autotune.cu -- tile-shape sweep of the all-pairs kernels through the
 // library's own calls: rows per lane R and the resident-CTA cap are timed
 // on the caller's inputs with CUDA events on the caller's stream, as the
-// per-iteration cost (t(6 iterations) - t(2 iterations)) / 4 so that the
-// prep and gradient launches cancel, and the fastest pair is applied to the
-// context.
+// per-iteration cost (t(2 + n iterations) - t(2 iterations)) / n (n = 20
+// below 2^30 pairs per iteration, 4 above) so that the prep and gradient
+// launches cancel, and the fastest pair is applied to the context.
 #include <math.h>
 
 #include <algorithm>
@@ -55,6 +55,10 @@ extern "C" cov_status cov_autotune_sinkhorn(cov_ctx* ctx, const float* x, int T,
             return COV_ERR_CUDA;
         return COV_OK;
     };
+    // iterations timed per candidate: enough that the difference spans a few
+    // hundred microseconds at small sizes (4 at the large ones)
+    const double pairs_iter = 2.0 * T * (double)M + (double)T * T;
+    const int n_diff = pairs_iter < (double)(1LL << 30) ? 20 : 4;
     for (int k = 0; k < kNumCandidates && r == COV_OK; ++k) {
         const Candidate c = kCandidates[k];
         ctx->rows_per_thread = c.R;  // the planner maps R to the built shapes for this d
@@ -63,12 +67,12 @@ extern "C" cov_status cov_autotune_sinkhorn(cov_ctx* ctx, const float* x, int T,
         float lo[3], hi[3];
         for (int rep = 0; rep < 3 && r == COV_OK; ++rep) {
             r = timed(2, &lo[rep]);
-            if (r == COV_OK) r = timed(6, &hi[rep]);
+            if (r == COV_OK) r = timed(2 + n_diff, &hi[rep]);
         }
         if (r != COV_OK) break;
         std::sort(lo, lo + 3);
         std::sort(hi, hi + 3);
-        const double us = 1e3 * (hi[1] - lo[1]) / 4.0;
+        const double us = 1e3 * (hi[1] - lo[1]) / n_diff;
         if (sweep) {
             sweep[3 * k] = c.R;
             sweep[3 * k + 1] = c.cps;

@@ -35,6 +35,8 @@ struct cov_ctx {
     int ctas_per_sm = 8;
     int use_graph = 1;
     int use_tc = 2;            // tensor-core exponents: 0 off, 1 on, 2 for launches of >= 2^30 pairs
+    int batch_share = 12;      // cov_solve_batched: percent of the GPU's CTA slots a problem's all-pairs launches plan for
+    int plan_share = 100;      // the share the planner uses now (batch_share while a batch is enqueued)
     long long spin_limit = 1LL << 22;
     std::string last_cuda_error;
     cov_graph_cache solve_graph;

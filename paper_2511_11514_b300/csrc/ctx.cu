@@ -158,6 +158,13 @@ extern "C" cov_status cov_ctx_set_option(cov_ctx* ctx, int key, long long value)
             if (value < 0 || value > 2) return COV_ERR_INVALID_ARG;
             ctx->use_tc = (int)value;
             break;
+        case COV_OPT_BATCH_SHARE:
+            if (value < 1 || value > 100) return COV_ERR_INVALID_ARG;
+            ctx->batch_share = (int)value;
+            if (ctx->batch_graph.exec) cudaGraphExecDestroy(ctx->batch_graph.exec);
+            if (ctx->batch_graph.graph) cudaGraphDestroy(ctx->batch_graph.graph);
+            ctx->batch_graph = cov_graph_cache{};
+            break;
         default:
             return COV_ERR_INVALID_ARG;
     }

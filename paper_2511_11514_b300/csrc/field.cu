@@ -1204,7 +1204,9 @@ static cov_status run_pairs(cov_ctx* ctx, int d, int family, PairArgs* seg, cons
         launch_tc_d(d, PairLaunch{}, 0, st, &occ);
     else
         launch_pairs_d(d, R, family, PairLaunch{}, 0, st, &occ);
-    const int slots = std::max(1, std::min(ctx->num_sms * std::min(occ, ctx->ctas_per_sm), kMaxSlots));
+    // inside a batch many problems' launches share the GPU: plan each for its share of the slots
+    const int slots_all = std::max(1, std::min(ctx->num_sms * std::min(occ, ctx->ctas_per_sm), kMaxSlots));
+    const int slots = ctx->plan_share >= 100 ? slots_all : std::max(1, slots_all * ctx->plan_share / 100);
     const int nacc = family == M_SVGD ? d : ((family == M_WY || family == M_WX || family == M_GW) ? 2 + d : 2);
     // uniform plan; when it is one wave that already fills at least half the
     // slots, re-plan to fill them exactly (CUDA-core kernel)

@@ -487,9 +487,11 @@ extern "C" cov_status cov_solve_batched(cov_ctx* ctx, const cov_problem* probs, 
     if (!ctx->use_graph) {
         for (int k = 0; k < n_outer && r == COV_OK; ++k) {
             r = fork_streams(ctx, st, ctx->pool, K);
+            ctx->plan_share = ctx->batch_share;
             for (int p = 0; p < n_probs && r == COV_OK; ++p)
                 r = enqueue_iteration(ctx, &probs[p], nn[p], mm[p], bufs[p], rest[p], rest_bytes[p], u[p], s_out[p],
                                       ctx->pool[p % K]);
+            ctx->plan_share = 100;
             if (r == COV_OK) r = join_streams(ctx, ctx->pool, K, st);
         }
         return r;
@@ -519,9 +521,11 @@ extern "C" cov_status cov_solve_batched(cov_ctx* ctx, const cov_problem* probs, 
             return COV_ERR_CUDA;
         }
         r = fork_streams(ctx, cap, ctx->pool, K);
+        ctx->plan_share = ctx->batch_share;  // the problems' launches run side by side
         for (int p = 0; p < n_probs && r == COV_OK; ++p)
             r = enqueue_iteration(ctx, &probs[p], nn[p], mm[p], bufs[p], rest[p], rest_bytes[p], u[p], s_out[p],
                                   ctx->pool[p % K]);
+        ctx->plan_share = 100;
         if (r == COV_OK) r = join_streams(ctx, ctx->pool, K, cap);
         cudaGraph_t g = nullptr;
         const cudaError_t ce = cudaStreamEndCapture(cap, &g);

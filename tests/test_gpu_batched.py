@@ -12,6 +12,7 @@ from paper_2511_11514_b300 import workloads as wl
 pytestmark = pytest.mark.gpu
 
 
+
 def _problem(cov, inst, ydev):
     w = inst.wl
     if w.field == wl.FIELD_SVGD:
@@ -20,8 +21,14 @@ def _problem(cov, inst, ydev):
                             n_iter=w.n_iter)
 
 
-@pytest.mark.parametrize("use_graph", [1, 0])
-def test_batch_equals_problems_solved_alone(cov, ctx, use_graph):
+@pytest.mark.parametrize("use_graph,share", [(1, 100), (0, 100), (1, 0)])
+def test_batch_equals_problems_solved_alone(cov, ctx, use_graph, share):
+    """With every problem's launches planned for the whole GPU (share 100)
+    the batch runs exactly the single-problem kernels and plans, so each
+    problem's result equals cov_solve on it alone, bit for bit.  With the
+    default planning share the column splits differ, so the sums are taken
+    in another order: then the trajectories agree to FP32 rounding of the
+    field (1e-5 of the displacement)."""
     insts = wl.make_batch(7, seed=3, T_range=(37, 700), M_range=(50, 1500), K_range=(2, 5))
     for i in insts:
         if i.wl.field == wl.FIELD_SINKHORN:
@@ -34,6 +41,8 @@ def test_batch_equals_problems_solved_alone(cov, ctx, use_graph):
     probs = [_problem(cov, i, y) for i, y in zip(insts, ys)]
     n_outer = 3
     ctx.set_option(cov.OPT_USE_GRAPH, use_graph)
+    if share:
+        ctx.set_option(cov.OPT_BATCH_SHARE, share)
     try:
         us = [dev64(i.u0) for i in insts]
         ss = cov.cov_solve_batched(ctx, probs, n_outer, us)
@@ -41,10 +50,15 @@ def test_batch_equals_problems_solved_alone(cov, ctx, use_graph):
         for i, pr, ub, sb in zip(insts, probs, us, ss):
             u1 = dev64(i.u0)
             s1 = cov.cov_solve(ctx, pr, n_outer, u1)
-            np.testing.assert_array_equal(host(sb), host(s1))
-            np.testing.assert_array_equal(host(ub), host(u1))
+            if share == 100:
+                np.testing.assert_array_equal(host(sb), host(s1))
+                np.testing.assert_array_equal(host(ub), host(u1))
+            else:
+                s_init = host(cov.cov_rollout(ctx, i.wl.model, i.s0, dev64(i.u0), i.wl.dt))
+                assert rel_norm(host(sb) - s_init, host(s1) - s_init) <= 1e-5
     finally:
         ctx.set_option(cov.OPT_USE_GRAPH, 1)
+        ctx.set_option(cov.OPT_BATCH_SHARE, cov.BATCH_SHARE_DEFAULT)
     assert ctx.device_status() == (cov.COV_OK, 0)
 
 
