@@ -44,17 +44,17 @@ DEFAULT_WORKLOAD = wl.SINKHORN_UNICYCLE_T65536.name
 L2_FLUSH_BYTES = 256 << 20
 # Algorithmic FP32-pipe instructions per Sinkhorn pair evaluation (base-2,
 # prescaled, column term folded) in the fixed-offset form the iteration runs
-# in from its third step: 2 FMA for the d = 2 inner product, the offset
+# in from its second step: 2 FMA for the d = 2 inner product, the offset
 # subtraction and the accumulation; one exponential (MUFU ex2).  With 128
 # FP32 lanes and 32 ex2 per SM and clock both pipes bound at 32 pairs/clk/SM.
 FP32_OPS_PER_PAIR = 4
 SM_COUNT_NOMINAL = 148
 SM_MAX_MHZ_NOMINAL = 2032.0
 FP32_LANES_PER_SM_CLK = 128
-# DRAM bytes (read + write) per launch of pairs_kernel at the benchmark
-# workload from one ncu capture of the current kernel (fixed-offset form):
-# 388 KB (g + p launch) and 291 KB (f launch), no writes.
-PAIRS_TRAFFIC_BYTES = 339456
+# DRAM bytes (read + write) per launch of pairs_kernel at the double-
+# integrator workload from one ncu capture of the current kernel (fixed-
+# offset form): 393 KB (g + p launch) and 290 KB (f launch), no writes.
+PAIRS_TRAFFIC_BYTES = 341504
 # The same for lse_tc_kernel at T = 65536, M = 262144 (the default path at
 # that size): 9.47 MB (g + p launch) and 13.43 MB (f launch), no writes.
 TC_LARGE_TRAFFIC_BYTES = 11454208
