@@ -368,7 +368,12 @@ static cov_status cov::solve_impl(cov_ctx* ctx, const cov_problem* prob, int n_o
 // ---------------------------------------------------------------------------
 namespace cov {
 
-static constexpr int kPoolStreams = 32;
+// Streams the batch's branches are captured on (problems p, p + K, ... of
+// one stream run one after another; build flag -DCOV_POOL_STREAMS=K).
+#ifndef COV_POOL_STREAMS
+#define COV_POOL_STREAMS 64
+#endif
+static constexpr int kPoolStreams = COV_POOL_STREAMS;
 
 static size_t problem_ws_bytes(const cov_problem* P, int n, int m) {
     const size_t solve = solve_buffers_bytes(P->T, P->d, n, m, prob_M(P));
