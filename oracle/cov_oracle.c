@@ -1191,6 +1191,69 @@ int orc_solve_backward(int model, int T, double dt, int d, const double* y,
  * divergence of the final positions to (y_loss, b_loss); its gradient with
  * respect to the final positions is -(1/T) times the field at converged
  * potentials (the envelope theorem, exact at convergence). */
+/* Reverse sweep of a Stein-field solve (Eq. 4 with a mixture reference) on a
+ * time-invariant model, the same steps as orc_solve_backward: at outer
+ * iteration k the LQR adjoint of eta ubar gives the field's cotangent, the
+ * Stein field's reverse mode at x^{k-1} (with the mixture score at x^{k-1})
+ * gives the cotangent of the points (kernel and score paths) and of the
+ * mixture, and the rollout adjoint carries the points' cotangent to u and
+ * s_0.  The mixture gradients of every outer iteration are summed. */
+int orc_solve_backward_svgd(int model, int T, double dt, int d, int K, const double* w,
+                            const double* mu, const double* sigma, double h,
+                            const double* Q, const double* R, double eta, int n_outer,
+                            const double* s_hist, const double* sbar_K, double* wbar,
+                            double* mubar, double* sigmabar, double* s0bar,
+                            double* u0bar) {
+    int n, m;
+    if (orc_model_dims(model, &n, &m) != 0 || model == ORC_UNICYCLE || d > n) return -1;
+    const size_t us = (size_t)T * m, ss = (size_t)(T + 1) * n;
+    double* A = (double*)malloc(sizeof(double) * (size_t)T * n * n);
+    double* Bm = (double*)malloc(sizeof(double) * (size_t)T * n * m);
+    double* ubar = (double*)calloc(us, sizeof(double));
+    double* ub2 = (double*)calloc(us, sizeof(double));
+    double* v = (double*)calloc(us, sizeof(double));
+    double* u0 = (double*)calloc(us, sizeof(double));
+    double* sbar = (double*)calloc(ss, sizeof(double));
+    double* x = (double*)malloc(sizeof(double) * (size_t)T * d);
+    double* score = (double*)malloc(sizeof(double) * (size_t)T * d);
+    double* xbar = (double*)calloc((size_t)T * d, sizeof(double));
+    double* scb = (double*)calloc((size_t)T * d, sizeof(double));
+    double* fa = (double*)calloc((size_t)T * d, sizeof(double));
+    double* abb = (double*)calloc((size_t)T * n, sizeof(double));
+    double* wk = (double*)malloc(sizeof(double) * K);
+    double* mk = (double*)malloc(sizeof(double) * (size_t)K * d);
+    double* sk = (double*)malloc(sizeof(double) * K);
+    for (int k = 0; k < K; ++k) wbar[k] = sigmabar[k] = 0.0;
+    for (int k = 0; k < K * d; ++k) mubar[k] = 0.0;
+    /* A, B do not depend on (s, u) for these models: take them anywhere */
+    orc_linearize(model, s_hist, u0, T, dt, A, Bm);
+    orc_rollout_vjp(model, s_hist, u0, T, dt, sbar_K, ubar, s0bar);
+    for (int k = n_outer; k >= 1; --k) {
+        const double* Sp = s_hist + (size_t)(k - 1) * ss;
+        for (size_t r = 0; r < us; ++r) v[r] = eta * ubar[r];
+        orc_lqr_vjp(A, Bm, Q, R, v, T, n, m, abb);
+        for (int i = 0; i < T; ++i)
+            for (int c = 0; c < d; ++c) {
+                fa[(size_t)i * d + c] = abb[(size_t)i * n + c];
+                x[(size_t)i * d + c] = Sp[(size_t)(i + 1) * n + c];
+            }
+        orc_gmm_score(x, T, d, K, w, mu, sigma, score);
+        orc_svgd_field_vjp(x, T, d, score, h, fa, xbar, scb);
+        orc_gmm_score_vjp(x, T, d, K, w, mu, sigma, scb, xbar, wk, mk, sk);
+        for (int c = 0; c < K; ++c) wbar[c] += wk[c], sigmabar[c] += sk[c];
+        for (int c = 0; c < K * d; ++c) mubar[c] += mk[c];
+        for (size_t r = 0; r < ss; ++r) sbar[r] = 0.0;
+        for (int i = 0; i < T; ++i)
+            for (int c = 0; c < d; ++c) sbar[(size_t)(i + 1) * n + c] = xbar[(size_t)i * d + c];
+        orc_rollout_vjp(model, Sp, u0, T, dt, sbar, ub2, s0bar);
+        for (size_t r = 0; r < us; ++r) ubar[r] += ub2[r];
+    }
+    if (u0bar) memcpy(u0bar, ubar, sizeof(double) * us);
+    free(A); free(Bm); free(ubar); free(ub2); free(v); free(u0); free(sbar);
+    free(x); free(score); free(xbar); free(scb); free(fa); free(abb); free(wk); free(mk); free(sk);
+    return 0;
+}
+
 double orc_solve_sinkhorn_grad(int model, int T, double dt, const double* s0,
                                int d, const double* y, const double* b, int M,
                                double eps, int n_iter, const double* Q,

@@ -139,6 +139,18 @@ void orc_rollout_vjp(int model, const double* s, const double* u, int T,
  * reference samples y [M][d], raw weights b [M] (may be NULL) and s0 [n].
  * Time-invariant models only (single / double integrator).  Returns L. */
 int orc_solve_backward(int model, int T, double dt, int d, const double* y, const double* b, int M, double eps, int n_iter, const double* Q, const double* R, double eta, int n_outer, const double* s_hist, const double* sbar_K, double* ybar, double* bbar, double* s0bar, double* u0bar);
+/* Reverse sweep of a Stein-field solve with a mixture reference (time-
+ * invariant model): the gradients of L(s^K) given dL/ds^K = sbar_K and the
+ * checkpoints s_hist [n_outer][T+1][n], with respect to the mixture's raw
+ * weights wbar [K], means mubar [K][d], standard deviations sigmabar [K]
+ * (summed over the outer iterations), s0bar [n] (accumulated into) and
+ * u0bar [T][m] (or NULL).  Returns 0, or -1 for an unsupported model. */
+int orc_solve_backward_svgd(int model, int T, double dt, int d, int K, const double* w,
+                            const double* mu, const double* sigma, double h,
+                            const double* Q, const double* R, double eta, int n_outer,
+                            const double* s_hist, const double* sbar_K, double* wbar,
+                            double* mubar, double* sigmabar, double* s0bar,
+                            double* u0bar);
 double orc_solve_sinkhorn_grad(int model, int T, double dt, const double* s0,
                                int d, const double* y, const double* b, int M,
                                double eps, int n_iter, const double* Q,

@@ -93,6 +93,8 @@ def _declare(L):
         "orc_rollout_vjp": (None, [_i, _D, _D, _i, _d, _D, _D, _D]),
         "orc_solve_backward": (_i, [_i, _i, _d, _i, _D, _D, _i, _d, _i, _D, _D, _d, _i, _D, _D,
                                     _D, _D, _D, _D]),
+        "orc_solve_backward_svgd": (_i, [_i, _i, _d, _i, _i, _D, _D, _D, _d, _D, _D, _d, _i, _D, _D, _D, _D, _D,
+                                         _D, _D]),
         "orc_solve_sinkhorn_grad": (_d, [_i, _i, _d, _D, _i, _D, _D, _i, _d, _i, _D, _D, _d, _i,
                                          _D, _D, _D, _i, _d, _D, _D, _D]),
     }
@@ -468,3 +470,24 @@ def solve_backward(model, dt, d, y, b, eps, n_iter, Q, R, eta, s_hist, sbar_K):
     if rc != 0:
         raise ValueError("orc_solve_backward: bad arguments")
     return ybar, bbar, s0bar, u0bar
+
+
+def solve_backward_svgd(model, dt, d, gmm, h, Q, R, eta, s_hist, sbar_K):
+    """Reverse sweep of a Stein-field solve with the mixture gmm = (w, mu,
+    sigma) through K = len(s_hist) outer iterations given the checkpoints
+    s_hist [K][T+1][n] and dL/ds^K: returns (wbar [K], mubar [K][d],
+    sigmabar [K], s0bar [n], u0bar [T][m])."""
+    n, m = MODEL_DIMS[model]
+    w, mu, sigma = (_f64(v) for v in gmm)
+    Q, R, sh, sb = _f64(Q), _f64(R), _f64(s_hist), _f64(sbar_K)
+    n_outer = sh.shape[0]
+    T = sh.shape[1] - 1
+    K = w.size
+    wbar, mubar, sigbar = np.zeros(K), np.zeros((K, d)), np.zeros(K)
+    s0bar, u0bar = np.zeros(n), np.zeros((T, m))
+    rc = lib().orc_solve_backward_svgd(int(model), T, float(dt), int(d), K, _p(w), _p(mu), _p(sigma), float(h),
+                                       _p(Q), _p(R), float(eta), int(n_outer), _p(sh), _p(sb), _p(wbar), _p(mubar),
+                                       _p(sigbar), _p(s0bar), _p(u0bar))
+    if rc != 0:
+        raise ValueError("orc_solve_backward_svgd: bad arguments")
+    return wbar, mubar, sigbar, s0bar, u0bar

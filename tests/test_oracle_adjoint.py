@@ -213,3 +213,48 @@ def test_backward_with_checkpoints_matches_central_differences_in_u0(orc):
     e = np.zeros(4)
     e[1] = 1.0
     assert s0bar[1] == pytest.approx(_fd(lambda ss: fun(s0=ss), kw["s0"], e, h=1e-5), rel=1e-6)
+
+
+def _stein_history(orc, model, dt, s0, u0, gmm, h, Q, R, eta, K):
+    """Checkpoints s^0..s^{K-1} and the final trajectory of a Stein solve."""
+    u = np.array(u0, dtype=np.float64)
+    hist = [orc.rollout(model, s0, u, dt)]
+    for _ in range(K):
+        u, s = orc.solve(model, dt, s0, u, wl.FIELD_SVGD, Q, R, eta, 1, gmm=gmm, h=h)
+        hist.append(s)
+    return np.stack(hist[:-1]), hist[-1]
+
+
+@pytest.mark.parametrize("model", [wl.SINGLE_INT, wl.DOUBLE_INT])
+def test_stein_solve_backward_matches_central_differences(orc, model):
+    """<c, s^K> through K = 3 outer iterations of a Stein-field solve,
+    differentiated by central differences along random directions in the
+    mixture's raw weights, means and standard deviations, s_0 and u_0
+    separately, against the oracle's reverse sweep."""
+    T, K, dt, h, eta = 24, 3, 0.1, 0.12, 0.01
+    n, m = wl.MODEL_DIMS[model]
+    w, mu, sigma = wl.gmm_params(3, seed=81)
+    if model == wl.SINGLE_INT:
+        s0, u0 = wl.line_controls_single(T, dt, seed=82)
+    else:
+        s0, u0 = wl.double_int_init(T, dt)
+    Q = wl.coverage_Q(model)
+    R = 0.05 * np.eye(m)
+    c = wl.rng(83).standard_normal((T + 1, n))
+
+    def L(w_, mu_, sig_, s0_, u0_):
+        _, sK = _stein_history(orc, model, dt, s0_, u0_, (w_, mu_, sig_), h, Q, R, eta, K)
+        return float(np.sum(c * sK))
+
+    hist, _ = _stein_history(orc, model, dt, s0, u0, (w, mu, sigma), h, Q, R, eta, K)
+    wb, mb, sb, s0b, u0b = orc.solve_backward_svgd(model, dt, 2, (w, mu, sigma), h, Q, R, eta, hist, c)
+    r = wl.rng(84)
+    for grad, base, fun in ((wb, w, lambda v: L(v, mu, sigma, s0, u0)),
+                            (mb, mu, lambda v: L(w, v, sigma, s0, u0)),
+                            (sb, sigma, lambda v: L(w, mu, v, s0, u0)),
+                            (s0b, np.asarray(s0, dtype=np.float64), lambda v: L(w, mu, sigma, v, u0)),
+                            (u0b, np.asarray(u0, dtype=np.float64), lambda v: L(w, mu, sigma, s0, v))):
+        dv = r.standard_normal(np.shape(base))
+        fd = _fd(fun, np.asarray(base, dtype=np.float64), dv)
+        assert float(np.sum(grad * dv)) == pytest.approx(fd, rel=1e-6, abs=1e-9)
+    assert abs(float(np.dot(w, wb))) <= 1e-9 * float(np.abs(w * wb).sum())
