@@ -517,6 +517,26 @@ COV_API cov_status cov_solve_backward(cov_ctx* ctx, const cov_problem* prob,
                                       float* ybar, float* bbar, double* s0bar,
                                       double* u0bar, cov_stream_t stream);
 
+/* Gradient of a scalar loss L(s^K) through K = n_outer outer iterations of a
+ * Stein-field solve (Eq. 4, Sec. II-C) with a Gaussian-mixture reference on
+ * a time-invariant model (COV_SINGLE_INT, COV_DOUBLE_INT; a pixel-density
+ * reference or the unicycle is COV_ERR_UNSUPPORTED): the reverse sweep of
+ * cov_solve_backward with the Stein field's reverse mode (cov_field_svgd_vjp
+ * through the mixture score) in place of the Sinkhorn one.
+ *   u0, s_hist, sbar_K, s0bar, u0bar as cov_solve_backward (s_hist from
+ *          cov_solve_checkpointed without COV_CKPT_RECORD, or NULL: rebuilt
+ *          by replaying the forward)
+ *   wbar [K], mubar [K][d], sigmabar [K] FP32 device or NULL, written: dL with
+ *          respect to the mixture's raw weights, means and standard
+ *          deviations (prob->gmm), summed over the outer iterations
+ * Workspace: cov_workspace_size_backward(prob, K, COV_BACKWARD_CHECKPOINTS
+ * or COV_BACKWARD_REPLAY). */
+COV_API cov_status cov_solve_backward_svgd(cov_ctx* ctx, const cov_problem* prob,
+                                           int n_outer, const double* u0,
+                                           const double* s_hist, const double* sbar_K,
+                                           float* wbar, float* mubar, float* sigmabar,
+                                           double* s0bar, double* u0bar, cov_stream_t stream);
+
 /* ---- measurement -------------------------------------------------------- */
 
 /* Issue-rate probes for the roofline of the all-pairs kernels: each runs

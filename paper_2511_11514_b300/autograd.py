@@ -1,7 +1,8 @@
 """Differentiable coverage synthesis on the libcov adjoint (torch.autograd).
 
-Three pieces, each a thin ``torch.autograd.Function`` over C-ABI calls (the
-forward and backward arithmetic runs in libcov's kernels):
+Four pieces, each a thin ``torch.autograd.Function`` over C-ABI calls (the
+forward and backward arithmetic runs in libcov's kernels), or input
+reparameterisation:
 
 * ``CoverageSolve``: the final trajectory s^K after K outer iterations of
   Sec. II-C (Sinkhorn field, time-invariant model) as a function of the
@@ -9,6 +10,9 @@ forward and backward arithmetic runs in libcov's kernels):
   ``cov_solve_checkpointed`` keeps the trajectory entering every outer
   iteration; backward: ``cov_solve_backward`` runs the reverse sweep (rollout,
   LQR and field adjoints) from those checkpoints.
+* ``CoverageSolveStein``: the same for the Stein field (Eq. 4) with a
+  Gaussian-mixture reference, as a function of the mixture's weights, means
+  and standard deviations and the initial state (``cov_solve_backward_svgd``).
 * ``SinkhornLoss``: the debiased Sinkhorn divergence of Eq. 6 between the
   samples x and a held-out reference set (uniform weights).  Give it a
   context of its own: a field call on the solve's context overwrites the
@@ -67,6 +71,42 @@ class CoverageSolve(torch.autograd.Function):
                                                      g_K.detach().double().contiguous(), hist, fctx.token, y, b)
         dev, dt = fctx.s0_meta
         return (ybar, bbar if fctx.has_b else None, s0bar.to(device=dev, dtype=dt), u0bar, None, None)
+
+
+class CoverageSolveStein(torch.autograd.Function):
+    """s_K = CoverageSolveStein.apply(w, mu, sigma, s0, u0, spec, ctx): the
+    final trajectory after K outer iterations of a Stein-field solve (Eq. 4,
+    Sec. II-C) with the Gaussian-mixture reference (w [K] raw weights, mu
+    [K, d], sigma [K]; any device, float) on a time-invariant model, as a
+    function of the mixture and the initial state s0 [n] (float64).
+    spec: dict(model, dt, Q, R, eta, h, n_outer).  The forward keeps the
+    trajectory entering every outer iteration (cov_solve_checkpointed); the
+    backward runs cov_solve_backward_svgd from those checkpoints.  Returns
+    s^K [T+1, n] float64 CUDA; the gradient for u0 [T, m] is returned too."""
+
+    @staticmethod
+    def forward(fctx, w, mu, sigma, s0, u0, spec, cctx):
+        T, m = u0.shape
+        d = mu.shape[1]
+        gmm = tuple(v.detach().cpu().float().numpy() for v in (w, mu, sigma))
+        P = cov.make_problem(spec["model"], T, spec["dt"], s0.detach().cpu().double().numpy(), cov.FIELD_SVGD,
+                             spec["Q"], spec["R"], spec["eta"], d=d, gmm=gmm, h=spec["h"])
+        u = u0.detach().clone().contiguous()
+        s_K, hist = cov.cov_solve_checkpointed(cctx, P, spec["n_outer"], u)
+        fctx.problem = P
+        fctx.cctx = cctx
+        fctx.n_outer = spec["n_outer"]
+        fctx.meta = [(v.device, v.dtype) for v in (w, mu, sigma, s0)]
+        fctx.save_for_backward(u0.detach(), hist)
+        return s_K
+
+    @staticmethod
+    def backward(fctx, g_K):
+        u0, hist = fctx.saved_tensors
+        wb, mb, sb, s0b, u0b = cov.cov_solve_backward_svgd(fctx.cctx, fctx.problem, fctx.n_outer, u0,
+                                                           g_K.detach().double().contiguous(), s_hist=hist)
+        out = [t.to(device=dv, dtype=dt) for t, (dv, dt) in zip((wb, mb, sb, s0b), fctx.meta)]
+        return (*out, u0b, None, None)
 
 
 class SinkhornLoss(torch.autograd.Function):

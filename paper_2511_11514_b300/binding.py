@@ -41,7 +41,7 @@ EXPORTS = (
     "cov_lqr_vjp", "cov_rollout_vjp", "cov_solve_checkpointed", "cov_workspace_size_backward",
     "cov_solve_backward", "cov_field_sinkhorn_annealed", "cov_density_score", "cov_autotune_sinkhorn",
     "cov_workspace_size_divergence", "cov_sinkhorn_divergence", "cov_workspace_size_svgd_vjp",
-    "cov_field_svgd_vjp",
+    "cov_field_svgd_vjp", "cov_solve_backward_svgd",
 )
 
 
@@ -116,6 +116,7 @@ def load(path: str = LIB_PATH):
         "cov_workspace_size_divergence": (_sz, [_i, _i, _i]),
         "cov_sinkhorn_divergence": (_i, [_P, _P, _i, _P, _P, _i, _i, _f, _i, _P, _i, _P, _P, _P]),
         "cov_workspace_size_svgd_vjp": (_sz, [_i, _i, _i]),
+        "cov_solve_backward_svgd": (_i, [_P, ctypes.POINTER(cov_problem), _i, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
         "cov_field_svgd_vjp": (_i, [_P, _P, _i, _i, _P, ctypes.POINTER(cov_gmm), _f, _P, _P, _P, _P, _P, _P,
                                     _P]),
     }
@@ -639,6 +640,41 @@ def cov_solve_backward(ctx: Context, problem, n_outer, u0, sbar_K, s_hist=None, 
                                    _ptr(u0bar, torch.float64, (T, m), "u0bar"), _stream(stream))
     ctx._check(st, "cov_solve_backward")
     return ybar, bbar, s0bar, u0bar
+
+
+def cov_solve_backward_svgd(ctx: Context, problem, n_outer, u0, sbar_K, s_hist=None, stream=None):
+    """(wbar [K], mubar [K, d], sigmabar [K], s0bar [n], u0bar [T, m]) = dL/d(mixture
+    weights, means, standard deviations, s0, u0) of a Stein-field solve with a
+    mixture reference, given dL/ds^K = sbar_K and the checkpoints (replayed
+    from u0 when None)."""
+    P, keep = problem
+    n, m = MODEL_DIMS[P.model]
+    T, K, d = P.T, P.gmm.K, P.d
+    mode = BACKWARD_REPLAY if s_hist is None else BACKWARD_CHECKPOINTS
+    need = int(load().cov_workspace_size_backward(ctypes.byref(P), int(n_outer), mode))
+    if need == 0:
+        raise CovError(COV_ERR_UNSUPPORTED, "cov_solve_backward_svgd (Stein field, mixture, time-invariant model)")
+    ctx.reserve(need)
+    dev = u0.device
+    wbar = torch.empty(K, device=dev, dtype=torch.float32)
+    mubar = torch.empty((K, d), device=dev, dtype=torch.float32)
+    sigmabar = torch.empty(K, device=dev, dtype=torch.float32)
+    s0bar = torch.empty(n, device=dev, dtype=torch.float64)
+    u0bar = torch.empty((T, m), device=dev, dtype=torch.float64)
+    hist_p = None
+    if s_hist is not None:
+        hist_p = _ptr(s_hist, torch.float64, name="s_hist")
+        if s_hist.shape[0] < int(n_outer) or tuple(s_hist.shape[1:]) != (T + 1, n):
+            raise ValueError("s_hist must be [n_outer, T+1, n]")
+    st = load().cov_solve_backward_svgd(ctx.h, ctypes.byref(P), int(n_outer), _ptr(u0, torch.float64, (T, m), "u0"),
+                                        hist_p, _ptr(sbar_K, torch.float64, (T + 1, n), "sbar_K"),
+                                        _ptr(wbar, torch.float32, (K,), "wbar"),
+                                        _ptr(mubar, torch.float32, (K, d), "mubar"),
+                                        _ptr(sigmabar, torch.float32, (K,), "sigmabar"),
+                                        _ptr(s0bar, torch.float64, (n,), "s0bar"),
+                                        _ptr(u0bar, torch.float64, (T, m), "u0bar"), _stream(stream))
+    ctx._check(st, "cov_solve_backward_svgd")
+    return wbar, mubar, sigmabar, s0bar, u0bar
 
 
 # -- graph-friendly forward/backward pair (used by autograd) -------------------

@@ -172,6 +172,14 @@ cov_status density_score_launch(cov_ctx* ctx, const float* map, int H, int W, co
                                 float* score, cudaStream_t stream);
 cov_status svgd_field_ws(cov_ctx* ctx, void* ws, size_t ws_bytes, const float* x, int x_ld, int T, int d,
                          const float* score, const cov_gmm* gmm, float h, float* a_out, cudaStream_t stream);
+// Reverse mode of the Stein field (svgd_vjp.cu) on an explicit workspace:
+// x, abar [T][d] row-major; score [T][d] or nullptr (then the mixture's);
+// xbar [T][d] written; sbar [T][d] or nullptr; the mixture gradients
+// wbar [K], mubar [K][d], sigmabar [K] written (accumulate = 0) or added to.
+size_t svgd_vjp_ws_bytes(int T, int d, int K, int num_sms);
+cov_status svgd_vjp_ws(cov_ctx* ctx, void* ws, size_t ws_bytes, const float* x, int T, int d, const float* score,
+                       const cov_gmm* gmm, float h, const float* abar, float* xbar, float* sbar, float* wbar,
+                       float* mubar, float* sigmabar, int accumulate, cudaStream_t st);
 cov_status lqr_track_ws(cov_ctx* ctx, void* ws, size_t ws_bytes, const double* A, const double* B,
                         const double* Q, const double* R, const double* abar, int T, int n, int m,
                         double* v_out, double* z_out, cudaStream_t stream);

@@ -617,6 +617,10 @@ static bool backward_supported(const cov_problem* P) {
     return P->field == COV_FIELD_SINKHORN && model_is_lti(P->model) && P->d <= 3 && P->warm == 0 &&
            !(P->eps_start > P->eps);
 }
+// Stein field with a mixture reference on a time-invariant model.
+static bool backward_svgd_supported(const cov_problem* P) {
+    return P->field == COV_FIELD_SVGD && model_is_lti(P->model) && !P->density;
+}
 
 // ws == nullptr only measures (L->needed).
 static void carve_layout(void* ws, size_t ws_bytes, const cov_problem* P, int n, int m, int K, int mode,
@@ -633,9 +637,14 @@ static void carve_layout(void* ws, size_t ws_bytes, const cov_problem* P, int n,
     L->bb = carve_back(cv, T, d, n, m, mode == BM_REPLAY ? K : 0);
     const size_t used = round_up(cv.off, 256);
     size_t rest = std::max(lqr_adj_ws_bytes(T, n, m), lqr_ws_bytes(T, n, m));
-    rest = std::max(rest, mode == BM_TAPED ? sinkhorn_vjp_bytes_given(T, P->M, d)
-                                           : sinkhorn_vjp_bytes(T, P->M, d, P->n_iter));
-    if (mode == BM_REPLAY) rest = std::max(rest, sinkhorn_ws_bytes(T, P->M, d));
+    if (P->field == COV_FIELD_SVGD) {
+        rest = std::max(rest, svgd_vjp_ws_bytes(T, d, P->gmm.K, 1024));
+        if (mode == BM_REPLAY) rest = std::max(rest, svgd_ws_bytes(T, d));
+    } else {
+        rest = std::max(rest, mode == BM_TAPED ? sinkhorn_vjp_bytes_given(T, P->M, d)
+                                               : sinkhorn_vjp_bytes(T, P->M, d, P->n_iter));
+        if (mode == BM_REPLAY) rest = std::max(rest, sinkhorn_ws_bytes(T, P->M, d));
+    }
     L->needed = used + rest + 4096;
     L->rest = ws ? static_cast<char*>(ws) + used : nullptr;
     L->rest_bytes = ws_bytes > used ? ws_bytes - used : 0;
@@ -753,7 +762,7 @@ extern "C" cov_status cov_solve_checkpointed(cov_ctx* ctx, const cov_problem* pr
 extern "C" size_t cov_workspace_size_backward(const cov_problem* prob, int n_outer, int mode) {
     int n, m;
     if (!prob || n_outer < 0 || mode < 0 || mode > 2 || cov::validate(prob, &n, &m) != COV_OK ||
-        !cov::backward_supported(prob))
+        !(cov::backward_supported(prob) || (cov::backward_svgd_supported(prob) && mode != cov::BM_TAPED)))
         return 0;
     cov::BackLayout L;
     cov::carve_layout(nullptr, 0, prob, n, m, n_outer, mode, &L);
@@ -850,6 +859,98 @@ extern "C" cov_status cov_solve_backward(cov_ctx* ctx, const cov_problem* prob, 
     key = fnv(&mode, sizeof(mode), key);
     const void* ptrs[9] = {u0, s_hist, sbar_K, ybar, bbar, s0bar, u0bar, ctx->ws,
                            reinterpret_cast<const void*>(ctx->ws_bytes)};
+    key = fnv(ptrs, sizeof(ptrs), key);
+    return run_cached_graph(ctx, ctx->back_graph, key, stream0, work);
+}
+
+// Gradient through K outer iterations of a Stein-field solve with a mixture
+// reference (time-invariant model): the reverse sweep of cov_solve_backward
+// with the Stein field's reverse mode in place of the Sinkhorn one; the
+// mixture gradients of every outer iteration are summed.
+extern "C" cov_status cov_solve_backward_svgd(cov_ctx* ctx, const cov_problem* prob, int n_outer, const double* u0,
+                                              const double* s_hist, const double* sbar_K, float* wbar, float* mubar,
+                                              float* sigmabar, double* s0bar, double* u0bar, cov_stream_t stream) {
+    using namespace cov;
+    int n, m;
+    if (!ctx || n_outer < 0 || !u0 || !sbar_K || !s0bar) return COV_ERR_INVALID_ARG;
+    cov_status r = validate(prob, &n, &m);
+    if (r != COV_OK) return r;
+    if (!backward_svgd_supported(prob)) return COV_ERR_UNSUPPORTED;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return COV_ERR_CUDA;
+    const int T = prob->T, d = prob->d, K = n_outer, KG = prob->gmm.K;
+    const int mode = s_hist ? BM_GIVEN : BM_REPLAY;
+    BackLayout L;
+    carve_layout(nullptr, 0, prob, n, m, K, mode, &L);
+    if (!ctx->ws || L.needed > ctx->ws_bytes) return COV_ERR_WORKSPACE;
+    carve_layout(ctx->ws, ctx->ws_bytes, prob, n, m, K, mode, &L);
+    ctx->tape_key = 0;  // the backward buffers overlap the record slots
+    const SolveBufs& sb = L.sb;
+    const BackBufs& bb = L.bb;
+    void* rest = L.rest;
+    const size_t rest_bytes = L.rest_bytes;
+    cudaStream_t stream0 = (cudaStream_t)stream;
+    const size_t ss = (size_t)(T + 1) * n;
+    const int nb = (T + 256) / 256;
+    r = ensure_lti_gains(ctx, prob, n, m, sb, sbar_K, u0, stream0);
+    if (r != COV_OK) return r;
+    auto work = [&](cudaStream_t st) -> cov_status {
+        cov_status q = COV_OK;
+        const double* hist = s_hist;
+        if (mode == BM_REPLAY) {
+            // rebuild the checkpoints s^0..s^{K-1} from u0
+            if (cuda_failed(ctx, cudaMemcpyAsync(bb.u, u0, sizeof(double) * T * m, cudaMemcpyDeviceToDevice, st)))
+                return COV_ERR_CUDA;
+            if (K > 0) {
+                q = update_rollout(ctx, prob->model, prob->s0, bb.u, nullptr, 0.0, T, prob->dt, bb.hist, st);
+                if (q != COV_OK) return q;
+            }
+            for (int k = 1; k < K; ++k) {
+                double* sk = bb.hist + (size_t)k * ss;
+                if (cuda_failed(ctx, cudaMemcpyAsync(sk, sk - ss, sizeof(double) * ss, cudaMemcpyDeviceToDevice, st)))
+                    return COV_ERR_CUDA;
+                q = enqueue_iteration(ctx, prob, n, m, sb, rest, rest_bytes, bb.u, sk, st);
+                if (q != COV_OK) return q;
+            }
+            hist = bb.hist;
+        }
+        q = rollout_vjp_ws(ctx, rest, rest_bytes, n, m, sb.A, sb.B, sbar_K, T, bb.ubar, s0bar, st);
+        if (q != COV_OK) return q;
+        if (K == 0) {
+            if ((wbar && cuda_failed(ctx, cudaMemsetAsync(wbar, 0, sizeof(float) * KG, st))) ||
+                (mubar && cuda_failed(ctx, cudaMemsetAsync(mubar, 0, sizeof(float) * KG * d, st))) ||
+                (sigmabar && cuda_failed(ctx, cudaMemsetAsync(sigmabar, 0, sizeof(float) * KG, st))))
+                return COV_ERR_CUDA;
+        }
+        const int Tm = T * m;
+        for (int k = K; k >= 1; --k) {
+            launch_pdl(back_scale_kernel, dim3((Tm + 255) / 256), dim3(256), 0, st, bb.ubar, prob->eta, Tm, bb.vbar);
+            q = lqr_vjp_ws(ctx, rest, rest_bytes, n, m, sb.B, sb.gains, prob->Q, bb.vbar, T, bb.abb, st);
+            if (q != COV_OK) return q;
+            launch_pdl(narrow_kernel, dim3(nb), dim3(256), 0, st, bb.abb, T, n, d, bb.abf);
+            launch_pdl(extract_kernel, dim3(nb), dim3(256), 0, st, hist + (size_t)(k - 1) * ss, T, n, d, sb.x);
+            q = svgd_vjp_ws(ctx, rest, rest_bytes, sb.x, T, d, nullptr, &prob->gmm, prob->h, bb.abf, bb.xbar, nullptr,
+                            wbar, mubar, sigmabar, k != K ? 1 : 0, st);
+            if (q != COV_OK) return q;
+            launch_pdl(lift_bar_kernel, dim3(nb), dim3(256), 0, st, bb.xbar, T, n, d, bb.sbar);
+            q = rollout_vjp_ws(ctx, rest, rest_bytes, n, m, sb.A, sb.B, bb.sbar, T, bb.ub2, bb.lam0, st);
+            if (q != COV_OK) return q;
+            launch_pdl(back_accum_kernel, dim3((Tm + 255) / 256), dim3(256), 0, st, bb.ubar, bb.ub2, Tm, s0bar,
+                       bb.lam0, n);
+        }
+        if (u0bar &&
+            cuda_failed(ctx, cudaMemcpyAsync(u0bar, bb.ubar, sizeof(double) * Tm, cudaMemcpyDeviceToDevice, st)))
+            return COV_ERR_CUDA;
+        return cuda_failed(ctx, cudaGetLastError()) ? COV_ERR_CUDA : COV_OK;
+    };
+    uint64_t key = 6700417ull;
+    key = fnv(prob, sizeof(cov_problem), key);
+    key = fnv(prob->gmm.w, sizeof(float) * KG, key);
+    key = fnv(prob->gmm.mu, sizeof(float) * KG * d, key);
+    key = fnv(prob->gmm.sigma, sizeof(float) * KG, key);
+    key = fnv(&K, sizeof(K), key);
+    key = fnv(&mode, sizeof(mode), key);
+    const void* ptrs[10] = {u0, s_hist, sbar_K, wbar, mubar, sigmabar, s0bar, u0bar, ctx->ws,
+                            reinterpret_cast<const void*>(ctx->ws_bytes)};
     key = fnv(ptrs, sizeof(ptrs), key);
     return run_cached_graph(ctx, ctx->back_graph, key, stream0, work);
 }

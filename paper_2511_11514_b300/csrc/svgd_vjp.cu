@@ -344,7 +344,7 @@ __global__ void __launch_bounds__(kGThreads) gmm_vjp_kernel(const float* __restr
 
 // Mixture gradients: the per-CTA sums added in CTA order.
 __global__ void gmm_vjp_sum_kernel(const double* __restrict__ gpart, int n_cta, int K, int d, float* __restrict__ wbar,
-                                   float* __restrict__ mubar, float* __restrict__ sigmabar) {
+                                   float* __restrict__ mubar, float* __restrict__ sigmabar, int accumulate) {
     pdl_prologue();
     const int e = blockIdx.x * blockDim.x + threadIdx.x;  // (k, component)
     const int per = d + 2;
@@ -352,13 +352,9 @@ __global__ void gmm_vjp_sum_kernel(const double* __restrict__ gpart, int n_cta, 
     const int k = e / per, c = e % per;
     double s = 0.0;
     for (int b = 0; b < n_cta; ++b) s += gpart[((size_t)b * K + k) * per + c];
-    if (c < d) {
-        if (mubar) mubar[(size_t)k * d + c] = (float)s;
-    } else if (c == d) {
-        if (sigmabar) sigmabar[k] = (float)s;
-    } else if (wbar) {
-        wbar[k] = (float)s;
-    }
+    float* out = c < d ? (mubar ? mubar + (size_t)k * d + c : nullptr) : (c == d ? (sigmabar ? sigmabar + k : nullptr)
+                                                                             : (wbar ? wbar + k : nullptr));
+    if (out) *out = accumulate ? *out + (float)s : (float)s;
 }
 
 int vjp_splits(int T, int num_sms) {
@@ -381,14 +377,14 @@ VjpBufs carve_vjp(Carver& cv, int T, int d, int K, int splits, bool with_gmm) {
 }
 
 template <int D>
-cov_status svgd_vjp_d(cov_ctx* ctx, const float* x, int T, const float* score, const GmmRaw* G, float h,
-                      const float* abar, float* xbar, float* sbar, float* wbar, float* mubar, float* sigmabar,
-                      cudaStream_t st) {
+cov_status svgd_vjp_d(cov_ctx* ctx, void* ws, size_t ws_bytes, const float* x, int T, const float* score,
+                      const GmmRaw* G, float h, const float* abar, float* xbar, float* sbar, float* wbar,
+                      float* mubar, float* sigmabar, int accumulate, cudaStream_t st) {
     const bool use_gmm = score == nullptr;
     const int splits = vjp_splits(T, ctx->num_sms);
-    Carver cv(ctx->ws);
+    Carver cv(ws);
     VjpBufs B = carve_vjp(cv, T, D, use_gmm ? G->K : 0, splits, use_gmm);
-    if (!ctx->ws || cv.off > ctx->ws_bytes) return COV_ERR_WORKSPACE;
+    if (!ws || cv.off > ws_bytes) return COV_ERR_WORKSPACE;
     const double c = sqrt(2.0 * 0.69314718055994531);
     GmmRaw Gv = use_gmm ? *G : GmmRaw{};
     float* sb = sbar ? sbar : B.sbar;
@@ -408,7 +404,7 @@ cov_status svgd_vjp_d(cov_ctx* ctx, const float* x, int T, const float* score, c
         if (wbar || mubar || sigmabar) {
             const int ne = Gv.K * (D + 2);
             launch_pdl(gmm_vjp_sum_kernel, dim3((ne + 127) / 128), dim3(128), 0, st, (const double*)B.gpart, n_gcta,
-                       Gv.K, D, wbar, mubar, sigmabar);
+                       Gv.K, D, wbar, mubar, sigmabar, accumulate);
         }
     }
     if (cuda_failed(ctx, cudaGetLastError())) return COV_ERR_CUDA;
@@ -423,6 +419,46 @@ size_t svgd_vjp_ws_bytes(int T, int d, int K, int num_sms) {
     return round_up(cv.off, 256);
 }
 
+// The mixture as plain arrays; COV_ERR_INVALID_ARG for an invalid descriptor.
+static cov_status gmm_raw(const cov_gmm* gmm, int d, GmmRaw* G) {
+    if (!gmm || gmm->K < 1 || gmm->K > COV_MAX_GMM || gmm->d != d || !gmm->w || !gmm->mu || !gmm->sigma)
+        return COV_ERR_INVALID_ARG;
+    *G = GmmRaw{};
+    G->K = gmm->K;
+    for (int k = 0; k < gmm->K; ++k) {
+        if (!(gmm->w[k] > 0.f) || !(gmm->sigma[k] > 0.f) || !isfinite(gmm->w[k]) || !isfinite(gmm->sigma[k]))
+            return COV_ERR_INVALID_ARG;
+        G->w[k] = gmm->w[k];
+        G->sigma[k] = gmm->sigma[k];
+        for (int c = 0; c < d; ++c) {
+            if (!isfinite(gmm->mu[k * d + c])) return COV_ERR_INVALID_ARG;
+            G->mu[k * COV_MAX_D + c] = gmm->mu[k * d + c];
+        }
+    }
+    return COV_OK;
+}
+
+cov_status svgd_vjp_ws(cov_ctx* ctx, void* ws, size_t ws_bytes, const float* x, int T, int d, const float* score,
+                       const cov_gmm* gmm, float h, const float* abar, float* xbar, float* sbar, float* wbar,
+                       float* mubar, float* sigmabar, int accumulate, cudaStream_t st) {
+    if (!ctx || !x || !abar || !xbar || T < 1 || d < 1 || d > COV_MAX_D || !(h > 0.f) || !isfinite(h))
+        return COV_ERR_INVALID_ARG;
+    GmmRaw G{};
+    if (!score) {
+        const cov_status r = gmm_raw(gmm, d, &G);
+        if (r != COV_OK) return r;
+    }
+    const GmmRaw* gp = score ? nullptr : &G;
+    switch (d) {
+        case 1: return svgd_vjp_d<1>(ctx, ws, ws_bytes, x, T, score, gp, h, abar, xbar, sbar, wbar, mubar, sigmabar, accumulate, st);
+        case 2: return svgd_vjp_d<2>(ctx, ws, ws_bytes, x, T, score, gp, h, abar, xbar, sbar, wbar, mubar, sigmabar, accumulate, st);
+        case 3: return svgd_vjp_d<3>(ctx, ws, ws_bytes, x, T, score, gp, h, abar, xbar, sbar, wbar, mubar, sigmabar, accumulate, st);
+        case 4: return svgd_vjp_d<4>(ctx, ws, ws_bytes, x, T, score, gp, h, abar, xbar, sbar, wbar, mubar, sigmabar, accumulate, st);
+        case 5: return svgd_vjp_d<5>(ctx, ws, ws_bytes, x, T, score, gp, h, abar, xbar, sbar, wbar, mubar, sigmabar, accumulate, st);
+        default: return svgd_vjp_d<6>(ctx, ws, ws_bytes, x, T, score, gp, h, abar, xbar, sbar, wbar, mubar, sigmabar, accumulate, st);
+    }
+}
+
 }  // namespace cov
 
 extern "C" size_t cov_workspace_size_svgd_vjp(int T, int d, int K) {
@@ -434,34 +470,9 @@ extern "C" size_t cov_workspace_size_svgd_vjp(int T, int d, int K) {
 extern "C" cov_status cov_field_svgd_vjp(cov_ctx* ctx, const float* x, int T, int d, const float* score,
                                          const cov_gmm* gmm, float h, const float* abar, float* xbar, float* sbar,
                                          float* wbar, float* mubar, float* sigmabar, cov_stream_t stream) {
-    if (!ctx || !x || !abar || !xbar || T < 1 || d < 1 || d > COV_MAX_D || !(h > 0.f) || !isfinite(h))
-        return COV_ERR_INVALID_ARG;
-    cov::GmmRaw G{};
-    if (!score) {
-        if (!gmm || gmm->K < 1 || gmm->K > COV_MAX_GMM || gmm->d != d || !gmm->w || !gmm->mu || !gmm->sigma)
-            return COV_ERR_INVALID_ARG;
-        G.K = gmm->K;
-        for (int k = 0; k < gmm->K; ++k) {
-            if (!(gmm->w[k] > 0.f) || !(gmm->sigma[k] > 0.f) || !isfinite(gmm->w[k]) || !isfinite(gmm->sigma[k]))
-                return COV_ERR_INVALID_ARG;
-            G.w[k] = gmm->w[k];
-            G.sigma[k] = gmm->sigma[k];
-            for (int c = 0; c < d; ++c) {
-                if (!isfinite(gmm->mu[k * d + c])) return COV_ERR_INVALID_ARG;
-                G.mu[k * COV_MAX_D + c] = gmm->mu[k * d + c];
-            }
-        }
-    }
+    if (!ctx) return COV_ERR_INVALID_ARG;
     if (cudaSetDevice(ctx->device) != cudaSuccess) return COV_ERR_CUDA;
     cov::clobber_ws_caches(ctx);
-    cudaStream_t st = (cudaStream_t)stream;
-    const cov::GmmRaw* gp = score ? nullptr : &G;
-    switch (d) {
-        case 1: return cov::svgd_vjp_d<1>(ctx, x, T, score, gp, h, abar, xbar, sbar, wbar, mubar, sigmabar, st);
-        case 2: return cov::svgd_vjp_d<2>(ctx, x, T, score, gp, h, abar, xbar, sbar, wbar, mubar, sigmabar, st);
-        case 3: return cov::svgd_vjp_d<3>(ctx, x, T, score, gp, h, abar, xbar, sbar, wbar, mubar, sigmabar, st);
-        case 4: return cov::svgd_vjp_d<4>(ctx, x, T, score, gp, h, abar, xbar, sbar, wbar, mubar, sigmabar, st);
-        case 5: return cov::svgd_vjp_d<5>(ctx, x, T, score, gp, h, abar, xbar, sbar, wbar, mubar, sigmabar, st);
-        default: return cov::svgd_vjp_d<6>(ctx, x, T, score, gp, h, abar, xbar, sbar, wbar, mubar, sigmabar, st);
-    }
+    return cov::svgd_vjp_ws(ctx, ctx->ws, ctx->ws_bytes, x, T, d, score, gmm, h, abar, xbar, sbar, wbar, mubar,
+                            sigmabar, 0, (cudaStream_t)stream);
 }
