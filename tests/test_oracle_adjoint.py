@@ -258,3 +258,31 @@ def test_stein_solve_backward_matches_central_differences(orc, model):
         fd = _fd(fun, np.asarray(base, dtype=np.float64), dv)
         assert float(np.sum(grad * dv)) == pytest.approx(fd, rel=1e-6, abs=1e-9)
     assert abs(float(np.dot(w, wb))) <= 1e-9 * float(np.abs(w * wb).sum())
+
+
+def test_field_vjp_every_coordinate_at_64_by_128(orc):
+    """Every coordinate of x (64 x 2), y (128 x 2) and b (128) separately by
+    central differences (step 1e-6), at T = 64, M = 128 with 6 iterations:
+    the all-coordinates check at a size where column splits and many rows
+    matter."""
+    T, M, d, eps, n_iter = 64, 128, 2, 0.05, 6
+    x = wl.random_points(T, d, seed=51)
+    y = wl.random_points(M, d, seed=52)
+    b = wl.random_weights(M, seed=53)
+    abar = wl.rng(54).standard_normal((T, d))
+    xbar, ybar, bbar = orc.sinkhorn_field_vjp(x, y, b, eps, n_iter, abar)
+
+    def fd_all(fun, base):
+        g = np.zeros_like(base)
+        for idx in np.ndindex(base.shape):
+            e = np.zeros_like(base)
+            e[idx] = 1.0
+            g[idx] = _fd(fun, base, e)
+        return g
+
+    gx = fd_all(lambda v: _field_obj(orc, v, y, b, eps, n_iter, abar), x)
+    gy = fd_all(lambda v: _field_obj(orc, x, v, b, eps, n_iter, abar), y)
+    gb = fd_all(lambda v: _field_obj(orc, x, y, v, eps, n_iter, abar), b)
+    np.testing.assert_allclose(xbar, gx, rtol=1e-5, atol=1e-6 * np.abs(gx).max())
+    np.testing.assert_allclose(ybar, gy, rtol=1e-5, atol=1e-6 * np.abs(gy).max())
+    np.testing.assert_allclose(bbar, gb, rtol=1e-5, atol=1e-6 * np.abs(gb).max())
