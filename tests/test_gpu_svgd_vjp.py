@@ -65,3 +65,17 @@ def test_vjp_is_deterministic_and_rejects_bad_arguments(cov, ctx):
     with pytest.raises(cov.CovError) as e:
         cov.cov_field_svgd_vjp(ctx, x, 0.0, ab, gmm=gmm)
     assert e.value.status == cov.COV_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("T,d,K", [(700, 3, 32), (257, 6, 7), (64, 1, 2)])
+def test_vjp_through_mixture_in_other_dimensions(cov, ctx, orc, T, d, K):
+    """The mixture path at d = 1, 3 and 6 and up to the largest mixture the
+    C-ABI takes (32 components)."""
+    x = wl.random_points(T, d, seed=300 + T, lo=0.15, hi=0.85)
+    gmm = tuple(wl.f32_pair(v)[1] for v in wl.gmm_params(K, seed=301 + K, d=d))
+    ab = wl.f32_pair(wl.rng(302 + d).standard_normal((T, d)))[1]
+    xb, sb, (wb, mb, sgb) = cov.cov_field_svgd_vjp(ctx, dev32(x), 0.15, dev32(ab), gmm=gmm)
+    xo, wo, mo, so = orc.svgd_gmm_field_vjp(x, *gmm, 0.15, ab)
+    for got, want in ((xb, xo), (mb, mo), (sgb, so), (wb, wo)):
+        assert rel_norm(host(got), want) <= TOL
+    assert ctx.device_status() == (cov.COV_OK, 0)
