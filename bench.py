@@ -56,8 +56,8 @@ FP32_LANES_PER_SM_CLK = 128
 # offset form): 393 KB (g + p launch) and 290 KB (f launch), no writes.
 PAIRS_TRAFFIC_BYTES = 341504
 # The same for lse_tc_kernel at T = 65536, M = 262144 (the default path at
-# that size): 9.47 MB (g + p launch) and 13.43 MB (f launch), no writes.
-TC_LARGE_TRAFFIC_BYTES = 11454208
+# that size): 9.47 MB (g + p launch) and 13.50 MB (f launch), no writes.
+TC_LARGE_TRAFFIC_BYTES = 11485824
 
 
 def parse_args():

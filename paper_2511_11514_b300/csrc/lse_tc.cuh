@@ -234,38 +234,73 @@ __global__ void __launch_bounds__(kTcThreads, kTcMinBlocks) lse_tc_kernel(const 
         float acc[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u) acc[u] = 0.f;
-        for (int t = 0; t < nt; ++t) {
-            const int b = t & 1;
-            const bool got = mbar_wait_bounded(&S.tfull[b], (unsigned)((t >> 1) & 1), spin);
+        // The two 32-column halves of a reader's 64 columns are loaded one
+        // step ahead, so that the tensor-memory load latency hides behind
+        // MUFU work: half 1 of tile t while half 0 is summed, half 0 of tile
+        // t + 1 (after its full barrier) while half 1 is summed.  pin() keeps
+        // the sums between a load and its wait.
+        auto pin = [&]() {
+            asm volatile("" : "+f"(acc[0]), "+f"(acc[1]), "+f"(acc[2]), "+f"(acc[3]), "+f"(acc[4]), "+f"(acc[5]),
+                         "+f"(acc[6]), "+f"(acc[7]));
+        };
+        // of the 64 values the last 2 kTcPolyPairs take 2^x on the FMA pipe
+        // (exp2_fma2, two at a time), the rest MUFU.EX2
+        auto sum32 = [&](const uint32_t (&v)[32], int base) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+                if (base + j < 64 - 2 * kTcPolyPairs) acc[j & 7] += ex2(__uint_as_float(v[j]));
+#pragma unroll
+            for (int j = 0; j < 32; j += 2)
+                if (base + j >= 64 - 2 * kTcPolyPairs) {
+                    const float2 e = exp2_fma2(make_float2(__uint_as_float(v[j]), __uint_as_float(v[j + 1])));
+                    acc[j & 7] += e.x;
+                    acc[(j + 1) & 7] += e.y;
+                }
+        };
+        const uint32_t tq = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(hf * 64);
+        uint32_t vA[32], vB[32];
+        bool live = nt > 0;
+        if (live) {
+            const bool got = mbar_wait_bounded(&S.tfull[0], 0u, spin);
             if (!__all_sync(0xffffffffu, got)) {
                 if (lane == 0) {
                     raise_status(a.status, kDevTimeout);
                     S.flag = 1;
                 }
-                break;
+                live = false;
+            } else {
+                tc_fence_after();
+                tmem_ld32(tq, vA, 0);
+                tmem_wait_ld(vA);
             }
-            tc_fence_after();
-            uint32_t v0[32], v1[32];
-            const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * kTcCols + hf * 64);
-            tmem_ld32(ta, v0, 0);
-            tmem_ld32(ta, v1, 32);
-            tmem_wait_ld(v0);
-            tmem_wait_ld(v1);
+        }
+        for (int t = 0; live && t < nt; ++t) {
+            const int b = t & 1;
+            tmem_ld32(tq + (uint32_t)(b * kTcCols), vB, 32);
+            pin();
+            sum32(vA, 0);
+            pin();
+            tmem_wait_ld(vB);
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&S.tempty[b]);
-            // of the 64 values the last 2 kTcPolyPairs take 2^x on the FMA
-            // pipe (exp2_fma2, two at a time), the rest MUFU.EX2
-#pragma unroll
-            for (int j = 0; j < 64 - 2 * kTcPolyPairs; ++j)
-                acc[j & 7] += ex2(__uint_as_float(j < 32 ? v0[j] : v1[j - 32]));
-#pragma unroll
-            for (int j = 64 - 2 * kTcPolyPairs; j < 64; j += 2) {
-                const float2 e = exp2_fma2(make_float2(__uint_as_float(j < 32 ? v0[j] : v1[j - 32]),
-                                                       __uint_as_float(j < 32 ? v0[j + 1] : v1[j - 31])));
-                acc[j & 7] += e.x;
-                acc[(j + 1) & 7] += e.y;
+            const bool more = t + 1 < nt;
+            if (more) {
+                const bool got = mbar_wait_bounded(&S.tfull[b ^ 1], (unsigned)(((t + 1) >> 1) & 1), spin);
+                if (!__all_sync(0xffffffffu, got)) {
+                    if (lane == 0) {
+                        raise_status(a.status, kDevTimeout);
+                        S.flag = 1;
+                    }
+                    break;
+                }
+                tc_fence_after();
+                tmem_ld32(tq + (uint32_t)((b ^ 1) * kTcCols), vA, 0);
             }
+            pin();
+            sum32(vB, 32);
+            pin();
+            if (more) tmem_wait_ld(vA);
         }
         S.red_s[hf][q * 32 + lane] = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
     }

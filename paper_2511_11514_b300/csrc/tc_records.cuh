@@ -22,12 +22,12 @@ constexpr int kTcMinBlocks = 512 / kTcTmemCols;    // resident CTAs per SM that 
 constexpr long long kTcAutoPairs = 1LL << 30;
 // Of the 64 exponentials a reader thread takes per tile, how many pairs go
 // to the FMA pipe (exp2_fma2) instead of MUFU (build flag
-// -DCOV_TC_POLY_PAIRS=0..32).  Default 0: at T = 65536, M = 262144 the
-// kernel ran at 0.727 of the roofline with none, 0.729 with 2 pairs (6 %),
-// 0.699 with 4 and 0.643 with 6 -- the readers are not bound by MUFU alone,
-// and the polynomial's ~8 instructions per value cost more than they free.
+// -DCOV_TC_POLY_PAIRS=0..32).  Default 1: at T = 65536, M = 262144 the
+// kernel ran at 0.741 of the MUFU rate with 1 pair (3 %), 0.737 with none
+// and 0.733 with 2 -- the readers are not bound by MUFU alone, and the
+// polynomial's ~8 instructions per value soon cost more than they free.
 #ifndef COV_TC_POLY_PAIRS
-#define COV_TC_POLY_PAIRS 0
+#define COV_TC_POLY_PAIRS 1
 #endif
 constexpr int kTcPolyPairs = COV_TC_POLY_PAIRS;
 constexpr int kTcRecC = 8;                         // floats per point in the coordinate record
