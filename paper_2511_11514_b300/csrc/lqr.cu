@@ -893,6 +893,309 @@ __global__ void __launch_bounds__(32) fill_kernel(const double* __restrict__ Mg,
 }
 
 // ---------------------------------------------------------------------------
+// Short horizons: both affine recursions of the LQR step in one CTA.  The
+// chunked scans above spread the FP64 work over the SMs but pay a launch per
+// level (ten launches for the two recursions at T = 256), which is most of
+// their time on a short horizon.  Here lane g of the CTA owns the steps
+// [g C, min((g+1) C, T) - 1], C = ceil(T / kShortLanes), and every phase is
+// lane-parallel, so each FP64 instruction does useful work in all 32 lanes
+// (the FP64 pipe takes one warp instruction per ~64 clocks per warp, about
+// four warps at a time per SM):
+//   1. every lane composes its chunk's affine map (Phi | phi);
+//   2. the maps are chained: an inclusive scan over the lanes of each warp
+//      (shuffles, five composition levels), the warps' totals in order by
+//      one thread, then each lane applies the scan of the chunks after it
+//      (BWD) or before it (FWD) to the value entering its warp;
+//   3. every lane runs its steps from the value entering its chunk.
+// BWD: p_t = M_t' p_{t+1} + c_t (c_t = -Q abar_{t-1}, c_0 = 0, p_T = -Q abar_T),
+//      k_t = N_t p_{t+1} (kept in shared memory for the forward pass);
+// FWD: z_0 = 0, z_{t+1} = M_t z_t + e_t (e_t = -B_t k_t), v_t = -K_t z_t - k_t.
+// Each step's arithmetic is that of compose_kernel / fill_kernel, in the
+// same order.
+// ---------------------------------------------------------------------------
+constexpr int kShortWarps = 4;
+constexpr int kShortLanes = 32 * kShortWarps;
+constexpr int kShortMaxT = 1024;
+
+template <int N>
+struct AffMap {
+    double P[N * N];  // row-major
+    double p[N];
+};
+
+template <int N>
+__device__ __forceinline__ void aff_identity(AffMap<N>& m) {
+#pragma unroll
+    for (int e = 0; e < N * N; ++e) m.P[e] = (e % (N + 1) == 0) ? 1.0 : 0.0;
+#pragma unroll
+    for (int e = 0; e < N; ++e) m.p[e] = 0.0;
+}
+
+// own <- own o other (other applied first): P = P_own P_other, p = P_own p_other + p_own.
+template <int N>
+__device__ __forceinline__ void aff_compose(AffMap<N>& own, const AffMap<N>& other) {
+    AffMap<N> r;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+#pragma unroll
+        for (int c = 0; c < N; ++c) {
+            double acc = 0.0;
+#pragma unroll
+            for (int q = 0; q < N; ++q) acc = fma(own.P[i * N + q], other.P[q * N + c], acc);
+            r.P[i * N + c] = acc;
+        }
+        double acc = own.p[i];
+#pragma unroll
+        for (int q = 0; q < N; ++q) acc = fma(own.P[i * N + q], other.p[q], acc);
+        r.p[i] = acc;
+    }
+    own = r;
+}
+
+template <int N>
+__device__ __forceinline__ AffMap<N> aff_shfl(const AffMap<N>& m, int off, bool down) {
+    AffMap<N> r;
+#pragma unroll
+    for (int e = 0; e < N * N; ++e)
+        r.P[e] = down ? __shfl_down_sync(0xffffffffu, m.P[e], off) : __shfl_up_sync(0xffffffffu, m.P[e], off);
+#pragma unroll
+    for (int e = 0; e < N; ++e)
+        r.p[e] = down ? __shfl_down_sync(0xffffffffu, m.p[e], off) : __shfl_up_sync(0xffffffffu, m.p[e], off);
+    return r;
+}
+
+template <int N>
+__device__ __forceinline__ void aff_apply(const AffMap<N>& m, const double* x, double* y) {
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        double acc = m.p[i];
+#pragma unroll
+        for (int q = 0; q < N; ++q) acc = fma(m.P[i * N + q], x[q], acc);
+        y[i] = acc;
+    }
+}
+
+// One CTA of kShortLanes threads; T <= kShortMaxT.  Gains layout as in
+// launch_affine_t: M [T][N][N], Nt and K [T][MC][N]; B [T][N][MC].
+template <int N, int MC>
+__global__ void __launch_bounds__(kShortLanes, 1) lqr_short_kernel(const double* __restrict__ Mg,
+                                                                   const double* __restrict__ Ng,
+                                                                   const double* __restrict__ Kg,
+                                                                   const double* __restrict__ Bg, LqrConst Cq,
+                                                                   const double* __restrict__ abar, int T,
+                                                                   double* __restrict__ v, double* __restrict__ z) {
+    pdl_prologue();
+    __shared__ double ks[kShortMaxT * MC];
+    __shared__ double tot[kShortWarps][N * N + N];
+    __shared__ double xw[kShortWarps][N];
+    const int g = threadIdx.x, lane = g & 31, warp = g >> 5;
+    const int C = (T + kShortLanes - 1) / kShortLanes;
+    const int lo = g * C, hi = min(lo + C, T) - 1;  // empty when lo > hi
+    // c_t = -Q abar_{t-1} (t >= 1), c_0 = 0
+    auto cvec = [&](int t, double* c) {
+#pragma unroll
+        for (int r = 0; r < N; ++r) {
+            double acc = 0.0;
+            if (t >= 1) {
+#pragma unroll
+                for (int q = 0; q < N; ++q) acc = fma(-Cq.Q[r * N + q], abar[(size_t)(t - 1) * N + q], acc);
+            }
+            c[r] = acc;
+        }
+    };
+    // e_t = -B_t k_t
+    auto evec = [&](int t, double* e) {
+#pragma unroll
+        for (int r = 0; r < N; ++r) {
+            double acc = 0.0;
+#pragma unroll
+            for (int q = 0; q < MC; ++q) acc = fma(-Bg[((size_t)t * N + r) * MC + q], ks[t * MC + q], acc);
+            e[r] = acc;
+        }
+    };
+    auto put_total = [&](const AffMap<N>& m) {
+#pragma unroll
+        for (int e = 0; e < N * N; ++e) tot[warp][e] = m.P[e];
+#pragma unroll
+        for (int e = 0; e < N; ++e) tot[warp][N * N + e] = m.p[e];
+    };
+    auto get_total = [&](int w, AffMap<N>& m) {
+#pragma unroll
+        for (int e = 0; e < N * N; ++e) m.P[e] = tot[w][e];
+#pragma unroll
+        for (int e = 0; e < N; ++e) m.p[e] = tot[w][N * N + e];
+    };
+
+    // ---- backward recursion ------------------------------------------------
+    AffMap<N> F;
+    aff_identity(F);
+    for (int t = hi; t >= lo; --t) {  // F: p_{hi+1} -> p_t
+        const double* Mt = Mg + (size_t)t * N * N;
+        double c[N];
+        cvec(t, c);
+        AffMap<N> G;
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+#pragma unroll
+            for (int cc = 0; cc < N; ++cc) {
+                double acc = 0.0;
+#pragma unroll
+                for (int q = 0; q < N; ++q) acc = fma(Mt[q * N + i], F.P[q * N + cc], acc);
+                G.P[i * N + cc] = acc;
+            }
+            double acc = c[i];
+#pragma unroll
+            for (int q = 0; q < N; ++q) acc = fma(Mt[q * N + i], F.p[q], acc);
+            G.p[i] = acc;
+        }
+        F = G;
+    }
+    // suffix scan over the warp's lanes: F <- F_g o F_{g+1} o ... (later chunks applied first)
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const AffMap<N> o = aff_shfl(F, off, true);
+        if (lane + off < 32) aff_compose(F, o);
+    }
+    AffMap<N> E = aff_shfl(F, 1, true);  // the chunks after this lane's, within the warp
+    if (lane == 31) aff_identity(E);
+    if (lane == 0) put_total(F);
+    __syncthreads();
+    if (g == 0) {
+        double x[N], y[N];
+#pragma unroll
+        for (int r = 0; r < N; ++r) {
+            double acc = 0.0;
+#pragma unroll
+            for (int q = 0; q < N; ++q) acc = fma(-Cq.Q[r * N + q], abar[(size_t)(T - 1) * N + q], acc);
+            x[r] = acc;  // p_T
+        }
+        for (int w = kShortWarps - 1; w >= 0; --w) {
+#pragma unroll
+            for (int r = 0; r < N; ++r) xw[w][r] = x[r];
+            if (w > 0) {
+                AffMap<N> Tw;
+                get_total(w, Tw);
+                aff_apply(Tw, x, y);
+#pragma unroll
+                for (int r = 0; r < N; ++r) x[r] = y[r];
+            }
+        }
+    }
+    __syncthreads();
+    {
+        double p[N], np[N];
+        aff_apply(E, xw[warp], p);  // p_{hi+1}
+        for (int t = hi; t >= lo; --t) {
+            const double* Mt = Mg + (size_t)t * N * N;
+            const double* Nt = Ng + (size_t)t * MC * N;
+#pragma unroll
+            for (int r = 0; r < MC; ++r) {
+                double acc = 0.0;
+#pragma unroll
+                for (int q = 0; q < N; ++q) acc = fma(Nt[r * N + q], p[q], acc);
+                ks[t * MC + r] = acc;
+            }
+            double c[N];
+            cvec(t, c);
+#pragma unroll
+            for (int r = 0; r < N; ++r) {
+                double acc = c[r];
+#pragma unroll
+                for (int q = 0; q < N; ++q) acc = fma(Mt[q * N + r], p[q], acc);
+                np[r] = acc;
+            }
+#pragma unroll
+            for (int r = 0; r < N; ++r) p[r] = np[r];
+        }
+    }
+    __syncthreads();
+
+    // ---- forward recursion -------------------------------------------------
+    aff_identity(F);
+    for (int t = lo; t <= hi; ++t) {  // F: z_lo -> z_{t+1}
+        const double* Mt = Mg + (size_t)t * N * N;
+        double e[N];
+        evec(t, e);
+        AffMap<N> G;
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+#pragma unroll
+            for (int cc = 0; cc < N; ++cc) {
+                double acc = 0.0;
+#pragma unroll
+                for (int q = 0; q < N; ++q) acc = fma(Mt[i * N + q], F.P[q * N + cc], acc);
+                G.P[i * N + cc] = acc;
+            }
+            double acc = e[i];
+#pragma unroll
+            for (int q = 0; q < N; ++q) acc = fma(Mt[i * N + q], F.p[q], acc);
+            G.p[i] = acc;
+        }
+        F = G;
+    }
+    // prefix scan over the warp's lanes: F <- F_g o F_{g-1} o ... (earlier chunks applied first)
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const AffMap<N> o = aff_shfl(F, off, false);
+        if (lane >= off) aff_compose(F, o);
+    }
+    E = aff_shfl(F, 1, false);  // the chunks before this lane's, within the warp
+    if (lane == 0) aff_identity(E);
+    if (lane == 31) put_total(F);
+    __syncthreads();
+    if (g == 0) {
+        double x[N], y[N];
+#pragma unroll
+        for (int r = 0; r < N; ++r) x[r] = 0.0;  // z_0
+        for (int w = 0; w < kShortWarps; ++w) {
+#pragma unroll
+            for (int r = 0; r < N; ++r) xw[w][r] = x[r];
+            if (w + 1 < kShortWarps) {
+                AffMap<N> Tw;
+                get_total(w, Tw);
+                aff_apply(Tw, x, y);
+#pragma unroll
+                for (int r = 0; r < N; ++r) x[r] = y[r];
+            }
+        }
+        if (z) {
+#pragma unroll
+            for (int r = 0; r < N; ++r) z[r] = 0.0;
+        }
+    }
+    __syncthreads();
+    {
+        double w[N], nw[N];
+        aff_apply(E, xw[warp], w);  // z_lo
+        for (int t = lo; t <= hi; ++t) {
+            const double* Mt = Mg + (size_t)t * N * N;
+            const double* Kt = Kg + (size_t)t * MC * N;
+#pragma unroll
+            for (int r = 0; r < MC; ++r) {
+                double acc = -ks[t * MC + r];
+#pragma unroll
+                for (int q = 0; q < N; ++q) acc = fma(Kt[r * N + q], -w[q], acc);
+                v[(size_t)t * MC + r] = acc;
+            }
+            double e[N];
+            evec(t, e);
+#pragma unroll
+            for (int r = 0; r < N; ++r) {
+                double acc = e[r];
+#pragma unroll
+                for (int q = 0; q < N; ++q) acc = fma(Mt[r * N + q], w[q], acc);
+                nw[r] = acc;
+            }
+#pragma unroll
+            for (int r = 0; r < N; ++r) {
+                w[r] = nw[r];
+                if (z) z[(size_t)(t + 1) * N + r] = nw[r];
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Adjoints.  The LQR solution v(abar) is linear in abar: v = H^-1 G'Q abar
 // with z = G v and H = G'QG + R (z_0 = 0), so its VJP abar_bar = Q G H^-1 vbar
 // is the same LQR with the linear control cost -2 vbar_t'w_t and no state
@@ -1723,12 +2026,32 @@ static void launch_boundaries(const ScanPlan& pl, const AffineBufs& ab, const Lq
                    (const double*)maps[l], pl.n[l], pl.G[l], (const double*)bnd[l + 1], C, abar, w0, T, bnd[l]);
 }
 
+// Longest horizon the one-CTA kernel takes for a state dimension.  Its FP64
+// work (compositions of N x (N + 1) maps, N^2 (N + 1) FMAs each, five of
+// them in the lane scan) runs on one SM: measured against the chunked scans
+// (cov_lqr_track, both in CUDA graphs) it saved 5-9 us at N = 2 for
+// T = 64-256, broke even at T = 512 and lost 11 us at T = 1024; at N = 3 it
+// lost 1-5 us already at T = 64-256.
+#ifndef COV_LQR_SHORT
+#define COV_LQR_SHORT 1
+#endif
+static int short_max_T(int n) {
+    if (!COV_LQR_SHORT) return 0;
+    return n == 1 ? kShortMaxT : (n == 2 ? 512 : 0);
+}
+
 template <int N, int MC>
 static void launch_affine_t(const double* B, const double* gains, const LqrConst& C, const double* abar, int T,
                             const ScanPlan& pl, const AffineBufs& ab, double* v, double* z, cudaStream_t s) {
     const double* K = gains;
     const double* M = gains + (size_t)T * MC * N;
     const double* Nt = M + (size_t)T * N * N;
+    if constexpr (N <= 2) {
+        if (T <= short_max_T(N)) {
+            launch_pdl(lqr_short_kernel<N, MC>, dim3(1), dim3(kShortLanes), 0, s, M, Nt, K, B, C, abar, T, v, z);
+            return;
+        }
+    }
     const size_t fsb = sizeof(double) * pl.C * N;
     launch_pdl(compose_kernel<N, MC, true>, dim3(pl.n_chunks), dim3(32), fsb, s, M, C, abar, nullptr, nullptr, nullptr, T, pl.C, ab.fc,
                                                              ab.maps);

@@ -68,6 +68,21 @@ def test_lqr_track_matches_oracle(cov, ctx, orc, T, n, m):
     assert ctx.device_status()[1] == 0
 
 
+@pytest.mark.parametrize("T,n,m", [(3, 1, 1), (127, 2, 2), (128, 2, 1), (129, 2, 3), (255, 2, 2), (256, 3, 3),
+                                   (511, 2, 2), (512, 2, 3), (513, 2, 2), (1023, 1, 2), (1024, 1, 3), (1025, 1, 1)])
+def test_lqr_short_horizon_kernel(cov, ctx, orc, T, n, m):
+    """The one-CTA kernel of both affine recursions (n = 1 up to T = 1024,
+    n = 2 up to T = 512; 128 lanes, so one step per lane up to T = 128 and
+    ragged last chunks past it), and the first horizons past its range,
+    against the oracle."""
+    A, B, Q, R, abar = _random_lqr(T, n, m, seed=3 * T + 10 * n + m)
+    v, z = cov.cov_lqr_track(ctx, dev64(A), dev64(B), Q, R, dev64(abar))
+    vo, zo, _ = orc.lqr_track(A, B, Q, R, abar)
+    np.testing.assert_allclose(host(v), vo, rtol=1e-9, atol=1e-10 * np.abs(vo).max())
+    np.testing.assert_allclose(host(z), zo, rtol=1e-9, atol=1e-10 * np.abs(zo).max())
+    assert ctx.device_status()[1] == 0
+
+
 def test_lqr_double_integrator_long_horizon(cov, ctx, orc):
     """The benchmark's LQR: double integrator, coverage weight on position
     only (Q PSD), R = 0.01 I, T = 4096."""
