@@ -256,6 +256,11 @@ __device__ __forceinline__ void cp_async4(void* dst, const void* src) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all_but_one() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+// Wait until at most G of this thread's committed groups are still in flight.
+template <int G>
+__device__ __forceinline__ void cp_async_wait_group() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(G) : "memory");
+}
 
 // L2-coherent loads for data written by other CTAs of the same launch.
 __device__ __forceinline__ float ld_cg(const float* p) { return __ldcg(p); }

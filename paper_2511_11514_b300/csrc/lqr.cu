@@ -910,85 +910,204 @@ __global__ void __launch_bounds__(32) fill_kernel(const double* __restrict__ Mg,
 // BWD: p_t = M_t' p_{t+1} + c_t (c_t = -Q abar_{t-1}, c_0 = 0, p_T = -Q abar_T),
 //      k_t = N_t p_{t+1} (kept in shared memory for the forward pass);
 // FWD: z_0 = 0, z_{t+1} = M_t z_t + e_t (e_t = -B_t k_t), v_t = -K_t z_t - k_t.
-// Each step's arithmetic is that of compose_kernel / fill_kernel, in the
-// same order.
+// The matrix parts Phi of all these maps depend on the gains alone, so they
+// are formed once per set of gains (lqr_short_pre_kernel, launched with the
+// Riccati recursion; for a time-invariant model once per solve) and stored
+// beside the gains; each LQR step (lqr_short_kernel) then composes and scans
+// only the vector parts phi, an N^2 instead of an N^2 (N + 1) FMA product
+// per composition.  A composition own o other (other applied first) is
+//   Phi = Phi_own Phi_other,  phi = Phi_own phi_other + phi_own,
+// and the cache holds, per lane and recursion, Phi_own before each of the
+// five scan levels, the Phi of the exclusive scan (the chunks after / before
+// the lane's, within its warp) and the warps' total Phi.  Each step's
+// arithmetic is that of compose_kernel / fill_kernel, in the same order.
 // ---------------------------------------------------------------------------
 constexpr int kShortWarps = 4;
 constexpr int kShortLanes = 32 * kShortWarps;
 constexpr int kShortMaxT = 1024;
+constexpr int kShortLevels = 5;                      // log2(32) scan levels
+constexpr int kShortLaneMats = kShortLevels + 1;     // + the exclusive scan's Phi
+constexpr int kShortRecMats = kShortLanes * kShortLaneMats + kShortWarps;  // per recursion
 
-template <int N>
-struct AffMap {
-    double P[N * N];  // row-major
-    double p[N];
-};
-
-template <int N>
-__device__ __forceinline__ void aff_identity(AffMap<N>& m) {
-#pragma unroll
-    for (int e = 0; e < N * N; ++e) m.P[e] = (e % (N + 1) == 0) ? 1.0 : 0.0;
-#pragma unroll
-    for (int e = 0; e < N; ++e) m.p[e] = 0.0;
+// Cache matrices (N x N, row-major): recursion r (0 BWD, 1 FWD), lane g,
+// slot k (0..4 scan levels, 5 exclusive scan); warp totals after the lanes.
+template <int N, class D>
+__device__ __forceinline__ D* short_lane_mat(D* cache, int r, int g, int k) {
+    return cache + ((size_t)r * kShortRecMats + (size_t)g * kShortLaneMats + k) * N * N;
+}
+template <int N, class D>
+__device__ __forceinline__ D* short_warp_mat(D* cache, int r, int w) {
+    return cache + ((size_t)r * kShortRecMats + (size_t)kShortLanes * kShortLaneMats + w) * N * N;
 }
 
-// own <- own o other (other applied first): P = P_own P_other, p = P_own p_other + p_own.
 template <int N>
-__device__ __forceinline__ void aff_compose(AffMap<N>& own, const AffMap<N>& other) {
-    AffMap<N> r;
+__device__ __forceinline__ void mat_identity(double (&P)[N * N]) {
 #pragma unroll
-    for (int i = 0; i < N; ++i) {
+    for (int e = 0; e < N * N; ++e) P[e] = (e % (N + 1) == 0) ? 1.0 : 0.0;
+}
+// P <- P Q
+template <int N>
+__device__ __forceinline__ void mat_mul_right(double (&P)[N * N], const double (&Q)[N * N]) {
+    double R[N * N];
+#pragma unroll
+    for (int i = 0; i < N; ++i)
 #pragma unroll
         for (int c = 0; c < N; ++c) {
             double acc = 0.0;
 #pragma unroll
-            for (int q = 0; q < N; ++q) acc = fma(own.P[i * N + q], other.P[q * N + c], acc);
-            r.P[i * N + c] = acc;
+            for (int q = 0; q < N; ++q) acc = fma(P[i * N + q], Q[q * N + c], acc);
+            R[i * N + c] = acc;
         }
-        double acc = own.p[i];
 #pragma unroll
-        for (int q = 0; q < N; ++q) acc = fma(own.P[i * N + q], other.p[q], acc);
-        r.p[i] = acc;
-    }
-    own = r;
+    for (int e = 0; e < N * N; ++e) P[e] = R[e];
 }
-
 template <int N>
-__device__ __forceinline__ AffMap<N> aff_shfl(const AffMap<N>& m, int off, bool down) {
-    AffMap<N> r;
+__device__ __forceinline__ void mat_shfl(const double (&P)[N * N], double (&Q)[N * N], int off, bool down) {
 #pragma unroll
     for (int e = 0; e < N * N; ++e)
-        r.P[e] = down ? __shfl_down_sync(0xffffffffu, m.P[e], off) : __shfl_up_sync(0xffffffffu, m.P[e], off);
+        Q[e] = down ? __shfl_down_sync(0xffffffffu, P[e], off) : __shfl_up_sync(0xffffffffu, P[e], off);
+}
+template <int N>
+__device__ __forceinline__ void vec_shfl(const double (&x)[N], double (&y)[N], int off, bool down) {
 #pragma unroll
     for (int e = 0; e < N; ++e)
-        r.p[e] = down ? __shfl_down_sync(0xffffffffu, m.p[e], off) : __shfl_up_sync(0xffffffffu, m.p[e], off);
-    return r;
+        y[e] = down ? __shfl_down_sync(0xffffffffu, x[e], off) : __shfl_up_sync(0xffffffffu, x[e], off);
 }
-
 template <int N>
-__device__ __forceinline__ void aff_apply(const AffMap<N>& m, const double* x, double* y) {
+__device__ __forceinline__ void mat_store(double* dst, const double (&P)[N * N]) {
+#pragma unroll
+    for (int e = 0; e < N * N; ++e) dst[e] = P[e];
+}
+// y = P x + b (P from memory)
+template <int N>
+__device__ __forceinline__ void mat_apply(const double* P, const double* x, const double* b, double* y) {
 #pragma unroll
     for (int i = 0; i < N; ++i) {
-        double acc = m.p[i];
+        double acc = b[i];
 #pragma unroll
-        for (int q = 0; q < N; ++q) acc = fma(m.P[i * N + q], x[q], acc);
+        for (int q = 0; q < N; ++q) acc = fma(P[i * N + q], x[q], acc);
         y[i] = acc;
     }
 }
 
-// One CTA of kShortLanes threads; T <= kShortMaxT.  Gains layout as in
-// launch_affine_t: M [T][N][N], Nt and K [T][MC][N]; B [T][N][MC].
-template <int N, int MC>
+// The matrix parts of the short kernel's maps (one CTA of kShortLanes
+// threads): BWD chunk map Phi = M_lo' ... M_hi', FWD Phi = M_hi ... M_lo,
+// and their warp scans, into `cache`.  M is staged in shared memory first
+// (T N^2 <= kShortPreMs).
+constexpr int kShortPreMs = 2048;
+template <int N>
+__global__ void __launch_bounds__(kShortLanes, 1) lqr_short_pre_kernel(const double* __restrict__ Mg, int T,
+                                                                       double* __restrict__ cache) {
+    pdl_prologue();
+    __shared__ double Ms[kShortPreMs];
+    const int g = threadIdx.x, lane = g & 31, warp = g >> 5;
+    for (int i = g; i < T * N * N; i += kShortLanes) cp_async8(Ms + i, Mg + i);
+    cp_async_commit();
+    cp_async_wait_all();
+    __syncthreads();
+    const int C = (T + kShortLanes - 1) / kShortLanes;
+    const int lo = g * C, hi = min(lo + C, T) - 1;
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const bool bwd = r == 0;
+        double P[N * N], O[N * N];
+        mat_identity<N>(P);
+        for (int j = 0; j <= hi - lo; ++j) {  // BWD: t = hi .. lo, P <- M_t' P; FWD: t = lo .. hi, P <- M_t P
+            const int t = bwd ? hi - j : lo + j;
+            const double* Mt = Ms + t * N * N;
+            double R[N * N];
+#pragma unroll
+            for (int i = 0; i < N; ++i)
+#pragma unroll
+                for (int c = 0; c < N; ++c) {
+                    double acc = 0.0;
+#pragma unroll
+                    for (int q = 0; q < N; ++q) acc = fma(bwd ? Mt[q * N + i] : Mt[i * N + q], P[q * N + c], acc);
+                    R[i * N + c] = acc;
+                }
+#pragma unroll
+            for (int e = 0; e < N * N; ++e) P[e] = R[e];
+        }
+#pragma unroll
+        for (int k = 0; k < kShortLevels; ++k) {
+            const int off = 1 << k;
+            mat_store<N>(short_lane_mat<N>(cache, r, g, k), P);
+            mat_shfl<N>(P, O, off, bwd);
+            if (bwd ? lane + off < 32 : lane >= off) mat_mul_right<N>(P, O);
+        }
+        mat_shfl<N>(P, O, 1, bwd);
+        if (lane == (bwd ? 31 : 0)) mat_identity<N>(O);
+        mat_store<N>(short_lane_mat<N>(cache, r, g, kShortLevels), O);
+        if (lane == (bwd ? 0 : 31)) mat_store<N>(short_warp_mat<N>(cache, r, warp), P);
+    }
+}
+
+// Doubles of dynamic shared memory the step kernel stages its inputs in.
+__host__ __device__ constexpr size_t short_smem_doubles(int T, int N, int MC) {
+    return (size_t)T * (N * N + N + 3 * MC * N + MC) + (size_t)2 * kShortRecMats * N * N;
+}
+
+// The single integrator's outer-iteration tail fused into the step kernel
+// (ROLL): the field a is lifted while staged, and after the forward pass
+// u_t += eta v_t and the Euler rollout s_{t+1} = s_t + dt u_t from s_0 (a
+// prefix sum over the lanes, as in update_rollout_kernel).
+struct ShortRoll {
+    const float* a;  // [T][d] field on the coverage coordinates
+    int d;
+    double eta, dt;
+    double s0[2];
+    double* u;       // [T][2] in/out
+    double* s;       // [T+1][2] out
+};
+
+// One LQR step's affine recursions on the cached matrix parts (one CTA of
+// kShortLanes threads; T <= kShortMaxT).  Gains layout as in
+// launch_affine_t: M [T][N][N], Nt and K [T][MC][N]; B [T][N][MC].  Every
+// input is first staged in shared memory by asynchronous copies in four
+// groups, in the order the phases need them (M, abar and the cache; N_t;
+// B_t; K_t), so no phase waits on a dependent global load.
+template <int N, int MC, bool ROLL>
 __global__ void __launch_bounds__(kShortLanes, 1) lqr_short_kernel(const double* __restrict__ Mg,
                                                                    const double* __restrict__ Ng,
                                                                    const double* __restrict__ Kg,
                                                                    const double* __restrict__ Bg, LqrConst Cq,
                                                                    const double* __restrict__ abar, int T,
-                                                                   double* __restrict__ v, double* __restrict__ z) {
+                                                                   const double* __restrict__ cache,
+                                                                   double* __restrict__ v, double* __restrict__ z,
+                                                                   ShortRoll ro) {
+    static_assert(!ROLL || (N == 2 && MC == 2), "the fused rollout is the single integrator's");
     pdl_prologue();
-    __shared__ double ks[kShortMaxT * MC];
-    __shared__ double tot[kShortWarps][N * N + N];
+    extern __shared__ __align__(16) double sm[];
+    double* Ms = sm;                                      // [T][N][N]
+    double* As = Ms + (size_t)T * N * N;                  // [T][N] abar
+    double* Cs = As + (size_t)T * N;                      // the cache
+    double* Ns = Cs + (size_t)2 * kShortRecMats * N * N;  // [T][MC][N]
+    double* Bs = Ns + (size_t)T * MC * N;                 // [T][N][MC]
+    double* Kq = Bs + (size_t)T * N * MC;                 // [T][MC][N]
+    double* ks = Kq + (size_t)T * MC * N;                 // [T][MC]: k_t
+    __shared__ double tphi[kShortWarps][N];
     __shared__ double xw[kShortWarps][N];
     const int g = threadIdx.x, lane = g & 31, warp = g >> 5;
+    auto stage = [&](double* dst, const double* src, int cnt) {
+        for (int i = g; i < cnt; i += kShortLanes) cp_async8(dst + i, src + i);
+    };
+    stage(Ms, Mg, T * N * N);
+    if constexpr (ROLL) {
+        for (int i = g; i < T * N; i += kShortLanes) {
+            const int t = i / N, r = i % N;
+            As[i] = r < ro.d ? (double)ro.a[(size_t)t * ro.d + r] : 0.0;
+        }
+    } else {
+        stage(As, abar, T * N);
+    }
+    stage(Cs, cache, 2 * kShortRecMats * N * N);
+    cp_async_commit();
+    stage(Ns, Ng, T * MC * N);
+    cp_async_commit();
+    stage(Bs, Bg, T * N * MC);
+    cp_async_commit();
+    stage(Kq, Kg, T * MC * N);
+    cp_async_commit();
     const int C = (T + kShortLanes - 1) / kShortLanes;
     const int lo = g * C, hi = min(lo + C, T) - 1;  // empty when lo > hi
     // c_t = -Q abar_{t-1} (t >= 1), c_0 = 0
@@ -998,7 +1117,7 @@ __global__ void __launch_bounds__(kShortLanes, 1) lqr_short_kernel(const double*
             double acc = 0.0;
             if (t >= 1) {
 #pragma unroll
-                for (int q = 0; q < N; ++q) acc = fma(-Cq.Q[r * N + q], abar[(size_t)(t - 1) * N + q], acc);
+                for (int q = 0; q < N; ++q) acc = fma(-Cq.Q[r * N + q], As[(t - 1) * N + q], acc);
             }
             c[r] = acc;
         }
@@ -1009,85 +1128,93 @@ __global__ void __launch_bounds__(kShortLanes, 1) lqr_short_kernel(const double*
         for (int r = 0; r < N; ++r) {
             double acc = 0.0;
 #pragma unroll
-            for (int q = 0; q < MC; ++q) acc = fma(-Bg[((size_t)t * N + r) * MC + q], ks[t * MC + q], acc);
+            for (int q = 0; q < MC; ++q) acc = fma(-Bs[(t * N + r) * MC + q], ks[t * MC + q], acc);
             e[r] = acc;
         }
     };
-    auto put_total = [&](const AffMap<N>& m) {
+    // vector part of the warp scan, the warps' chain (one thread, between
+    // two CTA barriers) and the value entering this lane's chunk
+    auto chain = [&](int r, double (&phi)[N], double (&in)[N]) {
+        const bool bwd = r == 0;
 #pragma unroll
-        for (int e = 0; e < N * N; ++e) tot[warp][e] = m.P[e];
+        for (int k = 0; k < kShortLevels; ++k) {
+            const int off = 1 << k;
+            double o[N], y[N];
+            vec_shfl<N>(phi, o, off, bwd);
+            if (bwd ? lane + off < 32 : lane >= off) {
+                mat_apply<N>(short_lane_mat<N>(Cs, r, g, k), o, phi, y);
 #pragma unroll
-        for (int e = 0; e < N; ++e) tot[warp][N * N + e] = m.p[e];
-    };
-    auto get_total = [&](int w, AffMap<N>& m) {
+                for (int e = 0; e < N; ++e) phi[e] = y[e];
+            }
+        }
+        double ex[N];
+        vec_shfl<N>(phi, ex, 1, bwd);
+        if (lane == (bwd ? 31 : 0)) {
 #pragma unroll
-        for (int e = 0; e < N * N; ++e) m.P[e] = tot[w][e];
+            for (int e = 0; e < N; ++e) ex[e] = 0.0;
+        }
+        if (lane == (bwd ? 0 : 31)) {
 #pragma unroll
-        for (int e = 0; e < N; ++e) m.p[e] = tot[w][N * N + e];
+            for (int e = 0; e < N; ++e) tphi[warp][e] = phi[e];
+        }
+        __syncthreads();
+        if (g == 0) {
+            double x[N], y[N];
+            if (bwd) {
+#pragma unroll
+                for (int i = 0; i < N; ++i) {
+                    double acc = 0.0;
+#pragma unroll
+                    for (int q = 0; q < N; ++q) acc = fma(-Cq.Q[i * N + q], As[(T - 1) * N + q], acc);
+                    x[i] = acc;  // p_T
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < N; ++i) x[i] = 0.0;  // z_0
+            }
+#pragma unroll
+            for (int j = 0; j < kShortWarps; ++j) {
+                const int w = bwd ? kShortWarps - 1 - j : j;
+#pragma unroll
+                for (int i = 0; i < N; ++i) xw[w][i] = x[i];
+                if (j + 1 < kShortWarps) {
+                    mat_apply<N>(short_warp_mat<N>(Cs, r, w), x, tphi[w], y);
+#pragma unroll
+                    for (int i = 0; i < N; ++i) x[i] = y[i];
+                }
+            }
+        }
+        __syncthreads();
+        mat_apply<N>(short_lane_mat<N>(Cs, r, g, kShortLevels), xw[warp], ex, in);
     };
 
     // ---- backward recursion ------------------------------------------------
-    AffMap<N> F;
-    aff_identity(F);
-    for (int t = hi; t >= lo; --t) {  // F: p_{hi+1} -> p_t
-        const double* Mt = Mg + (size_t)t * N * N;
-        double c[N];
-        cvec(t, c);
-        AffMap<N> G;
-#pragma unroll
-        for (int i = 0; i < N; ++i) {
-#pragma unroll
-            for (int cc = 0; cc < N; ++cc) {
-                double acc = 0.0;
-#pragma unroll
-                for (int q = 0; q < N; ++q) acc = fma(Mt[q * N + i], F.P[q * N + cc], acc);
-                G.P[i * N + cc] = acc;
-            }
-            double acc = c[i];
-#pragma unroll
-            for (int q = 0; q < N; ++q) acc = fma(Mt[q * N + i], F.p[q], acc);
-            G.p[i] = acc;
-        }
-        F = G;
-    }
-    // suffix scan over the warp's lanes: F <- F_g o F_{g+1} o ... (later chunks applied first)
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-        const AffMap<N> o = aff_shfl(F, off, true);
-        if (lane + off < 32) aff_compose(F, o);
-    }
-    AffMap<N> E = aff_shfl(F, 1, true);  // the chunks after this lane's, within the warp
-    if (lane == 31) aff_identity(E);
-    if (lane == 0) put_total(F);
-    __syncthreads();
-    if (g == 0) {
-        double x[N], y[N];
-#pragma unroll
-        for (int r = 0; r < N; ++r) {
-            double acc = 0.0;
-#pragma unroll
-            for (int q = 0; q < N; ++q) acc = fma(-Cq.Q[r * N + q], abar[(size_t)(T - 1) * N + q], acc);
-            x[r] = acc;  // p_T
-        }
-        for (int w = kShortWarps - 1; w >= 0; --w) {
-#pragma unroll
-            for (int r = 0; r < N; ++r) xw[w][r] = x[r];
-            if (w > 0) {
-                AffMap<N> Tw;
-                get_total(w, Tw);
-                aff_apply(Tw, x, y);
-#pragma unroll
-                for (int r = 0; r < N; ++r) x[r] = y[r];
-            }
-        }
-    }
+    cp_async_wait_group<3>();
     __syncthreads();
     {
-        double p[N], np[N];
-        aff_apply(E, xw[warp], p);  // p_{hi+1}
+        double phi[N], p[N], np[N];
+#pragma unroll
+        for (int e = 0; e < N; ++e) phi[e] = 0.0;
+        for (int t = hi; t >= lo; --t) {  // phi <- M_t' phi + c_t
+            const double* Mt = Ms + t * N * N;
+            double c[N];
+            cvec(t, c);
+#pragma unroll
+            for (int i = 0; i < N; ++i) {
+                double acc = c[i];
+#pragma unroll
+                for (int q = 0; q < N; ++q) acc = fma(Mt[q * N + i], phi[q], acc);
+                np[i] = acc;
+            }
+#pragma unroll
+            for (int e = 0; e < N; ++e) phi[e] = np[e];
+        }
+        chain(0, phi, p);  // p = p_{hi+1}
+        cp_async_wait_group<2>();
+        __syncthreads();
         for (int t = hi; t >= lo; --t) {
-            const double* Mt = Mg + (size_t)t * N * N;
-            const double* Nt = Ng + (size_t)t * MC * N;
+            const double* Mt = Ms + t * N * N;
+            const double* Nt = Ns + t * MC * N;
 #pragma unroll
             for (int r = 0; r < MC; ++r) {
                 double acc = 0.0;
@@ -1108,73 +1235,48 @@ __global__ void __launch_bounds__(kShortLanes, 1) lqr_short_kernel(const double*
             for (int r = 0; r < N; ++r) p[r] = np[r];
         }
     }
+    cp_async_wait_group<1>();
     __syncthreads();
 
     // ---- forward recursion -------------------------------------------------
-    aff_identity(F);
-    for (int t = lo; t <= hi; ++t) {  // F: z_lo -> z_{t+1}
-        const double* Mt = Mg + (size_t)t * N * N;
-        double e[N];
-        evec(t, e);
-        AffMap<N> G;
+    {
+        double phi[N], w[N], nw[N];
 #pragma unroll
-        for (int i = 0; i < N; ++i) {
+        for (int e = 0; e < N; ++e) phi[e] = 0.0;
+        for (int t = lo; t <= hi; ++t) {  // phi <- M_t phi + e_t
+            const double* Mt = Ms + t * N * N;
+            double e[N];
+            evec(t, e);
 #pragma unroll
-            for (int cc = 0; cc < N; ++cc) {
-                double acc = 0.0;
+            for (int i = 0; i < N; ++i) {
+                double acc = e[i];
 #pragma unroll
-                for (int q = 0; q < N; ++q) acc = fma(Mt[i * N + q], F.P[q * N + cc], acc);
-                G.P[i * N + cc] = acc;
+                for (int q = 0; q < N; ++q) acc = fma(Mt[i * N + q], phi[q], acc);
+                nw[i] = acc;
             }
-            double acc = e[i];
 #pragma unroll
-            for (int q = 0; q < N; ++q) acc = fma(Mt[i * N + q], F.p[q], acc);
-            G.p[i] = acc;
+            for (int i = 0; i < N; ++i) phi[i] = nw[i];
         }
-        F = G;
-    }
-    // prefix scan over the warp's lanes: F <- F_g o F_{g-1} o ... (earlier chunks applied first)
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-        const AffMap<N> o = aff_shfl(F, off, false);
-        if (lane >= off) aff_compose(F, o);
-    }
-    E = aff_shfl(F, 1, false);  // the chunks before this lane's, within the warp
-    if (lane == 0) aff_identity(E);
-    if (lane == 31) put_total(F);
-    __syncthreads();
-    if (g == 0) {
-        double x[N], y[N];
-#pragma unroll
-        for (int r = 0; r < N; ++r) x[r] = 0.0;  // z_0
-        for (int w = 0; w < kShortWarps; ++w) {
-#pragma unroll
-            for (int r = 0; r < N; ++r) xw[w][r] = x[r];
-            if (w + 1 < kShortWarps) {
-                AffMap<N> Tw;
-                get_total(w, Tw);
-                aff_apply(Tw, x, y);
-#pragma unroll
-                for (int r = 0; r < N; ++r) x[r] = y[r];
-            }
-        }
-        if (z) {
+        chain(1, phi, w);  // w = z_lo
+        cp_async_wait_group<0>();
+        __syncthreads();
+        if (g == 0 && z) {
 #pragma unroll
             for (int r = 0; r < N; ++r) z[r] = 0.0;
         }
-    }
-    __syncthreads();
-    {
-        double w[N], nw[N];
-        aff_apply(E, xw[warp], w);  // z_lo
+        double run[MC];  // ROLL: the chunk's sum of dt u_t (new controls)
+#pragma unroll
+        for (int r = 0; r < MC; ++r) run[r] = 0.0;
         for (int t = lo; t <= hi; ++t) {
-            const double* Mt = Mg + (size_t)t * N * N;
-            const double* Kt = Kg + (size_t)t * MC * N;
+            const double* Mt = Ms + t * N * N;
+            const double* Kt = Kq + t * MC * N;
+            double vt[MC];
 #pragma unroll
             for (int r = 0; r < MC; ++r) {
                 double acc = -ks[t * MC + r];
 #pragma unroll
                 for (int q = 0; q < N; ++q) acc = fma(Kt[r * N + q], -w[q], acc);
+                vt[r] = acc;
                 v[(size_t)t * MC + r] = acc;
             }
             double e[N];
@@ -1190,6 +1292,57 @@ __global__ void __launch_bounds__(kShortLanes, 1) lqr_short_kernel(const double*
             for (int r = 0; r < N; ++r) {
                 w[r] = nw[r];
                 if (z) z[(size_t)(t + 1) * N + r] = nw[r];
+            }
+            if constexpr (ROLL) {
+                // u_t += eta v_t; k_t is no longer needed, its slot keeps u_t
+#pragma unroll
+                for (int r = 0; r < MC; ++r) {
+                    const double un = fma(ro.eta, vt[r], ro.u[(size_t)t * MC + r]);
+                    ro.u[(size_t)t * MC + r] = un;
+                    ks[t * MC + r] = un;
+                    run[r] += ro.dt * un;
+                }
+            }
+        }
+        if constexpr (ROLL) {
+            // exclusive prefix of the chunk sums over the lanes, then each
+            // lane's positions s_{t+1} = s_0 + (prefix + running sum)
+            double inc[MC];
+#pragma unroll
+            for (int r = 0; r < MC; ++r) {
+                inc[r] = run[r];
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const double y = __shfl_up_sync(0xffffffffu, inc[r], o);
+                    if (lane >= o) inc[r] += y;
+                }
+                if (lane == 31) tphi[warp][r] = inc[r];
+            }
+            __syncthreads();
+            if (g == 0) {
+                double acc[MC];
+#pragma unroll
+                for (int r = 0; r < MC; ++r) acc[r] = 0.0;
+#pragma unroll
+                for (int w2 = 0; w2 < kShortWarps; ++w2)
+#pragma unroll
+                    for (int r = 0; r < MC; ++r) {
+                        xw[w2][r] = acc[r];
+                        acc[r] += tphi[w2][r];
+                    }
+#pragma unroll
+                for (int r = 0; r < MC; ++r) ro.s[r] = ro.s0[r];
+            }
+            __syncthreads();
+            double acc[MC];
+#pragma unroll
+            for (int r = 0; r < MC; ++r) acc[r] = xw[warp][r] + (inc[r] - run[r]);
+            for (int t = lo; t <= hi; ++t) {
+#pragma unroll
+                for (int r = 0; r < MC; ++r) {
+                    acc[r] += ro.dt * ks[t * MC + r];
+                    ro.s[(size_t)(t + 1) * MC + r] = ro.s0[r] + acc[r];
+                }
             }
         }
     }
@@ -1883,9 +2036,27 @@ static RicPlan ric_plan(int T, int sms) {
 // Gains per step: K [m][n], M [n][n], N [m][n], S^-1 [m][m]; then the
 // parallel Riccati's scratch: per level (chunks, then each grouping level)
 // its maps [count][3][n][n] and the P entering each [count][n][n].
-size_t lqr_gain_doubles(int T, int n, int m) {
+// Longest horizon the one-CTA short kernels take for a state dimension.
+// Their FP64 work runs on one SM: measured against the chunked scans
+// (cov_lqr_track, both in CUDA graphs, random time-varying A_t, before the
+// matrix parts were cached) one CTA saved 7-13 us at N = 1 for T = 64-1024
+// and 3-10 us at N = 2 for T = 64-512, and lost 11 us at N = 2, T = 1024
+// and 1-5 us at N = 3 for T = 64-256.
+#ifndef COV_LQR_SHORT
+#define COV_LQR_SHORT 1
+#endif
+static int short_max_T(int n) {
+    if (!COV_LQR_SHORT) return 0;
+    return n == 1 ? kShortMaxT : (n == 2 ? 512 : 0);
+}
+static bool short_ok(int T, int n) { return T <= short_max_T(n) && (size_t)T * n * n <= (size_t)kShortPreMs; }
+// The short kernels' cache of matrix parts, stored after the gains.
+static size_t short_cache_doubles(int T, int n) { return short_ok(T, n) ? (size_t)2 * kShortRecMats * n * n : 0; }
+static size_t gain_base_doubles(int T, int n, int m) {
     return (size_t)T * (2 * (size_t)m * n + (size_t)n * n + (size_t)m * m) + ric_scratch_maps(T) * 4 * n * n;
 }
+
+size_t lqr_gain_doubles(int T, int n, int m) { return gain_base_doubles(T, n, m) + short_cache_doubles(T, n); }
 
 // Affine scan buffers: forcing terms, k, and the scan scratch (chunk maps
 // and boundary values, then the maps and boundary values of the grouping
@@ -1974,6 +2145,18 @@ static void launch_riccati_t(const double* A, const double* B, const LqrConst& C
                (const double*)pin[0], pl.C1);
 }
 
+// The short kernels' matrix parts from fresh gains (horizons they take).
+template <int N, int MC>
+static void launch_short_pre_t(double* gains, int T, cudaStream_t s) {
+    if constexpr (N <= 2) {
+        if (short_ok(T, N)) {
+            const double* M = gains + (size_t)T * MC * N;
+            launch_pdl(lqr_short_pre_kernel<N>, dim3(1), dim3(kShortLanes), 0, s, M, T,
+                       gains + gain_base_doubles(T, N, MC));
+        }
+    }
+}
+
 // R^-1 on the host (m <= 3, Gauss-Jordan with partial pivoting).
 static bool invert_small(const double* R, int m, double* Ri) {
     double a[COV_MAX_M][2 * COV_MAX_M];
@@ -2026,20 +2209,6 @@ static void launch_boundaries(const ScanPlan& pl, const AffineBufs& ab, const Lq
                    (const double*)maps[l], pl.n[l], pl.G[l], (const double*)bnd[l + 1], C, abar, w0, T, bnd[l]);
 }
 
-// Longest horizon the one-CTA kernel takes for a state dimension.  Its FP64
-// work (compositions of N x (N + 1) maps, N^2 (N + 1) FMAs each, five of
-// them in the lane scan) runs on one SM: measured against the chunked scans
-// (cov_lqr_track, both in CUDA graphs) it saved 5-9 us at N = 2 for
-// T = 64-256, broke even at T = 512 and lost 11 us at T = 1024; at N = 3 it
-// lost 1-5 us already at T = 64-256.
-#ifndef COV_LQR_SHORT
-#define COV_LQR_SHORT 1
-#endif
-static int short_max_T(int n) {
-    if (!COV_LQR_SHORT) return 0;
-    return n == 1 ? kShortMaxT : (n == 2 ? 512 : 0);
-}
-
 template <int N, int MC>
 static void launch_affine_t(const double* B, const double* gains, const LqrConst& C, const double* abar, int T,
                             const ScanPlan& pl, const AffineBufs& ab, double* v, double* z, cudaStream_t s) {
@@ -2047,8 +2216,11 @@ static void launch_affine_t(const double* B, const double* gains, const LqrConst
     const double* M = gains + (size_t)T * MC * N;
     const double* Nt = M + (size_t)T * N * N;
     if constexpr (N <= 2) {
-        if (T <= short_max_T(N)) {
-            launch_pdl(lqr_short_kernel<N, MC>, dim3(1), dim3(kShortLanes), 0, s, M, Nt, K, B, C, abar, T, v, z);
+        if (short_ok(T, N)) {
+            const double* cache = gains + gain_base_doubles(T, N, MC);
+            launch_pdl(lqr_short_kernel<N, MC, false>, dim3(1), dim3(kShortLanes),
+                       sizeof(double) * short_smem_doubles(T, N, MC), s, M, Nt, K, B, C, abar, T, cache, v, z,
+                       ShortRoll{});
             return;
         }
     }
@@ -2069,6 +2241,16 @@ static void set_attrs_t() {
     const int big = (int)(sizeof(double) * kMaxChunks * N * (N + 1));
     cudaFuncSetAttribute(boundaries_kernel<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     cudaFuncSetAttribute(boundaries_kernel<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    if constexpr (N <= 2) {
+        if (short_max_T(N) > 0)
+            cudaFuncSetAttribute(lqr_short_kernel<N, MC, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(sizeof(double) * short_smem_doubles(short_max_T(N), N, MC)));
+        if constexpr (N == 2 && MC == 2) {
+            if (short_max_T(N) > 0)
+                cudaFuncSetAttribute(lqr_short_kernel<N, MC, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)(sizeof(double) * short_smem_doubles(short_max_T(N), N, MC)));
+        }
+    }
 }
 
 #define COV_LQR_DISPATCH(MACRO) \
@@ -2091,6 +2273,7 @@ cov_status lqr_riccati(cov_ctx* ctx, int n, int m, const double* A, const double
 #define COV_RIC_CASE(NN, MM)                                                      \
     if (n == NN && m == MM) {                                                     \
         launch_riccati_t<NN, MM>(A, B, C, Ci, T, gains, ctx->num_sms, ctx->status, stream);     \
+        launch_short_pre_t<NN, MM>(gains, T, stream);                             \
         return cuda_failed(ctx, cudaGetLastError()) ? COV_ERR_CUDA : COV_OK;     \
     }
     COV_LQR_DISPATCH(COV_RIC_CASE)
@@ -2117,6 +2300,37 @@ cov_status lqr_affine(cov_ctx* ctx, void* ws, size_t ws_bytes, int n, int m, con
     COV_LQR_DISPATCH(COV_AFF_CASE)
 #undef COV_AFF_CASE
     return COV_ERR_UNSUPPORTED;
+}
+
+// The single integrator's LQR step, control update and rollout in one
+// launch (short horizons): a [T][d] the field (lifted inside), v [T][2]
+// written, u [T][2] updated, s [T+1][2] the new trajectory from s0.
+// COV_ERR_UNSUPPORTED outside the short kernel's range (the caller then
+// runs the lift, lqr_affine and update_rollout).
+cov_status lqr_step_single_int(cov_ctx* ctx, const double* B, const double* gains, const double* Q, const float* a,
+                               int d, int T, double* v, double eta, double dt, const double* s0, double* u, double* s,
+                               cudaStream_t stream) {
+    constexpr int N = 2, MC = 2;
+    if (!short_ok(T, N) || d < 1 || d > N) return COV_ERR_UNSUPPORTED;
+    LqrConst C;
+    const double R1[COV_MAX_M * COV_MAX_M] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+    if (!make_lqr_const(Q, R1, N, MC, &C)) return COV_ERR_INVALID_ARG;
+    const double* K = gains;
+    const double* M = gains + (size_t)T * MC * N;
+    const double* Nt = M + (size_t)T * N * N;
+    const double* cache = gains + gain_base_doubles(T, N, MC);
+    ShortRoll ro{};
+    ro.a = a;
+    ro.d = d;
+    ro.eta = eta;
+    ro.dt = dt;
+    ro.s0[0] = s0[0];
+    ro.s0[1] = s0[1];
+    ro.u = u;
+    ro.s = s;
+    launch_pdl(lqr_short_kernel<N, MC, true>, dim3(1), dim3(kShortLanes), sizeof(double) * short_smem_doubles(T, N, MC),
+               stream, M, Nt, K, B, C, (const double*)nullptr, T, cache, v, (double*)nullptr, ro);
+    return cuda_failed(ctx, cudaGetLastError()) ? COV_ERR_CUDA : COV_OK;
 }
 
 cov_status lqr_track_ws(cov_ctx* ctx, void* ws, size_t ws_bytes, const double* A, const double* B, const double* Q,

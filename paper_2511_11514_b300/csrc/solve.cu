@@ -16,6 +16,9 @@ int model_dims(int model, int* n, int* m);
 size_t lqr_gain_doubles(int T, int n, int m);
 cov_status lqr_riccati(cov_ctx* ctx, int n, int m, const double* A, const double* B, const double* Q,
                        const double* R, int T, double* gains, cudaStream_t stream);
+cov_status lqr_step_single_int(cov_ctx* ctx, const double* B, const double* gains, const double* Q, const float* a,
+                               int d, int T, double* v, double eta, double dt, const double* s0, double* u, double* s,
+                               cudaStream_t stream);
 cov_status lqr_affine(cov_ctx* ctx, void* ws, size_t ws_bytes, int n, int m, const double* B, const double* gains,
                       const double* Q, const double* abar, int T, double* v_out, double* z_out, cudaStream_t stream);
 cov_status update_rollout(cov_ctx* ctx, int model, const double* s0, double* u, const double* v, double eta, int T,
@@ -193,6 +196,12 @@ static cov_status validate(const cov_problem* P, int* n, int* m) {
     return COV_OK;
 }
 
+// The single integrator's fused LQR step + update + rollout for short
+// horizons (build flag -DCOV_FUSED_SINGLE=0 takes the separate kernels).
+#ifndef COV_FUSED_SINGLE
+#define COV_FUSED_SINGLE 1
+#endif
+
 // Enqueue one outer iteration on `st`.
 static cov_status enqueue_iteration(cov_ctx* ctx, const cov_problem* P, int n, int m, const SolveBufs& b, void* rest,
                                     size_t rest_bytes, double* u, double* s, cudaStream_t st) {
@@ -216,6 +225,11 @@ static cov_status enqueue_iteration(cov_ctx* ctx, const cov_problem* P, int n, i
         r = svgd_field_ws(ctx, rest, rest_bytes, b.x, d, T, d, nullptr, &P->gmm, P->h, b.a, st);
     }
     if (r != COV_OK) return r;
+    if (COV_FUSED_SINGLE && P->model == COV_SINGLE_INT) {
+        // short horizons: LQR step, control update and rollout in one launch
+        r = lqr_step_single_int(ctx, b.B, b.gains, P->Q, b.a, d, T, b.v, P->eta, P->dt, P->s0, u, s, st);
+        if (r != COV_ERR_UNSUPPORTED) return r;
+    }
     launch_pdl(lift_kernel, dim3(nb), dim3(256), 0, st, b.a, T, n, d, b.abar);
     if (!model_is_lti(P->model)) {
         r = linearize_launch(ctx, P->model, s, u, T, P->dt, b.A, b.B, st);

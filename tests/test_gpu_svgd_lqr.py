@@ -149,6 +149,35 @@ def test_linearize_and_rollout_match_oracle(cov, ctx, orc, model, T):
     np.testing.assert_allclose(host(B), Bo, rtol=1e-13, atol=1e-15)
 
 
+@pytest.mark.parametrize("T", [1, 100, 256, 512, 513])
+def test_single_integrator_fused_step_matches_oracle(cov, ctx, orc, T):
+    """Up to T = 512 the single integrator's LQR step, control update and
+    rollout run as one launch (the short kernel with the update fused; T =
+    513 takes the separate kernels): one outer iteration of the Stein field
+    against the oracle's, controls and trajectory, and two more outer
+    iterations on the same context (cached gains and short-kernel matrices)."""
+    w = dataclasses.replace(wl.SVGD_SINGLE_T256, name="svgd_fused_check", T=T, dt=0.1 * 256 / max(T, 100), n_outer=1)
+    inst = wl.make_instance(w)
+    gmm = tuple(wl.f32_pair(v)[1] for v in inst.gmm)
+    prob = cov.make_problem(w.model, w.T, w.dt, inst.s0, w.field, inst.Q, inst.R, w.eta, gmm=gmm, h=w.h)
+    s_init = orc.rollout(w.model, inst.s0, inst.u0, w.dt)
+    u = dev64(inst.u0)
+    s = cov.cov_solve(ctx, prob, 1, u)
+    st, flags = ctx.device_status()
+    assert st == cov.COV_OK, flags
+    uo, so = orc.solve(w.model, w.dt, inst.s0, inst.u0, w.field, inst.Q, inst.R, w.eta, 1, gmm=gmm, h=w.h)
+    assert rel_norm(host(s) - s_init, so - s_init) <= 1e-4
+    assert rel_norm(host(u) - inst.u0, uo - inst.u0) <= 1e-4
+    np.testing.assert_array_equal(host(s)[0], inst.s0)
+    # the new trajectory is the rollout of the new controls
+    np.testing.assert_allclose(host(s), orc.rollout(w.model, inst.s0, host(u), w.dt), rtol=0, atol=1e-12)
+    cov.cov_solve_continue(ctx, prob, 2, u, s)
+    assert ctx.device_status()[0] == cov.COV_OK
+    uo3, so3 = orc.solve(w.model, w.dt, inst.s0, inst.u0, w.field, inst.Q, inst.R, w.eta, 3, gmm=gmm, h=w.h)
+    assert rel_norm(host(s) - s_init, so3 - s_init) <= 1e-4
+    np.testing.assert_allclose(host(s), orc.rollout(w.model, inst.s0, host(u), w.dt), rtol=0, atol=1e-12)
+
+
 @pytest.mark.parametrize("model", [wl.SINGLE_INT, wl.DOUBLE_INT, wl.UNICYCLE])
 def test_rollout_update_in_solve_matches_oracle(cov, ctx, orc, model):
     """The update u += eta v fused into the chunked rollout (the cov_solve
