@@ -172,6 +172,11 @@ cov_status density_score_launch(cov_ctx* ctx, const float* map, int H, int W, co
                                 float* score, cudaStream_t stream);
 cov_status svgd_field_ws(cov_ctx* ctx, void* ws, size_t ws_bytes, const float* x, int x_ld, int T, int d,
                          const float* score, const cov_gmm* gmm, float h, float* a_out, cudaStream_t stream);
+// The Stein field of a short trajectory (T <= 1024) in one launch, reading
+// the points as x[j x_ld + c] (FP64 states when x_double); COV_ERR_UNSUPPORTED
+// for longer ones.  svgd_field_ws takes it itself where it applies.
+cov_status svgd_field_small(cov_ctx* ctx, const void* x, bool x_double, int x_ld, int T, int d, const float* score,
+                            const cov_gmm* gmm, float h, float* a_out, cudaStream_t stream);
 // Reverse mode of the Stein field (svgd_vjp.cu) on an explicit workspace:
 // x, abar [T][d] row-major; score [T][d] or nullptr (then the mixture's);
 // xbar [T][d] written; sbar [T][d] or nullptr; the mixture gradients

@@ -57,6 +57,11 @@ constexpr int kWarps = 4;    // warps per CTA, each takes a quarter of a tile
 constexpr int kThreads = 32 * kWarps;
 constexpr int kRowPad = 1024;  // point arrays are padded to this multiple
 constexpr float kSvgdPad = 1.0e15f;  // SVGD padding coordinate (kernel -> 0)
+// The one-launch Stein field for short trajectories (build flag
+// -DCOV_SVGD_SMALL=0 takes the all-pairs kernel at every T).
+#ifndef COV_SVGD_SMALL
+#define COV_SVGD_SMALL 1
+#endif
 
 struct PairArgs {
     const float* rows;   // [D][row_ld]
@@ -1791,6 +1796,128 @@ __global__ void svgd_prep_kernel(const float* __restrict__ x, int x_ld, int T, i
     if (!ok) raise_status(status, kDevNonfinite);
 }
 
+// Stein field of a short trajectory in one launch (T <= kSvSmallMaxT):
+// every CTA forms the prescaled coordinates and scores of all T points in
+// shared memory (the mixture score recomputed per CTA, T K exponentials,
+// small next to its rows' pairs), then sums its 32 rows over all T columns
+// in the arithmetic of the all-pairs kernel's Stein pass,
+//   a_i = a_scale sum_j 2^(-|xt_i - xt_j|^2) (st_j + xt_i - xt_j),
+// warp q taking the columns j = q (mod 8) for all 32 rows (its lanes read the
+// same column: shared-memory broadcasts), and the 8 partial sums of a row
+// added in warp order.  The points are read as x[j x_ld + c] for j < T
+// (float coordinates, or the FP64 states of a solve, which this also
+// extracts).
+constexpr int kSvSmallRows = 32;
+constexpr int kSvSmallSplits = 8;
+constexpr int kSvSmallThreads = kSvSmallRows * kSvSmallSplits;
+constexpr int kSvSmallMaxT = 1024;
+
+template <int D, typename XT>
+__global__ void __launch_bounds__(kSvSmallThreads) svgd_small_kernel(const XT* __restrict__ x, int x_ld, int T,
+                                                                     const float* __restrict__ score, GmmParams G,
+                                                                     int use_gmm, float inv_hs, float hs,
+                                                                     float a_scale, float* __restrict__ a_out,
+                                                                     unsigned* status) {
+    pdl_prologue();
+    extern __shared__ float sv[];  // xt [D][T], st [D][T]
+    __shared__ float red[kSvSmallSplits][D][kSvSmallRows];
+    float* xs = sv;
+    float* ss = sv + (size_t)D * T;
+    bool ok = true;
+    for (int j = threadIdx.x; j < T; j += kSvSmallThreads) {
+        float xv[D], sc[D];
+#pragma unroll
+        for (int c = 0; c < D; ++c) xv[c] = (float)x[(size_t)j * x_ld + c];
+        if (use_gmm) {
+            gmm_score_at(G, xv, D, sc);
+        } else {
+#pragma unroll
+            for (int c = 0; c < D; ++c) sc[c] = score[(size_t)j * D + c];
+        }
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            xs[(size_t)c * T + j] = xv[c] * inv_hs;
+            ss[(size_t)c * T + j] = sc[c] * hs;
+            ok &= finitef(xv[c]) && finitef(sc[c]);
+        }
+    }
+    if (!ok && blockIdx.x == 0) raise_status(status, kDevNonfinite);
+    __syncthreads();
+    const int r = threadIdx.x % kSvSmallRows, q = threadIdx.x / kSvSmallRows;
+    const int i = min(blockIdx.x * kSvSmallRows + r, T - 1);  // rows past T repeat the last (not stored)
+    float xi[D], acc[D];
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+        xi[c] = xs[(size_t)c * T + i];
+        acc[c] = 0.f;
+    }
+    for (int j = q; j < T; j += kSvSmallSplits) {
+        float dl[D], r2 = 0.f;
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            dl[c] = xi[c] - xs[(size_t)c * T + j];
+            r2 = fmaf(dl[c], dl[c], r2);
+        }
+        const float k = ex2(-r2);
+#pragma unroll
+        for (int c = 0; c < D; ++c) acc[c] = fmaf(k, ss[(size_t)c * T + j] + dl[c], acc[c]);
+    }
+#pragma unroll
+    for (int c = 0; c < D; ++c) red[q][c][r] = acc[c];
+    __syncthreads();
+    if (threadIdx.x < kSvSmallRows * D) {
+        const int rr = threadIdx.x % kSvSmallRows, c = threadIdx.x / kSvSmallRows;
+        const int ii = blockIdx.x * kSvSmallRows + rr;
+        float sum = 0.f;
+#pragma unroll
+        for (int u = 0; u < kSvSmallSplits; ++u) sum += red[u][c][rr];
+        if (ii < T) a_out[(size_t)ii * D + c] = sum * a_scale;
+    }
+}
+
+template <typename XT>
+static cudaError_t launch_svgd_small(int d, const XT* x, int x_ld, int T, const float* score, const GmmParams& G,
+                                     int use_gmm, float inv_hs, float hs, float a_scale, float* a_out,
+                                     unsigned* status, cudaStream_t st) {
+    const dim3 grid((T + kSvSmallRows - 1) / kSvSmallRows), block(kSvSmallThreads);
+    const size_t smem = sizeof(float) * 2 * (size_t)d * T;
+    switch (d) {
+#define COV_SV_SMALL(DD)                                                                                          \
+    case DD:                                                                                                    \
+        return launch_pdl(svgd_small_kernel<DD, XT>, grid, block, smem, st, x, x_ld, T, score, G, use_gmm, inv_hs, \
+                          hs, a_scale, a_out, status);
+        COV_SV_SMALL(1) COV_SV_SMALL(2) COV_SV_SMALL(3) COV_SV_SMALL(4) COV_SV_SMALL(5) COV_SV_SMALL(6)
+#undef COV_SV_SMALL
+    }
+    return cudaErrorInvalidValue;
+}
+
+// The one-launch Stein field when T <= kSvSmallMaxT (x_double: x points to
+// FP64 states), else COV_ERR_UNSUPPORTED.
+cov_status svgd_field_small(cov_ctx* ctx, const void* x, bool x_double, int x_ld, int T, int d, const float* score,
+                            const cov_gmm* gmm, float h, float* a_out, cudaStream_t stream) {
+    // (the staged points and the partial sums within the default 48 KB of shared memory)
+    if (T > kSvSmallMaxT || !COV_SVGD_SMALL ||
+        sizeof(float) * ((size_t)2 * d * T + (size_t)kSvSmallSplits * d * kSvSmallRows) > 48 * 1024)
+        return COV_ERR_UNSUPPORTED;
+    if (!ctx || !x || !a_out || T < 1 || d < 1 || d > COV_MAX_D || x_ld < d || !(h > 0.f) || !isfinite(h))
+        return COV_ERR_INVALID_ARG;
+    GmmParams G{};
+    const int use_gmm = score ? 0 : 1;
+    if (use_gmm) {
+        const cov_status s = make_gmm_params(gmm, d, &G);
+        if (s != COV_OK) return s;
+    }
+    const double r2l = sqrt(2.0 * 0.69314718055994531);
+    const float inv_hs = (float)(1.0 / (h * r2l)), hs = (float)(h / r2l), a_scale = (float)(r2l / ((double)h * T));
+    const cudaError_t e =
+        x_double ? launch_svgd_small(d, static_cast<const double*>(x), x_ld, T, score, G, use_gmm, inv_hs, hs, a_scale,
+                                     a_out, ctx->status, stream)
+                 : launch_svgd_small(d, static_cast<const float*>(x), x_ld, T, score, G, use_gmm, inv_hs, hs, a_scale,
+                                     a_out, ctx->status, stream);
+    return cuda_failed(ctx, e) ? COV_ERR_CUDA : COV_OK;
+}
+
 struct SvBufs {
     float *xt, *st, *part;
     unsigned* counters;
@@ -1817,6 +1944,12 @@ cov_status svgd_field_ws(cov_ctx* ctx, void* ws, size_t ws_bytes, const float* x
                          const float* score, const cov_gmm* gmm, float h, float* a_out, cudaStream_t stream) {
     if (!ctx || !x || !a_out || T < 1 || d < 1 || d > COV_MAX_D || x_ld < d || !(h > 0.f) || !isfinite(h))
         return COV_ERR_INVALID_ARG;
+    // the workspace the call is documented to need, whichever path runs
+    if (!ws || svgd_ws_bytes(T, d) > ws_bytes) return COV_ERR_WORKSPACE;
+    {
+        const cov_status s = svgd_field_small(ctx, x, false, x_ld, T, d, score, gmm, h, a_out, stream);
+        if (s != COV_ERR_UNSUPPORTED) return s;
+    }
     GmmParams G{};
     const int use_gmm = score ? 0 : 1;
     if (use_gmm) {

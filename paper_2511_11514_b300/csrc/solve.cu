@@ -207,24 +207,30 @@ static cov_status enqueue_iteration(cov_ctx* ctx, const cov_problem* P, int n, i
                                     size_t rest_bytes, double* u, double* s, cudaStream_t st) {
     const int T = P->T, d = P->d;
     const int nb = (T + 255) / 256;
-    launch_pdl(extract_kernel, dim3(nb), dim3(256), 0, st, s, T, n, d, b.x);
-    cov_status r;
-    if (P->field == COV_FIELD_SINKHORN) {
-        const bool warm = P->warm == 1;
-        r = sinkhorn_field_ws(ctx, rest, rest_bytes, b.x, d, T, P->y, P->b, P->M, d, P->eps, P->n_iter,
-                              warm ? COV_WARM_START : 0, warm ? b.f : nullptr, warm ? b.g : nullptr,
-                              warm ? b.p : nullptr, b.a, st, b.scal, P->eps_start, P->eps_decay);
+    cov_status r = COV_ERR_UNSUPPORTED;
+    if (P->field == COV_FIELD_SVGD && !P->density) {
+        // short trajectories: the Stein field straight from the states s_1 .. s_T
+        r = svgd_field_small(ctx, s + n, true, n, T, d, nullptr, &P->gmm, P->h, b.a, st);
+        if (r != COV_OK && r != COV_ERR_UNSUPPORTED) return r;
     }
-    else if (P->density) {
-        // the score of the density reference, then the field (b.abar is free
-        // until the lift below: the score is kept there in FP32)
-        float* score = reinterpret_cast<float*>(b.abar);
-        r = density_score_launch(ctx, P->density, P->density_h, P->density_w, b.x, d, T, score, st);
-        if (r == COV_OK) r = svgd_field_ws(ctx, rest, rest_bytes, b.x, d, T, d, score, nullptr, P->h, b.a, st);
-    } else {
-        r = svgd_field_ws(ctx, rest, rest_bytes, b.x, d, T, d, nullptr, &P->gmm, P->h, b.a, st);
+    if (r == COV_ERR_UNSUPPORTED) {
+        launch_pdl(extract_kernel, dim3(nb), dim3(256), 0, st, s, T, n, d, b.x);
+        if (P->field == COV_FIELD_SINKHORN) {
+            const bool warm = P->warm == 1;
+            r = sinkhorn_field_ws(ctx, rest, rest_bytes, b.x, d, T, P->y, P->b, P->M, d, P->eps, P->n_iter,
+                                  warm ? COV_WARM_START : 0, warm ? b.f : nullptr, warm ? b.g : nullptr,
+                                  warm ? b.p : nullptr, b.a, st, b.scal, P->eps_start, P->eps_decay);
+        } else if (P->density) {
+            // the score of the density reference, then the field (b.abar is
+            // free until the lift below: the score is kept there in FP32)
+            float* score = reinterpret_cast<float*>(b.abar);
+            r = density_score_launch(ctx, P->density, P->density_h, P->density_w, b.x, d, T, score, st);
+            if (r == COV_OK) r = svgd_field_ws(ctx, rest, rest_bytes, b.x, d, T, d, score, nullptr, P->h, b.a, st);
+        } else {
+            r = svgd_field_ws(ctx, rest, rest_bytes, b.x, d, T, d, nullptr, &P->gmm, P->h, b.a, st);
+        }
+        if (r != COV_OK) return r;
     }
-    if (r != COV_OK) return r;
     if (COV_FUSED_SINGLE && P->model == COV_SINGLE_INT) {
         // short horizons: LQR step, control update and rollout in one launch
         r = lqr_step_single_int(ctx, b.B, b.gains, P->Q, b.a, d, T, b.v, P->eta, P->dt, P->s0, u, s, st);
