@@ -13,8 +13,12 @@ pytestmark = pytest.mark.gpu
 
 
 @pytest.mark.parametrize("T,d,K", [(1, 2, 1), (2, 2, 3), (37, 1, 2), (256, 2, 3), (1000, 3, 4), (4099, 2, 16),
-                                   (300, 6, 5)])
+                                   (300, 6, 5), (31, 2, 2), (33, 3, 2), (1024, 2, 3), (1025, 2, 3), (896, 6, 3),
+                                   (897, 6, 2)])
 def test_svgd_field_with_mixture_score(cov, ctx, orc, T, d, K):
+    """Both paths against the oracle: the one-launch kernel (T <= 1024, and
+    for d = 6 T <= 896 by its shared memory; 32 rows per CTA, ragged last
+    block) and the all-pairs kernel past them."""
     w, mu, sigma = wl.gmm_params(K, seed=T + K, d=d)
     w, mu, sigma = (wl.f32_pair(v)[1] for v in (w, mu, sigma))
     x = wl.random_points(T, d, seed=T)
