@@ -994,7 +994,7 @@ __device__ __forceinline__ void mat_apply(const double* P, const double* x, cons
 // threads): BWD chunk map Phi = M_lo' ... M_hi', FWD Phi = M_hi ... M_lo,
 // and their warp scans, into `cache`.  M is staged in shared memory first
 // (T N^2 <= kShortPreMs).
-constexpr int kShortPreMs = 2048;
+constexpr int kShortPreMs = 4096;
 template <int N>
 __global__ void __launch_bounds__(kShortLanes, 1) lqr_short_pre_kernel(const double* __restrict__ Mg, int T,
                                                                        double* __restrict__ cache) {
@@ -2045,18 +2045,36 @@ static RicPlan ric_plan(int T, int sms) {
 #ifndef COV_LQR_SHORT
 #define COV_LQR_SHORT 1
 #endif
+#ifndef COV_LQR_SHORT_T1
+#define COV_LQR_SHORT_T1 1024
+#endif
+#ifndef COV_LQR_SHORT_T2
+#define COV_LQR_SHORT_T2 512
+#endif
+#ifndef COV_LQR_SHORT_T3
+#define COV_LQR_SHORT_T3 0
+#endif
 static int short_max_T(int n) {
     if (!COV_LQR_SHORT) return 0;
-    return n == 1 ? kShortMaxT : (n == 2 ? 512 : 0);
+    return std::min(kShortMaxT, n == 1 ? COV_LQR_SHORT_T1 : (n == 2 ? COV_LQR_SHORT_T2 : (n == 3 ? COV_LQR_SHORT_T3 : 0)));
 }
-static bool short_ok(int T, int n) { return T <= short_max_T(n) && (size_t)T * n * n <= (size_t)kShortPreMs; }
+// Dynamic shared memory the step kernel may take (the 227 KB opt-in
+// maximum less room for its static arrays).
+constexpr size_t kShortSmemMax = (size_t)220 * 1024;
+// In range, and the staged inputs fit one CTA's shared memory.
+static bool short_ok(int T, int n, int m) {
+    return T <= short_max_T(n) && (size_t)T * n * n <= (size_t)kShortPreMs &&
+           sizeof(double) * short_smem_doubles(T, n, m) <= kShortSmemMax;
+}
 // The short kernels' cache of matrix parts, stored after the gains.
-static size_t short_cache_doubles(int T, int n) { return short_ok(T, n) ? (size_t)2 * kShortRecMats * n * n : 0; }
+static size_t short_cache_doubles(int T, int n, int m) {
+    return short_ok(T, n, m) ? (size_t)2 * kShortRecMats * n * n : 0;
+}
 static size_t gain_base_doubles(int T, int n, int m) {
     return (size_t)T * (2 * (size_t)m * n + (size_t)n * n + (size_t)m * m) + ric_scratch_maps(T) * 4 * n * n;
 }
 
-size_t lqr_gain_doubles(int T, int n, int m) { return gain_base_doubles(T, n, m) + short_cache_doubles(T, n); }
+size_t lqr_gain_doubles(int T, int n, int m) { return gain_base_doubles(T, n, m) + short_cache_doubles(T, n, m); }
 
 // Affine scan buffers: forcing terms, k, and the scan scratch (chunk maps
 // and boundary values, then the maps and boundary values of the grouping
@@ -2148,8 +2166,8 @@ static void launch_riccati_t(const double* A, const double* B, const LqrConst& C
 // The short kernels' matrix parts from fresh gains (horizons they take).
 template <int N, int MC>
 static void launch_short_pre_t(double* gains, int T, cudaStream_t s) {
-    if constexpr (N <= 2) {
-        if (short_ok(T, N)) {
+    if constexpr (N <= 3) {
+        if (short_ok(T, N, MC)) {
             const double* M = gains + (size_t)T * MC * N;
             launch_pdl(lqr_short_pre_kernel<N>, dim3(1), dim3(kShortLanes), 0, s, M, T,
                        gains + gain_base_doubles(T, N, MC));
@@ -2215,8 +2233,8 @@ static void launch_affine_t(const double* B, const double* gains, const LqrConst
     const double* K = gains;
     const double* M = gains + (size_t)T * MC * N;
     const double* Nt = M + (size_t)T * N * N;
-    if constexpr (N <= 2) {
-        if (short_ok(T, N)) {
+    if constexpr (N <= 3) {
+        if (short_ok(T, N, MC)) {
             const double* cache = gains + gain_base_doubles(T, N, MC);
             launch_pdl(lqr_short_kernel<N, MC, false>, dim3(1), dim3(kShortLanes),
                        sizeof(double) * short_smem_doubles(T, N, MC), s, M, Nt, K, B, C, abar, T, cache, v, z,
@@ -2241,14 +2259,16 @@ static void set_attrs_t() {
     const int big = (int)(sizeof(double) * kMaxChunks * N * (N + 1));
     cudaFuncSetAttribute(boundaries_kernel<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     cudaFuncSetAttribute(boundaries_kernel<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    if constexpr (N <= 2) {
+    if constexpr (N <= 3) {
         if (short_max_T(N) > 0)
             cudaFuncSetAttribute(lqr_short_kernel<N, MC, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(sizeof(double) * short_smem_doubles(short_max_T(N), N, MC)));
+                                 (int)std::min<size_t>(sizeof(double) * short_smem_doubles(short_max_T(N), N, MC),
+                                                       kShortSmemMax));
         if constexpr (N == 2 && MC == 2) {
             if (short_max_T(N) > 0)
                 cudaFuncSetAttribute(lqr_short_kernel<N, MC, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)(sizeof(double) * short_smem_doubles(short_max_T(N), N, MC)));
+                                     (int)std::min<size_t>(sizeof(double) * short_smem_doubles(short_max_T(N), N, MC),
+                                                           kShortSmemMax));
         }
     }
 }
@@ -2311,7 +2331,7 @@ cov_status lqr_step_single_int(cov_ctx* ctx, const double* B, const double* gain
                                int d, int T, double* v, double eta, double dt, const double* s0, double* u, double* s,
                                cudaStream_t stream) {
     constexpr int N = 2, MC = 2;
-    if (!short_ok(T, N) || d < 1 || d > N) return COV_ERR_UNSUPPORTED;
+    if (!short_ok(T, N, MC) || d < 1 || d > N) return COV_ERR_UNSUPPORTED;
     LqrConst C;
     const double R1[COV_MAX_M * COV_MAX_M] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
     if (!make_lqr_const(Q, R1, N, MC, &C)) return COV_ERR_INVALID_ARG;
