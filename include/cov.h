@@ -335,7 +335,9 @@ COV_API cov_status cov_rollout(cov_ctx* ctx, int model, const double* s0,
  *   z_{t+1} = A_t z_t + B_t v_t, z_0 = 0,
  * by the backward Riccati recursion and a forward rollout, in FP64, both as
  * parallel-in-time scans over chunks of the horizon (horizons under 64 steps
- * run the serial recursion in one warp).
+ * run the serial Riccati recursion in one warp; short horizons of state
+ * dimension 1 (T <= 1024) and 2 (T <= 512) run both affine recursions in
+ * one thread block).
  *   A [T][n][n], B [T][n][m]  FP64 device
  *   Q [n][n] (PSD), R [m][m] (SPD)  FP64 HOST
  *   abar [T][n] FP64 device: row t-1 holds the target at time t = 1..T
