@@ -9,9 +9,16 @@
 namespace cov {
 
 constexpr int kTcRows = 128;                       // rows per CTA (MMA M)
-constexpr int kTcCols = 256;                       // columns per tile (MMA N)
+#ifndef COV_TC_COLS
+#define COV_TC_COLS 256
+#endif
+#ifndef COV_TC_READERS
+#define COV_TC_READERS 16
+#endif
+constexpr int kTcCols = COV_TC_COLS;               // columns per tile (MMA N)
 constexpr int kTcStages = 2;                       // shared-memory ring of column tiles
-constexpr int kTcSoftWarps = 16;                   // accumulator readers: 4 lane quarters x 4 column quarters
+constexpr int kTcSoftWarps = COV_TC_READERS;       // accumulator readers: 4 lane quarters x (kTcCols / 64) column groups
+static_assert(kTcSoftWarps * 16 == kTcCols, "each reader warp takes 32 lanes x 64 columns of a tile");
 constexpr int kTcColGroups = kTcSoftWarps / 4;     // column groups of a tile, 64 columns each
 constexpr int kTcThreads = 32 * (kTcSoftWarps + 1);
 constexpr int kTcTmemCols = 2 * kTcCols;           // two accumulator buffers (all 512 columns of the SM)
