@@ -2,11 +2,11 @@
 // matrix on the 5th-generation tensor cores.  Included by field.cu (it uses
 // PairArgs, PairLaunch, the epilogue and the split merge defined there).
 //
-// For one CTA of 128 rows and a tile of 128 columns the base-2 exponent,
+// For one CTA of 128 rows and a tile of kTcCols (256) columns the base-2 exponent,
 // minus the row's fixed offset o_i (the previous log-sum-exp of the row),
 //     w_ij - o_i = h_j + 2 xhat_i . yhat_j - o_i,
 // is a rank-(d + 2) contraction.  It is computed exactly enough in FP32
-// arithmetic by two kind::tf32 MMAs (M = 128, N = 128, K = 8 each) from
+// arithmetic by two kind::tf32 MMAs (M = 128, N = kTcCols, K = 8 each) from
 // operands split into TF32 parts (v = v_hi + v_lo, and three parts for the
 // large terms h_j and o_i, which makes them exact):
 //   K slots 0-7  (coordinate record, constant over the iteration):
