@@ -53,6 +53,26 @@ def test_nonfinite_input_sets_status(cov, ctx):
     assert ctx.device_status() == (cov.COV_OK, 0)   # read clears
 
 
+@pytest.mark.parametrize("T", [50, 2000])
+def test_stein_field_nonfinite_and_empty(cov, ctx, T):
+    """A NaN coordinate sets the non-finite status on both Stein paths (the
+    one-launch kernel up to T = 1024, the all-pairs kernel above); an empty
+    trajectory is an argument error."""
+    x = wl.random_points(T, 2, 5)
+    x[T // 2, 1] = np.nan
+    w, mu, sigma = (wl.f32_pair(v)[1] for v in wl.gmm_params(3, seed=2, d=2))
+    cov.cov_field_svgd(ctx, dev32(x), 0.05, gmm=(w, mu, sigma))
+    st, fl = ctx.device_status()
+    assert fl & cov.DEV_NONFINITE and st == cov.COV_ERR_NONFINITE
+    assert ctx.device_status() == (cov.COV_OK, 0)
+    xd = dev32(wl.random_points(4, 2, 1))
+    out = torch.empty_like(xd)
+    L = cov.load()
+    st = L.cov_field_svgd(ctx.h, ctypes.c_void_p(xd.data_ptr()), 0, 2, ctypes.c_void_p(xd.data_ptr()), None,
+                          ctypes.c_float(0.1), ctypes.c_void_p(out.data_ptr()), None)
+    assert st == cov.COV_ERR_INVALID_ARG
+
+
 @pytest.mark.parametrize("tensor_cores", [0, 1])
 @pytest.mark.parametrize("n_iter", [1, 4])
 def test_bounded_wait_gives_up_and_reports_timeout(cov, ctx, orc, n_iter, tensor_cores):
