@@ -82,6 +82,8 @@ struct AdjArgs {
     const float* cgam;
     int col_ld;
     int n_cols8, cols_per_split, splits;
+    int n_hi;    // row blocks with `splits` splits; the others have splits - 1 of cps_lo columns
+    int cps_lo;
     float* part;
     int part_ld;
     unsigned* counters;
@@ -317,7 +319,21 @@ __global__ void __launch_bounds__(kAThreads) adj_kernel(const __grid_constant__ 
     const int segi = ((int)blockIdx.x >= L.ctas0) ? 1 : 0;
     const AdjArgs& a = segi ? L.seg[1] : L.seg[0];
     const int lb = (int)blockIdx.x - (segi ? L.ctas0 : 0);
-    const int rb = lb / a.splits, sp = lb % a.splits;
+    // this CTA's row block, split index, the row block's split count and its
+    // columns (a plan may give some row blocks one split fewer)
+    int rb, sp, ns, cps;
+    if (lb < a.n_hi * a.splits) {
+        rb = lb / a.splits;
+        sp = lb % a.splits;
+        ns = a.splits;
+        cps = a.cols_per_split;
+    } else {
+        const int l2 = lb - a.n_hi * a.splits;
+        ns = a.splits - 1;
+        rb = a.n_hi + l2 / ns;
+        sp = l2 % ns;
+        cps = a.cps_lo;
+    }
     const int row0 = rb * RB;
 
     if (threadIdx.x == 0) {
@@ -347,8 +363,8 @@ __global__ void __launch_bounds__(kAThreads) adj_kernel(const __grid_constant__ 
 #pragma unroll
         for (int k = 0; k < NACC; ++k) acc[r][k] = make_float2(0.f, 0.f);
 
-    const int c0 = sp * a.cols_per_split;
-    const int c1 = min(c0 + a.cols_per_split, a.n_cols8);
+    const int c0 = sp * cps;
+    const int c1 = min(c0 + cps, a.n_cols8);
     const int n_tiles = c1 > c0 ? (c1 - c0 + kATile - 1) / kATile : 0;
     __syncthreads();
 
@@ -427,7 +443,7 @@ __global__ void __launch_bounds__(kAThreads) adj_kernel(const __grid_constant__ 
             tot[k] = v;
         }
         const int i = row0 + q;
-        if (a.splits == 1) {
+        if (ns == 1) {
             adj_epilogue<D, KIND>(a, i, tot);
         } else {
             float* P = a.part + (size_t)sp * a.part_ld + i;
@@ -436,13 +452,13 @@ __global__ void __launch_bounds__(kAThreads) adj_kernel(const __grid_constant__ 
             for (int k = 0; k < NACC; ++k) P[k * cs] = tot[k];
         }
     }
-    if (a.splits == 1) return;
+    if (ns == 1) return;
 
     // ---- last CTA of this row block merges the splits ------------------------
     __syncthreads();
     if (threadIdx.x == 0) {
         const unsigned prev = ticket_add(&a.counters[rb], 1u);
-        s_last = (prev == (unsigned)(a.splits - 1));
+        s_last = (prev == (unsigned)(ns - 1));
     }
     __syncthreads();
     if (!s_last) return;
@@ -453,11 +469,11 @@ __global__ void __launch_bounds__(kAThreads) adj_kernel(const __grid_constant__ 
 #pragma unroll
         for (int k = 0; k < NACC; ++k) tot[k] = 0.f;
         // splits in groups of 8, all loads of a group in flight together
-        for (int p0 = 0; p0 < a.splits; p0 += 8) {
+        for (int p0 = 0; p0 < ns; p0 += 8) {
             float v[8][NACC];
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
-                const bool live = p0 + u < a.splits;
+                const bool live = p0 + u < ns;
                 const float* P = a.part + (size_t)(live ? p0 + u : 0) * a.part_ld + i;
 #pragma unroll
                 for (int k = 0; k < NACC; ++k) v[u][k] = live ? ld_cg(P + k * cs) : 0.f;
@@ -533,15 +549,29 @@ static int adj_nacc(int kind, int d) {
     return kind == A_COL ? d + 1 : (kind == A_MOM ? 1 + d + d * (d + 1) / 2 : 1 + 2 * d);
 }
 
+// Exact one-wave plans (fill_plan) for the reverse kernel (build flag
+// -DCOV_ADJ_FILL=0 keeps the uniform plan).
+#ifndef COV_ADJ_FILL
+#define COV_ADJ_FILL 1
+#endif
+
+// Uniform split plan; when it is one wave that already fills at least half
+// of `slots`, re-planned to fill them exactly (as the forward kernel does).
 static void adj_plan(AdjArgs& a, int n_cols, int RB, int slots, unsigned* counters) {
     const SplitPlan pl = plan_splits(a.n_rows, n_cols, RB, slots);
     a.n_cols8 = (int)round_up((size_t)n_cols, 8);
     a.cols_per_split = pl.cols_per_split;
     a.splits = pl.splits;
     a.n_rb = pl.n_rb;
+    a.n_hi = pl.n_rb;
+    a.cps_lo = pl.cols_per_split;
     a.part_ld = pl.n_rb * RB;
     a.counters = counters;
+    const long long ctas = (long long)a.n_rb * a.splits;
+    if (COV_ADJ_FILL && ctas <= slots && 2 * ctas >= slots && slots > a.n_rb) fill_plan(a, n_cols, slots, 8, kATile / 8);
 }
+
+static int adj_ctas(const AdjArgs& a) { return a.n_hi * a.splits + (a.n_rb - a.n_hi) * (a.splits - 1); }
 
 // One or two passes of one kind in a single grid (as run_pairs in field.cu).
 static cov_status run_adj(cov_ctx* ctx, int d, int kind, AdjArgs* seg, const int* n_cols, int nseg,
@@ -555,7 +585,7 @@ static cov_status run_adj(cov_ctx* ctx, int d, int kind, AdjArgs* seg, const int
         adj_plan(seg[0], n_cols[0], RB, slots, counters);
         L.seg[0] = seg[0];
         L.seg[1] = seg[0];
-        L.ctas0 = seg[0].n_rb * seg[0].splits;
+        L.ctas0 = adj_ctas(seg[0]);
     } else {
         const double w0 = (double)seg[0].n_rows * n_cols[0], w1 = (double)seg[1].n_rows * n_cols[1];
         int s0 = (int)llround(slots * w0 / (w0 + w1));
@@ -566,9 +596,9 @@ static cov_status run_adj(cov_ctx* ctx, int d, int kind, AdjArgs* seg, const int
         seg[1].part = seg[0].part + (size_t)adj_nacc(kind, d) * seg[0].splits * seg[0].part_ld;
         L.seg[0] = seg[0];
         L.seg[1] = seg[1];
-        L.ctas0 = seg[0].n_rb * seg[0].splits;
+        L.ctas0 = adj_ctas(seg[0]);
     }
-    const int total = L.ctas0 + (nseg == 2 ? seg[1].n_rb * seg[1].splits : 0);
+    const int total = L.ctas0 + (nseg == 2 ? adj_ctas(seg[1]) : 0);
     const cudaError_t e = adj_launch(d, kind, L, total, st, nullptr);
     return cuda_failed(ctx, e) ? COV_ERR_CUDA : COV_OK;
 }

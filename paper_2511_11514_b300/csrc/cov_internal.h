@@ -200,6 +200,36 @@ struct SplitPlan {
 SplitPlan plan_splits(int n_rows, int n_cols, int rows_per_cta, int slots, int unit = 8, int fixed = 64,
                       int max_waves = 2);
 
+// A one-wave plan that uses exactly `budget` CTAs: every row block gets s or
+// s + 1 column splits (the first n_hi row blocks s + 1), so that with budget
+// = resident capacity every SM holds the same number of CTAs of nearly the
+// same work.  (With a uniform split count the grid falls short of the
+// capacity, and the SMs that hold a full complement finish last.)  Seg has
+// the fields n_rb, splits, n_hi, cols_per_split, cps_lo.  With few splits
+// per row block, s and s + 1 splits differ too much in work per CTA
+// (measured slower for s = 1); with fewer than min_units planning units per
+// split, rounding would leave whole CTAs without columns: the uniform plan
+// is kept then.
+template <class Seg>
+inline void fill_plan(Seg& a, int n_cols, int budget, int unit, int min_units) {
+    const int units = (n_cols + unit - 1) / unit;
+    const long long total = (long long)budget < (long long)a.n_rb * units ? (long long)budget : (long long)a.n_rb * units;
+    const int s = (int)(total / a.n_rb);
+    const int extra = (int)(total - (long long)s * a.n_rb);
+    if (s < 3 || units / (s + 1) < min_units) return;
+    if (extra == 0) {
+        a.splits = s;
+        a.n_hi = a.n_rb;
+        a.cols_per_split = (units + s - 1) / s * unit;
+        a.cps_lo = a.cols_per_split;
+    } else {
+        a.splits = s + 1;
+        a.n_hi = extra;
+        a.cols_per_split = (units + s) / (s + 1) * unit;
+        a.cps_lo = (units + s - 1) / s * unit;
+    }
+}
+
 // GMM descriptor passed by value to kernels.
 struct GmmParams {
     int K;

@@ -1158,32 +1158,8 @@ static void plan_segment(PairArgs& a, int n_cols, int RB, int slots, unsigned* c
     a.counters = counters;
 }
 
-// A one-wave plan that uses exactly `budget` CTAs: every row block gets s or
-// s + 1 column splits (the first n_hi row blocks s + 1), so that with budget
-// = resident capacity every SM holds the same number of CTAs of nearly the
-// same work.  (With a uniform split count the grid falls short of the
-// capacity, and the SMs that hold a full complement finish last.)
-static void fill_segment(PairArgs& a, int n_cols, int budget, int unit) {
-    const int units = (n_cols + unit - 1) / unit;
-    const long long total = std::min<long long>(budget, (long long)a.n_rb * units);
-    const int s = (int)(total / a.n_rb);
-    const int extra = (int)(total - (long long)s * a.n_rb);
-    // with few splits per row block, s and s + 1 splits differ too much in
-    // work per CTA (measured slower for s = 1); with few columns per split,
-    // rounding would leave whole CTAs without columns: keep the uniform plan
-    if (s < 3 || units / (s + 1) < kTile / unit) return;
-    if (extra == 0) {
-        a.splits = s;
-        a.n_hi = a.n_rb;
-        a.cols_per_split = (units + s - 1) / s * unit;
-        a.cps_lo = a.cols_per_split;
-    } else {
-        a.splits = s + 1;
-        a.n_hi = extra;
-        a.cols_per_split = (units + s) / (s + 1) * unit;
-        a.cps_lo = (units + s - 1) / s * unit;
-    }
-}
+// The exact one-wave plan (fill_plan, cov_internal.h) in this kernel's tiles.
+static void fill_segment(PairArgs& a, int n_cols, int budget, int unit) { fill_plan(a, n_cols, budget, unit, kTile / unit); }
 
 static int seg_ctas(const PairArgs& a) { return a.n_hi * a.splits + (a.n_rb - a.n_hi) * (a.splits - 1); }
 
