@@ -40,6 +40,11 @@ struct LqrConst {
     double R[COV_MAX_M * COV_MAX_M];
 };
 
+// Cost of one launch in the scan planners' models (us; build flag).
+#ifndef COV_SCAN_LAUNCH_US
+#define COV_SCAN_LAUNCH_US 1.5
+#endif
+
 constexpr int kSB = 32;          // steps per streamed sub-block
 constexpr int kMaxChunk = 512;   // steps per scan chunk
 constexpr int kMaxChunks = 1024; // scan chunks
@@ -1891,7 +1896,7 @@ static int scan_chunk_cap(int T) {
 // chunk levels also pay the FP64 pipe time of the warps sharing an SM
 // (~N and ~N + 1 FP64 warp-instructions per step at ~9.4 ns each).
 constexpr double kScanComposeUs = 0.25, kScanFillUs = 0.38, kScanGroupUs = 0.3, kScanChainUs = 0.2,
-                 kScanLaunchUs = 1.5, kScanComposeWarpUs = 0.037, kScanFillWarpUs = 0.047;
+                 kScanLaunchUs = COV_SCAN_LAUNCH_US, kScanComposeWarpUs = 0.037, kScanFillWarpUs = 0.047;
 constexpr int kScanSms = 148;  // SMs the cost model assumes
 
 static bool scan_plan_search(int T, ScanPlan* p) {
@@ -1985,7 +1990,7 @@ static size_t ric_scratch_maps(int T) { return (size_t)2 * ric_chunk_cap(T) + kR
 // composition step and ~26 per Riccati step.)
 constexpr double kRicComposeNs = 1300, kRicComposeWarpNs = 190;
 constexpr double kRicStepNs = 1450, kRicStepWarpNs = 245;
-constexpr double kRicGroupNs = 1200, kRicChainNs = 1150, kRicLaunchNs = 1500;
+constexpr double kRicGroupNs = 1200, kRicChainNs = 1150, kRicLaunchNs = COV_SCAN_LAUNCH_US * 1000;
 
 // Serial cost of chaining nc1 chunk maps through `depth` grouping levels of
 // (about) equal group size g: each level composes g maps (group) and later
