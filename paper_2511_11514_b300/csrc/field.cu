@@ -377,8 +377,22 @@ struct PairLaunch {
 __device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void grid_dep_launch() { asm volatile("griddepcontrol.launch_dependents;" :::); }
 
+// Resident CTAs per SM the weighted (barycentre) modes are compiled for
+// (build flag; 1 leaves the register count to the compiler).
+#ifndef COV_BARY_MINB
+#define COV_BARY_MINB 1
+#endif
+// Rows per thread of the weighted modes (build flag; 0: the context's setting).
+#ifndef COV_BARY_R
+#define COV_BARY_R 0
+#endif
+template <int MODE>
+struct PairMinBlocks {
+    static constexpr int value = (MODE == M_WY || MODE == M_WX || MODE == M_GW) ? COV_BARY_MINB : 1;
+};
+
 template <int D, int R, int MODE>
-__global__ void __launch_bounds__(kThreads) pairs_kernel(const __grid_constant__ PairLaunch L) {
+__global__ void __launch_bounds__(kThreads, PairMinBlocks<MODE>::value) pairs_kernel(const __grid_constant__ PairLaunch L) {
     using TR = PairTraits<D, MODE>;
     constexpr int NC = TR::NC;
     constexpr int NACC = TR::NACC;
@@ -1173,7 +1187,9 @@ static cov_status run_pairs(cov_ctx* ctx, int d, int family, PairArgs* seg, cons
     // tensor cores (128-row CTAs, 128-column tiles)
     bool tc = family == M_GO && ctx->use_tc && d <= 3;
     for (int k = 0; k < nseg; ++k) tc = tc && seg[k].fixed && seg[k].rec0 && seg[k].rech;
-    const int R = effective_R(d, ctx->rows_per_thread);
+    // the weighted (barycentre) passes may take another row count per thread (build flag)
+    const bool weighted = family == M_WY || family == M_WX || family == M_GW;
+    const int R = effective_R(d, (weighted && COV_BARY_R > 0) ? COV_BARY_R : ctx->rows_per_thread);
     const int RB = tc ? kTcRows : 32 * R;
     const int unit = tc ? kTcCols : 8;
     const int fixed_cost = tc ? 2 * kTcCols : 64;
