@@ -242,6 +242,21 @@ def calibrate(inst, seconds):
     return max(T, M), max(1, int(round(seconds / max(dt_two / 2, 1e-9))))
 
 
+def host_cpu():
+    """The host's processor model (/proc/cpuinfo) and hardware thread count,
+    reported beside every oracle timing."""
+    model = "unknown"
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if line.startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return {"cpu_model": model, "hardware_threads": os.cpu_count() or 1}
+
+
 def cpu_baseline(inst, seconds, single_thread_seconds=None):
     """The FP64 oracle's pair-evaluation rate on a bounded sample of the
     workload (rows of each Sinkhorn update, or whole iterations when they
@@ -264,7 +279,7 @@ def cpu_baseline(inst, seconds, single_thread_seconds=None):
             f"{iters} full Sinkhorn iterations (g over T={T}, f over M={M}, p over T)")
     w = inst.wl
     rate = pairs / dt
-    out = {"value": rate, "unit": UNIT, "cores": orc.get_threads(), "kind": "oracle",
+    out = {"value": rate, "unit": UNIT, "cores": orc.get_threads(), "kind": "oracle", **host_cpu(),
            "sample": f"FP64 oracle: {what} of the workload from its initial trajectory, {pairs:.3e} pair "
                      f"evaluations in {dt:.1f} s, {orc.get_threads()} threads",
            "extrapolated": {"ms_per_step": w.pairs_per_field / rate * 1e3,
@@ -326,7 +341,7 @@ def run_reference(args):
             "impl": "reference",
             "config": workload_config(w, {"sample_rows_per_update": rows, "sample_iterations": iters,
                                           "precision": "f64 throughout (the oracle)"}),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": orc.get_threads(), "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": orc.get_threads(), "kind": "oracle", **host_cpu(),
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -844,7 +859,7 @@ def run_svgd(args, w, rank, local_rank, world):
             orc.solve(w.model, w.dt, inst.s0, inst.u0, w.field, inst.Q, inst.R, w.eta, w.n_outer, gmm=gmm, h=w.h)
             dt = time.perf_counter() - t0
             line["cpu_baseline"] = {"value": w.n_outer * pairs_step / dt, "unit": UNIT, "cores": orc.get_threads(),
-                                    "kind": "oracle",
+                                    "kind": "oracle", **host_cpu(),
                                     "sample": f"FP64 oracle: the whole coverage solve ({w.n_outer} outer "
                                               f"iterations) in {dt:.2f} s, {orc.get_threads()} threads",
                                     "ms_per_coverage_solve": dt * 1e3}
@@ -1262,7 +1277,7 @@ def run_horizon_sweep(args):
     ctx.close()
     line = {"metric": "coverage solve time vs horizon, GPU vs FP64 oracle (context)", "value": None, "unit": "ms",
             "higher_is_better": False, "n_gpus": 1, "dtype": "f32 fields, f64 LQR/rollout",
-            "data": "synthetic (seeded Philox mixtures)", "cpu_cores": orc.get_threads(), "points": points}
+            "data": "synthetic (seeded Philox mixtures)", "cpu_cores": orc.get_threads(), **host_cpu(), "points": points}
     print(json.dumps(line), flush=True)
     return 0
 

@@ -30,6 +30,7 @@ def test_reference_arm_prints_one_contract_line():
     assert d["config"]["workload"] == "sinkhorn_unicycle_T65536_M262144"
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["cpu_baseline"]["value"] == d["value"]
+    assert d["cpu_baseline"]["cpu_model"] and d["cpu_baseline"]["hardware_threads"] >= 1
     e = d["e2e"]
     assert e["value"] == d["value"] and e["unit"] == d["unit"]
     assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
