@@ -118,8 +118,10 @@ def test_full_shape_batch_of_1024_problems_against_oracle(cov, ctx, orc):
     """The batched workload at full shape: 1024 double-integrator problems,
     T ~ U{128..4096}, M ~ U{512..16384}, 2-16 component mixtures, half Stein
     and half Sinkhorn (eps = 0.005, 50 iterations), one outer iteration of all
-    of them in one graph launch; the first Stein problem, the smallest and
-    the largest Sinkhorn problem are checked against the FP64 oracle."""
+    of them in one graph launch; the first and the longest Stein problem (the
+    one-launch Stein field and, past T = 1024, the all-pairs one), the
+    smallest and the largest Sinkhorn problem are checked against the FP64
+    oracle."""
     insts = wl.make_batch(1024)
     ys = [dev32(i.y) if i.y is not None else None for i in insts]
     probs = [_problem(cov, i, y) for i, y in zip(insts, ys)]
@@ -131,7 +133,8 @@ def test_full_shape_batch_of_1024_problems_against_oracle(cov, ctx, orc):
         assert c.device_status() == (cov.COV_OK, 0)
         sk = [k for k, i in enumerate(insts) if i.wl.field == wl.FIELD_SINKHORN]
         cost = {k: insts[k].wl.T * (insts[k].wl.M + insts[k].wl.T) for k in sk}
-        picks = [0, min(sk, key=cost.get), max(sk, key=cost.get)]
+        sv = [k for k, i in enumerate(insts) if i.wl.field == wl.FIELD_SVGD]
+        picks = [sv[0], max(sv, key=lambda k: insts[k].wl.T), min(sk, key=cost.get), max(sk, key=cost.get)]
         for k in picks:
             _check_against_oracle(orc, insts[k], ss[k], us[k], 1e-4)
     finally:
