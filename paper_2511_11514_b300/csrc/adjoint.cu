@@ -554,6 +554,10 @@ static int adj_nacc(int kind, int d) {
 #ifndef COV_ADJ_FILL
 #define COV_ADJ_FILL 1
 #endif
+// Fewest 8-column units per split the re-plan may leave (build flag; default one tile).
+#ifndef COV_ADJ_FILL_MIN_UNITS
+#define COV_ADJ_FILL_MIN_UNITS (kATile / 8)
+#endif
 
 // Uniform split plan; when it is one wave that already fills at least half
 // of `slots`, re-planned to fill them exactly (as the forward kernel does).
@@ -568,7 +572,8 @@ static void adj_plan(AdjArgs& a, int n_cols, int RB, int slots, unsigned* counte
     a.part_ld = pl.n_rb * RB;
     a.counters = counters;
     const long long ctas = (long long)a.n_rb * a.splits;
-    if (COV_ADJ_FILL && ctas <= slots && 2 * ctas >= slots && slots > a.n_rb) fill_plan(a, n_cols, slots, 8, kATile / 8);
+    if (COV_ADJ_FILL && ctas <= slots && 2 * ctas >= slots && slots > a.n_rb)
+        fill_plan(a, n_cols, slots, 8, COV_ADJ_FILL_MIN_UNITS);
 }
 
 static int adj_ctas(const AdjArgs& a) { return a.n_hi * a.splits + (a.n_rb - a.n_hi) * (a.splits - 1); }
