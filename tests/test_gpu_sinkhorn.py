@@ -205,6 +205,24 @@ def test_full_size_unicycle_density_workload_warm_update(cov, ctx, orc, unicycle
     assert errs[3] <= FIELD_TOL, errs
 
 
+def test_full_size_field_is_permutation_equivariant(cov, ctx, unicycle_density_inputs):
+    """A property that holds at any size, checked on the whole field at
+    T = 65536, M = 262144 and 100 iterations on the default path: relabelling
+    the reference samples leaves the field unchanged and relabelling the
+    trajectory points relabels it (each within the field's parity bar; the
+    sums run in another order)."""
+    x, y, w = unicycle_density_inputs
+    xd, yd = dev32(x), dev32(y)
+    a = host(cov.cov_field_sinkhorn(ctx, xd, yd, w.eps, w.n_iter)[0])
+    rng = np.random.default_rng(11)
+    px, py = rng.permutation(len(x)), rng.permutation(len(y))
+    a_y = host(cov.cov_field_sinkhorn(ctx, xd, dev32(y[py]), w.eps, w.n_iter)[0])
+    assert rel_norm(a_y, a) <= FIELD_TOL
+    a_x = host(cov.cov_field_sinkhorn(ctx, dev32(x[px]), yd, w.eps, w.n_iter)[0])
+    assert rel_norm(a_x, a[px]) <= FIELD_TOL
+    assert ctx.device_status()[1] == 0
+
+
 def test_repeated_calls_are_bitwise_identical(cov, ctx):
     """Column splits are merged in split order (no float atomics), so the
     same inputs give the same bits, at a size with 30+ splits per row block."""

@@ -29,6 +29,23 @@ def test_svgd_field_with_mixture_score(cov, ctx, orc, T, d, K):
     assert ctx.device_status()[1] == 0
 
 
+@pytest.mark.parametrize("T", [700, 4099])
+def test_svgd_field_permutation_and_rotation_equivariance(cov, ctx, T):
+    """Both Stein paths (one launch at T = 700, all pairs at T = 4099):
+    relabelled points give the relabelled field, and rotating the points and
+    the mixture's means together rotates it (within FP32 rounding)."""
+    w, mu, sigma = (wl.f32_pair(v)[1] for v in wl.gmm_params(5, seed=T, d=2))
+    x = wl.random_points(T, 2, seed=T + 1)
+    gmm = (w, mu, sigma)
+    a = host(cov.cov_field_svgd(ctx, dev32(x), 0.05, gmm=gmm))
+    perm = np.random.default_rng(T).permutation(T)
+    assert rel_norm(host(cov.cov_field_svgd(ctx, dev32(x[perm]), 0.05, gmm=gmm)), a[perm]) <= 1e-5
+    R = np.array([[0.6, -0.8], [0.8, 0.6]])  # exact in binary to a few ulps
+    a_r = host(cov.cov_field_svgd(ctx, dev32(x @ R.T), 0.05, gmm=(w, mu @ R.T, sigma)))
+    assert rel_norm(a_r, a @ R.T) <= 1e-4
+    assert ctx.device_status()[1] == 0
+
+
 @pytest.mark.parametrize("T,d", [(5, 2), (777, 2), (2500, 3)])
 def test_svgd_field_with_given_score(cov, ctx, orc, T, d):
     x = wl.random_points(T, d, seed=1)

@@ -289,3 +289,30 @@ def test_fixed_iteration_divergence_converges_to_the_divergence(orc):
     conv = orc.sinkhorn_divergence(x, y, None, eps, tol=1e-14)
     assert orc.sinkhorn_divergence_iter(x, y, eps, 3000) == pytest.approx(conv, rel=1e-9, abs=1e-12)
     assert abs(orc.sinkhorn_divergence_iter(x, x, eps, 3000)) <= 1e-10
+
+
+def test_permutation_and_rotation_equivariance(orc):
+    """Relabelling the trajectory points permutes f, p and the field;
+    relabelling the reference samples permutes g and changes nothing else;
+    rotating both point sets by the same orthogonal map (the squared
+    distance is rotation invariant) leaves the potentials and rotates the
+    field (would catch a transposed operand or a swapped index)."""
+    x = wl.random_points(10, 2, seed=21)
+    y = wl.random_points(13, 2, seed=22)
+    eps, n = 0.03, 7
+    f, g, p = orc.sinkhorn(x, y, None, eps, n)
+    a = orc.sinkhorn_field(x, y, None, eps, g, p)
+    rng = np.random.default_rng(3)
+    px, py = rng.permutation(10), rng.permutation(13)
+    f2, g2, p2 = orc.sinkhorn(x[px], y[py], None, eps, n)
+    np.testing.assert_allclose(f2, f[px], atol=1e-12)
+    np.testing.assert_allclose(g2, g[py], atol=1e-12)
+    np.testing.assert_allclose(p2, p[px], atol=1e-12)
+    np.testing.assert_allclose(orc.sinkhorn_field(x[px], y[py], None, eps, g2, p2), a[px], atol=1e-12)
+    th = 0.7
+    R = np.array([[np.cos(th), -np.sin(th)], [np.sin(th), np.cos(th)]])
+    f3, g3, p3 = orc.sinkhorn(x @ R.T, y @ R.T, None, eps, n)
+    np.testing.assert_allclose(f3, f, atol=1e-10)
+    np.testing.assert_allclose(g3, g, atol=1e-10)
+    np.testing.assert_allclose(p3, p, atol=1e-10)
+    np.testing.assert_allclose(orc.sinkhorn_field(x @ R.T, y @ R.T, None, eps, g3, p3), a @ R.T, atol=1e-10)

@@ -259,3 +259,22 @@ def test_svgd_with_mixture_score_vjp_is_the_total_derivative(orc):
     np.testing.assert_allclose(mubar, _fd(lambda v: L(x, w, v, sigma), mu), rtol=1e-6, atol=1e-6)
     np.testing.assert_allclose(sigbar, _fd(lambda v: L(x, w, mu, v), sigma), rtol=1e-6, atol=1e-5)
     np.testing.assert_allclose(wbar, _fd(lambda v: L(x, v, mu, sigma), w), rtol=1e-6, atol=1e-6)
+
+
+def test_svgd_permutation_and_rotation_equivariance(orc):
+    """The Stein field of relabelled points is the relabelled field; rotating
+    the points and the mixture's means together (isotropic components) rotates
+    the score and the field (would catch a swapped i/j or a transposed
+    coordinate in either)."""
+    w, mu, sigma = wl.gmm_params(4, seed=8, d=2)
+    x = wl.random_points(12, 2, seed=9)
+    h = 0.1
+    a = orc.svgd_field(x, orc.gmm_score(x, w, mu, sigma), h)
+    perm = np.random.default_rng(4).permutation(12)
+    np.testing.assert_allclose(orc.svgd_field(x[perm], orc.gmm_score(x[perm], w, mu, sigma), h), a[perm],
+                               atol=1e-12)
+    th = -1.1
+    R = np.array([[np.cos(th), -np.sin(th)], [np.sin(th), np.cos(th)]])
+    sc_r = orc.gmm_score(x @ R.T, w, mu @ R.T, sigma)
+    np.testing.assert_allclose(sc_r, orc.gmm_score(x, w, mu, sigma) @ R.T, atol=1e-9)
+    np.testing.assert_allclose(orc.svgd_field(x @ R.T, sc_r, h), a @ R.T, atol=1e-9)
